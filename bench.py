@@ -1,0 +1,384 @@
+"""Benchmark of the BAE hot path on GB300.
+
+Workload (default): modified Helmholtz kappa^2 = 10 on the torus R = 0.5,
+r = 0.2 in [-1,1]^3, N = 128 (h = 1/64), u = sin(2x) cos(y) exp(z), double
+layer, GMRES tolerance 1e-10. One step = one full solve of Algorithm 1 for
+that problem: classification from phi (the LGF spectrum per (N, kappa^2 h^2)
+is cached by the context, as the numerical section reuses tables), the
+particular solution, the GMRES solve with float32 convolutions inside float64
+iterative refinement, and the volume reconstruction. Inputs are synthetic
+and resident in device memory; the L2 cache is flushed between steps.
+
+Prints one JSON line (rank 0). `--impl reference` times the CPU oracle on
+the host cores instead. Multi-GPU (torchrun): independent replicas, one
+problem per rank, no collective on the data path ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BAE solves/s + p50/p99 latency at 1e-8 err; LGF-conv GB/s vs HBM peak"
+UNIT = "solves/s"
+TOL = 1e-10
+N = 128
+KAPPA2 = 10.0
+WORKLOAD = "torus R=0.5 r=0.2, kappa^2=10, N=128 (h=1/64), double layer, GMRES tol 1e-10"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.device)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = max(smax, float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------ roofline arithmetic
+def kernel_model(n, pb, n_gm):
+    """Algorithmic (bytes, flops) of one launch of each convolution pass for
+    one right-hand side at grid size n, element precision pb bytes (complex
+    = 2 pb). FFT flops use the 5 L log2 L convention per complex transform
+    of length L = 2n; the spectral multiply counts 2 flops per element."""
+    c = 2 * pb
+    L = 2 * n
+    n1 = n + 1
+    A = n * n * n1 * c
+    B = 2 * n * n * n1 * c
+    F = 5.0 * L * math.log2(L)
+    src = 8 * n_gm + 4 * (n * n + 1)
+    return {
+        "conv_kfwd": (A + src, (n * n / 2) * F),
+        "conv_jfwd": (A + B, n * n1 * F),
+        "conv_i": (2 * B + n1 ** 3 * pb, 2 * (2 * n * n1) * F + 2.0 * (2 * n * n1) * L),
+        "conv_jinv": (A + B, n * n1 * F),
+        "conv_kinv": (A + n ** 3 * pb, (n * n / 2) * F),
+    }
+
+
+FP64_PEAK_TFLOPS = 1.25   # nominal FP64 rate of GB300
+
+
+def roofline_for(name, ms_total, launches, n_gm, hbm, hbm_kind):
+    base, _, prec = name.partition(".")
+    model = kernel_model(N, 4 if prec == "f32" else 8, n_gm)
+    if base not in model:
+        return None
+    nbytes, flops = model[base]
+    t = (ms_total / launches) / 1000.0
+    if prec == "f64":
+        a = flops / t / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": a, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": a / FP64_PEAK_TFLOPS, "traffic": None, "peak_kind": "nominal FP64 (recipe table)",
+                "us_per_launch": t * 1e6, "algorithmic_flops": flops}
+    a = nbytes / t / 1e9
+    return {"kernel": name, "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
+            "traffic": None, "peak_kind": hbm_kind + " HBM copy bandwidth", "us_per_launch": t * 1e6,
+            "algorithmic_bytes": nbytes}
+
+
+def _flush_l2(buf):
+    buf.add_(1.0)
+
+
+def _problem_inputs(P, torch, dev):
+    phi = torch.from_numpy(P.phi).to(dev)
+    f = torch.from_numpy(P.f()).to(dev)
+    return phi, f
+
+
+def run_ours(args, rank, world, dev):
+    import torch
+    import workloads as W
+    from paper_2502_05507_gb300 import Context, Problem, launch_count, profile_start, profile_stop
+
+    torch.cuda.set_device(dev)
+    P = W.torus_helmholtz(N, kappa2=KAPPA2)
+    ctx = Context(dev)
+    phi, f = _problem_inputs(P, torch, dev)
+    prob0 = Problem(ctx, phi, P.grid.h, P.grid.origin, P.kappa2, "double")
+    xs = prob0.boundary_points()
+    g = torch.from_numpy(P.g_at(xs)).to(dev)
+    n_gm = prob0.n_gm
+    prob0.close()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+
+    def step(precision):
+        pr = Problem(ctx, phi, P.grid.h, P.grid.origin, P.kappa2, "double")
+        q, u, st = pr.solve(f, g, tol=TOL, precision=precision)
+        pr.close()
+        return q, u, st
+
+    torch.cuda.set_stream(ctx.stream)   # events, flushes and library work share one stream
+    for _ in range(max(args.warmup, 0)):
+        step(args.precision)
+    torch.cuda.synchronize()
+
+    # ---------------------------------------------------------- timed region
+    clocks = ClockSampler(dev)
+    clocks.start()
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    l0 = launch_count()
+    profile_start(400000)
+    stats = []
+    for k in range(args.steps):
+        _flush_l2(flush)
+        e0[k].record()
+        q, u, st = step(args.precision)
+        e1[k].record()
+        stats.append(st)
+    torch.cuda.synchronize()
+    prof = profile_stop()
+    l1 = launch_count()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ms = np.array([a.elapsed_time(b) for a, b in zip(e0, e1)])
+    total_ms = float(ms.sum())
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    solves = args.steps * world
+    value = solves / (total_ms / 1000.0)
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": float(ms.mean()), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32 conv + f64 refinement" if args.precision == "mixed"
+           else "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "precision": args.precision, "l2": "flushed between steps (256 MB write)",
+                      "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+           "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)),
+                          "min": float(ms.min()), "max": float(ms.max())},
+           "solve": {"iterations": int(stats[-1]["iterations"]), "refinements": int(stats[-1]["refinements"]),
+                     "applies_fp32": int(stats[-1]["applies_fp32"]), "applies_fp64": int(stats[-1]["applies_fp64"]),
+                     "rel_residual": stats[-1]["rel_residual"], "n_gm": n_gm},
+           "gpu_launches": int(l1 - l0), "clocks": clk}
+    if rank != 0:
+        ctx.close()
+        return None
+
+    # ------------------------------------------------------ kernel roofline
+    hbm, hbm_kind = _peaks()
+    kt = sorted(prof.items(), key=lambda kv: -kv[1][0])
+    tot = sum(v[0] for v in prof.values())
+    out["kernels"] = [{"name": k, "ms_total": round(v[0], 3), "launches": v[1],
+                       "share": round(v[0] / tot, 4) if tot else None} for k, v in kt[:14]]
+    dom = next((k for k, _ in kt if k.startswith("conv_")), None)
+    out["roofline"] = roofline_for(dom, prof[dom][0], prof[dom][1], n_gm, hbm, hbm_kind) if dom else None
+    # the float32 i-pass (forward FFT, ghat multiply, inverse FFT) inside the timed region
+    if "conv_i.f32" in prof:
+        out["conv_f32_roofline"] = roofline_for("conv_i.f32", *prof["conv_i.f32"], n_gm, hbm, hbm_kind)
+    # whole float32 apply: algorithmic bytes of the five passes / their summed time
+    per = [prof.get(k) for k in ("conv_kfwd.f32", "conv_jfwd.f32", "conv_i.f32", "conv_jinv.f32", "conv_kinv.f32")]
+    if all(per):
+        m = kernel_model(N, 4, n_gm)
+        nb = sum(v[0] for v in m.values())
+        t_apply = sum(p[0] / p[1] for p in per) / 1000.0
+        out["conv_f32_apply"] = {"us": t_apply * 1e6, "algorithmic_bytes": nb, "GBps": nb / t_apply / 1e9,
+                                 "frac_hbm": nb / t_apply / 1e9 / hbm,
+                                 "note": "N=128 buffers fit in the 129 MB L2, so this can exceed HBM peak"}
+
+    # ---------------------------------------------- fp64 solve for comparison
+    step("fp64")
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    q64, u64, st64 = step("fp64")
+    t1.record()
+    torch.cuda.synchronize()
+    out["fp64_solve"] = {"solves_per_s": 1000.0 / t0.elapsed_time(t1), "iterations": st64["iterations"],
+                         "applies_fp64": st64["applies_fp64"]}
+    ud, uf = u.cpu().numpy(), u64.cpu().numpy()
+    out["err_mixed_vs_fp64"] = float(np.max(np.abs(ud - uf)) / np.max(np.abs(uf)))
+
+    # --------------------------------------------------------- e2e (host)
+    phi_h, f_h = P.phi, P.f()
+    g_h = P.g_at(xs.cpu().numpy() if hasattr(xs, "cpu") else xs)
+    e2e_ms = []
+    for k in range(min(args.steps, 8) + 1):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        pr = Problem(ctx, phi_h, P.grid.h, P.grid.origin, P.kappa2, "double")
+        qh, uh, sth = pr.solve(f_h, g_h, tol=TOL, precision=args.precision)
+        pr.close()
+        dt = time.perf_counter() - t
+        if k > 0:
+            e2e_ms.append(dt * 1000.0)
+    out["e2e"] = {"value": 1000.0 / float(np.mean(e2e_ms)), "unit": UNIT,
+                  "h2d_bytes_per_step": int(phi_h.nbytes + f_h.nbytes + g_h.nbytes),
+                  "d2h_bytes_per_step": int(qh.nbytes + uh.nbytes)}
+
+    # --------------------------------------------------------- cpu baseline
+    if world == 1 and not args.no_cpu:
+        out["cpu_baseline"], uo = cpu_oracle_solve(P)
+        m = np.abs(uo) > 0
+        out["err_vs_oracle"] = {"mixed": float(np.max(np.abs(ud[m] - uo[m])) / np.max(np.abs(uo[m]))),
+                                "fp64": float(np.max(np.abs(uf[m] - uo[m])) / np.max(np.abs(uo[m])))}
+    ctx.close()
+    return out
+
+
+def cpu_oracle_solve(P):
+    """The oracle (FFT route, float64 scipy.fft on every host core) solving
+    the same problem once; the LGF table is built beforehand and not timed
+    (the GPU side caches it too)."""
+    from oracle import lgf as OL
+    from oracle import potentials as OP
+    from oracle import solve as OS
+    cores = os.cpu_count() or 1
+    s = P.kappa2 * P.grid.h ** 2
+    t = time.perf_counter()
+    table = OL.LGFTable(P.grid.N, s)
+    spec = OP.lgf_spectrum(table)
+    t_table = time.perf_counter() - t
+    t = time.perf_counter()
+    r = OS.solve(P.phi, P.grid.h, P.grid.origin, P.f(), P.g_at, P.kappa2, layer="double", tol=TOL,
+                 potential="fft", spectrum=spec, workers=cores)
+    dt = time.perf_counter() - t
+    return ({"value": 1.0 / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+             "sample": f"one full oracle solve of the workload (FFT route, {r.iterations} GMRES iterations, "
+                       f"{dt:.1f} s); LGF table build ({t_table:.1f} s) excluded as cached"},
+            r.u)
+
+
+def run_reference(args):
+    """The oracle as the reference arm: each step is a bounded sample, one
+    oracle boundary-operator apply (the unit of a GMRES iteration);
+    solves/s = 1 / (mean apply time x applies per oracle solve), the apply
+    count taken from one untimed full oracle solve of the same workload."""
+    import workloads as W
+    from oracle import grid as OG
+    from oracle import lgf as OL
+    from oracle import potentials as OP
+    from oracle import solve as OS
+    cores = os.cpu_count() or 1
+    P = W.torus_helmholtz(N, kappa2=KAPPA2)
+    s = P.kappa2 * P.grid.h ** 2
+    spec = OP.lgf_spectrum(OL.LGFTable(N, s))
+    full = OS.solve(P.phi, P.grid.h, P.grid.origin, P.f(), P.g_at, P.kappa2, layer="double", tol=TOL,
+                    potential="fft", spectrum=spec, workers=cores)
+    applies = full.iterations + 2
+    cls = OG.classify(P.phi, P.grid.h, P.grid.origin)
+    q = np.random.default_rng(0).standard_normal(cls.gm_idx.size)
+
+    def apply_once():
+        v = OP.fft_convolve(OP.source_density(cls, q, "double"), spectrum=spec, workers=cores).reshape(-1)
+        return OS.closure_apply(cls, v)
+
+    for _ in range(args.warmup):
+        apply_once()
+    ts = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        apply_once()
+        ts.append(time.perf_counter() - t)
+    per_solve = float(np.mean(ts)) * applies
+    value = 1.0 / per_solve
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * per_solve, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "precision": "fp64 (oracle)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} oracle boundary applies (scipy.fft float64), scaled by "
+                                       f"{applies} applies per oracle solve"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)))
+        return
+    import torch
+    if world > 1:
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    out = run_ours(args, rank, world, local)
+    if rank == 0 and out is not None:
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

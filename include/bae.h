@@ -1,0 +1,214 @@
+/*
+ * bae.h - C ABI of the GB300 (sm_103a) unfitted boundary algebraic equation
+ * (BAE) solver with lattice Green's functions.
+ *
+ * Method: Xia, "Unfitted boundary algebraic equation method based on
+ * difference potentials and lattice Green's function in 3D". Equations are
+ * cited by their LaTeX labels in brackets, e.g. eq. [double_bae].
+ *
+ * Problem (Section 2, eq. [elliptic]):  -Lap u + kappa2 u = f in Omega,
+ * u = g on dOmega, kappa2 >= 0, Omega = {phi < 0} given by level-set samples
+ * on an N^3 Cartesian grid with spacing h. Node (i,j,k) sits at
+ * origin + (i,j,k) h; every N^3 array is C-order (k fastest).
+ *
+ * Conventions for every entry point:
+ *  - Return value: BAE_OK (0) or one of the BAE_ERR_* codes below; the
+ *    thread-local message of the last failure is bae_last_error(). No C++
+ *    exception crosses this boundary.
+ *  - Array arguments are plain pointers that may point to device memory of
+ *    the context's device or to host memory (pageable or pinned); the
+ *    library detects which (cudaPointerGetAttributes) and stages host arrays
+ *    through its own device buffers, copying on the context stream. The
+ *    caller owns every array it passes; the library never frees them.
+ *  - All work is issued on the context's stream. Entry points return after
+ *    the stream has finished the call's work (results are ready to read).
+ *  - Handles own their device memory; a problem must be destroyed before its
+ *    context. Handles are not thread-safe: one call at a time per handle.
+ *  - There is no CPU fallback: without a usable GPU every call that needs
+ *    one returns BAE_ERR_CUDA.
+ */
+#ifndef BAE_H
+#define BAE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ error codes */
+#define BAE_OK                 0
+#define BAE_ERR_INVALID_ARG    1  /* bad size, null pointer, non-finite input  */
+#define BAE_ERR_GEOMETRY       2  /* gamma- empty or touching the grid box faces */
+#define BAE_ERR_OOM            3  /* device allocation failed                   */
+#define BAE_ERR_NOT_CONVERGED  4  /* GMRES hit its limit; outputs still written */
+#define BAE_ERR_TIMEOUT        5  /* a bounded device wait ran out             */
+#define BAE_ERR_CUDA           6  /* any other CUDA failure                    */
+
+/* layer type of the indirect formulation (Section 3.2) */
+#define BAE_LAYER_DOUBLE 0     /* D(m,n), eq. [double_potential] (default)     */
+#define BAE_LAYER_SINGLE 1     /* S(m,n) = G(m-n), eq. [single_potential]      */
+
+/* arithmetic of the potential apply */
+#define BAE_FP64  0            /* every step in float64                        */
+#define BAE_MIXED 1            /* float32 convolution inside float64 iterative
+                                  refinement (solve only)                      */
+#define BAE_FP32  2            /* float32 convolution (apply entry points only)*/
+
+typedef struct bae_ctx bae_ctx;
+typedef struct bae_problem bae_problem;
+
+typedef struct bae_options {
+    double tol;          /* relative residual ||b - A q|| / ||b||, default 1e-10 */
+    int    max_iter;     /* total GMRES iterations (all cycles), default 500    */
+    int    restart;      /* GMRES restart length, default 200                   */
+    int    precision;    /* BAE_FP64 or BAE_MIXED, default BAE_FP64             */
+    int    max_refine;   /* outer refinement steps for BAE_MIXED, default 8     */
+    double inner_tol;    /* inner float32 GMRES reduction per step, default 1e-5 */
+} bae_options;
+
+typedef struct bae_stats {
+    int    iterations;       /* GMRES iterations, all cycles and refinement steps */
+    int    refinements;      /* outer refinement steps (BAE_MIXED), else 0        */
+    int    applies_fp64;     /* float64 potential applies in this call            */
+    int    applies_fp32;     /* float32 potential applies in this call            */
+    double rel_residual;     /* final ||b - A q|| / ||b||, A applied in float64   */
+    double ms_total;         /* wall time of the call on the context stream       */
+} bae_stats;
+
+/* ------------------------------------------------------------- utilities */
+
+/* ABI version, currently 1. */
+int bae_version(void);
+
+/* Message of the last failed call on this thread ("" if none). Owned by the
+ * library; valid until the next call on this thread. */
+const char* bae_last_error(void);
+
+/* Fills *opts with the defaults listed in bae_options. */
+void bae_default_options(bae_options* opts);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all contexts). */
+long long bae_launch_count(void);
+
+/* Process-wide kernel timing. bae_profile_start pre-creates CUDA events for
+ * up to max_launches launches; from then on every kernel launch of the
+ * library is bracketed by two events on its own stream. bae_profile_stop
+ * synchronises the device, and for each distinct kernel (in order of first
+ * launch, at most max_kernels) writes its name into `names` ('\n'-separated,
+ * NUL-terminated, truncated to names_len bytes), its summed device time in
+ * milliseconds into total_ms[k] and its launch count into launches[k];
+ * *n_kernels gets the number written. Any output pointer may be NULL (host
+ * memory). Returns BAE_ERR_INVALID_ARG if more than max_launches launches
+ * happened (the excess is not timed). Not part of the method; a measurement
+ * aid. */
+int bae_profile_start(int max_launches);
+int bae_profile_stop(char* names, int names_len, double* total_ms, long long* launches, int max_kernels,
+                     int* n_kernels);
+
+/* --------------------------------------------------------------- context */
+
+/* Creates a context on CUDA device `device`. `stream` is a cudaStream_t
+ * (for instance torch.cuda.current_stream().cuda_stream) or NULL for a new
+ * non-blocking stream owned by the context. The context caches LGF spectra
+ * per (N, s = kappa2 h^2) (numerical section: the table is precomputed once
+ * and reused across problems). */
+int bae_ctx_create(int device, void* stream, bae_ctx** out);
+
+/* Frees the context, its cache and its stream (if it created one). */
+void bae_ctx_destroy(bae_ctx* ctx);
+
+/* ------------------------------------------------------ LGF (Section 2.2) */
+
+/* G_s(n) of (6+s) - sum of the six neighbours (eq. [lgf] with h = 1, by
+ * Watson's Bessel integral eq. [lgf_bessel] with exp(-(6+s)t)), for all
+ * sorted offsets N > a >= b >= c >= 0 in lexicographic order of (a,b,c):
+ * index(a,b,c) = a(a+1)(a+2)/6 + b(b+1)/2 + c; `values` holds
+ * N(N+1)(N+2)/6 doubles. N in [2, 256], s >= 0 and finite. */
+int bae_lgf_table(bae_ctx* ctx, int N, double s, double* values);
+
+/* The real spectrum of G_s embedded evenly in the (2N)^3 periodic box
+ * (offset N set to 0), on the octant 0 <= k_i <= N: ghat[(k1 (N+1) + k2)(N+1)
+ * + k3] = sum_n Gemb(n) cos(pi k.n / N), unscaled. (N+1)^3 doubles. N must be
+ * a power of two in [8, 256]. */
+int bae_lgf_spectrum(bae_ctx* ctx, int N, double s, double* ghat);
+
+/* -------------------------------------------------- problem (Algorithm 1) */
+
+/* Classifies the grid from phi (N^3 doubles; phi < 0 is interior, phi == 0
+ * exterior; Section 2.1 point sets M+-, N+-, gamma+-), builds the closure
+ * (one row per gamma- node: among its M+ neighbours, in the order +x,-x,+y,
+ * -y,+z,-z with x = array axis 0, the one with the largest
+ * t = phi(p)/(phi(p)-phi(m)); x* = x_p + t (x_m - x_p); row
+ * t v(m) + (1-t) v(p) = g(x*), the hat basis of eq. [bc]), and fetches or
+ * builds the LGF spectrum for s = kappa2 h^2.
+ * N: power of two in [8, 256]. h > 0. layer: BAE_LAYER_DOUBLE (a gamma- node
+ * whose D_n is empty uses the single-layer column) or BAE_LAYER_SINGLE.
+ * BAE_ERR_GEOMETRY if gamma- is empty or touches the box faces. */
+int bae_problem_create(bae_ctx* ctx, int N, double h, const double origin[3],
+                       const double* phi, double kappa2, int layer, bae_problem** out);
+
+void bae_problem_destroy(bae_problem* prob);
+
+/* |gamma-| (unknowns of the boundary system), |gamma+|, |M+|. Any pointer
+ * may be NULL. Host-side, no device work. */
+int bae_problem_sizes(const bae_problem* prob, int64_t* n_gm, int64_t* n_gp, int64_t* n_mp);
+
+/* Boundary points x*(m) of the closure rows, gamma- in lexicographic order:
+ * xyz[3r + c]. The caller evaluates g there. */
+int bae_boundary_points(const bae_problem* prob, double* xyz);
+
+/* Classification export, any pointer may be NULL:
+ *  flags[N^3]: bit0 M+, bit1 gamma-, bit2 gamma+, bit3 D-node (outside N+,
+ *              next to gamma-), bits 4..6 |D_n| on gamma- nodes;
+ *  gm_idx[n_gm]: linear indices of gamma- (lexicographic);
+ *  partner[n_gm]: linear index of the closure partner p(m);
+ *  t[n_gm]: closure weight t(m). */
+int bae_classification(const bae_problem* prob, uint8_t* flags, int32_t* gm_idx,
+                       int32_t* partner, double* t);
+
+/* ---------------------------------------- the potential apply (hot path) */
+
+/* v = K q on the whole N^3 grid, K the problem's layer potential
+ * (Section 3.2: single eq. [single_potential], double eq. [double_potential]),
+ * i.e. the source stencil rho = B q, the free-space convolution with G_s by
+ * a zero-padded (2N)^3 FFT, v(m) = sum_x G_s(m-x) rho(x).
+ * q: n_gm doubles; v: N^3 doubles. precision BAE_FP64 or BAE_FP32. */
+int bae_potential_apply(bae_problem* prob, int precision, const double* q, double* v);
+
+/* The boundary operator of eq. [double_bae] (or its single-layer analogue):
+ * (A q)_m = t(m) (Kq)(m) + (1 - t(m)) (Kq)(p(m)) for every gamma- node m.
+ * q, Aq: n_gm doubles. precision BAE_FP64 or BAE_FP32. */
+int bae_boundary_apply(bae_problem* prob, int precision, const double* q, double* Aq);
+
+/* Particular solution on the free lattice (eq. [ps] with G_h = h^2 G_s):
+ * up(m) = sum_{x in M+} G_s(m-x) h^2 f(x) on the whole grid.
+ * f, up: N^3 doubles (paper sign). precision BAE_FP64 or BAE_FP32. */
+int bae_particular(bae_problem* prob, int precision, const double* f, double* up);
+
+/* ---------------------------------------------------- solve (Algorithm 1) */
+
+/* Solves the BAE of eq. [double_bae] (or single layer) by unrestarted-
+ * per-cycle GMRES with zero initial guess and no preconditioner:
+ *   b = g - Phi u_p,  A q = b,  u = u_p + K q.
+ * f: N^3 doubles (paper sign, -Lap u + kappa2 u = f); g: n_gm doubles, the
+ * Dirichlet data at bae_boundary_points(). Outputs: density q (n_gm doubles)
+ * and u (N^3 doubles: the discrete solution on N+ = M+ u gamma-, 0 elsewhere);
+ * either may be NULL. opts may be NULL (defaults); stats may be NULL.
+ * BAE_ERR_NOT_CONVERGED leaves valid outputs and stats. */
+int bae_solve(bae_problem* prob, const double* f, const double* g, const bae_options* opts,
+              double* density, double* u, bae_stats* stats);
+
+/* nrhs independent right-hand sides on one problem: f [nrhs][N^3],
+ * g [nrhs][n_gm], density [nrhs][n_gm], u [nrhs][N^3]. Every GMRES step
+ * applies the potential to all unconverged right-hand sides in one batched
+ * convolution. stats, if not NULL, points to nrhs entries. Returns the worst
+ * per-RHS code. */
+int bae_solve_batched(bae_problem* prob, int nrhs, const double* f, const double* g,
+                      const bae_options* opts, double* density, double* u, bae_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BAE_H */

@@ -17,7 +17,7 @@ phi along the edge m-p lies closest to m, i.e. the largest
 the first one on ties. x* = x_p + t (x_m - x_p) and the hat basis on that
 edge gives the row  t v(m) + (1 - t) v(p) = g(x*).
 
-Geometry check: every gamma- node must lie off the faces of the grid box so
+Geometry check: no M+ or gamma- node may lie on a face of the grid box, so
 that N+ and every D_n stay inside the N^3 grid.
 
 Parity: classify() is pinned against classify_bruteforce(), which builds the
@@ -94,9 +94,9 @@ def classify(phi: np.ndarray, h: float, origin: float, check_geometry: bool = Tr
     if check_geometry:
         if gm_idx.size == 0:
             raise GeometryError("empty gamma-: no interior node")
-        ijk = np.stack(np.unravel_index(gm_idx, phi.shape), axis=1)
+        ijk = np.stack(np.unravel_index(np.concatenate([gm_idx, np.flatnonzero(inside)]), phi.shape), axis=1)
         if (ijk.min() < 1) or (ijk.max() > N - 2):
-            raise GeometryError("gamma- touches the grid box faces")
+            raise GeometryError("M+ or gamma- touches the grid box faces")
 
     # closure partner and weight
     ijk = np.stack(np.unravel_index(gm_idx, phi.shape), axis=1)

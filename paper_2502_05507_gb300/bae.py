@@ -1,0 +1,312 @@
+"""Python binding of libbae (include/bae.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts torch
+tensors (device memory) or numpy arrays (host memory) into plain pointers,
+calls the C entry point with the same name and turns error codes into
+exceptions. There is no fallback: if libbae.so is missing or no GPU is
+usable, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbae.so")
+
+OK, ERR_INVALID_ARG, ERR_GEOMETRY, ERR_OOM, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_CUDA = range(7)
+LAYER_DOUBLE, LAYER_SINGLE = 0, 1
+FP64, MIXED, FP32 = 0, 1, 2
+_LAYERS = {"double": LAYER_DOUBLE, "single": LAYER_SINGLE}
+_PREC = {"fp64": FP64, "mixed": MIXED, "fp32": FP32}
+
+
+class BAEError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[bae error {code}] {msg}")
+        self.code = code
+
+
+class NotConverged(BAEError):
+    pass
+
+
+class GeometryError(BAEError):
+    pass
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("restart", ctypes.c_int),
+                ("precision", ctypes.c_int), ("max_refine", ctypes.c_int), ("inner_tol", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("refinements", ctypes.c_int), ("applies_fp64", ctypes.c_int),
+                ("applies_fp32", ctypes.c_int), ("rel_residual", ctypes.c_double), ("ms_total", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_I = ctypes.c_int
+
+
+def lib():
+    """Loads libbae.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2502_05507_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        sig = {
+            "bae_version": (_I, []),
+            "bae_last_error": (ctypes.c_char_p, []),
+            "bae_default_options": (None, [_P]),
+            "bae_launch_count": (ctypes.c_longlong, []),
+            "bae_profile_start": (_I, [_I]),
+            "bae_profile_stop": (_I, [ctypes.c_char_p, _I, _P, _P, _I, _P]),
+            "bae_ctx_create": (_I, [_I, _P, _P]),
+            "bae_ctx_destroy": (None, [_P]),
+            "bae_lgf_table": (_I, [_P, _I, _D, _P]),
+            "bae_lgf_spectrum": (_I, [_P, _I, _D, _P]),
+            "bae_problem_create": (_I, [_P, _I, _D, _P, _P, _D, _I, _P]),
+            "bae_problem_destroy": (None, [_P]),
+            "bae_problem_sizes": (_I, [_P, _P, _P, _P]),
+            "bae_boundary_points": (_I, [_P, _P]),
+            "bae_classification": (_I, [_P, _P, _P, _P, _P]),
+            "bae_potential_apply": (_I, [_P, _I, _P, _P]),
+            "bae_boundary_apply": (_I, [_P, _I, _P, _P]),
+            "bae_particular": (_I, [_P, _I, _P, _P]),
+            "bae_solve": (_I, [_P, _P, _P, _P, _P, _P, _P]),
+            "bae_solve_batched": (_I, [_P, _I, _P, _P, _P, _P, _P, _P]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+EXPORTED = ["bae_version", "bae_last_error", "bae_default_options", "bae_launch_count", "bae_profile_start",
+            "bae_profile_stop", "bae_ctx_create", "bae_ctx_destroy",
+            "bae_lgf_table", "bae_lgf_spectrum", "bae_problem_create", "bae_problem_destroy",
+            "bae_problem_sizes", "bae_boundary_points", "bae_classification", "bae_potential_apply",
+            "bae_boundary_apply", "bae_particular", "bae_solve", "bae_solve_batched"]
+
+
+def _check(rc: int, allow_not_converged=False):
+    if rc == OK:
+        return
+    msg = lib().bae_last_error().decode(errors="replace")
+    if rc == ERR_NOT_CONVERGED:
+        if allow_not_converged:
+            return
+        raise NotConverged(rc, msg)
+    if rc == ERR_GEOMETRY:
+        raise GeometryError(rc, msg)
+    raise BAEError(rc, msg)
+
+
+def _ptr(a):
+    """Device pointer of a contiguous torch tensor, or host pointer of a
+    contiguous numpy array."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("numpy array must be C-contiguous")
+        return a.ctypes.data
+    if not a.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return a.data_ptr()
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _new(shape, dtype, like):
+    """Output buffer matching the memory kind of `like` (torch on its device,
+    else numpy on the host)."""
+    if isinstance(like, np.ndarray) or like is None:
+        return np.empty(shape, dtype=dtype)
+    torch = _torch()
+    tdt = {np.float64: torch.float64, np.int32: torch.int32, np.uint8: torch.uint8}[dtype]
+    return torch.empty(shape, dtype=tdt, device=like.device)
+
+
+def _as_f64(a):
+    if isinstance(a, np.ndarray):
+        return np.ascontiguousarray(a, dtype=np.float64)
+    torch = _torch()
+    return a.to(torch.float64).contiguous()
+
+
+def launch_count() -> int:
+    """Kernels launched by the library in this process so far."""
+    return int(lib().bae_launch_count())
+
+
+def profile_start(max_launches: int = 200000):
+    _check(lib().bae_profile_start(int(max_launches)))
+
+
+def profile_stop(max_kernels: int = 128) -> dict:
+    """{kernel name: (total device ms, launches)} since profile_start."""
+    names = ctypes.create_string_buffer(16384)
+    ms = np.zeros(max_kernels)
+    cnt = np.zeros(max_kernels, dtype=np.int64)
+    nk = ctypes.c_int()
+    _check(lib().bae_profile_stop(names, len(names), ms.ctypes.data, cnt.ctypes.data, max_kernels,
+                                  ctypes.byref(nk)))
+    keys = names.value.decode().split("\n")[: nk.value]
+    return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(keys)}
+
+
+class Context:
+    """bae_ctx: one CUDA device and stream, with the LGF spectrum cache."""
+
+    def __init__(self, device: int = 0, stream=None):
+        """stream: a torch.cuda.Stream (or None for a new one). All library
+        work of this context runs on it; record timing events on ctx.stream."""
+        self.device = device
+        self._h = ctypes.c_void_p()
+        torch = _torch()
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=device)
+        _check(lib().bae_ctx_create(device, ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(self._h)))
+
+    def close(self):
+        if self._h:
+            lib().bae_ctx_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def lgf_table(self, N: int, s: float, out=None):
+        ntri = N * (N + 1) * (N + 2) // 6
+        out = np.empty(ntri) if out is None else out
+        _check(lib().bae_lgf_table(self._h, N, float(s), _ptr(out)))
+        return out
+
+    def lgf_spectrum(self, N: int, s: float, out=None):
+        out = np.empty((N + 1,) * 3) if out is None else out
+        _check(lib().bae_lgf_spectrum(self._h, N, float(s), _ptr(out)))
+        return out
+
+
+class Problem:
+    """bae_problem: classified grid, closure, source stencil and spectrum."""
+
+    def __init__(self, ctx: Context, phi, h: float, origin, kappa2: float = 0.0, layer: str = "double"):
+        self.ctx = ctx
+        phi = _as_f64(phi)
+        self.N = int(phi.shape[0])
+        self.h = float(h)
+        o = np.array(origin if np.ndim(origin) else [origin] * 3, dtype=np.float64)
+        self.origin = o
+        self.kappa2 = float(kappa2)
+        self.layer = layer
+        self._h = ctypes.c_void_p()
+        _check(lib().bae_problem_create(ctx._h, self.N, self.h, o.ctypes.data, _ptr(phi), self.kappa2,
+                                        _LAYERS[layer], ctypes.byref(self._h)))
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().bae_problem_sizes(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        self.n_gm, self.n_gp, self.n_mp = a.value, b.value, c.value
+
+    def close(self):
+        if self._h:
+            lib().bae_problem_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def boundary_points(self, like=None):
+        out = _new((self.n_gm, 3), np.float64, like)
+        _check(lib().bae_boundary_points(self._h, _ptr(out)))
+        return out
+
+    def classification(self):
+        N = self.N
+        flags = np.empty((N, N, N), np.uint8)
+        gm = np.empty(self.n_gm, np.int32)
+        partner = np.empty(self.n_gm, np.int32)
+        t = np.empty(self.n_gm, np.float64)
+        _check(lib().bae_classification(self._h, _ptr(flags), _ptr(gm), _ptr(partner), _ptr(t)))
+        return dict(flags=flags, gm=gm, partner=partner, t=t)
+
+    def potential_apply(self, q, precision="fp64", out=None):
+        q = _as_f64(q)
+        out = _new((self.N,) * 3, np.float64, q) if out is None else out
+        _check(lib().bae_potential_apply(self._h, _PREC[precision], _ptr(q), _ptr(out)))
+        return out
+
+    def boundary_apply(self, q, precision="fp64", out=None):
+        q = _as_f64(q)
+        out = _new((self.n_gm,), np.float64, q) if out is None else out
+        _check(lib().bae_boundary_apply(self._h, _PREC[precision], _ptr(q), _ptr(out)))
+        return out
+
+    def particular(self, f, precision="fp64", out=None):
+        f = _as_f64(f)
+        out = _new((self.N,) * 3, np.float64, f) if out is None else out
+        _check(lib().bae_particular(self._h, _PREC[precision], _ptr(f), _ptr(out)))
+        return out
+
+    def _opts(self, tol, precision, max_iter, restart, max_refine, inner_tol):
+        o = Options()
+        lib().bae_default_options(ctypes.byref(o))
+        o.tol = tol
+        o.precision = _PREC[precision]
+        if max_iter is not None:
+            o.max_iter = max_iter
+        if restart is not None:
+            o.restart = restart
+        if max_refine is not None:
+            o.max_refine = max_refine
+        if inner_tol is not None:
+            o.inner_tol = inner_tol
+        return o
+
+    def solve(self, f, g, tol=1e-10, precision="fp64", max_iter=None, restart=None, max_refine=None,
+              inner_tol=None, density=None, u=None, allow_not_converged=False):
+        """Returns (density, u, stats dict). f (N^3) and g (n_gm) may be
+        torch CUDA tensors or numpy arrays; outputs follow f's kind."""
+        f = _as_f64(f)
+        g = _as_f64(g)
+        density = _new((self.n_gm,), np.float64, f) if density is None else density
+        u = _new((self.N,) * 3, np.float64, f) if u is None else u
+        st = Stats()
+        o = self._opts(tol, precision, max_iter, restart, max_refine, inner_tol)
+        rc = lib().bae_solve(self._h, _ptr(f), _ptr(g), ctypes.byref(o), _ptr(density), _ptr(u), ctypes.byref(st))
+        _check(rc, allow_not_converged)
+        return density, u, st.as_dict()
+
+    def solve_batched(self, f, g, tol=1e-10, precision="fp64", max_iter=None, restart=None, max_refine=None,
+                      inner_tol=None, density=None, u=None, allow_not_converged=False):
+        """f [nrhs, N, N, N], g [nrhs, n_gm]; returns (density, u, [stats])."""
+        f = _as_f64(f)
+        g = _as_f64(g)
+        nrhs = int(f.shape[0])
+        density = _new((nrhs, self.n_gm), np.float64, f) if density is None else density
+        u = _new((nrhs,) + (self.N,) * 3, np.float64, f) if u is None else u
+        st = (Stats * nrhs)()
+        o = self._opts(tol, precision, max_iter, restart, max_refine, inner_tol)
+        rc = lib().bae_solve_batched(self._h, nrhs, _ptr(f), _ptr(g), ctypes.byref(o), _ptr(density), _ptr(u),
+                                     st)
+        _check(rc, allow_not_converged)
+        return density, u, [s.as_dict() for s in st]

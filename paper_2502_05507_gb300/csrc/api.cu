@@ -1,0 +1,977 @@
+// C ABI of the BAE library (include/bae.h): contexts, problems, the
+// potential apply, and the GMRES solve of Algorithm 1 (FP64, or FP32
+// convolution inside FP64 iterative refinement), single and batched.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "classify.cuh"
+#include "common.cuh"
+#include "conv.cuh"
+#include "krylov.cuh"
+#include "lgf.cuh"
+
+namespace bae {
+
+static thread_local std::string g_last_error;
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+// --------------------------------------------------- launches and profiling
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+namespace {
+struct ProfRec {
+    const char* name;
+    cudaEvent_t a, b;
+};
+struct Profiler {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    std::vector<ProfRec> recs;
+    cudaEvent_t pending = nullptr;
+    const char* pending_name = nullptr;
+    bool overflow = false;
+    cudaEvent_t next() {
+        if (used >= pool.size()) { overflow = true; return nullptr; }
+        return pool[used++];
+    }
+};
+Profiler g_prof;
+}  // namespace
+
+void prof_push(const char* name, cudaStream_t st) {
+    if (!g_prof.on) return;
+    g_prof.pending = g_prof.next();
+    g_prof.pending_name = name;
+    if (g_prof.pending) cudaEventRecord(g_prof.pending, st);
+}
+
+void prof_pop(cudaStream_t st) {
+    if (!g_prof.on || !g_prof.pending) return;
+    cudaEvent_t e = g_prof.next();
+    if (!e) return;
+    cudaEventRecord(e, st);
+    g_prof.recs.push_back({g_prof.pending_name, g_prof.pending, e});
+    g_prof.pending = nullptr;
+}
+
+void* dev_alloc(size_t bytes, cudaStream_t st) {
+    void* p = nullptr;
+    BAE_CUDA(cudaMallocAsync(&p, bytes ? bytes : 16, st));
+    return p;
+}
+
+void dev_free(void* p, cudaStream_t st) {
+    if (p) cudaFreeAsync(p, st);
+}
+
+namespace {
+
+// Device buffer that grows on demand and frees itself (stream-ordered).
+template <typename T>
+struct Grow {
+    T* p = nullptr;
+    long long cap = 0;
+    cudaStream_t st = nullptr;
+    T* need(long long n) {
+        if (n > cap) {
+            dev_free(p, st);
+            p = nullptr;
+            cap = 0;
+            p = dev_alloc_n<T>(n, st);
+            cap = n;
+        }
+        return p;
+    }
+    void release() { dev_free(p, st); p = nullptr; cap = 0; }
+    ~Grow() { release(); }
+};
+
+struct Spectrum {
+    int N = 0;
+    double s = 0.0;
+    double* g64 = nullptr;
+    float* g32 = nullptr;
+    cudaStream_t st = nullptr;
+    ~Spectrum() {
+        dev_free(g64, st);
+        dev_free(g32, st);
+    }
+};
+
+// Work space shared by every problem of a context (calls on one context
+// are serialised on its stream). Sized on demand for the largest call.
+struct Workspace {
+    Grow<double2> A, B;                       // convolution buffers (float64 sized)
+    Grow<double> v64, up, vstage;             // [nb][N^3]
+    Grow<float> v32;
+    Grow<double> V, w, partial, h, hsave, x, r, bvec, tmp, qstage, n2;   // Krylov
+    Grow<int> active;
+    Grow<double> in_f, in_g, out_q, out_u;    // staging of host arguments
+    void set_stream(cudaStream_t st) {
+        Grow<double>* ds[] = {&v64, &up, &vstage, &V, &w, &partial, &h, &hsave, &x, &r, &bvec, &tmp,
+                              &qstage, &n2, &in_f, &in_g, &out_q, &out_u};
+        for (auto* d : ds) d->st = st;
+        A.st = B.st = st;
+        v32.st = st;
+        active.st = st;
+    }
+};
+
+struct Twiddles {
+    double2* tw64 = nullptr;
+    float2* tw32 = nullptr;
+};
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+}  // namespace bae
+
+using namespace bae;
+
+struct bae_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::map<std::pair<int, uint64_t>, std::shared_ptr<Spectrum>> cache;
+    std::map<int, Twiddles> tw;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    Workspace ws;
+
+    const Twiddles& twiddles(int L) {
+        auto it = tw.find(L);
+        if (it != tw.end()) return it->second;
+        Twiddles t;
+        t.tw64 = dev_alloc_n<double2>(L, stream);
+        t.tw32 = dev_alloc_n<float2>(L, stream);
+        make_twiddles(L, t.tw64, t.tw32, stream);
+        return tw[L] = t;
+    }
+
+    std::shared_ptr<Spectrum> spectrum(int N, double s) {
+        uint64_t key;
+        std::memcpy(&key, &s, sizeof(key));
+        auto it = cache.find({N, key});
+        if (it != cache.end()) return it->second;
+        auto sp = std::make_shared<Spectrum>();
+        sp->N = N;
+        sp->s = s;
+        sp->st = stream;
+        const long long n3 = (long long)(N + 1) * (N + 1) * (N + 1);
+        sp->g64 = dev_alloc_n<double>(n3, stream);
+        sp->g32 = dev_alloc_n<float>(n3, stream);
+        const double L = 2.0 * N;
+        lgf_spectrum(N, s, 1.0 / (L * L * L), sp->g64, sp->g32, stream);
+        cache[{N, key}] = sp;
+        return sp;
+    }
+};
+
+struct bae_problem {
+    bae_ctx* ctx = nullptr;
+    Geometry geo;
+    std::shared_ptr<Spectrum> spec;
+    double kappa2 = 0.0, s = 0.0;
+    Workspace& ws() { return ctx->ws; }
+    long long n3() const { return (long long)geo.N * geo.N * geo.N; }
+};
+
+namespace bae {
+namespace {
+
+long long n_gm(const bae_problem* P) { return P->geo.n_gm; }
+
+template <typename T>
+ConvArgs<T> conv_args(bae_problem* P, int nb) {
+    const int N = P->geo.N;
+    const long long N1 = N + 1;
+    ConvArgs<T> a;
+    a.N = N;
+    a.nbatch = nb;
+    a.A = reinterpret_cast<cplx_t<T>*>(P->ws().A.need((long long)nb * N * N * N1));
+    a.B = reinterpret_cast<cplx_t<T>*>(P->ws().B.need((long long)nb * N * 2 * N * N1));
+    const Twiddles& tw = P->ctx->twiddles(2 * N);
+    if constexpr (sizeof(T) == 8) {
+        a.ghat = reinterpret_cast<const T*>(P->spec->g64);
+        a.tw = reinterpret_cast<const cplx_t<T>*>(tw.tw64);
+    } else {
+        a.ghat = reinterpret_cast<const T*>(P->spec->g32);
+        a.tw = reinterpret_cast<const cplx_t<T>*>(tw.tw32);
+    }
+    return a;
+}
+
+template <typename T>
+T* vbuf(bae_problem* P, int nb) {
+    if constexpr (sizeof(T) == 8) return reinterpret_cast<T*>(P->ws().v64.need((long long)nb * P->n3()));
+    else return reinterpret_cast<T*>(P->ws().v32.need((long long)nb * P->n3()));
+}
+
+// v[b] = K q[b] on the N^3 grid, q [nb][n_gm] on the device
+template <typename T>
+T* apply_potential(bae_problem* P, int nb, const double* q) {
+    ConvArgs<T> a = conv_args<T>(P, nb);
+    a.mode = SRC_DENSITY;
+    a.q = q;
+    a.q_stride = n_gm(P);
+    a.rec = P->geo.recipe();
+    a.v = vbuf<T>(P, nb);
+    conv_apply<T>(a, P->ctx->stream);
+    return a.v;
+}
+
+// v[b] = sum_{x in M+} G(m - x) scale f[b](x)
+template <typename T>
+T* apply_volume(bae_problem* P, int nb, const double* f, double scale) {
+    ConvArgs<T> a = conv_args<T>(P, nb);
+    a.mode = SRC_VOLUME;
+    a.f = f;
+    a.flags = P->geo.flags;
+    a.scale = scale;
+    a.v = vbuf<T>(P, nb);
+    conv_apply<T>(a, P->ctx->stream);
+    return a.v;
+}
+
+// Aq[b] = Phi K q[b], both [nb][n_gm] on the device
+template <typename T>
+void boundary_apply(bae_problem* P, int nb, const double* q, double* Aq) {
+    T* v = apply_potential<T>(P, nb, q);
+    closure_gather<T>(v, P->n3(), P->geo.gm, P->geo.partner, P->geo.t, (int)n_gm(P), nb, Aq, n_gm(P),
+                      P->ctx->stream);
+}
+
+void boundary_apply_prec(bae_problem* P, int prec, int nb, const double* q, double* Aq) {
+    if (prec == BAE_FP32) boundary_apply<float>(P, nb, q, Aq);
+    else boundary_apply<double>(P, nb, q, Aq);
+}
+
+// --------------------------------------------------------------- GMRES
+struct RhsState {
+    bool converged = false;
+    int iterations = 0;
+    double target = 0.0;     // absolute residual target
+    double beta = 0.0;
+    double est = 0.0;        // current residual estimate
+    std::vector<double> H;   // (m+1) x m column-major Hessenberg (rotated)
+    std::vector<double> cs, sn, g;
+};
+
+// Solves A x = rhs for the RHS in `which` (indices into [nb] arrays) with
+// restarted GMRES (CGS2 Arnoldi on the device, Givens on the host),
+// starting from x (device [nb][n]; x_zero: known to be 0, which skips the
+// first residual apply). The apply uses precision `prec`; applies[b] counts
+// the applies each RHS took part in. Returns the number of RHS that reached
+// their target.
+int gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, const double* rhs, double* x,
+          bool x_zero, std::vector<RhsState>& S, int max_iter, int restart, std::vector<int>& applies) {
+    cudaStream_t st = P->ctx->stream;
+    const int n = (int)n_gm(P);
+    const int m = std::max(1, std::min(restart, max_iter));
+    KrylovBatch k;
+    k.n = n;
+    k.nb = nb;
+    k.mp1 = m + 1;
+    k.nchunk = krylov_chunks(n);
+    k.V = P->ws().V.need((long long)nb * (m + 1) * n);
+    k.w = P->ws().w.need((long long)nb * n);
+    k.partial = P->ws().partial.need((long long)nb * (m + 2) * k.nchunk);
+    k.h = P->ws().h.need((long long)nb * (m + 2));
+    double* hsave = P->ws().hsave.need((long long)nb * (m + 2));
+    double* r = P->ws().r.need((long long)nb * n);
+    double* qst = P->ws().qstage.need((long long)nb * n);
+    double* tmp = P->ws().tmp.need((long long)nb * n);
+    double* n2 = P->ws().n2.need((long long)nb * std::max(k.nchunk, 1) + nb);
+    double* d_alpha = P->ws().bvec.need(nb);
+    int* d_act = P->ws().active.need(nb);
+
+    std::vector<double> h_host((size_t)nb * (m + 2)), h1_host((size_t)nb * (m + 2));
+    std::vector<double> nrm((size_t)nb), alpha((size_t)nb);
+    int total_iters_left = max_iter;
+    std::vector<int> todo;
+    for (int b : which)
+        if (!S[b].converged) todo.push_back(b);
+
+    while (!todo.empty() && total_iters_left > 0) {
+        const int na = (int)todo.size();
+        BAE_CUDA(cudaMemcpyAsync(d_act, todo.data(), na * sizeof(int), cudaMemcpyHostToDevice, st));
+        // r = rhs - A x
+        if (x_zero) {
+            kr_gather_rows(rhs, d_act, na, n, qst, st);
+            kr_scatter_rows(qst, d_act, na, n, r, st);
+            x_zero = false;
+        } else {
+            kr_gather_rows(x, d_act, na, n, qst, st);
+            boundary_apply_prec(P, prec, na, qst, tmp);
+            for (int b : todo) applies[b] += 1;
+            kr_scatter_rows(tmp, d_act, na, n, r, st);
+            kr_sub(rhs, r, d_act, na, n, r, st);
+        }
+        kr_norm2(r, d_act, na, n, n2 + nb, k.nchunk, n2, st);
+        BAE_CUDA(cudaMemcpyAsync(nrm.data(), n2, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+        BAE_CUDA(cudaStreamSynchronize(st));
+        std::vector<int> cyc;
+        for (int b : todo) {
+            RhsState& R = S[b];
+            R.beta = std::sqrt(nrm[b]);
+            R.est = R.beta;
+            if (R.beta <= R.target) {
+                R.converged = true;
+                continue;
+            }
+            cyc.push_back(b);
+            R.H.assign((size_t)(m + 1) * m, 0.0);
+            R.cs.assign(m, 0.0);
+            R.sn.assign(m, 0.0);
+            R.g.assign(m + 1, 0.0);
+            R.g[0] = R.beta;
+            alpha[b] = 1.0 / R.beta;
+        }
+        if (cyc.empty()) break;
+        int nc = (int)cyc.size();
+        BAE_CUDA(cudaMemcpyAsync(d_alpha, alpha.data(), nb * sizeof(double), cudaMemcpyHostToDevice, st));
+        BAE_CUDA(cudaMemcpyAsync(d_act, cyc.data(), nc * sizeof(int), cudaMemcpyHostToDevice, st));
+        // V[b][0] = r / beta: scale r into w, then copy w into V[0] with norm 1
+        kr_scale(r, d_alpha, d_act, nc, n, k.w, st);
+        {
+            // put 1.0 into the norm slot so that kr_scale_into copies w unchanged
+            std::vector<double> ones((size_t)nb * (m + 2), 1.0);
+            BAE_CUDA(cudaMemcpyAsync(k.h, ones.data(), ones.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+            kr_scale_into(k, d_act, nc, 0, st);
+            BAE_CUDA(cudaStreamSynchronize(st));
+        }
+        std::vector<int> live = cyc;          // RHS still iterating in this cycle
+        std::vector<int> ncols(nb, 0);        // basis size reached per RHS
+        int j = 0;
+        for (; j < m && !live.empty() && total_iters_left > 0; ++j) {
+            const int nl = (int)live.size();
+            BAE_CUDA(cudaMemcpyAsync(d_act, live.data(), nl * sizeof(int), cudaMemcpyHostToDevice, st));
+            // w = A V[j]
+            for (int q = 0; q < nl; ++q) {
+                const int b = live[q];
+                BAE_CUDA(cudaMemcpyAsync(qst + (long long)q * n, k.V + ((long long)b * k.mp1 + j) * n,
+                                         n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            }
+            boundary_apply_prec(P, prec, nl, qst, tmp);
+            for (int b : live) applies[b] += 1;
+            kr_scatter_rows(tmp, d_act, nl, n, k.w, st);
+            // CGS2
+            kr_dots(k, d_act, nl, j + 1, st);
+            BAE_CUDA(cudaMemcpyAsync(hsave, k.h, (size_t)nb * (m + 2) * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            kr_update_norm(k, d_act, nl, j + 1, st);
+            kr_dots(k, d_act, nl, j + 1, st);
+            kr_update_norm(k, d_act, nl, j + 1, st);
+            kr_scale_into(k, d_act, nl, j + 1, st);
+            BAE_CUDA(cudaMemcpyAsync(h_host.data(), k.h, h_host.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+            BAE_CUDA(cudaMemcpyAsync(h1_host.data(), hsave, h1_host.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+            BAE_CUDA(cudaStreamSynchronize(st));
+            --total_iters_left;
+            std::vector<int> next;
+            for (int b : live) {
+                RhsState& R = S[b];
+                double* col = R.H.data() + (size_t)j * (m + 1);
+                const double* h2 = h_host.data() + (size_t)b * (m + 2);
+                const double* h1 = h1_host.data() + (size_t)b * (m + 2);
+                for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
+                col[j + 1] = std::sqrt(std::max(h2[m + 1], 0.0));
+                for (int i = 0; i < j; ++i) {
+                    const double a = col[i], c = col[i + 1];
+                    col[i] = R.cs[i] * a + R.sn[i] * c;
+                    col[i + 1] = -R.sn[i] * a + R.cs[i] * c;
+                }
+                const double rr = std::hypot(col[j], col[j + 1]);
+                const bool breakdown = (rr == 0.0);
+                R.cs[j] = breakdown ? 1.0 : col[j] / rr;
+                R.sn[j] = breakdown ? 0.0 : col[j + 1] / rr;
+                col[j] = rr;
+                col[j + 1] = 0.0;
+                R.g[j + 1] = -R.sn[j] * R.g[j];
+                R.g[j] = R.cs[j] * R.g[j];
+                R.est = std::fabs(R.g[j + 1]);
+                R.iterations += 1;
+                ncols[b] = j + 1;
+                if (R.est <= R.target || breakdown || h2[m + 1] <= 0.0) continue;  // leaves the cycle
+                next.push_back(b);
+            }
+            live.swap(next);
+        }
+        // x += V y for every RHS of the cycle
+        std::vector<double> y((size_t)nb * m, 0.0);
+        for (int b : cyc) {
+            RhsState& R = S[b];
+            const int c = ncols[b];
+            for (int i = c - 1; i >= 0; --i) {
+                double acc = R.g[i];
+                for (int l = i + 1; l < c; ++l) acc -= R.H[(size_t)l * (m + 1) + i] * y[(size_t)b * m + l];
+                const double d = R.H[(size_t)i * (m + 1) + i];
+                y[(size_t)b * m + i] = d != 0.0 ? acc / d : 0.0;
+            }
+        }
+        double* d_y = P->ws().bvec.need((long long)nb * m + nb);
+        BAE_CUDA(cudaMemcpyAsync(d_y, y.data(), y.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        BAE_CUDA(cudaMemcpyAsync(d_act, cyc.data(), nc * sizeof(int), cudaMemcpyHostToDevice, st));
+        int maxc = 0;
+        for (int b : cyc) maxc = std::max(maxc, ncols[b]);
+        kr_combine(k, d_act, nc, maxc, d_y, m, x, st);
+        BAE_CUDA(cudaStreamSynchronize(st));
+        // decide which RHS need another cycle: estimates below target are
+        // accepted (the caller checks the true residual)
+        std::vector<int> again;
+        for (int b : cyc) {
+            if (S[b].est <= S[b].target) S[b].converged = true;
+            else again.push_back(b);
+        }
+        todo.swap(again);
+        d_alpha = P->ws().bvec.need(nb);  // bvec may have moved
+    }
+    int nconv = 0;
+    for (int b : which) nconv += S[b].converged ? 1 : 0;
+    return nconv;
+}
+
+// ------------------------------------------------------------ full solve
+struct HostArg {
+    const double* in = nullptr;
+    double* out = nullptr;
+};
+
+int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const bae_options* opts_in,
+               double* density, double* u, bae_stats* stats) {
+    bae_options o;
+    bae_default_options(&o);
+    if (opts_in) o = *opts_in;
+    BAE_REQUIRE(nb >= 1, BAE_ERR_INVALID_ARG, "nrhs must be >= 1");
+    BAE_REQUIRE(f && g, BAE_ERR_INVALID_ARG, "f and g must not be null");
+    BAE_REQUIRE(o.tol > 0 && std::isfinite(o.tol), BAE_ERR_INVALID_ARG, "tol must be positive");
+    BAE_REQUIRE(o.max_iter >= 1 && o.restart >= 1, BAE_ERR_INVALID_ARG, "max_iter and restart must be >= 1");
+    BAE_REQUIRE(o.precision == BAE_FP64 || o.precision == BAE_MIXED, BAE_ERR_INVALID_ARG,
+                "precision must be BAE_FP64 or BAE_MIXED");
+    cudaStream_t st = P->ctx->stream;
+    BAE_CUDA(cudaEventRecord(P->ctx->ev0, st));
+    const long long n3 = P->n3();
+    const int n = (int)n_gm(P);
+    const double h = P->geo.h;
+
+    // stage host inputs
+    const double* d_f = f;
+    const double* d_g = g;
+    if (!is_device_ptr(f)) {
+        double* p = P->ws().in_f.need((long long)nb * n3);
+        BAE_CUDA(cudaMemcpyAsync(p, f, (size_t)nb * n3 * sizeof(double), cudaMemcpyHostToDevice, st));
+        d_f = p;
+    }
+    if (!is_device_ptr(g)) {
+        double* p = P->ws().in_g.need((long long)nb * n);
+        BAE_CUDA(cudaMemcpyAsync(p, g, (size_t)nb * n * sizeof(double), cudaMemcpyHostToDevice, st));
+        d_g = p;
+    }
+    std::vector<bae_stats> st_local(nb);
+    for (auto& s : st_local) std::memset(&s, 0, sizeof(s));
+
+    // particular solution u_p = G_h[chi_{M+} f] (float64) and b = g - Phi u_p
+    double* up = P->ws().up.need((long long)nb * n3);
+    {
+        double* v = apply_volume<double>(P, nb, d_f, h * h);
+        BAE_CUDA(cudaMemcpyAsync(up, v, (size_t)nb * n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        for (auto& s : st_local) s.applies_fp64 += 1;
+    }
+    double* bvec = P->ws().x.need((long long)nb * n * 3);   // [b | q | r] blocks
+    double* q = bvec + (long long)nb * n;
+    double* res = q + (long long)nb * n;
+    closure_gather<double>(up, n3, P->geo.gm, P->geo.partner, P->geo.t, n, nb, res, n, st);
+    {
+        std::vector<int> all(nb);
+        for (int b = 0; b < nb; ++b) all[b] = b;
+        int* d_act = P->ws().active.need(nb);
+        BAE_CUDA(cudaMemcpyAsync(d_act, all.data(), nb * sizeof(int), cudaMemcpyHostToDevice, st));
+        kr_sub(d_g, res, d_act, nb, n, bvec, st);
+    }
+    BAE_CUDA(cudaMemsetAsync(q, 0, (size_t)nb * n * sizeof(double), st));
+
+    // ||b||
+    std::vector<double> bn2(nb), rn2(nb);
+    double* n2 = P->ws().n2.need((long long)nb * krylov_chunks(n) + nb);
+    std::vector<int> all(nb);
+    for (int b = 0; b < nb; ++b) all[b] = b;
+    int* d_act = P->ws().active.need(nb);
+    BAE_CUDA(cudaMemcpyAsync(d_act, all.data(), nb * sizeof(int), cudaMemcpyHostToDevice, st));
+    kr_norm2(bvec, d_act, nb, n, n2 + nb, krylov_chunks(n), n2, st);
+    BAE_CUDA(cudaMemcpyAsync(bn2.data(), n2, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+    BAE_CUDA(cudaStreamSynchronize(st));
+
+    std::vector<RhsState> S(nb);
+    std::vector<int> iters_used(nb, 0);
+    std::vector<bool> done(nb, false);
+    std::vector<double> relres(nb, 0.0);
+    double* v_last = nullptr;   // float64 K q of the final q, [nb][N^3]
+
+    // residual r = b - A64 q (also leaves K q in the float64 volume buffer)
+    auto true_residual = [&]() {
+        int* d_all = P->ws().active.need(nb);
+        BAE_CUDA(cudaMemcpyAsync(d_all, all.data(), nb * sizeof(int), cudaMemcpyHostToDevice, st));
+        double* tmp = P->ws().tmp.need((long long)nb * n);
+        double* v = apply_potential<double>(P, nb, q);
+        closure_gather<double>(v, n3, P->geo.gm, P->geo.partner, P->geo.t, n, nb, tmp, n, st);
+        for (auto& s : st_local) s.applies_fp64 += 1;
+        kr_sub(bvec, tmp, d_all, nb, n, res, st);
+        kr_norm2(res, d_all, nb, n, n2 + nb, krylov_chunks(n), n2, st);
+        BAE_CUDA(cudaMemcpyAsync(rn2.data(), n2, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+        BAE_CUDA(cudaStreamSynchronize(st));
+        v_last = v;
+        for (int b = 0; b < nb; ++b) relres[b] = bn2[b] > 0 ? std::sqrt(rn2[b] / bn2[b]) : 0.0;
+    };
+
+    if (o.precision == BAE_FP64) {
+        for (int b = 0; b < nb; ++b) S[b].target = o.tol * std::sqrt(bn2[b]);
+        std::vector<int> applies(nb, 0);
+        gmres(P, BAE_FP64, nb, all, bvec, q, true, S, o.max_iter, o.restart, applies);
+        for (int b = 0; b < nb; ++b) {
+            st_local[b].iterations = S[b].iterations;
+            st_local[b].applies_fp64 += applies[b];
+        }
+        true_residual();
+    } else {
+        // iterative refinement: inner float32-apply GMRES on A d = r, q += d,
+        // r = b - A64 q in float64
+        double* d = P->ws().vstage.need((long long)nb * n);
+        BAE_CUDA(cudaMemcpyAsync(res, bvec, (size_t)nb * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        rn2 = bn2;
+        for (int b = 0; b < nb; ++b) relres[b] = bn2[b] > 0 ? 1.0 : 0.0;
+        int iters_left = o.max_iter;
+        for (int step = 0; step < std::max(1, o.max_refine); ++step) {
+            std::vector<int> act;
+            for (int b = 0; b < nb; ++b)
+                if (relres[b] > o.tol && bn2[b] > 0) act.push_back(b);
+            if (act.empty() || iters_left <= 0) break;
+            std::vector<RhsState> Si(nb);
+            for (int b : act) {
+                const double rn = std::sqrt(rn2[b]);
+                Si[b].target = std::max(o.inner_tol * rn, 0.3 * o.tol * std::sqrt(bn2[b]));
+            }
+            for (int b = 0; b < nb; ++b)
+                if (std::find(act.begin(), act.end(), b) == act.end()) Si[b].converged = true;
+            BAE_CUDA(cudaMemsetAsync(d, 0, (size_t)nb * n * sizeof(double), st));
+            std::vector<int> applies(nb, 0);
+            gmres(P, BAE_FP32, nb, act, res, d, true, Si, iters_left, o.restart, applies);
+            int used = 0;
+            for (int b : act) {
+                st_local[b].iterations += Si[b].iterations;
+                st_local[b].refinements += 1;
+                used = std::max(used, Si[b].iterations);
+            }
+            iters_left -= std::max(used, 1);
+            int* d_a = P->ws().active.need(nb);
+            BAE_CUDA(cudaMemcpyAsync(d_a, act.data(), act.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+            kr_add(d, d_a, (int)act.size(), n, q, st);
+            for (int b : act) st_local[b].applies_fp32 += applies[b];
+            true_residual();
+        }
+        if (!v_last) true_residual();
+    }
+
+    // outputs: u = u_p + K q on N+, density q
+    bool q_host = density && !is_device_ptr(density);
+    bool u_host = u && !is_device_ptr(u);
+    if (u) {
+        double* du = u_host ? P->ws().out_u.need((long long)nb * n3) : u;
+        volume_combine<double>(v_last, up, P->geo.flags, n3, nb, du, st);
+        if (u_host) BAE_CUDA(cudaMemcpyAsync(u, du, (size_t)nb * n3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    if (density) {
+        if (q_host) BAE_CUDA(cudaMemcpyAsync(density, q, (size_t)nb * n * sizeof(double), cudaMemcpyDeviceToHost, st));
+        else BAE_CUDA(cudaMemcpyAsync(density, q, (size_t)nb * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
+    BAE_CUDA(cudaEventRecord(P->ctx->ev1, st));
+    BAE_CUDA(cudaStreamSynchronize(st));
+    float ms = 0.f;
+    BAE_CUDA(cudaEventElapsedTime(&ms, P->ctx->ev0, P->ctx->ev1));
+    int rc = BAE_OK;
+    for (int b = 0; b < nb; ++b) {
+        st_local[b].rel_residual = relres[b];
+        st_local[b].ms_total = ms;
+        if (!(relres[b] <= o.tol) && bn2[b] > 0) rc = BAE_ERR_NOT_CONVERGED;
+    }
+    if (stats)
+        for (int b = 0; b < nb; ++b) stats[b] = st_local[b];
+    if (rc != BAE_OK) set_last_error("GMRES did not reach the requested tolerance");
+    return rc;
+}
+
+// Runs fn with device versions of (possibly host) in/out arrays.
+struct Staged {
+    bae_problem* P;
+    double* dev = nullptr;
+    const void* user = nullptr;
+    size_t bytes = 0;
+    bool host = false;
+};
+
+template <typename F>
+int guarded(F&& fn) {
+    try {
+        return fn();
+    } catch (const Error& e) {
+        set_last_error(e.what());
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        set_last_error("host allocation failed");
+        return BAE_ERR_OOM;
+    } catch (const std::exception& e) {
+        set_last_error(e.what());
+        return BAE_ERR_CUDA;
+    }
+}
+
+void check_device(bae_ctx* ctx) {
+    BAE_REQUIRE(ctx, BAE_ERR_INVALID_ARG, "null context");
+    BAE_CUDA(cudaSetDevice(ctx->device));
+}
+
+// copy a (host or device) input of `count` doubles into device memory
+const double* device_in(Grow<double>& buf, const double* p, long long count, cudaStream_t st) {
+    if (is_device_ptr(p)) return p;
+    double* d = buf.need(count);
+    BAE_CUDA(cudaMemcpyAsync(d, p, (size_t)count * sizeof(double), cudaMemcpyHostToDevice, st));
+    return d;
+}
+
+template <typename T>
+void copy_out(T* user, const T* dev, long long count, cudaStream_t st) {
+    BAE_CUDA(cudaMemcpyAsync(user, dev, (size_t)count * sizeof(T), cudaMemcpyDefault, st));
+}
+
+}  // namespace
+}  // namespace bae
+
+// =================================================================== C ABI
+extern "C" {
+
+int bae_version(void) { return 1; }
+
+long long bae_launch_count(void) { return bae::g_launches.load(); }
+
+int bae_profile_start(int max_launches) {
+    return guarded([&]() -> int {
+        BAE_REQUIRE(max_launches > 0, BAE_ERR_INVALID_ARG, "max_launches must be positive");
+        BAE_REQUIRE(!g_prof.on, BAE_ERR_INVALID_ARG, "profiling already started");
+        const size_t need = 2 * (size_t)max_launches;
+        while (g_prof.pool.size() < need) {
+            cudaEvent_t e;
+            BAE_CUDA(cudaEventCreate(&e));
+            g_prof.pool.push_back(e);
+        }
+        g_prof.used = 0;
+        g_prof.recs.clear();
+        g_prof.overflow = false;
+        g_prof.on = true;
+        return BAE_OK;
+    });
+}
+
+int bae_profile_stop(char* names, int names_len, double* total_ms, long long* launches, int max_kernels,
+                     int* n_kernels) {
+    return guarded([&]() -> int {
+        BAE_REQUIRE(g_prof.on, BAE_ERR_INVALID_ARG, "profiling not started");
+        g_prof.on = false;
+        BAE_CUDA(cudaDeviceSynchronize());
+        std::vector<std::string> order;
+        std::map<std::string, std::pair<double, long long>> agg;
+        for (const ProfRec& r : g_prof.recs) {
+            float ms = 0.f;
+            BAE_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+            auto it = agg.find(r.name);
+            if (it == agg.end()) {
+                order.push_back(r.name);
+                agg[r.name] = {ms, 1};
+            } else {
+                it->second.first += ms;
+                it->second.second += 1;
+            }
+        }
+        std::string joined;
+        int k = 0;
+        for (const std::string& nm : order) {
+            if (k >= max_kernels) break;
+            if (total_ms) total_ms[k] = agg[nm].first;
+            if (launches) launches[k] = agg[nm].second;
+            joined += nm;
+            joined += '\n';
+            ++k;
+        }
+        if (n_kernels) *n_kernels = k;
+        if (names && names_len > 0) {
+            const size_t n = std::min((size_t)names_len - 1, joined.size());
+            std::memcpy(names, joined.data(), n);
+            names[n] = 0;
+        }
+        g_prof.recs.clear();
+        if (g_prof.overflow) {
+            set_last_error("profile event pool overflowed; some launches were not timed");
+            return BAE_ERR_INVALID_ARG;
+        }
+        return BAE_OK;
+    });
+}
+
+const char* bae_last_error(void) { return bae::g_last_error.c_str(); }
+
+void bae_default_options(bae_options* o) {
+    if (!o) return;
+    o->tol = 1e-10;
+    o->max_iter = 500;
+    o->restart = 200;
+    o->precision = BAE_FP64;
+    o->max_refine = 8;
+    o->inner_tol = 1e-5;
+}
+
+int bae_ctx_create(int device, void* stream, bae_ctx** out) {
+    return guarded([&]() -> int {
+        BAE_REQUIRE(out, BAE_ERR_INVALID_ARG, "out is null");
+        int count = 0;
+        BAE_CUDA(cudaGetDeviceCount(&count));
+        BAE_REQUIRE(device >= 0 && device < count, BAE_ERR_INVALID_ARG, "no such CUDA device");
+        BAE_CUDA(cudaSetDevice(device));
+        auto c = std::make_unique<bae_ctx>();
+        c->device = device;
+        if (stream) {
+            c->stream = (cudaStream_t)stream;
+        } else {
+            BAE_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+            c->own_stream = true;
+        }
+        BAE_CUDA(cudaEventCreate(&c->ev0));
+        BAE_CUDA(cudaEventCreate(&c->ev1));
+        // keep freed blocks of the default pool for reuse (problem set-up
+        // and work space come from it)
+        cudaMemPool_t pool;
+        BAE_CUDA(cudaDeviceGetDefaultMemPool(&pool, device));
+        uint64_t thr = UINT64_MAX;
+        BAE_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+        c->ws.set_stream(c->stream);
+        *out = c.release();
+        return BAE_OK;
+    });
+}
+
+void bae_ctx_destroy(bae_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    ctx->cache.clear();
+    for (auto& kv : ctx->tw) {
+        dev_free(kv.second.tw64, ctx->stream);
+        dev_free(kv.second.tw32, ctx->stream);
+    }
+    ctx->ws = Workspace();
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+int bae_lgf_table(bae_ctx* ctx, int N, double s, double* values) {
+    return guarded([&]() -> int {
+        check_device(ctx);
+        BAE_REQUIRE(values, BAE_ERR_INVALID_ARG, "values is null");
+        BAE_REQUIRE(N >= 2 && N <= 256, BAE_ERR_INVALID_ARG, "N must be in [2, 256]");
+        const long long ntri = (long long)N * (N + 1) * (N + 2) / 6;
+        double* d = is_device_ptr(values) ? values : ctx->ws.out_u.need(ntri);
+        lgf_table(N, s, d, ctx->stream);
+        if (d != values) copy_out(values, d, ntri, ctx->stream);
+        BAE_CUDA(cudaStreamSynchronize(ctx->stream));
+        return BAE_OK;
+    });
+}
+
+int bae_lgf_spectrum(bae_ctx* ctx, int N, double s, double* ghat) {
+    return guarded([&]() -> int {
+        check_device(ctx);
+        BAE_REQUIRE(ghat, BAE_ERR_INVALID_ARG, "ghat is null");
+        BAE_REQUIRE(is_pow2(N) && N >= 8 && N <= 256, BAE_ERR_INVALID_ARG, "N must be a power of two in [8, 256]");
+        const long long n3 = (long long)(N + 1) * (N + 1) * (N + 1);
+        double* d = is_device_ptr(ghat) ? ghat : ctx->ws.out_u.need(n3);
+        lgf_spectrum(N, s, 1.0, d, nullptr, ctx->stream);
+        if (d != ghat) copy_out(ghat, d, n3, ctx->stream);
+        BAE_CUDA(cudaStreamSynchronize(ctx->stream));
+        return BAE_OK;
+    });
+}
+
+int bae_problem_create(bae_ctx* ctx, int N, double h, const double origin[3], const double* phi, double kappa2,
+                       int layer, bae_problem** out) {
+    return guarded([&]() -> int {
+        check_device(ctx);
+        BAE_REQUIRE(out && phi && origin, BAE_ERR_INVALID_ARG, "null argument");
+        BAE_REQUIRE(is_pow2(N) && N >= 8 && N <= 256, BAE_ERR_INVALID_ARG, "N must be a power of two in [8, 256]");
+        BAE_REQUIRE(std::isfinite(h) && h > 0, BAE_ERR_INVALID_ARG, "h must be positive and finite");
+        BAE_REQUIRE(std::isfinite(kappa2) && kappa2 >= 0, BAE_ERR_INVALID_ARG, "kappa2 must be finite and >= 0");
+        BAE_REQUIRE(std::isfinite(origin[0]) && std::isfinite(origin[1]) && std::isfinite(origin[2]),
+                    BAE_ERR_INVALID_ARG, "origin must be finite");
+        BAE_REQUIRE(layer == BAE_LAYER_DOUBLE || layer == BAE_LAYER_SINGLE, BAE_ERR_INVALID_ARG, "unknown layer");
+        auto P = std::make_unique<bae_problem>();
+        P->ctx = ctx;
+        P->kappa2 = kappa2;
+        P->s = kappa2 * h * h;
+        const long long n3 = (long long)N * N * N;
+        const double* d_phi = device_in(ctx->ws.in_f, phi, n3, ctx->stream);
+        try {
+            build_geometry(d_phi, N, h, origin, layer, P->geo, ctx->stream);
+        } catch (...) {
+            P->geo.release();
+            throw;
+        }
+        P->spec = ctx->spectrum(N, P->s);
+        *out = P.release();
+        return BAE_OK;
+    });
+}
+
+void bae_problem_destroy(bae_problem* P) {
+    if (!P) return;
+    cudaSetDevice(P->ctx->device);
+    cudaStreamSynchronize(P->ctx->stream);
+    P->geo.release();
+    delete P;
+}
+
+int bae_problem_sizes(const bae_problem* P, int64_t* n_gm, int64_t* n_gp, int64_t* n_mp) {
+    return guarded([&]() -> int {
+        BAE_REQUIRE(P, BAE_ERR_INVALID_ARG, "null problem");
+        if (n_gm) *n_gm = P->geo.n_gm;
+        if (n_gp) *n_gp = P->geo.n_gp;
+        if (n_mp) *n_mp = P->geo.n_mp;
+        return BAE_OK;
+    });
+}
+
+int bae_boundary_points(const bae_problem* P, double* xyz) {
+    return guarded([&]() -> int {
+        BAE_REQUIRE(P && xyz, BAE_ERR_INVALID_ARG, "null argument");
+        check_device(P->ctx);
+        copy_out(xyz, P->geo.xstar, 3 * P->geo.n_gm, P->ctx->stream);
+        BAE_CUDA(cudaStreamSynchronize(P->ctx->stream));
+        return BAE_OK;
+    });
+}
+
+int bae_classification(const bae_problem* P, uint8_t* flags, int32_t* gm_idx, int32_t* partner, double* t) {
+    return guarded([&]() -> int {
+        BAE_REQUIRE(P, BAE_ERR_INVALID_ARG, "null problem");
+        check_device(P->ctx);
+        cudaStream_t st = P->ctx->stream;
+        const long long n3 = (long long)P->geo.N * P->geo.N * P->geo.N;
+        if (flags) copy_out(flags, P->geo.flags, n3, st);
+        if (gm_idx) copy_out(gm_idx, P->geo.gm, P->geo.n_gm, st);
+        if (partner) copy_out(partner, P->geo.partner, P->geo.n_gm, st);
+        if (t) copy_out(t, P->geo.t, P->geo.n_gm, st);
+        BAE_CUDA(cudaStreamSynchronize(st));
+        return BAE_OK;
+    });
+}
+
+int bae_potential_apply(bae_problem* P, int precision, const double* q, double* v) {
+    return guarded([&]() -> int {
+        BAE_REQUIRE(P && q && v, BAE_ERR_INVALID_ARG, "null argument");
+        BAE_REQUIRE(precision == BAE_FP64 || precision == BAE_FP32, BAE_ERR_INVALID_ARG,
+                    "precision must be BAE_FP64 or BAE_FP32");
+        check_device(P->ctx);
+        cudaStream_t st = P->ctx->stream;
+        const double* dq = device_in(P->ws().in_g, q, P->geo.n_gm, st);
+        const long long n3 = P->n3();
+        const bool vh = !is_device_ptr(v);
+        double* dv = vh ? P->ws().out_u.need(n3) : v;
+        if (precision == BAE_FP64) {
+            double* r = apply_potential<double>(P, 1, dq);
+            BAE_CUDA(cudaMemcpyAsync(dv, r, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        } else {
+            float* r = apply_potential<float>(P, 1, dq);
+            widen<float>(r, n3, dv, st);
+        }
+        if (vh) copy_out(v, dv, n3, st);
+        BAE_CUDA(cudaStreamSynchronize(st));
+        return BAE_OK;
+    });
+}
+
+int bae_boundary_apply(bae_problem* P, int precision, const double* q, double* Aq) {
+    return guarded([&]() -> int {
+        BAE_REQUIRE(P && q && Aq, BAE_ERR_INVALID_ARG, "null argument");
+        BAE_REQUIRE(precision == BAE_FP64 || precision == BAE_FP32, BAE_ERR_INVALID_ARG,
+                    "precision must be BAE_FP64 or BAE_FP32");
+        check_device(P->ctx);
+        cudaStream_t st = P->ctx->stream;
+        const long long n = P->geo.n_gm;
+        const double* dq = device_in(P->ws().in_g, q, n, st);
+        const bool oh = !is_device_ptr(Aq);
+        double* dA = oh ? P->ws().out_q.need(n) : Aq;
+        boundary_apply_prec(P, precision, 1, dq, dA);
+        if (oh) copy_out(Aq, dA, n, st);
+        BAE_CUDA(cudaStreamSynchronize(st));
+        return BAE_OK;
+    });
+}
+
+int bae_particular(bae_problem* P, int precision, const double* f, double* up) {
+    return guarded([&]() -> int {
+        BAE_REQUIRE(P && f && up, BAE_ERR_INVALID_ARG, "null argument");
+        BAE_REQUIRE(precision == BAE_FP64 || precision == BAE_FP32, BAE_ERR_INVALID_ARG,
+                    "precision must be BAE_FP64 or BAE_FP32");
+        check_device(P->ctx);
+        cudaStream_t st = P->ctx->stream;
+        const long long n3 = P->n3();
+        const double* df = device_in(P->ws().in_f, f, n3, st);
+        const bool oh = !is_device_ptr(up);
+        double* du = oh ? P->ws().out_u.need(n3) : up;
+        const double h2 = P->geo.h * P->geo.h;
+        if (precision == BAE_FP64) {
+            double* r = apply_volume<double>(P, 1, df, h2);
+            BAE_CUDA(cudaMemcpyAsync(du, r, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        } else {
+            float* r = apply_volume<float>(P, 1, df, h2);
+            widen<float>(r, n3, du, st);
+        }
+        if (oh) copy_out(up, du, n3, st);
+        BAE_CUDA(cudaStreamSynchronize(st));
+        return BAE_OK;
+    });
+}
+
+int bae_solve(bae_problem* P, const double* f, const double* g, const bae_options* opts, double* density,
+              double* u, bae_stats* stats) {
+    return guarded([&]() -> int {
+        BAE_REQUIRE(P, BAE_ERR_INVALID_ARG, "null problem");
+        check_device(P->ctx);
+        return solve_impl(P, 1, f, g, opts, density, u, stats);
+    });
+}
+
+int bae_solve_batched(bae_problem* P, int nrhs, const double* f, const double* g, const bae_options* opts,
+                      double* density, double* u, bae_stats* stats) {
+    return guarded([&]() -> int {
+        BAE_REQUIRE(P, BAE_ERR_INVALID_ARG, "null problem");
+        BAE_REQUIRE(nrhs >= 1 && nrhs <= 65535, BAE_ERR_INVALID_ARG, "nrhs must be in [1, 65535]");
+        check_device(P->ctx);
+        return solve_impl(P, nrhs, f, g, opts, density, u, stats);
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,46 @@
+// Point sets, closure and source stencil of a problem (Section 2.1, 3.2).
+#pragma once
+
+#include "common.cuh"
+#include "conv.cuh"
+
+namespace bae {
+
+// Owning device arrays describing one classified grid.
+struct Geometry {
+    int N = 0;
+    double h = 0.0;
+    double origin[3] = {0, 0, 0};
+    int layer = BAE_LAYER_DOUBLE;
+    cudaStream_t stream = nullptr;  // stream that owns the allocations
+    long long n_gm = 0, n_gp = 0, n_mp = 0, n_src = 0, n_terms = 0;
+    uint8_t* flags = nullptr;     // N^3: bit0 M+, bit1 gamma-, bit2 gamma+, bit3 D-node, bits4-6 |D_n|
+    int* gm = nullptr;            // gamma- linear indices, lexicographic
+    int* partner = nullptr;       // closure partner per gamma- node
+    double* t = nullptr;          // closure weight per gamma- node
+    double* xstar = nullptr;      // boundary points, 3 per gamma- node
+    int* line_off = nullptr;      // source recipe (see SrcRecipe)
+    int* src_lin = nullptr;
+    int* term_off = nullptr;
+    int* term_idx = nullptr;
+    float* term_coef = nullptr;
+
+    SrcRecipe recipe() const {
+        SrcRecipe r;
+        r.line_off = line_off;
+        r.src_lin = src_lin;
+        r.term_off = term_off;
+        r.term_idx = term_idx;
+        r.term_coef = term_coef;
+        return r;
+    }
+    void release();
+};
+
+// Classifies phi (device, N^3 float64), builds the closure and the source
+// recipe. Throws Error(BAE_ERR_GEOMETRY) when gamma- is empty or when M+ or
+// gamma- reaches the box faces, Error(BAE_ERR_INVALID_ARG) on non-finite phi.
+void build_geometry(const double* phi, int N, double h, const double origin[3], int layer,
+                    Geometry& g, cudaStream_t st);
+
+}  // namespace bae

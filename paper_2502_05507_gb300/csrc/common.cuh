@@ -1,0 +1,98 @@
+// Shared helpers of the BAE library: error reporting, complex arithmetic,
+// launch checks. Device code targets sm_103a only.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <stdexcept>
+#include <string>
+
+#include "../../include/bae.h"
+
+namespace bae {
+
+// Error carried from deep inside the library to the C ABI boundary, where
+// it becomes a return code and the thread-local message.
+struct Error : std::runtime_error {
+    int code;
+    Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+void set_last_error(const std::string& msg);
+
+// Launch bookkeeping: every kernel launch of the library goes through
+// BAE_LAUNCH, which counts it and, while profiling is on, brackets it with
+// CUDA events on its stream (per-kernel device time, see bae_profile_*).
+void count_launch();
+void prof_push(const char* name, cudaStream_t st);
+void prof_pop(cudaStream_t st);
+
+// Stream-ordered device allocation from the device's default memory pool
+// (kept pooled: freed blocks are reused without returning to the driver).
+void* dev_alloc(size_t bytes, cudaStream_t st);
+void dev_free(void* p, cudaStream_t st);
+template <typename T>
+T* dev_alloc_n(long long n, cudaStream_t st) {
+    return static_cast<T*>(dev_alloc((size_t)(n > 0 ? n : 1) * sizeof(T), st));
+}
+
+#define BAE_CUDA(call)                                                              \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess) {                                                    \
+            int c_ = (e_ == cudaErrorMemoryAllocation) ? BAE_ERR_OOM : BAE_ERR_CUDA; \
+            throw ::bae::Error(c_, std::string(#call) + ": " + cudaGetErrorString(e_) \
+                                       + " (" __FILE__ ":" + std::to_string(__LINE__) + ")"); \
+        }                                                                           \
+    } while (0)
+
+#define BAE_CHECK_LAUNCH() BAE_CUDA(cudaGetLastError())
+
+#define BAE_LAUNCH(name, st, ...)            \
+    do {                                     \
+        ::bae::prof_push((name), (st));      \
+        __VA_ARGS__;                         \
+        ::bae::prof_pop(st);                 \
+        ::bae::count_launch();               \
+        BAE_CHECK_LAUNCH();                  \
+    } while (0)
+
+#define BAE_REQUIRE(cond, code, msg)                        \
+    do {                                                    \
+        if (!(cond)) throw ::bae::Error((code), (msg));     \
+    } while (0)
+
+// ----------------------------------------------------------- complex types
+template <typename T> struct Cplx;
+template <> struct Cplx<float> { using type = float2; };
+template <> struct Cplx<double> { using type = double2; };
+template <typename T> using cplx_t = typename Cplx<T>::type;
+
+template <typename C> __device__ __forceinline__ C cmake(decltype(C::x) a, decltype(C::x) b) {
+    C r; r.x = a; r.y = b; return r;
+}
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return cmake<C>(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return cmake<C>(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+    return cmake<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename C> __device__ __forceinline__ C cmulc(C a, C b) {
+    return cmake<C>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <typename C> __device__ __forceinline__ C cconj(C a) { return cmake<C>(a.x, -a.y); }
+template <typename C, typename T> __device__ __forceinline__ C cscale(C a, T s) { return cmake<C>(a.x * s, a.y * s); }
+
+inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+inline bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
+
+inline int ilog2(long long v) {
+    int r = 0;
+    while ((1LL << r) < v) ++r;
+    return r;
+}
+
+}  // namespace bae

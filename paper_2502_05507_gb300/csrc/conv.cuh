@@ -1,0 +1,59 @@
+// Host interface of the LGF convolution (the potential apply).
+#pragma once
+
+#include "common.cuh"
+
+namespace bae {
+
+// Compact description of the source stencil rho = B q (Section 3.2): the
+// source nodes in lexicographic order, grouped by (i,j) grid line, each
+// with its terms rho(x) = sum coef * q[idx].
+struct SrcRecipe {
+    const int* line_off = nullptr;   // N*N + 1 offsets into src_lin
+    const int* src_lin = nullptr;    // linear grid index of each source node
+    const int* term_off = nullptr;   // ns + 1 offsets into term_idx/term_coef
+    const int* term_idx = nullptr;   // gamma- index of each term
+    const float* term_coef = nullptr;
+};
+
+enum SourceMode { SRC_DENSITY = 0, SRC_VOLUME = 1 };
+
+template <typename T>
+struct ConvArgs {
+    int N = 0;
+    int nbatch = 1;
+    SourceMode mode = SRC_DENSITY;
+    // SRC_DENSITY: q [nbatch][q_stride] float64 density on gamma-
+    const double* q = nullptr;
+    long long q_stride = 0;
+    SrcRecipe rec;
+    // SRC_VOLUME: rho = scale * f on nodes with (flags & 1)
+    const double* f = nullptr;
+    const uint8_t* flags = nullptr;
+    double scale = 1.0;
+    // work buffers (per batch item): A = N*N*(N+1), B = N*2N*(N+1) complex
+    cplx_t<T>* A = nullptr;
+    cplx_t<T>* B = nullptr;
+    const T* ghat = nullptr;      // (N+1)^3 octant, includes 1/(2N)^3
+    const cplx_t<T>* tw = nullptr;  // exp(-2 pi i m / 2N), m < 2N
+    T* v = nullptr;               // [nbatch][N^3] output potential
+};
+
+template <typename T>
+void conv_apply(const ConvArgs<T>& a, cudaStream_t st);
+
+// out[b][r] = t[r] v[b][gm[r]] + (1 - t[r]) v[b][partner[r]]
+template <typename T>
+void closure_gather(const T* v, long long v_stride, const int* gm, const int* partner, const double* t,
+                    int n, int nbatch, double* out, long long out_stride, cudaStream_t st);
+
+// u[b][x] = (nplus(x) ? add[b][x] + v[b][x] : 0) over the N^3 grid
+template <typename T>
+void volume_combine(const T* v, const double* add, const uint8_t* flags, long long n3, int nbatch,
+                    double* u, cudaStream_t st);
+
+// v (T) -> out (double), plain copy
+template <typename T>
+void widen(const T* v, long long n, double* out, cudaStream_t st);
+
+}  // namespace bae
