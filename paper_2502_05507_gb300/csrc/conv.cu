@@ -11,7 +11,10 @@
 // Data layout (per right-hand side), i = x index (outermost), k = z (fastest):
 //   A[i][j][kk]  i < N, j < N,  kk <= N   after the R2C pass along k
 //   B[i][jj][kk] i < N, jj < 2N, kk <= N  after the pass along j
-// Passes (forward, then inverse in reverse order):
+// Every pass transforms its lines in registers (four-step factorisation,
+// one shared-memory exchange per transform, see fft2.cuh), reading and
+// writing global memory directly. Passes (forward, then inverse in reverse
+// order):
 //   kpass   : two real k-lines per complex FFT (x_a + i x_b), only the N
 //             nonzero samples are loaded, spectra split by Hermitian symmetry
 //   jpass   : FFT along j (N nonzero inputs, 2N outputs)      A -> B
@@ -20,84 +23,106 @@
 //   jpass^-1: inverse along j, keep j < N                     B -> A
 //   kpass^-1: C2R of two lines per complex inverse FFT, keep k < N -> v
 #include "conv.cuh"
-#include "fft.cuh"
+#include "fft2.cuh"
 
 namespace bae {
 
 namespace {
 
-template <int L> struct Shape {
-    static constexpr int TPL = L / 8;                       // threads per line
-    static constexpr int PPC = (256 / TPL) > 0 ? 256 / TPL : 1;  // k-pass FFTs per CTA
-    static constexpr int W = (256 / TPL) < 8 ? 8 : ((256 / TPL) > 32 ? 32 : 256 / TPL);  // columns per CTA
-    static constexpr int STRIDE = L + 1;                    // padded line stride in smem
+// Launch geometry per transform length and precision.
+template <typename T, int L> struct Geo {
+    using C = cplx_t<T>;
+    static constexpr int R1 = Factors<L>::R1, R2 = Factors<L>::R2;
+    // column passes: W columns per CTA, R1 threads per column
+    static constexpr int WB = 65536 / (L * (int)sizeof(C));
+    static constexpr int W = WB > 32 ? 32 : (WB < 8 ? 8 : WB);
+    static constexpr int CT = W * R1;
+    // line passes (k): P line pairs per CTA, R1 threads per pair
+    static constexpr int PB = 65536 / (L * (int)sizeof(C));
+    static constexpr int P = (256 / R1) < PB ? (256 / R1) : (PB < 4 ? 4 : PB);
+    static constexpr int KT = P * R1;
+    static constexpr int XS = R2 * (R1 + 1) + 1;   // exchange stride per pair (odd)
 };
 
-template <typename C>
-__device__ __forceinline__ void load_twiddles(C* s_tw, const C* tw, int L) {
-    for (int m = threadIdx.x; m < L; m += blockDim.x) s_tw[m] = tw[m];
-}
+template <typename T>
+const char* kname(const char* f32, const char* f64) { return sizeof(T) == 4 ? f32 : f64; }
 
 // ------------------------------------------------------------- k pass (R2C)
+// Two real k-lines (i, 2p) and (i, 2p+1) per complex transform z = x_a + i x_b.
 template <typename T, int L>
-__global__ void __launch_bounds__(256) k_kpass_fwd(ConvArgs<T> a) {
+__global__ void __launch_bounds__(Geo<T, L>::KT) k_kpass_fwd(ConvArgs<T> a) {
     using C = cplx_t<T>;
-    using S = Shape<L>;
-    constexpr int N = L / 2;
-    constexpr int N1 = N + 1;
+    using G = Geo<T, L>;
+    constexpr int N = L / 2, N1 = N + 1, R1 = G::R1, R2 = G::R2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* s_tw = reinterpret_cast<C*>(smem_raw);
-    C* s_lines = s_tw + L;
+    C* xch = reinterpret_cast<C*>(smem_raw);                 // P * XS
+    T* rho = reinterpret_cast<T*>(xch + G::P * G::XS);      // P * 2N
 
     const int b = blockIdx.z;
-    const int p = threadIdx.x / S::TPL;          // FFT slot in this CTA
-    const int t = threadIdx.x % S::TPL;
-    const long long pair = (long long)blockIdx.x * S::PPC + p;
+    const int t = threadIdx.x % R1;
+    const int p = threadIdx.x / R1;
+    const long long pair = (long long)blockIdx.x * G::P + p;
     const bool active = pair < (long long)N * N / 2;
-    C* line = s_lines + p * S::STRIDE;
+    const long long la = 2 * pair, lb = la + 1;
+    T* r = rho + p * 2 * N;
 
-    load_twiddles(s_tw, a.tw, L);
-    for (int k = t; k < L; k += S::TPL) line[k] = cmake<C>((T)0, (T)0);
-    __syncthreads();
-
-    if (active) {
-        const long long la = 2 * pair, lb = la + 1;
-        if (a.mode == SRC_DENSITY) {
+    C v[R2];
+    if (a.mode == SRC_DENSITY) {
+        for (int k = t; k < 2 * N; k += R1) r[k] = (T)0;
+        __syncthreads();
+        if (active) {
             const double* q = a.q + (long long)b * a.q_stride;
 #pragma unroll
             for (int half = 0; half < 2; ++half) {
                 const long long l = half ? lb : la;
                 const int s0 = a.rec.line_off[l], s1 = a.rec.line_off[l + 1];
-                for (int s = s0 + t; s < s1; s += S::TPL) {
+                for (int s = s0 + t; s < s1; s += R1) {
                     const int k = a.rec.src_lin[s] - (int)(l * N);
                     double val = 0.0;
                     for (int e = a.rec.term_off[s]; e < a.rec.term_off[s + 1]; ++e)
                         val += (double)a.rec.term_coef[e] * q[a.rec.term_idx[e]];
-                    if (half) line[k].y = (T)val; else line[k].x = (T)val;
+                    r[half * N + k] = (T)val;
                 }
             }
-        } else {
-            const double* f = a.f + (long long)b * N * N * N;
-            for (int k = t; k < N; k += S::TPL) {
-                const long long xa = la * N + k, xb = lb * N + k;
-                const double va = (a.flags[xa] & 1) ? a.scale * f[xa] : 0.0;
-                const double vb = (a.flags[xb] & 1) ? a.scale * f[xb] : 0.0;
-                line[k] = cmake<C>((T)va, (T)vb);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < R2; ++m) {
+            const int n = t + R1 * m;
+            v[m] = (n < N) ? cmake<C>(r[n], r[N + n]) : cmake<C>((T)0, (T)0);
+        }
+    } else {
+        const double* f = a.f + (long long)b * N * N * N;
+#pragma unroll
+        for (int m = 0; m < R2; ++m) {
+            const int n = t + R1 * m;
+            T va = 0, vb = 0;
+            if (active && n < N) {
+                const long long xa = la * N + n, xb = lb * N + n;
+                va = (a.flags[xa] & 1) ? (T)(a.scale * f[xa]) : (T)0;
+                vb = (a.flags[xb] & 1) ? (T)(a.scale * f[xb]) : (T)0;
             }
+            v[m] = cmake<C>(va, vb);
         }
     }
+    const int base = p * G::XS;
+    fft_n2k<L, false>(v, xch, base, R1 + 1, 1, t, a.tw);
+    // natural order into the exchange area, then split the two spectra
+    // X_a = (Z[k] + conj Z[L-k]) / 2, X_b = (Z[k] - conj Z[L-k]) / 2i
+    C* z = xch + base;
+#pragma unroll
+    for (int q = 0; q < R2 / R1; ++q)
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) z[t + q * R1 + R2 * k1] = v[q * R1 + k1];
     __syncthreads();
-    fft_line<C, L, false>(line, s_tw, t);
-
     if (active) {
         C* A = a.A + (long long)b * N * N * N1;
-        const long long la = 2 * pair, lb = la + 1;
         const T half = (T)0.5;
-        for (int k = t; k <= N; k += S::TPL) {
-            const C z = line[k];
-            const C zr = line[(L - k) & (L - 1)];
-            A[la * N1 + k] = cmake<C>((z.x + zr.x) * half, (z.y - zr.y) * half);
-            A[lb * N1 + k] = cmake<C>((z.y + zr.y) * half, (zr.x - z.x) * half);
+        for (int k = t; k <= N; k += R1) {
+            const C zk = z[k];
+            const C zr = z[(L - k) & (L - 1)];
+            A[la * N1 + k] = cmake<C>((zk.x + zr.x) * half, (zk.y - zr.y) * half);
+            A[lb * N1 + k] = cmake<C>((zk.y + zr.y) * half, (zr.x - zk.x) * half);
         }
     }
 }
@@ -106,134 +131,147 @@ __global__ void __launch_bounds__(256) k_kpass_fwd(ConvArgs<T> a) {
 enum ColMode { COL_FWD_J = 0, COL_CONV_I = 1, COL_INV_J = 2 };
 
 template <typename T, int L, int MODE>
-__global__ void __launch_bounds__(512) k_colpass(ConvArgs<T> a) {
+__global__ void __launch_bounds__(Geo<T, L>::CT) k_colpass(ConvArgs<T> a) {
     using C = cplx_t<T>;
-    using S = Shape<L>;
-    constexpr int N = L / 2;
-    constexpr int N1 = N + 1;
-    constexpr int W = S::W;
+    using G = Geo<T, L>;
+    constexpr int N = L / 2, N1 = N + 1, R1 = G::R1, R2 = G::R2, W = G::W, Q = R2 / R1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* s_tw = reinterpret_cast<C*>(smem_raw);
-    C* s_lines = s_tw + L;
+    C* xch = reinterpret_cast<C*>(smem_raw);   // L * W
 
     const int b = blockIdx.z;
     const int o = blockIdx.y;               // i (j passes) or jj (i pass)
-    const int col0 = blockIdx.x * W;        // first kk column
-    const int nthr = blockDim.x;
+    const int c = threadIdx.x % W;
+    const int t = threadIdx.x / W;
+    const int col = blockIdx.x * W + c;     // kk
+    const bool ok = col < N1;
 
+    C* Ab = a.A + (long long)b * N * N * N1;
+    C* Bb = a.B + (long long)b * N * (2 * N) * N1;
     const C* in;
     C* out;
     long long stride;
-    int n_in, n_out;
-    C* Ab = a.A + (long long)b * N * N * N1;
-    C* Bb = a.B + (long long)b * N * (2 * N) * N1;
     if (MODE == COL_FWD_J) {
-        in = Ab + (long long)o * N * N1; out = Bb + (long long)o * (2 * N) * N1;
-        stride = N1; n_in = N; n_out = 2 * N;
+        in = Ab + (long long)o * N * N1 + col; out = Bb + (long long)o * (2 * N) * N1 + col; stride = N1;
     } else if (MODE == COL_CONV_I) {
-        in = Bb + (long long)o * N1; out = Bb + (long long)o * N1;
-        stride = (long long)(2 * N) * N1; n_in = N; n_out = N;
+        out = Bb + (long long)o * N1 + col; in = out; stride = (long long)(2 * N) * N1;
     } else {
-        in = Bb + (long long)o * (2 * N) * N1; out = Ab + (long long)o * N * N1;
-        stride = N1; n_in = 2 * N; n_out = N;
+        in = Bb + (long long)o * (2 * N) * N1 + col; out = Ab + (long long)o * N * N1 + col; stride = N1;
     }
 
-    load_twiddles(s_tw, a.tw, L);
-    for (int idx = threadIdx.x; idx < W * L; idx += nthr) {
-        const int w = idx % W, e = idx / W;
-        const int col = col0 + w;
-        C val = cmake<C>((T)0, (T)0);
-        if (e < n_in && col < N1) val = in[e * stride + col];
-        s_lines[w * S::STRIDE + e] = val;
-    }
-    __syncthreads();
-
-    const int w = threadIdx.x / S::TPL;
-    const int t = threadIdx.x % S::TPL;
-    C* line = s_lines + w * S::STRIDE;
-    fft_line<C, L, MODE == COL_INV_J>(line, s_tw, t);
-
-    if (MODE == COL_CONV_I) {
-        const int col = col0 + w;
-        if (col < N1) {
-            const int jj = o <= N ? o : L - o;
-            const T* g = a.ghat + (long long)jj * N1 + col;
-            for (int e = t; e < L; e += S::TPL) {
-                const int ii = e <= N ? e : L - e;
-                const T gv = g[(long long)ii * N1 * N1];
-                line[e] = cscale(line[e], gv);
+    C v[R2];
+    const C zero = cmake<C>((T)0, (T)0);
+    if (MODE == COL_INV_J) {
+        // k-layout load of all L rows
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+#pragma unroll
+            for (int k1 = 0; k1 < R1; ++k1) {
+                const int k = t + q * R1 + R2 * k1;
+                v[q * R1 + k1] = ok ? in[k * stride] : zero;
             }
+        fft_k2n<L, true>(v, xch, c, R1 * W, W, t, a.tw);
+    } else {
+        // n-layout load of the N nonzero rows
+#pragma unroll
+        for (int m = 0; m < R2; ++m) {
+            const int n = t + R1 * m;
+            v[m] = (ok && n < N) ? in[n * stride] : zero;
         }
-        __syncthreads();
-        fft_line<C, L, true>(line, s_tw, t);
+        fft_n2k<L, false>(v, xch, c, R1 * W, W, t, a.tw);
     }
 
-    for (int idx = threadIdx.x; idx < W * n_out; idx += nthr) {
-        const int ww = idx % W, e = idx / W;
-        const int col = col0 + ww;
-        if (col < N1) out[e * stride + col] = s_lines[ww * S::STRIDE + e];
+    if (MODE == COL_FWD_J) {
+        if (ok) {
+#pragma unroll
+            for (int q = 0; q < Q; ++q)
+#pragma unroll
+                for (int k1 = 0; k1 < R1; ++k1) out[(t + q * R1 + R2 * k1) * stride] = v[q * R1 + k1];
+        }
+        return;
+    }
+    if (MODE == COL_CONV_I) {
+        // times the real, even spectrum (octant fold), then back
+        const int jj = o <= N ? o : L - o;
+        const T* g = a.ghat + (long long)jj * N1 + (ok ? col : 0);
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+#pragma unroll
+            for (int k1 = 0; k1 < R1; ++k1) {
+                const int k = t + q * R1 + R2 * k1;
+                const int ii = k <= N ? k : L - k;
+                v[q * R1 + k1] = cscale(v[q * R1 + k1], g[(long long)ii * N1 * N1]);
+            }
+        fft_k2n<L, true>(v, xch, c, R1 * W, W, t, a.tw);
+    }
+    // n-layout store of the first N rows
+    if (ok) {
+#pragma unroll
+        for (int m = 0; m < R2; ++m) {
+            const int n = t + R1 * m;
+            if (n < N) out[n * stride] = v[m];
+        }
     }
 }
 
 // ----------------------------------------------------------- k pass (C2R)
 template <typename T, int L>
-__global__ void __launch_bounds__(256) k_kpass_inv(ConvArgs<T> a) {
+__global__ void __launch_bounds__(Geo<T, L>::KT) k_kpass_inv(ConvArgs<T> a) {
     using C = cplx_t<T>;
-    using S = Shape<L>;
-    constexpr int N = L / 2;
-    constexpr int N1 = N + 1;
+    using G = Geo<T, L>;
+    constexpr int N = L / 2, N1 = N + 1, R1 = G::R1, R2 = G::R2, Q = R2 / R1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* s_tw = reinterpret_cast<C*>(smem_raw);
-    C* s_lines = s_tw + L;
+    C* xch = reinterpret_cast<C*>(smem_raw);
 
     const int b = blockIdx.z;
-    const int p = threadIdx.x / S::TPL;
-    const int t = threadIdx.x % S::TPL;
-    const long long pair = (long long)blockIdx.x * S::PPC + p;
+    const int t = threadIdx.x % R1;
+    const int p = threadIdx.x / R1;
+    const long long pair = (long long)blockIdx.x * G::P + p;
     const bool active = pair < (long long)N * N / 2;
-    C* line = s_lines + p * S::STRIDE;
     const long long la = 2 * pair, lb = la + 1;
     const C* A = a.A + (long long)b * N * N * N1;
 
-    load_twiddles(s_tw, a.tw, L);
-    for (int k = t; k < L; k += S::TPL) {
-        C z = cmake<C>((T)0, (T)0);
-        if (active) {
-            C xa, xb;
-            if (k <= N) {
-                xa = A[la * N1 + k];
-                xb = A[lb * N1 + k];
-                if (k == 0 || k == N) { xa.y = (T)0; xb.y = (T)0; }
-            } else {
-                xa = cconj(A[la * N1 + (L - k)]);
-                xb = cconj(A[lb * N1 + (L - k)]);
+    C v[R2];
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) {
+            const int k = t + q * R1 + R2 * k1;
+            C z = cmake<C>((T)0, (T)0);
+            if (active) {
+                C xa, xb;
+                if (k <= N) {
+                    xa = A[la * N1 + k];
+                    xb = A[lb * N1 + k];
+                    if (k == 0 || k == N) { xa.y = (T)0; xb.y = (T)0; }
+                } else {
+                    xa = cconj(A[la * N1 + (L - k)]);
+                    xb = cconj(A[lb * N1 + (L - k)]);
+                }
+                z = cmake<C>(xa.x - xb.y, xa.y + xb.x);   // xa + i xb
             }
-            z = cmake<C>(xa.x - xb.y, xa.y + xb.x);   // xa + i xb
+            v[q * R1 + k1] = z;
         }
-        line[k] = z;
-    }
-    __syncthreads();
-    fft_line<C, L, true>(line, s_tw, t);
+    fft_k2n<L, true>(v, xch, p * G::XS, R1 + 1, 1, t, a.tw);
     if (active) {
-        T* v = a.v + (long long)b * N * N * N;
-        for (int k = t; k < N; k += S::TPL) {
-            const C z = line[k];
-            v[la * N + k] = z.x;
-            v[lb * N + k] = z.y;
+        T* out = a.v + (long long)b * N * N * N;
+#pragma unroll
+        for (int m = 0; m < R2; ++m) {
+            const int n = t + R1 * m;
+            if (n < N) {
+                out[la * N + n] = v[m].x;
+                out[lb * N + n] = v[m].y;
+            }
         }
     }
 }
 
-template <typename T>
-const char* kname(const char* f32, const char* f64) { return sizeof(T) == 4 ? f32 : f64; }
-
 template <typename T, int L>
 void run_conv(const ConvArgs<T>& a, cudaStream_t st) {
     using C = cplx_t<T>;
-    using S = Shape<L>;
+    using G = Geo<T, L>;
     constexpr int N = L / 2;
-    const size_t smem_k = (size_t)(L + S::PPC * S::STRIDE) * sizeof(C);
-    const size_t smem_c = (size_t)(L + S::W * S::STRIDE) * sizeof(C);
+    const size_t smem_k = (size_t)G::P * G::XS * sizeof(C) + (size_t)G::P * 2 * N * sizeof(T);
+    const size_t smem_c = (size_t)L * G::W * sizeof(C);
     static bool configured = false;  // per instantiation
     if (!configured) {
         BAE_CUDA(cudaFuncSetAttribute(k_kpass_fwd<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_k));
@@ -244,15 +282,13 @@ void run_conv(const ConvArgs<T>& a, cudaStream_t st) {
         configured = true;
     }
     const int nb = a.nbatch;
-    const dim3 gk(ceil_div((long long)N * N / 2, S::PPC), 1, nb);
-    const int tk = S::PPC * S::TPL;
-    const int ncolblk = ceil_div(N + 1, S::W);
-    const int tc = S::W * S::TPL;
-    BAE_LAUNCH(kname<T>("conv_kfwd.f32", "conv_kfwd.f64"), st, k_kpass_fwd<T, L><<<gk, tk, smem_k, st>>>(a));
-    BAE_LAUNCH(kname<T>("conv_jfwd.f32", "conv_jfwd.f64"), st, k_colpass<T, L, COL_FWD_J><<<dim3(ncolblk, N, nb), tc, smem_c, st>>>(a));
-    BAE_LAUNCH(kname<T>("conv_i.f32", "conv_i.f64"), st, k_colpass<T, L, COL_CONV_I><<<dim3(ncolblk, 2 * N, nb), tc, smem_c, st>>>(a));
-    BAE_LAUNCH(kname<T>("conv_jinv.f32", "conv_jinv.f64"), st, k_colpass<T, L, COL_INV_J><<<dim3(ncolblk, N, nb), tc, smem_c, st>>>(a));
-    BAE_LAUNCH(kname<T>("conv_kinv.f32", "conv_kinv.f64"), st, k_kpass_inv<T, L><<<gk, tk, smem_k, st>>>(a));
+    const dim3 gk(ceil_div((long long)N * N / 2, G::P), 1, nb);
+    const int ncolblk = ceil_div(N + 1, G::W);
+    BAE_LAUNCH(kname<T>("conv_kfwd.f32", "conv_kfwd.f64"), st, k_kpass_fwd<T, L><<<gk, G::KT, smem_k, st>>>(a));
+    BAE_LAUNCH(kname<T>("conv_jfwd.f32", "conv_jfwd.f64"), st, k_colpass<T, L, COL_FWD_J><<<dim3(ncolblk, N, nb), G::CT, smem_c, st>>>(a));
+    BAE_LAUNCH(kname<T>("conv_i.f32", "conv_i.f64"), st, k_colpass<T, L, COL_CONV_I><<<dim3(ncolblk, 2 * N, nb), G::CT, smem_c, st>>>(a));
+    BAE_LAUNCH(kname<T>("conv_jinv.f32", "conv_jinv.f64"), st, k_colpass<T, L, COL_INV_J><<<dim3(ncolblk, N, nb), G::CT, smem_c, st>>>(a));
+    BAE_LAUNCH(kname<T>("conv_kinv.f32", "conv_kinv.f64"), st, k_kpass_inv<T, L><<<gk, G::KT, smem_k, st>>>(a));
 }
 
 // ------------------------------------------------------------------ gathers

@@ -1,0 +1,181 @@
+// Register-resident FFT building blocks for the convolution passes.
+//
+// A transform of length L = R1 * R2 (R2 = R1 or 2 R1) is done by R1 threads
+// per line with the four-step factorisation n = n1 + R1 n2, k = k2 + R2 k1:
+//   X[k2 + R2 k1] = sum_n1 W_R1^{n1 k1} W_L^{n1 k2} sum_n2 x[n1 + R1 n2] W_R2^{n2 k2}.
+// "n-layout": thread t holds x[t + R1 m], m < R2 (global loads/stores of a
+// strided line are coalesced across the columns a warp covers).
+// "k-layout": thread t holds X[k2 + R2 k1] for k2 = t + q R1 (q < R2/R1),
+// k1 < R1, in v[q R1 + k1].
+// Forward: R2-point DFT in registers, twiddle, one exchange through shared
+// memory, R1-point DFTs in registers. The inverse runs the same steps
+// backwards from the k-layout to the n-layout. Every register DFT has
+// compile-time indices and constant twiddles, so nothing is spilled to
+// local memory; one shared-memory round trip per transform.
+#pragma once
+
+#include "common.cuh"
+
+namespace bae {
+
+// cos and sin of 2 pi m / 32 from the first-octant values by symmetry
+struct Root32 {
+    double c, s;
+};
+__host__ __device__ constexpr Root32 root32(int m) {
+    // cos(pi j / 16), j = 0..8
+    constexpr double C[9] = {1.0,
+                             0.98078528040323044913,
+                             0.92387953251128675613,
+                             0.83146961230254523708,
+                             0.70710678118654752440,
+                             0.55557023301960222474,
+                             0.38268343236508977173,
+                             0.19509032201612826785,
+                             0.0};
+    m = ((m % 32) + 32) % 32;
+    const int q = m / 8, r = m % 8;  // angle = q pi/2 + r pi/16
+    const double cr = C[r], sr = C[8 - r];
+    if (q == 0) return {cr, sr};
+    if (q == 1) return {-sr, cr};
+    if (q == 2) return {-cr, -sr};
+    return {sr, -cr};
+}
+
+// x * exp(-/+ 2 pi i M / R) with compile-time M, R | 32
+template <int R, int M, bool INV, typename C>
+__device__ __forceinline__ C wmul(C x) {
+    using T = decltype(x.x);
+    constexpr int m = ((M * (32 / R)) % 32 + 32) % 32;
+    if constexpr (m == 0) return x;
+    if constexpr (m == 16) return cmake<C>(-x.x, -x.y);
+    if constexpr (m == 8) {   // forward: -i, inverse: +i
+        if constexpr (INV) return cmake<C>(-x.y, x.x);
+        else return cmake<C>(x.y, -x.x);
+    }
+    if constexpr (m == 24) {  // forward: +i, inverse: -i
+        if constexpr (INV) return cmake<C>(x.y, -x.x);
+        else return cmake<C>(-x.y, x.x);
+    }
+    constexpr Root32 w = root32(m);
+    const T c = (T)w.c;
+    const T s = INV ? (T)w.s : (T)-w.s;
+    return cmake<C>(x.x * c - x.y * s, x.x * s + x.y * c);
+}
+
+template <bool INV, typename C>
+__device__ __forceinline__ void rdft2(C& a, C& b) {
+    const C t = a;
+    a = cadd(t, b);
+    b = csub(t, b);
+}
+
+template <bool INV, typename C>
+__device__ __forceinline__ void rdft4(C& x0, C& x1, C& x2, C& x3) {
+    const C t0 = cadd(x0, x2), t1 = csub(x0, x2), t2 = cadd(x1, x3);
+    const C t3 = wmul<4, 1, INV>(csub(x1, x3));
+    x0 = cadd(t0, t2);
+    x2 = csub(t0, t2);
+    x1 = cadd(t1, t3);
+    x3 = csub(t1, t3);
+}
+
+// In-register DFT of v[0..R) in natural order, R in {2, 4, 8, 16, 32}.
+template <int R, bool INV, typename C>
+__device__ __forceinline__ void rdft(C* v);
+
+template <int R, bool INV, typename C, int K>
+struct TwTail {  // v[K] *= W_R^{K} ... applied to the odd half (radix-2 split)
+    __device__ __forceinline__ static void run(C* odd) {
+        odd[K] = wmul<R, K, INV>(odd[K]);
+        if constexpr (K + 1 < R / 2) TwTail<R, INV, C, K + 1>::run(odd);
+    }
+};
+
+template <int R, bool INV, typename C>
+__device__ __forceinline__ void rdft(C* v) {
+    if constexpr (R == 2) {
+        rdft2<INV>(v[0], v[1]);
+    } else if constexpr (R == 4) {
+        rdft4<INV>(v[0], v[1], v[2], v[3]);
+    } else {
+        // radix-2 decimation in time: even and odd halves, then butterflies
+        C e[R / 2], o[R / 2];
+#pragma unroll
+        for (int i = 0; i < R / 2; ++i) {
+            e[i] = v[2 * i];
+            o[i] = v[2 * i + 1];
+        }
+        rdft<R / 2, INV>(e);
+        rdft<R / 2, INV>(o);
+        TwTail<R, INV, C, 1>::run(o);
+#pragma unroll
+        for (int k = 0; k < R / 2; ++k) {
+            v[k] = cadd(e[k], o[k]);
+            v[k + R / 2] = csub(e[k], o[k]);
+        }
+    }
+}
+
+template <int L> struct Factors;
+template <> struct Factors<16> { static constexpr int R1 = 4, R2 = 4; };
+template <> struct Factors<32> { static constexpr int R1 = 4, R2 = 8; };
+template <> struct Factors<64> { static constexpr int R1 = 8, R2 = 8; };
+template <> struct Factors<128> { static constexpr int R1 = 8, R2 = 16; };
+template <> struct Factors<256> { static constexpr int R1 = 16, R2 = 16; };
+template <> struct Factors<512> { static constexpr int R1 = 16, R2 = 32; };
+
+// Exchange buffer for one transform: R2 x R1 complex at
+// xch[base + k2 * sk + n1 * sn]; the caller picks the strides so that the
+// lanes of a warp touch distinct banks (columns interleaved: sk = R1 W,
+// sn = W, base = column; lines: sk = R1 + 1, sn = 1, base = line offset).
+
+// n-layout -> k-layout (forward, or inverse when INV: then from the
+// n-layout of X to the k-layout of the inverse transform, same steps with
+// conjugate twiddles). tw: exp(-2 pi i m / L), m < L.
+template <int L, bool INV, typename C>
+__device__ __forceinline__ void fft_n2k(C* v, C* xch, int base, int sk, int sn, int t, const C* __restrict__ tw) {
+    constexpr int R1 = Factors<L>::R1, R2 = Factors<L>::R2, Q = R2 / R1;
+    rdft<R2, INV>(v);                                   // v[k2] = Y[t][k2]
+#pragma unroll
+    for (int k2 = 1; k2 < R2; ++k2) {
+        const C w = __ldg(reinterpret_cast<const C*>(tw) + t * k2);
+        v[k2] = INV ? cmulc(v[k2], w) : cmul(v[k2], w);
+    }
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) xch[base + k2 * sk + t * sn] = v[k2];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+#pragma unroll
+        for (int n1 = 0; n1 < R1; ++n1) v[q * R1 + n1] = xch[base + (t + q * R1) * sk + n1 * sn];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < Q; ++q) rdft<R1, INV>(v + q * R1);   // v[q R1 + k1] = X[k2 + R2 k1]
+}
+
+// k-layout -> n-layout (inverse when INV, the mirror of fft_n2k).
+template <int L, bool INV, typename C>
+__device__ __forceinline__ void fft_k2n(C* v, C* xch, int base, int sk, int sn, int t, const C* __restrict__ tw) {
+    constexpr int R1 = Factors<L>::R1, R2 = Factors<L>::R2, Q = R2 / R1;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) rdft<R1, INV>(v + q * R1);   // v[q R1 + n1] = Z[k2][n1]
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+#pragma unroll
+        for (int n1 = 0; n1 < R1; ++n1) {
+            const int k2 = t + q * R1;
+            if (n1 > 0 && k2 > 0) {
+                const C w = __ldg(reinterpret_cast<const C*>(tw) + n1 * k2);
+                v[q * R1 + n1] = INV ? cmulc(v[q * R1 + n1], w) : cmul(v[q * R1 + n1], w);
+            }
+            xch[base + k2 * sk + n1 * sn] = v[q * R1 + n1];
+        }
+    __syncthreads();
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) v[k2] = xch[base + k2 * sk + t * sn];
+    __syncthreads();
+    rdft<R2, INV>(v);                                   // v[n2] = x[t + R1 n2]
+}
+
+}  // namespace bae
