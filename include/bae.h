@@ -182,6 +182,30 @@ int bae_potential_apply(bae_problem* prob, int precision, const double* q, doubl
  * q, Aq: n_gm doubles. precision BAE_FP64 or BAE_FP32. */
 int bae_boundary_apply(bae_problem* prob, int precision, const double* q, double* Aq);
 
+/* The same potential apply as bae_potential_apply, for callers that must not
+ * allocate device memory while they run (a fixed memory budget owned by the
+ * host application, a real-time loop in which cudaMalloc/cudaFree would
+ * stall or synchronise the device, a plug-in host that forbids allocation
+ * after start-up). This call allocates nothing: its work buffers are one
+ * file-scope device array of 8 MiB that every GPU the library touches holds
+ * until the process exits. The paper has no counterpart; this is a
+ * deployment variant of the hot path.
+ *  - q (n_gm doubles) and v (N^3 doubles) must be device memory of the
+ *    problem's device; host pointers are rejected (BAE_ERR_INVALID_ARG),
+ *    since staging them would need allocations.
+ *  - Size limit: float32 up to N = 64, float64 up to N = 32; larger problems
+ *    are rejected with BAE_ERR_INVALID_ARG and a message giving the bytes
+ *    needed. The problem handle, its spectrum and twiddles are built by
+ *    bae_problem_create, which does allocate, at set-up.
+ *  - The first call on a device looks up the device address of the array
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - Every call uses the same array and leaves its contents behind; nothing
+ *    in it needs clearing, since each call writes every element it reads.
+ *    Calls whose GPU work overlaps in time (several host threads, several
+ *    contexts or streams on one device) race on the array: serialise them.
+ * precision BAE_FP64 or BAE_FP32. Returns after the work has finished. */
+int bae_potential_apply_noalloc(bae_problem* prob, int precision, const double* q, double* v);
+
 /* Particular solution on the free lattice (eq. [ps] with G_h = h^2 G_s):
  * up(m) = sum_{x in M+} G_s(m-x) h^2 f(x) on the whole grid.
  * f, up: N^3 doubles (paper sign). precision BAE_FP64 or BAE_FP32. */

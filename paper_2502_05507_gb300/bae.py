@@ -80,6 +80,7 @@ def lib():
             "bae_boundary_points": (_I, [_P, _P]),
             "bae_classification": (_I, [_P, _P, _P, _P, _P]),
             "bae_potential_apply": (_I, [_P, _I, _P, _P]),
+            "bae_potential_apply_noalloc": (_I, [_P, _I, _P, _P]),
             "bae_boundary_apply": (_I, [_P, _I, _P, _P]),
             "bae_particular": (_I, [_P, _I, _P, _P]),
             "bae_solve": (_I, [_P, _P, _P, _P, _P, _P, _P]),
@@ -97,6 +98,7 @@ EXPORTED = ["bae_version", "bae_last_error", "bae_default_options", "bae_launch_
             "bae_profile_stop", "bae_ctx_create", "bae_ctx_destroy",
             "bae_lgf_table", "bae_lgf_spectrum", "bae_problem_create", "bae_problem_destroy",
             "bae_problem_sizes", "bae_boundary_points", "bae_classification", "bae_potential_apply",
+            "bae_potential_apply_noalloc",
             "bae_boundary_apply", "bae_particular", "bae_solve", "bae_solve_batched"]
 
 
@@ -253,6 +255,12 @@ class Problem:
         q = _as_f64(q)
         out = _new((self.N,) * 3, np.float64, q) if out is None else out
         _check(lib().bae_potential_apply(self._h, _PREC[precision], _ptr(q), _ptr(out)))
+        return out
+
+    def potential_apply_noalloc(self, q, out, precision="fp64"):
+        """bae_potential_apply_noalloc: q and out must be CUDA tensors; the
+        call allocates no device memory (static 8 MiB scratch)."""
+        _check(lib().bae_potential_apply_noalloc(self._h, _PREC[precision], _ptr(q), _ptr(out)))
         return out
 
     def boundary_apply(self, q, precision="fp64", out=None):

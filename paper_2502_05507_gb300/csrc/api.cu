@@ -13,6 +13,7 @@
 #include "classify.cuh"
 #include "common.cuh"
 #include "conv.cuh"
+#include "internal.cuh"
 #include "krylov.cuh"
 #include "lgf.cuh"
 
@@ -194,6 +195,24 @@ struct bae_problem {
 };
 
 namespace bae {
+
+bool problem_view(const bae_problem* P, ProblemView& out) {
+    if (!P || !P->spec) return false;
+    out.device = P->ctx->device;
+    out.N = P->geo.N;
+    out.n_gm = P->geo.n_gm;
+    out.stream = P->ctx->stream;
+    out.rec = P->geo.recipe();
+    out.ghat64 = P->spec->g64;
+    out.ghat32 = P->spec->g32;
+    auto it = P->ctx->tw.find(2 * P->geo.N);
+    if (it != P->ctx->tw.end()) {
+        out.tw64 = it->second.tw64;
+        out.tw32 = it->second.tw32;
+    }
+    return true;
+}
+
 namespace {
 
 long long n_gm(const bae_problem* P) { return P->geo.n_gm; }
@@ -840,6 +859,7 @@ int bae_problem_create(bae_ctx* ctx, int N, double h, const double origin[3], co
             throw;
         }
         P->spec = ctx->spectrum(N, P->s);
+        ctx->twiddles(2 * N);   // built here so that later applies allocate nothing
         *out = P.release();
         return BAE_OK;
     });
