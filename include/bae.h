@@ -54,6 +54,11 @@ extern "C" {
 #define BAE_MIXED 1            /* float32 convolution inside float64 iterative
                                   refinement (solve only)                      */
 #define BAE_FP32  2            /* float32 convolution (apply entry points only)*/
+#define BAE_DF64  3            /* double-float convolution: each value a pair of
+                                  float32 (about 48 significant bits) on the
+                                  float32 pipes; float64-accurate to ~1e-14
+                                  (apply entry points, and the refinement
+                                  residual of BAE_MIXED)                      */
 
 typedef struct bae_ctx bae_ctx;
 typedef struct bae_problem bae_problem;
@@ -62,15 +67,25 @@ typedef struct bae_options {
     double tol;          /* relative residual ||b - A q|| / ||b||, default 1e-10 */
     int    max_iter;     /* total GMRES iterations (all cycles), default 500    */
     int    restart;      /* GMRES restart length, default 200                   */
-    int    precision;    /* BAE_FP64 or BAE_MIXED, default BAE_FP64             */
+    int    precision;    /* BAE_FP64 (every apply native float64), BAE_DF64
+                            (every apply double-float) or BAE_MIXED (float32
+                            applies inside iterative refinement), default
+                            BAE_FP64                                         */
     int    max_refine;   /* outer refinement steps for BAE_MIXED, default 8     */
     double inner_tol;    /* inner float32 GMRES reduction per step, default 1e-5 */
+    int    use_graphs;   /* 1: each Arnoldi step (apply, CGS2, Givens) is captured
+                            once as a CUDA graph and replayed; 0: launched
+                            kernel by kernel (same kernels, for per-kernel
+                            timing). Default 1. */
+    int    residual_precision;  /* BAE_MIXED only: arithmetic of the particular
+                            solution, the refinement residuals and the
+                            reconstruction, BAE_DF64 (default) or BAE_FP64 */
 } bae_options;
 
 typedef struct bae_stats {
     int    iterations;       /* GMRES iterations, all cycles and refinement steps */
     int    refinements;      /* outer refinement steps (BAE_MIXED), else 0        */
-    int    applies_fp64;     /* float64 potential applies in this call            */
+    int    applies_fp64;     /* float64-accurate applies (BAE_FP64 or BAE_DF64)   */
     int    applies_fp32;     /* float32 potential applies in this call            */
     double rel_residual;     /* final ||b - A q|| / ||b||, A applied in float64   */
     double ms_total;         /* wall time of the call on the context stream       */

@@ -18,9 +18,9 @@ LIB_PATH = os.path.join(_HERE, "libbae.so")
 
 OK, ERR_INVALID_ARG, ERR_GEOMETRY, ERR_OOM, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_CUDA = range(7)
 LAYER_DOUBLE, LAYER_SINGLE = 0, 1
-FP64, MIXED, FP32 = 0, 1, 2
+FP64, MIXED, FP32, DF64 = 0, 1, 2, 3
 _LAYERS = {"double": LAYER_DOUBLE, "single": LAYER_SINGLE}
-_PREC = {"fp64": FP64, "mixed": MIXED, "fp32": FP32}
+_PREC = {"fp64": FP64, "mixed": MIXED, "fp32": FP32, "df64": DF64}
 
 
 class BAEError(RuntimeError):
@@ -39,7 +39,8 @@ class GeometryError(BAEError):
 
 class Options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("restart", ctypes.c_int),
-                ("precision", ctypes.c_int), ("max_refine", ctypes.c_int), ("inner_tol", ctypes.c_double)]
+                ("precision", ctypes.c_int), ("max_refine", ctypes.c_int), ("inner_tol", ctypes.c_double),
+                ("use_graphs", ctypes.c_int), ("residual_precision", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -275,9 +276,13 @@ class Problem:
         _check(lib().bae_particular(self._h, _PREC[precision], _ptr(f), _ptr(out)))
         return out
 
-    def _opts(self, tol, precision, max_iter, restart, max_refine, inner_tol):
+    def _opts(self, tol, precision, max_iter, restart, max_refine, inner_tol, use_graphs=True,
+              residual_precision=None):
         o = Options()
         lib().bae_default_options(ctypes.byref(o))
+        o.use_graphs = 1 if use_graphs else 0
+        if residual_precision is not None:
+            o.residual_precision = _PREC[residual_precision]
         o.tol = tol
         o.precision = _PREC[precision]
         if max_iter is not None:
@@ -291,7 +296,8 @@ class Problem:
         return o
 
     def solve(self, f, g, tol=1e-10, precision="fp64", max_iter=None, restart=None, max_refine=None,
-              inner_tol=None, density=None, u=None, allow_not_converged=False):
+              inner_tol=None, density=None, u=None, allow_not_converged=False, use_graphs=True,
+              residual_precision=None):
         """Returns (density, u, stats dict). f (N^3) and g (n_gm) may be
         torch CUDA tensors or numpy arrays; outputs follow f's kind."""
         f = _as_f64(f)
@@ -299,13 +305,14 @@ class Problem:
         density = _new((self.n_gm,), np.float64, f) if density is None else density
         u = _new((self.N,) * 3, np.float64, f) if u is None else u
         st = Stats()
-        o = self._opts(tol, precision, max_iter, restart, max_refine, inner_tol)
+        o = self._opts(tol, precision, max_iter, restart, max_refine, inner_tol, use_graphs, residual_precision)
         rc = lib().bae_solve(self._h, _ptr(f), _ptr(g), ctypes.byref(o), _ptr(density), _ptr(u), ctypes.byref(st))
         _check(rc, allow_not_converged)
         return density, u, st.as_dict()
 
     def solve_batched(self, f, g, tol=1e-10, precision="fp64", max_iter=None, restart=None, max_refine=None,
-                      inner_tol=None, density=None, u=None, allow_not_converged=False):
+                      inner_tol=None, density=None, u=None, allow_not_converged=False, use_graphs=True,
+                      residual_precision=None):
         """f [nrhs, N, N, N], g [nrhs, n_gm]; returns (density, u, [stats])."""
         f = _as_f64(f)
         g = _as_f64(g)
@@ -313,7 +320,7 @@ class Problem:
         density = _new((nrhs, self.n_gm), np.float64, f) if density is None else density
         u = _new((nrhs,) + (self.N,) * 3, np.float64, f) if u is None else u
         st = (Stats * nrhs)()
-        o = self._opts(tol, precision, max_iter, restart, max_refine, inner_tol)
+        o = self._opts(tol, precision, max_iter, restart, max_refine, inner_tol, use_graphs, residual_precision)
         rc = lib().bae_solve_batched(self._h, nrhs, _ptr(f), _ptr(g), ctypes.byref(o), _ptr(density), _ptr(u),
                                      st)
         _check(rc, allow_not_converged)

@@ -4,10 +4,14 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <condition_variable>
+#include <mutex>
+#include <set>
 #include <cstring>
 #include <map>
 #include <memory>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "classify.cuh"
@@ -24,7 +28,18 @@ void set_last_error(const std::string& msg) { g_last_error = msg; }
 
 // --------------------------------------------------- launches and profiling
 static std::atomic<long long> g_launches{0};
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static thread_local long long t_capture_kernels = -1;   // >= 0 while capturing a graph
+void count_launch() {
+    if (t_capture_kernels >= 0) ++t_capture_kernels;
+    else g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+void count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+void capture_begin() { t_capture_kernels = 0; }
+long long capture_end() {
+    const long long k = t_capture_kernels;
+    t_capture_kernels = -1;
+    return k;
+}
 
 namespace {
 struct ProfRec {
@@ -48,14 +63,14 @@ Profiler g_prof;
 }  // namespace
 
 void prof_push(const char* name, cudaStream_t st) {
-    if (!g_prof.on) return;
+    if (!g_prof.on || t_capture_kernels >= 0) return;
     g_prof.pending = g_prof.next();
     g_prof.pending_name = name;
     if (g_prof.pending) cudaEventRecord(g_prof.pending, st);
 }
 
 void prof_pop(cudaStream_t st) {
-    if (!g_prof.on || !g_prof.pending) return;
+    if (!g_prof.on || !g_prof.pending || t_capture_kernels >= 0) return;
     cudaEvent_t e = g_prof.next();
     if (!e) return;
     cudaEventRecord(e, st);
@@ -83,6 +98,10 @@ struct Grow {
     cudaStream_t st = nullptr;
     T* need(long long n) {
         if (n > cap) {
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            BAE_CUDA(cudaStreamIsCapturing(st, &cs));
+            BAE_REQUIRE(cs == cudaStreamCaptureStatusNone, BAE_ERR_CUDA,
+                        "internal: work-space growth during graph capture");
             dev_free(p, st);
             p = nullptr;
             cap = 0;
@@ -95,15 +114,20 @@ struct Grow {
     ~Grow() { release(); }
 };
 
+// One LGF spectrum, shared by every problem (and every context of a
+// server) with the same (N, s); plain cudaMalloc so that it outlives the
+// stream that built it.
 struct Spectrum {
     int N = 0;
     double s = 0.0;
     double* g64 = nullptr;
     float* g32 = nullptr;
-    cudaStream_t st = nullptr;
+    dsf* gds = nullptr;
+    size_t bytes = 0;
     ~Spectrum() {
-        dev_free(g64, st);
-        dev_free(g32, st);
+        if (g64) cudaFree(g64);
+        if (g32) cudaFree(g32);
+        if (gds) cudaFree(gds);
     }
 };
 
@@ -114,21 +138,27 @@ struct Workspace {
     Grow<double> v64, up, vstage;             // [nb][N^3]
     Grow<float> v32;
     Grow<double> V, w, partial, h, hsave, x, r, bvec, tmp, qstage, n2;   // Krylov
-    Grow<int> active;
+    Grow<double> arnH, arnCS, arnG, arnY, arnScal;
+    Grow<int> active, arnI;
+    Grow<unsigned int> arnCtr;
     Grow<double> in_f, in_g, out_q, out_u;    // staging of host arguments
     void set_stream(cudaStream_t st) {
         Grow<double>* ds[] = {&v64, &up, &vstage, &V, &w, &partial, &h, &hsave, &x, &r, &bvec, &tmp,
                               &qstage, &n2, &in_f, &in_g, &out_q, &out_u};
         for (auto* d : ds) d->st = st;
+        Grow<double>* ds2[] = {&arnH, &arnCS, &arnG, &arnY, &arnScal};
+        for (auto* d : ds2) d->st = st;
         A.st = B.st = st;
         v32.st = st;
-        active.st = st;
+        active.st = arnI.st = st;
+        arnCtr.st = st;
     }
 };
 
 struct Twiddles {
     double2* tw64 = nullptr;
     float2* tw32 = nullptr;
+    dsc* twds = nullptr;
 };
 
 bool is_device_ptr(const void* p) {
@@ -147,14 +177,86 @@ bool is_device_ptr(const void* p) {
 
 using namespace bae;
 
+namespace bae {
+// Spectra keyed by (N, bit pattern of s). Thread-safe: a context that needs
+// a spectrum another one is building waits for it instead of building it
+// twice. Entries live as long as the cache.
+struct SpectrumCache {
+    std::mutex mu;
+    std::condition_variable cv;
+    std::map<std::pair<int, uint64_t>, std::shared_ptr<Spectrum>> map;
+    std::set<std::pair<int, uint64_t>> building;
+
+    std::shared_ptr<Spectrum> get(int N, double s, cudaStream_t st) {
+        uint64_t bits;
+        std::memcpy(&bits, &s, sizeof(bits));
+        const auto key = std::make_pair(N, bits);
+        std::unique_lock<std::mutex> lock(mu);
+        for (;;) {
+            auto it = map.find(key);
+            if (it != map.end()) return it->second;
+            if (!building.count(key)) break;
+            cv.wait(lock);
+        }
+        building.insert(key);
+        lock.unlock();
+        std::shared_ptr<Spectrum> sp;
+        try {
+            sp = std::make_shared<Spectrum>();
+            sp->N = N;
+            sp->s = s;
+            const long long n3 = (long long)(N + 1) * (N + 1) * (N + 1);
+            BAE_CUDA(cudaMalloc(&sp->g64, n3 * sizeof(double)));
+            BAE_CUDA(cudaMalloc(&sp->g32, n3 * sizeof(float)));
+            BAE_CUDA(cudaMalloc(&sp->gds, n3 * sizeof(dsf)));
+            sp->bytes = n3 * (sizeof(double) + sizeof(float) + sizeof(dsf));
+            const double L = 2.0 * N;
+            lgf_spectrum(N, s, 1.0 / (L * L * L), sp->g64, sp->g32, st);
+            to_dsf(sp->g64, n3, sp->gds, st);
+            BAE_CUDA(cudaStreamSynchronize(st));
+        } catch (...) {
+            lock.lock();
+            building.erase(key);
+            cv.notify_all();
+            throw;
+        }
+        lock.lock();
+        building.erase(key);
+        map[key] = sp;
+        cv.notify_all();
+        return sp;
+    }
+
+    size_t bytes() {
+        std::lock_guard<std::mutex> lock(mu);
+        size_t b = 0;
+        for (auto& kv : map) b += kv.second->bytes;
+        return b;
+    }
+};
+}  // namespace bae
+
 struct bae_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    std::map<std::pair<int, uint64_t>, std::shared_ptr<Spectrum>> cache;
+    std::shared_ptr<SpectrumCache> cache;
     std::map<int, Twiddles> tw;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t poll_ev[2] = {nullptr, nullptr};
+    int* pinned = nullptr;
+    int pinned_cap = 0;
     Workspace ws;
+
+    int* pinned_flags(int nb) {   // host-pinned [2][nb] polling buffer
+        if (2 * nb > pinned_cap) {
+            if (pinned) cudaFreeHost(pinned);
+            pinned = nullptr;
+            BAE_CUDA(cudaMallocHost(&pinned, 2 * (size_t)nb * sizeof(int)));
+            pinned_cap = 2 * nb;
+        }
+        return pinned;
+    }
 
     const Twiddles& twiddles(int L) {
         auto it = tw.find(L);
@@ -162,27 +264,13 @@ struct bae_ctx {
         Twiddles t;
         t.tw64 = dev_alloc_n<double2>(L, stream);
         t.tw32 = dev_alloc_n<float2>(L, stream);
+        t.twds = dev_alloc_n<dsc>(L, stream);
         make_twiddles(L, t.tw64, t.tw32, stream);
+        to_dsf(reinterpret_cast<const double*>(t.tw64), 2LL * L, reinterpret_cast<dsf*>(t.twds), stream);
         return tw[L] = t;
     }
 
-    std::shared_ptr<Spectrum> spectrum(int N, double s) {
-        uint64_t key;
-        std::memcpy(&key, &s, sizeof(key));
-        auto it = cache.find({N, key});
-        if (it != cache.end()) return it->second;
-        auto sp = std::make_shared<Spectrum>();
-        sp->N = N;
-        sp->s = s;
-        sp->st = stream;
-        const long long n3 = (long long)(N + 1) * (N + 1) * (N + 1);
-        sp->g64 = dev_alloc_n<double>(n3, stream);
-        sp->g32 = dev_alloc_n<float>(n3, stream);
-        const double L = 2.0 * N;
-        lgf_spectrum(N, s, 1.0 / (L * L * L), sp->g64, sp->g32, stream);
-        cache[{N, key}] = sp;
-        return sp;
-    }
+    std::shared_ptr<Spectrum> spectrum(int N, double s) { return cache->get(N, s, stream); }
 };
 
 struct bae_problem {
@@ -227,7 +315,10 @@ ConvArgs<T> conv_args(bae_problem* P, int nb) {
     a.A = reinterpret_cast<cplx_t<T>*>(P->ws().A.need((long long)nb * N * N * N1));
     a.B = reinterpret_cast<cplx_t<T>*>(P->ws().B.need((long long)nb * N * 2 * N * N1));
     const Twiddles& tw = P->ctx->twiddles(2 * N);
-    if constexpr (sizeof(T) == 8) {
+    if constexpr (std::is_same<T, dsf>::value) {
+        a.ghat = P->spec->gds;
+        a.tw = tw.twds;
+    } else if constexpr (sizeof(T) == 8) {
         a.ghat = reinterpret_cast<const T*>(P->spec->g64);
         a.tw = reinterpret_cast<const cplx_t<T>*>(tw.tw64);
     } else {
@@ -238,14 +329,17 @@ ConvArgs<T> conv_args(bae_problem* P, int nb) {
 }
 
 template <typename T>
-T* vbuf(bae_problem* P, int nb) {
-    if constexpr (sizeof(T) == 8) return reinterpret_cast<T*>(P->ws().v64.need((long long)nb * P->n3()));
-    else return reinterpret_cast<T*>(P->ws().v32.need((long long)nb * P->n3()));
+using out_t = typename OutOf<T>::type;
+
+template <typename T>
+out_t<T>* vbuf(bae_problem* P, int nb) {
+    if constexpr (std::is_same<out_t<T>, double>::value) return P->ws().v64.need((long long)nb * P->n3());
+    else return P->ws().v32.need((long long)nb * P->n3());
 }
 
 // v[b] = K q[b] on the N^3 grid, q [nb][n_gm] on the device
 template <typename T>
-T* apply_potential(bae_problem* P, int nb, const double* q) {
+out_t<T>* apply_potential(bae_problem* P, int nb, const double* q) {
     ConvArgs<T> a = conv_args<T>(P, nb);
     a.mode = SRC_DENSITY;
     a.q = q;
@@ -258,7 +352,7 @@ T* apply_potential(bae_problem* P, int nb, const double* q) {
 
 // v[b] = sum_{x in M+} G(m - x) scale f[b](x)
 template <typename T>
-T* apply_volume(bae_problem* P, int nb, const double* f, double scale) {
+out_t<T>* apply_volume(bae_problem* P, int nb, const double* f, double scale) {
     ConvArgs<T> a = conv_args<T>(P, nb);
     a.mode = SRC_VOLUME;
     a.f = f;
@@ -272,14 +366,24 @@ T* apply_volume(bae_problem* P, int nb, const double* f, double scale) {
 // Aq[b] = Phi K q[b], both [nb][n_gm] on the device
 template <typename T>
 void boundary_apply(bae_problem* P, int nb, const double* q, double* Aq) {
-    T* v = apply_potential<T>(P, nb, q);
-    closure_gather<T>(v, P->n3(), P->geo.gm, P->geo.partner, P->geo.t, (int)n_gm(P), nb, Aq, n_gm(P),
+    out_t<T>* v = apply_potential<T>(P, nb, q);
+    closure_gather<out_t<T>>(v, P->n3(), P->geo.gm, P->geo.partner, P->geo.t, (int)n_gm(P), nb, Aq, n_gm(P),
                       P->ctx->stream);
 }
 
 void boundary_apply_prec(bae_problem* P, int prec, int nb, const double* q, double* Aq) {
     if (prec == BAE_FP32) boundary_apply<float>(P, nb, q, Aq);
+    else if (prec == BAE_DF64) boundary_apply<dsf>(P, nb, q, Aq);
     else boundary_apply<double>(P, nb, q, Aq);
+}
+
+// K q[b] in float64 storage for the float64-accurate precisions
+double* apply_potential64(bae_problem* P, int prec, int nb, const double* q) {
+    return prec == BAE_DF64 ? apply_potential<dsf>(P, nb, q) : apply_potential<double>(P, nb, q);
+}
+
+double* apply_volume64(bae_problem* P, int prec, int nb, const double* f, double scale) {
+    return prec == BAE_DF64 ? apply_volume<dsf>(P, nb, f, scale) : apply_volume<double>(P, nb, f, scale);
 }
 
 // --------------------------------------------------------------- GMRES
@@ -287,182 +391,195 @@ struct RhsState {
     bool converged = false;
     int iterations = 0;
     double target = 0.0;     // absolute residual target
-    double beta = 0.0;
-    double est = 0.0;        // current residual estimate
-    std::vector<double> H;   // (m+1) x m column-major Hessenberg (rotated)
-    std::vector<double> cs, sn, g;
+    double est = 0.0;        // last residual estimate
 };
 
-// Solves A x = rhs for the RHS in `which` (indices into [nb] arrays) with
-// restarted GMRES (CGS2 Arnoldi on the device, Givens on the host),
-// starting from x (device [nb][n]; x_zero: known to be 0, which skips the
-// first residual apply). The apply uses precision `prec`; applies[b] counts
-// the applies each RHS took part in. Returns the number of RHS that reached
-// their target.
-int gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, const double* rhs, double* x,
-          bool x_zero, std::vector<RhsState>& S, int max_iter, int restart, std::vector<int>& applies) {
+// w[b] = A q[b] with q read at q + b q_stride + (*q_row) q_row_stride, for
+// items with active[b] != 0 (all device arrays; capturable in a graph)
+template <typename T>
+void apply_rows(bae_problem* P, int nb, const double* q, long long q_stride, const int* q_row,
+                long long q_row_stride, const int* active, double* out) {
+    ConvArgs<T> a = conv_args<T>(P, nb);
+    a.mode = SRC_DENSITY;
+    a.q = q;
+    a.q_stride = q_stride;
+    a.q_row = q_row;
+    a.q_row_stride = q_row_stride;
+    a.active = active;
+    a.rec = P->geo.recipe();
+    a.v = vbuf<T>(P, nb);
+    conv_apply<T>(a, P->ctx->stream);
+    closure_gather<out_t<T>>(a.v, P->n3(), P->geo.gm, P->geo.partner, P->geo.t, (int)n_gm(P), nb, out, n_gm(P),
+                      P->ctx->stream, active);
+}
+
+void apply_rows_prec(bae_problem* P, int prec, int nb, const double* q, long long q_stride, const int* q_row,
+                     long long q_row_stride, const int* active, double* out) {
+    if (prec == BAE_FP32) apply_rows<float>(P, nb, q, q_stride, q_row, q_row_stride, active, out);
+    else if (prec == BAE_DF64) apply_rows<dsf>(P, nb, q, q_stride, q_row, q_row_stride, active, out);
+    else apply_rows<double>(P, nb, q, q_stride, q_row, q_row_stride, active, out);
+}
+
+// Restarted GMRES for the RHS b in `which` (rows of rhs/x [nb][n], device):
+// every Arnoldi step (apply of precision `prec`, CGS2, Givens) runs on the
+// device; with use_graph it is captured once as a CUDA graph and replayed.
+// The host only polls the convergence flags (double-buffered, one step
+// behind) and closes each cycle. x_zero: x is known to be 0.
+void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, const double* rhs, double* x,
+           bool x_zero, std::vector<RhsState>& S, int max_iter, int restart, std::vector<int>& applies,
+           bool use_graph) {
     cudaStream_t st = P->ctx->stream;
+    Workspace& ws = P->ws();
     const int n = (int)n_gm(P);
     const int m = std::max(1, std::min(restart, max_iter));
-    KrylovBatch k;
-    k.n = n;
-    k.nb = nb;
-    k.mp1 = m + 1;
-    k.nchunk = krylov_chunks(n);
-    k.V = P->ws().V.need((long long)nb * (m + 1) * n);
-    k.w = P->ws().w.need((long long)nb * n);
-    k.partial = P->ws().partial.need((long long)nb * (m + 2) * k.nchunk);
-    k.h = P->ws().h.need((long long)nb * (m + 2));
-    double* hsave = P->ws().hsave.need((long long)nb * (m + 2));
-    double* r = P->ws().r.need((long long)nb * n);
-    double* qst = P->ws().qstage.need((long long)nb * n);
-    double* tmp = P->ws().tmp.need((long long)nb * n);
-    double* n2 = P->ws().n2.need((long long)nb * std::max(k.nchunk, 1) + nb);
-    double* d_alpha = P->ws().bvec.need(nb);
-    int* d_act = P->ws().active.need(nb);
+    Arnoldi a;
+    a.n = n;
+    a.nb = nb;
+    a.m = m;
+    a.nchunk = krylov_chunks(n);
+    a.V = ws.V.need((long long)nb * (m + 1) * n);
+    a.w = ws.w.need((long long)nb * n);
+    a.part = ws.partial.need((long long)nb * (m + 2) * a.nchunk);
+    a.h1 = ws.h.need((long long)nb * (m + 1));
+    a.hcol = ws.hsave.need((long long)nb * (m + 1));
+    a.H = ws.arnH.need((long long)nb * m * (m + 1));
+    a.cs = ws.arnCS.need((long long)nb * m * 2);
+    a.sn = a.cs + (long long)nb * m;
+    a.g = ws.arnG.need((long long)nb * (m + 1));
+    a.y = ws.arnY.need((long long)nb * m);
+    double* scal = ws.arnScal.need((long long)nb * 4);
+    a.est = scal;
+    a.target = scal + nb;
+    a.inv = scal + 2 * nb;
+    double* nrm2 = scal + 3 * nb;
+    int* ibuf = ws.arnI.need((long long)nb * 3 + 1);
+    a.flag = ibuf;
+    a.ncols = ibuf + nb;
+    int* member = ibuf + 2 * nb;
+    a.j = ibuf + 3 * nb;
+    a.ctr = reinterpret_cast<unsigned int*>(ws.arnCtr.need((long long)nb * 3));
+    double* r = ws.r.need((long long)nb * n);
+    double* tmp = ws.tmp.need((long long)nb * n);
+    double* npart = ws.n2.need((long long)nb * a.nchunk + nb);
+    int* d_all = ws.active.need(nb);
 
-    std::vector<double> h_host((size_t)nb * (m + 2)), h1_host((size_t)nb * (m + 2));
-    std::vector<double> nrm((size_t)nb), alpha((size_t)nb);
-    int total_iters_left = max_iter;
-    std::vector<int> todo;
-    for (int b : which)
-        if (!S[b].converged) todo.push_back(b);
-
-    while (!todo.empty() && total_iters_left > 0) {
-        const int na = (int)todo.size();
-        BAE_CUDA(cudaMemcpyAsync(d_act, todo.data(), na * sizeof(int), cudaMemcpyHostToDevice, st));
-        // r = rhs - A x
-        if (x_zero) {
-            kr_gather_rows(rhs, d_act, na, n, qst, st);
-            kr_scatter_rows(qst, d_act, na, n, r, st);
-            x_zero = false;
-        } else {
-            kr_gather_rows(x, d_act, na, n, qst, st);
-            boundary_apply_prec(P, prec, na, qst, tmp);
-            for (int b : todo) applies[b] += 1;
-            kr_scatter_rows(tmp, d_act, na, n, r, st);
-            kr_sub(rhs, r, d_act, na, n, r, st);
-        }
-        kr_norm2(r, d_act, na, n, n2 + nb, k.nchunk, n2, st);
-        BAE_CUDA(cudaMemcpyAsync(nrm.data(), n2, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
-        BAE_CUDA(cudaStreamSynchronize(st));
-        std::vector<int> cyc;
-        for (int b : todo) {
-            RhsState& R = S[b];
-            R.beta = std::sqrt(nrm[b]);
-            R.est = R.beta;
-            if (R.beta <= R.target) {
-                R.converged = true;
-                continue;
-            }
-            cyc.push_back(b);
-            R.H.assign((size_t)(m + 1) * m, 0.0);
-            R.cs.assign(m, 0.0);
-            R.sn.assign(m, 0.0);
-            R.g.assign(m + 1, 0.0);
-            R.g[0] = R.beta;
-            alpha[b] = 1.0 / R.beta;
-        }
-        if (cyc.empty()) break;
-        int nc = (int)cyc.size();
-        BAE_CUDA(cudaMemcpyAsync(d_alpha, alpha.data(), nb * sizeof(double), cudaMemcpyHostToDevice, st));
-        BAE_CUDA(cudaMemcpyAsync(d_act, cyc.data(), nc * sizeof(int), cudaMemcpyHostToDevice, st));
-        // V[b][0] = r / beta: scale r into w, then copy w into V[0] with norm 1
-        kr_scale(r, d_alpha, d_act, nc, n, k.w, st);
-        {
-            // put 1.0 into the norm slot so that kr_scale_into copies w unchanged
-            std::vector<double> ones((size_t)nb * (m + 2), 1.0);
-            BAE_CUDA(cudaMemcpyAsync(k.h, ones.data(), ones.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-            kr_scale_into(k, d_act, nc, 0, st);
-            BAE_CUDA(cudaStreamSynchronize(st));
-        }
-        std::vector<int> live = cyc;          // RHS still iterating in this cycle
-        std::vector<int> ncols(nb, 0);        // basis size reached per RHS
-        int j = 0;
-        for (; j < m && !live.empty() && total_iters_left > 0; ++j) {
-            const int nl = (int)live.size();
-            BAE_CUDA(cudaMemcpyAsync(d_act, live.data(), nl * sizeof(int), cudaMemcpyHostToDevice, st));
-            // w = A V[j]
-            for (int q = 0; q < nl; ++q) {
-                const int b = live[q];
-                BAE_CUDA(cudaMemcpyAsync(qst + (long long)q * n, k.V + ((long long)b * k.mp1 + j) * n,
-                                         n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-            }
-            boundary_apply_prec(P, prec, nl, qst, tmp);
-            for (int b : live) applies[b] += 1;
-            kr_scatter_rows(tmp, d_act, nl, n, k.w, st);
-            // CGS2
-            kr_dots(k, d_act, nl, j + 1, st);
-            BAE_CUDA(cudaMemcpyAsync(hsave, k.h, (size_t)nb * (m + 2) * sizeof(double), cudaMemcpyDeviceToDevice, st));
-            kr_update_norm(k, d_act, nl, j + 1, st);
-            kr_dots(k, d_act, nl, j + 1, st);
-            kr_update_norm(k, d_act, nl, j + 1, st);
-            kr_scale_into(k, d_act, nl, j + 1, st);
-            BAE_CUDA(cudaMemcpyAsync(h_host.data(), k.h, h_host.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-            BAE_CUDA(cudaMemcpyAsync(h1_host.data(), hsave, h1_host.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-            BAE_CUDA(cudaStreamSynchronize(st));
-            --total_iters_left;
-            std::vector<int> next;
-            for (int b : live) {
-                RhsState& R = S[b];
-                double* col = R.H.data() + (size_t)j * (m + 1);
-                const double* h2 = h_host.data() + (size_t)b * (m + 2);
-                const double* h1 = h1_host.data() + (size_t)b * (m + 2);
-                for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
-                col[j + 1] = std::sqrt(std::max(h2[m + 1], 0.0));
-                for (int i = 0; i < j; ++i) {
-                    const double a = col[i], c = col[i + 1];
-                    col[i] = R.cs[i] * a + R.sn[i] * c;
-                    col[i + 1] = -R.sn[i] * a + R.cs[i] * c;
-                }
-                const double rr = std::hypot(col[j], col[j + 1]);
-                const bool breakdown = (rr == 0.0);
-                R.cs[j] = breakdown ? 1.0 : col[j] / rr;
-                R.sn[j] = breakdown ? 0.0 : col[j + 1] / rr;
-                col[j] = rr;
-                col[j + 1] = 0.0;
-                R.g[j + 1] = -R.sn[j] * R.g[j];
-                R.g[j] = R.cs[j] * R.g[j];
-                R.est = std::fabs(R.g[j + 1]);
-                R.iterations += 1;
-                ncols[b] = j + 1;
-                if (R.est <= R.target || breakdown || h2[m + 1] <= 0.0) continue;  // leaves the cycle
-                next.push_back(b);
-            }
-            live.swap(next);
-        }
-        // x += V y for every RHS of the cycle
-        std::vector<double> y((size_t)nb * m, 0.0);
-        for (int b : cyc) {
-            RhsState& R = S[b];
-            const int c = ncols[b];
-            for (int i = c - 1; i >= 0; --i) {
-                double acc = R.g[i];
-                for (int l = i + 1; l < c; ++l) acc -= R.H[(size_t)l * (m + 1) + i] * y[(size_t)b * m + l];
-                const double d = R.H[(size_t)i * (m + 1) + i];
-                y[(size_t)b * m + i] = d != 0.0 ? acc / d : 0.0;
-            }
-        }
-        double* d_y = P->ws().bvec.need((long long)nb * m + nb);
-        BAE_CUDA(cudaMemcpyAsync(d_y, y.data(), y.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-        BAE_CUDA(cudaMemcpyAsync(d_act, cyc.data(), nc * sizeof(int), cudaMemcpyHostToDevice, st));
-        int maxc = 0;
-        for (int b : cyc) maxc = std::max(maxc, ncols[b]);
-        kr_combine(k, d_act, nc, maxc, d_y, m, x, st);
-        BAE_CUDA(cudaStreamSynchronize(st));
-        // decide which RHS need another cycle: estimates below target are
-        // accepted (the caller checks the true residual)
-        std::vector<int> again;
-        for (int b : cyc) {
-            if (S[b].est <= S[b].target) S[b].converged = true;
-            else again.push_back(b);
-        }
-        todo.swap(again);
-        d_alpha = P->ws().bvec.need(nb);  // bvec may have moved
+    std::vector<int> all(nb), mem(nb, 0);
+    std::vector<double> tgt(nb, 0.0);
+    for (int b = 0; b < nb; ++b) {
+        all[b] = b;
+        tgt[b] = S[b].target;
     }
-    int nconv = 0;
-    for (int b : which) nconv += S[b].converged ? 1 : 0;
-    return nconv;
+    for (int b : which)
+        if (!S[b].converged) mem[b] = 1;
+    BAE_CUDA(cudaMemcpyAsync(d_all, all.data(), nb * sizeof(int), cudaMemcpyHostToDevice, st));
+    BAE_CUDA(cudaMemcpyAsync(a.target, tgt.data(), nb * sizeof(double), cudaMemcpyHostToDevice, st));
+    BAE_CUDA(cudaMemsetAsync(a.ctr, 0, (size_t)nb * 3 * sizeof(unsigned int), st));
+    int* hflag = P->ctx->pinned_flags(nb);
+    cudaEvent_t ev[2] = {P->ctx->poll_ev[0], P->ctx->poll_ev[1]};
+    cudaGraphExec_t exec = nullptr;
+    long long graph_kernels = 0;
+    int iters_left = max_iter;
+    std::vector<int> ncols(nb), flg(nb);
+    std::vector<double> est(nb);
+
+    auto one_step = [&]() {
+        apply_rows_prec(P, prec, nb, a.V, (long long)(m + 1) * n, a.j, n, a.flag, a.w);
+        arn_step(a, st);
+    };
+    // size every buffer and set every kernel attribute the step needs before
+    // any capture (nothing may allocate or configure inside it)
+    if (prec == BAE_FP32) {
+        conv_args<float>(P, nb);
+        vbuf<float>(P, nb);
+        conv_prepare<float>(P->geo.N);
+    } else if (prec == BAE_DF64) {
+        conv_args<dsf>(P, nb);
+        vbuf<dsf>(P, nb);
+        conv_prepare<dsf>(P->geo.N);
+    } else {
+        conv_args<double>(P, nb);
+        vbuf<double>(P, nb);
+        conv_prepare<double>(P->geo.N);
+    }
+
+    try {
+        while (iters_left > 0) {
+            int any = 0;
+            for (int b = 0; b < nb; ++b) any |= mem[b];
+            if (!any) break;
+            BAE_CUDA(cudaMemcpyAsync(member, mem.data(), nb * sizeof(int), cudaMemcpyHostToDevice, st));
+            // r = rhs - A x for the members
+            if (x_zero) {
+                BAE_CUDA(cudaMemcpyAsync(r, rhs, (size_t)nb * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+                x_zero = false;
+            } else {
+                apply_rows_prec(P, prec, nb, x, n, nullptr, 0, member, tmp);
+                for (int b = 0; b < nb; ++b) applies[b] += mem[b];
+                kr_sub(rhs, tmp, d_all, nb, n, r, st);
+            }
+            kr_norm2(r, d_all, nb, n, npart + nb, a.nchunk, npart, st);
+            arn_init(a, r, npart, member, st);
+            const int steps = std::min(m, iters_left);
+            int launched = 0;
+            for (int it = 0; it < steps; ++it) {
+                if (use_graph) {
+                    if (!exec) {
+                        cudaGraph_t graph;
+                        capture_begin();
+                        BAE_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+                        try {
+                            one_step();
+                        } catch (...) {
+                            cudaStreamEndCapture(st, &graph);
+                            capture_end();
+                            throw;
+                        }
+                        BAE_CUDA(cudaStreamEndCapture(st, &graph));
+                        graph_kernels = capture_end();
+                        const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+                        cudaGraphDestroy(graph);
+                        BAE_CUDA(e);
+                    }
+                    BAE_CUDA(cudaGraphLaunch(exec, st));
+                    count_launches(graph_kernels);
+                } else {
+                    one_step();
+                }
+                ++launched;
+                BAE_CUDA(cudaMemcpyAsync(hflag + (it & 1) * nb, a.flag, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
+                BAE_CUDA(cudaEventRecord(ev[it & 1], st));
+                if (it >= 1) {
+                    BAE_CUDA(cudaEventSynchronize(ev[(it - 1) & 1]));
+                    int live = 0;
+                    for (int b = 0; b < nb; ++b) live |= hflag[((it - 1) & 1) * nb + b];
+                    if (!live) break;
+                }
+            }
+            BAE_CUDA(cudaMemcpyAsync(ncols.data(), a.ncols, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
+            BAE_CUDA(cudaStreamSynchronize(st));
+            int maxc = 0;
+            for (int b = 0; b < nb; ++b) maxc = std::max(maxc, ncols[b]);
+            arn_finish(a, x, maxc, st);
+            BAE_CUDA(cudaMemcpyAsync(est.data(), a.est, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+            BAE_CUDA(cudaStreamSynchronize(st));
+            for (int b = 0; b < nb; ++b) {
+                if (!mem[b]) continue;
+                S[b].iterations += ncols[b];
+                applies[b] += ncols[b];
+                S[b].est = est[b];
+                if (est[b] <= S[b].target) {
+                    S[b].converged = true;
+                    mem[b] = 0;
+                }
+            }
+            iters_left -= std::max(maxc, 1);
+            (void)launched;
+        }
+    } catch (...) {
+        if (exec) cudaGraphExecDestroy(exec);
+        throw;
+    }
+    if (exec) cudaGraphExecDestroy(exec);
 }
 
 // ------------------------------------------------------------ full solve
@@ -480,8 +597,13 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
     BAE_REQUIRE(f && g, BAE_ERR_INVALID_ARG, "f and g must not be null");
     BAE_REQUIRE(o.tol > 0 && std::isfinite(o.tol), BAE_ERR_INVALID_ARG, "tol must be positive");
     BAE_REQUIRE(o.max_iter >= 1 && o.restart >= 1, BAE_ERR_INVALID_ARG, "max_iter and restart must be >= 1");
-    BAE_REQUIRE(o.precision == BAE_FP64 || o.precision == BAE_MIXED, BAE_ERR_INVALID_ARG,
-                "precision must be BAE_FP64 or BAE_MIXED");
+    BAE_REQUIRE(o.precision == BAE_FP64 || o.precision == BAE_MIXED || o.precision == BAE_DF64,
+                BAE_ERR_INVALID_ARG, "precision must be BAE_FP64, BAE_MIXED or BAE_DF64");
+    BAE_REQUIRE(o.residual_precision == BAE_FP64 || o.residual_precision == BAE_DF64, BAE_ERR_INVALID_ARG,
+                "residual_precision must be BAE_FP64 or BAE_DF64");
+    // arithmetic of every float64-accurate apply (particular solution,
+    // refinement residuals, reconstruction)
+    const int hp = o.precision == BAE_MIXED ? o.residual_precision : o.precision;
     cudaStream_t st = P->ctx->stream;
     BAE_CUDA(cudaEventRecord(P->ctx->ev0, st));
     const long long n3 = P->n3();
@@ -507,7 +629,7 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
     // particular solution u_p = G_h[chi_{M+} f] (float64) and b = g - Phi u_p
     double* up = P->ws().up.need((long long)nb * n3);
     {
-        double* v = apply_volume<double>(P, nb, d_f, h * h);
+        double* v = apply_volume64(P, hp, nb, d_f, h * h);
         BAE_CUDA(cudaMemcpyAsync(up, v, (size_t)nb * n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
         for (auto& s : st_local) s.applies_fp64 += 1;
     }
@@ -546,7 +668,7 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
         int* d_all = P->ws().active.need(nb);
         BAE_CUDA(cudaMemcpyAsync(d_all, all.data(), nb * sizeof(int), cudaMemcpyHostToDevice, st));
         double* tmp = P->ws().tmp.need((long long)nb * n);
-        double* v = apply_potential<double>(P, nb, q);
+        double* v = apply_potential64(P, hp, nb, q);
         closure_gather<double>(v, n3, P->geo.gm, P->geo.partner, P->geo.t, n, nb, tmp, n, st);
         for (auto& s : st_local) s.applies_fp64 += 1;
         kr_sub(bvec, tmp, d_all, nb, n, res, st);
@@ -557,10 +679,10 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
         for (int b = 0; b < nb; ++b) relres[b] = bn2[b] > 0 ? std::sqrt(rn2[b] / bn2[b]) : 0.0;
     };
 
-    if (o.precision == BAE_FP64) {
+    if (o.precision != BAE_MIXED) {
         for (int b = 0; b < nb; ++b) S[b].target = o.tol * std::sqrt(bn2[b]);
         std::vector<int> applies(nb, 0);
-        gmres(P, BAE_FP64, nb, all, bvec, q, true, S, o.max_iter, o.restart, applies);
+        gmres(P, o.precision, nb, all, bvec, q, true, S, o.max_iter, o.restart, applies, o.use_graphs != 0);
         for (int b = 0; b < nb; ++b) {
             st_local[b].iterations = S[b].iterations;
             st_local[b].applies_fp64 += applies[b];
@@ -588,7 +710,7 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
                 if (std::find(act.begin(), act.end(), b) == act.end()) Si[b].converged = true;
             BAE_CUDA(cudaMemsetAsync(d, 0, (size_t)nb * n * sizeof(double), st));
             std::vector<int> applies(nb, 0);
-            gmres(P, BAE_FP32, nb, act, res, d, true, Si, iters_left, o.restart, applies);
+            gmres(P, BAE_FP32, nb, act, res, d, true, Si, iters_left, o.restart, applies, o.use_graphs != 0);
             int used = 0;
             for (int b : act) {
                 st_local[b].iterations += Si[b].iterations;
@@ -759,6 +881,8 @@ void bae_default_options(bae_options* o) {
     o->precision = BAE_FP64;
     o->max_refine = 8;
     o->inner_tol = 1e-5;
+    o->use_graphs = 1;
+    o->residual_precision = BAE_DF64;
 }
 
 int bae_ctx_create(int device, void* stream, bae_ctx** out) {
@@ -778,6 +902,8 @@ int bae_ctx_create(int device, void* stream, bae_ctx** out) {
         }
         BAE_CUDA(cudaEventCreate(&c->ev0));
         BAE_CUDA(cudaEventCreate(&c->ev1));
+        BAE_CUDA(cudaEventCreateWithFlags(&c->poll_ev[0], cudaEventDisableTiming));
+        BAE_CUDA(cudaEventCreateWithFlags(&c->poll_ev[1], cudaEventDisableTiming));
         // keep freed blocks of the default pool for reuse (problem set-up
         // and work space come from it)
         cudaMemPool_t pool;
@@ -785,6 +911,7 @@ int bae_ctx_create(int device, void* stream, bae_ctx** out) {
         uint64_t thr = UINT64_MAX;
         BAE_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
         c->ws.set_stream(c->stream);
+        c->cache = std::make_shared<SpectrumCache>();
         *out = c.release();
         return BAE_OK;
     });
@@ -794,15 +921,19 @@ void bae_ctx_destroy(bae_ctx* ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
-    ctx->cache.clear();
+    ctx->cache.reset();
     for (auto& kv : ctx->tw) {
         dev_free(kv.second.tw64, ctx->stream);
         dev_free(kv.second.tw32, ctx->stream);
+        dev_free(kv.second.twds, ctx->stream);
     }
     ctx->ws = Workspace();
     cudaStreamSynchronize(ctx->stream);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    for (cudaEvent_t e : ctx->poll_ev)
+        if (e) cudaEventDestroy(e);
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -911,16 +1042,16 @@ int bae_classification(const bae_problem* P, uint8_t* flags, int32_t* gm_idx, in
 int bae_potential_apply(bae_problem* P, int precision, const double* q, double* v) {
     return guarded([&]() -> int {
         BAE_REQUIRE(P && q && v, BAE_ERR_INVALID_ARG, "null argument");
-        BAE_REQUIRE(precision == BAE_FP64 || precision == BAE_FP32, BAE_ERR_INVALID_ARG,
-                    "precision must be BAE_FP64 or BAE_FP32");
+        BAE_REQUIRE(precision == BAE_FP64 || precision == BAE_FP32 || precision == BAE_DF64, BAE_ERR_INVALID_ARG,
+                    "precision must be BAE_FP64, BAE_FP32 or BAE_DF64");
         check_device(P->ctx);
         cudaStream_t st = P->ctx->stream;
         const double* dq = device_in(P->ws().in_g, q, P->geo.n_gm, st);
         const long long n3 = P->n3();
         const bool vh = !is_device_ptr(v);
         double* dv = vh ? P->ws().out_u.need(n3) : v;
-        if (precision == BAE_FP64) {
-            double* r = apply_potential<double>(P, 1, dq);
+        if (precision != BAE_FP32) {
+            double* r = apply_potential64(P, precision, 1, dq);
             BAE_CUDA(cudaMemcpyAsync(dv, r, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
         } else {
             float* r = apply_potential<float>(P, 1, dq);
@@ -935,8 +1066,8 @@ int bae_potential_apply(bae_problem* P, int precision, const double* q, double* 
 int bae_boundary_apply(bae_problem* P, int precision, const double* q, double* Aq) {
     return guarded([&]() -> int {
         BAE_REQUIRE(P && q && Aq, BAE_ERR_INVALID_ARG, "null argument");
-        BAE_REQUIRE(precision == BAE_FP64 || precision == BAE_FP32, BAE_ERR_INVALID_ARG,
-                    "precision must be BAE_FP64 or BAE_FP32");
+        BAE_REQUIRE(precision == BAE_FP64 || precision == BAE_FP32 || precision == BAE_DF64, BAE_ERR_INVALID_ARG,
+                    "precision must be BAE_FP64, BAE_FP32 or BAE_DF64");
         check_device(P->ctx);
         cudaStream_t st = P->ctx->stream;
         const long long n = P->geo.n_gm;
@@ -953,8 +1084,8 @@ int bae_boundary_apply(bae_problem* P, int precision, const double* q, double* A
 int bae_particular(bae_problem* P, int precision, const double* f, double* up) {
     return guarded([&]() -> int {
         BAE_REQUIRE(P && f && up, BAE_ERR_INVALID_ARG, "null argument");
-        BAE_REQUIRE(precision == BAE_FP64 || precision == BAE_FP32, BAE_ERR_INVALID_ARG,
-                    "precision must be BAE_FP64 or BAE_FP32");
+        BAE_REQUIRE(precision == BAE_FP64 || precision == BAE_FP32 || precision == BAE_DF64, BAE_ERR_INVALID_ARG,
+                    "precision must be BAE_FP64, BAE_FP32 or BAE_DF64");
         check_device(P->ctx);
         cudaStream_t st = P->ctx->stream;
         const long long n3 = P->n3();
@@ -962,8 +1093,8 @@ int bae_particular(bae_problem* P, int precision, const double* f, double* up) {
         const bool oh = !is_device_ptr(up);
         double* du = oh ? P->ws().out_u.need(n3) : up;
         const double h2 = P->geo.h * P->geo.h;
-        if (precision == BAE_FP64) {
-            double* r = apply_volume<double>(P, 1, df, h2);
+        if (precision != BAE_FP32) {
+            double* r = apply_volume64(P, precision, 1, df, h2);
             BAE_CUDA(cudaMemcpyAsync(du, r, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
         } else {
             float* r = apply_volume<float>(P, 1, df, h2);

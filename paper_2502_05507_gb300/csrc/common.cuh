@@ -26,6 +26,9 @@ void set_last_error(const std::string& msg);
 // BAE_LAUNCH, which counts it and, while profiling is on, brackets it with
 // CUDA events on its stream (per-kernel device time, see bae_profile_*).
 void count_launch();
+void count_launches(long long k);   // k kernels launched at once (a graph)
+void capture_begin();               // launches until capture_end() are counted, not timed
+long long capture_end();            // returns the number counted
 void prof_push(const char* name, cudaStream_t st);
 void prof_pop(cudaStream_t st);
 
@@ -84,6 +87,15 @@ template <typename C> __device__ __forceinline__ C cmulc(C a, C b) {
 }
 template <typename C> __device__ __forceinline__ C cconj(C a) { return cmake<C>(a.x, -a.y); }
 template <typename C, typename T> __device__ __forceinline__ C cscale(C a, T s) { return cmake<C>(a.x * s, a.y * s); }
+
+// read-only cached load of one complex value
+template <typename C> __device__ __forceinline__ C ldg_c(const C* p) { return __ldg(p); }
+
+// element type of the potential written by the last convolution pass, and
+// the conversion to it (float32 -> float, float64 -> double)
+template <typename T> struct OutOf { using type = T; };
+__device__ __forceinline__ float to_out(float v) { return v; }
+__device__ __forceinline__ double to_out(double v) { return v; }
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 

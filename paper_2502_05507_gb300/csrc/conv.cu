@@ -22,6 +22,8 @@
 //             in place in B
 //   jpass^-1: inverse along j, keep j < N                     B -> A
 //   kpass^-1: C2R of two lines per complex inverse FFT, keep k < N -> v
+#include <type_traits>
+
 #include "conv.cuh"
 #include "fft2.cuh"
 
@@ -45,7 +47,10 @@ template <typename T, int L> struct Geo {
 };
 
 template <typename T>
-const char* kname(const char* f32, const char* f64) { return sizeof(T) == 4 ? f32 : f64; }
+const char* kname(const char* f32, const char* f64, const char* ds) {
+    if constexpr (std::is_same<T, dsf>::value) return ds;
+    return sizeof(T) == 4 ? f32 : f64;
+}
 
 // ------------------------------------------------------------- k pass (R2C)
 // Two real k-lines (i, 2p) and (i, 2p+1) per complex transform z = x_a + i x_b.
@@ -59,6 +64,7 @@ __global__ void __launch_bounds__(Geo<T, L>::KT) k_kpass_fwd(ConvArgs<T> a) {
     T* rho = reinterpret_cast<T*>(xch + G::P * G::XS);      // P * 2N
 
     const int b = blockIdx.z;
+    if (a.active && !a.active[b]) return;   // whole CTA: no barrier is skipped
     const int t = threadIdx.x % R1;
     const int p = threadIdx.x / R1;
     const long long pair = (long long)blockIdx.x * G::P + p;
@@ -71,7 +77,7 @@ __global__ void __launch_bounds__(Geo<T, L>::KT) k_kpass_fwd(ConvArgs<T> a) {
         for (int k = t; k < 2 * N; k += R1) r[k] = (T)0;
         __syncthreads();
         if (active) {
-            const double* q = a.q + (long long)b * a.q_stride;
+            const double* q = a.q + (long long)b * a.q_stride + (a.q_row ? (long long)(*a.q_row) * a.q_row_stride : 0);
 #pragma unroll
             for (int half = 0; half < 2; ++half) {
                 const long long l = half ? lb : la;
@@ -96,7 +102,7 @@ __global__ void __launch_bounds__(Geo<T, L>::KT) k_kpass_fwd(ConvArgs<T> a) {
 #pragma unroll
         for (int m = 0; m < R2; ++m) {
             const int n = t + R1 * m;
-            T va = 0, vb = 0;
+            T va = (T)0.0, vb = (T)0.0;
             if (active && n < N) {
                 const long long xa = la * N + n, xb = lb * N + n;
                 va = (a.flags[xa] & 1) ? (T)(a.scale * f[xa]) : (T)0;
@@ -139,6 +145,7 @@ __global__ void __launch_bounds__(Geo<T, L>::CT) k_colpass(ConvArgs<T> a) {
     C* xch = reinterpret_cast<C*>(smem_raw);   // L * W
 
     const int b = blockIdx.z;
+    if (a.active && !a.active[b]) return;
     const int o = blockIdx.y;               // i (j passes) or jj (i pass)
     const int c = threadIdx.x % W;
     const int t = threadIdx.x / W;
@@ -223,6 +230,7 @@ __global__ void __launch_bounds__(Geo<T, L>::KT) k_kpass_inv(ConvArgs<T> a) {
     C* xch = reinterpret_cast<C*>(smem_raw);
 
     const int b = blockIdx.z;
+    if (a.active && !a.active[b]) return;
     const int t = threadIdx.x % R1;
     const int p = threadIdx.x / R1;
     const long long pair = (long long)blockIdx.x * G::P + p;
@@ -253,16 +261,35 @@ __global__ void __launch_bounds__(Geo<T, L>::KT) k_kpass_inv(ConvArgs<T> a) {
         }
     fft_k2n<L, true>(v, xch, p * G::XS, R1 + 1, 1, t, a.tw);
     if (active) {
-        T* out = a.v + (long long)b * N * N * N;
+        typename OutOf<T>::type* out = a.v + (long long)b * N * N * N;
 #pragma unroll
         for (int m = 0; m < R2; ++m) {
             const int n = t + R1 * m;
             if (n < N) {
-                out[la * N + n] = v[m].x;
-                out[lb * N + n] = v[m].y;
+                out[la * N + n] = to_out(v[m].x);
+                out[lb * N + n] = to_out(v[m].y);
             }
         }
     }
+}
+
+template <typename T, int L>
+void configure_conv() {
+    using C = cplx_t<T>;
+    using G = Geo<T, L>;
+    constexpr int N = L / 2;
+    const size_t smem_k = (size_t)G::P * G::XS * sizeof(C) + (size_t)G::P * 2 * N * sizeof(T);
+    const size_t smem_c = (size_t)L * G::W * sizeof(C);
+    // once per instantiation (thread-safe static initialisation)
+    static const bool configured = [&]() {
+        BAE_CUDA(cudaFuncSetAttribute(k_kpass_fwd<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_k));
+        BAE_CUDA(cudaFuncSetAttribute(k_kpass_inv<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_k));
+        BAE_CUDA(cudaFuncSetAttribute(k_colpass<T, L, COL_FWD_J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
+        BAE_CUDA(cudaFuncSetAttribute(k_colpass<T, L, COL_CONV_I>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
+        BAE_CUDA(cudaFuncSetAttribute(k_colpass<T, L, COL_INV_J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
+        return true;
+    }();
+    (void)configured;
 }
 
 template <typename T, int L>
@@ -272,30 +299,23 @@ void run_conv(const ConvArgs<T>& a, cudaStream_t st) {
     constexpr int N = L / 2;
     const size_t smem_k = (size_t)G::P * G::XS * sizeof(C) + (size_t)G::P * 2 * N * sizeof(T);
     const size_t smem_c = (size_t)L * G::W * sizeof(C);
-    static bool configured = false;  // per instantiation
-    if (!configured) {
-        BAE_CUDA(cudaFuncSetAttribute(k_kpass_fwd<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_k));
-        BAE_CUDA(cudaFuncSetAttribute(k_kpass_inv<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_k));
-        BAE_CUDA(cudaFuncSetAttribute(k_colpass<T, L, COL_FWD_J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
-        BAE_CUDA(cudaFuncSetAttribute(k_colpass<T, L, COL_CONV_I>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
-        BAE_CUDA(cudaFuncSetAttribute(k_colpass<T, L, COL_INV_J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
-        configured = true;
-    }
+    configure_conv<T, L>();
     const int nb = a.nbatch;
     const dim3 gk(ceil_div((long long)N * N / 2, G::P), 1, nb);
     const int ncolblk = ceil_div(N + 1, G::W);
-    BAE_LAUNCH(kname<T>("conv_kfwd.f32", "conv_kfwd.f64"), st, k_kpass_fwd<T, L><<<gk, G::KT, smem_k, st>>>(a));
-    BAE_LAUNCH(kname<T>("conv_jfwd.f32", "conv_jfwd.f64"), st, k_colpass<T, L, COL_FWD_J><<<dim3(ncolblk, N, nb), G::CT, smem_c, st>>>(a));
-    BAE_LAUNCH(kname<T>("conv_i.f32", "conv_i.f64"), st, k_colpass<T, L, COL_CONV_I><<<dim3(ncolblk, 2 * N, nb), G::CT, smem_c, st>>>(a));
-    BAE_LAUNCH(kname<T>("conv_jinv.f32", "conv_jinv.f64"), st, k_colpass<T, L, COL_INV_J><<<dim3(ncolblk, N, nb), G::CT, smem_c, st>>>(a));
-    BAE_LAUNCH(kname<T>("conv_kinv.f32", "conv_kinv.f64"), st, k_kpass_inv<T, L><<<gk, G::KT, smem_k, st>>>(a));
+    BAE_LAUNCH(kname<T>("conv_kfwd.f32", "conv_kfwd.f64", "conv_kfwd.df64"), st, k_kpass_fwd<T, L><<<gk, G::KT, smem_k, st>>>(a));
+    BAE_LAUNCH(kname<T>("conv_jfwd.f32", "conv_jfwd.f64", "conv_jfwd.df64"), st, k_colpass<T, L, COL_FWD_J><<<dim3(ncolblk, N, nb), G::CT, smem_c, st>>>(a));
+    BAE_LAUNCH(kname<T>("conv_i.f32", "conv_i.f64", "conv_i.df64"), st, k_colpass<T, L, COL_CONV_I><<<dim3(ncolblk, 2 * N, nb), G::CT, smem_c, st>>>(a));
+    BAE_LAUNCH(kname<T>("conv_jinv.f32", "conv_jinv.f64", "conv_jinv.df64"), st, k_colpass<T, L, COL_INV_J><<<dim3(ncolblk, N, nb), G::CT, smem_c, st>>>(a));
+    BAE_LAUNCH(kname<T>("conv_kinv.f32", "conv_kinv.f64", "conv_kinv.df64"), st, k_kpass_inv<T, L><<<gk, G::KT, smem_k, st>>>(a));
 }
 
 // ------------------------------------------------------------------ gathers
 template <typename T>
 __global__ void k_closure_gather(const T* v, long long v_stride, const int* gm, const int* partner,
-                                 const double* t, int n, double* out, long long out_stride) {
+                                 const double* t, int n, double* out, long long out_stride, const int* active) {
     const int b = blockIdx.y;
+    if (active && !active[b]) return;
     const T* vb = v + b * v_stride;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
         const double tr = t[r];
@@ -310,6 +330,11 @@ __global__ void k_volume_combine(const T* v, const double* add, const uint8_t* f
         const bool np = (flags[x] & 3) != 0;   // M+ or gamma-
         u[b * n3 + x] = np ? (add ? add[b * n3 + x] : 0.0) + (double)v[b * n3 + x] : 0.0;
     }
+}
+
+__global__ void k_to_dsf(const double* in, long long n, dsf* out) {
+    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n; x += (long long)gridDim.x * blockDim.x)
+        out[x] = dsf(in[x]);
 }
 
 template <typename T>
@@ -334,11 +359,24 @@ void conv_apply(const ConvArgs<T>& a, cudaStream_t st) {
 }
 
 template <typename T>
+void conv_prepare(int N) {
+    switch (N) {
+        case 8: configure_conv<T, 16>(); break;
+        case 16: configure_conv<T, 32>(); break;
+        case 32: configure_conv<T, 64>(); break;
+        case 64: configure_conv<T, 128>(); break;
+        case 128: configure_conv<T, 256>(); break;
+        case 256: configure_conv<T, 512>(); break;
+        default: throw Error(BAE_ERR_INVALID_ARG, "conv: N must be a power of two in [8, 256]");
+    }
+}
+
+template <typename T>
 void closure_gather(const T* v, long long v_stride, const int* gm, const int* partner, const double* t,
-                    int n, int nbatch, double* out, long long out_stride, cudaStream_t st) {
+                    int n, int nbatch, double* out, long long out_stride, cudaStream_t st, const int* active) {
     if (n == 0) return;
     dim3 grid(ceil_div(n, 256) < 1184 ? ceil_div(n, 256) : 1184, nbatch);
-    BAE_LAUNCH(kname<T>("closure_gather.f32", "closure_gather.f64"), st, k_closure_gather<T><<<grid, 256, 0, st>>>(v, v_stride, gm, partner, t, n, out, out_stride));
+    BAE_LAUNCH(kname<T>("closure_gather.f32", "closure_gather.f64", "closure_gather.f64"), st, k_closure_gather<T><<<grid, 256, 0, st>>>(v, v_stride, gm, partner, t, n, out, out_stride, active));
 }
 
 template <typename T>
@@ -353,10 +391,18 @@ void widen(const T* v, long long n, double* out, cudaStream_t st) {
     BAE_LAUNCH("k_widen", st, k_widen<T><<<ceil_div(n, 256) < 2432 ? ceil_div(n, 256) : 2432, 256, 0, st>>>(v, n, out));
 }
 
+void to_dsf(const double* in, long long n, dsf* out, cudaStream_t st) {
+    BAE_LAUNCH("k_to_dsf", st, k_to_dsf<<<ceil_div(n, 256) < 2432 ? ceil_div(n, 256) : 2432, 256, 0, st>>>(in, n, out));
+}
+
 template void conv_apply<float>(const ConvArgs<float>&, cudaStream_t);
 template void conv_apply<double>(const ConvArgs<double>&, cudaStream_t);
-template void closure_gather<float>(const float*, long long, const int*, const int*, const double*, int, int, double*, long long, cudaStream_t);
-template void closure_gather<double>(const double*, long long, const int*, const int*, const double*, int, int, double*, long long, cudaStream_t);
+template void conv_apply<dsf>(const ConvArgs<dsf>&, cudaStream_t);
+template void conv_prepare<float>(int);
+template void conv_prepare<double>(int);
+template void conv_prepare<dsf>(int);
+template void closure_gather<float>(const float*, long long, const int*, const int*, const double*, int, int, double*, long long, cudaStream_t, const int*);
+template void closure_gather<double>(const double*, long long, const int*, const int*, const double*, int, int, double*, long long, cudaStream_t, const int*);
 template void volume_combine<float>(const float*, const double*, const uint8_t*, long long, int, double*, cudaStream_t);
 template void volume_combine<double>(const double*, const double*, const uint8_t*, long long, int, double*, cudaStream_t);
 template void widen<float>(const float*, long long, double*, cudaStream_t);

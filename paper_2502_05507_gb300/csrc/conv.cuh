@@ -2,6 +2,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "dsf.cuh"
 
 namespace bae {
 
@@ -23,9 +24,15 @@ struct ConvArgs {
     int N = 0;
     int nbatch = 1;
     SourceMode mode = SRC_DENSITY;
-    // SRC_DENSITY: q [nbatch][q_stride] float64 density on gamma-
+    // SRC_DENSITY: q [nbatch][q_stride] float64 density on gamma-; when q_row
+    // is set, batch item b reads q + b q_stride + (*q_row) q_row_stride (the
+    // row index lives in device memory, so a captured graph can advance it)
     const double* q = nullptr;
     long long q_stride = 0;
+    const int* q_row = nullptr;
+    long long q_row_stride = 0;
+    // optional per-item flags: items with active[b] == 0 are skipped
+    const int* active = nullptr;
     SrcRecipe rec;
     // SRC_VOLUME: rho = scale * f on nodes with (flags & 1)
     const double* f = nullptr;
@@ -36,21 +43,31 @@ struct ConvArgs {
     cplx_t<T>* B = nullptr;
     const T* ghat = nullptr;      // (N+1)^3 octant, includes 1/(2N)^3
     const cplx_t<T>* tw = nullptr;  // exp(-2 pi i m / 2N), m < 2N
-    T* v = nullptr;               // [nbatch][N^3] output potential
+    typename OutOf<T>::type* v = nullptr;   // [nbatch][N^3] output potential
 };
 
 template <typename T>
 void conv_apply(const ConvArgs<T>& a, cudaStream_t st);
 
-// out[b][r] = t[r] v[b][gm[r]] + (1 - t[r]) v[b][partner[r]]
+// Sets the kernel attributes conv_apply needs for grid size N (done on the
+// first apply anyway; call it before capturing applies in a CUDA graph).
+template <typename T>
+void conv_prepare(int N);
+
+// out[b][r] = t[r] v[b][gm[r]] + (1 - t[r]) v[b][partner[r]]  (items with
+// active[b] == 0 skipped when active is not null)
 template <typename T>
 void closure_gather(const T* v, long long v_stride, const int* gm, const int* partner, const double* t,
-                    int n, int nbatch, double* out, long long out_stride, cudaStream_t st);
+                    int n, int nbatch, double* out, long long out_stride, cudaStream_t st,
+                    const int* active = nullptr);
 
 // u[b][x] = (nplus(x) ? add[b][x] + v[b][x] : 0) over the N^3 grid
 template <typename T>
 void volume_combine(const T* v, const double* add, const uint8_t* flags, long long n3, int nbatch,
                     double* u, cudaStream_t st);
+
+// out[i] = nearest double-float of in[i]
+void to_dsf(const double* in, long long n, dsf* out, cudaStream_t st);
 
 // v (T) -> out (double), plain copy
 template <typename T>

@@ -1,0 +1,81 @@
+// Double-float arithmetic: a value is hi + lo with two float32 parts
+// (|lo| <= ulp(hi)/2), about 48 significant bits. Used for the
+// float64-accurate potential apply on GB300, whose float32 pipes are ~58x
+// faster than its float64 ones (measured: 70.2 vs 1.20 TFLOP/s), so the
+// float64-accurate FFT runs on the float32 units at a fraction of the cost.
+//
+// The algorithms are the classical error-free transformations: Knuth's
+// TwoSum, Dekker's Fast2Sum (QuickTwoSum) and the fused-multiply-add
+// TwoProd, combined as in the double-double arithmetic of Hida, Li and
+// Bailey ("Algorithms for quad-double precision floating point
+// arithmetic", 2001): the IEEE-style accurate addition and the
+// FMA-based multiplication.
+#pragma once
+
+#include "common.cuh"
+
+namespace bae {
+
+struct __align__(8) dsf {
+    float hi, lo;
+    __host__ __device__ dsf() = default;
+    __host__ __device__ constexpr dsf(float h, float l) : hi(h), lo(l) {}
+    // nearest double-float to a double (exact for up to 48 significant bits)
+    __host__ __device__ explicit dsf(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+    __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+
+__device__ __forceinline__ dsf fast_two_sum(float a, float b) {   // |a| >= |b|
+    const float s = __fadd_rn(a, b);
+    const float e = __fsub_rn(b, __fsub_rn(s, a));
+    return dsf(s, e);
+}
+
+__device__ __forceinline__ dsf two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return dsf(s, e);
+}
+
+__device__ __forceinline__ dsf operator+(dsf a, dsf b) {
+    dsf s = two_sum(a.hi, b.hi);
+    const dsf t = two_sum(a.lo, b.lo);
+    s.lo = __fadd_rn(s.lo, t.hi);
+    s = fast_two_sum(s.hi, s.lo);
+    s.lo = __fadd_rn(s.lo, t.lo);
+    return fast_two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ dsf operator-(dsf a) { return dsf(-a.hi, -a.lo); }
+__device__ __forceinline__ dsf operator-(dsf a, dsf b) { return a + (-b); }
+
+__device__ __forceinline__ dsf operator*(dsf a, dsf b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return fast_two_sum(p, e);
+}
+
+// complex double-float
+struct __align__(16) dsc {
+    dsf x, y;
+};
+
+template <> struct Cplx<dsf> { using type = dsc; };
+
+template <>
+__device__ __forceinline__ dsc ldg_c<dsc>(const dsc* p) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    dsc r;
+    r.x = dsf(v.x, v.y);
+    r.y = dsf(v.z, v.w);
+    return r;
+}
+
+// element type written by the last convolution pass
+template <> struct OutOf<dsf> { using type = double; };
+__device__ __forceinline__ double to_out(dsf v) { return (double)v.hi + (double)v.lo; }
+
+}  // namespace bae

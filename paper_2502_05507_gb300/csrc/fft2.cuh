@@ -139,7 +139,7 @@ __device__ __forceinline__ void fft_n2k(C* v, C* xch, int base, int sk, int sn, 
     rdft<R2, INV>(v);                                   // v[k2] = Y[t][k2]
 #pragma unroll
     for (int k2 = 1; k2 < R2; ++k2) {
-        const C w = __ldg(reinterpret_cast<const C*>(tw) + t * k2);
+        const C w = ldg_c(tw + t * k2);
         v[k2] = INV ? cmulc(v[k2], w) : cmul(v[k2], w);
     }
 #pragma unroll
@@ -166,7 +166,7 @@ __device__ __forceinline__ void fft_k2n(C* v, C* xch, int base, int sk, int sn, 
         for (int n1 = 0; n1 < R1; ++n1) {
             const int k2 = t + q * R1;
             if (n1 > 0 && k2 > 0) {
-                const C w = __ldg(reinterpret_cast<const C*>(tw) + n1 * k2);
+                const C w = ldg_c(tw + n1 * k2);
                 v[q * R1 + n1] = INV ? cmulc(v[q * R1 + n1], w) : cmul(v[q * R1 + n1], w);
             }
             xch[base + k2 * sk + n1 * sn] = v[q * R1 + n1];

@@ -14,104 +14,16 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// partial[b][i][c] = sum over chunk c of V[b][i][r] w[b][r], i in [i0, i0+ICH) n [0, cols)
-__global__ void __launch_bounds__(256) k_dots(KrylovBatch k, const int* __restrict__ active, int cols) {
-    __shared__ double s_w[CH];
-    const int b = active[blockIdx.y];
-    const int c = blockIdx.x;
-    const long long r0 = (long long)c * CH;
-    const double* w = k.w + (long long)b * k.n;
-    for (int e = threadIdx.x; e < CH; e += blockDim.x) s_w[e] = (r0 + e < k.n) ? w[r0 + e] : 0.0;
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int i0 = blockIdx.z * ICH;
-    for (int i = i0 + warp; i < i0 + ICH && i < cols; i += 8) {
-        const double* v = k.V + ((long long)b * k.mp1 + i) * k.n;
-        double acc = 0.0;
-        for (int e = lane; e < CH; e += 32)
-            if (r0 + e < k.n) acc += v[r0 + e] * s_w[e];
-        acc = warp_sum(acc);
-        if (lane == 0) k.partial[((long long)b * (k.mp1 + 1) + i) * k.nchunk + c] = acc;
-    }
-}
-
-// h[b][i] = sum_c partial[b][i][c] for i in rows [i_lo, i_hi)
-__global__ void k_reduce(KrylovBatch k, const int* __restrict__ active, int i_lo, int i_hi) {
-    const int b = active[blockIdx.y];
-    for (int i = i_lo + blockIdx.x * blockDim.x + threadIdx.x; i < i_hi; i += gridDim.x * blockDim.x) {
-        const double* p = k.partial + ((long long)b * (k.mp1 + 1) + i) * k.nchunk;
-        double acc = 0.0;
-        for (int c = 0; c < k.nchunk; ++c) acc += p[c];
-        k.h[(long long)b * (k.mp1 + 1) + i] = acc;
-    }
-}
-
-// w[b] -= sum_i V[b][i] h[b][i]; partial of ||w||^2 into row mp1
-__global__ void __launch_bounds__(256) k_update_norm(KrylovBatch k, const int* __restrict__ active, int cols) {
-    __shared__ double s_h[256];
-    __shared__ double s_red[8];
-    const int b = active[blockIdx.y];
-    const int c = blockIdx.x;
-    const long long r0 = (long long)c * CH;
-    double* w = k.w + (long long)b * k.n;
-    const double* hb = k.h + (long long)b * (k.mp1 + 1);
-    double nrm = 0.0;
-    for (int e = threadIdx.x; e < CH; e += blockDim.x) {
-        const long long r = r0 + e;
-        double acc = (r < k.n) ? w[r] : 0.0;
-        for (int i0 = 0; i0 < cols; i0 += 256) {
-            // stage h in shared memory, 256 at a time (same for every e)
-            __syncthreads();
-            if (i0 + (int)threadIdx.x < cols) s_h[threadIdx.x] = hb[i0 + threadIdx.x];
-            __syncthreads();
-            const int iend = min(cols - i0, 256);
-            if (r < k.n)
-                for (int i = 0; i < iend; ++i)
-                    acc -= k.V[((long long)b * k.mp1 + i0 + i) * k.n + r] * s_h[i];
-        }
-        if (r < k.n) {
-            w[r] = acc;
-            nrm += acc * acc;
-        }
-    }
-    nrm = warp_sum(nrm);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) s_red[warp] = nrm;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += s_red[q];
-        k.partial[((long long)b * (k.mp1 + 1) + k.mp1) * k.nchunk + c] = s;
-    }
-}
-
-__global__ void k_scale_into(KrylovBatch k, const int* __restrict__ active, int j) {
-    const int b = active[blockIdx.y];
-    const double n2 = k.h[(long long)b * (k.mp1 + 1) + k.mp1];
-    const double s = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
-    const double* w = k.w + (long long)b * k.n;
-    double* v = k.V + ((long long)b * k.mp1 + j) * k.n;
-    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < k.n; r += (long long)gridDim.x * blockDim.x)
-        v[r] = w[r] * s;
-}
-
-__global__ void k_combine(KrylovBatch k, const int* __restrict__ active, int cols, const double* __restrict__ y,
+// x[b] += sum_{i < cols} V[b][i] y[b][i], V [nb][mp1][n], y [nb][ystride]
+__global__ void k_combine(const double* __restrict__ V, int n, int mp1, int cols, const double* __restrict__ y,
                           int ystride, double* __restrict__ x) {
-    const int b = active[blockIdx.y];
+    const int b = blockIdx.y;
     const double* yb = y + (long long)b * ystride;
-    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < k.n; r += (long long)gridDim.x * blockDim.x) {
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
         double acc = 0.0;
-        for (int i = 0; i < cols; ++i) acc += k.V[((long long)b * k.mp1 + i) * k.n + r] * yb[i];
-        x[(long long)b * k.n + r] += acc;
+        for (int i = 0; i < cols; ++i) acc += V[((long long)b * mp1 + i) * n + r] * yb[i];
+        x[(long long)b * n + r] += acc;
     }
-}
-
-__global__ void k_scale(const double* __restrict__ x, const double* __restrict__ alpha, const int* __restrict__ active,
-                        int n, double* __restrict__ y) {
-    const int b = active[blockIdx.y];
-    const double a = alpha[b];
-    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
-        y[(long long)b * n + r] = x[(long long)b * n + r] * a;
 }
 
 __global__ void k_norm2_partial(const double* __restrict__ x, const int* __restrict__ active, int n, double* partial,
@@ -156,53 +68,11 @@ __global__ void k_add(const double* x, const int* __restrict__ active, int n, do
         y[(long long)b * n + r] += x[(long long)b * n + r];
 }
 
-__global__ void k_gather_rows(const double* src, const int* __restrict__ active, long long n, double* dst) {
-    const int q = blockIdx.y;
-    const int b = active[q];
-    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
-        dst[(long long)q * n + r] = src[(long long)b * n + r];
-}
-
-__global__ void k_scatter_rows(const double* src, const int* __restrict__ active, long long n, double* dst) {
-    const int q = blockIdx.y;
-    const int b = active[q];
-    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
-        dst[(long long)b * n + r] = src[(long long)q * n + r];
-}
-
 int blocks_for(long long n) { return (int)std::min<long long>((n + 255) / 256, 1216); }
 
 }  // namespace
 
 int krylov_chunks(int n) { return ceil_div(n, CH); }
-
-void kr_dots(const KrylovBatch& k, const int* active, int na, int cols, cudaStream_t st) {
-    if (na == 0 || cols == 0) return;
-    BAE_LAUNCH("k_dots", st, k_dots<<<dim3(k.nchunk, na, ceil_div(cols, ICH)), 256, 0, st>>>(k, active, cols));
-    BAE_LAUNCH("k_reduce", st, k_reduce<<<dim3(ceil_div(cols, 128), na), 128, 0, st>>>(k, active, 0, cols));
-}
-
-void kr_update_norm(const KrylovBatch& k, const int* active, int na, int cols, cudaStream_t st) {
-    if (na == 0) return;
-    BAE_LAUNCH("k_update_norm", st, k_update_norm<<<dim3(k.nchunk, na), 256, 0, st>>>(k, active, cols));
-    BAE_LAUNCH("k_reduce", st, k_reduce<<<dim3(1, na), 32, 0, st>>>(k, active, k.mp1, k.mp1 + 1));
-}
-
-void kr_scale_into(const KrylovBatch& k, const int* active, int na, int j, cudaStream_t st) {
-    if (na == 0) return;
-    BAE_LAUNCH("k_scale_into", st, k_scale_into<<<dim3(blocks_for(k.n), na), 256, 0, st>>>(k, active, j));
-}
-
-void kr_combine(const KrylovBatch& k, const int* active, int na, int cols, const double* y, int ystride, double* x,
-                cudaStream_t st) {
-    if (na == 0 || cols == 0) return;
-    BAE_LAUNCH("k_combine", st, k_combine<<<dim3(blocks_for(k.n), na), 256, 0, st>>>(k, active, cols, y, ystride, x));
-}
-
-void kr_scale(const double* x, const double* alpha, const int* active, int na, int n, double* y, cudaStream_t st) {
-    if (na == 0) return;
-    BAE_LAUNCH("k_scale", st, k_scale<<<dim3(blocks_for(n), na), 256, 0, st>>>(x, alpha, active, n, y));
-}
 
 void kr_norm2(const double* x, const int* active, int na, int n, double* partial, int nchunk, double* out,
               cudaStream_t st) {
@@ -221,14 +91,262 @@ void kr_add(const double* x, const int* active, int na, int n, double* y, cudaSt
     BAE_LAUNCH("k_add", st, k_add<<<dim3(blocks_for(n), na), 256, 0, st>>>(x, active, n, y));
 }
 
-void kr_gather_rows(const double* src, const int* active, int na, long long n, double* dst, cudaStream_t st) {
-    if (na == 0) return;
-    BAE_LAUNCH("k_gather_rows", st, k_gather_rows<<<dim3(blocks_for(n), na), 256, 0, st>>>(src, active, n, dst));
+}  // namespace bae
+
+// ======================================================= device-side GMRES
+namespace bae {
+
+namespace {
+
+__device__ __forceinline__ bool last_block(unsigned int* ctr, unsigned int nblocks, int* s_flag) {
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int t = atomicAdd(ctr, 1u);
+        *s_flag = (t == nblocks - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    return *s_flag != 0;
 }
 
-void kr_scatter_rows(const double* src, const int* active, int na, long long n, double* dst, cudaStream_t st) {
-    if (na == 0) return;
-    BAE_LAUNCH("k_scatter_rows", st, k_scatter_rows<<<dim3(blocks_for(n), na), 256, 0, st>>>(src, active, n, dst));
+__global__ void k_arn_init(Arnoldi a, const double* __restrict__ nrm2, const int* __restrict__ member) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < a.nb; b += gridDim.x * blockDim.x) {
+        const double beta = sqrt(nrm2[b]);
+        const bool go = member[b] != 0 && beta > a.target[b];
+        double* g = a.g + (long long)b * (a.m + 1);
+        for (int i = 0; i <= a.m; ++i) g[i] = 0.0;
+        g[0] = beta;
+        a.est[b] = beta;
+        a.flag[b] = go ? 1 : 0;
+        a.inv[b] = beta > 0.0 ? 1.0 / beta : 0.0;
+        a.ncols[b] = 0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.j = 0;
+}
+
+__global__ void k_arn_row0(Arnoldi a, const double* __restrict__ r) {
+    const int b = blockIdx.y;
+    if (!a.flag[b]) return;
+    const double s = a.inv[b];
+    double* v = a.V + (long long)b * (a.m + 1) * a.n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.n; i += (long long)gridDim.x * blockDim.x)
+        v[i] = r[(long long)b * a.n + i] * s;
+}
+
+// pass 1: h1 = V^T w over rows i <= j
+__global__ void __launch_bounds__(256) k_arn_dots(Arnoldi a) {
+    __shared__ double s_w[CH];
+    __shared__ int s_last;
+    const int b = blockIdx.y;
+    if (!a.flag[b]) return;
+    const int cols = *a.j + 1;
+    const int c = blockIdx.x;
+    const long long r0 = (long long)c * CH;
+    const double* w = a.w + (long long)b * a.n;
+    for (int e = threadIdx.x; e < CH; e += blockDim.x) s_w[e] = (r0 + e < a.n) ? w[r0 + e] : 0.0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double* part = a.part + (long long)b * (a.m + 2) * a.nchunk;
+    for (int i = warp; i < cols; i += 8) {
+        const double* v = a.V + ((long long)b * (a.m + 1) + i) * a.n;
+        double acc = 0.0;
+        for (int e = lane; e < CH; e += 32)
+            if (r0 + e < a.n) acc += v[r0 + e] * s_w[e];
+        acc = warp_sum(acc);
+        if (lane == 0) part[(long long)i * a.nchunk + c] = acc;
+    }
+    if (last_block(a.ctr + 3 * b + 0, gridDim.x, &s_last)) {
+        for (int i = threadIdx.x; i < cols; i += blockDim.x) {
+            double s = 0.0;
+            for (int q = 0; q < a.nchunk; ++q) s += __ldcg(part + (long long)i * a.nchunk + q);
+            a.h1[(long long)b * (a.m + 1) + i] = s;
+        }
+        if (threadIdx.x == 0) a.ctr[3 * b + 0] = 0;
+    }
+}
+
+// pass 2: w -= V h1, then h2 = V^T w; hcol = h1 + h2, h1 <- h2
+__global__ void __launch_bounds__(256) k_arn_update_dots(Arnoldi a) {
+    extern __shared__ double s_dyn[];
+    double* s_h = s_dyn;             // m + 1
+    double* s_w = s_dyn + (a.m + 1); // CH
+    __shared__ int s_last;
+    const int b = blockIdx.y;
+    if (!a.flag[b]) return;
+    const int cols = *a.j + 1;
+    const int c = blockIdx.x;
+    const long long r0 = (long long)c * CH;
+    double* w = a.w + (long long)b * a.n;
+    const double* h1 = a.h1 + (long long)b * (a.m + 1);
+    for (int i = threadIdx.x; i < cols; i += blockDim.x) s_h[i] = h1[i];
+    __syncthreads();
+    const double* Vb = a.V + (long long)b * (a.m + 1) * a.n;
+    for (int e = threadIdx.x; e < CH; e += blockDim.x) {
+        const long long r = r0 + e;
+        double acc = 0.0;
+        if (r < a.n) {
+            acc = w[r];
+            for (int i = 0; i < cols; ++i) acc -= Vb[(long long)i * a.n + r] * s_h[i];
+            w[r] = acc;
+        }
+        s_w[e] = acc;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double* part = a.part + (long long)b * (a.m + 2) * a.nchunk;
+    for (int i = warp; i < cols; i += 8) {
+        const double* v = Vb + (long long)i * a.n;
+        double acc = 0.0;
+        for (int e = lane; e < CH; e += 32)
+            if (r0 + e < a.n) acc += v[r0 + e] * s_w[e];
+        acc = warp_sum(acc);
+        if (lane == 0) part[(long long)i * a.nchunk + c] = acc;
+    }
+    if (last_block(a.ctr + 3 * b + 1, gridDim.x, &s_last)) {
+        for (int i = threadIdx.x; i < cols; i += blockDim.x) {
+            double s = 0.0;
+            for (int q = 0; q < a.nchunk; ++q) s += __ldcg(part + (long long)i * a.nchunk + q);
+            a.hcol[(long long)b * (a.m + 1) + i] = s_h[i] + s;
+            a.h1[(long long)b * (a.m + 1) + i] = s;
+        }
+        if (threadIdx.x == 0) a.ctr[3 * b + 1] = 0;
+    }
+}
+
+// pass 3: w -= V h2, ||w||; the last block applies the Givens rotations,
+// updates the residual estimate and the flags
+__global__ void __launch_bounds__(256) k_arn_update_norm(Arnoldi a) {
+    extern __shared__ double s_dyn[];
+    double* s_h = s_dyn;
+    __shared__ double s_red[8];
+    __shared__ int s_last;
+    const int b = blockIdx.y;
+    if (!a.flag[b]) return;
+    const int j = *a.j;
+    const int cols = j + 1;
+    const int c = blockIdx.x;
+    const long long r0 = (long long)c * CH;
+    double* w = a.w + (long long)b * a.n;
+    const double* h2 = a.h1 + (long long)b * (a.m + 1);
+    for (int i = threadIdx.x; i < cols; i += blockDim.x) s_h[i] = h2[i];
+    __syncthreads();
+    const double* Vb = a.V + (long long)b * (a.m + 1) * a.n;
+    double nrm = 0.0;
+    for (int e = threadIdx.x; e < CH; e += blockDim.x) {
+        const long long r = r0 + e;
+        if (r < a.n) {
+            double acc = w[r];
+            for (int i = 0; i < cols; ++i) acc -= Vb[(long long)i * a.n + r] * s_h[i];
+            w[r] = acc;
+            nrm += acc * acc;
+        }
+    }
+    nrm = warp_sum(nrm);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = nrm;
+    __syncthreads();
+    double* part = a.part + (long long)b * (a.m + 2) * a.nchunk;
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += s_red[q];
+        part[(long long)(a.m + 1) * a.nchunk + c] = s;
+    }
+    if (last_block(a.ctr + 3 * b + 2, gridDim.x, &s_last)) {
+        if (threadIdx.x == 0) {
+            double n2 = 0.0;
+            for (int q = 0; q < a.nchunk; ++q) n2 += __ldcg(part + (long long)(a.m + 1) * a.nchunk + q);
+            const double hn = sqrt(n2);
+            const int m = a.m;
+            double* col = a.H + ((long long)b * m + j) * (m + 1);
+            const double* hc = a.hcol + (long long)b * (m + 1);
+            double* cs = a.cs + (long long)b * m;
+            double* sn = a.sn + (long long)b * m;
+            double* g = a.g + (long long)b * (m + 1);
+            for (int i = 0; i <= j; ++i) col[i] = hc[i];
+            col[j + 1] = hn;
+            for (int i = 0; i < j; ++i) {
+                const double x0 = col[i], x1 = col[i + 1];
+                col[i] = cs[i] * x0 + sn[i] * x1;
+                col[i + 1] = -sn[i] * x0 + cs[i] * x1;
+            }
+            const double rr = hypot(col[j], col[j + 1]);
+            const double cj = rr > 0.0 ? col[j] / rr : 1.0;
+            const double sj = rr > 0.0 ? col[j + 1] / rr : 0.0;
+            cs[j] = cj;
+            sn[j] = sj;
+            col[j] = rr;
+            col[j + 1] = 0.0;
+            g[j + 1] = -sj * g[j];
+            g[j] = cj * g[j];
+            const double e = fabs(g[j + 1]);
+            a.est[b] = e;
+            a.ncols[b] = j + 1;
+            a.inv[b] = hn > 0.0 ? 1.0 / hn : 0.0;
+            a.flag[b] = (e > a.target[b] && hn > 0.0 && j + 1 < m) ? 1 : 0;
+            a.ctr[3 * b + 2] = 0;
+        }
+    }
+}
+
+__global__ void k_arn_next(Arnoldi a) {
+    const int b = blockIdx.y;
+    if (!a.flag[b]) return;
+    const int j = *a.j;
+    const double s = a.inv[b];
+    const double* w = a.w + (long long)b * a.n;
+    double* v = a.V + ((long long)b * (a.m + 1) + j + 1) * a.n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.n; i += (long long)gridDim.x * blockDim.x)
+        v[i] = w[i] * s;
+}
+
+__global__ void k_arn_advance(Arnoldi a) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *a.j += 1;
+}
+
+// y = R^{-1} g, one warp per RHS (column-oriented back substitution)
+__global__ void k_arn_backsub(Arnoldi a) {
+    extern __shared__ double s_rhs[];
+    const int b = blockIdx.x;
+    const int c = a.ncols[b];
+    const int m = a.m;
+    double* y = a.y + (long long)b * m;
+    const double* g = a.g + (long long)b * (m + 1);
+    const double* H = a.H + (long long)b * m * (m + 1);
+    for (int l = threadIdx.x; l < m; l += blockDim.x) {
+        s_rhs[l] = l < c ? g[l] : 0.0;
+        y[l] = 0.0;
+    }
+    __syncwarp();
+    for (int i = c - 1; i >= 0; --i) {
+        const double d = H[(long long)i * (m + 1) + i];
+        const double yi = d != 0.0 ? s_rhs[i] / d : 0.0;
+        __syncwarp();
+        for (int l = threadIdx.x; l < i; l += blockDim.x) s_rhs[l] -= H[(long long)i * (m + 1) + l] * yi;
+        if (threadIdx.x == 0) y[i] = yi;
+        __syncwarp();
+    }
+}
+
+}  // namespace
+
+void arn_init(const Arnoldi& a, const double* r, const double* nrm2, const int* member, cudaStream_t st) {
+    BAE_LAUNCH("k_arn_init", st, k_arn_init<<<ceil_div(a.nb, 128), 128, 0, st>>>(a, nrm2, member));
+    BAE_LAUNCH("k_arn_row0", st, k_arn_row0<<<dim3(blocks_for(a.n), a.nb), 256, 0, st>>>(a, r));
+}
+
+void arn_step(const Arnoldi& a, cudaStream_t st) {
+    const size_t sh = (size_t)(a.m + 1 + CH) * sizeof(double);
+    BAE_LAUNCH("k_arn_dots", st, k_arn_dots<<<dim3(a.nchunk, a.nb), 256, 0, st>>>(a));
+    BAE_LAUNCH("k_arn_update_dots", st, k_arn_update_dots<<<dim3(a.nchunk, a.nb), 256, sh, st>>>(a));
+    BAE_LAUNCH("k_arn_update_norm", st, k_arn_update_norm<<<dim3(a.nchunk, a.nb), 256, (a.m + 1) * sizeof(double), st>>>(a));
+    BAE_LAUNCH("k_arn_next", st, k_arn_next<<<dim3(blocks_for(a.n), a.nb), 256, 0, st>>>(a));
+    BAE_LAUNCH("k_arn_advance", st, k_arn_advance<<<1, 32, 0, st>>>(a));
+}
+
+void arn_finish(const Arnoldi& a, double* x, int maxcols, cudaStream_t st) {
+    BAE_LAUNCH("k_arn_backsub", st, k_arn_backsub<<<a.nb, 32, a.m * sizeof(double), st>>>(a));
+    if (maxcols <= 0) return;
+    // every RHS: those with ncols = 0 have y = 0
+    BAE_LAUNCH("k_combine", st, k_combine<<<dim3(blocks_for(a.n), a.nb), 256, 0, st>>>(a.V, a.n, a.m + 1, maxcols, a.y, a.m, x));
 }
 
 }  // namespace bae

@@ -43,6 +43,8 @@ def test_apply_full_size(setup):
     assert np.max(np.abs(v - ref)) <= 1e-12 * scale
     v32 = prob.potential_apply(torch.from_numpy(q).cuda(), "fp32").cpu().numpy()
     assert np.max(np.abs(v32 - ref)) <= 2e-6 * scale
+    vds = prob.potential_apply(torch.from_numpy(q).cuda(), "df64").cpu().numpy()
+    assert np.max(np.abs(vds - ref)) <= 1e-12 * scale
 
 
 def test_apply_full_size_sampled_direct_sum(setup):
@@ -59,7 +61,7 @@ def test_apply_full_size_sampled_direct_sum(setup):
     assert np.max(np.abs(v - ref)) <= 1e-12 * np.max(np.abs(ref))
 
 
-@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+@pytest.mark.parametrize("precision", ["mixed", "fp64", "df64"])
 def test_solve_full_size(setup, precision):
     import torch
     P, spec, prob = setup["P"], setup["spec"], setup["prob"]

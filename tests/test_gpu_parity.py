@@ -124,6 +124,8 @@ def test_potential_apply_matches_direct_sum(ctx, make, layer):
     assert np.max(np.abs(v - ref)) <= 1e-12 * scale
     v32 = prob.potential_apply(torch.from_numpy(q).cuda(), "fp32").cpu().numpy()
     assert np.max(np.abs(v32 - ref)) <= 2e-6 * scale
+    vds = prob.potential_apply(torch.from_numpy(q).cuda(), "df64").cpu().numpy()
+    assert np.max(np.abs(vds - ref)) <= 1e-12 * scale
     # boundary operator: closure rows of K q
     Aq = prob.boundary_apply(torch.from_numpy(q).cuda(), "fp64").cpu().numpy()
     ref_A = OS.closure_apply(cls, ref.reshape(-1))
@@ -145,6 +147,8 @@ def test_particular_solution(ctx):
     assert np.max(np.abs(up - ref)) <= 1e-12 * np.max(np.abs(ref))
     up32 = prob.particular(torch.from_numpy(f).cuda(), "fp32").cpu().numpy()
     assert np.max(np.abs(up32 - ref)) <= 2e-6 * np.max(np.abs(ref))
+    upds = prob.particular(torch.from_numpy(f).cuda(), "df64").cpu().numpy()
+    assert np.max(np.abs(upds - ref)) <= 1e-12 * np.max(np.abs(ref))
     prob.close()
 
 
@@ -166,14 +170,16 @@ def test_apply_accepts_host_arrays(ctx):
     (lambda: W.torus_helmholtz(32, kappa2=10.0), "double"),
     (lambda: W.star(32), "double"),
 ])
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "df64", "mixed/fp64res"])
 def test_solve_matches_oracle(ctx, make, layer, precision):
     import torch
     P = make()
     prob = _problem(ctx, P, layer)
     ref = OS.solve(P.phi, P.grid.h, P.grid.origin, P.f(), P.g_at, P.kappa2, layer=layer, tol=1e-12)
     g = torch.from_numpy(P.g_at(prob.boundary_points())).cuda()
-    q, u, st = prob.solve(torch.from_numpy(P.f()).cuda(), g, tol=1e-10, precision=precision)
+    prec, _, res = precision.partition("/")
+    q, u, st = prob.solve(torch.from_numpy(P.f()).cuda(), g, tol=1e-10, precision=prec,
+                          residual_precision="fp64" if res == "fp64res" else None)
     u = u.cpu().numpy()
     q = q.cpu().numpy()
     # Algorithm 1's output is u on M+; u on gamma- (the rest of N+) is the
@@ -188,8 +194,33 @@ def test_solve_matches_oracle(ctx, make, layer, precision):
     assert e_np <= 1e-6 and e_q <= 1e-6, info
     assert np.all(u[~m] == 0)
     assert st["rel_residual"] <= 1e-10
-    if precision == "fp64":
+    if prec in ("fp64", "df64"):
         assert st["iterations"] <= ref.iterations + 2, info   # oracle ran to 1e-12
     else:
         assert st["applies_fp32"] > 0 and st["refinements"] >= 1
     prob.close()
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_fresh_context_graph_vs_plain_launches(precision):
+    # a context whose very first call is a solve (buffers sized before the
+    # Arnoldi step is captured), and the graph-replayed solve equals the
+    # kernel-by-kernel one bit for bit (same kernels, fixed-order reductions)
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2502_05507_gb300 import Context, Problem
+    P = W.torus_helmholtz(32, kappa2=10.0)
+    outs = []
+    for use_graphs in (True, False):
+        ctx = Context(0)
+        prob = Problem(ctx, torch.from_numpy(P.phi).cuda(), P.grid.h, P.grid.origin, P.kappa2, "double")
+        g = torch.from_numpy(P.g_at(prob.boundary_points())).cuda()
+        q, u, st = prob.solve(torch.from_numpy(P.f()).cuda(), g, tol=1e-10, precision=precision,
+                              use_graphs=use_graphs)
+        outs.append((q.cpu().numpy(), u.cpu().numpy(), st))
+        prob.close()
+        ctx.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
+    assert outs[0][2]["iterations"] == outs[1][2]["iterations"]
