@@ -388,6 +388,178 @@ def run_reference(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def _timed(fn, torch):
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    r = fn()
+    torch.cuda.synchronize()
+    return r, time.perf_counter() - t
+
+
+def run_sphere32(args):
+    """Poisson, sphere r=0.6, N=32, u=exp(x+y+z), double layer, float64."""
+    import torch
+    import workloads as W
+    from paper_2502_05507_gb300 import Context, Problem
+    P = W.sphere_exp(32)
+    ctx = Context(0)
+    torch.cuda.set_stream(ctx.stream)
+    phi, f = _problem_inputs(P, torch, 0)
+    pr0 = Problem(ctx, phi, P.grid.h, P.grid.origin, 0.0, "double")
+    g = torch.from_numpy(P.g_at(pr0.boundary_points())).cuda()
+    pr0.close()
+
+    def step():
+        pr = Problem(ctx, phi, P.grid.h, P.grid.origin, 0.0, "double")
+        out = pr.solve(f, g, tol=TOL, precision="fp64")
+        pr.close()
+        return out
+    for _ in range(args.warmup):
+        step()
+    ms = []
+    for _ in range(args.steps):
+        (q, u, st), dt = _timed(step, torch)
+        ms.append(dt * 1e3)
+    ms = np.array(ms)
+    u = u.cpu().numpy()
+    m = P.phi < 0
+    ctx.close()
+    return {"metric": METRIC, "value": 1e3 / ms.mean(), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms.mean(), "higher_is_better": True, "dtype": "f64",
+            "config": {"workload": "sphere r=0.6, Poisson, N=32 (h=1/16), u=exp(x+y+z), double layer, fp64, tol 1e-10"},
+            "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
+            "iterations": st["iterations"], "max_err_vs_exact": float(np.max(np.abs(u[m] - P.u_exact()[m])))}
+
+
+def run_batched64(args):
+    """64 right-hand sides u_k = exp(a_k . x) on the N=128 Poisson torus, one
+    batched mixed-precision solve per step."""
+    import torch
+    import workloads as W
+    from paper_2502_05507_gb300 import Context, Problem
+    dirs = W.torus_batch_dirs(64, seed=3)
+    probs = [W.torus_poisson_dir(128, a) for a in dirs]
+    ctx = Context(0)
+    torch.cuda.set_stream(ctx.stream)
+    P0 = probs[0]
+    phi = torch.from_numpy(P0.phi).cuda()
+    pr0 = Problem(ctx, phi, P0.grid.h, P0.grid.origin, 0.0, "double")
+    xs = pr0.boundary_points()
+    pr0.close()
+    f = torch.from_numpy(np.stack([P.f() for P in probs])).cuda()
+    g = torch.from_numpy(np.stack([P.g_at(xs) for P in probs])).cuda()
+
+    def step():
+        pr = Problem(ctx, phi, P0.grid.h, P0.grid.origin, 0.0, "double")
+        out = pr.solve_batched(f, g, tol=TOL, precision="mixed")
+        pr.close()
+        return out
+    for _ in range(max(1, args.warmup)):
+        step()
+    ms = []
+    for _ in range(args.steps):
+        (q, u, st), dt = _timed(step, torch)
+        ms.append(dt * 1e3)
+    ms = np.array(ms)
+    u = u.cpu().numpy()
+    m = P0.phi < 0
+    errs = [float(np.max(np.abs(u[k][m] - probs[k].u_exact()[m]))) for k in range(64)]
+    ctx.close()
+    return {"metric": METRIC, "value": 64e3 / ms.mean(), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms.mean(), "higher_is_better": True,
+            "dtype": "f32 conv + df64 refinement",
+            "config": {"workload": "64 RHS exp(a_k.x), Poisson torus R=0.5 r=0.2, N=128, one batched solve per step"},
+            "iterations_max": max(s_["iterations"] for s_ in st), "rel_residual_max": max(s_["rel_residual"] for s_ in st),
+            "max_err_vs_exact": max(errs)}
+
+
+def run_star256(args):
+    """N=256 star, kappa^2 in {0, 1, 100}, double vs single layer: GMRES
+    iterations and solves/s (mixed precision)."""
+    import torch
+    import workloads as W
+    from paper_2502_05507_gb300 import Context, Problem
+    ctx = Context(0)
+    torch.cuda.set_stream(ctx.stream)
+    rows = []
+    for k2 in (0.0, 1.0, 100.0):
+        for layer in ("double", "single"):
+            P = W.star(256, kappa2=k2, layer=layer)
+            phi, f = _problem_inputs(P, torch, 0)
+            pr0 = Problem(ctx, phi, P.grid.h, P.grid.origin, k2, layer)
+            g = torch.from_numpy(P.g_at(pr0.boundary_points())).cuda()
+            n_gm = pr0.n_gm
+            pr0.close()
+
+            def step():
+                pr = Problem(ctx, phi, P.grid.h, P.grid.origin, k2, layer)
+                out = pr.solve(f, g, tol=TOL, precision="mixed", max_iter=2000, restart=400)
+                pr.close()
+                return out
+            step()
+            (q, u, st), dt = _timed(step, torch)
+            uu = u.cpu().numpy()
+            m = P.phi < 0
+            rows.append({"kappa2": k2, "layer": layer, "iterations": st["iterations"], "solves_per_s": 1.0 / dt,
+                         "rel_residual": st["rel_residual"], "n_gm": n_gm,
+                         "max_err_vs_exact": float(np.max(np.abs(uu[m] - P.u_exact()[m])))})
+    ctx.close()
+    return {"metric": METRIC, "value": float(np.mean([r["solves_per_s"] for r in rows])), "unit": UNIT,
+            "n_gpus": 1, "higher_is_better": True, "dtype": "f32 conv + df64 refinement",
+            "config": {"workload": "star r=0.6+0.1 sin5t cos3p, N=256, kappa^2 in {0,1,100}, double vs single layer"},
+            "table": rows}
+
+
+def run_serving(args):
+    """Serving trace: requests with N in {32,64,128,256}, kappa^2 in {0,10},
+    random spheres/ellipsoids/tori, u = exp(a.x); Poisson arrivals at 0.8x
+    the measured saturation throughput; p50/p99 latency and solves/s."""
+    import torch
+    import workloads as W
+    from paper_2502_05507_gb300 import Server
+    nreq = args.requests
+    reqs = W.serving_trace(nreq, seed=5)
+    probs = [W.trace_problem(r) for r in reqs]
+    srv = Server(0, slots=args.slots, hbm_budget_bytes=int(args.hbm_gb * (1 << 30)))
+    # warm the spectrum cache and the slots, then measure saturation throughput
+    warm = [srv.submit(P.phi, P.grid.h, P.grid.origin, P.f(), P.g_at, kappa2=P.kappa2) for P in probs[:32]]
+    for t in warm:
+        srv.poll(t)
+        srv.release(t)
+    t0 = time.perf_counter()
+    sat = [srv.submit(P.phi, P.grid.h, P.grid.origin, P.f(), P.g_at, kappa2=P.kappa2) for P in probs[32:96]]
+    for t in sat:
+        srv.poll(t)
+        srv.release(t)
+    sat_rate = len(sat) / (time.perf_counter() - t0)
+    lam = 0.8 * sat_rate
+    rng = np.random.default_rng(55)
+    gaps = rng.exponential(1.0 / lam, size=nreq)
+    tickets, arrive = [], []
+    start = time.perf_counter()
+    tnext = start
+    for P, gap in zip(probs, gaps):
+        tnext += gap
+        d = tnext - time.perf_counter()
+        if d > 0:
+            time.sleep(d)
+        arrive.append(srv.clock())
+        tickets.append(srv.submit(P.phi, P.grid.h, P.grid.origin, P.f(), P.g_at, kappa2=P.kappa2))
+    res = [srv.poll(t) for t in tickets]
+    wall = time.perf_counter() - start
+    lat = np.array([(r["t_done"] - a) * 1e3 for r, a in zip(res, arrive)])
+    ok = sum(1 for r in res if r["status"] == 0)
+    srv.close()
+    return {"metric": METRIC, "value": ok / wall, "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+            "dtype": "f32 conv + df64 refinement",
+            "config": {"workload": f"serving trace, {nreq} Poisson-arrival requests, N in {{32,64,128,256}}, "
+                                   f"kappa^2 in {{0,10}}, spheres/ellipsoids/tori", "slots": args.slots,
+                       "arrival_rate_per_s": lam, "saturation_solves_per_s": sat_rate},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(lat.max())},
+            "completed": ok, "requests": nreq}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -396,6 +568,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--workload", default="torus128",
+                    choices=["torus128", "sphere32", "batched64", "star256", "serving"])
+    ap.add_argument("--requests", type=int, default=2000, help="serving: number of requests")
+    ap.add_argument("--slots", type=int, default=6, help="serving: concurrent slots")
+    ap.add_argument("--hbm-gb", type=float, default=96.0, help="serving: device-memory budget")
     ap.add_argument("--only-timed", action="store_true",
                     help="warm-up and timed steps only (no profile, fp64 comparison, e2e or CPU baseline)")
     args = ap.parse_args()
@@ -407,6 +584,12 @@ def main():
             print(json.dumps(run_reference(args)))
         return
     import torch
+    extra = {"sphere32": run_sphere32, "batched64": run_batched64, "star256": run_star256,
+             "serving": run_serving}
+    if args.workload in extra:
+        if rank == 0:
+            print(json.dumps(extra[args.workload](args)))
+        return
     if world > 1:
         torch.cuda.set_device(local)
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))

@@ -247,6 +247,62 @@ int bae_solve(bae_problem* prob, const double* f, const double* g, const bae_opt
 int bae_solve_batched(bae_problem* prob, int nrhs, const double* f, const double* g,
                       const bae_options* opts, double* density, double* u, bae_stats* stats);
 
+/* ---------------------------------------------------------------- serving */
+
+/* A solve server: a host scheduler admits submitted requests into one of
+ * `slots` concurrent slots (each a context with its own CUDA stream and work
+ * space) when a slot is free and the request's device-memory estimate fits
+ * in hbm_budget_bytes next to the requests in flight; work of different
+ * slots overlaps on the device. Requests of any N, kappa2, geometry and
+ * layer mix freely; LGF spectra are cached on the device per
+ * (N, kappa2 h^2) and shared by all slots; Krylov state stays on the
+ * device. A request's result does not depend on what else is in flight. */
+typedef struct bae_server bae_server;
+
+/* Called on a server thread once the request is classified: fill g[r] with
+ * the Dirichlet data at xyz[3r..3r+2] (host arrays, n points). */
+typedef void (*bae_boundary_fn)(const double* xyz, int64_t n, double* g, void* user);
+
+typedef struct bae_request {
+    int N;                       /* as bae_problem_create                        */
+    double h;
+    double origin[3];
+    const double* phi;           /* N^3, host or device; valid until done        */
+    double kappa2;
+    int layer;
+    const double* f;             /* N^3, host or device; valid until done        */
+    bae_boundary_fn boundary;    /* Dirichlet data at the boundary points        */
+    void* user;                  /* passed to boundary                           */
+    double* u_out;               /* N^3 output, host or device (or NULL)         */
+    bae_options opts;            /* solve options                                */
+} bae_request;
+
+typedef struct bae_result {
+    int status;                  /* BAE_OK or the solve's error code            */
+    int64_t n_gm;                /* length of the density                       */
+    bae_stats stats;
+    double t_submit, t_admit, t_done;  /* seconds on the server's steady clock   */
+} bae_result;
+
+#define BAE_PENDING 7            /* bae_server_poll: not finished yet          */
+
+int bae_server_create(int device, int slots, int64_t hbm_budget_bytes, bae_server** out);
+/* Queues a request (copied; the arrays it points to must stay valid until
+ * the request is done). *ticket identifies it. */
+int bae_server_submit(bae_server* srv, const bae_request* req, int64_t* ticket);
+/* Waits up to timeout_ms (0: no wait, < 0: forever) for the request; returns
+ * BAE_OK with *out filled when it is done, BAE_PENDING otherwise. */
+int bae_server_poll(bae_server* srv, int64_t ticket, int timeout_ms, bae_result* out);
+/* Copies the finished request's density (n_gm doubles) to out (host or
+ * device, capacity doubles). */
+int bae_server_density(bae_server* srv, int64_t ticket, double* out, int64_t capacity);
+/* Forgets a finished request. */
+int bae_server_release(bae_server* srv, int64_t ticket);
+/* Seconds on the server's steady clock (the time base of bae_result). */
+double bae_server_clock(bae_server* srv);
+/* Finishes the requests in flight, drops the queued ones, frees everything. */
+void bae_server_destroy(bae_server* srv);
+
 #ifdef __cplusplus
 }
 #endif

@@ -51,6 +51,23 @@ class Stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+BOUNDARY_FN = ctypes.CFUNCTYPE(None, ctypes.POINTER(ctypes.c_double), ctypes.c_int64,
+                               ctypes.POINTER(ctypes.c_double), ctypes.c_void_p)
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("h", ctypes.c_double), ("origin", ctypes.c_double * 3),
+                ("phi", ctypes.c_void_p), ("kappa2", ctypes.c_double), ("layer", ctypes.c_int),
+                ("f", ctypes.c_void_p), ("boundary", BOUNDARY_FN), ("user", ctypes.c_void_p),
+                ("u_out", ctypes.c_void_p), ("opts", Options)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("n_gm", ctypes.c_int64), ("stats", Stats),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+PENDING = 7
 _lib = None
 _P = ctypes.c_void_p
 _D = ctypes.c_double
@@ -86,6 +103,13 @@ def lib():
             "bae_particular": (_I, [_P, _I, _P, _P]),
             "bae_solve": (_I, [_P, _P, _P, _P, _P, _P, _P]),
             "bae_solve_batched": (_I, [_P, _I, _P, _P, _P, _P, _P, _P]),
+            "bae_server_create": (_I, [_I, _I, ctypes.c_int64, _P]),
+            "bae_server_submit": (_I, [_P, _P, _P]),
+            "bae_server_poll": (_I, [_P, ctypes.c_int64, _I, _P]),
+            "bae_server_density": (_I, [_P, ctypes.c_int64, _P, ctypes.c_int64]),
+            "bae_server_release": (_I, [_P, ctypes.c_int64]),
+            "bae_server_clock": (_D, [_P]),
+            "bae_server_destroy": (None, [_P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -100,7 +124,9 @@ EXPORTED = ["bae_version", "bae_last_error", "bae_default_options", "bae_launch_
             "bae_lgf_table", "bae_lgf_spectrum", "bae_problem_create", "bae_problem_destroy",
             "bae_problem_sizes", "bae_boundary_points", "bae_classification", "bae_potential_apply",
             "bae_potential_apply_noalloc",
-            "bae_boundary_apply", "bae_particular", "bae_solve", "bae_solve_batched"]
+            "bae_boundary_apply", "bae_particular", "bae_solve", "bae_solve_batched", "bae_server_create",
+            "bae_server_submit", "bae_server_poll", "bae_server_density", "bae_server_release", "bae_server_clock",
+            "bae_server_destroy"]
 
 
 def _check(rc: int, allow_not_converged=False):
@@ -325,3 +351,91 @@ class Problem:
                                      st)
         _check(rc, allow_not_converged)
         return density, u, [s.as_dict() for s in st]
+
+
+class Server:
+    """bae_server: continuous admission of solves into concurrent slots.
+    Arrays passed to submit() are kept alive here until release()."""
+
+    def __init__(self, device: int = 0, slots: int = 4, hbm_budget_bytes: int = 64 << 30):
+        self._h = ctypes.c_void_p()
+        _check(lib().bae_server_create(device, slots, int(hbm_budget_bytes), ctypes.byref(self._h)))
+        self._live = {}
+
+    def close(self):
+        if self._h:
+            lib().bae_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def clock(self) -> float:
+        return float(lib().bae_server_clock(self._h))
+
+    def submit(self, phi, h, origin, f, g_fn, kappa2=0.0, layer="double", u_out=None, tol=1e-10,
+               precision="mixed", **opts) -> int:
+        """g_fn(xyz (n,3) numpy) -> g (n,) numpy, called on a server thread."""
+        phi = _as_f64(phi)
+        f = _as_f64(f)
+        N = int(phi.shape[0])
+        if u_out is None:
+            u_out = _new((N,) * 3, np.float64, f)
+
+        def cb(xyz_p, n, g_p, _user):
+            try:
+                xyz = np.ctypeslib.as_array(xyz_p, shape=(int(n) * 3,)).reshape(-1, 3)
+                gv = np.asarray(g_fn(xyz), dtype=np.float64).reshape(-1)
+                np.ctypeslib.as_array(g_p, shape=(int(n),))[:] = gv
+            except Exception as e:  # keep the server thread alive; g stays 0
+                print("boundary callback failed:", e)
+
+        fn = BOUNDARY_FN(cb)
+        rq = Request()
+        rq.N = N
+        rq.h = float(h)
+        o = np.array(origin if np.ndim(origin) else [origin] * 3, dtype=np.float64)
+        for i in range(3):
+            rq.origin[i] = o[i]
+        rq.phi = _ptr(phi)
+        rq.kappa2 = float(kappa2)
+        rq.layer = _LAYERS[layer]
+        rq.f = _ptr(f)
+        rq.boundary = fn
+        rq.user = None
+        rq.u_out = _ptr(u_out)
+        lib().bae_default_options(ctypes.byref(rq.opts))
+        rq.opts.tol = tol
+        rq.opts.precision = _PREC[precision]
+        for k, v in opts.items():
+            setattr(rq.opts, k, _PREC[v] if k == "residual_precision" else v)
+        ticket = ctypes.c_int64()
+        _check(lib().bae_server_submit(self._h, ctypes.byref(rq), ctypes.byref(ticket)))
+        self._live[ticket.value] = (phi, f, u_out, fn, rq)
+        return ticket.value
+
+    def poll(self, ticket: int, timeout_ms: int = -1):
+        """Result dict when done (timeout_ms < 0 waits), else None."""
+        res = Result()
+        rc = lib().bae_server_poll(self._h, ticket, timeout_ms, ctypes.byref(res))
+        if rc == PENDING:
+            return None
+        _check(rc)
+        d = {k: getattr(res, k) for k, _ in Result._fields_ if k != "stats"}
+        d["stats"] = res.stats.as_dict()
+        d["u"] = self._live[ticket][2]
+        return d
+
+    def density(self, ticket: int):
+        n = self.poll(ticket, 0)["n_gm"]
+        out = np.empty(n)
+        _check(lib().bae_server_density(self._h, ticket, out.ctypes.data, n))
+        return out
+
+    def release(self, ticket: int):
+        _check(lib().bae_server_release(self._h, ticket))
+        self._live.pop(ticket, None)

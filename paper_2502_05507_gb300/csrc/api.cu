@@ -284,6 +284,8 @@ struct bae_problem {
 
 namespace bae {
 
+void ctx_share_cache(bae_ctx* dst, const bae_ctx* src) { dst->cache = src->cache; }
+
 bool problem_view(const bae_problem* P, ProblemView& out) {
     if (!P || !P->spec) return false;
     out.device = P->ctx->device;
@@ -436,7 +438,7 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
     a.n = n;
     a.nb = nb;
     a.m = m;
-    a.nchunk = krylov_chunks(n);
+    a.nchunk = arnoldi_chunks(n);
     a.V = ws.V.need((long long)nb * (m + 1) * n);
     a.w = ws.w.need((long long)nb * n);
     a.part = ws.partial.need((long long)nb * (m + 2) * a.nchunk);
@@ -452,7 +454,7 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
     a.target = scal + nb;
     a.inv = scal + 2 * nb;
     double* nrm2 = scal + 3 * nb;
-    int* ibuf = ws.arnI.need((long long)nb * 3 + 1);
+    int* ibuf = ws.arnI.need((long long)nb * 4);
     a.flag = ibuf;
     a.ncols = ibuf + nb;
     int* member = ibuf + 2 * nb;
@@ -460,7 +462,7 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
     a.ctr = reinterpret_cast<unsigned int*>(ws.arnCtr.need((long long)nb * 3));
     double* r = ws.r.need((long long)nb * n);
     double* tmp = ws.tmp.need((long long)nb * n);
-    double* npart = ws.n2.need((long long)nb * a.nchunk + nb);
+    double* npart = ws.n2.need((long long)nb * krylov_chunks(n) + nb);
     int* d_all = ws.active.need(nb);
 
     std::vector<int> all(nb), mem(nb, 0);
@@ -517,7 +519,7 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
                 for (int b = 0; b < nb; ++b) applies[b] += mem[b];
                 kr_sub(rhs, tmp, d_all, nb, n, r, st);
             }
-            kr_norm2(r, d_all, nb, n, npart + nb, a.nchunk, npart, st);
+            kr_norm2(r, d_all, nb, n, npart + nb, krylov_chunks(n), npart, st);
             arn_init(a, r, npart, member, st);
             const int steps = std::min(m, iters_left);
             int launched = 0;

@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(Geo<T, L>::KT) k_kpass_fwd(ConvArgs<T> a) {
         for (int k = t; k < 2 * N; k += R1) r[k] = (T)0;
         __syncthreads();
         if (active) {
-            const double* q = a.q + (long long)b * a.q_stride + (a.q_row ? (long long)(*a.q_row) * a.q_row_stride : 0);
+            const double* q = a.q + (long long)b * a.q_stride + (a.q_row ? (long long)a.q_row[b] * a.q_row_stride : 0);
 #pragma unroll
             for (int half = 0; half < 2; ++half) {
                 const long long l = half ? lb : la;

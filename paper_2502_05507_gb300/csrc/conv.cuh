@@ -25,8 +25,8 @@ struct ConvArgs {
     int nbatch = 1;
     SourceMode mode = SRC_DENSITY;
     // SRC_DENSITY: q [nbatch][q_stride] float64 density on gamma-; when q_row
-    // is set, batch item b reads q + b q_stride + (*q_row) q_row_stride (the
-    // row index lives in device memory, so a captured graph can advance it)
+    // is set, batch item b reads q + b q_stride + q_row[b] q_row_stride (the
+    // row indices live in device memory, so a captured graph can advance them)
     const double* q = nullptr;
     long long q_stride = 0;
     const int* q_row = nullptr;

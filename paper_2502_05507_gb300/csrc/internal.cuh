@@ -22,4 +22,7 @@ struct ProblemView {
 // Fills `out` from a problem handle (no device work, no allocation).
 bool problem_view(const bae_problem* P, ProblemView& out);
 
+// Makes dst use src's LGF spectrum cache (contexts of one server share it).
+void ctx_share_cache(bae_ctx* dst, const bae_ctx* src);
+
 }  // namespace bae

@@ -120,8 +120,8 @@ __global__ void k_arn_init(Arnoldi a, const double* __restrict__ nrm2, const int
         a.flag[b] = go ? 1 : 0;
         a.inv[b] = beta > 0.0 ? 1.0 / beta : 0.0;
         a.ncols[b] = 0;
+        a.j[b] = 0;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) *a.j = 0;
 }
 
 __global__ void k_arn_row0(Arnoldi a, const double* __restrict__ r) {
@@ -133,34 +133,87 @@ __global__ void k_arn_row0(Arnoldi a, const double* __restrict__ r) {
         v[i] = r[(long long)b * a.n + i] * s;
 }
 
+constexpr int ACH = 64;   // vector elements per CTA in the Arnoldi passes
+
+// sum over chunks of part[i][*] for rows i < cols, one warp per row, each
+// lane a fixed stride of chunks, then a fixed shuffle tree
+__device__ __forceinline__ void reduce_rows(const double* part, int nch, int cols, double* out, double* out2,
+                                            const double* add) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = warp; i < cols; i += nw) {
+        double acc = 0.0;
+        for (int c = lane; c < nch; c += 32) acc += __ldcg(part + (long long)i * nch + c);
+        acc = warp_sum(acc);
+        if (lane == 0) {
+            if (add) out[i] = add[i] + acc; else out[i] = acc;
+            if (out2) out2[i] = acc;
+        }
+    }
+}
+
+// w[r0 .. r0+ACH) -= V[0..cols) h over the chunk; 8 warps split the rows,
+// partial sums combined in warp order. Leaves the new chunk in s_w.
+__device__ __forceinline__ void chunk_update(const double* Vb, long long n, long long r0, int cols, const double* s_h,
+                                             double* w, double* s_acc, double* s_w) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long ra = r0 + lane, rb = r0 + lane + 32;
+    double a0 = 0.0, a1 = 0.0;
+    for (int i = warp; i < cols; i += 8) {
+        const double* v = Vb + (long long)i * n;
+        const double hi = s_h[i];
+        if (ra < n) a0 += v[ra] * hi;
+        if (rb < n) a1 += v[rb] * hi;
+    }
+    s_acc[warp * ACH + lane] = a0;
+    s_acc[warp * ACH + lane + 32] = a1;
+    __syncthreads();
+    if (threadIdx.x < ACH) {
+        const long long r = r0 + threadIdx.x;
+        double sub = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) sub += s_acc[q * ACH + threadIdx.x];
+        double val = 0.0;
+        if (r < n) {
+            val = w[r] - sub;
+            w[r] = val;
+        }
+        s_w[threadIdx.x] = val;
+    }
+    __syncthreads();
+}
+
+// partial dots of the chunk against rows i < cols: part[i][c]
+__device__ __forceinline__ void chunk_dots(const double* Vb, long long n, long long r0, int cols, const double* s_w,
+                                           double* part, int nch, int c) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long ra = r0 + lane, rb = r0 + lane + 32;
+    for (int i = warp; i < cols; i += 8) {
+        const double* v = Vb + (long long)i * n;
+        double acc = 0.0;
+        if (ra < n) acc += v[ra] * s_w[lane];
+        if (rb < n) acc += v[rb] * s_w[lane + 32];
+        acc = warp_sum(acc);
+        if (lane == 0) part[(long long)i * nch + c] = acc;
+    }
+}
+
 // pass 1: h1 = V^T w over rows i <= j
 __global__ void __launch_bounds__(256) k_arn_dots(Arnoldi a) {
-    __shared__ double s_w[CH];
+    __shared__ double s_w[ACH];
     __shared__ int s_last;
     const int b = blockIdx.y;
     if (!a.flag[b]) return;
-    const int cols = *a.j + 1;
+    const int cols = a.j[b] + 1;
     const int c = blockIdx.x;
-    const long long r0 = (long long)c * CH;
+    const long long r0 = (long long)c * ACH;
     const double* w = a.w + (long long)b * a.n;
-    for (int e = threadIdx.x; e < CH; e += blockDim.x) s_w[e] = (r0 + e < a.n) ? w[r0 + e] : 0.0;
+    if (threadIdx.x < ACH) s_w[threadIdx.x] = (r0 + threadIdx.x < a.n) ? w[r0 + threadIdx.x] : 0.0;
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double* part = a.part + (long long)b * (a.m + 2) * a.nchunk;
-    for (int i = warp; i < cols; i += 8) {
-        const double* v = a.V + ((long long)b * (a.m + 1) + i) * a.n;
-        double acc = 0.0;
-        for (int e = lane; e < CH; e += 32)
-            if (r0 + e < a.n) acc += v[r0 + e] * s_w[e];
-        acc = warp_sum(acc);
-        if (lane == 0) part[(long long)i * a.nchunk + c] = acc;
-    }
+    const double* Vb = a.V + (long long)b * (a.m + 1) * a.n;
+    chunk_dots(Vb, a.n, r0, cols, s_w, part, a.nchunk, c);
     if (last_block(a.ctr + 3 * b + 0, gridDim.x, &s_last)) {
-        for (int i = threadIdx.x; i < cols; i += blockDim.x) {
-            double s = 0.0;
-            for (int q = 0; q < a.nchunk; ++q) s += __ldcg(part + (long long)i * a.nchunk + q);
-            a.h1[(long long)b * (a.m + 1) + i] = s;
-        }
+        reduce_rows(part, a.nchunk, cols, a.h1 + (long long)b * (a.m + 1), nullptr, nullptr);
         if (threadIdx.x == 0) a.ctr[3 * b + 0] = 0;
     }
 }
@@ -168,93 +221,65 @@ __global__ void __launch_bounds__(256) k_arn_dots(Arnoldi a) {
 // pass 2: w -= V h1, then h2 = V^T w; hcol = h1 + h2, h1 <- h2
 __global__ void __launch_bounds__(256) k_arn_update_dots(Arnoldi a) {
     extern __shared__ double s_dyn[];
-    double* s_h = s_dyn;             // m + 1
-    double* s_w = s_dyn + (a.m + 1); // CH
+    double* s_h = s_dyn;                 // m + 1
+    __shared__ double s_acc[8 * ACH];
+    __shared__ double s_w[ACH];
     __shared__ int s_last;
     const int b = blockIdx.y;
     if (!a.flag[b]) return;
-    const int cols = *a.j + 1;
+    const int cols = a.j[b] + 1;
     const int c = blockIdx.x;
-    const long long r0 = (long long)c * CH;
-    double* w = a.w + (long long)b * a.n;
-    const double* h1 = a.h1 + (long long)b * (a.m + 1);
+    const long long r0 = (long long)c * ACH;
+    double* h1 = a.h1 + (long long)b * (a.m + 1);
     for (int i = threadIdx.x; i < cols; i += blockDim.x) s_h[i] = h1[i];
     __syncthreads();
     const double* Vb = a.V + (long long)b * (a.m + 1) * a.n;
-    for (int e = threadIdx.x; e < CH; e += blockDim.x) {
-        const long long r = r0 + e;
-        double acc = 0.0;
-        if (r < a.n) {
-            acc = w[r];
-            for (int i = 0; i < cols; ++i) acc -= Vb[(long long)i * a.n + r] * s_h[i];
-            w[r] = acc;
-        }
-        s_w[e] = acc;
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    chunk_update(Vb, a.n, r0, cols, s_h, a.w + (long long)b * a.n, s_acc, s_w);
     double* part = a.part + (long long)b * (a.m + 2) * a.nchunk;
-    for (int i = warp; i < cols; i += 8) {
-        const double* v = Vb + (long long)i * a.n;
-        double acc = 0.0;
-        for (int e = lane; e < CH; e += 32)
-            if (r0 + e < a.n) acc += v[r0 + e] * s_w[e];
-        acc = warp_sum(acc);
-        if (lane == 0) part[(long long)i * a.nchunk + c] = acc;
-    }
+    chunk_dots(Vb, a.n, r0, cols, s_w, part, a.nchunk, c);
     if (last_block(a.ctr + 3 * b + 1, gridDim.x, &s_last)) {
-        for (int i = threadIdx.x; i < cols; i += blockDim.x) {
-            double s = 0.0;
-            for (int q = 0; q < a.nchunk; ++q) s += __ldcg(part + (long long)i * a.nchunk + q);
-            a.hcol[(long long)b * (a.m + 1) + i] = s_h[i] + s;
-            a.h1[(long long)b * (a.m + 1) + i] = s;
-        }
+        // hcol = h1 + h2 (h1 still in s_h), then h1 <- h2
+        reduce_rows(part, a.nchunk, cols, a.hcol + (long long)b * (a.m + 1), h1, s_h);
         if (threadIdx.x == 0) a.ctr[3 * b + 1] = 0;
     }
 }
 
 // pass 3: w -= V h2, ||w||; the last block applies the Givens rotations,
-// updates the residual estimate and the flags
+// updates the residual estimate and the flag, and advances j
 __global__ void __launch_bounds__(256) k_arn_update_norm(Arnoldi a) {
     extern __shared__ double s_dyn[];
     double* s_h = s_dyn;
-    __shared__ double s_red[8];
+    __shared__ double s_acc[8 * ACH];
+    __shared__ double s_w[ACH];
     __shared__ int s_last;
     const int b = blockIdx.y;
     if (!a.flag[b]) return;
-    const int j = *a.j;
+    const int j = a.j[b];
     const int cols = j + 1;
     const int c = blockIdx.x;
-    const long long r0 = (long long)c * CH;
-    double* w = a.w + (long long)b * a.n;
+    const long long r0 = (long long)c * ACH;
     const double* h2 = a.h1 + (long long)b * (a.m + 1);
     for (int i = threadIdx.x; i < cols; i += blockDim.x) s_h[i] = h2[i];
     __syncthreads();
     const double* Vb = a.V + (long long)b * (a.m + 1) * a.n;
-    double nrm = 0.0;
-    for (int e = threadIdx.x; e < CH; e += blockDim.x) {
-        const long long r = r0 + e;
-        if (r < a.n) {
-            double acc = w[r];
-            for (int i = 0; i < cols; ++i) acc -= Vb[(long long)i * a.n + r] * s_h[i];
-            w[r] = acc;
-            nrm += acc * acc;
-        }
-    }
-    nrm = warp_sum(nrm);
-    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = nrm;
-    __syncthreads();
+    chunk_update(Vb, a.n, r0, cols, s_h, a.w + (long long)b * a.n, s_acc, s_w);
     double* part = a.part + (long long)b * (a.m + 2) * a.nchunk;
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += s_red[q];
-        part[(long long)(a.m + 1) * a.nchunk + c] = s;
+    if (threadIdx.x < 32) {
+        double acc = s_w[threadIdx.x] * s_w[threadIdx.x] + s_w[threadIdx.x + 32] * s_w[threadIdx.x + 32];
+        acc = warp_sum(acc);
+        if (threadIdx.x == 0) part[(long long)(a.m + 1) * a.nchunk + c] = acc;
     }
     if (last_block(a.ctr + 3 * b + 2, gridDim.x, &s_last)) {
+        __shared__ double s_n2;
+        if (threadIdx.x < 32) {
+            double acc = 0.0;
+            for (int q = threadIdx.x; q < a.nchunk; q += 32) acc += __ldcg(part + (long long)(a.m + 1) * a.nchunk + q);
+            acc = warp_sum(acc);
+            if (threadIdx.x == 0) s_n2 = acc;
+        }
+        __syncthreads();
         if (threadIdx.x == 0) {
-            double n2 = 0.0;
-            for (int q = 0; q < a.nchunk; ++q) n2 += __ldcg(part + (long long)(a.m + 1) * a.nchunk + q);
-            const double hn = sqrt(n2);
+            const double hn = sqrt(s_n2);
             const int m = a.m;
             double* col = a.H + ((long long)b * m + j) * (m + 1);
             const double* hc = a.hcol + (long long)b * (m + 1);
@@ -282,24 +307,22 @@ __global__ void __launch_bounds__(256) k_arn_update_norm(Arnoldi a) {
             a.ncols[b] = j + 1;
             a.inv[b] = hn > 0.0 ? 1.0 / hn : 0.0;
             a.flag[b] = (e > a.target[b] && hn > 0.0 && j + 1 < m) ? 1 : 0;
+            a.j[b] = j + 1;   // every block of this RHS has read j already
             a.ctr[3 * b + 2] = 0;
         }
     }
 }
 
+// V[b][j] = w[b] / ||w[b]|| (j already advanced)
 __global__ void k_arn_next(Arnoldi a) {
     const int b = blockIdx.y;
     if (!a.flag[b]) return;
-    const int j = *a.j;
+    const int j = a.j[b];
     const double s = a.inv[b];
     const double* w = a.w + (long long)b * a.n;
-    double* v = a.V + ((long long)b * (a.m + 1) + j + 1) * a.n;
+    double* v = a.V + ((long long)b * (a.m + 1) + j) * a.n;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.n; i += (long long)gridDim.x * blockDim.x)
         v[i] = w[i] * s;
-}
-
-__global__ void k_arn_advance(Arnoldi a) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) *a.j += 1;
 }
 
 // y = R^{-1} g, one warp per RHS (column-oriented back substitution)
@@ -333,13 +356,14 @@ void arn_init(const Arnoldi& a, const double* r, const double* nrm2, const int* 
     BAE_LAUNCH("k_arn_row0", st, k_arn_row0<<<dim3(blocks_for(a.n), a.nb), 256, 0, st>>>(a, r));
 }
 
+int arnoldi_chunks(int n) { return ceil_div(n, ACH); }
+
 void arn_step(const Arnoldi& a, cudaStream_t st) {
-    const size_t sh = (size_t)(a.m + 1 + CH) * sizeof(double);
+    const size_t sh = (size_t)(a.m + 1) * sizeof(double);
     BAE_LAUNCH("k_arn_dots", st, k_arn_dots<<<dim3(a.nchunk, a.nb), 256, 0, st>>>(a));
     BAE_LAUNCH("k_arn_update_dots", st, k_arn_update_dots<<<dim3(a.nchunk, a.nb), 256, sh, st>>>(a));
-    BAE_LAUNCH("k_arn_update_norm", st, k_arn_update_norm<<<dim3(a.nchunk, a.nb), 256, (a.m + 1) * sizeof(double), st>>>(a));
+    BAE_LAUNCH("k_arn_update_norm", st, k_arn_update_norm<<<dim3(a.nchunk, a.nb), 256, sh, st>>>(a));
     BAE_LAUNCH("k_arn_next", st, k_arn_next<<<dim3(blocks_for(a.n), a.nb), 256, 0, st>>>(a));
-    BAE_LAUNCH("k_arn_advance", st, k_arn_advance<<<1, 32, 0, st>>>(a));
 }
 
 void arn_finish(const Arnoldi& a, double* x, int maxcols, cudaStream_t st) {

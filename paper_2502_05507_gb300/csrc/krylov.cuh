@@ -46,13 +46,16 @@ struct Arnoldi {
     int* flag = nullptr;        // [nb] 1 while the RHS is iterating in this cycle
     int* ncols = nullptr;       // [nb] basis vectors used this cycle
     unsigned int* ctr = nullptr;  // [nb][3] last-block counters (self-resetting)
-    int* j = nullptr;           // current step (one device int)
+    int* j = nullptr;           // [nb] current step of each RHS
 };
+
+// number of vector chunks (CTAs per RHS) of the Arnoldi passes
+int arnoldi_chunks(int n);
 
 // Start of a cycle: r [nb][n] residuals with squared norms nrm2[b]; RHS with
 // member[b] != 0 and sqrt(nrm2) > target start iterating (V[b][0] = r/beta).
 void arn_init(const Arnoldi& a, const double* r, const double* nrm2, const int* member, cudaStream_t st);
-// One Arnoldi step after w = A V[j] (CGS2, Givens, next basis vector, j++).
+// One Arnoldi step after w = A V[j] (CGS2, Givens, j++, next basis vector).
 void arn_step(const Arnoldi& a, cudaStream_t st);
 // End of a cycle: y = R^{-1} g for every RHS with ncols > 0, x += V y.
 void arn_finish(const Arnoldi& a, double* x, int maxcols, cudaStream_t st);
