@@ -116,6 +116,9 @@ def kernel_model(n, pb, n_gm):
         "conv_i": (2 * B + n1 ** 3 * pb, 2 * (2 * n * n1) * F + 2.0 * (2 * n * n1) * L),
         "conv_jinv": (A + B, n * n1 * F),
         "conv_kinv": (A + n ** 3 * pb, (n * n / 2) * F),
+        # k and j fused per plane: A stays in shared memory
+        "conv_plane_fwd": (B + src, (n * n / 2) * F + n * n1 * F),
+        "conv_plane_inv": (B + n ** 3 * pb, (n * n / 2) * F + n * n1 * F),
     }
 
 
@@ -257,14 +260,17 @@ def run_ours(args, rank, world, dev):
     # the float32 i-pass (forward FFT, ghat multiply, inverse FFT) inside the timed region
     if "conv_i.f32" in prof:
         out["conv_f32_roofline"] = roofline_for("conv_i.f32", *prof["conv_i.f32"], n_gm, hbm, hbm_kind)
-    # whole float32 apply: algorithmic bytes of the five passes / their summed time
-    per = [prof.get(k) for k in ("conv_kfwd.f32", "conv_jfwd.f32", "conv_i.f32", "conv_jinv.f32", "conv_kinv.f32")]
-    if all(per):
+    # whole float32 apply: algorithmic bytes of the passes that ran / their
+    # summed time per apply (either schedule the autotuner picked)
+    if "conv_i.f32" in prof:
+        napp = prof["conv_i.f32"][1]
         m = kernel_model(N, 4, n_gm)
-        nb = sum(v[0] for v in m.values())
-        t_apply = sum(p[0] / p[1] for p in per) / 1000.0
-        out["conv_f32_apply"] = {"us": t_apply * 1e6, "algorithmic_bytes": nb, "GBps": nb / t_apply / 1e9,
-                                 "frac_hbm": nb / t_apply / 1e9 / hbm,
+        names = [k for k in prof if k.startswith("conv_") and k.endswith(".f32")]
+        nbytes = sum(m[k.split(".")[0]][0] * prof[k][1] / napp for k in names)
+        t_apply = sum(prof[k][0] for k in names) / napp / 1000.0
+        out["conv_f32_apply"] = {"us": t_apply * 1e6, "passes": sorted(k.split(".")[0] for k in names),
+                                 "algorithmic_bytes": nbytes, "GBps": nbytes / t_apply / 1e9,
+                                 "frac_hbm": nbytes / t_apply / 1e9 / hbm,
                                  "note": "N=128 buffers fit in the 129 MB L2, so this can exceed HBM peak"}
 
     # ------------------------------------- other arithmetics, for comparison
@@ -437,7 +443,8 @@ def run_batched64(args):
     import torch
     import workloads as W
     from paper_2502_05507_gb300 import Context, Problem
-    dirs = W.torus_batch_dirs(64, seed=3)
+    nrhs = args.nrhs
+    dirs = W.torus_batch_dirs(64, seed=3)[:nrhs]
     probs = [W.torus_poisson_dir(128, a) for a in dirs]
     ctx = Context(0)
     torch.cuda.set_stream(ctx.stream)
@@ -463,12 +470,12 @@ def run_batched64(args):
     ms = np.array(ms)
     u = u.cpu().numpy()
     m = P0.phi < 0
-    errs = [float(np.max(np.abs(u[k][m] - probs[k].u_exact()[m]))) for k in range(64)]
+    errs = [float(np.max(np.abs(u[k][m] - probs[k].u_exact()[m]))) for k in range(nrhs)]
     ctx.close()
-    return {"metric": METRIC, "value": 64e3 / ms.mean(), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+    return {"metric": METRIC, "value": nrhs * 1e3 / ms.mean(), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms.mean(), "higher_is_better": True,
             "dtype": "f32 conv + df64 refinement",
-            "config": {"workload": "64 RHS exp(a_k.x), Poisson torus R=0.5 r=0.2, N=128, one batched solve per step"},
+            "config": {"workload": f"{nrhs} RHS exp(a_k.x), Poisson torus R=0.5 r=0.2, N=128, one batched solve per step"},
             "iterations_max": max(s_["iterations"] for s_ in st), "rel_residual_max": max(s_["rel_residual"] for s_ in st),
             "max_err_vs_exact": max(errs)}
 
@@ -571,6 +578,7 @@ def main():
     ap.add_argument("--workload", default="torus128",
                     choices=["torus128", "sphere32", "batched64", "star256", "serving"])
     ap.add_argument("--requests", type=int, default=2000, help="serving: number of requests")
+    ap.add_argument("--nrhs", type=int, default=64, help="batched64: right-hand sides (at most 64)")
     ap.add_argument("--slots", type=int, default=6, help="serving: concurrent slots")
     ap.add_argument("--hbm-gb", type=float, default=96.0, help="serving: device-memory budget")
     ap.add_argument("--only-timed", action="store_true",

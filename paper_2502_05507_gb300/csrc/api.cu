@@ -490,6 +490,11 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
     };
     // size every buffer and set every kernel attribute the step needs before
     // any capture (nothing may allocate or configure inside it)
+    // and let the autotuner pick the convolution schedule for this batch size
+    // on an uncaptured apply (its result is discarded)
+    const bool tuned = prec == BAE_FP32 ? conv_tuned<float>(P->geo.N, nb)
+                       : prec == BAE_DF64 ? conv_tuned<dsf>(P->geo.N, nb) : conv_tuned<double>(P->geo.N, nb);
+    if (!tuned) apply_rows_prec(P, prec, nb, rhs, n, nullptr, 0, nullptr, ws.tmp.need((long long)nb * n));
     if (prec == BAE_FP32) {
         conv_args<float>(P, nb);
         vbuf<float>(P, nb);

@@ -22,6 +22,11 @@
 //             in place in B
 //   jpass^-1: inverse along j, keep j < N                     B -> A
 //   kpass^-1: C2R of two lines per complex inverse FFT, keep k < N -> v
+#include <map>
+#include <mutex>
+#include <string>
+#include <cstdio>
+#include <cstdlib>
 #include <type_traits>
 
 #include "conv.cuh"
@@ -45,6 +50,64 @@ template <typename T, int L> struct Geo {
     static constexpr int KT = P * R1;
     static constexpr int XS = R2 * (R1 + 1) + 1;   // exchange stride per pair (odd)
 };
+
+// ------------------------------------------------------------- autotuner
+// Two schedules compute the same transforms: five separate passes, or the
+// k and j passes fused per plane (where the plane fits in shared memory).
+// Which is faster depends on the batch size (the fused kernels run one
+// 200 KB CTA per SM, fewer CTAs in flight). The first apply for a given
+// (element type, N, batch size) outside a graph capture times both on the
+// real data and keeps the faster; the choices persist in the JSON file
+// named by BAE_TUNE_FILE if set. BAE_CONV_PLANE=0/1 forces a schedule.
+enum Sched { SCHED_PASSES = 0, SCHED_PLANE = 1 };
+
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune;
+bool g_tune_loaded = false;
+
+void tune_load_locked() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char* path = getenv("BAE_TUNE_FILE");
+    if (!path) return;
+    FILE* fp = fopen(path, "r");
+    if (!fp) return;
+    char key[128];
+    int val;
+    // one "key": value pair per line inside braces
+    char line[256];
+    while (fgets(line, sizeof line, fp))
+        if (sscanf(line, " \"%127[^\"]\" : %d", key, &val) == 2) g_tune[key] = val;
+    fclose(fp);
+}
+
+void tune_save_locked() {
+    const char* path = getenv("BAE_TUNE_FILE");
+    if (!path) return;
+    FILE* fp = fopen(path, "w");
+    if (!fp) return;
+    fprintf(fp, "{\n");
+    size_t k = 0;
+    for (const auto& kv : g_tune)
+        fprintf(fp, "  \"%s\": %d%s\n", kv.first.c_str(), kv.second, ++k < g_tune.size() ? "," : "");
+    fprintf(fp, "}\n");
+    fclose(fp);
+}
+
+int forced_sched() {
+    static const int f = []() {
+        const char* e = getenv("BAE_CONV_PLANE");
+        if (!e) return -1;
+        return e[0] == '0' ? (int)SCHED_PASSES : (int)SCHED_PLANE;
+    }();
+    return f;
+}
+
+template <typename T>
+const char* tname() {
+    if constexpr (std::is_same<T, dsf>::value) return "df64";
+    return sizeof(T) == 4 ? "f32" : "f64";
+}
 
 template <typename T>
 const char* kname(const char* f32, const char* f64, const char* ds) {
@@ -273,6 +336,219 @@ __global__ void __launch_bounds__(Geo<T, L>::KT) k_kpass_inv(ConvArgs<T> a) {
     }
 }
 
+// ------------------------------------------ plane-fused passes (k with j)
+// One CTA per (i plane, batch item) keeps the whole N x (N+1) plane of
+// k-spectra in shared memory, so the forward k and j passes (and the
+// inverse j and k passes) run in one kernel and A never goes to global
+// memory: 16 N^3 fewer bytes per apply. Used where the plane fits next to
+// the exchange buffers (float32 up to N = 128, 16-byte types up to N = 64).
+template <typename T, int L> struct PlaneGeo {
+    using C = cplx_t<T>;
+    static constexpr int N = L / 2, N1 = N + 1;
+    static constexpr int R1 = Factors<L>::R1, R2 = Factors<L>::R2;
+    static constexpr int PT = 512;                  // threads per CTA
+    static constexpr int PP = PT / R1;              // line pairs per round
+    static constexpr int PW = PT / R1;              // columns per round
+    static constexpr int XS = R2 * (R1 + 1) + 1;    // exchange stride per pair
+    static constexpr size_t PLANE = (size_t)N * N1 * sizeof(C);
+    static constexpr size_t XL = (size_t)PP * XS * sizeof(C);
+    static constexpr size_t XC = (size_t)L * PW * sizeof(C);
+    static constexpr size_t SMEM = PLANE + (XL > XC ? XL : XC);
+    static constexpr int ROUNDS = (N / 2 + PP - 1) / PP;   // k-line rounds (last may be partial)
+    static constexpr bool FITS = SMEM <= 227 * 1024;
+};
+
+template <typename T, int L>
+__global__ void __launch_bounds__(512) k_plane_fwd(ConvArgs<T> a) {
+    using C = cplx_t<T>;
+    using G = PlaneGeo<T, L>;
+    constexpr int N = G::N, N1 = G::N1, R1 = G::R1, R2 = G::R2, Q = R2 / R1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* plane = reinterpret_cast<C*>(smem_raw);                 // [N][N1]
+    C* xch = reinterpret_cast<C*>(smem_raw + G::PLANE);
+    const int b = blockIdx.y;
+    if (a.active && !a.active[b]) return;
+    const int i = blockIdx.x;
+
+    // ---- k lines of plane i, PP pairs per round
+    {
+        const int t = threadIdx.x % R1, p = threadIdx.x / R1;
+        for (int round = 0; round < G::ROUNDS; ++round) {
+            const int pr = round * G::PP + p;
+            const bool act = pr < N / 2;      // the last round may be partial
+            const int ja = 2 * pr, jb = ja + 1;
+            const long long la = (long long)i * N + ja, lb = la + 1;   // global line indices
+            C v[R2];
+            if (a.mode == SRC_DENSITY) {
+                // stage the two real lines in the plane rows they will own
+                T* ra = reinterpret_cast<T*>(plane + (long long)(act ? ja : 0) * N1);
+                T* rb = reinterpret_cast<T*>(plane + (long long)(act ? jb : 0) * N1);
+                if (act)
+                    for (int k = t; k < N; k += R1) { ra[k] = (T)0.0; rb[k] = (T)0.0; }
+                __syncthreads();
+                if (act) {
+                    const double* q = a.q + (long long)b * a.q_stride + (a.q_row ? (long long)a.q_row[b] * a.q_row_stride : 0);
+#pragma unroll
+                    for (int half = 0; half < 2; ++half) {
+                        const long long l = half ? lb : la;
+                        T* r = half ? rb : ra;
+                        const int s0 = a.rec.line_off[l], s1 = a.rec.line_off[l + 1];
+                        for (int s = s0 + t; s < s1; s += R1) {
+                            const int k = a.rec.src_lin[s] - (int)(l * N);
+                            double val = 0.0;
+                            for (int e = a.rec.term_off[s]; e < a.rec.term_off[s + 1]; ++e)
+                                val += (double)a.rec.term_coef[e] * q[a.rec.term_idx[e]];
+                            r[k] = (T)val;
+                        }
+                    }
+                }
+                __syncthreads();
+#pragma unroll
+                for (int m = 0; m < R2; ++m) {
+                    const int n = t + R1 * m;
+                    v[m] = (act && n < N) ? cmake<C>(ra[n], rb[n]) : cmake<C>((T)0.0, (T)0.0);
+                }
+            } else {
+                const double* f = a.f + (long long)b * N * N * N;
+#pragma unroll
+                for (int m = 0; m < R2; ++m) {
+                    const int n = t + R1 * m;
+                    T va = (T)0.0, vb = (T)0.0;
+                    if (act && n < N) {
+                        const long long xa = la * N + n, xb = lb * N + n;
+                        va = (a.flags[xa] & 1) ? (T)(a.scale * f[xa]) : (T)0.0;
+                        vb = (a.flags[xb] & 1) ? (T)(a.scale * f[xb]) : (T)0.0;
+                    }
+                    v[m] = cmake<C>(va, vb);
+                }
+            }
+            const int base = p * G::XS;
+            fft_n2k<L, false>(v, xch, base, R1 + 1, 1, t, a.tw);
+            C* z = xch + base;
+#pragma unroll
+            for (int q2 = 0; q2 < Q; ++q2)
+#pragma unroll
+                for (int k1 = 0; k1 < R1; ++k1) z[t + q2 * R1 + R2 * k1] = v[q2 * R1 + k1];
+            __syncthreads();
+            const T half = (T)0.5;
+            if (act) {
+                for (int k = t; k <= N; k += R1) {
+                    const C zk = z[k];
+                    const C zr = z[(L - k) & (L - 1)];
+                    plane[(long long)ja * N1 + k] = cmake<C>((zk.x + zr.x) * half, (zk.y - zr.y) * half);
+                    plane[(long long)jb * N1 + k] = cmake<C>((zk.y + zr.y) * half, (zr.x - zk.x) * half);
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // ---- j columns of the plane, PW columns per round, straight to B
+    {
+        const int c = threadIdx.x % G::PW, t = threadIdx.x / G::PW;
+        C* out = a.B + (long long)b * N * (2 * N) * N1 + (long long)i * (2 * N) * N1;
+        for (int col0 = 0; col0 < N1; col0 += G::PW) {
+            const int col = col0 + c;
+            const bool ok = col < N1;
+            C v[R2];
+#pragma unroll
+            for (int m = 0; m < R2; ++m) {
+                const int n = t + R1 * m;
+                v[m] = (ok && n < N) ? plane[(long long)n * N1 + col] : cmake<C>((T)0.0, (T)0.0);
+            }
+            fft_n2k<L, false>(v, xch, c, R1 * G::PW, G::PW, t, a.tw);
+            if (ok) {
+#pragma unroll
+                for (int q2 = 0; q2 < Q; ++q2)
+#pragma unroll
+                    for (int k1 = 0; k1 < R1; ++k1)
+                        out[(long long)(t + q2 * R1 + R2 * k1) * N1 + col] = v[q2 * R1 + k1];
+            }
+        }
+    }
+}
+
+template <typename T, int L>
+__global__ void __launch_bounds__(512) k_plane_inv(ConvArgs<T> a) {
+    using C = cplx_t<T>;
+    using G = PlaneGeo<T, L>;
+    constexpr int N = G::N, N1 = G::N1, R1 = G::R1, R2 = G::R2, Q = R2 / R1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* plane = reinterpret_cast<C*>(smem_raw);
+    C* xch = reinterpret_cast<C*>(smem_raw + G::PLANE);
+    const int b = blockIdx.y;
+    if (a.active && !a.active[b]) return;
+    const int i = blockIdx.x;
+
+    // ---- inverse j on every column, keep j < N in the plane
+    {
+        const int c = threadIdx.x % G::PW, t = threadIdx.x / G::PW;
+        const C* in = a.B + (long long)b * N * (2 * N) * N1 + (long long)i * (2 * N) * N1;
+        for (int col0 = 0; col0 < N1; col0 += G::PW) {
+            const int col = col0 + c;
+            const bool ok = col < N1;
+            C v[R2];
+#pragma unroll
+            for (int q2 = 0; q2 < Q; ++q2)
+#pragma unroll
+                for (int k1 = 0; k1 < R1; ++k1) {
+                    const int k = t + q2 * R1 + R2 * k1;
+                    v[q2 * R1 + k1] = ok ? in[(long long)k * N1 + col] : cmake<C>((T)0.0, (T)0.0);
+                }
+            fft_k2n<L, true>(v, xch, c, R1 * G::PW, G::PW, t, a.tw);
+            if (ok) {
+#pragma unroll
+                for (int m = 0; m < R2; ++m) {
+                    const int n = t + R1 * m;
+                    if (n < N) plane[(long long)n * N1 + col] = v[m];
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // ---- C2R of two k lines per transform, keep k < N
+    {
+        const int t = threadIdx.x % R1, p = threadIdx.x / R1;
+        auto* out = a.v + (long long)b * N * N * N;
+        for (int round = 0; round < G::ROUNDS; ++round) {
+            const int pr = round * G::PP + p;
+            const bool act = pr < N / 2;
+            const int ja = act ? 2 * pr : 0, jb = ja + 1;
+            const long long la = (long long)i * N + ja, lb = la + 1;
+            C v[R2];
+#pragma unroll
+            for (int q2 = 0; q2 < Q; ++q2)
+#pragma unroll
+                for (int k1 = 0; k1 < R1; ++k1) {
+                    const int k = t + q2 * R1 + R2 * k1;
+                    C xa, xb;
+                    if (!act) {
+                        xa = cmake<C>((T)0.0, (T)0.0);
+                        xb = xa;
+                    } else if (k <= N) {
+                        xa = plane[(long long)ja * N1 + k];
+                        xb = plane[(long long)jb * N1 + k];
+                        if (k == 0 || k == N) { xa.y = (T)0.0; xb.y = (T)0.0; }
+                    } else {
+                        xa = cconj(plane[(long long)ja * N1 + (L - k)]);
+                        xb = cconj(plane[(long long)jb * N1 + (L - k)]);
+                    }
+                    v[q2 * R1 + k1] = cmake<C>(xa.x - xb.y, xa.y + xb.x);
+                }
+            fft_k2n<L, true>(v, xch, p * G::XS, R1 + 1, 1, t, a.tw);
+            if (act) {
+#pragma unroll
+                for (int m = 0; m < R2; ++m) {
+                    const int n = t + R1 * m;
+                    if (n < N) {
+                        out[la * N + n] = to_out(v[m].x);
+                        out[lb * N + n] = to_out(v[m].y);
+                    }
+                }
+            }
+        }
+    }
+}
+
 template <typename T, int L>
 void configure_conv() {
     using C = cplx_t<T>;
@@ -287,27 +563,95 @@ void configure_conv() {
         BAE_CUDA(cudaFuncSetAttribute(k_colpass<T, L, COL_FWD_J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
         BAE_CUDA(cudaFuncSetAttribute(k_colpass<T, L, COL_CONV_I>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
         BAE_CUDA(cudaFuncSetAttribute(k_colpass<T, L, COL_INV_J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
+        if constexpr (PlaneGeo<T, L>::FITS) {
+            BAE_CUDA(cudaFuncSetAttribute(k_plane_fwd<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)PlaneGeo<T, L>::SMEM));
+            BAE_CUDA(cudaFuncSetAttribute(k_plane_inv<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)PlaneGeo<T, L>::SMEM));
+        }
         return true;
     }();
     (void)configured;
 }
 
 template <typename T, int L>
-void run_conv(const ConvArgs<T>& a, cudaStream_t st) {
+void launch_sched(const ConvArgs<T>& a, cudaStream_t st, int sched) {
     using C = cplx_t<T>;
     using G = Geo<T, L>;
+    using PG = PlaneGeo<T, L>;
     constexpr int N = L / 2;
     const size_t smem_k = (size_t)G::P * G::XS * sizeof(C) + (size_t)G::P * 2 * N * sizeof(T);
     const size_t smem_c = (size_t)L * G::W * sizeof(C);
-    configure_conv<T, L>();
     const int nb = a.nbatch;
     const dim3 gk(ceil_div((long long)N * N / 2, G::P), 1, nb);
     const int ncolblk = ceil_div(N + 1, G::W);
-    BAE_LAUNCH(kname<T>("conv_kfwd.f32", "conv_kfwd.f64", "conv_kfwd.df64"), st, k_kpass_fwd<T, L><<<gk, G::KT, smem_k, st>>>(a));
-    BAE_LAUNCH(kname<T>("conv_jfwd.f32", "conv_jfwd.f64", "conv_jfwd.df64"), st, k_colpass<T, L, COL_FWD_J><<<dim3(ncolblk, N, nb), G::CT, smem_c, st>>>(a));
+    if (sched == SCHED_PLANE) {
+        if constexpr (PG::FITS)
+            BAE_LAUNCH(kname<T>("conv_plane_fwd.f32", "conv_plane_fwd.f64", "conv_plane_fwd.df64"), st,
+                       k_plane_fwd<T, L><<<dim3(N, nb), PG::PT, PG::SMEM, st>>>(a));
+    } else {
+        BAE_LAUNCH(kname<T>("conv_kfwd.f32", "conv_kfwd.f64", "conv_kfwd.df64"), st, k_kpass_fwd<T, L><<<gk, G::KT, smem_k, st>>>(a));
+        BAE_LAUNCH(kname<T>("conv_jfwd.f32", "conv_jfwd.f64", "conv_jfwd.df64"), st, k_colpass<T, L, COL_FWD_J><<<dim3(ncolblk, N, nb), G::CT, smem_c, st>>>(a));
+    }
     BAE_LAUNCH(kname<T>("conv_i.f32", "conv_i.f64", "conv_i.df64"), st, k_colpass<T, L, COL_CONV_I><<<dim3(ncolblk, 2 * N, nb), G::CT, smem_c, st>>>(a));
-    BAE_LAUNCH(kname<T>("conv_jinv.f32", "conv_jinv.f64", "conv_jinv.df64"), st, k_colpass<T, L, COL_INV_J><<<dim3(ncolblk, N, nb), G::CT, smem_c, st>>>(a));
-    BAE_LAUNCH(kname<T>("conv_kinv.f32", "conv_kinv.f64", "conv_kinv.df64"), st, k_kpass_inv<T, L><<<gk, G::KT, smem_k, st>>>(a));
+    if (sched == SCHED_PLANE) {
+        if constexpr (PG::FITS)
+            BAE_LAUNCH(kname<T>("conv_plane_inv.f32", "conv_plane_inv.f64", "conv_plane_inv.df64"), st,
+                       k_plane_inv<T, L><<<dim3(N, nb), PG::PT, PG::SMEM, st>>>(a));
+    } else {
+        BAE_LAUNCH(kname<T>("conv_jinv.f32", "conv_jinv.f64", "conv_jinv.df64"), st, k_colpass<T, L, COL_INV_J><<<dim3(ncolblk, N, nb), G::CT, smem_c, st>>>(a));
+        BAE_LAUNCH(kname<T>("conv_kinv.f32", "conv_kinv.f64", "conv_kinv.df64"), st, k_kpass_inv<T, L><<<gk, G::KT, smem_k, st>>>(a));
+    }
+}
+
+template <typename T, int L>
+void run_conv(const ConvArgs<T>& a, cudaStream_t st) {
+    configure_conv<T, L>();
+    using PG = PlaneGeo<T, L>;
+    if constexpr (!PG::FITS) {
+        launch_sched<T, L>(a, st, SCHED_PASSES);
+        return;
+    } else {
+        if (forced_sched() >= 0) {
+            launch_sched<T, L>(a, st, forced_sched());
+            return;
+        }
+        const std::string key = std::string(tname<T>()) + "/N" + std::to_string(L / 2) + "/nb" + std::to_string(a.nbatch);
+        int sched = -1;
+        {
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            tune_load_locked();
+            auto it = g_tune.find(key);
+            if (it != g_tune.end()) sched = it->second;
+        }
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        BAE_CUDA(cudaStreamIsCapturing(st, &cs));
+        if (sched < 0 && cs != cudaStreamCaptureStatusNone) sched = a.nbatch <= 4 ? SCHED_PLANE : SCHED_PASSES;
+        if (sched >= 0) {
+            launch_sched<T, L>(a, st, sched);
+            return;
+        }
+        // time both schedules on the real data (twice each, keep the better
+        // time); the last launch leaves a valid result
+        cudaEvent_t e[3];
+        for (auto& x : e) BAE_CUDA(cudaEventCreate(&x));
+        float best[2] = {1e30f, 1e30f};
+        for (int rep = 0; rep < 2; ++rep)
+            for (int sc = 0; sc < 2; ++sc) {
+                BAE_CUDA(cudaEventRecord(e[0], st));
+                launch_sched<T, L>(a, st, sc);
+                BAE_CUDA(cudaEventRecord(e[1], st));
+                BAE_CUDA(cudaEventSynchronize(e[1]));
+                float ms = 0.f;
+                BAE_CUDA(cudaEventElapsedTime(&ms, e[0], e[1]));
+                best[sc] = ms < best[sc] ? ms : best[sc];
+            }
+        for (auto& x : e) cudaEventDestroy(x);
+        sched = best[SCHED_PLANE] < best[SCHED_PASSES] ? SCHED_PLANE : SCHED_PASSES;
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune[key] = sched;
+        tune_save_locked();
+    }
 }
 
 // ------------------------------------------------------------------ gathers
@@ -359,6 +703,15 @@ void conv_apply(const ConvArgs<T>& a, cudaStream_t st) {
 }
 
 template <typename T>
+bool conv_tuned(int N, int nbatch) {
+    if (forced_sched() >= 0) return true;
+    const std::string key = std::string(tname<T>()) + "/N" + std::to_string(N) + "/nb" + std::to_string(nbatch);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    tune_load_locked();
+    return g_tune.count(key) != 0;
+}
+
+template <typename T>
 void conv_prepare(int N) {
     switch (N) {
         case 8: configure_conv<T, 16>(); break;
@@ -398,6 +751,9 @@ void to_dsf(const double* in, long long n, dsf* out, cudaStream_t st) {
 template void conv_apply<float>(const ConvArgs<float>&, cudaStream_t);
 template void conv_apply<double>(const ConvArgs<double>&, cudaStream_t);
 template void conv_apply<dsf>(const ConvArgs<dsf>&, cudaStream_t);
+template bool conv_tuned<float>(int, int);
+template bool conv_tuned<double>(int, int);
+template bool conv_tuned<dsf>(int, int);
 template void conv_prepare<float>(int);
 template void conv_prepare<double>(int);
 template void conv_prepare<dsf>(int);

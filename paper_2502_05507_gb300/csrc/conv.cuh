@@ -54,6 +54,11 @@ void conv_apply(const ConvArgs<T>& a, cudaStream_t st);
 template <typename T>
 void conv_prepare(int N);
 
+// Whether the schedule for (element type, N, batch size) has been chosen
+// already (an apply outside graph capture chooses it by timing both).
+template <typename T>
+bool conv_tuned(int N, int nbatch);
+
 // out[b][r] = t[r] v[b][gm[r]] + (1 - t[r]) v[b][partner[r]]  (items with
 // active[b] == 0 skipped when active is not null)
 template <typename T>

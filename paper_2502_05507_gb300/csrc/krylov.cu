@@ -151,18 +151,31 @@ __device__ __forceinline__ void reduce_rows(const double* part, int nch, int col
     }
 }
 
-// w[r0 .. r0+ACH) -= V[0..cols) h over the chunk; 8 warps split the rows,
-// partial sums combined in warp order. Leaves the new chunk in s_w.
+// w[r0 .. r0+ACH) -= V[0..cols) h over the chunk; 8 warps split the rows
+// (warp q takes rows q, q+8, ...; four rows per loop trip so that eight
+// loads are in flight), partial sums combined in warp order. Indices past
+// the end of the vector are clamped (their results are never stored).
+// Leaves the new chunk in s_w (zero past the end).
 __device__ __forceinline__ void chunk_update(const double* Vb, long long n, long long r0, int cols, const double* s_h,
                                              double* w, double* s_acc, double* s_w) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long ra = r0 + lane, rb = r0 + lane + 32;
+    const long long ra = min(r0 + lane, n - 1), rb = min(r0 + lane + 32, n - 1);
     double a0 = 0.0, a1 = 0.0;
-    for (int i = warp; i < cols; i += 8) {
+    int i = warp;
+    for (; i + 24 < cols; i += 32) {
+        const double* v0 = Vb + (long long)i * n;
+        const double* v1 = v0 + 8 * n;
+        const double* v2 = v0 + 16 * n;
+        const double* v3 = v0 + 24 * n;
+        const double x0 = v0[ra], y0 = v0[rb], x1 = v1[ra], y1 = v1[rb];
+        const double x2 = v2[ra], y2 = v2[rb], x3 = v3[ra], y3 = v3[rb];
+        a0 += x0 * s_h[i] + x1 * s_h[i + 8] + x2 * s_h[i + 16] + x3 * s_h[i + 24];
+        a1 += y0 * s_h[i] + y1 * s_h[i + 8] + y2 * s_h[i + 16] + y3 * s_h[i + 24];
+    }
+    for (; i < cols; i += 8) {
         const double* v = Vb + (long long)i * n;
-        const double hi = s_h[i];
-        if (ra < n) a0 += v[ra] * hi;
-        if (rb < n) a1 += v[rb] * hi;
+        a0 += v[ra] * s_h[i];
+        a1 += v[rb] * s_h[i];
     }
     s_acc[warp * ACH + lane] = a0;
     s_acc[warp * ACH + lane + 32] = a1;
@@ -182,16 +195,34 @@ __device__ __forceinline__ void chunk_update(const double* Vb, long long n, long
     __syncthreads();
 }
 
-// partial dots of the chunk against rows i < cols: part[i][c]
+// partial dots of the chunk against rows i < cols: part[i][c] (four rows
+// per warp per loop trip)
 __device__ __forceinline__ void chunk_dots(const double* Vb, long long n, long long r0, int cols, const double* s_w,
                                            double* part, int nch, int c) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long ra = r0 + lane, rb = r0 + lane + 32;
-    for (int i = warp; i < cols; i += 8) {
+    const long long ra = min(r0 + lane, n - 1), rb = min(r0 + lane + 32, n - 1);
+    const double wa = s_w[lane], wb = s_w[lane + 32];
+    int i = warp;
+    for (; i + 24 < cols; i += 32) {
+        const double* v0 = Vb + (long long)i * n;
+        double d0 = v0[ra] * wa + v0[rb] * wb;
+        double d1 = v0[8 * n + ra] * wa + v0[8 * n + rb] * wb;
+        double d2 = v0[16 * n + ra] * wa + v0[16 * n + rb] * wb;
+        double d3 = v0[24 * n + ra] * wa + v0[24 * n + rb] * wb;
+        d0 = warp_sum(d0);
+        d1 = warp_sum(d1);
+        d2 = warp_sum(d2);
+        d3 = warp_sum(d3);
+        if (lane == 0) {
+            part[(long long)i * nch + c] = d0;
+            part[(long long)(i + 8) * nch + c] = d1;
+            part[(long long)(i + 16) * nch + c] = d2;
+            part[(long long)(i + 24) * nch + c] = d3;
+        }
+    }
+    for (; i < cols; i += 8) {
         const double* v = Vb + (long long)i * n;
-        double acc = 0.0;
-        if (ra < n) acc += v[ra] * s_w[lane];
-        if (rb < n) acc += v[rb] * s_w[lane + 32];
+        double acc = v[ra] * wa + v[rb] * wb;
         acc = warp_sum(acc);
         if (lane == 0) part[(long long)i * nch + c] = acc;
     }
