@@ -155,6 +155,19 @@ def roofline_for(name, ms_total, launches, n_gm, hbm, hbm_kind):
             "algorithmic_bytes": nbytes}
 
 
+def aggregate_replicas(local_ms, steps, world, device):
+    """Whole-job throughput of independent replicas: every rank solved
+    `steps` problems in local_ms; the job took the slowest rank's time (a
+    MAX all-reduce, the only collective: the solves exchange nothing)."""
+    total_ms = float(local_ms)
+    if world > 1:
+        import torch
+        t = torch.tensor([total_ms], device=device, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return steps * world / (total_ms / 1000.0), total_ms
+
+
 def _flush_l2(buf):
     buf.add_(1.0)
 
@@ -214,13 +227,7 @@ def run_ours(args, rank, world, dev):
         torch.distributed.barrier()
     clk = clocks.stop()
     ms = np.array([a.elapsed_time(b) for a, b in zip(e0, e1)])
-    total_ms = float(ms.sum())
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    solves = args.steps * world
-    value = solves / (total_ms / 1000.0)
+    value, total_ms = aggregate_replicas(float(ms.sum()), args.steps, world, torch.device("cuda", dev))
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": float(ms.mean()), "higher_is_better": True,

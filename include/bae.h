@@ -107,6 +107,23 @@ void bae_default_options(bae_options* opts);
  * (all contexts). */
 long long bae_launch_count(void);
 
+/* Schedule of the FFT convolution inside every potential apply of this
+ * process (all contexts): BAE_SCHED_AUTO (-1, the default) times the two
+ * schedules on the first apply of each (precision, N, batch size) outside
+ * graph capture and keeps the faster; BAE_SCHED_PASSES (0) runs the k, j and
+ * i transforms as five separate kernels; BAE_SCHED_PLANE (1) fuses the k and
+ * j transforms per x-plane (one CTA per plane where the plane of k-spectra
+ * fits in shared memory, a thread-block cluster sharing it through
+ * distributed shared memory where it does not). Both compute the same
+ * convolution (Section 3.2, the discrete potentials as lattice sums); they
+ * differ in rounding order only. Overrides the BAE_CONV_PLANE environment
+ * variable. Returns BAE_ERR_INVALID_ARG for any other value. Not part of the
+ * method: a performance control. */
+#define BAE_SCHED_AUTO (-1)
+#define BAE_SCHED_PASSES 0
+#define BAE_SCHED_PLANE 1
+int bae_set_conv_schedule(int schedule);
+
 /* Process-wide kernel timing. bae_profile_start pre-creates CUDA events for
  * up to max_launches launches; from then on every kernel launch of the
  * library is bracketed by two events on its own stream. bae_profile_stop

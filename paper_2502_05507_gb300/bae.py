@@ -86,6 +86,7 @@ def lib():
             "bae_last_error": (ctypes.c_char_p, []),
             "bae_default_options": (None, [_P]),
             "bae_launch_count": (ctypes.c_longlong, []),
+            "bae_set_conv_schedule": (_I, [_I]),
             "bae_profile_start": (_I, [_I]),
             "bae_profile_stop": (_I, [ctypes.c_char_p, _I, _P, _P, _I, _P]),
             "bae_ctx_create": (_I, [_I, _P, _P]),
@@ -119,7 +120,7 @@ def lib():
     return _lib
 
 
-EXPORTED = ["bae_version", "bae_last_error", "bae_default_options", "bae_launch_count", "bae_profile_start",
+EXPORTED = ["bae_version", "bae_last_error", "bae_default_options", "bae_launch_count", "bae_set_conv_schedule", "bae_profile_start",
             "bae_profile_stop", "bae_ctx_create", "bae_ctx_destroy",
             "bae_lgf_table", "bae_lgf_spectrum", "bae_problem_create", "bae_problem_destroy",
             "bae_problem_sizes", "bae_boundary_points", "bae_classification", "bae_potential_apply",
@@ -181,6 +182,18 @@ def _as_f64(a):
 def launch_count() -> int:
     """Kernels launched by the library in this process so far."""
     return int(lib().bae_launch_count())
+
+
+SCHEDULES = {"auto": -1, "passes": 0, "plane": 1}
+
+
+def set_conv_schedule(schedule: str = "auto"):
+    """Forces the FFT convolution schedule of every potential apply in this
+    process: "passes" (five kernels), "plane" (k and j fused per x-plane) or
+    "auto" (timed once per precision, N and batch size)."""
+    if schedule not in SCHEDULES:
+        raise ValueError(f"schedule must be one of {sorted(SCHEDULES)}")
+    _check(lib().bae_set_conv_schedule(SCHEDULES[schedule]))
 
 
 def profile_start(max_launches: int = 200000):

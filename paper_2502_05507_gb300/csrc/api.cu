@@ -17,6 +17,7 @@
 #include "classify.cuh"
 #include "common.cuh"
 #include "conv.cuh"
+#include "conv_tune.cuh"
 #include "internal.cuh"
 #include "krylov.cuh"
 #include "lgf.cuh"
@@ -630,6 +631,16 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
         BAE_CUDA(cudaMemcpyAsync(p, g, (size_t)nb * n * sizeof(double), cudaMemcpyHostToDevice, st));
         d_g = p;
     }
+    {   // f on M+ and g must be finite
+        int* d_bad = P->ws().arnI.need(4);
+        int bad = 0;
+        BAE_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(int), st));
+        kr_nonfinite(d_f, (long long)nb * n3, P->geo.flags, n3, d_bad, st);
+        kr_nonfinite(d_g, (long long)nb * n, nullptr, 1, d_bad, st);
+        BAE_CUDA(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+        BAE_CUDA(cudaStreamSynchronize(st));
+        BAE_REQUIRE(!bad, BAE_ERR_INVALID_ARG, "f (on M+) or g contains non-finite values");
+    }
     std::vector<bae_stats> st_local(nb);
     for (auto& s : st_local) std::memset(&s, 0, sizeof(s));
 
@@ -814,6 +825,15 @@ extern "C" {
 int bae_version(void) { return 1; }
 
 long long bae_launch_count(void) { return bae::g_launches.load(); }
+
+int bae_set_conv_schedule(int schedule) {
+    return guarded([&]() -> int {
+        BAE_REQUIRE(schedule >= BAE_SCHED_AUTO && schedule <= BAE_SCHED_PLANE, BAE_ERR_INVALID_ARG,
+                    "schedule must be BAE_SCHED_AUTO, BAE_SCHED_PASSES or BAE_SCHED_PLANE");
+        bae::set_forced_sched(schedule);
+        return BAE_OK;
+    });
+}
 
 int bae_profile_start(int max_launches) {
     return guarded([&]() -> int {

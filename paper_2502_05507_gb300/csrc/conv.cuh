@@ -49,6 +49,23 @@ struct ConvArgs {
 template <typename T>
 void conv_apply(const ConvArgs<T>& a, cudaStream_t st);
 
+// The apply and the kernel set-up for one transform length L = 2N,
+// instantiated per element type in conv_f32.cu, conv_f64.cu and
+// conv_df64*.cu.
+template <typename T, int L>
+void run_conv(const ConvArgs<T>& a, cudaStream_t st);
+template <typename T, int L>
+void conv_configure();
+
+// The cluster plane kernels (conv_cplane_*.cu) for L where one plane of
+// k-spectra does not fit one CTA: cplane_ready sets their attributes and
+// says whether the device can place a cluster; cplane_launch runs the
+// forward (k, j) or the inverse (j, k) kernel.
+template <typename T, int L>
+bool cplane_ready();
+template <typename T, int L>
+void cplane_launch(const ConvArgs<T>& a, cudaStream_t st, bool inverse);
+
 // Sets the kernel attributes conv_apply needs for grid size N (done on the
 // first apply anyway; call it before capturing applies in a CUDA graph).
 template <typename T>

@@ -1,4 +1,5 @@
-// The matrix-free potential apply: source stencil, zero-padded (2N)^3 real
+#pragma once
+// Kernels of the matrix-free potential apply: source stencil, zero-padded (2N)^3 real
 // FFT convolution with the lattice Green's function, and the gathers.
 //
 // v(m) = sum_x G_s(m - x) rho(x) for m, x in the N^3 grid (Section 3.2,
@@ -22,98 +23,24 @@
 //             in place in B
 //   jpass^-1: inverse along j, keep j < N                     B -> A
 //   kpass^-1: C2R of two lines per complex inverse FFT, keep k < N -> v
-#include <map>
-#include <mutex>
+//
+// A thread holding sample n = t + R1 m of a line (0 <= t < R1, R1 R2 = 2N)
+// holds a nonzero input / a kept output exactly when m < R2 / 2; the kernels
+// test m, a compile-time index, so the compiler drops the arithmetic on the
+// zero padding and on the discarded half.
 #include <string>
-#include <cstdio>
-#include <cstdlib>
 #include <type_traits>
 
-#include "conv.cuh"
-#include "fft2.cuh"
+#include "conv_geo.cuh"
+#include "conv_tune.cuh"
+
+// Included once per element type by conv_<type>.cu, which instantiates
+// run_conv and conv_configure for its transform lengths, so the kernels of
+// the three element types compile in parallel.
 
 namespace bae {
 
 namespace {
-
-// Launch geometry per transform length and precision.
-template <typename T, int L> struct Geo {
-    using C = cplx_t<T>;
-    static constexpr int R1 = Factors<L>::R1, R2 = Factors<L>::R2;
-    // column passes: W columns per CTA, R1 threads per column
-    static constexpr int WB = 65536 / (L * (int)sizeof(C));
-    static constexpr int W = WB > 32 ? 32 : (WB < 8 ? 8 : WB);
-    static constexpr int CT = W * R1;
-    // line passes (k): P line pairs per CTA, R1 threads per pair
-    static constexpr int PB = 65536 / (L * (int)sizeof(C));
-    static constexpr int P = (256 / R1) < PB ? (256 / R1) : (PB < 4 ? 4 : PB);
-    static constexpr int KT = P * R1;
-    static constexpr int XS = R2 * (R1 + 1) + 1;   // exchange stride per pair (odd)
-};
-
-// ------------------------------------------------------------- autotuner
-// Two schedules compute the same transforms: five separate passes, or the
-// k and j passes fused per plane (where the plane fits in shared memory).
-// Which is faster depends on the batch size (the fused kernels run one
-// 200 KB CTA per SM, fewer CTAs in flight). The first apply for a given
-// (element type, N, batch size) outside a graph capture times both on the
-// real data and keeps the faster; the choices persist in the JSON file
-// named by BAE_TUNE_FILE if set. BAE_CONV_PLANE=0/1 forces a schedule.
-enum Sched { SCHED_PASSES = 0, SCHED_PLANE = 1 };
-
-std::mutex g_tune_mu;
-std::map<std::string, int> g_tune;
-bool g_tune_loaded = false;
-
-void tune_load_locked() {
-    if (g_tune_loaded) return;
-    g_tune_loaded = true;
-    const char* path = getenv("BAE_TUNE_FILE");
-    if (!path) return;
-    FILE* fp = fopen(path, "r");
-    if (!fp) return;
-    char key[128];
-    int val;
-    // one "key": value pair per line inside braces
-    char line[256];
-    while (fgets(line, sizeof line, fp))
-        if (sscanf(line, " \"%127[^\"]\" : %d", key, &val) == 2) g_tune[key] = val;
-    fclose(fp);
-}
-
-void tune_save_locked() {
-    const char* path = getenv("BAE_TUNE_FILE");
-    if (!path) return;
-    FILE* fp = fopen(path, "w");
-    if (!fp) return;
-    fprintf(fp, "{\n");
-    size_t k = 0;
-    for (const auto& kv : g_tune)
-        fprintf(fp, "  \"%s\": %d%s\n", kv.first.c_str(), kv.second, ++k < g_tune.size() ? "," : "");
-    fprintf(fp, "}\n");
-    fclose(fp);
-}
-
-int forced_sched() {
-    static const int f = []() {
-        const char* e = getenv("BAE_CONV_PLANE");
-        if (!e) return -1;
-        return e[0] == '0' ? (int)SCHED_PASSES : (int)SCHED_PLANE;
-    }();
-    return f;
-}
-
-template <typename T>
-const char* tname() {
-    if constexpr (std::is_same<T, dsf>::value) return "df64";
-    return sizeof(T) == 4 ? "f32" : "f64";
-}
-
-template <typename T>
-const char* kname(const char* f32, const char* f64, const char* ds) {
-    if constexpr (std::is_same<T, dsf>::value) return ds;
-    return sizeof(T) == 4 ? f32 : f64;
-}
 
 // ------------------------------------------------------------- k pass (R2C)
 // Two real k-lines (i, 2p) and (i, 2p+1) per complex transform z = x_a + i x_b.
@@ -158,7 +85,7 @@ __global__ void __launch_bounds__(Geo<T, L>::KT) k_kpass_fwd(ConvArgs<T> a) {
 #pragma unroll
         for (int m = 0; m < R2; ++m) {
             const int n = t + R1 * m;
-            v[m] = (n < N) ? cmake<C>(r[n], r[N + n]) : cmake<C>((T)0, (T)0);
+            v[m] = (m < R2 / 2) ? cmake<C>(r[n], r[N + n]) : cmake<C>((T)0, (T)0);
         }
     } else {
         const double* f = a.f + (long long)b * N * N * N;
@@ -166,7 +93,7 @@ __global__ void __launch_bounds__(Geo<T, L>::KT) k_kpass_fwd(ConvArgs<T> a) {
         for (int m = 0; m < R2; ++m) {
             const int n = t + R1 * m;
             T va = (T)0.0, vb = (T)0.0;
-            if (active && n < N) {
+            if (active && m < R2 / 2) {
                 const long long xa = la * N + n, xb = lb * N + n;
                 va = (a.flags[xa] & 1) ? (T)(a.scale * f[xa]) : (T)0;
                 vb = (a.flags[xb] & 1) ? (T)(a.scale * f[xb]) : (T)0;
@@ -245,7 +172,7 @@ __global__ void __launch_bounds__(Geo<T, L>::CT) k_colpass(ConvArgs<T> a) {
 #pragma unroll
         for (int m = 0; m < R2; ++m) {
             const int n = t + R1 * m;
-            v[m] = (ok && n < N) ? in[n * stride] : zero;
+            v[m] = (ok && m < R2 / 2) ? in[n * stride] : zero;
         }
         fft_n2k<L, false>(v, xch, c, R1 * W, W, t, a.tw);
     }
@@ -278,7 +205,7 @@ __global__ void __launch_bounds__(Geo<T, L>::CT) k_colpass(ConvArgs<T> a) {
 #pragma unroll
         for (int m = 0; m < R2; ++m) {
             const int n = t + R1 * m;
-            if (n < N) out[n * stride] = v[m];
+            if (m < R2 / 2) out[n * stride] = v[m];
         }
     }
 }
@@ -328,7 +255,7 @@ __global__ void __launch_bounds__(Geo<T, L>::KT) k_kpass_inv(ConvArgs<T> a) {
 #pragma unroll
         for (int m = 0; m < R2; ++m) {
             const int n = t + R1 * m;
-            if (n < N) {
+            if (m < R2 / 2) {
                 out[la * N + n] = to_out(v[m].x);
                 out[lb * N + n] = to_out(v[m].y);
             }
@@ -342,21 +269,6 @@ __global__ void __launch_bounds__(Geo<T, L>::KT) k_kpass_inv(ConvArgs<T> a) {
 // inverse j and k passes) run in one kernel and A never goes to global
 // memory: 16 N^3 fewer bytes per apply. Used where the plane fits next to
 // the exchange buffers (float32 up to N = 128, 16-byte types up to N = 64).
-template <typename T, int L> struct PlaneGeo {
-    using C = cplx_t<T>;
-    static constexpr int N = L / 2, N1 = N + 1;
-    static constexpr int R1 = Factors<L>::R1, R2 = Factors<L>::R2;
-    static constexpr int PT = 512;                  // threads per CTA
-    static constexpr int PP = PT / R1;              // line pairs per round
-    static constexpr int PW = PT / R1;              // columns per round
-    static constexpr int XS = R2 * (R1 + 1) + 1;    // exchange stride per pair
-    static constexpr size_t PLANE = (size_t)N * N1 * sizeof(C);
-    static constexpr size_t XL = (size_t)PP * XS * sizeof(C);
-    static constexpr size_t XC = (size_t)L * PW * sizeof(C);
-    static constexpr size_t SMEM = PLANE + (XL > XC ? XL : XC);
-    static constexpr int ROUNDS = (N / 2 + PP - 1) / PP;   // k-line rounds (last may be partial)
-    static constexpr bool FITS = SMEM <= 227 * 1024;
-};
 
 template <typename T, int L>
 __global__ void __launch_bounds__(512) k_plane_fwd(ConvArgs<T> a) {
@@ -406,7 +318,7 @@ __global__ void __launch_bounds__(512) k_plane_fwd(ConvArgs<T> a) {
 #pragma unroll
                 for (int m = 0; m < R2; ++m) {
                     const int n = t + R1 * m;
-                    v[m] = (act && n < N) ? cmake<C>(ra[n], rb[n]) : cmake<C>((T)0.0, (T)0.0);
+                    v[m] = (act && m < R2 / 2) ? cmake<C>(ra[n], rb[n]) : cmake<C>((T)0.0, (T)0.0);
                 }
             } else {
                 const double* f = a.f + (long long)b * N * N * N;
@@ -414,7 +326,7 @@ __global__ void __launch_bounds__(512) k_plane_fwd(ConvArgs<T> a) {
                 for (int m = 0; m < R2; ++m) {
                     const int n = t + R1 * m;
                     T va = (T)0.0, vb = (T)0.0;
-                    if (act && n < N) {
+                    if (act && m < R2 / 2) {
                         const long long xa = la * N + n, xb = lb * N + n;
                         va = (a.flags[xa] & 1) ? (T)(a.scale * f[xa]) : (T)0.0;
                         vb = (a.flags[xb] & 1) ? (T)(a.scale * f[xb]) : (T)0.0;
@@ -453,7 +365,7 @@ __global__ void __launch_bounds__(512) k_plane_fwd(ConvArgs<T> a) {
 #pragma unroll
             for (int m = 0; m < R2; ++m) {
                 const int n = t + R1 * m;
-                v[m] = (ok && n < N) ? plane[(long long)n * N1 + col] : cmake<C>((T)0.0, (T)0.0);
+                v[m] = (ok && m < R2 / 2) ? plane[(long long)n * N1 + col] : cmake<C>((T)0.0, (T)0.0);
             }
             fft_n2k<L, false>(v, xch, c, R1 * G::PW, G::PW, t, a.tw);
             if (ok) {
@@ -499,7 +411,7 @@ __global__ void __launch_bounds__(512) k_plane_inv(ConvArgs<T> a) {
 #pragma unroll
                 for (int m = 0; m < R2; ++m) {
                     const int n = t + R1 * m;
-                    if (n < N) plane[(long long)n * N1 + col] = v[m];
+                    if (m < R2 / 2) plane[(long long)n * N1 + col] = v[m];
                 }
             }
         }
@@ -539,7 +451,7 @@ __global__ void __launch_bounds__(512) k_plane_inv(ConvArgs<T> a) {
 #pragma unroll
                 for (int m = 0; m < R2; ++m) {
                     const int n = t + R1 * m;
-                    if (n < N) {
+                    if (m < R2 / 2) {
                         out[la * N + n] = to_out(v[m].x);
                         out[lb * N + n] = to_out(v[m].y);
                     }
@@ -569,6 +481,7 @@ void configure_conv() {
             BAE_CUDA(cudaFuncSetAttribute(k_plane_inv<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)PlaneGeo<T, L>::SMEM));
         }
+        if constexpr (!PlaneGeo<T, L>::FITS && CPlaneGeo<T, L>::USE) cplane_ready<T, L>();
         return true;
     }();
     (void)configured;
@@ -589,6 +502,8 @@ void launch_sched(const ConvArgs<T>& a, cudaStream_t st, int sched) {
         if constexpr (PG::FITS)
             BAE_LAUNCH(kname<T>("conv_plane_fwd.f32", "conv_plane_fwd.f64", "conv_plane_fwd.df64"), st,
                        k_plane_fwd<T, L><<<dim3(N, nb), PG::PT, PG::SMEM, st>>>(a));
+        else if constexpr (CPlaneGeo<T, L>::USE)
+            cplane_launch<T, L>(a, st, false);
     } else {
         BAE_LAUNCH(kname<T>("conv_kfwd.f32", "conv_kfwd.f64", "conv_kfwd.df64"), st, k_kpass_fwd<T, L><<<gk, G::KT, smem_k, st>>>(a));
         BAE_LAUNCH(kname<T>("conv_jfwd.f32", "conv_jfwd.f64", "conv_jfwd.df64"), st, k_colpass<T, L, COL_FWD_J><<<dim3(ncolblk, N, nb), G::CT, smem_c, st>>>(a));
@@ -598,32 +513,36 @@ void launch_sched(const ConvArgs<T>& a, cudaStream_t st, int sched) {
         if constexpr (PG::FITS)
             BAE_LAUNCH(kname<T>("conv_plane_inv.f32", "conv_plane_inv.f64", "conv_plane_inv.df64"), st,
                        k_plane_inv<T, L><<<dim3(N, nb), PG::PT, PG::SMEM, st>>>(a));
+        else if constexpr (CPlaneGeo<T, L>::USE)
+            cplane_launch<T, L>(a, st, true);
     } else {
         BAE_LAUNCH(kname<T>("conv_jinv.f32", "conv_jinv.f64", "conv_jinv.df64"), st, k_colpass<T, L, COL_INV_J><<<dim3(ncolblk, N, nb), G::CT, smem_c, st>>>(a));
         BAE_LAUNCH(kname<T>("conv_kinv.f32", "conv_kinv.f64", "conv_kinv.df64"), st, k_kpass_inv<T, L><<<gk, G::KT, smem_k, st>>>(a));
     }
 }
 
+}  // namespace
+
 template <typename T, int L>
 void run_conv(const ConvArgs<T>& a, cudaStream_t st) {
     configure_conv<T, L>();
     using PG = PlaneGeo<T, L>;
-    if constexpr (!PG::FITS) {
+    if constexpr (!PG::FITS && !CPlaneGeo<T, L>::USE) {
         launch_sched<T, L>(a, st, SCHED_PASSES);
         return;
     } else {
+        if constexpr (!PG::FITS) {
+            if (!cplane_ready<T, L>()) {
+                launch_sched<T, L>(a, st, SCHED_PASSES);
+                return;
+            }
+        }
         if (forced_sched() >= 0) {
             launch_sched<T, L>(a, st, forced_sched());
             return;
         }
         const std::string key = std::string(tname<T>()) + "/N" + std::to_string(L / 2) + "/nb" + std::to_string(a.nbatch);
-        int sched = -1;
-        {
-            std::lock_guard<std::mutex> lock(g_tune_mu);
-            tune_load_locked();
-            auto it = g_tune.find(key);
-            if (it != g_tune.end()) sched = it->second;
-        }
+        int sched = tune_lookup(key);
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         BAE_CUDA(cudaStreamIsCapturing(st, &cs));
         if (sched < 0 && cs != cudaStreamCaptureStatusNone) sched = a.nbatch <= 4 ? SCHED_PLANE : SCHED_PASSES;
@@ -648,120 +567,14 @@ void run_conv(const ConvArgs<T>& a, cudaStream_t st) {
             }
         for (auto& x : e) cudaEventDestroy(x);
         sched = best[SCHED_PLANE] < best[SCHED_PASSES] ? SCHED_PLANE : SCHED_PASSES;
-        std::lock_guard<std::mutex> lock(g_tune_mu);
-        g_tune[key] = sched;
-        tune_save_locked();
+        tune_store(key, sched);
     }
 }
 
-// ------------------------------------------------------------------ gathers
-template <typename T>
-__global__ void k_closure_gather(const T* v, long long v_stride, const int* gm, const int* partner,
-                                 const double* t, int n, double* out, long long out_stride, const int* active) {
-    const int b = blockIdx.y;
-    if (active && !active[b]) return;
-    const T* vb = v + b * v_stride;
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
-        const double tr = t[r];
-        out[b * out_stride + r] = tr * (double)vb[gm[r]] + (1.0 - tr) * (double)vb[partner[r]];
-    }
+
+template <typename T, int L>
+void conv_configure() {
+    configure_conv<T, L>();
 }
-
-template <typename T>
-__global__ void k_volume_combine(const T* v, const double* add, const uint8_t* flags, long long n3, double* u) {
-    const int b = blockIdx.y;
-    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n3; x += (long long)gridDim.x * blockDim.x) {
-        const bool np = (flags[x] & 3) != 0;   // M+ or gamma-
-        u[b * n3 + x] = np ? (add ? add[b * n3 + x] : 0.0) + (double)v[b * n3 + x] : 0.0;
-    }
-}
-
-__global__ void k_to_dsf(const double* in, long long n, dsf* out) {
-    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n; x += (long long)gridDim.x * blockDim.x)
-        out[x] = dsf(in[x]);
-}
-
-template <typename T>
-__global__ void k_widen(const T* v, long long n, double* out) {
-    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n; x += (long long)gridDim.x * blockDim.x)
-        out[x] = (double)v[x];
-}
-
-}  // namespace
-
-template <typename T>
-void conv_apply(const ConvArgs<T>& a, cudaStream_t st) {
-    switch (a.N) {
-        case 8: run_conv<T, 16>(a, st); break;
-        case 16: run_conv<T, 32>(a, st); break;
-        case 32: run_conv<T, 64>(a, st); break;
-        case 64: run_conv<T, 128>(a, st); break;
-        case 128: run_conv<T, 256>(a, st); break;
-        case 256: run_conv<T, 512>(a, st); break;
-        default: throw Error(BAE_ERR_INVALID_ARG, "conv: N must be a power of two in [8, 256]");
-    }
-}
-
-template <typename T>
-bool conv_tuned(int N, int nbatch) {
-    if (forced_sched() >= 0) return true;
-    const std::string key = std::string(tname<T>()) + "/N" + std::to_string(N) + "/nb" + std::to_string(nbatch);
-    std::lock_guard<std::mutex> lock(g_tune_mu);
-    tune_load_locked();
-    return g_tune.count(key) != 0;
-}
-
-template <typename T>
-void conv_prepare(int N) {
-    switch (N) {
-        case 8: configure_conv<T, 16>(); break;
-        case 16: configure_conv<T, 32>(); break;
-        case 32: configure_conv<T, 64>(); break;
-        case 64: configure_conv<T, 128>(); break;
-        case 128: configure_conv<T, 256>(); break;
-        case 256: configure_conv<T, 512>(); break;
-        default: throw Error(BAE_ERR_INVALID_ARG, "conv: N must be a power of two in [8, 256]");
-    }
-}
-
-template <typename T>
-void closure_gather(const T* v, long long v_stride, const int* gm, const int* partner, const double* t,
-                    int n, int nbatch, double* out, long long out_stride, cudaStream_t st, const int* active) {
-    if (n == 0) return;
-    dim3 grid(ceil_div(n, 256) < 1184 ? ceil_div(n, 256) : 1184, nbatch);
-    BAE_LAUNCH(kname<T>("closure_gather.f32", "closure_gather.f64", "closure_gather.f64"), st, k_closure_gather<T><<<grid, 256, 0, st>>>(v, v_stride, gm, partner, t, n, out, out_stride, active));
-}
-
-template <typename T>
-void volume_combine(const T* v, const double* add, const uint8_t* flags, long long n3, int nbatch,
-                    double* u, cudaStream_t st) {
-    dim3 grid(ceil_div(n3, 256) < 2432 ? ceil_div(n3, 256) : 2432, nbatch);
-    BAE_LAUNCH("k_volume_combine", st, k_volume_combine<T><<<grid, 256, 0, st>>>(v, add, flags, n3, u));
-}
-
-template <typename T>
-void widen(const T* v, long long n, double* out, cudaStream_t st) {
-    BAE_LAUNCH("k_widen", st, k_widen<T><<<ceil_div(n, 256) < 2432 ? ceil_div(n, 256) : 2432, 256, 0, st>>>(v, n, out));
-}
-
-void to_dsf(const double* in, long long n, dsf* out, cudaStream_t st) {
-    BAE_LAUNCH("k_to_dsf", st, k_to_dsf<<<ceil_div(n, 256) < 2432 ? ceil_div(n, 256) : 2432, 256, 0, st>>>(in, n, out));
-}
-
-template void conv_apply<float>(const ConvArgs<float>&, cudaStream_t);
-template void conv_apply<double>(const ConvArgs<double>&, cudaStream_t);
-template void conv_apply<dsf>(const ConvArgs<dsf>&, cudaStream_t);
-template bool conv_tuned<float>(int, int);
-template bool conv_tuned<double>(int, int);
-template bool conv_tuned<dsf>(int, int);
-template void conv_prepare<float>(int);
-template void conv_prepare<double>(int);
-template void conv_prepare<dsf>(int);
-template void closure_gather<float>(const float*, long long, const int*, const int*, const double*, int, int, double*, long long, cudaStream_t, const int*);
-template void closure_gather<double>(const double*, long long, const int*, const int*, const double*, int, int, double*, long long, cudaStream_t, const int*);
-template void volume_combine<float>(const float*, const double*, const uint8_t*, long long, int, double*, cudaStream_t);
-template void volume_combine<double>(const double*, const double*, const uint8_t*, long long, int, double*, cudaStream_t);
-template void widen<float>(const float*, long long, double*, cudaStream_t);
-template void widen<double>(const double*, long long, double*, cudaStream_t);
 
 }  // namespace bae

@@ -68,11 +68,24 @@ __global__ void k_add(const double* x, const int* __restrict__ active, int n, do
         y[(long long)b * n + r] += x[(long long)b * n + r];
 }
 
+// *flag |= 1 if some x[i] with (flags == null or flags[i % period] & 1) is not finite
+__global__ void k_nonfinite(const double* __restrict__ x, long long n, const uint8_t* __restrict__ flags,
+                            long long period, int* flag) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        if (!isfinite(x[i]) && (!flags || (flags[i % period] & 1))) atomicOr(flag, 1);
+}
+
 int blocks_for(long long n) { return (int)std::min<long long>((n + 255) / 256, 1216); }
 
 }  // namespace
 
 int krylov_chunks(int n) { return ceil_div(n, CH); }
+
+void kr_nonfinite(const double* x, long long n, const uint8_t* flags, long long period, int* d_flag,
+                  cudaStream_t st) {
+    if (n <= 0) return;
+    BAE_LAUNCH("k_nonfinite", st, k_nonfinite<<<blocks_for(n), 256, 0, st>>>(x, n, flags, period, d_flag));
+}
 
 void kr_norm2(const double* x, const int* active, int na, int n, double* partial, int nchunk, double* out,
               cudaStream_t st) {

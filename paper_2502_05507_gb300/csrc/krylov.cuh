@@ -11,6 +11,11 @@ namespace bae {
 
 int krylov_chunks(int n);
 
+// *d_flag |= 1 if some x[i] is not finite, counting only i whose
+// flags[i % period] has bit 0 (M+) when flags is not null
+void kr_nonfinite(const double* x, long long n, const uint8_t* flags, long long period, int* d_flag,
+                  cudaStream_t st);
+
 // nrm2[b] = ||x[b]||^2 (deterministic), x [nb][n] with row stride n
 void kr_norm2(const double* x, const int* active, int na, int n, double* partial, int nchunk, double* out,
               cudaStream_t st);

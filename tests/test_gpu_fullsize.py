@@ -47,6 +47,25 @@ def test_apply_full_size(setup):
     assert np.max(np.abs(vds - ref)) <= 1e-12 * scale
 
 
+@pytest.mark.parametrize("precision,tol", [("fp32", 2e-6), ("fp64", 1e-12), ("df64", 1e-12)])
+def test_apply_full_size_each_schedule(setup, precision, tol):
+    # the five-pass schedule and the plane-fused one (one CTA per plane for
+    # float32, a two-CTA cluster sharing the plane for the 16-byte types)
+    import torch
+    from paper_2502_05507_gb300 import set_conv_schedule
+    P, cls, spec, prob = setup["P"], setup["cls"], setup["spec"], setup["prob"]
+    q = W.random_density(cls.gm_idx.size, seed=23)
+    ref = OP.fft_convolve(OP.source_density(cls, q, "double"), spectrum=spec, workers=-1)
+    scale = np.max(np.abs(ref))
+    try:
+        for name in ("passes", "plane"):
+            set_conv_schedule(name)
+            v = prob.potential_apply(torch.from_numpy(q).cuda(), precision).cpu().numpy()
+            assert np.max(np.abs(v - ref)) <= tol * scale, name
+    finally:
+        set_conv_schedule("auto")
+
+
 def test_apply_full_size_sampled_direct_sum(setup):
     # a sparse density: the oracle sums G(m - x) rho(x) term by term at
     # sampled targets, with G from the oracle's table

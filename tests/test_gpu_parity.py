@@ -224,3 +224,31 @@ def test_fresh_context_graph_vs_plain_launches(precision):
     assert np.array_equal(outs[0][0], outs[1][0])
     assert np.array_equal(outs[0][1], outs[1][1])
     assert outs[0][2]["iterations"] == outs[1][2]["iterations"]
+
+
+def test_solve_errors_and_not_converged(ctx):
+    # non-finite data is rejected; an iteration cap below what the problem
+    # needs returns BAE_ERR_NOT_CONVERGED with the outputs and stats written
+    import torch
+    from paper_2502_05507_gb300 import BAEError, NotConverged
+    P = W.sphere_exp(16)
+    prob = _problem(ctx, P)
+    g = torch.from_numpy(P.g_at(prob.boundary_points())).cuda()
+    f = torch.from_numpy(P.f()).cuda()
+    fb = f.clone()
+    fb.view(-1)[int(np.flatnonzero(P.phi.reshape(-1) < 0)[3])] = float("nan")
+    with pytest.raises(BAEError):
+        prob.solve(fb, g, tol=1e-10)
+    gb = g.clone()
+    gb[5] = float("inf")
+    with pytest.raises(BAEError):
+        prob.solve(f, gb, tol=1e-10)
+    fo = f.clone()
+    fo.view(-1)[int(np.flatnonzero(P.phi.reshape(-1) > 0)[0])] = float("nan")   # outside M+: unused
+    prob.solve(fo, g, tol=1e-10)
+    with pytest.raises(NotConverged):
+        prob.solve(f, g, tol=1e-10, max_iter=3)
+    q, u, st = prob.solve(f, g, tol=1e-10, max_iter=3, allow_not_converged=True)
+    assert st["iterations"] == 3 and st["rel_residual"] > 1e-10
+    assert torch.isfinite(u).all()
+    prob.close()
