@@ -106,19 +106,23 @@ def kernel_model(n, pb, n_gm):
     c = 2 * pb
     L = 2 * n
     n1 = n + 1
-    A = n * n * n1 * c
-    B = 2 * n * n * n1 * c
+    # N k-columns per (i, j): the real kk = N spectrum is packed into column 0
+    A = n * n * n * c
+    B = 2 * n * n * n * c
     F = 5.0 * L * math.log2(L)
     src = 8 * n_gm + 4 * (n * n + 1)
+    plane_f = (n * n / 2) * F + n * n * F
     return {
         "conv_kfwd": (A + src, (n * n / 2) * F),
-        "conv_jfwd": (A + B, n * n1 * F),
-        "conv_i": (2 * B + n1 ** 3 * pb, 2 * (2 * n * n1) * F + 2.0 * (2 * n * n1) * L),
-        "conv_jinv": (A + B, n * n1 * F),
+        "conv_jfwd": (A + B, n * n * F),
+        "conv_i": (2 * B + n1 ** 3 * pb, 2 * (2 * n * n) * F + 2.0 * (2 * n * n) * L),
+        "conv_jinv": (A + B, n * n * F),
         "conv_kinv": (A + n ** 3 * pb, (n * n / 2) * F),
-        # k and j fused per plane: A stays in shared memory
-        "conv_plane_fwd": (B + src, (n * n / 2) * F + n * n1 * F),
-        "conv_plane_inv": (B + n ** 3 * pb, (n * n / 2) * F + n * n1 * F),
+        # k and j fused per plane (one CTA, or a cluster): A stays on chip
+        "conv_plane_fwd": (B + src, plane_f),
+        "conv_plane_inv": (B + n ** 3 * pb, plane_f),
+        "conv_cplane_fwd": (B + src, plane_f),
+        "conv_cplane_inv": (B + n ** 3 * pb, plane_f),
     }
 
 

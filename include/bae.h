@@ -66,7 +66,7 @@ typedef struct bae_problem bae_problem;
 typedef struct bae_options {
     double tol;          /* relative residual ||b - A q|| / ||b||, default 1e-10 */
     int    max_iter;     /* total GMRES iterations (all cycles), default 500    */
-    int    restart;      /* GMRES restart length, default 200                   */
+    int    restart;      /* GMRES restart length, 1..1024, default 200          */
     int    precision;    /* BAE_FP64 (every apply native float64), BAE_DF64
                             (every apply double-float) or BAE_MIXED (float32
                             applies inside iterative refinement), default

@@ -397,11 +397,12 @@ struct RhsState {
     double est = 0.0;        // last residual estimate
 };
 
-// w[b] = A q[b] with q read at q + b q_stride + (*q_row) q_row_stride, for
-// items with active[b] != 0 (all device arrays; capturable in a graph)
+// v[b] = K q[b] on the grid with q read at q + b q_stride + (*q_row)
+// q_row_stride, for items with active[b] != 0 (all device arrays;
+// capturable in a graph); returns v [nb][N^3]
 template <typename T>
-void apply_rows(bae_problem* P, int nb, const double* q, long long q_stride, const int* q_row,
-                long long q_row_stride, const int* active, double* out) {
+out_t<T>* potential_rows(bae_problem* P, int nb, const double* q, long long q_stride, const int* q_row,
+                         long long q_row_stride, const int* active) {
     ConvArgs<T> a = conv_args<T>(P, nb);
     a.mode = SRC_DENSITY;
     a.q = q;
@@ -412,7 +413,15 @@ void apply_rows(bae_problem* P, int nb, const double* q, long long q_stride, con
     a.rec = P->geo.recipe();
     a.v = vbuf<T>(P, nb);
     conv_apply<T>(a, P->ctx->stream);
-    closure_gather<out_t<T>>(a.v, P->n3(), P->geo.gm, P->geo.partner, P->geo.t, (int)n_gm(P), nb, out, n_gm(P),
+    return a.v;
+}
+
+// w[b] = A q[b] = Phi K q[b] (the potential, then the closure gather)
+template <typename T>
+void apply_rows(bae_problem* P, int nb, const double* q, long long q_stride, const int* q_row,
+                long long q_row_stride, const int* active, double* out) {
+    out_t<T>* v = potential_rows<T>(P, nb, q, q_stride, q_row, q_row_stride, active);
+    closure_gather<out_t<T>>(v, P->n3(), P->geo.gm, P->geo.partner, P->geo.t, (int)n_gm(P), nb, out, n_gm(P),
                       P->ctx->stream, active);
 }
 
@@ -485,8 +494,18 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
     std::vector<int> ncols(nb), flg(nb);
     std::vector<double> est(nb);
 
+    // one step: v = K V[j] for the iterating RHS, then the Arnoldi passes
+    // (whose first pass gathers w = Phi v)
+    a.v_f32 = prec == BAE_FP32;
+    a.v_stride = P->n3();
+    a.gm = P->geo.gm;
+    a.partner = P->geo.partner;
+    a.t = P->geo.t;
     auto one_step = [&]() {
-        apply_rows_prec(P, prec, nb, a.V, (long long)(m + 1) * n, a.j, n, a.flag, a.w);
+        const long long qs = (long long)(m + 1) * n;
+        if (prec == BAE_FP32) a.v = potential_rows<float>(P, nb, a.V, qs, a.j, n, a.flag);
+        else if (prec == BAE_DF64) a.v = potential_rows<dsf>(P, nb, a.V, qs, a.j, n, a.flag);
+        else a.v = potential_rows<double>(P, nb, a.V, qs, a.j, n, a.flag);
         arn_step(a, st);
     };
     // size every buffer and set every kernel attribute the step needs before
@@ -604,7 +623,8 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
     BAE_REQUIRE(nb >= 1, BAE_ERR_INVALID_ARG, "nrhs must be >= 1");
     BAE_REQUIRE(f && g, BAE_ERR_INVALID_ARG, "f and g must not be null");
     BAE_REQUIRE(o.tol > 0 && std::isfinite(o.tol), BAE_ERR_INVALID_ARG, "tol must be positive");
-    BAE_REQUIRE(o.max_iter >= 1 && o.restart >= 1, BAE_ERR_INVALID_ARG, "max_iter and restart must be >= 1");
+    BAE_REQUIRE(o.max_iter >= 1 && o.restart >= 1 && o.restart <= 1024, BAE_ERR_INVALID_ARG,
+                "max_iter must be >= 1 and restart in [1, 1024]");
     BAE_REQUIRE(o.precision == BAE_FP64 || o.precision == BAE_MIXED || o.precision == BAE_DF64,
                 BAE_ERR_INVALID_ARG, "precision must be BAE_FP64, BAE_MIXED or BAE_DF64");
     BAE_REQUIRE(o.residual_precision == BAE_FP64 || o.residual_precision == BAE_DF64, BAE_ERR_INVALID_ARG,

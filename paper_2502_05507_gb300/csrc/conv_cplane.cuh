@@ -87,13 +87,12 @@ __global__ void __launch_bounds__(CPlaneGeo<T, L>::PT) k_cplane_fwd(ConvArgs<T> 
 #pragma unroll
                 for (int k1 = 0; k1 < R1; ++k1) z[t + q2 * R1 + R2 * k1] = v[q2 * R1 + k1];
             __syncthreads();
-            const T half = (T)0.5;
             if (act) {
-                for (int k = t; k <= N; k += R1) {
-                    const C zk = z[k];
-                    const C zr = z[(L - k) & (L - 1)];
-                    rows[(long long)jla * N1 + k] = cmake<C>((zk.x + zr.x) * half, (zk.y - zr.y) * half);
-                    rows[(long long)jlb * N1 + k] = cmake<C>((zk.y + zr.y) * half, (zr.x - zk.x) * half);
+                for (int k = t; k < N; k += R1) {
+                    C xa, xb;
+                    split_lines(z, k, L, xa, xb);
+                    rows[(long long)jla * N1 + k] = xa;
+                    rows[(long long)jlb * N1 + k] = xb;
                 }
             }
             __syncthreads();
@@ -106,7 +105,7 @@ __global__ void __launch_bounds__(CPlaneGeo<T, L>::PT) k_cplane_fwd(ConvArgs<T> 
         const C* part[G::CS];
 #pragma unroll
         for (int q = 0; q < G::CS; ++q) part[q] = cluster.map_shared_rank(rows, q);
-        const int cbeg = r * G::CW, cend = min(N1, cbeg + G::CW);
+        const int cbeg = r * G::CW, cend = cbeg + G::CW;
         for (int col0 = cbeg; col0 < cend; col0 += G::PW) {
             const int col = col0 + c;
             const bool ok = col < cend;
@@ -121,6 +120,7 @@ __global__ void __launch_bounds__(CPlaneGeo<T, L>::PT) k_cplane_fwd(ConvArgs<T> 
                 v[m] = (ok && m < HALF) ? part[owner][(long long)(n - owner * NR) * N1 + col] : cmake<C>((T)0.0, (T)0.0);
             }
             fft_n2k<L, false>(v, xch, c, R1 * G::PW, G::PW, t, a.tw);
+            if (col0 == 0) split_column0<L>(v, xch, c, t);
             if (ok) {
 #pragma unroll
                 for (int q2 = 0; q2 < Q; ++q2)
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(CPlaneGeo<T, L>::PT) k_cplane_inv(ConvArgs<T> 
         C* part[G::CS];
 #pragma unroll
         for (int q = 0; q < G::CS; ++q) part[q] = cluster.map_shared_rank(rows, q);
-        const int cbeg = r * G::CW, cend = min(N1, cbeg + G::CW);
+        const int cbeg = r * G::CW, cend = cbeg + G::CW;
         for (int col0 = cbeg; col0 < cend; col0 += G::PW) {
             const int col = col0 + c;
             const bool ok = col < cend;
@@ -165,7 +165,9 @@ __global__ void __launch_bounds__(CPlaneGeo<T, L>::PT) k_cplane_inv(ConvArgs<T> 
 #pragma unroll
                 for (int k1 = 0; k1 < R1; ++k1) {
                     const int k = t + q2 * R1 + R2 * k1;
-                    v[q2 * R1 + k1] = ok ? in[(long long)k * N1 + col] : cmake<C>((T)0.0, (T)0.0);
+                    C x = ok ? in[(long long)k * N1 + col] : cmake<C>((T)0.0, (T)0.0);
+                    if (col == 0) x = slot_merge(x, in[(long long)((L - k) & (L - 1)) * N1], k, N);
+                    v[q2 * R1 + k1] = x;
                 }
             fft_k2n<L, true>(v, xch, c, R1 * G::PW, G::PW, t, a.tw);
             if (ok) {
@@ -193,17 +195,10 @@ __global__ void __launch_bounds__(CPlaneGeo<T, L>::PT) k_cplane_inv(ConvArgs<T> 
 #pragma unroll
                 for (int k1 = 0; k1 < R1; ++k1) {
                     const int k = t + q2 * R1 + R2 * k1;
-                    C xa, xb;
-                    if (!act) {
-                        xa = cmake<C>((T)0.0, (T)0.0);
-                        xb = xa;
-                    } else if (k <= N) {
-                        xa = rows[(long long)jla * N1 + k];
-                        xb = rows[(long long)jlb * N1 + k];
-                        if (k == 0 || k == N) { xa.y = (T)0.0; xb.y = (T)0.0; }
-                    } else {
-                        xa = cconj(rows[(long long)jla * N1 + (L - k)]);
-                        xb = cconj(rows[(long long)jlb * N1 + (L - k)]);
+                    C xa = cmake<C>((T)0.0, (T)0.0), xb = xa;
+                    if (act) {
+                        xa = line_spectrum(rows + (long long)jla * N1, k, N);
+                        xb = line_spectrum(rows + (long long)jlb * N1, k, N);
                     }
                     v[q2 * R1 + k1] = cmake<C>(xa.x - xb.y, xa.y + xb.x);
                 }

@@ -59,6 +59,90 @@ template <typename T, int L> struct PlaneGeo {
     static constexpr bool FITS = SMEM <= 227 * 1024;
 };
 
+// ------------------------------------------------ packed Nyquist column
+// The k-spectrum of a real line is real at kk = 0 and at kk = N, so both
+// live in column 0 as X0 + i XN and every pass after the k transform runs
+// over N columns (not N + 1). X0 and XN are real along j, so after the j
+// transform Z = F0 + i FN with F0, FN Hermitian in the j frequency q; the
+// j pass separates them (two real transforms for the price of one complex
+// one) and stores, per slot s of column 0,
+//   s in (0, N): F0(s),  s in (N, 2N): FN(2N - s),  s = 0, N: Z(s) = F0 + i FN
+// so that the i pass sees independent pencils (the kk = 0 spectrum for
+// s < N, the kk = N spectrum for s > N) except at s = 0 and N, where it
+// splits F0 and FN by the Hermitian symmetry in the i frequency. The
+// inverse j pass merges the slots back into R0 + i RN.
+
+// (X_a[k], X_b[k]) for k in [0, N) of two real lines transformed together
+// as z = x_a + i x_b (natural order, length L), column 0 packed
+template <typename C>
+__device__ __forceinline__ void split_lines(const C* z, int k, int L, C& xa, C& xb) {
+    using T = decltype(xa.x);
+    if (k == 0) {
+        const C z0 = z[0], zn = z[L / 2];
+        xa = cmake<C>(z0.x, zn.x);
+        xb = cmake<C>(z0.y, zn.y);
+    } else {
+        const T half = (T)0.5;
+        const C zk = z[k], zr = z[L - k];
+        xa = cmake<C>((zk.x + zr.x) * half, (zk.y - zr.y) * half);
+        xb = cmake<C>((zk.y + zr.y) * half, (zr.x - zk.x) * half);
+    }
+}
+
+// X[k], k in [0, 2N), of a real line from its packed row (columns 0..N-1)
+template <typename C>
+__device__ __forceinline__ C line_spectrum(const C* row, int k, int N) {
+    using T = decltype(row[0].x);
+    if (k == 0) return cmake<C>(row[0].x, (T)0.0);
+    if (k == N) return cmake<C>(row[0].y, (T)0.0);
+    if (k < N) return row[k];
+    return cconj(row[2 * N - k]);
+}
+
+// slot k of column 0 after the forward j transform, from Z(k) and Z(2N - k)
+template <typename C>
+__device__ __forceinline__ C slot_split(C zk, C zr, int k, int N) {
+    using T = decltype(zk.x);
+    const T half = (T)0.5;
+    if (k == 0 || k == N) return zk;
+    if (k < N) return cmake<C>((zk.x + zr.x) * half, (zk.y - zr.y) * half);
+    return cmake<C>((zr.y + zk.y) * half, (zk.x - zr.x) * half);
+}
+
+// After the forward j transform of a column group (column c held by R1
+// threads t in k-layout, k = t + q R1 + R2 k1; the exchange buffer free),
+// replaces the outputs of column c == 0 by its slots. Every thread of the
+// CTA calls it (two barriers).
+template <int L, typename C>
+__device__ __forceinline__ void split_column0(C* v, C* xch, int c, int t) {
+    constexpr int R1 = Factors<L>::R1, R2 = Factors<L>::R2, Q = R2 / R1;
+    if (c == 0) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+#pragma unroll
+            for (int k1 = 0; k1 < R1; ++k1) xch[t + q * R1 + R2 * k1] = v[q * R1 + k1];
+    }
+    __syncthreads();
+    if (c == 0) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+#pragma unroll
+            for (int k1 = 0; k1 < R1; ++k1) {
+                const int k = t + q * R1 + R2 * k1;
+                v[q * R1 + k1] = slot_split(v[q * R1 + k1], xch[(L - k) & (L - 1)], k, L / 2);
+            }
+    }
+    __syncthreads();
+}
+
+// R0(k) + i RN(k) for the inverse j transform, from slots k and 2N - k
+template <typename C>
+__device__ __forceinline__ C slot_merge(C sk, C sr, int k, int N) {
+    if (k == 0 || k == N) return sk;
+    if (k < N) return cmake<C>(sk.x - sr.y, sk.y + sr.x);
+    return cmake<C>(sr.x + sk.y, sk.x - sr.y);
+}
+
 // ------------------------------ cluster plane passes (distributed shared memory)
 // When a plane does not fit one SM (float32 at N = 256, 16-byte types at
 // N >= 128), a cluster of CS CTAs holds it: CTA r keeps rows
@@ -83,7 +167,7 @@ template <typename T, int L> struct CPlaneGeo {
     static constexpr int PP = PT / R1;                // line pairs per round
     static constexpr int PW = PT / R1;                // columns per round
     static constexpr int ROUNDS = (NR / 2 + PP - 1) / PP;
-    static constexpr int CW = (N1 + CS - 1) / CS;     // columns per CTA
+    static constexpr int CW = N / CS;                 // columns per CTA (column 0 packs kk = N)
     static constexpr size_t XL = (size_t)PP * XS * sizeof(C);
     static constexpr size_t XC = (size_t)L * PW * sizeof(C);
     static constexpr size_t SMEM = ROWS + (XL > XC ? XL : XC);

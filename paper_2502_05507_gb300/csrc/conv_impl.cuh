@@ -113,12 +113,11 @@ __global__ void __launch_bounds__(Geo<T, L>::KT) k_kpass_fwd(ConvArgs<T> a) {
     __syncthreads();
     if (active) {
         C* A = a.A + (long long)b * N * N * N1;
-        const T half = (T)0.5;
-        for (int k = t; k <= N; k += R1) {
-            const C zk = z[k];
-            const C zr = z[(L - k) & (L - 1)];
-            A[la * N1 + k] = cmake<C>((zk.x + zr.x) * half, (zk.y - zr.y) * half);
-            A[lb * N1 + k] = cmake<C>((zk.y + zr.y) * half, (zr.x - zk.x) * half);
+        for (int k = t; k < N; k += R1) {
+            C xa, xb;
+            split_lines(z, k, L, xa, xb);
+            A[la * N1 + k] = xa;
+            A[lb * N1 + k] = xb;
         }
     }
 }
@@ -139,8 +138,9 @@ __global__ void __launch_bounds__(Geo<T, L>::CT) k_colpass(ConvArgs<T> a) {
     const int o = blockIdx.y;               // i (j passes) or jj (i pass)
     const int c = threadIdx.x % W;
     const int t = threadIdx.x / W;
-    const int col = blockIdx.x * W + c;     // kk
-    const bool ok = col < N1;
+    const int col = blockIdx.x * W + c;     // kk (column 0 holds kk = 0 and N)
+    const bool ok = col < N;
+    const bool col0 = blockIdx.x == 0;      // this CTA holds column 0 (c == 0)
 
     C* Ab = a.A + (long long)b * N * N * N1;
     C* Bb = a.B + (long long)b * N * (2 * N) * N1;
@@ -158,13 +158,15 @@ __global__ void __launch_bounds__(Geo<T, L>::CT) k_colpass(ConvArgs<T> a) {
     C v[R2];
     const C zero = cmake<C>((T)0, (T)0);
     if (MODE == COL_INV_J) {
-        // k-layout load of all L rows
+        // k-layout load of all L rows (column 0: merge slots k and L - k)
 #pragma unroll
         for (int q = 0; q < Q; ++q)
 #pragma unroll
             for (int k1 = 0; k1 < R1; ++k1) {
                 const int k = t + q * R1 + R2 * k1;
-                v[q * R1 + k1] = ok ? in[k * stride] : zero;
+                C x = ok ? in[k * stride] : zero;
+                if (col0 && c == 0) x = slot_merge(x, in[((L - k) & (L - 1)) * stride], k, N);
+                v[q * R1 + k1] = x;
             }
         fft_k2n<L, true>(v, xch, c, R1 * W, W, t, a.tw);
     } else {
@@ -178,6 +180,7 @@ __global__ void __launch_bounds__(Geo<T, L>::CT) k_colpass(ConvArgs<T> a) {
     }
 
     if (MODE == COL_FWD_J) {
+        if (col0) split_column0<L>(v, xch, c, t);   // column 0: separate F0 and FN
         if (ok) {
 #pragma unroll
             for (int q = 0; q < Q; ++q)
@@ -187,17 +190,57 @@ __global__ void __launch_bounds__(Geo<T, L>::CT) k_colpass(ConvArgs<T> a) {
         return;
     }
     if (MODE == COL_CONV_I) {
-        // times the real, even spectrum (octant fold), then back
+        // times the real, even spectrum (octant fold), then back. Column 0
+        // carries the kk = 0 spectrum in slots jj < N, the kk = N spectrum
+        // in slots jj > N, and both (packed) at jj = 0 and N.
         const int jj = o <= N ? o : L - o;
-        const T* g = a.ghat + (long long)jj * N1 + (ok ? col : 0);
+        const int gc = (col0 && c == 0 && o > N) ? N : (ok ? col : 0);
+        const T* g = a.ghat + (long long)jj * N1 + gc;
+        if (col0 && (o == 0 || o == N)) {   // y = F0 + i FN, both Hermitian in p
+            if (c == 0) {
 #pragma unroll
-        for (int q = 0; q < Q; ++q)
+                for (int q = 0; q < Q; ++q)
 #pragma unroll
-            for (int k1 = 0; k1 < R1; ++k1) {
-                const int k = t + q * R1 + R2 * k1;
-                const int ii = k <= N ? k : L - k;
-                v[q * R1 + k1] = cscale(v[q * R1 + k1], g[(long long)ii * N1 * N1]);
+                    for (int k1 = 0; k1 < R1; ++k1) xch[t + q * R1 + R2 * k1] = v[q * R1 + k1];
             }
+            __syncthreads();
+            if (c == 0) {
+                const T half = (T)0.5;
+#pragma unroll
+                for (int q = 0; q < Q; ++q)
+#pragma unroll
+                    for (int k1 = 0; k1 < R1; ++k1) {
+                        const int k = t + q * R1 + R2 * k1;
+                        const int ii = k <= N ? k : L - k;
+                        const T g0 = g[(long long)ii * N1 * N1], gn = g[(long long)ii * N1 * N1 + N];
+                        // (g0 + gN) y(p) / 2 + (g0 - gN) conj y(-p) / 2
+                        const C yr = cconj(xch[(L - k) & (L - 1)]);
+                        const C y = v[q * R1 + k1];
+                        const T sp = (g0 + gn) * half, sm = (g0 - gn) * half;
+                        v[q * R1 + k1] = cmake<C>(y.x * sp + yr.x * sm, y.y * sp + yr.y * sm);
+                    }
+            }
+            __syncthreads();
+            if (c != 0) {
+#pragma unroll
+                for (int q = 0; q < Q; ++q)
+#pragma unroll
+                    for (int k1 = 0; k1 < R1; ++k1) {
+                        const int k = t + q * R1 + R2 * k1;
+                        const int ii = k <= N ? k : L - k;
+                        v[q * R1 + k1] = cscale(v[q * R1 + k1], g[(long long)ii * N1 * N1]);
+                    }
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < Q; ++q)
+#pragma unroll
+                for (int k1 = 0; k1 < R1; ++k1) {
+                    const int k = t + q * R1 + R2 * k1;
+                    const int ii = k <= N ? k : L - k;
+                    v[q * R1 + k1] = cscale(v[q * R1 + k1], g[(long long)ii * N1 * N1]);
+                }
+        }
         fft_k2n<L, true>(v, xch, c, R1 * W, W, t, a.tw);
     }
     // n-layout store of the first N rows
@@ -236,15 +279,8 @@ __global__ void __launch_bounds__(Geo<T, L>::KT) k_kpass_inv(ConvArgs<T> a) {
             const int k = t + q * R1 + R2 * k1;
             C z = cmake<C>((T)0, (T)0);
             if (active) {
-                C xa, xb;
-                if (k <= N) {
-                    xa = A[la * N1 + k];
-                    xb = A[lb * N1 + k];
-                    if (k == 0 || k == N) { xa.y = (T)0; xb.y = (T)0; }
-                } else {
-                    xa = cconj(A[la * N1 + (L - k)]);
-                    xb = cconj(A[lb * N1 + (L - k)]);
-                }
+                const C xa = line_spectrum(A + la * N1, k, N);
+                const C xb = line_spectrum(A + lb * N1, k, N);
                 z = cmake<C>(xa.x - xb.y, xa.y + xb.x);   // xa + i xb
             }
             v[q * R1 + k1] = z;
@@ -342,13 +378,12 @@ __global__ void __launch_bounds__(512) k_plane_fwd(ConvArgs<T> a) {
 #pragma unroll
                 for (int k1 = 0; k1 < R1; ++k1) z[t + q2 * R1 + R2 * k1] = v[q2 * R1 + k1];
             __syncthreads();
-            const T half = (T)0.5;
             if (act) {
-                for (int k = t; k <= N; k += R1) {
-                    const C zk = z[k];
-                    const C zr = z[(L - k) & (L - 1)];
-                    plane[(long long)ja * N1 + k] = cmake<C>((zk.x + zr.x) * half, (zk.y - zr.y) * half);
-                    plane[(long long)jb * N1 + k] = cmake<C>((zk.y + zr.y) * half, (zr.x - zk.x) * half);
+                for (int k = t; k < N; k += R1) {
+                    C xa, xb;
+                    split_lines(z, k, L, xa, xb);
+                    plane[(long long)ja * N1 + k] = xa;
+                    plane[(long long)jb * N1 + k] = xb;
                 }
             }
             __syncthreads();
@@ -358,9 +393,9 @@ __global__ void __launch_bounds__(512) k_plane_fwd(ConvArgs<T> a) {
     {
         const int c = threadIdx.x % G::PW, t = threadIdx.x / G::PW;
         C* out = a.B + (long long)b * N * (2 * N) * N1 + (long long)i * (2 * N) * N1;
-        for (int col0 = 0; col0 < N1; col0 += G::PW) {
+        for (int col0 = 0; col0 < N; col0 += G::PW) {
             const int col = col0 + c;
-            const bool ok = col < N1;
+            const bool ok = col < N;
             C v[R2];
 #pragma unroll
             for (int m = 0; m < R2; ++m) {
@@ -368,6 +403,7 @@ __global__ void __launch_bounds__(512) k_plane_fwd(ConvArgs<T> a) {
                 v[m] = (ok && m < R2 / 2) ? plane[(long long)n * N1 + col] : cmake<C>((T)0.0, (T)0.0);
             }
             fft_n2k<L, false>(v, xch, c, R1 * G::PW, G::PW, t, a.tw);
+            if (col0 == 0) split_column0<L>(v, xch, c, t);
             if (ok) {
 #pragma unroll
                 for (int q2 = 0; q2 < Q; ++q2)
@@ -395,16 +431,18 @@ __global__ void __launch_bounds__(512) k_plane_inv(ConvArgs<T> a) {
     {
         const int c = threadIdx.x % G::PW, t = threadIdx.x / G::PW;
         const C* in = a.B + (long long)b * N * (2 * N) * N1 + (long long)i * (2 * N) * N1;
-        for (int col0 = 0; col0 < N1; col0 += G::PW) {
+        for (int col0 = 0; col0 < N; col0 += G::PW) {
             const int col = col0 + c;
-            const bool ok = col < N1;
+            const bool ok = col < N;
             C v[R2];
 #pragma unroll
             for (int q2 = 0; q2 < Q; ++q2)
 #pragma unroll
                 for (int k1 = 0; k1 < R1; ++k1) {
                     const int k = t + q2 * R1 + R2 * k1;
-                    v[q2 * R1 + k1] = ok ? in[(long long)k * N1 + col] : cmake<C>((T)0.0, (T)0.0);
+                    C x = ok ? in[(long long)k * N1 + col] : cmake<C>((T)0.0, (T)0.0);
+                    if (col == 0) x = slot_merge(x, in[(long long)((L - k) & (L - 1)) * N1], k, N);
+                    v[q2 * R1 + k1] = x;
                 }
             fft_k2n<L, true>(v, xch, c, R1 * G::PW, G::PW, t, a.tw);
             if (ok) {
@@ -432,17 +470,10 @@ __global__ void __launch_bounds__(512) k_plane_inv(ConvArgs<T> a) {
 #pragma unroll
                 for (int k1 = 0; k1 < R1; ++k1) {
                     const int k = t + q2 * R1 + R2 * k1;
-                    C xa, xb;
-                    if (!act) {
-                        xa = cmake<C>((T)0.0, (T)0.0);
-                        xb = xa;
-                    } else if (k <= N) {
-                        xa = plane[(long long)ja * N1 + k];
-                        xb = plane[(long long)jb * N1 + k];
-                        if (k == 0 || k == N) { xa.y = (T)0.0; xb.y = (T)0.0; }
-                    } else {
-                        xa = cconj(plane[(long long)ja * N1 + (L - k)]);
-                        xb = cconj(plane[(long long)jb * N1 + (L - k)]);
+                    C xa = cmake<C>((T)0.0, (T)0.0), xb = xa;
+                    if (act) {
+                        xa = line_spectrum(plane + (long long)ja * N1, k, N);
+                        xb = line_spectrum(plane + (long long)jb * N1, k, N);
                     }
                     v[q2 * R1 + k1] = cmake<C>(xa.x - xb.y, xa.y + xb.x);
                 }
@@ -497,7 +528,7 @@ void launch_sched(const ConvArgs<T>& a, cudaStream_t st, int sched) {
     const size_t smem_c = (size_t)L * G::W * sizeof(C);
     const int nb = a.nbatch;
     const dim3 gk(ceil_div((long long)N * N / 2, G::P), 1, nb);
-    const int ncolblk = ceil_div(N + 1, G::W);
+    const int ncolblk = ceil_div(N, G::W);   // column 0 also holds kk = N
     if (sched == SCHED_PLANE) {
         if constexpr (PG::FITS)
             BAE_LAUNCH(kname<T>("conv_plane_fwd.f32", "conv_plane_fwd.f64", "conv_plane_fwd.df64"), st,

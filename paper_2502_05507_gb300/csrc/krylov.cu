@@ -168,9 +168,11 @@ __device__ __forceinline__ void reduce_rows(const double* part, int nch, int col
 // (warp q takes rows q, q+8, ...; four rows per loop trip so that eight
 // loads are in flight), partial sums combined in warp order. Indices past
 // the end of the vector are clamped (their results are never stored).
-// Leaves the new chunk in s_w (zero past the end).
+// Leaves the new chunk in s_w (zero past the end) and stores it into w, or,
+// when dst is set, stores scale times it into dst instead.
 __device__ __forceinline__ void chunk_update(const double* Vb, long long n, long long r0, int cols, const double* s_h,
-                                             double* w, double* s_acc, double* s_w) {
+                                             double* w, double* s_acc, double* s_w, double* dst = nullptr,
+                                             double scale = 1.0) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long ra = min(r0 + lane, n - 1), rb = min(r0 + lane + 32, n - 1);
     double a0 = 0.0, a1 = 0.0;
@@ -201,7 +203,8 @@ __device__ __forceinline__ void chunk_update(const double* Vb, long long n, long
         double val = 0.0;
         if (r < n) {
             val = w[r] - sub;
-            w[r] = val;
+            if (dst) dst[r] = val * scale;
+            else w[r] = val;
         }
         s_w[threadIdx.x] = val;
     }
@@ -241,8 +244,10 @@ __device__ __forceinline__ void chunk_dots(const double* Vb, long long n, long l
     }
 }
 
-// pass 1: h1 = V^T w over rows i <= j
-__global__ void __launch_bounds__(256) k_arn_dots(Arnoldi a) {
+// pass 1: w = A V[j] by the closure gather of the potential v (the same
+// expression as closure_gather), then h1 = V^T w over rows i <= j
+template <typename VT>
+__global__ void __launch_bounds__(256) k_arn_gather_dots(Arnoldi a) {
     __shared__ double s_w[ACH];
     __shared__ int s_last;
     const int b = blockIdx.y;
@@ -250,8 +255,18 @@ __global__ void __launch_bounds__(256) k_arn_dots(Arnoldi a) {
     const int cols = a.j[b] + 1;
     const int c = blockIdx.x;
     const long long r0 = (long long)c * ACH;
-    const double* w = a.w + (long long)b * a.n;
-    if (threadIdx.x < ACH) s_w[threadIdx.x] = (r0 + threadIdx.x < a.n) ? w[r0 + threadIdx.x] : 0.0;
+    double* w = a.w + (long long)b * a.n;
+    if (threadIdx.x < ACH) {
+        const long long r = r0 + threadIdx.x;
+        double val = 0.0;
+        if (r < a.n) {
+            const VT* vb = static_cast<const VT*>(a.v) + b * a.v_stride;
+            const double tr = a.t[r];
+            val = tr * (double)vb[a.gm[r]] + (1.0 - tr) * (double)vb[a.partner[r]];
+            w[r] = val;
+        }
+        s_w[threadIdx.x] = val;
+    }
     __syncthreads();
     double* part = a.part + (long long)b * (a.m + 2) * a.nchunk;
     const double* Vb = a.V + (long long)b * (a.m + 1) * a.n;
@@ -262,39 +277,21 @@ __global__ void __launch_bounds__(256) k_arn_dots(Arnoldi a) {
     }
 }
 
-// pass 2: w -= V h1, then h2 = V^T w; hcol = h1 + h2, h1 <- h2
+// pass 2: w -= V h1, then h2 = V^T w and ||w||^2. The last block forms
+// hcol = h1 + h2 and the new subdiagonal entry ||w - V h2|| by the
+// Pythagorean identity ||w||^2 - ||h2||^2 (V orthonormal), applies the
+// Givens rotations (staged in shared memory), updates the residual
+// estimate and the flag, sets inv = 1 / ||w - V h2|| and advances j.
 __global__ void __launch_bounds__(256) k_arn_update_dots(Arnoldi a) {
     extern __shared__ double s_dyn[];
-    double* s_h = s_dyn;                 // m + 1
+    const int m = a.m;
+    double* s_h = s_dyn;                 // m + 1: h1
+    double* s_col = s_dyn + (m + 1);     // m + 2: the new Hessenberg column
+    double* s_cs = s_col + (m + 2);      // m
+    double* s_sn = s_cs + m;             // m
     __shared__ double s_acc[8 * ACH];
     __shared__ double s_w[ACH];
-    __shared__ int s_last;
-    const int b = blockIdx.y;
-    if (!a.flag[b]) return;
-    const int cols = a.j[b] + 1;
-    const int c = blockIdx.x;
-    const long long r0 = (long long)c * ACH;
-    double* h1 = a.h1 + (long long)b * (a.m + 1);
-    for (int i = threadIdx.x; i < cols; i += blockDim.x) s_h[i] = h1[i];
-    __syncthreads();
-    const double* Vb = a.V + (long long)b * (a.m + 1) * a.n;
-    chunk_update(Vb, a.n, r0, cols, s_h, a.w + (long long)b * a.n, s_acc, s_w);
-    double* part = a.part + (long long)b * (a.m + 2) * a.nchunk;
-    chunk_dots(Vb, a.n, r0, cols, s_w, part, a.nchunk, c);
-    if (last_block(a.ctr + 3 * b + 1, gridDim.x, &s_last)) {
-        // hcol = h1 + h2 (h1 still in s_h), then h1 <- h2
-        reduce_rows(part, a.nchunk, cols, a.hcol + (long long)b * (a.m + 1), h1, s_h);
-        if (threadIdx.x == 0) a.ctr[3 * b + 1] = 0;
-    }
-}
-
-// pass 3: w -= V h2, ||w||; the last block applies the Givens rotations,
-// updates the residual estimate and the flag, and advances j
-__global__ void __launch_bounds__(256) k_arn_update_norm(Arnoldi a) {
-    extern __shared__ double s_dyn[];
-    double* s_h = s_dyn;
-    __shared__ double s_acc[8 * ACH];
-    __shared__ double s_w[ACH];
+    __shared__ double s_n2;
     __shared__ int s_last;
     const int b = blockIdx.y;
     if (!a.flag[b]) return;
@@ -302,48 +299,63 @@ __global__ void __launch_bounds__(256) k_arn_update_norm(Arnoldi a) {
     const int cols = j + 1;
     const int c = blockIdx.x;
     const long long r0 = (long long)c * ACH;
-    const double* h2 = a.h1 + (long long)b * (a.m + 1);
-    for (int i = threadIdx.x; i < cols; i += blockDim.x) s_h[i] = h2[i];
+    double* h1 = a.h1 + (long long)b * (m + 1);
+    for (int i = threadIdx.x; i < cols; i += blockDim.x) s_h[i] = h1[i];
     __syncthreads();
-    const double* Vb = a.V + (long long)b * (a.m + 1) * a.n;
+    const double* Vb = a.V + (long long)b * (m + 1) * a.n;
     chunk_update(Vb, a.n, r0, cols, s_h, a.w + (long long)b * a.n, s_acc, s_w);
-    double* part = a.part + (long long)b * (a.m + 2) * a.nchunk;
-    if (threadIdx.x < 32) {
-        double acc = s_w[threadIdx.x] * s_w[threadIdx.x] + s_w[threadIdx.x + 32] * s_w[threadIdx.x + 32];
+    double* part = a.part + (long long)b * (m + 2) * a.nchunk;
+    chunk_dots(Vb, a.n, r0, cols, s_w, part, a.nchunk, c);
+    if (threadIdx.x >= 224) {   // the last warp: ||w||^2 over the chunk
+        const int l = threadIdx.x - 224;
+        double acc = s_w[l] * s_w[l] + s_w[l + 32] * s_w[l + 32];
         acc = warp_sum(acc);
-        if (threadIdx.x == 0) part[(long long)(a.m + 1) * a.nchunk + c] = acc;
+        if (l == 0) part[(long long)(m + 1) * a.nchunk + c] = acc;
     }
-    if (last_block(a.ctr + 3 * b + 2, gridDim.x, &s_last)) {
-        __shared__ double s_n2;
+    if (last_block(a.ctr + 3 * b + 1, gridDim.x, &s_last)) {
+        double* hc = a.hcol + (long long)b * (m + 1);
+        // hcol = h1 + h2 (h1 still in s_h), then h1 <- h2
+        reduce_rows(part, a.nchunk, cols, hc, h1, s_h);
         if (threadIdx.x < 32) {
             double acc = 0.0;
-            for (int q = threadIdx.x; q < a.nchunk; q += 32) acc += __ldcg(part + (long long)(a.m + 1) * a.nchunk + q);
+            for (int q = threadIdx.x; q < a.nchunk; q += 32) acc += __ldcg(part + (long long)(m + 1) * a.nchunk + q);
             acc = warp_sum(acc);
             if (threadIdx.x == 0) s_n2 = acc;
         }
         __syncthreads();
+        double* cs = a.cs + (long long)b * m;
+        double* sn = a.sn + (long long)b * m;
+        for (int i = threadIdx.x; i <= j; i += blockDim.x) s_col[i] = __ldcg(hc + i);
+        for (int i = threadIdx.x; i < j; i += blockDim.x) {
+            s_cs[i] = cs[i];
+            s_sn[i] = sn[i];
+        }
+        if (threadIdx.x < 32) {   // ||h2||^2 in a fixed order
+            double acc = 0.0;
+            for (int i = threadIdx.x; i <= j; i += 32) {
+                const double x = __ldcg(h1 + i);
+                acc += x * x;
+            }
+            acc = warp_sum(acc);
+            if (threadIdx.x == 0) s_n2 = fmax(s_n2 - acc, 0.0);
+        }
+        __syncthreads();
         if (threadIdx.x == 0) {
             const double hn = sqrt(s_n2);
-            const int m = a.m;
-            double* col = a.H + ((long long)b * m + j) * (m + 1);
-            const double* hc = a.hcol + (long long)b * (m + 1);
-            double* cs = a.cs + (long long)b * m;
-            double* sn = a.sn + (long long)b * m;
             double* g = a.g + (long long)b * (m + 1);
-            for (int i = 0; i <= j; ++i) col[i] = hc[i];
-            col[j + 1] = hn;
+            s_col[j + 1] = hn;
             for (int i = 0; i < j; ++i) {
-                const double x0 = col[i], x1 = col[i + 1];
-                col[i] = cs[i] * x0 + sn[i] * x1;
-                col[i + 1] = -sn[i] * x0 + cs[i] * x1;
+                const double x0 = s_col[i], x1 = s_col[i + 1];
+                s_col[i] = s_cs[i] * x0 + s_sn[i] * x1;
+                s_col[i + 1] = -s_sn[i] * x0 + s_cs[i] * x1;
             }
-            const double rr = hypot(col[j], col[j + 1]);
-            const double cj = rr > 0.0 ? col[j] / rr : 1.0;
-            const double sj = rr > 0.0 ? col[j + 1] / rr : 0.0;
+            const double rr = hypot(s_col[j], s_col[j + 1]);
+            const double cj = rr > 0.0 ? s_col[j] / rr : 1.0;
+            const double sj = rr > 0.0 ? s_col[j + 1] / rr : 0.0;
             cs[j] = cj;
             sn[j] = sj;
-            col[j] = rr;
-            col[j + 1] = 0.0;
+            s_col[j] = rr;
+            s_col[j + 1] = 0.0;
             g[j + 1] = -sj * g[j];
             g[j] = cj * g[j];
             const double e = fabs(g[j + 1]);
@@ -352,21 +364,32 @@ __global__ void __launch_bounds__(256) k_arn_update_norm(Arnoldi a) {
             a.inv[b] = hn > 0.0 ? 1.0 / hn : 0.0;
             a.flag[b] = (e > a.target[b] && hn > 0.0 && j + 1 < m) ? 1 : 0;
             a.j[b] = j + 1;   // every block of this RHS has read j already
-            a.ctr[3 * b + 2] = 0;
+            a.ctr[3 * b + 1] = 0;
         }
+        __syncthreads();
+        double* col = a.H + ((long long)b * m + j) * (m + 1);
+        for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) col[i] = s_col[i];
     }
 }
 
-// V[b][j] = w[b] / ||w[b]|| (j already advanced)
-__global__ void k_arn_next(Arnoldi a) {
+// pass 3: V[j] = (w - V h2) / ||w - V h2|| with j already advanced (w itself
+// is not written back: the next step's gather replaces it)
+__global__ void __launch_bounds__(256) k_arn_update_next(Arnoldi a) {
+    extern __shared__ double s_dyn[];
+    double* s_h = s_dyn;
+    __shared__ double s_acc[8 * ACH];
+    __shared__ double s_w[ACH];
     const int b = blockIdx.y;
     if (!a.flag[b]) return;
     const int j = a.j[b];
-    const double s = a.inv[b];
-    const double* w = a.w + (long long)b * a.n;
-    double* v = a.V + ((long long)b * (a.m + 1) + j) * a.n;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.n; i += (long long)gridDim.x * blockDim.x)
-        v[i] = w[i] * s;
+    const int cols = j;   // rows 0 .. j-1: the basis before this step's vector
+    const int c = blockIdx.x;
+    const long long r0 = (long long)c * ACH;
+    const double* h2 = a.h1 + (long long)b * (a.m + 1);
+    for (int i = threadIdx.x; i < cols; i += blockDim.x) s_h[i] = h2[i];
+    __syncthreads();
+    double* Vb = a.V + (long long)b * (a.m + 1) * a.n;
+    chunk_update(Vb, a.n, r0, cols, s_h, a.w + (long long)b * a.n, s_acc, s_w, Vb + (long long)j * a.n, a.inv[b]);
 }
 
 // y = R^{-1} g, one warp per RHS (column-oriented back substitution)
@@ -403,11 +426,16 @@ void arn_init(const Arnoldi& a, const double* r, const double* nrm2, const int* 
 int arnoldi_chunks(int n) { return ceil_div(n, ACH); }
 
 void arn_step(const Arnoldi& a, cudaStream_t st) {
-    const size_t sh = (size_t)(a.m + 1) * sizeof(double);
-    BAE_LAUNCH("k_arn_dots", st, k_arn_dots<<<dim3(a.nchunk, a.nb), 256, 0, st>>>(a));
-    BAE_LAUNCH("k_arn_update_dots", st, k_arn_update_dots<<<dim3(a.nchunk, a.nb), 256, sh, st>>>(a));
-    BAE_LAUNCH("k_arn_update_norm", st, k_arn_update_norm<<<dim3(a.nchunk, a.nb), 256, sh, st>>>(a));
-    BAE_LAUNCH("k_arn_next", st, k_arn_next<<<dim3(blocks_for(a.n), a.nb), 256, 0, st>>>(a));
+    BAE_REQUIRE(a.v && a.gm && a.partner && a.t, BAE_ERR_INVALID_ARG, "arn_step: gather inputs not set");
+    const size_t sh_h = (size_t)(a.m + 1) * sizeof(double);
+    const size_t sh_g = (size_t)(4 * a.m + 3) * sizeof(double);
+    const dim3 grid(a.nchunk, a.nb);
+    if (a.v_f32)
+        BAE_LAUNCH("k_arn_gather_dots.f32", st, k_arn_gather_dots<float><<<grid, 256, 0, st>>>(a));
+    else
+        BAE_LAUNCH("k_arn_gather_dots.f64", st, k_arn_gather_dots<double><<<grid, 256, 0, st>>>(a));
+    BAE_LAUNCH("k_arn_update_dots", st, k_arn_update_dots<<<grid, 256, sh_g, st>>>(a));
+    BAE_LAUNCH("k_arn_update_next", st, k_arn_update_next<<<grid, 256, sh_h, st>>>(a));
 }
 
 void arn_finish(const Arnoldi& a, double* x, int maxcols, cudaStream_t st) {

@@ -52,6 +52,15 @@ struct Arnoldi {
     int* ncols = nullptr;       // [nb] basis vectors used this cycle
     unsigned int* ctr = nullptr;  // [nb][3] last-block counters (self-resetting)
     int* j = nullptr;           // [nb] current step of each RHS
+    // w = A V[j] is formed inside the first projection pass from the
+    // potential v [nb][v_stride] (float32 or float64) by the closure gather
+    // w[r] = t[r] v[gm[r]] + (1 - t[r]) v[partner[r]] (eq. [double_bae])
+    const void* v = nullptr;
+    bool v_f32 = false;
+    long long v_stride = 0;
+    const int* gm = nullptr;
+    const int* partner = nullptr;
+    const double* t = nullptr;
 };
 
 // number of vector chunks (CTAs per RHS) of the Arnoldi passes
@@ -60,7 +69,9 @@ int arnoldi_chunks(int n);
 // Start of a cycle: r [nb][n] residuals with squared norms nrm2[b]; RHS with
 // member[b] != 0 and sqrt(nrm2) > target start iterating (V[b][0] = r/beta).
 void arn_init(const Arnoldi& a, const double* r, const double* nrm2, const int* member, cudaStream_t st);
-// One Arnoldi step after w = A V[j] (CGS2, Givens, j++, next basis vector).
+// One Arnoldi step after the potential v = K V[j] (gather into w = A V[j],
+// CGS2 with the norm of the reorthogonalised vector from the Pythagorean
+// identity, Givens, j++, next basis vector): three kernels.
 void arn_step(const Arnoldi& a, cudaStream_t st);
 // End of a cycle: y = R^{-1} g for every RHS with ncols > 0, x += V y.
 void arn_finish(const Arnoldi& a, double* x, int maxcols, cudaStream_t st);
