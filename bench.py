@@ -135,6 +135,16 @@ DF64_OPS_PER_FLOP = 14.8
 FP32_INST_PEAK_T = 35.1
 
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
+# the default workload's convolution kernels, from one ncu capture of the
+# current kernels (profiles/conv_i_traffic_torus_N128.md); a kernel changed
+# since its capture must be dropped from this table (its traffic is then
+# reported as null)
+NCU_TRAFFIC_TORUS128 = {
+    "conv_i.f32": 42.43e6,
+}
+
+
 def roofline_for(name, ms_total, launches, n_gm, hbm, hbm_kind):
     base, _, prec = name.partition(".")
     model = kernel_model(N, 4 if prec == "f32" else 8, n_gm)
@@ -155,7 +165,8 @@ def roofline_for(name, ms_total, launches, n_gm, hbm, hbm_kind):
                 "us_per_launch": t * 1e6, "algorithmic_flops": flops}
     a = nbytes / t / 1e9
     return {"kernel": name, "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
-            "traffic": None, "peak_kind": hbm_kind + " HBM copy bandwidth", "us_per_launch": t * 1e6,
+            "traffic": NCU_TRAFFIC_TORUS128.get(name) if N == 128 else None,
+            "peak_kind": hbm_kind + " HBM copy bandwidth", "us_per_launch": t * 1e6,
             "algorithmic_bytes": nbytes}
 
 
