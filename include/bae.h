@@ -72,7 +72,8 @@ typedef struct bae_options {
                             applies inside iterative refinement), default
                             BAE_FP64                                         */
     int    max_refine;   /* outer refinement steps for BAE_MIXED, default 8     */
-    double inner_tol;    /* inner float32 GMRES reduction per step, default 1e-5 */
+    double inner_tol;    /* inner float32 GMRES reduction per step, default 1e-5;
+                            the step that can reach tol aims at 0.3 tol ||b|| */
     int    use_graphs;   /* 1: each Arnoldi step (apply, CGS2, Givens) is captured
                             once as a CUDA graph and replayed; 0: launched
                             kernel by kernel (same kernels, for per-kernel

@@ -741,8 +741,15 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
             if (act.empty() || iters_left <= 0) break;
             std::vector<RhsState> Si(nb);
             for (int b : act) {
-                const double rn = std::sqrt(rn2[b]);
-                Si[b].target = std::max(o.inner_tol * rn, 0.3 * o.tol * std::sqrt(bn2[b]));
+                // reduce the residual by inner_tol; when that lands within ten
+                // times the outer target, aim straight at 0.3 tol ||b|| so that
+                // this is the last step (no further float64-accurate residual
+                // and restart); the float32 apply error, ~1e-7 of |A d|, stays
+                // far below that
+                const double rn = std::sqrt(rn2[b]), floor_b = 0.3 * o.tol * std::sqrt(bn2[b]);
+                double tgt = o.inner_tol * rn;
+                if (tgt <= 10.0 * o.tol * std::sqrt(bn2[b])) tgt = floor_b;
+                Si[b].target = std::max(tgt, floor_b);
             }
             for (int b = 0; b < nb; ++b)
                 if (std::find(act.begin(), act.end(), b) == act.end()) Si[b].converged = true;
