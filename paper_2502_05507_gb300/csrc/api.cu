@@ -142,6 +142,7 @@ struct Workspace {
     Grow<double> arnH, arnCS, arnG, arnY, arnScal;
     Grow<int> active, arnI;
     Grow<unsigned int> arnCtr;
+    Grow<unsigned long long> arnBar;
     Grow<double> in_f, in_g, out_q, out_u;    // staging of host arguments
     void set_stream(cudaStream_t st) {
         Grow<double>* ds[] = {&v64, &up, &vstage, &V, &w, &partial, &h, &hsave, &x, &r, &bvec, &tmp,
@@ -153,6 +154,7 @@ struct Workspace {
         v32.st = st;
         active.st = arnI.st = st;
         arnCtr.st = st;
+        arnBar.st = st;
     }
 };
 
@@ -459,17 +461,22 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
     a.sn = a.cs + (long long)nb * m;
     a.g = ws.arnG.need((long long)nb * (m + 1));
     a.y = ws.arnY.need((long long)nb * m);
-    double* scal = ws.arnScal.need((long long)nb * 4);
+    double* scal = ws.arnScal.need((long long)nb * 5);
     a.est = scal;
     a.target = scal + nb;
     a.inv = scal + 2 * nb;
     double* nrm2 = scal + 3 * nb;
-    int* ibuf = ws.arnI.need((long long)nb * 4);
+    int* ibuf = ws.arnI.need((long long)nb * 4 + 1);
     a.flag = ibuf;
     a.ncols = ibuf + nb;
     int* member = ibuf + 2 * nb;
     a.j = ibuf + 3 * nb;
     a.ctr = reinterpret_cast<unsigned int*>(ws.arnCtr.need((long long)nb * 3));
+    // the fused cooperative step where the device can place it
+    a.coop_grid = arn_coop_grid(n, nb, m);
+    a.bar = ws.arnBar.need(1);
+    a.err = ibuf + 4 * nb;
+    a.n2 = scal + 4 * nb;
     double* r = ws.r.need((long long)nb * n);
     double* tmp = ws.tmp.need((long long)nb * n);
     double* npart = ws.n2.need((long long)nb * krylov_chunks(n) + nb);
@@ -486,6 +493,8 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
     BAE_CUDA(cudaMemcpyAsync(d_all, all.data(), nb * sizeof(int), cudaMemcpyHostToDevice, st));
     BAE_CUDA(cudaMemcpyAsync(a.target, tgt.data(), nb * sizeof(double), cudaMemcpyHostToDevice, st));
     BAE_CUDA(cudaMemsetAsync(a.ctr, 0, (size_t)nb * 3 * sizeof(unsigned int), st));
+    BAE_CUDA(cudaMemsetAsync(a.bar, 0, sizeof(unsigned long long), st));
+    BAE_CUDA(cudaMemsetAsync(a.err, 0, sizeof(int), st));
     int* hflag = P->ctx->pinned_flags(nb);
     cudaEvent_t ev[2] = {P->ctx->poll_ev[0], P->ctx->poll_ev[1]};
     cudaGraphExec_t exec = nullptr;
@@ -607,6 +616,12 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
         throw;
     }
     if (exec) cudaGraphExecDestroy(exec);
+    if (a.coop_grid > 0) {
+        int err = 0;
+        BAE_CUDA(cudaMemcpyAsync(&err, a.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        BAE_CUDA(cudaStreamSynchronize(st));
+        BAE_REQUIRE(err == 0, BAE_ERR_CUDA, "GMRES: a grid barrier of the fused Arnoldi step timed out");
+    }
 }
 
 // ------------------------------------------------------------ full solve

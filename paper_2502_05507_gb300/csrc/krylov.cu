@@ -1,4 +1,7 @@
 // Batched GMRES vector kernels with fixed-order reductions (see krylov.cuh).
+#include <algorithm>
+#include <cstdlib>
+
 #include "krylov.cuh"
 
 namespace bae {
@@ -392,6 +395,224 @@ __global__ void __launch_bounds__(256) k_arn_update_next(Arnoldi a) {
     chunk_update(Vb, a.n, r0, cols, s_h, a.w + (long long)b * a.n, s_acc, s_w, Vb + (long long)j * a.n, a.inv[b]);
 }
 
+// ------------------------------------------------ fused cooperative step
+// The three passes above and their last-CTA reductions as one cooperative
+// launch: the CTAs (all resident at once) meet at four grid barriers, and
+// the reductions are spread over all warps instead of one CTA. The sums use
+// the same partition and order as the three-kernel step, so both give
+// bit-identical results.
+constexpr int COOP_MAX_NB = 64;
+constexpr long long BAR_SPIN_LIMIT = 1LL << 22;   // about half a second of waiting
+
+// All CTAs of the grid wait here until every CTA has arrived. The counter
+// only grows (by G per barrier), so the k-th barrier of a CTA completes when
+// it reaches the next multiple of G. A wait that runs out sets *err and
+// returns (the results are then wrong, and the host reports the error).
+__device__ __forceinline__ void grid_barrier(unsigned long long* ctr, unsigned long long G, int* err) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned long long old = atomicAdd(ctr, 1ull);
+        const unsigned long long target = (old / G + 1) * G;
+        long long spins = 0;
+        while (*reinterpret_cast<volatile unsigned long long*>(ctr) < target) {
+            if (++spins > BAR_SPIN_LIMIT) {
+                atomicOr(err, 1);
+                break;
+            }
+            __nanosleep(100);
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// out[b][i] = sum over chunks of part[b][i][*] for rows i <= j_b of the
+// iterating right-hand sides, one warp per row, in the order of reduce_rows;
+// with add, also out2 = out and out = add + out. Row m + 1 (the squared
+// norm partials) goes to n2[b] when n2 is set.
+__device__ __forceinline__ void coop_reduce(const Arnoldi& a, const int* s_j, const int* s_flag, double* out,
+                                            double* out2, const double* add, double* n2) {
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    const int rows = a.m + 2;
+    for (int item = gw; item < a.nb * rows; item += nw) {
+        const int b = item / rows, i = item % rows;
+        if (!s_flag[b]) continue;
+        const bool norm = i == a.m + 1;
+        if (norm ? !n2 : i > s_j[b]) continue;
+        const double* p = a.part + ((long long)b * (a.m + 2) + i) * a.nchunk;
+        double acc = 0.0;
+        for (int c = lane; c < a.nchunk; c += 32) acc += __ldcg(p + c);
+        acc = warp_sum(acc);
+        if (lane == 0) {
+            if (norm) {
+                n2[b] = acc;
+            } else {
+                const long long o = (long long)b * (a.m + 1) + i;
+                if (add) out[o] = __ldcg(add + o) + acc; else out[o] = acc;
+                if (out2) out2[o] = acc;
+            }
+        }
+    }
+}
+
+template <typename VT>
+__global__ void __launch_bounds__(256) k_arn_step_coop(Arnoldi a) {
+    extern __shared__ double s_dyn[];
+    const int m = a.m;
+    double* s_h = s_dyn;                 // m + 1
+    double* s_col = s_dyn + (m + 1);     // m + 2
+    double* s_cs = s_col + (m + 2);      // m
+    double* s_sn = s_cs + m;             // m
+    __shared__ double s_acc[8 * ACH];
+    __shared__ double s_w[ACH];
+    __shared__ double s_red[2];
+    __shared__ int s_j[COOP_MAX_NB], s_flag[COOP_MAX_NB];
+    const unsigned long long G = gridDim.x;
+    const int items = a.nb * a.nchunk;
+    // step index and flags as they were at the start of the step (the Givens
+    // CTA of each right-hand side advances them at the end)
+    for (int b = threadIdx.x; b < a.nb; b += blockDim.x) {
+        s_j[b] = a.j[b];
+        s_flag[b] = a.flag[b];
+    }
+    __syncthreads();
+
+    // phase 1: w = gather of v, partial dots against V[0..j]
+    for (int item = blockIdx.x; item < items; item += gridDim.x) {
+        const int b = item / a.nchunk, c = item % a.nchunk;
+        if (!s_flag[b]) continue;
+        const long long r0 = (long long)c * ACH;
+        double* w = a.w + (long long)b * a.n;
+        if (threadIdx.x < ACH) {
+            const long long r = r0 + threadIdx.x;
+            double val = 0.0;
+            if (r < a.n) {
+                const VT* vb = static_cast<const VT*>(a.v) + b * a.v_stride;
+                const double tr = a.t[r];
+                val = tr * (double)vb[a.gm[r]] + (1.0 - tr) * (double)vb[a.partner[r]];
+                w[r] = val;
+            }
+            s_w[threadIdx.x] = val;
+        }
+        __syncthreads();
+        chunk_dots(a.V + (long long)b * (m + 1) * a.n, a.n, r0, s_j[b] + 1, s_w,
+                   a.part + (long long)b * (m + 2) * a.nchunk, a.nchunk, c);
+        __syncthreads();
+    }
+    grid_barrier(a.bar, G, a.err);
+    // phase 2: h1
+    coop_reduce(a, s_j, s_flag, a.h1, nullptr, nullptr, nullptr);
+    grid_barrier(a.bar, G, a.err);
+    // phase 3: w -= V h1, partial dots for h2 and ||w||^2
+    for (int item = blockIdx.x; item < items; item += gridDim.x) {
+        const int b = item / a.nchunk, c = item % a.nchunk;
+        if (!s_flag[b]) continue;
+        const int cols = s_j[b] + 1;
+        const long long r0 = (long long)c * ACH;
+        const double* h1 = a.h1 + (long long)b * (m + 1);
+        for (int i = threadIdx.x; i < cols; i += blockDim.x) s_h[i] = __ldcg(h1 + i);
+        __syncthreads();
+        const double* Vb = a.V + (long long)b * (m + 1) * a.n;
+        double* part = a.part + (long long)b * (m + 2) * a.nchunk;
+        chunk_update(Vb, a.n, r0, cols, s_h, a.w + (long long)b * a.n, s_acc, s_w);
+        chunk_dots(Vb, a.n, r0, cols, s_w, part, a.nchunk, c);
+        if (threadIdx.x >= 224) {
+            const int l = threadIdx.x - 224;
+            double acc = s_w[l] * s_w[l] + s_w[l + 32] * s_w[l + 32];
+            acc = warp_sum(acc);
+            if (l == 0) part[(long long)(m + 1) * a.nchunk + c] = acc;
+        }
+        __syncthreads();
+    }
+    grid_barrier(a.bar, G, a.err);
+    // phase 4: h2 (into h1), hcol = h1 + h2, ||w||^2
+    coop_reduce(a, s_j, s_flag, a.hcol, a.h1, a.h1, a.n2);
+    grid_barrier(a.bar, G, a.err);
+
+    // phase 5: hn = sqrt(||w||^2 - ||h2||^2) (every CTA, same order), then
+    // V[j+1] = (w - V h2) / hn; CTA b % G also does the Givens update of b
+    for (int item = blockIdx.x; item < items; item += gridDim.x) {
+        const int b = item / a.nchunk, c = item % a.nchunk;
+        if (!s_flag[b]) continue;
+        const int j = s_j[b], cols = j + 1;
+        const double* h2 = a.h1 + (long long)b * (m + 1);
+        for (int i = threadIdx.x; i < cols; i += blockDim.x) s_h[i] = __ldcg(h2 + i);
+        if (threadIdx.x < 32) {
+            double acc = 0.0;
+            for (int i = threadIdx.x; i <= j; i += 32) {
+                const double x = __ldcg(h2 + i);
+                acc += x * x;
+            }
+            acc = warp_sum(acc);
+            if (threadIdx.x == 0) {
+                const double hn = sqrt(fmax(__ldcg(a.n2 + b) - acc, 0.0));
+                s_red[0] = hn;
+                s_red[1] = hn > 0.0 ? 1.0 / hn : 0.0;
+            }
+        }
+        __syncthreads();
+        double* Vb = a.V + (long long)b * (m + 1) * a.n;
+        chunk_update(Vb, a.n, (long long)c * ACH, cols, s_h, a.w + (long long)b * a.n, s_acc, s_w,
+                     Vb + (long long)(j + 1) * a.n, s_red[1]);
+        __syncthreads();
+    }
+    for (int b = blockIdx.x; b < a.nb; b += gridDim.x) {
+        if (!s_flag[b]) continue;
+        const int j = s_j[b];
+        const double* hc = a.hcol + (long long)b * (m + 1);
+        const double* h2 = a.h1 + (long long)b * (m + 1);
+        double* cs = a.cs + (long long)b * m;
+        double* sn = a.sn + (long long)b * m;
+        for (int i = threadIdx.x; i <= j; i += blockDim.x) s_col[i] = __ldcg(hc + i);
+        for (int i = threadIdx.x; i < j; i += blockDim.x) {
+            s_cs[i] = cs[i];
+            s_sn[i] = sn[i];
+        }
+        if (threadIdx.x < 32) {
+            double acc = 0.0;
+            for (int i = threadIdx.x; i <= j; i += 32) {
+                const double x = __ldcg(h2 + i);
+                acc += x * x;
+            }
+            acc = warp_sum(acc);
+            if (threadIdx.x == 0) s_red[0] = sqrt(fmax(__ldcg(a.n2 + b) - acc, 0.0));
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const double hn = s_red[0];
+            double* g = a.g + (long long)b * (m + 1);
+            s_col[j + 1] = hn;
+            for (int i = 0; i < j; ++i) {
+                const double x0 = s_col[i], x1 = s_col[i + 1];
+                s_col[i] = s_cs[i] * x0 + s_sn[i] * x1;
+                s_col[i + 1] = -s_sn[i] * x0 + s_cs[i] * x1;
+            }
+            const double rr = hypot(s_col[j], s_col[j + 1]);
+            const double cj = rr > 0.0 ? s_col[j] / rr : 1.0;
+            const double sj = rr > 0.0 ? s_col[j + 1] / rr : 0.0;
+            cs[j] = cj;
+            sn[j] = sj;
+            s_col[j] = rr;
+            s_col[j + 1] = 0.0;
+            g[j + 1] = -sj * g[j];
+            g[j] = cj * g[j];
+            const double e = fabs(g[j + 1]);
+            a.est[b] = e;
+            a.ncols[b] = j + 1;
+            a.inv[b] = hn > 0.0 ? 1.0 / hn : 0.0;
+            a.flag[b] = (e > a.target[b] && hn > 0.0 && j + 1 < m) ? 1 : 0;
+            a.j[b] = j + 1;
+        }
+        __syncthreads();
+        double* col = a.H + ((long long)b * m + j) * (m + 1);
+        for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) col[i] = s_col[i];
+        __syncthreads();
+    }
+}
+
 // y = R^{-1} g, one warp per RHS (column-oriented back substitution)
 __global__ void k_arn_backsub(Arnoldi a) {
     extern __shared__ double s_rhs[];
@@ -425,10 +646,49 @@ void arn_init(const Arnoldi& a, const double* r, const double* nrm2, const int* 
 
 int arnoldi_chunks(int n) { return ceil_div(n, ACH); }
 
+int arn_coop_grid(int n, int nb, int m) {
+    static const bool off = []() {
+        const char* e = getenv("BAE_ARNOLDI_COOP");
+        return e && e[0] == '0';
+    }();
+    if (off || nb > COOP_MAX_NB || n <= 0) return 0;
+    int dev = 0, coop = 0, sms = 0;
+    BAE_CUDA(cudaGetDevice(&dev));
+    BAE_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    BAE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (!coop) return 0;
+    const size_t sh = (size_t)(4 * m + 3) * sizeof(double);
+    int k32 = 0, k64 = 0;
+    BAE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k32, k_arn_step_coop<float>, 256, sh));
+    BAE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k64, k_arn_step_coop<double>, 256, sh));
+    const long long cap = (long long)std::min(k32, k64) * sms;
+    const long long items = (long long)nb * ceil_div(n, ACH);
+    return (int)std::min(cap, items);
+}
+
 void arn_step(const Arnoldi& a, cudaStream_t st) {
     BAE_REQUIRE(a.v && a.gm && a.partner && a.t, BAE_ERR_INVALID_ARG, "arn_step: gather inputs not set");
     const size_t sh_h = (size_t)(a.m + 1) * sizeof(double);
     const size_t sh_g = (size_t)(4 * a.m + 3) * sizeof(double);
+    if (a.coop_grid > 0) {
+        BAE_REQUIRE(a.bar && a.err && a.n2 && a.nb <= COOP_MAX_NB, BAE_ERR_INVALID_ARG,
+                    "arn_step: cooperative step state not set");
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(a.coop_grid);
+        cfg.blockDim = dim3(256);
+        cfg.dynamicSmemBytes = sh_g;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        if (a.v_f32)
+            BAE_LAUNCH("k_arn_step_coop.f32", st, BAE_CUDA(cudaLaunchKernelEx(&cfg, k_arn_step_coop<float>, a)));
+        else
+            BAE_LAUNCH("k_arn_step_coop.f64", st, BAE_CUDA(cudaLaunchKernelEx(&cfg, k_arn_step_coop<double>, a)));
+        return;
+    }
     const dim3 grid(a.nchunk, a.nb);
     if (a.v_f32)
         BAE_LAUNCH("k_arn_gather_dots.f32", st, k_arn_gather_dots<float><<<grid, 256, 0, st>>>(a));

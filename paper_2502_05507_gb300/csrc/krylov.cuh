@@ -61,6 +61,14 @@ struct Arnoldi {
     const int* gm = nullptr;
     const int* partner = nullptr;
     const double* t = nullptr;
+    // fused step (one cooperative kernel with grid barriers), used when
+    // coop_grid > 0: the barrier counter (reset to 0 before the first step,
+    // a multiple of coop_grid between steps), an error flag set when a
+    // barrier wait runs out, and [nb] squared norms
+    int coop_grid = 0;
+    unsigned long long* bar = nullptr;
+    int* err = nullptr;
+    double* n2 = nullptr;
 };
 
 // number of vector chunks (CTAs per RHS) of the Arnoldi passes
@@ -73,6 +81,10 @@ void arn_init(const Arnoldi& a, const double* r, const double* nrm2, const int* 
 // CGS2 with the norm of the reorthogonalised vector from the Pythagorean
 // identity, Givens, j++, next basis vector): three kernels.
 void arn_step(const Arnoldi& a, cudaStream_t st);
+// CTAs of the fused cooperative step for this batch (0 if the device cannot
+// run it: no cooperative launch, or more than 64 right-hand sides); call
+// before any graph capture.
+int arn_coop_grid(int n, int nb, int m);
 // End of a cycle: y = R^{-1} g for every RHS with ncols > 0, x += V y.
 void arn_finish(const Arnoldi& a, double* x, int maxcols, cudaStream_t st);
 
