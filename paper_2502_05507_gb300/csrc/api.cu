@@ -310,13 +310,20 @@ namespace {
 
 long long n_gm(const bae_problem* P) { return P->geo.n_gm; }
 
+// pruned: only the x-planes that hold sources or gathered / reconstructed
+// nodes are transformed (applies whose output is read at gamma-, the
+// partners and M+ only); otherwise the potential covers the whole grid
 template <typename T>
-ConvArgs<T> conv_args(bae_problem* P, int nb) {
+ConvArgs<T> conv_args(bae_problem* P, int nb, bool pruned = false) {
     const int N = P->geo.N;
     const long long N1 = N + 1;
     ConvArgs<T> a;
     a.N = N;
     a.nbatch = nb;
+    if (pruned) {
+        a.p0 = P->geo.plane_lo;
+        a.p1 = P->geo.plane_hi;
+    }
     a.A = reinterpret_cast<cplx_t<T>*>(P->ws().A.need((long long)nb * N * N * N1));
     a.B = reinterpret_cast<cplx_t<T>*>(P->ws().B.need((long long)nb * N * 2 * N * N1));
     const Twiddles& tw = P->ctx->twiddles(2 * N);
@@ -342,10 +349,11 @@ out_t<T>* vbuf(bae_problem* P, int nb) {
     else return P->ws().v32.need((long long)nb * P->n3());
 }
 
-// v[b] = K q[b] on the N^3 grid, q [nb][n_gm] on the device
+// v[b] = K q[b] on the N^3 grid (on the plane range only when pruned),
+// q [nb][n_gm] on the device
 template <typename T>
-out_t<T>* apply_potential(bae_problem* P, int nb, const double* q) {
-    ConvArgs<T> a = conv_args<T>(P, nb);
+out_t<T>* apply_potential(bae_problem* P, int nb, const double* q, bool pruned = false) {
+    ConvArgs<T> a = conv_args<T>(P, nb, pruned);
     a.mode = SRC_DENSITY;
     a.q = q;
     a.q_stride = n_gm(P);
@@ -357,8 +365,8 @@ out_t<T>* apply_potential(bae_problem* P, int nb, const double* q) {
 
 // v[b] = sum_{x in M+} G(m - x) scale f[b](x)
 template <typename T>
-out_t<T>* apply_volume(bae_problem* P, int nb, const double* f, double scale) {
-    ConvArgs<T> a = conv_args<T>(P, nb);
+out_t<T>* apply_volume(bae_problem* P, int nb, const double* f, double scale, bool pruned = false) {
+    ConvArgs<T> a = conv_args<T>(P, nb, pruned);
     a.mode = SRC_VOLUME;
     a.f = f;
     a.flags = P->geo.flags;
@@ -371,7 +379,7 @@ out_t<T>* apply_volume(bae_problem* P, int nb, const double* f, double scale) {
 // Aq[b] = Phi K q[b], both [nb][n_gm] on the device
 template <typename T>
 void boundary_apply(bae_problem* P, int nb, const double* q, double* Aq) {
-    out_t<T>* v = apply_potential<T>(P, nb, q);
+    out_t<T>* v = apply_potential<T>(P, nb, q, true);
     closure_gather<out_t<T>>(v, P->n3(), P->geo.gm, P->geo.partner, P->geo.t, (int)n_gm(P), nb, Aq, n_gm(P),
                       P->ctx->stream);
 }
@@ -383,12 +391,13 @@ void boundary_apply_prec(bae_problem* P, int prec, int nb, const double* q, doub
 }
 
 // K q[b] in float64 storage for the float64-accurate precisions
-double* apply_potential64(bae_problem* P, int prec, int nb, const double* q) {
-    return prec == BAE_DF64 ? apply_potential<dsf>(P, nb, q) : apply_potential<double>(P, nb, q);
+double* apply_potential64(bae_problem* P, int prec, int nb, const double* q, bool pruned = false) {
+    return prec == BAE_DF64 ? apply_potential<dsf>(P, nb, q, pruned) : apply_potential<double>(P, nb, q, pruned);
 }
 
-double* apply_volume64(bae_problem* P, int prec, int nb, const double* f, double scale) {
-    return prec == BAE_DF64 ? apply_volume<dsf>(P, nb, f, scale) : apply_volume<double>(P, nb, f, scale);
+double* apply_volume64(bae_problem* P, int prec, int nb, const double* f, double scale, bool pruned = false) {
+    return prec == BAE_DF64 ? apply_volume<dsf>(P, nb, f, scale, pruned)
+                            : apply_volume<double>(P, nb, f, scale, pruned);
 }
 
 // --------------------------------------------------------------- GMRES
@@ -405,7 +414,7 @@ struct RhsState {
 template <typename T>
 out_t<T>* potential_rows(bae_problem* P, int nb, const double* q, long long q_stride, const int* q_row,
                          long long q_row_stride, const int* active) {
-    ConvArgs<T> a = conv_args<T>(P, nb);
+    ConvArgs<T> a = conv_args<T>(P, nb, true);
     a.mode = SRC_DENSITY;
     a.q = q;
     a.q_stride = q_stride;
@@ -682,7 +691,7 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
     // particular solution u_p = G_h[chi_{M+} f] (float64) and b = g - Phi u_p
     double* up = P->ws().up.need((long long)nb * n3);
     {
-        double* v = apply_volume64(P, hp, nb, d_f, h * h);
+        double* v = apply_volume64(P, hp, nb, d_f, h * h, true);
         BAE_CUDA(cudaMemcpyAsync(up, v, (size_t)nb * n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
         for (auto& s : st_local) s.applies_fp64 += 1;
     }
@@ -721,7 +730,7 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
         int* d_all = P->ws().active.need(nb);
         BAE_CUDA(cudaMemcpyAsync(d_all, all.data(), nb * sizeof(int), cudaMemcpyHostToDevice, st));
         double* tmp = P->ws().tmp.need((long long)nb * n);
-        double* v = apply_potential64(P, hp, nb, q);
+        double* v = apply_potential64(P, hp, nb, q, true);
         closure_gather<double>(v, n3, P->geo.gm, P->geo.partner, P->geo.t, n, nb, tmp, n, st);
         for (auto& s : st_local) s.applies_fp64 += 1;
         kr_sub(bvec, tmp, d_all, nb, n, res, st);

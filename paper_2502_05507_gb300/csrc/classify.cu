@@ -6,6 +6,7 @@
 //
 // Every list is produced in lexicographic (i,j,k) order by a deterministic
 // exclusive scan, so the results are bit-identical from run to run.
+#include <algorithm>
 #include <vector>
 
 #include "classify.cuh"
@@ -370,7 +371,20 @@ void build_geometry(const double* phi, int N, double h, const double origin[3], 
                                                    g.term_idx, g.term_coef));
     g.line_off = dev_alloc_n<int>((long long)N * N + 1, st);
     BAE_LAUNCH("k_line_offsets", st, k_line_offsets<<<grid_for((long long)N * N + 1), 256, 0, st>>>(g.src_lin, (int)g.n_src, N, g.line_off));
+    // x-planes holding every source (gamma- and D-nodes, or M+ for the
+    // volume term) and every gathered node (gamma- and the partners, one
+    // step from gamma-): the lists are in lexicographic order, so the first
+    // and last entries bound them
+    int ends[4] = {0, 0, 0, 0};
+    BAE_CUDA(cudaMemcpyAsync(ends + 0, g.gm, sizeof(int), cudaMemcpyDeviceToHost, st));
+    BAE_CUDA(cudaMemcpyAsync(ends + 1, g.gm + (g.n_gm - 1), sizeof(int), cudaMemcpyDeviceToHost, st));
+    BAE_CUDA(cudaMemcpyAsync(ends + 2, g.src_lin, sizeof(int), cudaMemcpyDeviceToHost, st));
+    BAE_CUDA(cudaMemcpyAsync(ends + 3, g.src_lin + (g.n_src - 1), sizeof(int), cudaMemcpyDeviceToHost, st));
     BAE_CUDA(cudaStreamSynchronize(st));
+    const long long nn = (long long)N * N;
+    const long long first = std::min(ends[0], ends[2]) / nn, last = std::max(ends[1], ends[3]) / nn;
+    g.plane_lo = (int)std::max(0LL, first - 1);
+    g.plane_hi = (int)std::min((long long)N, last + 2);
 }
 
 }  // namespace bae

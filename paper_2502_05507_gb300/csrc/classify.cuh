@@ -24,6 +24,9 @@ struct Geometry {
     int* term_off = nullptr;
     int* term_idx = nullptr;
     float* term_coef = nullptr;
+    // x-planes [plane_lo, plane_hi) contain every source and every node the
+    // gather and the reconstruction read
+    int plane_lo = 0, plane_hi = 0;
 
     SrcRecipe recipe() const {
         SrcRecipe r;

@@ -44,6 +44,12 @@ struct ConvArgs {
     const T* ghat = nullptr;      // (N+1)^3 octant, includes 1/(2N)^3
     const cplx_t<T>* tw = nullptr;  // exp(-2 pi i m / 2N), m < 2N
     typename OutOf<T>::type* v = nullptr;   // [nbatch][N^3] output potential
+    // x-planes [p0, p1) hold every nonzero source and every output the
+    // caller reads (p1 == 0: all N planes). Planes outside are skipped: their
+    // sources are zero, and their part of v is left unwritten.
+    int p0 = 0, p1 = 0;
+    __host__ __device__ int plane_lo() const { return p1 > 0 ? p0 : 0; }
+    __host__ __device__ int plane_hi() const { return p1 > 0 ? p1 : N; }
 };
 
 template <typename T>

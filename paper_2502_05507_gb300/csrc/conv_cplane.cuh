@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(CPlaneGeo<T, L>::PT) k_cplane_fwd(ConvArgs<T> 
     C* xch = reinterpret_cast<C*>(smem_raw + G::ROWS);
     cg::cluster_group cluster = cg::this_cluster();
     const int r = (int)cluster.block_rank();
-    const int i = blockIdx.x / G::CS;
+    const int i = a.plane_lo() + (int)(blockIdx.x / G::CS);
     const int b = blockIdx.y;
     const bool skip = a.active && !a.active[b];               // uniform over the cluster
 
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(CPlaneGeo<T, L>::PT) k_cplane_inv(ConvArgs<T> 
     C* xch = reinterpret_cast<C*>(smem_raw + G::ROWS);
     cg::cluster_group cluster = cg::this_cluster();
     const int r = (int)cluster.block_rank();
-    const int i = blockIdx.x / G::CS;
+    const int i = a.plane_lo() + (int)(blockIdx.x / G::CS);
     const int b = blockIdx.y;
     const bool skip = a.active && !a.active[b];
     static_assert(NR % R1 == 0, "a CTA's rows must hold whole R1 groups");
@@ -278,7 +278,7 @@ bool cplane_ready() {
 template <typename T, int L>
 void cplane_launch(const ConvArgs<T>& a, cudaStream_t st, bool inverse) {
     using G = CPlaneGeo<T, L>;
-    const dim3 grid(G::CS * (L / 2), a.nbatch);
+    const dim3 grid(G::CS * (a.plane_hi() - a.plane_lo()), a.nbatch);
     if (!inverse)
         BAE_LAUNCH(kname<T>("conv_cplane_fwd.f32", "conv_cplane_fwd.f64", "conv_cplane_fwd.df64"), st,
                    launch_cluster(k_cplane_fwd<T, L>, G::CS, grid, G::PT, G::SMEM, st, a));

@@ -57,8 +57,8 @@ __global__ void __launch_bounds__(Geo<T, L>::KT) k_kpass_fwd(ConvArgs<T> a) {
     if (a.active && !a.active[b]) return;   // whole CTA: no barrier is skipped
     const int t = threadIdx.x % R1;
     const int p = threadIdx.x / R1;
-    const long long pair = (long long)blockIdx.x * G::P + p;
-    const bool active = pair < (long long)N * N / 2;
+    const long long pair = (long long)a.plane_lo() * (N / 2) + (long long)blockIdx.x * G::P + p;
+    const bool active = pair < (long long)a.plane_hi() * (N / 2);
     const long long la = 2 * pair, lb = la + 1;
     T* r = rho + p * 2 * N;
 
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(Geo<T, L>::CT) k_colpass(ConvArgs<T> a) {
 
     const int b = blockIdx.z;
     if (a.active && !a.active[b]) return;
-    const int o = blockIdx.y;               // i (j passes) or jj (i pass)
+    const int o = MODE == COL_CONV_I ? (int)blockIdx.y : a.plane_lo() + (int)blockIdx.y;   // jj, or i
     const int c = threadIdx.x % W;
     const int t = threadIdx.x / W;
     const int col = blockIdx.x * W + c;     // kk (column 0 holds kk = 0 and N)
@@ -174,7 +174,9 @@ __global__ void __launch_bounds__(Geo<T, L>::CT) k_colpass(ConvArgs<T> a) {
 #pragma unroll
         for (int m = 0; m < R2; ++m) {
             const int n = t + R1 * m;
-            v[m] = (ok && m < R2 / 2) ? in[n * stride] : zero;
+            // rows outside [p0, p1) are zero planes (not even written)
+            const bool live = MODE != COL_CONV_I || (n >= a.plane_lo() && n < a.plane_hi());
+            v[m] = (ok && m < R2 / 2 && live) ? in[n * stride] : zero;
         }
         fft_n2k<L, false>(v, xch, c, R1 * W, W, t, a.tw);
     }
@@ -248,7 +250,8 @@ __global__ void __launch_bounds__(Geo<T, L>::CT) k_colpass(ConvArgs<T> a) {
 #pragma unroll
         for (int m = 0; m < R2; ++m) {
             const int n = t + R1 * m;
-            if (m < R2 / 2) out[n * stride] = v[m];
+            if (m < R2 / 2 && (MODE != COL_CONV_I || (n >= a.plane_lo() && n < a.plane_hi())))
+                out[n * stride] = v[m];
         }
     }
 }
@@ -266,8 +269,8 @@ __global__ void __launch_bounds__(Geo<T, L>::KT) k_kpass_inv(ConvArgs<T> a) {
     if (a.active && !a.active[b]) return;
     const int t = threadIdx.x % R1;
     const int p = threadIdx.x / R1;
-    const long long pair = (long long)blockIdx.x * G::P + p;
-    const bool active = pair < (long long)N * N / 2;
+    const long long pair = (long long)a.plane_lo() * (N / 2) + (long long)blockIdx.x * G::P + p;
+    const bool active = pair < (long long)a.plane_hi() * (N / 2);
     const long long la = 2 * pair, lb = la + 1;
     const C* A = a.A + (long long)b * N * N * N1;
 
@@ -316,7 +319,7 @@ __global__ void __launch_bounds__(512) k_plane_fwd(ConvArgs<T> a) {
     C* xch = reinterpret_cast<C*>(smem_raw + G::PLANE);
     const int b = blockIdx.y;
     if (a.active && !a.active[b]) return;
-    const int i = blockIdx.x;
+    const int i = a.plane_lo() + (int)blockIdx.x;
 
     // ---- k lines of plane i, PP pairs per round
     {
@@ -425,7 +428,7 @@ __global__ void __launch_bounds__(512) k_plane_inv(ConvArgs<T> a) {
     C* xch = reinterpret_cast<C*>(smem_raw + G::PLANE);
     const int b = blockIdx.y;
     if (a.active && !a.active[b]) return;
-    const int i = blockIdx.x;
+    const int i = a.plane_lo() + (int)blockIdx.x;
 
     // ---- inverse j on every column, keep j < N in the plane
     {
@@ -527,27 +530,28 @@ void launch_sched(const ConvArgs<T>& a, cudaStream_t st, int sched) {
     const size_t smem_k = (size_t)G::P * G::XS * sizeof(C) + (size_t)G::P * 2 * N * sizeof(T);
     const size_t smem_c = (size_t)L * G::W * sizeof(C);
     const int nb = a.nbatch;
-    const dim3 gk(ceil_div((long long)N * N / 2, G::P), 1, nb);
+    const int np = a.plane_hi() - a.plane_lo();   // x-planes holding sources or read outputs
+    const dim3 gk(ceil_div((long long)np * N / 2, G::P), 1, nb);
     const int ncolblk = ceil_div(N, G::W);   // column 0 also holds kk = N
     if (sched == SCHED_PLANE) {
         if constexpr (PG::FITS)
             BAE_LAUNCH(kname<T>("conv_plane_fwd.f32", "conv_plane_fwd.f64", "conv_plane_fwd.df64"), st,
-                       k_plane_fwd<T, L><<<dim3(N, nb), PG::PT, PG::SMEM, st>>>(a));
+                       k_plane_fwd<T, L><<<dim3(np, nb), PG::PT, PG::SMEM, st>>>(a));
         else if constexpr (CPlaneGeo<T, L>::USE)
             cplane_launch<T, L>(a, st, false);
     } else {
         BAE_LAUNCH(kname<T>("conv_kfwd.f32", "conv_kfwd.f64", "conv_kfwd.df64"), st, k_kpass_fwd<T, L><<<gk, G::KT, smem_k, st>>>(a));
-        BAE_LAUNCH(kname<T>("conv_jfwd.f32", "conv_jfwd.f64", "conv_jfwd.df64"), st, k_colpass<T, L, COL_FWD_J><<<dim3(ncolblk, N, nb), G::CT, smem_c, st>>>(a));
+        BAE_LAUNCH(kname<T>("conv_jfwd.f32", "conv_jfwd.f64", "conv_jfwd.df64"), st, k_colpass<T, L, COL_FWD_J><<<dim3(ncolblk, np, nb), G::CT, smem_c, st>>>(a));
     }
     BAE_LAUNCH(kname<T>("conv_i.f32", "conv_i.f64", "conv_i.df64"), st, k_colpass<T, L, COL_CONV_I><<<dim3(ncolblk, 2 * N, nb), G::CT, smem_c, st>>>(a));
     if (sched == SCHED_PLANE) {
         if constexpr (PG::FITS)
             BAE_LAUNCH(kname<T>("conv_plane_inv.f32", "conv_plane_inv.f64", "conv_plane_inv.df64"), st,
-                       k_plane_inv<T, L><<<dim3(N, nb), PG::PT, PG::SMEM, st>>>(a));
+                       k_plane_inv<T, L><<<dim3(np, nb), PG::PT, PG::SMEM, st>>>(a));
         else if constexpr (CPlaneGeo<T, L>::USE)
             cplane_launch<T, L>(a, st, true);
     } else {
-        BAE_LAUNCH(kname<T>("conv_jinv.f32", "conv_jinv.f64", "conv_jinv.df64"), st, k_colpass<T, L, COL_INV_J><<<dim3(ncolblk, N, nb), G::CT, smem_c, st>>>(a));
+        BAE_LAUNCH(kname<T>("conv_jinv.f32", "conv_jinv.f64", "conv_jinv.df64"), st, k_colpass<T, L, COL_INV_J><<<dim3(ncolblk, np, nb), G::CT, smem_c, st>>>(a));
         BAE_LAUNCH(kname<T>("conv_kinv.f32", "conv_kinv.f64", "conv_kinv.df64"), st, k_kpass_inv<T, L><<<gk, G::KT, smem_k, st>>>(a));
     }
 }

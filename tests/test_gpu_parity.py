@@ -133,6 +133,28 @@ def test_potential_apply_matches_direct_sum(ctx, make, layer):
     prob.close()
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-6), ("df64", 1e-12)])
+@pytest.mark.parametrize("layer", ["double", "single"])
+def test_boundary_apply_after_full_apply(ctx, precision, tol, layer):
+    # the boundary operator transforms only the x-planes that hold sources
+    # and gathered nodes; a full-grid apply of another density first leaves
+    # every plane filled with other values, so a needed plane left out of the
+    # range would show up here
+    import torch
+    P = W.sphere_exp(32, radius=0.6)
+    prob = _problem(ctx, P, layer)
+    cls = OG.classify(P.phi, P.grid.h, P.grid.origin)
+    T = OL.LGFTable(32, 0.0)
+    q1 = W.random_density(cls.gm_idx.size, seed=31)
+    q2 = W.random_density(cls.gm_idx.size, seed=32)
+    prob.potential_apply(torch.from_numpy(q1).cuda(), precision)
+    Aq = prob.boundary_apply(torch.from_numpy(q2).cuda(), precision).cpu().numpy()
+    ref = OP.fft_convolve(OP.source_density(cls, q2, layer), table=T)
+    ref_A = OS.closure_apply(cls, ref.reshape(-1))
+    assert np.max(np.abs(Aq - ref_A)) <= tol * np.max(np.abs(ref))
+    prob.close()
+
+
 def test_particular_solution(ctx):
     import torch
     P = W.torus_helmholtz(32, kappa2=10.0)
