@@ -9,9 +9,12 @@
 // evenly (offset N unused). Its spectrum is real and even and is stored on
 // the octant (N+1)^3 with the 1/(2N)^3 of the inverse transform folded in.
 //
-// Data layout (per right-hand side), i = x index (outermost), k = z (fastest):
-//   A[i][j][kk]  i < N, j < N,  kk <= N   after the R2C pass along k
-//   B[i][jj][kk] i < N, jj < 2N, kk <= N  after the pass along j
+// Data layout (per right-hand side), i = x index (outermost), k = z (fastest),
+// rows of N + 1 elements of which columns kk < N are used (column 0 holds
+// the real kk = 0 and kk = N spectra packed, see conv_geo.cuh):
+//   A[i][j][kk]  i < N, j < N,  kk < N    after the R2C pass along k
+//   B[i][jj][kk] i < N, jj < 2N, kk < N   after the pass along j
+// Only the x-planes [p0, p1) of ConvArgs are transformed.
 // Every pass transforms its lines in registers (four-step factorisation,
 // one shared-memory exchange per transform, see fft2.cuh), reading and
 // writing global memory directly. Passes (forward, then inverse in reverse
@@ -585,15 +588,18 @@ void run_conv(const ConvArgs<T>& a, cudaStream_t st) {
             launch_sched<T, L>(a, st, sched);
             return;
         }
-        // time both schedules on the real data (twice each, keep the better
-        // time); the last launch leaves a valid result
+        // time both schedules on the real data: five rounds in alternating
+        // order, three back-to-back applies per timing, keep each schedule's
+        // best round (the two are often within 10%, where a single launch
+        // mostly measures launch jitter); every apply leaves a valid result
         cudaEvent_t e[3];
         for (auto& x : e) BAE_CUDA(cudaEventCreate(&x));
         float best[2] = {1e30f, 1e30f};
-        for (int rep = 0; rep < 2; ++rep)
-            for (int sc = 0; sc < 2; ++sc) {
+        for (int rep = 0; rep < 5; ++rep)
+            for (int k = 0; k < 2; ++k) {
+                const int sc = (rep & 1) ? 1 - k : k;
                 BAE_CUDA(cudaEventRecord(e[0], st));
-                launch_sched<T, L>(a, st, sc);
+                for (int r = 0; r < 3; ++r) launch_sched<T, L>(a, st, sc);
                 BAE_CUDA(cudaEventRecord(e[1], st));
                 BAE_CUDA(cudaEventSynchronize(e[1]));
                 float ms = 0.f;
