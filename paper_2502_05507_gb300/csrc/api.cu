@@ -482,7 +482,7 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
     a.j = ibuf + 3 * nb;
     a.ctr = reinterpret_cast<unsigned int*>(ws.arnCtr.need((long long)nb * 3));
     // the fused cooperative step where the device can place it
-    a.coop_grid = arn_coop_grid(n, nb, m);
+    a.coop_grid = arn_coop_grid(n, nb, m, &a.coop_resident);
     a.bar = ws.arnBar.need(1);
     a.err = ibuf + 4 * nb;
     a.n2 = scal + 4 * nb;

@@ -16,6 +16,7 @@ namespace {
 
 template <typename T, int L>
 __global__ void __launch_bounds__(CPlaneGeo<T, L>::PT) k_cplane_fwd(ConvArgs<T> a) {
+    wait_prior_grid();   // no-op: launched without programmatic serialisation
     using C = cplx_t<T>;
     using G = CPlaneGeo<T, L>;
     constexpr int N = G::N, N1 = G::N1, R1 = G::R1, R2 = G::R2, Q = R2 / R1, NR = G::NR;
@@ -135,6 +136,7 @@ __global__ void __launch_bounds__(CPlaneGeo<T, L>::PT) k_cplane_fwd(ConvArgs<T> 
 
 template <typename T, int L>
 __global__ void __launch_bounds__(CPlaneGeo<T, L>::PT) k_cplane_inv(ConvArgs<T> a) {
+    wait_prior_grid();   // no-op: launched without programmatic serialisation
     using C = cplx_t<T>;
     using G = CPlaneGeo<T, L>;
     constexpr int N = G::N, N1 = G::N1, R1 = G::R1, R2 = G::R2, Q = R2 / R1, NR = G::NR;

@@ -59,6 +59,29 @@ template <typename T, int L> struct PlaneGeo {
     static constexpr bool FITS = SMEM <= 227 * 1024;
 };
 
+// ------------------------------------------ programmatic dependent launch
+// The convolution kernels are launched with programmatic stream
+// serialisation: the launch of a kernel is set up while the kernel before it
+// on the stream is still running, and the kernel's first statement waits
+// for that kernel's completion (and its memory) before reading anything. A
+// launch without the attribute makes the wait a no-op.
+__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
+template <typename K, typename A>
+void launch_pdl(K kernel, dim3 grid, int threads, size_t smem, cudaStream_t st, const A& a) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    BAE_CUDA(cudaLaunchKernelEx(&cfg, kernel, a));
+}
+
 // ------------------------------------------------ packed Nyquist column
 // The k-spectrum of a real line is real at kk = 0 and at kk = N, so both
 // live in column 0 as X0 + i XN and every pass after the k transform runs

@@ -49,6 +49,7 @@ namespace {
 // Two real k-lines (i, 2p) and (i, 2p+1) per complex transform z = x_a + i x_b.
 template <typename T, int L>
 __global__ void __launch_bounds__(Geo<T, L>::KT) k_kpass_fwd(ConvArgs<T> a) {
+    wait_prior_grid();   // results of the previous kernel on the stream
     using C = cplx_t<T>;
     using G = Geo<T, L>;
     constexpr int N = L / 2, N1 = N + 1, R1 = G::R1, R2 = G::R2;
@@ -130,6 +131,7 @@ enum ColMode { COL_FWD_J = 0, COL_CONV_I = 1, COL_INV_J = 2 };
 
 template <typename T, int L, int MODE>
 __global__ void __launch_bounds__(Geo<T, L>::CT) k_colpass(ConvArgs<T> a) {
+    wait_prior_grid();   // results of the previous kernel on the stream
     using C = cplx_t<T>;
     using G = Geo<T, L>;
     constexpr int N = L / 2, N1 = N + 1, R1 = G::R1, R2 = G::R2, W = G::W, Q = R2 / R1;
@@ -262,6 +264,7 @@ __global__ void __launch_bounds__(Geo<T, L>::CT) k_colpass(ConvArgs<T> a) {
 // ----------------------------------------------------------- k pass (C2R)
 template <typename T, int L>
 __global__ void __launch_bounds__(Geo<T, L>::KT) k_kpass_inv(ConvArgs<T> a) {
+    wait_prior_grid();   // results of the previous kernel on the stream
     using C = cplx_t<T>;
     using G = Geo<T, L>;
     constexpr int N = L / 2, N1 = N + 1, R1 = G::R1, R2 = G::R2, Q = R2 / R1;
@@ -314,6 +317,7 @@ __global__ void __launch_bounds__(Geo<T, L>::KT) k_kpass_inv(ConvArgs<T> a) {
 
 template <typename T, int L>
 __global__ void __launch_bounds__(512) k_plane_fwd(ConvArgs<T> a) {
+    wait_prior_grid();   // results of the previous kernel on the stream
     using C = cplx_t<T>;
     using G = PlaneGeo<T, L>;
     constexpr int N = G::N, N1 = G::N1, R1 = G::R1, R2 = G::R2, Q = R2 / R1;
@@ -423,6 +427,7 @@ __global__ void __launch_bounds__(512) k_plane_fwd(ConvArgs<T> a) {
 
 template <typename T, int L>
 __global__ void __launch_bounds__(512) k_plane_inv(ConvArgs<T> a) {
+    wait_prior_grid();   // results of the previous kernel on the stream
     using C = cplx_t<T>;
     using G = PlaneGeo<T, L>;
     constexpr int N = G::N, N1 = G::N1, R1 = G::R1, R2 = G::R2, Q = R2 / R1;
@@ -539,23 +544,23 @@ void launch_sched(const ConvArgs<T>& a, cudaStream_t st, int sched) {
     if (sched == SCHED_PLANE) {
         if constexpr (PG::FITS)
             BAE_LAUNCH(kname<T>("conv_plane_fwd.f32", "conv_plane_fwd.f64", "conv_plane_fwd.df64"), st,
-                       k_plane_fwd<T, L><<<dim3(np, nb), PG::PT, PG::SMEM, st>>>(a));
+                       launch_pdl(k_plane_fwd<T, L>, dim3(np, nb), PG::PT, PG::SMEM, st, a));
         else if constexpr (CPlaneGeo<T, L>::USE)
             cplane_launch<T, L>(a, st, false);
     } else {
-        BAE_LAUNCH(kname<T>("conv_kfwd.f32", "conv_kfwd.f64", "conv_kfwd.df64"), st, k_kpass_fwd<T, L><<<gk, G::KT, smem_k, st>>>(a));
-        BAE_LAUNCH(kname<T>("conv_jfwd.f32", "conv_jfwd.f64", "conv_jfwd.df64"), st, k_colpass<T, L, COL_FWD_J><<<dim3(ncolblk, np, nb), G::CT, smem_c, st>>>(a));
+        BAE_LAUNCH(kname<T>("conv_kfwd.f32", "conv_kfwd.f64", "conv_kfwd.df64"), st, launch_pdl(k_kpass_fwd<T, L>, gk, G::KT, smem_k, st, a));
+        BAE_LAUNCH(kname<T>("conv_jfwd.f32", "conv_jfwd.f64", "conv_jfwd.df64"), st, launch_pdl(k_colpass<T, L, COL_FWD_J>, dim3(ncolblk, np, nb), G::CT, smem_c, st, a));
     }
-    BAE_LAUNCH(kname<T>("conv_i.f32", "conv_i.f64", "conv_i.df64"), st, k_colpass<T, L, COL_CONV_I><<<dim3(ncolblk, 2 * N, nb), G::CT, smem_c, st>>>(a));
+    BAE_LAUNCH(kname<T>("conv_i.f32", "conv_i.f64", "conv_i.df64"), st, launch_pdl(k_colpass<T, L, COL_CONV_I>, dim3(ncolblk, 2 * N, nb), G::CT, smem_c, st, a));
     if (sched == SCHED_PLANE) {
         if constexpr (PG::FITS)
             BAE_LAUNCH(kname<T>("conv_plane_inv.f32", "conv_plane_inv.f64", "conv_plane_inv.df64"), st,
-                       k_plane_inv<T, L><<<dim3(np, nb), PG::PT, PG::SMEM, st>>>(a));
+                       launch_pdl(k_plane_inv<T, L>, dim3(np, nb), PG::PT, PG::SMEM, st, a));
         else if constexpr (CPlaneGeo<T, L>::USE)
             cplane_launch<T, L>(a, st, true);
     } else {
-        BAE_LAUNCH(kname<T>("conv_jinv.f32", "conv_jinv.f64", "conv_jinv.df64"), st, k_colpass<T, L, COL_INV_J><<<dim3(ncolblk, np, nb), G::CT, smem_c, st>>>(a));
-        BAE_LAUNCH(kname<T>("conv_kinv.f32", "conv_kinv.f64", "conv_kinv.df64"), st, k_kpass_inv<T, L><<<gk, G::KT, smem_k, st>>>(a));
+        BAE_LAUNCH(kname<T>("conv_jinv.f32", "conv_jinv.f64", "conv_jinv.df64"), st, launch_pdl(k_colpass<T, L, COL_INV_J>, dim3(ncolblk, np, nb), G::CT, smem_c, st, a));
+        BAE_LAUNCH(kname<T>("conv_kinv.f32", "conv_kinv.f64", "conv_kinv.df64"), st, launch_pdl(k_kpass_inv<T, L>, gk, G::KT, smem_k, st, a));
     }
 }
 

@@ -167,33 +167,50 @@ __device__ __forceinline__ void reduce_rows(const double* part, int nch, int col
     }
 }
 
+// The chunk [r0, r0 + 64) of the basis rows, as seen by lane l of a warp:
+// elements base[i rs + oa] and base[i rs + ob] of row i (global memory with
+// indices clamped to the vector, or a shared-memory copy of the chunk).
+struct RowView {
+    const double* base;
+    long long rs, oa, ob;
+};
+
+__device__ __forceinline__ RowView global_rows(const double* Vb, long long n, long long r0) {
+    const int lane = threadIdx.x & 31;
+    return {Vb, n, min(r0 + lane, n - 1), min(r0 + lane + 32, n - 1)};
+}
+
+__device__ __forceinline__ RowView shared_rows(const double* sV) {
+    const int lane = threadIdx.x & 31;
+    return {sV, ACH, lane, lane + 32};
+}
+
 // w[r0 .. r0+ACH) -= V[0..cols) h over the chunk; 8 warps split the rows
 // (warp q takes rows q, q+8, ...; four rows per loop trip so that eight
 // loads are in flight), partial sums combined in warp order. Indices past
 // the end of the vector are clamped (their results are never stored).
 // Leaves the new chunk in s_w (zero past the end) and stores it into w, or,
 // when dst is set, stores scale times it into dst instead.
-__device__ __forceinline__ void chunk_update(const double* Vb, long long n, long long r0, int cols, const double* s_h,
+__device__ __forceinline__ void chunk_update(const RowView& V, long long n, long long r0, int cols, const double* s_h,
                                              double* w, double* s_acc, double* s_w, double* dst = nullptr,
                                              double scale = 1.0) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long ra = min(r0 + lane, n - 1), rb = min(r0 + lane + 32, n - 1);
     double a0 = 0.0, a1 = 0.0;
     int i = warp;
     for (; i + 24 < cols; i += 32) {
-        const double* v0 = Vb + (long long)i * n;
-        const double* v1 = v0 + 8 * n;
-        const double* v2 = v0 + 16 * n;
-        const double* v3 = v0 + 24 * n;
-        const double x0 = v0[ra], y0 = v0[rb], x1 = v1[ra], y1 = v1[rb];
-        const double x2 = v2[ra], y2 = v2[rb], x3 = v3[ra], y3 = v3[rb];
+        const double* v0 = V.base + (long long)i * V.rs;
+        const double* v1 = v0 + 8 * V.rs;
+        const double* v2 = v0 + 16 * V.rs;
+        const double* v3 = v0 + 24 * V.rs;
+        const double x0 = v0[V.oa], y0 = v0[V.ob], x1 = v1[V.oa], y1 = v1[V.ob];
+        const double x2 = v2[V.oa], y2 = v2[V.ob], x3 = v3[V.oa], y3 = v3[V.ob];
         a0 += x0 * s_h[i] + x1 * s_h[i + 8] + x2 * s_h[i + 16] + x3 * s_h[i + 24];
         a1 += y0 * s_h[i] + y1 * s_h[i + 8] + y2 * s_h[i + 16] + y3 * s_h[i + 24];
     }
     for (; i < cols; i += 8) {
-        const double* v = Vb + (long long)i * n;
-        a0 += v[ra] * s_h[i];
-        a1 += v[rb] * s_h[i];
+        const double* v = V.base + (long long)i * V.rs;
+        a0 += v[V.oa] * s_h[i];
+        a1 += v[V.ob] * s_h[i];
     }
     s_acc[warp * ACH + lane] = a0;
     s_acc[warp * ACH + lane + 32] = a1;
@@ -216,18 +233,17 @@ __device__ __forceinline__ void chunk_update(const double* Vb, long long n, long
 
 // partial dots of the chunk against rows i < cols: part[i][c] (four rows
 // per warp per loop trip)
-__device__ __forceinline__ void chunk_dots(const double* Vb, long long n, long long r0, int cols, const double* s_w,
-                                           double* part, int nch, int c) {
+__device__ __forceinline__ void chunk_dots(const RowView& V, int cols, const double* s_w, double* part, int nch,
+                                           int c) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long ra = min(r0 + lane, n - 1), rb = min(r0 + lane + 32, n - 1);
     const double wa = s_w[lane], wb = s_w[lane + 32];
     int i = warp;
     for (; i + 24 < cols; i += 32) {
-        const double* v0 = Vb + (long long)i * n;
-        double d0 = v0[ra] * wa + v0[rb] * wb;
-        double d1 = v0[8 * n + ra] * wa + v0[8 * n + rb] * wb;
-        double d2 = v0[16 * n + ra] * wa + v0[16 * n + rb] * wb;
-        double d3 = v0[24 * n + ra] * wa + v0[24 * n + rb] * wb;
+        const double* v0 = V.base + (long long)i * V.rs;
+        double d0 = v0[V.oa] * wa + v0[V.ob] * wb;
+        double d1 = v0[8 * V.rs + V.oa] * wa + v0[8 * V.rs + V.ob] * wb;
+        double d2 = v0[16 * V.rs + V.oa] * wa + v0[16 * V.rs + V.ob] * wb;
+        double d3 = v0[24 * V.rs + V.oa] * wa + v0[24 * V.rs + V.ob] * wb;
         d0 = warp_sum(d0);
         d1 = warp_sum(d1);
         d2 = warp_sum(d2);
@@ -240,8 +256,8 @@ __device__ __forceinline__ void chunk_dots(const double* Vb, long long n, long l
         }
     }
     for (; i < cols; i += 8) {
-        const double* v = Vb + (long long)i * n;
-        double acc = v[ra] * wa + v[rb] * wb;
+        const double* v = V.base + (long long)i * V.rs;
+        double acc = v[V.oa] * wa + v[V.ob] * wb;
         acc = warp_sum(acc);
         if (lane == 0) part[(long long)i * nch + c] = acc;
     }
@@ -273,7 +289,7 @@ __global__ void __launch_bounds__(256) k_arn_gather_dots(Arnoldi a) {
     __syncthreads();
     double* part = a.part + (long long)b * (a.m + 2) * a.nchunk;
     const double* Vb = a.V + (long long)b * (a.m + 1) * a.n;
-    chunk_dots(Vb, a.n, r0, cols, s_w, part, a.nchunk, c);
+    chunk_dots(global_rows(Vb, a.n, r0), cols, s_w, part, a.nchunk, c);
     if (last_block(a.ctr + 3 * b + 0, gridDim.x, &s_last)) {
         reduce_rows(part, a.nchunk, cols, a.h1 + (long long)b * (a.m + 1), nullptr, nullptr);
         if (threadIdx.x == 0) a.ctr[3 * b + 0] = 0;
@@ -306,9 +322,9 @@ __global__ void __launch_bounds__(256) k_arn_update_dots(Arnoldi a) {
     for (int i = threadIdx.x; i < cols; i += blockDim.x) s_h[i] = h1[i];
     __syncthreads();
     const double* Vb = a.V + (long long)b * (m + 1) * a.n;
-    chunk_update(Vb, a.n, r0, cols, s_h, a.w + (long long)b * a.n, s_acc, s_w);
+    chunk_update(global_rows(Vb, a.n, r0), a.n, r0, cols, s_h, a.w + (long long)b * a.n, s_acc, s_w);
     double* part = a.part + (long long)b * (m + 2) * a.nchunk;
-    chunk_dots(Vb, a.n, r0, cols, s_w, part, a.nchunk, c);
+    chunk_dots(global_rows(Vb, a.n, r0), cols, s_w, part, a.nchunk, c);
     if (threadIdx.x >= 224) {   // the last warp: ||w||^2 over the chunk
         const int l = threadIdx.x - 224;
         double acc = s_w[l] * s_w[l] + s_w[l + 32] * s_w[l + 32];
@@ -392,7 +408,8 @@ __global__ void __launch_bounds__(256) k_arn_update_next(Arnoldi a) {
     for (int i = threadIdx.x; i < cols; i += blockDim.x) s_h[i] = h2[i];
     __syncthreads();
     double* Vb = a.V + (long long)b * (a.m + 1) * a.n;
-    chunk_update(Vb, a.n, r0, cols, s_h, a.w + (long long)b * a.n, s_acc, s_w, Vb + (long long)j * a.n, a.inv[b]);
+    chunk_update(global_rows(Vb, a.n, r0), a.n, r0, cols, s_h, a.w + (long long)b * a.n, s_acc, s_w,
+                 Vb + (long long)j * a.n, a.inv[b]);
 }
 
 // ------------------------------------------------ fused cooperative step
@@ -458,7 +475,11 @@ __device__ __forceinline__ void coop_reduce(const Arnoldi& a, const int* s_j, co
     }
 }
 
-template <typename VT>
+// SV: every CTA holds exactly one (RHS, chunk) item and keeps its chunk of
+// the basis rows V[0..j] in shared memory (copied asynchronously while the
+// gather runs), so the three projections read it from there; the sums are
+// the same expressions in the same order as with global rows.
+template <typename VT, bool SV>
 __global__ void __launch_bounds__(256) k_arn_step_coop(Arnoldi a) {
     extern __shared__ double s_dyn[];
     const int m = a.m;
@@ -466,6 +487,7 @@ __global__ void __launch_bounds__(256) k_arn_step_coop(Arnoldi a) {
     double* s_col = s_dyn + (m + 1);     // m + 2
     double* s_cs = s_col + (m + 2);      // m
     double* s_sn = s_cs + m;             // m
+    double* s_V = s_sn + m;              // SV: (m + 1) x ACH
     __shared__ double s_acc[8 * ACH];
     __shared__ double s_w[ACH];
     __shared__ double s_red[2];
@@ -480,6 +502,20 @@ __global__ void __launch_bounds__(256) k_arn_step_coop(Arnoldi a) {
     }
     __syncthreads();
 
+    if (SV && blockIdx.x < items && s_flag[blockIdx.x / a.nchunk]) {
+        // the chunk of V[0..j] into shared memory, clamped at the vector end
+        const int b = blockIdx.x / a.nchunk;
+        const long long r0 = (long long)(blockIdx.x % a.nchunk) * ACH;
+        const double* Vb = a.V + (long long)b * (m + 1) * a.n;
+        const int cnt = (s_j[b] + 1) * ACH;
+        for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+            const int i = e / ACH, l = e % ACH;
+            const double* src = Vb + (long long)i * a.n + min(r0 + l, (long long)a.n - 1);
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(s_V + e);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
     // phase 1: w = gather of v, partial dots against V[0..j]
     for (int item = blockIdx.x; item < items; item += gridDim.x) {
         const int b = item / a.nchunk, c = item % a.nchunk;
@@ -497,9 +533,10 @@ __global__ void __launch_bounds__(256) k_arn_step_coop(Arnoldi a) {
             }
             s_w[threadIdx.x] = val;
         }
+        if (SV) asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         __syncthreads();
-        chunk_dots(a.V + (long long)b * (m + 1) * a.n, a.n, r0, s_j[b] + 1, s_w,
-                   a.part + (long long)b * (m + 2) * a.nchunk, a.nchunk, c);
+        const RowView V = SV ? shared_rows(s_V) : global_rows(a.V + (long long)b * (m + 1) * a.n, a.n, r0);
+        chunk_dots(V, s_j[b] + 1, s_w, a.part + (long long)b * (m + 2) * a.nchunk, a.nchunk, c);
         __syncthreads();
     }
     grid_barrier(a.bar, G, a.err);
@@ -517,8 +554,9 @@ __global__ void __launch_bounds__(256) k_arn_step_coop(Arnoldi a) {
         __syncthreads();
         const double* Vb = a.V + (long long)b * (m + 1) * a.n;
         double* part = a.part + (long long)b * (m + 2) * a.nchunk;
-        chunk_update(Vb, a.n, r0, cols, s_h, a.w + (long long)b * a.n, s_acc, s_w);
-        chunk_dots(Vb, a.n, r0, cols, s_w, part, a.nchunk, c);
+        const RowView V = SV ? shared_rows(s_V) : global_rows(Vb, a.n, r0);
+        chunk_update(V, a.n, r0, cols, s_h, a.w + (long long)b * a.n, s_acc, s_w);
+        chunk_dots(V, cols, s_w, part, a.nchunk, c);
         if (threadIdx.x >= 224) {
             const int l = threadIdx.x - 224;
             double acc = s_w[l] * s_w[l] + s_w[l + 32] * s_w[l + 32];
@@ -555,8 +593,10 @@ __global__ void __launch_bounds__(256) k_arn_step_coop(Arnoldi a) {
         }
         __syncthreads();
         double* Vb = a.V + (long long)b * (m + 1) * a.n;
-        chunk_update(Vb, a.n, (long long)c * ACH, cols, s_h, a.w + (long long)b * a.n, s_acc, s_w,
-                     Vb + (long long)(j + 1) * a.n, s_red[1]);
+        const long long r0 = (long long)c * ACH;
+        const RowView V = SV ? shared_rows(s_V) : global_rows(Vb, a.n, r0);
+        chunk_update(V, a.n, r0, cols, s_h, a.w + (long long)b * a.n, s_acc, s_w, Vb + (long long)(j + 1) * a.n,
+                     s_red[1]);
         __syncthreads();
     }
     for (int b = blockIdx.x; b < a.nb; b += gridDim.x) {
@@ -646,7 +686,7 @@ void arn_init(const Arnoldi& a, const double* r, const double* nrm2, const int* 
 
 int arnoldi_chunks(int n) { return ceil_div(n, ACH); }
 
-int arn_coop_grid(int n, int nb, int m) {
+int arn_coop_grid(int n, int nb, int m, bool* resident) {
     static const bool off = []() {
         const char* e = getenv("BAE_ARNOLDI_COOP");
         return e && e[0] == '0';
@@ -658,11 +698,27 @@ int arn_coop_grid(int n, int nb, int m) {
     BAE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     if (!coop) return 0;
     const size_t sh = (size_t)(4 * m + 3) * sizeof(double);
-    int k32 = 0, k64 = 0;
-    BAE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k32, k_arn_step_coop<float>, 256, sh));
-    BAE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k64, k_arn_step_coop<double>, 256, sh));
-    const long long cap = (long long)std::min(k32, k64) * sms;
     const long long items = (long long)nb * ceil_div(n, ACH);
+    // resident basis chunks: one item per CTA, all CTAs on the device at once
+    const size_t sh_sv = sh + (size_t)(m + 1) * ACH * sizeof(double);
+    *resident = false;
+    if (sh_sv <= 200 * 1024) {
+        BAE_CUDA(cudaFuncSetAttribute(k_arn_step_coop<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sh_sv));
+        BAE_CUDA(cudaFuncSetAttribute(k_arn_step_coop<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sh_sv));
+        int s32 = 0, s64 = 0;
+        BAE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s32, k_arn_step_coop<float, true>, 256, sh_sv));
+        BAE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s64, k_arn_step_coop<double, true>, 256, sh_sv));
+        if (items <= (long long)std::min(s32, s64) * sms) {
+            *resident = true;
+            return (int)items;
+        }
+    }
+    int k32 = 0, k64 = 0;
+    BAE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k32, k_arn_step_coop<float, false>, 256, sh));
+    BAE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k64, k_arn_step_coop<double, false>, 256, sh));
+    const long long cap = (long long)std::min(k32, k64) * sms;
     return (int)std::min(cap, items);
 }
 
@@ -676,17 +732,24 @@ void arn_step(const Arnoldi& a, cudaStream_t st) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(a.coop_grid);
         cfg.blockDim = dim3(256);
-        cfg.dynamicSmemBytes = sh_g;
+        cfg.dynamicSmemBytes = sh_g + (a.coop_resident ? (size_t)(a.m + 1) * ACH * sizeof(double) : 0);
         cfg.stream = st;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeCooperative;
         attr[0].val.cooperative = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        if (a.v_f32)
-            BAE_LAUNCH("k_arn_step_coop.f32", st, BAE_CUDA(cudaLaunchKernelEx(&cfg, k_arn_step_coop<float>, a)));
-        else
-            BAE_LAUNCH("k_arn_step_coop.f64", st, BAE_CUDA(cudaLaunchKernelEx(&cfg, k_arn_step_coop<double>, a)));
+        if (a.coop_resident) {
+            BAE_REQUIRE(a.coop_grid == a.nb * a.nchunk, BAE_ERR_INVALID_ARG, "arn_step: resident step needs one CTA per chunk");
+            if (a.v_f32)
+                BAE_LAUNCH("k_arn_step_coop.f32", st, BAE_CUDA(cudaLaunchKernelEx(&cfg, k_arn_step_coop<float, true>, a)));
+            else
+                BAE_LAUNCH("k_arn_step_coop.f64", st, BAE_CUDA(cudaLaunchKernelEx(&cfg, k_arn_step_coop<double, true>, a)));
+        } else if (a.v_f32) {
+            BAE_LAUNCH("k_arn_step_coop.f32", st, BAE_CUDA(cudaLaunchKernelEx(&cfg, k_arn_step_coop<float, false>, a)));
+        } else {
+            BAE_LAUNCH("k_arn_step_coop.f64", st, BAE_CUDA(cudaLaunchKernelEx(&cfg, k_arn_step_coop<double, false>, a)));
+        }
         return;
     }
     const dim3 grid(a.nchunk, a.nb);

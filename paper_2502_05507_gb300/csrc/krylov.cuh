@@ -66,6 +66,7 @@ struct Arnoldi {
     // a multiple of coop_grid between steps), an error flag set when a
     // barrier wait runs out, and [nb] squared norms
     int coop_grid = 0;
+    bool coop_resident = false;   // one CTA per chunk, basis chunk in shared memory
     unsigned long long* bar = nullptr;
     int* err = nullptr;
     double* n2 = nullptr;
@@ -84,7 +85,9 @@ void arn_step(const Arnoldi& a, cudaStream_t st);
 // CTAs of the fused cooperative step for this batch (0 if the device cannot
 // run it: no cooperative launch, or more than 64 right-hand sides); call
 // before any graph capture.
-int arn_coop_grid(int n, int nb, int m);
+// *resident: every (RHS, chunk) item gets its own resident CTA, which keeps
+// its chunk of the basis in shared memory.
+int arn_coop_grid(int n, int nb, int m, bool* resident);
 // End of a cycle: y = R^{-1} g for every RHS with ncols > 0, x += V y.
 void arn_finish(const Arnoldi& a, double* x, int maxcols, cudaStream_t st);
 
