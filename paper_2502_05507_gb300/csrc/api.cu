@@ -139,7 +139,7 @@ struct Workspace {
     Grow<double> v64, up, vstage;             // [nb][N^3]
     Grow<float> v32;
     Grow<double> V, w, partial, h, hsave, x, r, bvec, tmp, qstage, n2;   // Krylov
-    Grow<double> arnH, arnCS, arnG, arnY, arnScal;
+    Grow<double> arnH, arnCS, arnG, arnY, arnScal, arnP;
     Grow<int> active, arnI;
     Grow<unsigned int> arnCtr;
     Grow<unsigned long long> arnBar;
@@ -148,7 +148,7 @@ struct Workspace {
         Grow<double>* ds[] = {&v64, &up, &vstage, &V, &w, &partial, &h, &hsave, &x, &r, &bvec, &tmp,
                               &qstage, &n2, &in_f, &in_g, &out_q, &out_u};
         for (auto* d : ds) d->st = st;
-        Grow<double>* ds2[] = {&arnH, &arnCS, &arnG, &arnY, &arnScal};
+        Grow<double>* ds2[] = {&arnH, &arnCS, &arnG, &arnY, &arnScal, &arnP};
         for (auto* d : ds2) d->st = st;
         A.st = B.st = st;
         v32.st = st;
@@ -475,7 +475,7 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
     a.target = scal + nb;
     a.inv = scal + 2 * nb;
     double* nrm2 = scal + 3 * nb;
-    int* ibuf = ws.arnI.need((long long)nb * 4 + 1);
+    int* ibuf = ws.arnI.need((long long)nb * 6 + 1);
     a.flag = ibuf;
     a.ncols = ibuf + nb;
     int* member = ibuf + 2 * nb;
@@ -483,9 +483,13 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
     a.ctr = reinterpret_cast<unsigned int*>(ws.arnCtr.need((long long)nb * 3));
     // the fused cooperative step where the device can place it
     a.coop_grid = arn_coop_grid(n, nb, m, &a.coop_resident);
-    a.bar = ws.arnBar.need(1);
+    a.bar = ws.arnBar.need(2);
+    a.bar2 = a.bar + 1;
     a.err = ibuf + 4 * nb;
+    a.gflag = ibuf + 4 * nb + 1;
+    a.live = ibuf + 5 * nb + 1;
     a.n2 = scal + 4 * nb;
+    a.pcol = ws.arnP.need((long long)nb * 2 * (m + 2));
     double* r = ws.r.need((long long)nb * n);
     double* tmp = ws.tmp.need((long long)nb * n);
     double* npart = ws.n2.need((long long)nb * krylov_chunks(n) + nb);
@@ -502,7 +506,7 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
     BAE_CUDA(cudaMemcpyAsync(d_all, all.data(), nb * sizeof(int), cudaMemcpyHostToDevice, st));
     BAE_CUDA(cudaMemcpyAsync(a.target, tgt.data(), nb * sizeof(double), cudaMemcpyHostToDevice, st));
     BAE_CUDA(cudaMemsetAsync(a.ctr, 0, (size_t)nb * 3 * sizeof(unsigned int), st));
-    BAE_CUDA(cudaMemsetAsync(a.bar, 0, sizeof(unsigned long long), st));
+    BAE_CUDA(cudaMemsetAsync(a.bar, 0, 2 * sizeof(unsigned long long), st));
     BAE_CUDA(cudaMemsetAsync(a.err, 0, sizeof(int), st));
     int* hflag = P->ctx->pinned_flags(nb);
     cudaEvent_t ev[2] = {P->ctx->poll_ev[0], P->ctx->poll_ev[1]};
@@ -564,7 +568,9 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
             }
             kr_norm2(r, d_all, nb, n, npart + nb, krylov_chunks(n), npart, st);
             arn_init(a, r, npart, member, st);
-            const int steps = std::min(m, iters_left);
+            // the fused step applies the rotations of a column one step later:
+            // one more launch finishes the last column of the cycle
+            const int steps = std::min(m, iters_left) + (a.coop_grid > 0 ? 1 : 0);
             int launched = 0;
             for (int it = 0; it < steps; ++it) {
                 if (use_graph) {
@@ -591,7 +597,7 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
                     one_step();
                 }
                 ++launched;
-                BAE_CUDA(cudaMemcpyAsync(hflag + (it & 1) * nb, a.flag, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
+                BAE_CUDA(cudaMemcpyAsync(hflag + (it & 1) * nb, a.live, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
                 BAE_CUDA(cudaEventRecord(ev[it & 1], st));
                 if (it >= 1) {
                     BAE_CUDA(cudaEventSynchronize(ev[(it - 1) & 1]));

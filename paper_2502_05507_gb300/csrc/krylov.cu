@@ -134,6 +134,8 @@ __global__ void k_arn_init(Arnoldi a, const double* __restrict__ nrm2, const int
         g[0] = beta;
         a.est[b] = beta;
         a.flag[b] = go ? 1 : 0;
+        a.live[b] = go ? 1 : 0;
+        if (a.gflag) a.gflag[b] = 0;
         a.inv[b] = beta > 0.0 ? 1.0 / beta : 0.0;
         a.ncols[b] = 0;
         a.j[b] = 0;
@@ -263,6 +265,28 @@ __device__ __forceinline__ void chunk_dots(const RowView& V, int cols, const dou
     }
 }
 
+// Applies the rotations (s_cs[i], s_sn[i]), i < j, to the Hessenberg column
+// s_col[0..j+1] (s_col[j+1] = the new subdiagonal), forms the rotation that
+// zeroes s_col[j+1] (stored in cs[j], sn[j]) and rotates g[j], g[j+1]. One
+// thread; the three-kernel and the fused step share it.
+__device__ __forceinline__ void givens_apply(double* s_col, const double* s_cs, const double* s_sn, int j, double* cs,
+                                             double* sn, double* g) {
+    for (int i = 0; i < j; ++i) {
+        const double x0 = s_col[i], x1 = s_col[i + 1];
+        s_col[i] = s_cs[i] * x0 + s_sn[i] * x1;
+        s_col[i + 1] = -s_sn[i] * x0 + s_cs[i] * x1;
+    }
+    const double rr = hypot(s_col[j], s_col[j + 1]);
+    const double cj = rr > 0.0 ? s_col[j] / rr : 1.0;
+    const double sj = rr > 0.0 ? s_col[j + 1] / rr : 0.0;
+    cs[j] = cj;
+    sn[j] = sj;
+    s_col[j] = rr;
+    s_col[j + 1] = 0.0;
+    g[j + 1] = -sj * g[j];
+    g[j] = cj * g[j];
+}
+
 // pass 1: w = A V[j] by the closure gather of the potential v (the same
 // expression as closure_gather), then h1 = V^T w over rows i <= j
 template <typename VT>
@@ -363,25 +387,13 @@ __global__ void __launch_bounds__(256) k_arn_update_dots(Arnoldi a) {
             const double hn = sqrt(s_n2);
             double* g = a.g + (long long)b * (m + 1);
             s_col[j + 1] = hn;
-            for (int i = 0; i < j; ++i) {
-                const double x0 = s_col[i], x1 = s_col[i + 1];
-                s_col[i] = s_cs[i] * x0 + s_sn[i] * x1;
-                s_col[i + 1] = -s_sn[i] * x0 + s_cs[i] * x1;
-            }
-            const double rr = hypot(s_col[j], s_col[j + 1]);
-            const double cj = rr > 0.0 ? s_col[j] / rr : 1.0;
-            const double sj = rr > 0.0 ? s_col[j + 1] / rr : 0.0;
-            cs[j] = cj;
-            sn[j] = sj;
-            s_col[j] = rr;
-            s_col[j + 1] = 0.0;
-            g[j + 1] = -sj * g[j];
-            g[j] = cj * g[j];
+            givens_apply(s_col, s_cs, s_sn, j, cs, sn, g);
             const double e = fabs(g[j + 1]);
             a.est[b] = e;
             a.ncols[b] = j + 1;
             a.inv[b] = hn > 0.0 ? 1.0 / hn : 0.0;
             a.flag[b] = (e > a.target[b] && hn > 0.0 && j + 1 < m) ? 1 : 0;
+            a.live[b] = a.flag[b];
             a.j[b] = j + 1;   // every block of this RHS has read j already
             a.ctr[3 * b + 1] = 0;
         }
@@ -448,11 +460,11 @@ __device__ __forceinline__ void grid_barrier(unsigned long long* ctr, unsigned l
 // iterating right-hand sides, one warp per row, in the order of reduce_rows;
 // with add, also out2 = out and out = add + out. Row m + 1 (the squared
 // norm partials) goes to n2[b] when n2 is set.
-__device__ __forceinline__ void coop_reduce(const Arnoldi& a, const int* s_j, const int* s_flag, double* out,
-                                            double* out2, const double* add, double* n2) {
+__device__ __forceinline__ void coop_reduce(const Arnoldi& a, int nctas, const int* s_j, const int* s_flag,
+                                            double* out, double* out2, const double* add, double* n2) {
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int nw = gridDim.x * (blockDim.x >> 5);
+    const int nw = nctas * (blockDim.x >> 5);
     const int rows = a.m + 2;
     for (int item = gw; item < a.nb * rows; item += nw) {
         const int b = item / rows, i = item % rows;
@@ -493,14 +505,59 @@ __global__ void __launch_bounds__(256) k_arn_step_coop(Arnoldi a) {
     __shared__ double s_red[2];
     __shared__ int s_j[COOP_MAX_NB], s_flag[COOP_MAX_NB];
     const unsigned long long G = gridDim.x;
+    const int NI = (int)gridDim.x - a.nb;   // chunk CTAs; the last nb CTAs do the rotations
     const int items = a.nb * a.nchunk;
-    // step index and flags as they were at the start of the step (the Givens
-    // CTA of each right-hand side advances them at the end)
+    // step index and flags as they were at the start of the step (the
+    // rotation CTAs advance them at the end)
     for (int b = threadIdx.x; b < a.nb; b += blockDim.x) {
         s_j[b] = a.j[b];
         s_flag[b] = a.flag[b];
     }
     __syncthreads();
+
+    if ((int)blockIdx.x >= NI) {
+        // ---- rotations of the column stored by the previous step
+        const int b = (int)blockIdx.x - NI;
+        const int j = s_j[b];
+        const bool pending = a.gflag[b] != 0;   // column j - 1 waits in pcol[b][(j - 1) % 2]
+        const int c = j - 1;
+        double* cs = a.cs + (long long)b * m;
+        double* sn = a.sn + (long long)b * m;
+        if (pending) {
+            const double* pc = a.pcol + ((long long)b * 2 + (c & 1)) * (m + 2);
+            for (int i = threadIdx.x; i <= c + 1; i += blockDim.x) s_col[i] = pc[i];
+            for (int i = threadIdx.x; i < c; i += blockDim.x) {
+                s_cs[i] = cs[i];
+                s_sn[i] = sn[i];
+            }
+        }
+        // every chunk CTA has read j and the flags once all CTAs are here
+        grid_barrier(a.bar, G, a.err);
+        if (threadIdx.x == 0) {
+            bool converged = false;
+            if (pending) {
+                const double hn = s_col[c + 1];
+                givens_apply(s_col, s_cs, s_sn, c, cs, sn, a.g + (long long)b * (m + 1));
+                const double e = fabs(a.g[(long long)b * (m + 1) + c + 1]);
+                a.est[b] = e;
+                a.ncols[b] = c + 1;
+                converged = !(e > a.target[b] && hn > 0.0);
+            }
+            const bool ran = s_flag[b] != 0;   // the chunk CTAs computed column j in this step
+            const int gf = (ran && !converged) ? 1 : 0;
+            const int fl = (ran && !converged && j + 1 < m) ? 1 : 0;
+            a.gflag[b] = gf;
+            a.flag[b] = fl;
+            a.live[b] = gf | fl;
+            a.j[b] = ran ? j + 1 : j;
+        }
+        __syncthreads();
+        if (pending) {
+            double* col = a.H + ((long long)b * m + c) * (m + 1);
+            for (int i = threadIdx.x; i <= c + 1; i += blockDim.x) col[i] = s_col[i];
+        }
+        return;   // takes part in the first barrier only
+    }
 
     if (SV && blockIdx.x < items && s_flag[blockIdx.x / a.nchunk]) {
         // the chunk of V[0..j] into shared memory, clamped at the vector end
@@ -517,7 +574,7 @@ __global__ void __launch_bounds__(256) k_arn_step_coop(Arnoldi a) {
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     }
     // phase 1: w = gather of v, partial dots against V[0..j]
-    for (int item = blockIdx.x; item < items; item += gridDim.x) {
+    for (int item = blockIdx.x; item < items; item += NI) {
         const int b = item / a.nchunk, c = item % a.nchunk;
         if (!s_flag[b]) continue;
         const long long r0 = (long long)c * ACH;
@@ -539,12 +596,13 @@ __global__ void __launch_bounds__(256) k_arn_step_coop(Arnoldi a) {
         chunk_dots(V, s_j[b] + 1, s_w, a.part + (long long)b * (m + 2) * a.nchunk, a.nchunk, c);
         __syncthreads();
     }
-    grid_barrier(a.bar, G, a.err);
+    grid_barrier(a.bar, G, a.err);            // all G CTAs
+    const unsigned long long GI = (unsigned long long)NI;
     // phase 2: h1
-    coop_reduce(a, s_j, s_flag, a.h1, nullptr, nullptr, nullptr);
-    grid_barrier(a.bar, G, a.err);
+    coop_reduce(a, NI, s_j, s_flag, a.h1, nullptr, nullptr, nullptr);
+    grid_barrier(a.bar2, GI, a.err);          // chunk CTAs only from here on
     // phase 3: w -= V h1, partial dots for h2 and ||w||^2
-    for (int item = blockIdx.x; item < items; item += gridDim.x) {
+    for (int item = blockIdx.x; item < items; item += NI) {
         const int b = item / a.nchunk, c = item % a.nchunk;
         if (!s_flag[b]) continue;
         const int cols = s_j[b] + 1;
@@ -565,14 +623,15 @@ __global__ void __launch_bounds__(256) k_arn_step_coop(Arnoldi a) {
         }
         __syncthreads();
     }
-    grid_barrier(a.bar, G, a.err);
+    grid_barrier(a.bar2, GI, a.err);
     // phase 4: h2 (into h1), hcol = h1 + h2, ||w||^2
-    coop_reduce(a, s_j, s_flag, a.hcol, a.h1, a.h1, a.n2);
-    grid_barrier(a.bar, G, a.err);
+    coop_reduce(a, NI, s_j, s_flag, a.hcol, a.h1, a.h1, a.n2);
+    grid_barrier(a.bar2, GI, a.err);
 
     // phase 5: hn = sqrt(||w||^2 - ||h2||^2) (every CTA, same order), then
-    // V[j+1] = (w - V h2) / hn; CTA b % G also does the Givens update of b
-    for (int item = blockIdx.x; item < items; item += gridDim.x) {
+    // V[j+1] = (w - V h2) / hn; the CTA of chunk 0 stores the column
+    // (hcol, then hn) for the rotations of the next step
+    for (int item = blockIdx.x; item < items; item += NI) {
         const int b = item / a.nchunk, c = item % a.nchunk;
         if (!s_flag[b]) continue;
         const int j = s_j[b], cols = j + 1;
@@ -592,63 +651,17 @@ __global__ void __launch_bounds__(256) k_arn_step_coop(Arnoldi a) {
             }
         }
         __syncthreads();
+        if (c == 0) {
+            double* pc = a.pcol + ((long long)b * 2 + (j & 1)) * (m + 2);
+            const double* hc = a.hcol + (long long)b * (m + 1);
+            for (int i = threadIdx.x; i <= j; i += blockDim.x) pc[i] = __ldcg(hc + i);
+            if (threadIdx.x == 0) pc[j + 1] = s_red[0];
+        }
         double* Vb = a.V + (long long)b * (m + 1) * a.n;
         const long long r0 = (long long)c * ACH;
         const RowView V = SV ? shared_rows(s_V) : global_rows(Vb, a.n, r0);
         chunk_update(V, a.n, r0, cols, s_h, a.w + (long long)b * a.n, s_acc, s_w, Vb + (long long)(j + 1) * a.n,
                      s_red[1]);
-        __syncthreads();
-    }
-    for (int b = blockIdx.x; b < a.nb; b += gridDim.x) {
-        if (!s_flag[b]) continue;
-        const int j = s_j[b];
-        const double* hc = a.hcol + (long long)b * (m + 1);
-        const double* h2 = a.h1 + (long long)b * (m + 1);
-        double* cs = a.cs + (long long)b * m;
-        double* sn = a.sn + (long long)b * m;
-        for (int i = threadIdx.x; i <= j; i += blockDim.x) s_col[i] = __ldcg(hc + i);
-        for (int i = threadIdx.x; i < j; i += blockDim.x) {
-            s_cs[i] = cs[i];
-            s_sn[i] = sn[i];
-        }
-        if (threadIdx.x < 32) {
-            double acc = 0.0;
-            for (int i = threadIdx.x; i <= j; i += 32) {
-                const double x = __ldcg(h2 + i);
-                acc += x * x;
-            }
-            acc = warp_sum(acc);
-            if (threadIdx.x == 0) s_red[0] = sqrt(fmax(__ldcg(a.n2 + b) - acc, 0.0));
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const double hn = s_red[0];
-            double* g = a.g + (long long)b * (m + 1);
-            s_col[j + 1] = hn;
-            for (int i = 0; i < j; ++i) {
-                const double x0 = s_col[i], x1 = s_col[i + 1];
-                s_col[i] = s_cs[i] * x0 + s_sn[i] * x1;
-                s_col[i + 1] = -s_sn[i] * x0 + s_cs[i] * x1;
-            }
-            const double rr = hypot(s_col[j], s_col[j + 1]);
-            const double cj = rr > 0.0 ? s_col[j] / rr : 1.0;
-            const double sj = rr > 0.0 ? s_col[j + 1] / rr : 0.0;
-            cs[j] = cj;
-            sn[j] = sj;
-            s_col[j] = rr;
-            s_col[j + 1] = 0.0;
-            g[j + 1] = -sj * g[j];
-            g[j] = cj * g[j];
-            const double e = fabs(g[j + 1]);
-            a.est[b] = e;
-            a.ncols[b] = j + 1;
-            a.inv[b] = hn > 0.0 ? 1.0 / hn : 0.0;
-            a.flag[b] = (e > a.target[b] && hn > 0.0 && j + 1 < m) ? 1 : 0;
-            a.j[b] = j + 1;
-        }
-        __syncthreads();
-        double* col = a.H + ((long long)b * m + j) * (m + 1);
-        for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) col[i] = s_col[i];
         __syncthreads();
     }
 }
@@ -710,16 +723,18 @@ int arn_coop_grid(int n, int nb, int m, bool* resident) {
         int s32 = 0, s64 = 0;
         BAE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s32, k_arn_step_coop<float, true>, 256, sh_sv));
         BAE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s64, k_arn_step_coop<double, true>, 256, sh_sv));
-        if (items <= (long long)std::min(s32, s64) * sms) {
+        if (items + nb <= (long long)std::min(s32, s64) * sms) {   // one CTA per chunk plus one rotation CTA per right-hand side
             *resident = true;
-            return (int)items;
+            return (int)(items + nb);
         }
     }
     int k32 = 0, k64 = 0;
     BAE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k32, k_arn_step_coop<float, false>, 256, sh));
     BAE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k64, k_arn_step_coop<double, false>, 256, sh));
     const long long cap = (long long)std::min(k32, k64) * sms;
-    return (int)std::min(cap, items);
+    // persistent chunk CTAs plus one rotation CTA per right-hand side
+    if (cap <= nb) return 0;
+    return (int)std::min(cap, items + nb);
 }
 
 void arn_step(const Arnoldi& a, cudaStream_t st) {
@@ -727,8 +742,9 @@ void arn_step(const Arnoldi& a, cudaStream_t st) {
     const size_t sh_h = (size_t)(a.m + 1) * sizeof(double);
     const size_t sh_g = (size_t)(4 * a.m + 3) * sizeof(double);
     if (a.coop_grid > 0) {
-        BAE_REQUIRE(a.bar && a.err && a.n2 && a.nb <= COOP_MAX_NB, BAE_ERR_INVALID_ARG,
-                    "arn_step: cooperative step state not set");
+        BAE_REQUIRE(a.bar && a.bar2 && a.err && a.n2 && a.gflag && a.live && a.pcol && a.nb <= COOP_MAX_NB &&
+                        a.coop_grid > a.nb,
+                    BAE_ERR_INVALID_ARG, "arn_step: cooperative step state not set");
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(a.coop_grid);
         cfg.blockDim = dim3(256);
@@ -740,7 +756,8 @@ void arn_step(const Arnoldi& a, cudaStream_t st) {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         if (a.coop_resident) {
-            BAE_REQUIRE(a.coop_grid == a.nb * a.nchunk, BAE_ERR_INVALID_ARG, "arn_step: resident step needs one CTA per chunk");
+            BAE_REQUIRE(a.coop_grid == a.nb * a.nchunk + a.nb, BAE_ERR_INVALID_ARG,
+                        "arn_step: resident step needs one CTA per chunk and per right-hand side");
             if (a.v_f32)
                 BAE_LAUNCH("k_arn_step_coop.f32", st, BAE_CUDA(cudaLaunchKernelEx(&cfg, k_arn_step_coop<float, true>, a)));
             else

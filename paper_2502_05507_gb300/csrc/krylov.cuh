@@ -70,6 +70,18 @@ struct Arnoldi {
     unsigned long long* bar = nullptr;
     int* err = nullptr;
     double* n2 = nullptr;
+    // In the fused step the Givens rotations of column j run one step later,
+    // on the last nb CTAs of the grid, while the other CTAs compute column
+    // j + 1: the step stores column j (h1 + h2, and ||w - V h2|| after it)
+    // in pcol[b][j % 2] and sets gflag[b]; the next step applies the
+    // rotations, updates g and the residual estimate, and decides flag[b]
+    // (the right-hand side that converged at column j has computed column
+    // j + 1 for nothing). live[b] = flag[b] | gflag[b] tells the host that
+    // another step is needed; bar2 counts the barriers of the chunk CTAs.
+    int* gflag = nullptr;                  // [nb]
+    int* live = nullptr;                   // [nb]
+    double* pcol = nullptr;                // [nb][2][m + 2]
+    unsigned long long* bar2 = nullptr;
 };
 
 // number of vector chunks (CTAs per RHS) of the Arnoldi passes
