@@ -169,22 +169,31 @@ __device__ __forceinline__ void reduce_rows(const double* part, int nch, int col
     }
 }
 
-// The chunk [r0, r0 + 64) of the basis rows, as seen by lane l of a warp:
-// elements base[i rs + oa] and base[i rs + ob] of row i (global memory with
-// indices clamped to the vector, or a shared-memory copy of the chunk).
+// The chunk [r0, r0 + 64) of the basis rows: element e of row i is
+// base[i rs + off(e)], off(e) = min(r0 + e, n - 1) in global memory (indices
+// clamped to the vector) or e in a shared-memory copy (row stride ACH + 1,
+// so that lanes reading different rows hit different banks). oa, ob: the
+// offsets of this lane's two elements (e = lane, lane + 32).
 struct RowView {
     const double* base;
     long long rs, oa, ob;
+    long long r0, nlast;   // global: r0 and n - 1; shared: nlast < 0
+    __device__ __forceinline__ double at(int i, int e) const {
+        const long long o = nlast < 0 ? (long long)e : min(r0 + e, nlast);
+        return base[(long long)i * rs + o];
+    }
 };
+
+constexpr int SV_STRIDE = ACH + 1;
 
 __device__ __forceinline__ RowView global_rows(const double* Vb, long long n, long long r0) {
     const int lane = threadIdx.x & 31;
-    return {Vb, n, min(r0 + lane, n - 1), min(r0 + lane + 32, n - 1)};
+    return {Vb, n, min(r0 + lane, n - 1), min(r0 + lane + 32, n - 1), r0, n - 1};
 }
 
 __device__ __forceinline__ RowView shared_rows(const double* sV) {
     const int lane = threadIdx.x & 31;
-    return {sV, ACH, lane, lane + 32};
+    return {sV, SV_STRIDE, lane, lane + 32, 0, -1};
 }
 
 // w[r0 .. r0+ACH) -= V[0..cols) h over the chunk; 8 warps split the rows
@@ -233,35 +242,42 @@ __device__ __forceinline__ void chunk_update(const RowView& V, long long n, long
     __syncthreads();
 }
 
-// partial dots of the chunk against rows i < cols: part[i][c] (four rows
-// per warp per loop trip)
+// partial dots of the chunk against rows i < cols: part[i][c]. Warp q sums
+// the elements [8q, 8q + 8) of 32 rows at a time (lane = row, two
+// accumulators), then warp 0 adds the eight warp partials of its row in
+// warp order: ~2 float64 warp instructions per row instead of a shuffle
+// tree per row (each float64 warp instruction occupies GB300's FP64 pipe
+// for ~64 cycles). s_red: 8 x 32 doubles of shared memory.
 __device__ __forceinline__ void chunk_dots(const RowView& V, int cols, const double* s_w, double* part, int nch,
-                                           int c) {
+                                           int c, double* s_red) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const double wa = s_w[lane], wb = s_w[lane + 32];
-    int i = warp;
-    for (; i + 24 < cols; i += 32) {
-        const double* v0 = V.base + (long long)i * V.rs;
-        double d0 = v0[V.oa] * wa + v0[V.ob] * wb;
-        double d1 = v0[8 * V.rs + V.oa] * wa + v0[8 * V.rs + V.ob] * wb;
-        double d2 = v0[16 * V.rs + V.oa] * wa + v0[16 * V.rs + V.ob] * wb;
-        double d3 = v0[24 * V.rs + V.oa] * wa + v0[24 * V.rs + V.ob] * wb;
-        d0 = warp_sum(d0);
-        d1 = warp_sum(d1);
-        d2 = warp_sum(d2);
-        d3 = warp_sum(d3);
-        if (lane == 0) {
-            part[(long long)i * nch + c] = d0;
-            part[(long long)(i + 8) * nch + c] = d1;
-            part[(long long)(i + 16) * nch + c] = d2;
-            part[(long long)(i + 24) * nch + c] = d3;
+    double wv[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) wv[u] = s_w[8 * warp + u];
+    for (int i0 = 0; i0 < cols; i0 += 32) {
+        const int i = i0 + lane;
+        double acc = 0.0;
+        if (i < cols) {
+            double x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) x[u] = V.at(i, 8 * warp + u);
+            double p0 = x[0] * wv[0], p1 = x[1] * wv[1];
+#pragma unroll
+            for (int u = 2; u < 8; u += 2) {
+                p0 = __fma_rn(x[u], wv[u], p0);
+                p1 = __fma_rn(x[u + 1], wv[u + 1], p1);
+            }
+            acc = p0 + p1;
         }
-    }
-    for (; i < cols; i += 8) {
-        const double* v = V.base + (long long)i * V.rs;
-        double acc = v[V.oa] * wa + v[V.ob] * wb;
-        acc = warp_sum(acc);
-        if (lane == 0) part[(long long)i * nch + c] = acc;
+        s_red[warp * 32 + lane] = acc;
+        __syncthreads();
+        if (warp == 0 && i < cols) {
+            double t = s_red[lane];
+#pragma unroll
+            for (int q = 1; q < 8; ++q) t += s_red[q * 32 + lane];
+            part[(long long)i * nch + c] = t;
+        }
+        __syncthreads();
     }
 }
 
@@ -292,6 +308,7 @@ __device__ __forceinline__ void givens_apply(double* s_col, const double* s_cs, 
 template <typename VT>
 __global__ void __launch_bounds__(256) k_arn_gather_dots(Arnoldi a) {
     __shared__ double s_w[ACH];
+    __shared__ double s_red8[8 * 32];
     __shared__ int s_last;
     const int b = blockIdx.y;
     if (!a.flag[b]) return;
@@ -313,7 +330,7 @@ __global__ void __launch_bounds__(256) k_arn_gather_dots(Arnoldi a) {
     __syncthreads();
     double* part = a.part + (long long)b * (a.m + 2) * a.nchunk;
     const double* Vb = a.V + (long long)b * (a.m + 1) * a.n;
-    chunk_dots(global_rows(Vb, a.n, r0), cols, s_w, part, a.nchunk, c);
+    chunk_dots(global_rows(Vb, a.n, r0), cols, s_w, part, a.nchunk, c, s_red8);
     if (last_block(a.ctr + 3 * b + 0, gridDim.x, &s_last)) {
         reduce_rows(part, a.nchunk, cols, a.h1 + (long long)b * (a.m + 1), nullptr, nullptr);
         if (threadIdx.x == 0) a.ctr[3 * b + 0] = 0;
@@ -348,7 +365,7 @@ __global__ void __launch_bounds__(256) k_arn_update_dots(Arnoldi a) {
     const double* Vb = a.V + (long long)b * (m + 1) * a.n;
     chunk_update(global_rows(Vb, a.n, r0), a.n, r0, cols, s_h, a.w + (long long)b * a.n, s_acc, s_w);
     double* part = a.part + (long long)b * (m + 2) * a.nchunk;
-    chunk_dots(global_rows(Vb, a.n, r0), cols, s_w, part, a.nchunk, c);
+    chunk_dots(global_rows(Vb, a.n, r0), cols, s_w, part, a.nchunk, c, s_acc);
     if (threadIdx.x >= 224) {   // the last warp: ||w||^2 over the chunk
         const int l = threadIdx.x - 224;
         double acc = s_w[l] * s_w[l] + s_w[l + 32] * s_w[l + 32];
@@ -499,7 +516,7 @@ __global__ void __launch_bounds__(256) k_arn_step_coop(Arnoldi a) {
     double* s_col = s_dyn + (m + 1);     // m + 2
     double* s_cs = s_col + (m + 2);      // m
     double* s_sn = s_cs + m;             // m
-    double* s_V = s_sn + m;              // SV: (m + 1) x ACH
+    double* s_V = s_sn + m;              // SV: (m + 1) x SV_STRIDE
     __shared__ double s_acc[8 * ACH];
     __shared__ double s_w[ACH];
     __shared__ double s_red[2];
@@ -568,7 +585,7 @@ __global__ void __launch_bounds__(256) k_arn_step_coop(Arnoldi a) {
         for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
             const int i = e / ACH, l = e % ACH;
             const double* src = Vb + (long long)i * a.n + min(r0 + l, (long long)a.n - 1);
-            const unsigned dst = (unsigned)__cvta_generic_to_shared(s_V + e);
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(s_V + i * SV_STRIDE + l);
             asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -593,7 +610,7 @@ __global__ void __launch_bounds__(256) k_arn_step_coop(Arnoldi a) {
         if (SV) asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         __syncthreads();
         const RowView V = SV ? shared_rows(s_V) : global_rows(a.V + (long long)b * (m + 1) * a.n, a.n, r0);
-        chunk_dots(V, s_j[b] + 1, s_w, a.part + (long long)b * (m + 2) * a.nchunk, a.nchunk, c);
+        chunk_dots(V, s_j[b] + 1, s_w, a.part + (long long)b * (m + 2) * a.nchunk, a.nchunk, c, s_acc);
         __syncthreads();
     }
     grid_barrier(a.bar, G, a.err);            // all G CTAs
@@ -614,7 +631,7 @@ __global__ void __launch_bounds__(256) k_arn_step_coop(Arnoldi a) {
         double* part = a.part + (long long)b * (m + 2) * a.nchunk;
         const RowView V = SV ? shared_rows(s_V) : global_rows(Vb, a.n, r0);
         chunk_update(V, a.n, r0, cols, s_h, a.w + (long long)b * a.n, s_acc, s_w);
-        chunk_dots(V, cols, s_w, part, a.nchunk, c);
+        chunk_dots(V, cols, s_w, part, a.nchunk, c, s_acc);
         if (threadIdx.x >= 224) {
             const int l = threadIdx.x - 224;
             double acc = s_w[l] * s_w[l] + s_w[l + 32] * s_w[l + 32];
@@ -713,7 +730,7 @@ int arn_coop_grid(int n, int nb, int m, bool* resident) {
     const size_t sh = (size_t)(4 * m + 3) * sizeof(double);
     const long long items = (long long)nb * ceil_div(n, ACH);
     // resident basis chunks: one item per CTA, all CTAs on the device at once
-    const size_t sh_sv = sh + (size_t)(m + 1) * ACH * sizeof(double);
+    const size_t sh_sv = sh + (size_t)(m + 1) * SV_STRIDE * sizeof(double);
     *resident = false;
     if (sh_sv <= 200 * 1024) {
         BAE_CUDA(cudaFuncSetAttribute(k_arn_step_coop<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -748,7 +765,7 @@ void arn_step(const Arnoldi& a, cudaStream_t st) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(a.coop_grid);
         cfg.blockDim = dim3(256);
-        cfg.dynamicSmemBytes = sh_g + (a.coop_resident ? (size_t)(a.m + 1) * ACH * sizeof(double) : 0);
+        cfg.dynamicSmemBytes = sh_g + (a.coop_resident ? (size_t)(a.m + 1) * SV_STRIDE * sizeof(double) : 0);
         cfg.stream = st;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeCooperative;
