@@ -40,7 +40,7 @@ class GeometryError(BAEError):
 class Options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("restart", ctypes.c_int),
                 ("precision", ctypes.c_int), ("max_refine", ctypes.c_int), ("inner_tol", ctypes.c_double),
-                ("use_graphs", ctypes.c_int), ("residual_precision", ctypes.c_int)]
+                ("use_graphs", ctypes.c_int), ("residual_precision", ctypes.c_int), ("precond", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -316,10 +316,12 @@ class Problem:
         return out
 
     def _opts(self, tol, precision, max_iter, restart, max_refine, inner_tol, use_graphs=True,
-              residual_precision=None):
+              residual_precision=None, precond=None):
         o = Options()
         lib().bae_default_options(ctypes.byref(o))
         o.use_graphs = 1 if use_graphs else 0
+        if precond is not None:   # False/0: never, True/1: after the first step, 2: every step
+            o.precond = int(precond)
         if residual_precision is not None:
             o.residual_precision = _PREC[residual_precision]
         o.tol = tol
@@ -336,7 +338,7 @@ class Problem:
 
     def solve(self, f, g, tol=1e-10, precision="fp64", max_iter=None, restart=None, max_refine=None,
               inner_tol=None, density=None, u=None, allow_not_converged=False, use_graphs=True,
-              residual_precision=None):
+              residual_precision=None, precond=None):
         """Returns (density, u, stats dict). f (N^3) and g (n_gm) may be
         torch CUDA tensors or numpy arrays; outputs follow f's kind."""
         f = _as_f64(f)
@@ -344,14 +346,15 @@ class Problem:
         density = _new((self.n_gm,), np.float64, f) if density is None else density
         u = _new((self.N,) * 3, np.float64, f) if u is None else u
         st = Stats()
-        o = self._opts(tol, precision, max_iter, restart, max_refine, inner_tol, use_graphs, residual_precision)
+        o = self._opts(tol, precision, max_iter, restart, max_refine, inner_tol, use_graphs, residual_precision,
+                       precond)
         rc = lib().bae_solve(self._h, _ptr(f), _ptr(g), ctypes.byref(o), _ptr(density), _ptr(u), ctypes.byref(st))
         _check(rc, allow_not_converged)
         return density, u, st.as_dict()
 
     def solve_batched(self, f, g, tol=1e-10, precision="fp64", max_iter=None, restart=None, max_refine=None,
                       inner_tol=None, density=None, u=None, allow_not_converged=False, use_graphs=True,
-                      residual_precision=None):
+                      residual_precision=None, precond=None):
         """f [nrhs, N, N, N], g [nrhs, n_gm]; returns (density, u, [stats])."""
         f = _as_f64(f)
         g = _as_f64(g)
@@ -359,7 +362,8 @@ class Problem:
         density = _new((nrhs, self.n_gm), np.float64, f) if density is None else density
         u = _new((nrhs,) + (self.N,) * 3, np.float64, f) if u is None else u
         st = (Stats * nrhs)()
-        o = self._opts(tol, precision, max_iter, restart, max_refine, inner_tol, use_graphs, residual_precision)
+        o = self._opts(tol, precision, max_iter, restart, max_refine, inner_tol, use_graphs, residual_precision,
+                       precond)
         rc = lib().bae_solve_batched(self._h, nrhs, _ptr(f), _ptr(g), ctypes.byref(o), _ptr(density), _ptr(u),
                                      st)
         _check(rc, allow_not_converged)

@@ -21,6 +21,7 @@
 #include "internal.cuh"
 #include "krylov.cuh"
 #include "lgf.cuh"
+#include "precond.cuh"
 
 namespace bae {
 
@@ -144,9 +145,10 @@ struct Workspace {
     Grow<unsigned int> arnCtr;
     Grow<unsigned long long> arnBar;
     Grow<double> in_f, in_g, out_q, out_u;    // staging of host arguments
+    Grow<double> qpre, zpre;                  // M^{-1} y of the preconditioned inner solves
     void set_stream(cudaStream_t st) {
         Grow<double>* ds[] = {&v64, &up, &vstage, &V, &w, &partial, &h, &hsave, &x, &r, &bvec, &tmp,
-                              &qstage, &n2, &in_f, &in_g, &out_q, &out_u};
+                              &qstage, &n2, &in_f, &in_g, &out_q, &out_u, &qpre, &zpre};
         for (auto* d : ds) d->st = st;
         Grow<double>* ds2[] = {&arnH, &arnCS, &arnG, &arnY, &arnScal, &arnP};
         for (auto* d : ds2) d->st = st;
@@ -247,16 +249,19 @@ struct bae_ctx {
     std::map<int, Twiddles> tw;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaEvent_t poll_ev[2] = {nullptr, nullptr};
-    int* pinned = nullptr;
+    int* pinned = nullptr;       // mapped host memory the kernels write the live flags into
+    int* pinned_dev = nullptr;   // its device address
     int pinned_cap = 0;
     Workspace ws;
 
-    int* pinned_flags(int nb) {   // host-pinned [2][nb] polling buffer
-        if (2 * nb > pinned_cap) {
+    int* pinned_flags(int nb) {   // host-pinned, device-mapped [nb] polling buffer
+        if (nb > pinned_cap) {
             if (pinned) cudaFreeHost(pinned);
             pinned = nullptr;
-            BAE_CUDA(cudaMallocHost(&pinned, 2 * (size_t)nb * sizeof(int)));
-            pinned_cap = 2 * nb;
+            pinned_dev = nullptr;
+            BAE_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&pinned), (size_t)nb * sizeof(int), cudaHostAllocMapped));
+            BAE_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&pinned_dev), pinned, 0));
+            pinned_cap = nb;
         }
         return pinned;
     }
@@ -279,6 +284,7 @@ struct bae_ctx {
 struct bae_problem {
     bae_ctx* ctx = nullptr;
     Geometry geo;
+    Precond pre;   // block-Jacobi right preconditioner, built on the first mixed solve that asks for it
     std::shared_ptr<Spectrum> spec;
     double kappa2 = 0.0, s = 0.0;
     Workspace& ws() { return ctx->ws; }
@@ -448,9 +454,11 @@ void apply_rows_prec(bae_problem* P, int prec, int nb, const double* q, long lon
 // device; with use_graph it is captured once as a CUDA graph and replayed.
 // The host only polls the convergence flags (double-buffered, one step
 // behind) and closes each cycle. x_zero: x is known to be 0.
+// pre: right-preconditioned (x is the preconditioned variable y of
+// A M^{-1} y = rhs; the caller maps it back with M^{-1})
 void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, const double* rhs, double* x,
            bool x_zero, std::vector<RhsState>& S, int max_iter, int restart, std::vector<int>& applies,
-           bool use_graph) {
+           bool use_graph, bool pre = false) {
     cudaStream_t st = P->ctx->stream;
     Workspace& ws = P->ws();
     const int n = (int)n_gm(P);
@@ -508,7 +516,10 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
     BAE_CUDA(cudaMemsetAsync(a.ctr, 0, (size_t)nb * 3 * sizeof(unsigned int), st));
     BAE_CUDA(cudaMemsetAsync(a.bar, 0, 2 * sizeof(unsigned long long), st));
     BAE_CUDA(cudaMemsetAsync(a.err, 0, sizeof(int), st));
-    int* hflag = P->ctx->pinned_flags(nb);
+    // the kernels that decide the flags also write live[b] into mapped host
+    // memory: no copy between the replayed steps
+    volatile int* hlive = P->ctx->pinned_flags(nb);
+    a.live_host = P->ctx->pinned_dev;
     cudaEvent_t ev[2] = {P->ctx->poll_ev[0], P->ctx->poll_ev[1]};
     cudaGraphExec_t exec = nullptr;
     long long graph_kernels = 0;
@@ -523,11 +534,21 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
     a.gm = P->geo.gm;
     a.partner = P->geo.partner;
     a.t = P->geo.t;
+    // right preconditioning: the step applies A to z = M^{-1} V[j]
+    double* zpre = pre ? ws.zpre.need((long long)nb * n) : nullptr;
     auto one_step = [&]() {
-        const long long qs = (long long)(m + 1) * n;
-        if (prec == BAE_FP32) a.v = potential_rows<float>(P, nb, a.V, qs, a.j, n, a.flag);
-        else if (prec == BAE_DF64) a.v = potential_rows<dsf>(P, nb, a.V, qs, a.j, n, a.flag);
-        else a.v = potential_rows<double>(P, nb, a.V, qs, a.j, n, a.flag);
+        const double* q = a.V;
+        long long qs = (long long)(m + 1) * n;
+        const int* qrow = a.j;
+        if (pre) {
+            precond_apply(P->pre, a.V, qs, a.j, n, zpre, n, nb, a.flag, st);
+            q = zpre;
+            qs = n;
+            qrow = nullptr;
+        }
+        if (prec == BAE_FP32) a.v = potential_rows<float>(P, nb, q, qs, qrow, n, a.flag);
+        else if (prec == BAE_DF64) a.v = potential_rows<dsf>(P, nb, q, qs, qrow, n, a.flag);
+        else a.v = potential_rows<double>(P, nb, q, qs, qrow, n, a.flag);
         arn_step(a, st);
     };
     // size every buffer and set every kernel attribute the step needs before
@@ -562,7 +583,12 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
                 BAE_CUDA(cudaMemcpyAsync(r, rhs, (size_t)nb * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
                 x_zero = false;
             } else {
-                apply_rows_prec(P, prec, nb, x, n, nullptr, 0, member, tmp);
+                if (pre) {
+                    precond_apply(P->pre, x, n, nullptr, 0, zpre, n, nb, member, st);
+                    apply_rows_prec(P, prec, nb, zpre, n, nullptr, 0, member, tmp);
+                } else {
+                    apply_rows_prec(P, prec, nb, x, n, nullptr, 0, member, tmp);
+                }
                 for (int b = 0; b < nb; ++b) applies[b] += mem[b];
                 kr_sub(rhs, tmp, d_all, nb, n, r, st);
             }
@@ -597,12 +623,13 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
                     one_step();
                 }
                 ++launched;
-                BAE_CUDA(cudaMemcpyAsync(hflag + (it & 1) * nb, a.live, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
                 BAE_CUDA(cudaEventRecord(ev[it & 1], st));
                 if (it >= 1) {
+                    // after step it - 1 completed the flags are those of that
+                    // step or of a later one (they only drop to 0 in a cycle)
                     BAE_CUDA(cudaEventSynchronize(ev[(it - 1) & 1]));
                     int live = 0;
-                    for (int b = 0; b < nb; ++b) live |= hflag[((it - 1) & 1) * nb + b];
+                    for (int b = 0; b < nb; ++b) live |= hlive[b];
                     if (!live) break;
                 }
             }
@@ -659,6 +686,7 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
                 BAE_ERR_INVALID_ARG, "precision must be BAE_FP64, BAE_MIXED or BAE_DF64");
     BAE_REQUIRE(o.residual_precision == BAE_FP64 || o.residual_precision == BAE_DF64, BAE_ERR_INVALID_ARG,
                 "residual_precision must be BAE_FP64 or BAE_DF64");
+    BAE_REQUIRE(o.precond >= 0 && o.precond <= 2, BAE_ERR_INVALID_ARG, "precond must be 0, 1 or 2");
     // arithmetic of every float64-accurate apply (particular solution,
     // refinement residuals, reconstruction)
     const int hp = o.precision == BAE_MIXED ? o.residual_precision : o.precision;
@@ -760,6 +788,11 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
         // iterative refinement: inner float32-apply GMRES on A d = r, q += d,
         // r = b - A64 q in float64
         double* d = P->ws().vstage.need((long long)nb * n);
+        // block-Jacobi right preconditioner of the inner solves (the inner
+        // unknown is y with d = M^{-1} y)
+        const bool any_pre = o.precond != 0;
+        if (any_pre && !P->pre.built) build_precond(P->geo, P->s, P->pre);
+        double* dq = any_pre ? P->ws().qpre.need((long long)nb * n) : d;
         BAE_CUDA(cudaMemcpyAsync(res, bvec, (size_t)nb * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
         rn2 = bn2;
         for (int b = 0; b < nb; ++b) relres[b] = bn2[b] > 0 ? 1.0 : 0.0;
@@ -769,14 +802,21 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
             for (int b = 0; b < nb; ++b)
                 if (relres[b] > o.tol && bn2[b] > 0) act.push_back(b);
             if (act.empty() || iters_left <= 0) break;
+            // the preconditioner serves the steps after the first (precond 1)
+            // or all steps (precond 2): measured on the torus and star
+            // workloads, it slows the first, coarse reduction and speeds the
+            // later, accurate ones
+            const bool use_pre = o.precond == 2 || (o.precond == 1 && step > 0);
             std::vector<RhsState> Si(nb);
             for (int b : act) {
                 // reduce the residual by inner_tol; when that lands within ten
-                // times the outer target, aim straight at 0.3 tol ||b|| so that
-                // this is the last step (no further float64-accurate residual
-                // and restart); the float32 apply error, ~1e-7 of |A d|, stays
-                // far below that
-                const double rn = std::sqrt(rn2[b]), floor_b = 0.3 * o.tol * std::sqrt(bn2[b]);
+                // times the outer target, aim straight below the outer target
+                // so that this is the last step (no further float64-accurate
+                // residual and restart): at 0.3 tol ||b||, or 0.03 tol ||b|| in
+                // a preconditioned step, whose float32 basis applies leave a
+                // true residual up to ~10 times above the estimate
+                const double floor_b = (use_pre ? 0.03 : 0.3) * o.tol * std::sqrt(bn2[b]);
+                const double rn = std::sqrt(rn2[b]);
                 double tgt = o.inner_tol * rn;
                 if (tgt <= 10.0 * o.tol * std::sqrt(bn2[b])) tgt = floor_b;
                 Si[b].target = std::max(tgt, floor_b);
@@ -785,7 +825,8 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
                 if (std::find(act.begin(), act.end(), b) == act.end()) Si[b].converged = true;
             BAE_CUDA(cudaMemsetAsync(d, 0, (size_t)nb * n * sizeof(double), st));
             std::vector<int> applies(nb, 0);
-            gmres(P, BAE_FP32, nb, act, res, d, true, Si, iters_left, o.restart, applies, o.use_graphs != 0);
+            gmres(P, BAE_FP32, nb, act, res, d, true, Si, iters_left, o.restart, applies, o.use_graphs != 0, use_pre);
+            if (use_pre) precond_apply(P->pre, d, n, nullptr, 0, dq, n, nb, nullptr, st);
             int used = 0;
             for (int b : act) {
                 st_local[b].iterations += Si[b].iterations;
@@ -795,7 +836,7 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
             iters_left -= std::max(used, 1);
             int* d_a = P->ws().active.need(nb);
             BAE_CUDA(cudaMemcpyAsync(d_a, act.data(), act.size() * sizeof(int), cudaMemcpyHostToDevice, st));
-            kr_add(d, d_a, (int)act.size(), n, q, st);
+            kr_add(use_pre ? dq : d, d_a, (int)act.size(), n, q, st);
             for (int b : act) st_local[b].applies_fp32 += applies[b];
             true_residual();
         }
@@ -967,6 +1008,7 @@ void bae_default_options(bae_options* o) {
     o->inner_tol = 1e-5;
     o->use_graphs = 1;
     o->residual_precision = BAE_DF64;
+    o->precond = 1;
 }
 
 int bae_ctx_create(int device, void* stream, bae_ctx** out) {
@@ -1084,6 +1126,7 @@ void bae_problem_destroy(bae_problem* P) {
     if (!P) return;
     cudaSetDevice(P->ctx->device);
     cudaStreamSynchronize(P->ctx->stream);
+    P->pre.release();
     P->geo.release();
     delete P;
 }

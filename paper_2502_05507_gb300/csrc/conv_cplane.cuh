@@ -53,10 +53,7 @@ __global__ void __launch_bounds__(CPlaneGeo<T, L>::PT) k_cplane_fwd(ConvArgs<T> 
                         const int s0 = a.rec.line_off[l], s1 = a.rec.line_off[l + 1];
                         for (int s = s0 + t; s < s1; s += R1) {
                             const int k = a.rec.src_lin[s] - (int)(l * N);
-                            double val = 0.0;
-                            for (int e = a.rec.term_off[s]; e < a.rec.term_off[s + 1]; ++e)
-                                val += (double)a.rec.term_coef[e] * q[a.rec.term_idx[e]];
-                            rr[k] = (T)val;
+                            rr[k] = source_value<T>(a.rec, s, q);
                         }
                     }
                 }

@@ -59,6 +59,27 @@ template <typename T, int L> struct PlaneGeo {
     static constexpr bool FITS = SMEM <= 227 * 1024;
 };
 
+// ---------------------------------------------------- source stencil value
+// rho(x) = sum of coef * q over the terms of source node x (Section 3.2).
+// For the float32 apply the sum is formed in float32: its value is rounded
+// to float32 anyway, and on GB300 every float64 warp instruction occupies
+// the FP64 pipe for ~64 cycles. The float64 and double-float applies sum in
+// float64.
+template <typename T>
+__device__ __forceinline__ T source_value(const SrcRecipe& rec, int s, const double* q) {
+    if constexpr (std::is_same<T, float>::value) {
+        float val = 0.f;
+        for (int e = rec.term_off[s]; e < rec.term_off[s + 1]; ++e)
+            val = __fmaf_rn(rec.term_coef[e], (float)q[rec.term_idx[e]], val);
+        return val;
+    } else {
+        double val = 0.0;
+        for (int e = rec.term_off[s]; e < rec.term_off[s + 1]; ++e)
+            val += (double)rec.term_coef[e] * q[rec.term_idx[e]];
+        return (T)val;
+    }
+}
+
 // ------------------------------------------ programmatic dependent launch
 // The convolution kernels are launched with programmatic stream
 // serialisation: the launch of a kernel is set up while the kernel before it

@@ -78,10 +78,7 @@ __global__ void __launch_bounds__(Geo<T, L>::KT) k_kpass_fwd(ConvArgs<T> a) {
                 const int s0 = a.rec.line_off[l], s1 = a.rec.line_off[l + 1];
                 for (int s = s0 + t; s < s1; s += R1) {
                     const int k = a.rec.src_lin[s] - (int)(l * N);
-                    double val = 0.0;
-                    for (int e = a.rec.term_off[s]; e < a.rec.term_off[s + 1]; ++e)
-                        val += (double)a.rec.term_coef[e] * q[a.rec.term_idx[e]];
-                    r[half * N + k] = (T)val;
+                    r[half * N + k] = source_value<T>(a.rec, s, q);
                 }
             }
         }
@@ -353,10 +350,7 @@ __global__ void __launch_bounds__(512) k_plane_fwd(ConvArgs<T> a) {
                         const int s0 = a.rec.line_off[l], s1 = a.rec.line_off[l + 1];
                         for (int s = s0 + t; s < s1; s += R1) {
                             const int k = a.rec.src_lin[s] - (int)(l * N);
-                            double val = 0.0;
-                            for (int e = a.rec.term_off[s]; e < a.rec.term_off[s + 1]; ++e)
-                                val += (double)a.rec.term_coef[e] * q[a.rec.term_idx[e]];
-                            r[k] = (T)val;
+                            r[k] = source_value<T>(a.rec, s, q);
                         }
                     }
                 }

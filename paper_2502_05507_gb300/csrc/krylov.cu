@@ -135,6 +135,10 @@ __global__ void k_arn_init(Arnoldi a, const double* __restrict__ nrm2, const int
         a.est[b] = beta;
         a.flag[b] = go ? 1 : 0;
         a.live[b] = go ? 1 : 0;
+        if (a.live_host) {
+            a.live_host[b] = go ? 1 : 0;
+            __threadfence_system();
+        }
         if (a.gflag) a.gflag[b] = 0;
         a.inv[b] = beta > 0.0 ? 1.0 / beta : 0.0;
         a.ncols[b] = 0;
@@ -411,6 +415,10 @@ __global__ void __launch_bounds__(256) k_arn_update_dots(Arnoldi a) {
             a.inv[b] = hn > 0.0 ? 1.0 / hn : 0.0;
             a.flag[b] = (e > a.target[b] && hn > 0.0 && j + 1 < m) ? 1 : 0;
             a.live[b] = a.flag[b];
+            if (a.live_host) {
+                a.live_host[b] = a.flag[b];
+                __threadfence_system();
+            }
             a.j[b] = j + 1;   // every block of this RHS has read j already
             a.ctr[3 * b + 1] = 0;
         }
@@ -566,6 +574,10 @@ __global__ void __launch_bounds__(256) k_arn_step_coop(Arnoldi a) {
             a.gflag[b] = gf;
             a.flag[b] = fl;
             a.live[b] = gf | fl;
+            if (a.live_host) {
+                a.live_host[b] = gf | fl;
+                __threadfence_system();
+            }
             a.j[b] = ran ? j + 1 : j;
         }
         __syncthreads();

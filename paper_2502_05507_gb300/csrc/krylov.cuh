@@ -80,6 +80,7 @@ struct Arnoldi {
     // another step is needed; bar2 counts the barriers of the chunk CTAs.
     int* gflag = nullptr;                  // [nb]
     int* live = nullptr;                   // [nb]
+    int* live_host = nullptr;              // [nb] device address of mapped host memory, or null
     double* pcol = nullptr;                // [nb][2][m + 2]
     unsigned long long* bar2 = nullptr;
 };

@@ -31,6 +31,14 @@ for prec in ("mixed", "fp64"):
     np.save({path!r} + "_" + prec + "_q.npy", q.cpu().numpy())
     np.save({path!r} + "_" + prec + "_u.npy", u.cpu().numpy())
     out[prec] = st["iterations"]
+# short restart cycles (the last column of every cycle, the restart
+# boundary) and an iteration cap that stops a cycle in the middle
+q, u, st = prob.solve(f, g, tol=1e-10, precision="fp64", restart=7)
+np.save({path!r} + "_r7_u.npy", u.cpu().numpy())
+out["r7"] = st["iterations"]
+q, u, st = prob.solve(f, g, tol=1e-10, precision="fp64", restart=11, max_iter=30, allow_not_converged=True)
+np.save({path!r} + "_cap_u.npy", u.cpu().numpy())
+out["cap"] = [st["iterations"], st["rel_residual"]]
 xyz = np.asarray(prob.boundary_points())
 G = np.stack([P.g_at(xyz), np.sin(xyz[:, 0]) + xyz[:, 1] * xyz[:, 2], np.cos(2 * xyz[:, 2])])
 F = np.stack([P.f(), np.zeros_like(P.f()), P.f()])
@@ -58,7 +66,8 @@ def test_fused_step_bit_identical_to_three_kernel_step(tmp_path):
     p_on, it_on = _run(tmp_path, "coop", {})
     p_off, it_off = _run(tmp_path, "three", {"BAE_ARNOLDI_COOP": "0"})
     assert it_on == it_off
-    for name in ("mixed_q", "mixed_u", "fp64_q", "fp64_u", "batch_u"):
+    assert it_on["cap"][0] == 30, it_on
+    for name in ("mixed_q", "mixed_u", "fp64_q", "fp64_u", "batch_u", "r7_u", "cap_u"):
         a = np.load(p_on + "_" + name + ".npy")
         b = np.load(p_off + "_" + name + ".npy")
         assert np.array_equal(a, b), name
