@@ -98,31 +98,35 @@ class ClockSampler:
 
 
 # ------------------------------------------------------ roofline arithmetic
-def kernel_model(n, pb, n_gm):
+def kernel_model(n, pb, n_gm, npl=None):
     """Algorithmic (bytes, flops) of one launch of each convolution pass for
     one right-hand side at grid size n, element precision pb bytes (complex
-    = 2 pb). FFT flops use the 5 L log2 L convention per complex transform
-    of length L = 2n; the spectral multiply counts 2 flops per element."""
+    = 2 pb), when the solve transforms npl of the n x-planes (the planes that
+    hold sources or read-back nodes; all n if None). FFT flops use the
+    5 L log2 L convention per complex transform of length L = 2n; the
+    spectral multiply counts 2 flops per element."""
+    npl = n if npl is None else npl
     c = 2 * pb
     L = 2 * n
     n1 = n + 1
     # N k-columns per (i, j): the real kk = N spectrum is packed into column 0
-    A = n * n * n * c
-    B = 2 * n * n * n * c
+    A = npl * n * n * c            # k-spectra of the transformed planes
+    B = 2 * npl * n * n * c        # after the j pass: 2n rows, n columns per plane
     F = 5.0 * L * math.log2(L)
-    src = 8 * n_gm + 4 * (n * n + 1)
-    plane_f = (n * n / 2) * F + n * n * F
+    src = 8 * n_gm + 4 * (npl * n + 1)
+    plane_f = (npl * n / 2) * F + npl * n * F
     return {
-        "conv_kfwd": (A + src, (n * n / 2) * F),
-        "conv_jfwd": (A + B, n * n * F),
+        "conv_kfwd": (A + src, (npl * n / 2) * F),
+        "conv_jfwd": (A + B, npl * n * F),
+        # i pass: reads and writes the rows of the transformed planes
         "conv_i": (2 * B + n1 ** 3 * pb, 2 * (2 * n * n) * F + 2.0 * (2 * n * n) * L),
-        "conv_jinv": (A + B, n * n * F),
-        "conv_kinv": (A + n ** 3 * pb, (n * n / 2) * F),
+        "conv_jinv": (A + B, npl * n * F),
+        "conv_kinv": (A + npl * n * n * pb, (npl * n / 2) * F),
         # k and j fused per plane (one CTA, or a cluster): A stays on chip
         "conv_plane_fwd": (B + src, plane_f),
-        "conv_plane_inv": (B + n ** 3 * pb, plane_f),
+        "conv_plane_inv": (B + npl * n * n * pb, plane_f),
         "conv_cplane_fwd": (B + src, plane_f),
-        "conv_cplane_inv": (B + n ** 3 * pb, plane_f),
+        "conv_cplane_inv": (B + npl * n * n * pb, plane_f),
     }
 
 
@@ -141,13 +145,13 @@ FP32_INST_PEAK_T = 35.1
 # since its capture must be dropped from this table (its traffic is then
 # reported as null)
 NCU_TRAFFIC_TORUS128 = {
-    "conv_i.f32": 42.43e6,
+    "conv_i.f32": 33.98e6,
 }
 
 
-def roofline_for(name, ms_total, launches, n_gm, hbm, hbm_kind):
+def roofline_for(name, ms_total, launches, n_gm, hbm, hbm_kind, npl=None):
     base, _, prec = name.partition(".")
-    model = kernel_model(N, 4 if prec == "f32" else 8, n_gm)
+    model = kernel_model(N, 4 if prec == "f32" else 8, n_gm, npl)
     if base not in model:
         return None
     nbytes, flops = model[base]
@@ -206,6 +210,8 @@ def run_ours(args, rank, world, dev):
     xs = prob0.boundary_points()
     g = torch.from_numpy(P.g_at(xs)).to(dev)
     n_gm = prob0.n_gm
+    plo, phi_ = prob0.plane_range()
+    npl = phi_ - plo
     prob0.close()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
 
@@ -278,15 +284,15 @@ def run_ours(args, rank, world, dev):
     out["kernels"] = [{"name": k, "ms_total": round(v[0], 3), "launches": v[1],
                        "share": round(v[0] / tot, 4) if tot else None} for k, v in kt[:14]]
     dom = next((k for k, _ in kt if k.startswith("conv_")), None)
-    out["roofline"] = roofline_for(dom, prof[dom][0], prof[dom][1], n_gm, hbm, hbm_kind) if dom else None
+    out["roofline"] = roofline_for(dom, prof[dom][0], prof[dom][1], n_gm, hbm, hbm_kind, npl) if dom else None
     # the float32 i-pass (forward FFT, ghat multiply, inverse FFT) inside the timed region
     if "conv_i.f32" in prof:
-        out["conv_f32_roofline"] = roofline_for("conv_i.f32", *prof["conv_i.f32"], n_gm, hbm, hbm_kind)
+        out["conv_f32_roofline"] = roofline_for("conv_i.f32", *prof["conv_i.f32"], n_gm, hbm, hbm_kind, npl)
     # whole float32 apply: algorithmic bytes of the passes that ran / their
     # summed time per apply (either schedule the autotuner picked)
     if "conv_i.f32" in prof:
         napp = prof["conv_i.f32"][1]
-        m = kernel_model(N, 4, n_gm)
+        m = kernel_model(N, 4, n_gm, npl)
         names = [k for k in prof if k.startswith("conv_") and k.endswith(".f32")]
         nbytes = sum(m[k.split(".")[0]][0] * prof[k][1] / napp for k in names)
         t_apply = sum(prof[k][0] for k in names) / napp / 1000.0

@@ -197,6 +197,13 @@ void bae_problem_destroy(bae_problem* prob);
  * may be NULL. Host-side, no device work. */
 int bae_problem_sizes(const bae_problem* prob, int64_t* n_gm, int64_t* n_gp, int64_t* n_mp);
 
+/* The x-planes [*lo, *hi) that hold every source (gamma-, the D-nodes, M+)
+ * and every node a solve reads back (gamma-, the closure partners, M+):
+ * inside a solve and in bae_boundary_apply the convolution transforms only
+ * these planes (the others are zero on input and unread on output). Not a
+ * quantity of the paper; a cost model aid. Host-side, no device work. */
+int bae_problem_plane_range(const bae_problem* prob, int* lo, int* hi);
+
 /* Boundary points x*(m) of the closure rows, gamma- in lexicographic order:
  * xyz[3r + c]. The caller evaluates g there. */
 int bae_boundary_points(const bae_problem* prob, double* xyz);

@@ -96,6 +96,7 @@ def lib():
             "bae_problem_create": (_I, [_P, _I, _D, _P, _P, _D, _I, _P]),
             "bae_problem_destroy": (None, [_P]),
             "bae_problem_sizes": (_I, [_P, _P, _P, _P]),
+            "bae_problem_plane_range": (_I, [_P, _P, _P]),
             "bae_boundary_points": (_I, [_P, _P]),
             "bae_classification": (_I, [_P, _P, _P, _P, _P]),
             "bae_potential_apply": (_I, [_P, _I, _P, _P]),
@@ -123,7 +124,7 @@ def lib():
 EXPORTED = ["bae_version", "bae_last_error", "bae_default_options", "bae_launch_count", "bae_set_conv_schedule", "bae_profile_start",
             "bae_profile_stop", "bae_ctx_create", "bae_ctx_destroy",
             "bae_lgf_table", "bae_lgf_spectrum", "bae_problem_create", "bae_problem_destroy",
-            "bae_problem_sizes", "bae_boundary_points", "bae_classification", "bae_potential_apply",
+            "bae_problem_sizes", "bae_problem_plane_range", "bae_boundary_points", "bae_classification", "bae_potential_apply",
             "bae_potential_apply_noalloc",
             "bae_boundary_apply", "bae_particular", "bae_solve", "bae_solve_batched", "bae_server_create",
             "bae_server_submit", "bae_server_poll", "bae_server_density", "bae_server_release", "bae_server_clock",
@@ -276,6 +277,12 @@ class Problem:
             self.close()
         except Exception:
             pass
+
+    def plane_range(self):
+        """(lo, hi): the x-planes the solve's convolutions transform."""
+        lo, hi = ctypes.c_int(), ctypes.c_int()
+        _check(lib().bae_problem_plane_range(self._h, ctypes.byref(lo), ctypes.byref(hi)))
+        return lo.value, hi.value
 
     def boundary_points(self, like=None):
         out = _new((self.n_gm, 3), np.float64, like)

@@ -1141,6 +1141,15 @@ int bae_problem_sizes(const bae_problem* P, int64_t* n_gm, int64_t* n_gp, int64_
     });
 }
 
+int bae_problem_plane_range(const bae_problem* P, int* lo, int* hi) {
+    return guarded([&]() -> int {
+        BAE_REQUIRE(P && lo && hi, BAE_ERR_INVALID_ARG, "null argument");
+        *lo = P->geo.plane_lo;
+        *hi = P->geo.plane_hi;
+        return BAE_OK;
+    });
+}
+
 int bae_boundary_points(const bae_problem* P, double* xyz) {
     return guarded([&]() -> int {
         BAE_REQUIRE(P && xyz, BAE_ERR_INVALID_ARG, "null argument");
