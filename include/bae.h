@@ -82,14 +82,15 @@ typedef struct bae_options {
                             solution, the refinement residuals and the
                             reconstruction, BAE_DF64 (default) or BAE_FP64 */
     int    precond;      /* BAE_MIXED only: right-preconditions the inner
-                            float32 GMRES with the block-Jacobi inverse of the
-                            BAE matrix over the gamma- nodes of each 2 x 2 x 2
-                            grid cell (the local form of the right
-                            preconditioning in Section 4's remark; built once
-                            per problem on the device from a small LGF table):
-                            1 (default) in the refinement steps after the
-                            first, 2 in every step, 0 never. The solution is
-                            the same to tol.                               */
+                            float32 GMRES with a restricted additive Schwarz
+                            inverse of the BAE matrix (each gamma- node's row
+                            of the inverse of its 3 x 3 x 3 neighbourhood
+                            block; a local form of the right preconditioning
+                            in Section 4's remark; built once per problem on
+                            the device from a small LGF table): 1 (default)
+                            in every refinement step, 2 in the steps after
+                            the first, 0 never. The solution is the same to
+                            tol.                                           */
 } bae_options;
 
 typedef struct bae_stats {

@@ -327,7 +327,7 @@ class Problem:
         o = Options()
         lib().bae_default_options(ctypes.byref(o))
         o.use_graphs = 1 if use_graphs else 0
-        if precond is not None:   # False/0: never, True/1: after the first step, 2: every step
+        if precond is not None:   # False/0: never, True/1: every refinement step, 2: after the first
             o.precond = int(precond)
         if residual_precision is not None:
             o.residual_precision = _PREC[residual_precision]

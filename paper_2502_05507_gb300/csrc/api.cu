@@ -284,7 +284,7 @@ struct bae_ctx {
 struct bae_problem {
     bae_ctx* ctx = nullptr;
     Geometry geo;
-    Precond pre;   // block-Jacobi right preconditioner, built on the first mixed solve that asks for it
+    Precond pre;   // right preconditioner, built on the first mixed solve that asks for it
     std::shared_ptr<Spectrum> spec;
     double kappa2 = 0.0, s = 0.0;
     Workspace& ws() { return ctx->ws; }
@@ -788,8 +788,8 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
         // iterative refinement: inner float32-apply GMRES on A d = r, q += d,
         // r = b - A64 q in float64
         double* d = P->ws().vstage.need((long long)nb * n);
-        // block-Jacobi right preconditioner of the inner solves (the inner
-        // unknown is y with d = M^{-1} y)
+        // right preconditioner of the inner solves (restricted additive
+        // Schwarz; the inner unknown is y with d = M^{-1} y)
         const bool any_pre = o.precond != 0;
         if (any_pre && !P->pre.built) build_precond(P->geo, P->s, P->pre);
         double* dq = any_pre ? P->ws().qpre.need((long long)nb * n) : d;
@@ -802,11 +802,9 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
             for (int b = 0; b < nb; ++b)
                 if (relres[b] > o.tol && bn2[b] > 0) act.push_back(b);
             if (act.empty() || iters_left <= 0) break;
-            // the preconditioner serves the steps after the first (precond 1)
-            // or all steps (precond 2): measured on the torus and star
-            // workloads, it slows the first, coarse reduction and speeds the
-            // later, accurate ones
-            const bool use_pre = o.precond == 2 || (o.precond == 1 && step > 0);
+            // every refinement step (precond 1) or the steps after the first
+            // (precond 2)
+            const bool use_pre = o.precond == 1 || (o.precond == 2 && step > 0);
             std::vector<RhsState> Si(nb);
             for (int b : act) {
                 // reduce the residual by inner_tol; when that lands within ten

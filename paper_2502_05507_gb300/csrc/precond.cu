@@ -1,6 +1,7 @@
-// Block-Jacobi right preconditioner of the BAE (see precond.cuh): built on
-// the device in two kernels (cell table, then one thread per gamma- node
-// forms and inverts its cell's block and keeps its own row of the inverse).
+// Restricted additive Schwarz right preconditioner of the BAE (see
+// precond.cuh): built on the device (a node map, then one thread per
+// gamma- node forms its neighbourhood block and solves for its own row of
+// that block's inverse).
 #include <algorithm>
 
 #include "lgf.cuh"
@@ -10,22 +11,13 @@ namespace bae {
 
 namespace {
 
-constexpr int TN = 8;   // LGF table extent: the block entries need offsets up to 3 per axis
+constexpr int TN = 8;   // LGF table extent: the block entries need offsets up to 4 per axis
 constexpr int TAB = TN * (TN + 1) * (TN + 2) / 6;
 
-__device__ __forceinline__ long long cell_of(long long lin, int N) {
-    const long long i = lin / ((long long)N * N), j = (lin / N) % N, k = lin % N;
-    const long long C = N / 2 + 1;
-    return ((i / 2) * C + j / 2) * C + k / 2;
-}
-
-// every gamma- node enters its 2 x 2 x 2 cell (at most 8 per cell)
-__global__ void k_cell_fill(const int* __restrict__ gm, long long n, int N, int* count, int* members) {
-    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
-        const long long c = cell_of(gm[r], N);
-        const int slot = atomicAdd(count + c, 1);
-        if (slot < MAXB) members[c * MAXB + slot] = (int)r;
-    }
+// node_of[lin] = gamma- index of grid node lin, -1 elsewhere
+__global__ void k_node_map(const int* __restrict__ gm, long long n, int* node_of) {
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
+        node_of[gm[r]] = (int)r;
 }
 
 // G_s at a lattice offset from the sorted table (offsets below TN per axis)
@@ -59,72 +51,78 @@ __device__ double kval(const double* tab, const uint8_t* flags, int N, int layer
     return nd == 0 ? g0 : acc + nd * g0;
 }
 
-// one thread per gamma- node r: its cell's block A[B, B] (members in node
-// order), inverted by Gauss-Jordan with partial pivoting (the identity if a
-// pivot is negligible), row r of the inverse into the 8 slots of r
-__global__ void k_block_rows(const int* __restrict__ gm, const int* __restrict__ partner, const double* __restrict__ t,
-                             const uint8_t* __restrict__ flags, const double* __restrict__ tab, long long n, int N,
-                             int layer, const int* __restrict__ count, const int* __restrict__ members, int* col,
-                             double* val) {
+// One thread per gamma- node r: S = the gamma- nodes of the 3 x 3 x 3
+// neighbourhood of r (in node order), A_S = A[S, S] from the LGF table, and
+// row r of M^{-1} = the row of r in inv(A_S), from the LU solve (partial
+// pivoting) of A_S^T z = e_r; a numerically singular block keeps the identity
+// row. Written into the MAXR slots of r.
+__global__ void __launch_bounds__(64) k_ras_rows(const int* __restrict__ gm, const int* __restrict__ partner,
+                                                 const double* __restrict__ t, const uint8_t* __restrict__ flags,
+                                                 const double* __restrict__ tab, const int* __restrict__ node_of,
+                                                 long long n, int N, int layer, int* col, double* val) {
     for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
-        const long long cell = cell_of(gm[r], N);
-        const int k = min(count[cell], MAXB);
-        int mem[MAXB];
-        for (int p = 0; p < k; ++p) mem[p] = members[cell * MAXB + p];
-        for (int p = 1; p < k; ++p)   // node order, the same in every member's thread
-            for (int q = p; q > 0 && mem[q - 1] > mem[q]; --q) {
-                const int x = mem[q - 1];
-                mem[q - 1] = mem[q];
-                mem[q] = x;
-            }
-        double a[MAXB][MAXB], inv[MAXB][MAXB];
+        const long long lin = gm[r], NN = (long long)N * N;
+        int S[MAXR];
+        int k = 0, me = 0;
+        for (int di = -1; di <= 1; ++di)
+            for (int dj = -1; dj <= 1; ++dj)
+                for (int dk = -1; dk <= 1; ++dk) {
+                    const int s = node_of[lin + di * NN + dj * N + dk];   // gamma- is not on a box face
+                    if (s < 0) continue;
+                    if (s == (int)r) me = k;
+                    S[k++] = s;
+                }
+        // M = A_S^T, row-major: M[q][p] = A_S[p][q]
+        double M[MAXR][MAXR], z[MAXR];
         double scale = 0.0;
         for (int p = 0; p < k; ++p) {
-            const int rp = mem[p];
+            const int rp = S[p];
             const double tp = t[rp];
             for (int q = 0; q < k; ++q) {
-                const long long cq = gm[mem[q]];
-                a[p][q] = tp * kval(tab, flags, N, layer, gm[rp], cq) + (1.0 - tp) * kval(tab, flags, N, layer, partner[rp], cq);
-                inv[p][q] = p == q ? 1.0 : 0.0;
-                scale = fmax(scale, fabs(a[p][q]));
+                const long long cq = gm[S[q]];
+                const double v = tp * kval(tab, flags, N, layer, gm[rp], cq) + (1.0 - tp) * kval(tab, flags, N, layer, partner[rp], cq);
+                M[q][p] = v;
+                scale = fmax(scale, fabs(v));
             }
+            z[p] = p == me ? 1.0 : 0.0;
         }
         bool ok = true;
-        for (int c = 0; c < k && ok; ++c) {
+        for (int c = 0; c < k; ++c) {   // forward elimination with partial pivoting
             int piv = c;
             for (int q = c + 1; q < k; ++q)
-                if (fabs(a[q][c]) > fabs(a[piv][c])) piv = q;
-            if (!(fabs(a[piv][c]) > 1e-12 * scale)) {
+                if (fabs(M[q][c]) > fabs(M[piv][c])) piv = q;
+            if (!(fabs(M[piv][c]) > 1e-12 * scale)) {
                 ok = false;
                 break;
             }
-            if (piv != c)
-                for (int q = 0; q < k; ++q) {
-                    double x = a[piv][q]; a[piv][q] = a[c][q]; a[c][q] = x;
-                    x = inv[piv][q]; inv[piv][q] = inv[c][q]; inv[c][q] = x;
+            if (piv != c) {
+                for (int q = c; q < k; ++q) {
+                    const double x = M[piv][q];
+                    M[piv][q] = M[c][q];
+                    M[c][q] = x;
                 }
-            const double dinv = 1.0 / a[c][c];
-            for (int q = 0; q < k; ++q) {
-                a[c][q] *= dinv;
-                inv[c][q] *= dinv;
+                const double x = z[piv];
+                z[piv] = z[c];
+                z[c] = x;
             }
-            for (int p = 0; p < k; ++p) {
-                if (p == c) continue;
-                const double f = a[p][c];
+            const double dinv = 1.0 / M[c][c];
+            for (int p = c + 1; p < k; ++p) {
+                const double f = M[p][c] * dinv;
                 if (f == 0.0) continue;
-                for (int q = 0; q < k; ++q) {
-                    a[p][q] -= f * a[c][q];
-                    inv[p][q] -= f * inv[c][q];
-                }
+                for (int q = c + 1; q < k; ++q) M[p][q] -= f * M[c][q];
+                z[p] -= f * z[c];
             }
         }
-        int me = 0;
-        for (int p = 0; p < k; ++p)
-            if (mem[p] == (int)r) me = p;
-        for (int q = 0; q < MAXB; ++q) {
+        if (ok)
+            for (int c = k - 1; c >= 0; --c) {   // back substitution
+                double x = z[c];
+                for (int q = c + 1; q < k; ++q) x -= M[c][q] * z[q];
+                z[c] = x / M[c][c];
+            }
+        for (int q = 0; q < MAXR; ++q) {
             const bool use = q < k;
-            col[r * MAXB + q] = use ? mem[q] : (int)r;
-            val[r * MAXB + q] = use ? (ok ? inv[me][q] : (q == me ? 1.0 : 0.0)) : 0.0;
+            col[r * MAXR + q] = use ? S[q] : (int)r;
+            val[r * MAXR + q] = use ? (ok ? z[q] : (q == me ? 1.0 : 0.0)) : 0.0;
         }
     }
 }
@@ -138,8 +136,10 @@ __global__ void k_precond_apply(const int* __restrict__ col, const double* __res
     double* y = out + b * out_stride;
     for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
         double acc = 0.0;
-#pragma unroll
-        for (int q = 0; q < MAXB; ++q) acc += val[r * MAXB + q] * x[col[r * MAXB + q]];
+        for (int q = 0; q < MAXR; ++q) {
+            const double v = val[r * MAXR + q];
+            if (v != 0.0) acc += v * x[col[r * MAXR + q]];
+        }
         y[r] = acc;
     }
 }
@@ -159,25 +159,22 @@ void Precond::release() {
 void build_precond(const Geometry& g, double s, Precond& out) {
     cudaStream_t st = g.stream;
     const int N = g.N;
-    const long long n = g.n_gm;
-    const long long C = N / 2 + 1, cells = C * C * C;
+    const long long n = g.n_gm, n3 = (long long)N * N * N;
     // G_s at offsets [0, TN)^3, the function the convolution's spectrum comes from
     double* tab = dev_alloc_n<double>(TAB, st);
     lgf_table(TN, s, tab, st);
-    int* count = dev_alloc_n<int>(cells, st);
-    int* members = dev_alloc_n<int>(cells * MAXB, st);
-    BAE_CUDA(cudaMemsetAsync(count, 0, (size_t)cells * sizeof(int), st));
+    int* node_of = dev_alloc_n<int>(n3, st);
+    BAE_CUDA(cudaMemsetAsync(node_of, 0xff, (size_t)n3 * sizeof(int), st));
     out.release();
     out.stream = st;
     out.n = n;
-    out.col = dev_alloc_n<int>(n * MAXB, st);
-    out.val = dev_alloc_n<double>(n * MAXB, st);
-    BAE_LAUNCH("k_cell_fill", st, k_cell_fill<<<grid_for(n), 256, 0, st>>>(g.gm, n, N, count, members));
-    BAE_LAUNCH("k_block_rows", st,
-               k_block_rows<<<grid_for(n), 128, 0, st>>>(g.gm, g.partner, g.t, g.flags, tab, n, N, g.layer, count,
-                                                          members, out.col, out.val));
-    dev_free(members, st);
-    dev_free(count, st);
+    out.col = dev_alloc_n<int>(n * MAXR, st);
+    out.val = dev_alloc_n<double>(n * MAXR, st);
+    BAE_LAUNCH("k_node_map", st, k_node_map<<<grid_for(n), 256, 0, st>>>(g.gm, n, node_of));
+    BAE_LAUNCH("k_ras_rows", st,
+               k_ras_rows<<<grid_for(n), 64, 0, st>>>(g.gm, g.partner, g.t, g.flags, tab, node_of, n, N, g.layer,
+                                                       out.col, out.val));
+    dev_free(node_of, st);
     dev_free(tab, st);
     out.built = true;
 }

@@ -1,9 +1,9 @@
-"""Block-Jacobi right preconditioning of the inner float32 GMRES (the local
-form of the right preconditioning remarked in Section 4; the numerical
-section asks for preconditioning). It changes the iteration, not the
-discrete solution: with and without it the mixed solve reaches the same u on
-M+ to the tolerance and matches the oracle's solve; on the single layer,
-which needs many iterations, it needs far fewer."""
+"""Restricted additive Schwarz right preconditioning of the inner float32
+GMRES (a local form of the right preconditioning remarked in Section 4; the
+numerical section asks for preconditioning). It changes the iteration, not
+the discrete solution: with and without it the mixed solve reaches the same
+u on M+ to the tolerance and matches the oracle's solve, in far fewer
+iterations."""
 import numpy as np
 import pytest
 
@@ -43,7 +43,7 @@ def test_precond_same_solution(ctx, name, make, layer):
         g = torch.from_numpy(P.g_at(prob.boundary_points())).cuda()
         f = torch.from_numpy(P.f()).cuda()
         out = {}
-        for pre in (0, 1, 2):   # never, after the first refinement step, every step
+        for pre in (0, 1, 2):   # never, every refinement step, after the first step
             q, u, st = prob.solve(f, g, tol=1e-10, precision="mixed", precond=pre, max_iter=1000)
             assert st["rel_residual"] <= 1e-10, (pre, st)
             out[pre] = (u.cpu().numpy(), st)
@@ -52,10 +52,8 @@ def test_precond_same_solution(ctx, name, make, layer):
         for pre in (1, 2):
             assert np.max(np.abs(out[pre][0][mp] - u0)) <= 1e-8 * np.max(np.abs(u0)), pre
         print(name, layer, "iterations", [out[k][1]["iterations"] for k in (0, 1, 2)])
-        if name == "star64":
-            # the single layer needs many iterations; preconditioning every
-            # step cuts them by a third or more
-            assert out[2][1]["iterations"] < 0.8 * out[0][1]["iterations"], [out[k][1] for k in (0, 2)]
+        # the neighbourhood blocks cut the iterations several times over
+        assert out[1][1]["iterations"] < 0.6 * out[0][1]["iterations"], [out[k][1] for k in (0, 1)]
         if name == "sphere32":
             ref = OS.solve(P.phi, P.grid.h, P.grid.origin, P.f(), P.g_at, P.kappa2, layer=layer, tol=1e-12)
             assert np.max(np.abs(out[1][0][mp] - ref.u[mp])) <= 1e-8 * np.max(np.abs(ref.u[mp]))
@@ -74,10 +72,10 @@ def test_precond_batched_equals_alone(ctx):
         G = np.stack([P.g_at(xyz), np.cos(xyz[:, 0] + 2 * xyz[:, 2])])
         F = np.stack([P.f(), np.zeros_like(P.f())])
         qb, ub, stb = prob.solve_batched(torch.from_numpy(F).cuda(), torch.from_numpy(G).cuda(), tol=1e-10,
-                                         precision="mixed", precond=2)
+                                         precision="mixed", precond=1)
         for b in range(2):
             q1, u1, st1 = prob.solve(torch.from_numpy(F[b]).cuda(), torch.from_numpy(G[b]).cuda(), tol=1e-10,
-                                     precision="mixed", precond=2)
+                                     precision="mixed", precond=1)
             assert np.array_equal(ub[b].cpu().numpy(), u1.cpu().numpy()), b
             assert stb[b]["iterations"] == st1["iterations"]
     finally:
