@@ -125,11 +125,13 @@ struct Spectrum {
     double* g64 = nullptr;
     float* g32 = nullptr;
     dsf* gds = nullptr;
+    double* near = nullptr;   // G_s on the offsets below NEAR_TN (preconditioner blocks)
     size_t bytes = 0;
     ~Spectrum() {
         if (g64) cudaFree(g64);
         if (g32) cudaFree(g32);
         if (gds) cudaFree(gds);
+        if (near) cudaFree(near);
     }
 };
 
@@ -218,6 +220,8 @@ struct SpectrumCache {
             const double L = 2.0 * N;
             lgf_spectrum(N, s, 1.0 / (L * L * L), sp->g64, sp->g32, st);
             to_dsf(sp->g64, n3, sp->gds, st);
+            BAE_CUDA(cudaMalloc(&sp->near, NEAR_TAB * sizeof(double)));
+            lgf_table(NEAR_TN, s, sp->near, st);
             BAE_CUDA(cudaStreamSynchronize(st));
         } catch (...) {
             lock.lock();
@@ -791,7 +795,7 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
         // right preconditioner of the inner solves (restricted additive
         // Schwarz; the inner unknown is y with d = M^{-1} y)
         const bool any_pre = o.precond != 0;
-        if (any_pre && !P->pre.built) build_precond(P->geo, P->s, P->pre);
+        if (any_pre && !P->pre.built) build_precond(P->geo, P->s, P->spec->near, P->pre);
         double* dq = any_pre ? P->ws().qpre.need((long long)nb * n) : d;
         BAE_CUDA(cudaMemcpyAsync(res, bvec, (size_t)nb * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
         rn2 = bn2;

@@ -11,8 +11,6 @@ namespace bae {
 
 namespace {
 
-constexpr int TN = 8;   // LGF table extent: the block entries need offsets up to 4 per axis
-constexpr int TAB = TN * (TN + 1) * (TN + 2) / 6;
 
 // node_of[lin] = gamma- index of grid node lin, -1 elsewhere
 __global__ void k_node_map(const int* __restrict__ gm, long long n, int* node_of) {
@@ -20,12 +18,12 @@ __global__ void k_node_map(const int* __restrict__ gm, long long n, int* node_of
         node_of[gm[r]] = (int)r;
 }
 
-// G_s at a lattice offset from the sorted table (offsets below TN per axis)
-__device__ __forceinline__ double lgf_at(const double* tab, long long dx, long long dy, long long dz) {
-    long long a = dx < 0 ? -dx : dx, b = dy < 0 ? -dy : dy, c = dz < 0 ? -dz : dz;
-    if (a < b) { const long long x = a; a = b; b = x; }
-    if (b < c) { const long long x = b; b = c; c = x; }
-    if (a < b) { const long long x = a; a = b; b = x; }
+// G_s at a lattice offset from the sorted table (offsets below NEAR_TN per axis)
+__device__ __forceinline__ float lgf_at(const float* tab, int dx, int dy, int dz) {
+    int a = dx < 0 ? -dx : dx, b = dy < 0 ? -dy : dy, c = dz < 0 ? -dz : dz;
+    if (a < b) { const int x = a; a = b; b = x; }
+    if (b < c) { const int x = b; b = c; c = x; }
+    if (a < b) { const int x = a; a = b; b = x; }
     return tab[a * (a + 1) * (a + 2) / 6 + b * (b + 1) / 2 + c];
 }
 
@@ -33,22 +31,22 @@ __device__ __forceinline__ double lgf_at(const double* tab, long long dx, long l
 // G(x - c); double layer |D_c| G(x - c) - sum_{k in D_c} G(x - k), or the
 // single-layer column when D_c is empty (eqs. [single_potential],
 // [double_potential])
-__device__ double kval(const double* tab, const uint8_t* flags, int N, int layer, long long x, long long c) {
+__device__ float kval(const float* tab, const uint8_t* flags, int N, int layer, long long x, long long c) {
     const long long NN = (long long)N * N;
-    const long long xi = x / NN, xj = (x / N) % N, xk = x % N;
-    const long long ci = c / NN, cj = (c / N) % N, ck = c % N;
-    const double g0 = lgf_at(tab, xi - ci, xj - cj, xk - ck);
+    const int xi = (int)(x / NN), xj = (int)((x / N) % N), xk = (int)(x % N);
+    const int ci = (int)(c / NN), cj = (int)((c / N) % N), ck = (int)(c % N);
+    const float g0 = lgf_at(tab, xi - ci, xj - cj, xk - ck);
     if (layer != BAE_LAYER_DOUBLE) return g0;
-    double acc = 0.0;
+    float acc = 0.f;
     int nd = 0;
     const int d[6][3] = {{1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
     for (int q = 0; q < 6; ++q) {
-        const long long ki = ci + d[q][0], kj = cj + d[q][1], kk = ck + d[q][2];
-        if (flags[(ki * N + kj) * N + kk] & 3) continue;   // in N+ = M+ and gamma-
+        const int ki = ci + d[q][0], kj = cj + d[q][1], kk = ck + d[q][2];
+        if (flags[((long long)ki * N + kj) * N + kk] & 3) continue;   // in N+ = M+ and gamma-
         acc -= lgf_at(tab, xi - ki, xj - kj, xk - kk);
         ++nd;
     }
-    return nd == 0 ? g0 : acc + nd * g0;
+    return nd == 0 ? g0 : acc + (float)nd * g0;
 }
 
 // One thread per gamma- node r: S = the gamma- nodes of the 3 x 3 x 3
@@ -58,8 +56,11 @@ __device__ double kval(const double* tab, const uint8_t* flags, int N, int layer
 // row. Written into the MAXR slots of r.
 __global__ void __launch_bounds__(64) k_ras_rows(const int* __restrict__ gm, const int* __restrict__ partner,
                                                  const double* __restrict__ t, const uint8_t* __restrict__ flags,
-                                                 const double* __restrict__ tab, const int* __restrict__ node_of,
+                                                 const double* __restrict__ tab64, const int* __restrict__ node_of,
                                                  long long n, int N, int layer, int* col, double* val) {
+    __shared__ float tab[NEAR_TAB];
+    for (int e = threadIdx.x; e < NEAR_TAB; e += blockDim.x) tab[e] = (float)tab64[e];
+    __syncthreads();
     for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
         const long long lin = gm[r], NN = (long long)N * N;
         int S[MAXR];
@@ -72,57 +73,57 @@ __global__ void __launch_bounds__(64) k_ras_rows(const int* __restrict__ gm, con
                     if (s == (int)r) me = k;
                     S[k++] = s;
                 }
-        // M = A_S^T, row-major: M[q][p] = A_S[p][q]
-        double M[MAXR][MAXR], z[MAXR];
-        double scale = 0.0;
+        // M = A_S^T, row-major: M[q][p] = A_S[p][q] (float32)
+        float M[MAXR][MAXR], z[MAXR];
+        float scale = 0.f;
         for (int p = 0; p < k; ++p) {
             const int rp = S[p];
-            const double tp = t[rp];
+            const float tp = (float)t[rp];
             for (int q = 0; q < k; ++q) {
                 const long long cq = gm[S[q]];
-                const double v = tp * kval(tab, flags, N, layer, gm[rp], cq) + (1.0 - tp) * kval(tab, flags, N, layer, partner[rp], cq);
+                const float v = tp * kval(tab, flags, N, layer, gm[rp], cq) + (1.f - tp) * kval(tab, flags, N, layer, partner[rp], cq);
                 M[q][p] = v;
-                scale = fmax(scale, fabs(v));
+                scale = fmaxf(scale, fabsf(v));
             }
-            z[p] = p == me ? 1.0 : 0.0;
+            z[p] = p == me ? 1.f : 0.f;
         }
         bool ok = true;
         for (int c = 0; c < k; ++c) {   // forward elimination with partial pivoting
             int piv = c;
             for (int q = c + 1; q < k; ++q)
-                if (fabs(M[q][c]) > fabs(M[piv][c])) piv = q;
-            if (!(fabs(M[piv][c]) > 1e-12 * scale)) {
+                if (fabsf(M[q][c]) > fabsf(M[piv][c])) piv = q;
+            if (!(fabsf(M[piv][c]) > 1e-6f * scale)) {
                 ok = false;
                 break;
             }
             if (piv != c) {
                 for (int q = c; q < k; ++q) {
-                    const double x = M[piv][q];
+                    const float x = M[piv][q];
                     M[piv][q] = M[c][q];
                     M[c][q] = x;
                 }
-                const double x = z[piv];
+                const float x = z[piv];
                 z[piv] = z[c];
                 z[c] = x;
             }
-            const double dinv = 1.0 / M[c][c];
+            const float dinv = 1.f / M[c][c];
             for (int p = c + 1; p < k; ++p) {
-                const double f = M[p][c] * dinv;
-                if (f == 0.0) continue;
+                const float f = M[p][c] * dinv;
+                if (f == 0.f) continue;
                 for (int q = c + 1; q < k; ++q) M[p][q] -= f * M[c][q];
                 z[p] -= f * z[c];
             }
         }
         if (ok)
             for (int c = k - 1; c >= 0; --c) {   // back substitution
-                double x = z[c];
+                float x = z[c];
                 for (int q = c + 1; q < k; ++q) x -= M[c][q] * z[q];
                 z[c] = x / M[c][c];
             }
         for (int q = 0; q < MAXR; ++q) {
             const bool use = q < k;
             col[r * MAXR + q] = use ? S[q] : (int)r;
-            val[r * MAXR + q] = use ? (ok ? z[q] : (q == me ? 1.0 : 0.0)) : 0.0;
+            val[r * MAXR + q] = use ? (ok ? (double)z[q] : (q == me ? 1.0 : 0.0)) : 0.0;
         }
     }
 }
@@ -156,13 +157,17 @@ void Precond::release() {
     built = false;
 }
 
-void build_precond(const Geometry& g, double s, Precond& out) {
+void build_precond(const Geometry& g, double s, const double* near, Precond& out) {
     cudaStream_t st = g.stream;
     const int N = g.N;
     const long long n = g.n_gm, n3 = (long long)N * N * N;
-    // G_s at offsets [0, TN)^3, the function the convolution's spectrum comes from
-    double* tab = dev_alloc_n<double>(TAB, st);
-    lgf_table(TN, s, tab, st);
+    // G_s at offsets [0, NEAR_TN)^3, the function the convolution's spectrum comes from
+    double* own = nullptr;
+    if (!near) {
+        own = dev_alloc_n<double>(NEAR_TAB, st);
+        lgf_table(NEAR_TN, s, own, st);
+        near = own;
+    }
     int* node_of = dev_alloc_n<int>(n3, st);
     BAE_CUDA(cudaMemsetAsync(node_of, 0xff, (size_t)n3 * sizeof(int), st));
     out.release();
@@ -172,10 +177,10 @@ void build_precond(const Geometry& g, double s, Precond& out) {
     out.val = dev_alloc_n<double>(n * MAXR, st);
     BAE_LAUNCH("k_node_map", st, k_node_map<<<grid_for(n), 256, 0, st>>>(g.gm, n, node_of));
     BAE_LAUNCH("k_ras_rows", st,
-               k_ras_rows<<<grid_for(n), 64, 0, st>>>(g.gm, g.partner, g.t, g.flags, tab, node_of, n, N, g.layer,
+               k_ras_rows<<<grid_for(n), 64, 0, st>>>(g.gm, g.partner, g.t, g.flags, near, node_of, n, N, g.layer,
                                                        out.col, out.val));
     dev_free(node_of, st);
-    dev_free(tab, st);
+    if (own) dev_free(own, st);
     out.built = true;
 }
 

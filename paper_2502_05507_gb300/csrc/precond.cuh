@@ -21,6 +21,8 @@
 namespace bae {
 
 constexpr int MAXR = 27;   // gamma- nodes in a 3 x 3 x 3 neighbourhood, at most
+constexpr int NEAR_TN = 8;  // the blocks use G_s at offsets [0, NEAR_TN)^3 (up to 4 per axis)
+constexpr int NEAR_TAB = NEAR_TN * (NEAR_TN + 1) * (NEAR_TN + 2) / 6;   // sorted-table length
 
 struct Precond {
     bool built = false;
@@ -36,8 +38,12 @@ struct Precond {
 // Builds the preconditioner of the problem's BAE (layer and LGF parameter
 // s = kappa^2 h^2 as in the geometry) on the geometry's stream: a small LGF
 // table, a node map, and one thread per gamma- node that forms its
-// neighbourhood block and solves for its row.
-void build_precond(const Geometry& g, double s, Precond& out);
+// neighbourhood block and solves for its row in float32 (a preconditioner
+// only approximates the inverse; M^{-1} itself is applied exactly in
+// float64, so the preconditioned system is unchanged).
+// near: G_s on the sorted offsets below NEAR_TN (lgf_table(NEAR_TN, s)),
+// device; computed here when null.
+void build_precond(const Geometry& g, double s, const double* near, Precond& out);
 
 // out[b] = M^{-1} in[b] with in[b] at in + b in_stride (+ row[b] row_stride
 // when row is not null, device), out[b] at out + b out_stride, for items
