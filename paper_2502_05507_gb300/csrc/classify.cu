@@ -15,14 +15,13 @@ namespace bae {
 
 namespace {
 
-constexpr int SCAN_T = 256;
-constexpr int SCAN_E = 8;
-constexpr int SCAN_CHUNK = SCAN_T * SCAN_E;
+constexpr int SCAN_E = 8;   // entries per thread of the line-count scans
 
 __constant__ int c_dir[6][3] = {{1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
 
 // ---------------------------------------------------------------- scans
-// Block-local exclusive scan of SCAN_CHUNK ints; block totals to sums[].
+// exclusive scan over the CTA (blockDim.x a multiple of 32, at most 1024);
+// the CTA total is left in s_warp[32]
 __device__ int block_exclusive_scan(int v, int* s_warp) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int x = v;
@@ -50,143 +49,173 @@ __device__ int block_exclusive_scan(int v, int* s_warp) {
     return before + x - v;  // exclusive
 }
 
-__global__ void k_scan_local(const int* __restrict__ in, int* __restrict__ out, long long n, int* __restrict__ sums) {
-    __shared__ int s_warp[33];
-    const long long base = (long long)blockIdx.x * SCAN_CHUNK + threadIdx.x * SCAN_E;
-    int v[SCAN_E], tot = 0;
-#pragma unroll
-    for (int e = 0; e < SCAN_E; ++e) {
-        v[e] = (base + e < n) ? in[base + e] : 0;
-        tot += v[e];
-    }
-    const int ex = block_exclusive_scan(tot, s_warp);
-    int run = ex;
-#pragma unroll
-    for (int e = 0; e < SCAN_E; ++e) {
-        if (base + e < n) out[base + e] = run;
-        run += v[e];
-    }
-    if (threadIdx.x == 0) sums[blockIdx.x] = s_warp[32];
+// ------------------------------------------------------------ point sets
+// One CTA per grid line (i, j), its threads over k.
+constexpr int LINE_T = 128;
+
+// slots of the small device record the host reads once
+enum { I_ERR = 0, I_GP, I_MP, I_FIRST, I_LAST, I_NGM, I_NSRC, I_NTERM, I_COUNT };
+
+__device__ __forceinline__ bool in_grid(int i, int j, int k, int N) {
+    return (unsigned)i < (unsigned)N && (unsigned)j < (unsigned)N && (unsigned)k < (unsigned)N;
 }
 
-// single CTA: exclusive scan of nb block sums in place; grand total to *total
-__global__ void k_scan_sums(int* sums, int nb, int* total) {
+// bits per node from phi: bit0 in M+ (phi < 0), bit1 an M+ neighbour (nodes
+// outside the box count as exterior)
+__global__ void __launch_bounds__(LINE_T) k_nbits(const double* __restrict__ phi, int N, uint8_t* __restrict__ nb,
+                                                 int* __restrict__ info) {
+    const int line = blockIdx.x, i = line / N, j = line - i * N;
+    const long long base = (long long)line * N;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        const double p = phi[base + k];
+        if (!isfinite(p)) atomicOr(info + I_ERR, 1);
+        bool h = false;
+        for (int d = 0; d < 6; ++d) {
+            const int ii = i + c_dir[d][0], jj = j + c_dir[d][1], kk = k + c_dir[d][2];
+            if (in_grid(ii, jj, kk, N) && phi[((long long)ii * N + jj) * N + kk] < 0.0) h = true;
+        }
+        nb[base + k] = (uint8_t)((p < 0.0 ? 1 : 0) | (h ? 2 : 0));
+    }
+}
+
+// Node flags from the bits of the node and its six neighbours: M+ (bit0),
+// gamma- = outside M+ with an M+ neighbour (bit1), gamma+ = M+ with an
+// exterior neighbour (bit2), D-node = outside N+ = M+ and gamma-, next to a
+// gamma- node (bit3), and for gamma- nodes |D_n| = the neighbours outside
+// N+ (bits 4-6). Per line: the gamma- nodes, the sources (flags & src_mask)
+// and their stencil terms (1 per gamma- node, one per gamma- neighbour of a
+// D-node); gamma+ and M+ counts and the range of source planes go to info.
+__global__ void __launch_bounds__(LINE_T) k_flags_lines(const uint8_t* __restrict__ nb, int N, int src_mask,
+                                                       uint8_t* __restrict__ flags, int* __restrict__ cnt_gm,
+                                                       int* __restrict__ cnt_src, int* __restrict__ cnt_term,
+                                                       int* __restrict__ info) {
+    __shared__ int s_red[5][LINE_T / 32];
+    const int line = blockIdx.x, i = line / N, j = line - i * N;
+    const long long base = (long long)line * N;
+    int c[5] = {0, 0, 0, 0, 0};   // gamma-, sources, terms, gamma+, M+
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        const int me = nb[base + k];
+        bool out_nb = false;
+        int n_out = 0, n_gm = 0;
+        for (int d = 0; d < 6; ++d) {
+            const int ii = i + c_dir[d][0], jj = j + c_dir[d][1], kk = k + c_dir[d][2];
+            const int q = in_grid(ii, jj, kk, N) ? nb[((long long)ii * N + jj) * N + kk] : 0;
+            if (!(q & 1)) out_nb = true;
+            if (!(q & 3)) ++n_out;               // not in N+
+            if (!(q & 1) && (q & 2)) ++n_gm;     // a gamma- node
+        }
+        const bool in = me & 1, gm = !in && (me & 2);
+        const bool gp = in && out_nb;
+        const bool dnode = !in && !gm && n_gm > 0;
+        const bool face = (i == 0 || j == 0 || k == 0 || i == N - 1 || j == N - 1 || k == N - 1);
+        if ((gm || in) && face) atomicOr(info + I_ERR, 2);
+        const int f = (in ? 1 : 0) | (gm ? 2 : 0) | (gp ? 4 : 0) | (dnode ? 8 : 0) | ((gm ? n_out : 0) << 4);
+        flags[base + k] = (uint8_t)f;
+        const bool src = (f & src_mask) != 0;
+        c[0] += gm;
+        c[1] += src;
+        c[2] += src ? (gm ? 1 : n_gm) : 0;
+        c[3] += gp;
+        c[4] += in;
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int e = 0; e < 5; ++e) {
+        const int v = __reduce_add_sync(0xffffffffu, c[e]);
+        if (lane == 0) s_red[e][w] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t[5] = {0, 0, 0, 0, 0};
+        for (int e = 0; e < 5; ++e)
+            for (int x = 0; x < (int)(blockDim.x >> 5); ++x) t[e] += s_red[e][x];
+        cnt_gm[line] = t[0];
+        cnt_src[line] = t[1];
+        cnt_term[line] = t[2];
+        if (t[3]) atomicAdd(info + I_GP, t[3]);
+        if (t[4]) atomicAdd(info + I_MP, t[4]);
+        if (t[1]) {
+            atomicMax(info + I_FIRST, N - i);
+            atomicMax(info + I_LAST, i + 1);
+        }
+    }
+}
+
+// In-place exclusive scans of the three per-line counts (nl + 1 entries,
+// the last one becomes the total), one CTA each; totals to info.
+__global__ void __launch_bounds__(1024) k_scan_lines(int* c0, int* c1, int* c2, int nl, int* info) {
     __shared__ int s_warp[33];
     __shared__ int s_carry;
+    int* arr = blockIdx.x == 0 ? c0 : (blockIdx.x == 1 ? c1 : c2);
     if (threadIdx.x == 0) s_carry = 0;
     __syncthreads();
-    for (int base = 0; base < nb; base += blockDim.x * SCAN_E) {
+    for (int base = 0; base <= nl; base += blockDim.x * SCAN_E) {
         int v[SCAN_E], tot = 0;
         const int b0 = base + threadIdx.x * SCAN_E;
 #pragma unroll
         for (int e = 0; e < SCAN_E; ++e) {
-            v[e] = (b0 + e < nb) ? sums[b0 + e] : 0;
+            v[e] = (b0 + e < nl) ? arr[b0 + e] : 0;
             tot += v[e];
         }
         const int ex = block_exclusive_scan(tot, s_warp);
         int run = ex + s_carry;
 #pragma unroll
         for (int e = 0; e < SCAN_E; ++e) {
-            if (b0 + e < nb) sums[b0 + e] = run;
+            if (b0 + e <= nl) arr[b0 + e] = run;
             run += v[e];
         }
         __syncthreads();
         if (threadIdx.x == 0) s_carry += s_warp[32];
         __syncthreads();
     }
-    if (threadIdx.x == 0) *total = s_carry;
+    if (threadIdx.x == 0) info[I_NGM + blockIdx.x] = s_carry;
 }
 
-__global__ void k_scan_add(int* out, long long n, const int* sums) {
-    const int add = sums[blockIdx.x];
-    const long long base = (long long)blockIdx.x * SCAN_CHUNK + threadIdx.x * SCAN_E;
-#pragma unroll
-    for (int e = 0; e < SCAN_E; ++e)
-        if (base + e < n) out[base + e] += add;
-}
-
-// exclusive scan of n ints on the device; returns the total (synchronises)
-int exclusive_scan(const int* in, int* out, long long n, int* scratch_sums, int* d_total, cudaStream_t st) {
-    const int nb = ceil_div(n, SCAN_CHUNK);
-    BAE_LAUNCH("k_scan_local", st, k_scan_local<<<nb, SCAN_T, 0, st>>>(in, out, n, scratch_sums));
-    BAE_LAUNCH("k_scan_sums", st, k_scan_sums<<<1, 1024, 0, st>>>(scratch_sums, nb, d_total));
-    BAE_LAUNCH("k_scan_add", st, k_scan_add<<<nb, SCAN_T, 0, st>>>(out, n, scratch_sums));
-    int total = 0;
-    BAE_CUDA(cudaMemcpyAsync(&total, d_total, sizeof(int), cudaMemcpyDeviceToHost, st));
-    BAE_CUDA(cudaStreamSynchronize(st));
-    return total;
-}
-
-// ------------------------------------------------------------ point sets
-__global__ void k_inside(const double* __restrict__ phi, long long n3, uint8_t* __restrict__ inside, int* err) {
-    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n3; x += (long long)gridDim.x * blockDim.x) {
-        const double p = phi[x];
-        if (!isfinite(p)) atomicOr(err, 1);
-        inside[x] = p < 0.0 ? 1 : 0;
-    }
-}
-
-__device__ __forceinline__ bool in_grid(int i, int j, int k, int N) {
-    return (unsigned)i < (unsigned)N && (unsigned)j < (unsigned)N && (unsigned)k < (unsigned)N;
-}
-
-__device__ __forceinline__ int IN(const uint8_t* inside, int i, int j, int k, int N) {
-    return in_grid(i, j, k, N) ? inside[((long long)i * N + j) * N + k] : 0;
-}
-
-// node has an M+ neighbour (grid-outside counts as exterior)
-__device__ __forceinline__ bool has_in_nb(const uint8_t* inside, int i, int j, int k, int N) {
-    for (int d = 0; d < 6; ++d)
-        if (IN(inside, i + c_dir[d][0], j + c_dir[d][1], k + c_dir[d][2], N)) return true;
-    return false;
-}
-
-__device__ __forceinline__ bool is_gm(const uint8_t* inside, int i, int j, int k, int N) {
-    return in_grid(i, j, k, N) && !IN(inside, i, j, k, N) && has_in_nb(inside, i, j, k, N);
-}
-
-__device__ __forceinline__ bool is_nplus(const uint8_t* inside, int i, int j, int k, int N) {
-    return in_grid(i, j, k, N) && (IN(inside, i, j, k, N) || has_in_nb(inside, i, j, k, N));
-}
-
-__global__ void k_flags(const uint8_t* __restrict__ inside, int N, uint8_t* __restrict__ flags, int* err) {
-    const long long n3 = (long long)N * N * N;
-    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n3; x += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(x / ((long long)N * N)), j = (int)((x / N) % N), k = (int)(x % N);
-        const bool in = inside[x] != 0;
-        const bool face = (i == 0 || j == 0 || k == 0 || i == N - 1 || j == N - 1 || k == N - 1);
-        bool out_nb = false;
-        for (int d = 0; d < 6; ++d)
-            if (!IN(inside, i + c_dir[d][0], j + c_dir[d][1], k + c_dir[d][2], N)) out_nb = true;
-        const bool gm = !in && has_in_nb(inside, i, j, k, N);
-        const bool gp = in && out_nb;
-        int cnt = 0;
-        bool dnode = false;
-        if (gm) {
-            for (int d = 0; d < 6; ++d)
-                if (!is_nplus(inside, i + c_dir[d][0], j + c_dir[d][1], k + c_dir[d][2], N)) ++cnt;
-        } else if (!in) {  // outside N+ (not gm, not M+): next to a gamma- node?
-            for (int d = 0; d < 6; ++d)
-                if (is_gm(inside, i + c_dir[d][0], j + c_dir[d][1], k + c_dir[d][2], N)) dnode = true;
+// The lists in lexicographic order: per line, the CTA scans its nodes
+// (gamma-, source and term counts packed in one int: at most 256, 256 and
+// 1536 per line) from the line's offsets. node_of[x] = index of gamma- node
+// x (set only at gamma- nodes); term_off[s] = first term of source s.
+__global__ void __launch_bounds__(LINE_T) k_scatter_lines(const uint8_t* __restrict__ flags, int N, int src_mask,
+                                                         const int* __restrict__ off_gm, const int* __restrict__ off_src,
+                                                         const int* __restrict__ off_term, const int* __restrict__ info,
+                                                         int* __restrict__ gm, int* __restrict__ node_of,
+                                                         int* __restrict__ src_lin, int* __restrict__ term_off) {
+    __shared__ int s_warp[33];
+    const int line = blockIdx.x, i = line / N, j = line - i * N;
+    if (line == (int)gridDim.x - 1 && threadIdx.x == 0) term_off[info[I_NSRC]] = info[I_NTERM];
+    int pg = off_gm[line], ps = off_src[line], pt = off_term[line];
+    if (ps == off_src[line + 1]) return;   // no source (so no gamma- node) on this line: the whole CTA
+    const int base = line * N;
+    for (int k0 = 0; k0 < N; k0 += blockDim.x) {
+        const int k = k0 + (int)threadIdx.x;
+        int g = 0, s = 0, nt = 0;
+        if (k < N) {
+            const int f = flags[base + k];
+            g = (f >> 1) & 1;
+            s = (f & src_mask) != 0;
+            if (s && g) {
+                nt = 1;
+            } else if (s) {
+                for (int d = 0; d < 6; ++d) {
+                    const int ii = i + c_dir[d][0], jj = j + c_dir[d][1], kk = k + c_dir[d][2];
+                    if (in_grid(ii, jj, kk, N) && (flags[(ii * N + jj) * N + kk] & 2)) ++nt;
+                }
+            }
         }
-        if ((gm || in) && face) atomicOr(err, 2);
-        flags[x] = (uint8_t)((in ? 1 : 0) | (gm ? 2 : 0) | (gp ? 4 : 0) | (dnode ? 8 : 0) | (cnt << 4));
+        const int ex = block_exclusive_scan(g | (s << 10) | (nt << 20), s_warp);
+        const int tot = s_warp[32];
+        if (g) {
+            gm[pg + (ex & 1023)] = base + k;
+            node_of[base + k] = pg + (ex & 1023);
+        }
+        if (s) {
+            src_lin[ps + ((ex >> 10) & 1023)] = base + k;
+            term_off[ps + ((ex >> 10) & 1023)] = pt + (ex >> 20);
+        }
+        pg += tot & 1023;
+        ps += (tot >> 10) & 1023;
+        pt += tot >> 20;
     }
-}
-
-__global__ void k_pred(const uint8_t* __restrict__ flags, long long n3, int mask, int* __restrict__ out) {
-    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n3; x += (long long)gridDim.x * blockDim.x)
-        out[x] = (flags[x] & mask) ? 1 : 0;
-}
-
-__global__ void k_scatter_list(const uint8_t* __restrict__ flags, long long n3, int mask, const int* __restrict__ pos,
-                               int* __restrict__ list) {
-    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n3; x += (long long)gridDim.x * blockDim.x)
-        if (flags[x] & mask) list[pos[x]] = (int)x;
-}
-
-__global__ void k_index_map(const int* __restrict__ list, int n, int* __restrict__ map) {
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) map[list[r]] = r;
 }
 
 // Closure per gamma- node: partner p with the largest t = phi(p)/(phi(p)-phi(m)),
@@ -225,23 +254,6 @@ __global__ void k_closure(const double* __restrict__ phi, const uint8_t* __restr
 }
 
 // ------------------------------------------------------------ source recipe
-// number of terms of each source node: 1 for gamma- nodes, the number of
-// gamma- neighbours for D-nodes
-__global__ void k_term_count(const int* __restrict__ src, int ns, const uint8_t* __restrict__ flags, int N,
-                             int* __restrict__ cnt) {
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += gridDim.x * blockDim.x) {
-        const int x = src[s];
-        if (flags[x] & 2) { cnt[s] = 1; continue; }
-        const int i = x / (N * N), j = (x / N) % N, k = x % N;
-        int c = 0;
-        for (int d = 0; d < 6; ++d) {
-            const int ii = i + c_dir[d][0], jj = j + c_dir[d][1], kk = k + c_dir[d][2];
-            if (in_grid(ii, jj, kk, N) && (flags[(ii * N + jj) * N + kk] & 2)) ++c;
-        }
-        cnt[s] = c;
-    }
-}
-
 // rho(x) = coef(x) q(x) on gamma- (coef = |D_x| for the double layer, or 1
 // when D_x is empty or for the single layer); rho(k) = -sum q(n) over the
 // gamma- neighbours n of a D-node k (k is in D_n for each of them).
@@ -272,20 +284,6 @@ __global__ void k_term_fill(const int* __restrict__ src, int ns, const uint8_t* 
     }
 }
 
-// line_off[l] = first source with src_lin >= l * N  (lower bound)
-__global__ void k_line_offsets(const int* __restrict__ src, int ns, int N, int* __restrict__ line_off) {
-    const int nl = N * N;
-    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l <= nl; l += gridDim.x * blockDim.x) {
-        const long long key = (long long)l * N;
-        int lo = 0, hi = ns;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if ((long long)src[mid] < key) lo = mid + 1; else hi = mid;
-        }
-        line_off[l] = lo;
-    }
-}
-
 struct Scratch {
     cudaStream_t st;
     std::vector<void*> ptrs;
@@ -299,9 +297,9 @@ int grid_for(long long n) { return (int)std::min<long long>((n + 255) / 256, 152
 }  // namespace
 
 void Geometry::release() {
-    void* ps[] = {flags, gm, partner, t, xstar, line_off, src_lin, term_off, term_idx, term_coef};
+    void* ps[] = {flags, gm, node_of, partner, t, xstar, line_off, src_lin, term_off, term_idx, term_coef};
     for (void* p : ps) if (p) dev_free(p, stream);
-    flags = nullptr; gm = partner = nullptr; t = xstar = nullptr;
+    flags = nullptr; gm = node_of = partner = nullptr; t = xstar = nullptr;
     line_off = src_lin = term_off = term_idx = nullptr; term_coef = nullptr;
 }
 
@@ -315,74 +313,53 @@ void build_geometry(const double* phi, int N, double h, const double origin[3], 
     for (int c = 0; c < 3; ++c) g.origin[c] = origin[c];
     g.layer = layer;
 
-    int* d_err = sc.get<int>(2);
-    BAE_CUDA(cudaMemsetAsync(d_err, 0, 2 * sizeof(int), st));
-    uint8_t* inside = sc.get<uint8_t>(n3);
-    BAE_LAUNCH("k_inside", st, k_inside<<<grid_for(n3), 256, 0, st>>>(phi, n3, inside, d_err));
+    const long long nl = (long long)N * N;
+    int* info = sc.get<int>(I_COUNT);
+    BAE_CUDA(cudaMemsetAsync(info, 0, I_COUNT * sizeof(int), st));
+    uint8_t* nbits = sc.get<uint8_t>(n3);
+    BAE_LAUNCH("k_nbits", st, k_nbits<<<(unsigned)nl, LINE_T, 0, st>>>(phi, N, nbits, info));
+    const int src_mask = layer == BAE_LAYER_DOUBLE ? (2 | 8) : 2;   // gamma- and D-nodes, or gamma- only
     g.flags = dev_alloc_n<uint8_t>(n3, st);
-    BAE_LAUNCH("k_flags", st, k_flags<<<grid_for(n3), 256, 0, st>>>(inside, N, g.flags, d_err));
-    int err = 0;
-    BAE_CUDA(cudaMemcpyAsync(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    g.line_off = dev_alloc_n<int>(nl + 1, st);   // per-line source counts, then their scan
+    int* off_gm = sc.get<int>(nl + 1);
+    int* off_term = sc.get<int>(nl + 1);
+    BAE_LAUNCH("k_flags_lines", st,
+               k_flags_lines<<<(unsigned)nl, LINE_T, 0, st>>>(nbits, N, src_mask, g.flags, off_gm, g.line_off, off_term, info));
+    BAE_LAUNCH("k_scan_lines", st, k_scan_lines<<<3, 1024, 0, st>>>(off_gm, g.line_off, off_term, (int)nl, info));
+    int rec[I_COUNT];
+    BAE_CUDA(cudaMemcpyAsync(rec, info, sizeof(rec), cudaMemcpyDeviceToHost, st));
     BAE_CUDA(cudaStreamSynchronize(st));
-    if (err & 1) throw Error(BAE_ERR_INVALID_ARG, "phi contains non-finite values");
-    if (err & 2) throw Error(BAE_ERR_GEOMETRY, "M+ or gamma- reaches the faces of the grid box");
-
-    int* pred = sc.get<int>(n3);
-    int* pos = sc.get<int>(n3);
-    int* sums = sc.get<int>(ceil_div(n3, SCAN_CHUNK) + 1);
-    int* d_total = d_err + 1;
-    auto make_list = [&](int mask, long long& count) -> int* {
-        BAE_LAUNCH("k_pred", st, k_pred<<<grid_for(n3), 256, 0, st>>>(g.flags, n3, mask, pred));
-        count = exclusive_scan(pred, pos, n3, sums, d_total, st);
-        int* list = dev_alloc_n<int>(count, st);
-        BAE_LAUNCH("k_scatter_list", st, k_scatter_list<<<grid_for(n3), 256, 0, st>>>(g.flags, n3, mask, pos, list));
-        return list;
-    };
-    g.gm = make_list(2, g.n_gm);
+    if (rec[I_ERR] & 1) throw Error(BAE_ERR_INVALID_ARG, "phi contains non-finite values");
+    if (rec[I_ERR] & 2) throw Error(BAE_ERR_GEOMETRY, "M+ or gamma- reaches the faces of the grid box");
+    g.n_gm = rec[I_NGM];
+    g.n_src = rec[I_NSRC];
+    g.n_terms = rec[I_NTERM];
+    g.n_gp = rec[I_GP];
+    g.n_mp = rec[I_MP];
     if (g.n_gm == 0) throw Error(BAE_ERR_GEOMETRY, "gamma- is empty (no interior node)");
-    {
-        long long dummy;
-        int* l = make_list(4, g.n_gp);
-        dev_free(l, st);
-        l = make_list(1, g.n_mp);
-        dev_free(l, st);
-        (void)dummy;
-    }
+
+    g.gm = dev_alloc_n<int>(g.n_gm, st);
+    g.node_of = dev_alloc_n<int>(n3, st);
+    g.src_lin = dev_alloc_n<int>(g.n_src, st);
+    g.term_off = dev_alloc_n<int>(g.n_src + 1, st);
+    BAE_LAUNCH("k_scatter_lines", st,
+               k_scatter_lines<<<(unsigned)nl, LINE_T, 0, st>>>(g.flags, N, src_mask, off_gm, g.line_off, off_term, info,
+                                                                g.gm, g.node_of, g.src_lin, g.term_off));
     // closure
     g.partner = dev_alloc_n<int>(g.n_gm, st);
     g.t = dev_alloc_n<double>(g.n_gm, st);
     g.xstar = dev_alloc_n<double>(3 * g.n_gm, st);
     BAE_LAUNCH("k_closure", st, k_closure<<<grid_for(g.n_gm), 256, 0, st>>>(phi, g.flags, g.gm, (int)g.n_gm, N, h, origin[0], origin[1], origin[2],
                                                 g.partner, g.t, g.xstar));
-
     // source recipe
-    int* gidx = sc.get<int>(n3);
-    BAE_CUDA(cudaMemsetAsync(gidx, 0xff, n3 * sizeof(int), st));
-    BAE_LAUNCH("k_index_map", st, k_index_map<<<grid_for(g.n_gm), 256, 0, st>>>(g.gm, (int)g.n_gm, gidx));
-    g.src_lin = make_list(layer == BAE_LAYER_DOUBLE ? (2 | 8) : 2, g.n_src);
-    int* cnt = sc.get<int>(g.n_src + 1);
-    BAE_LAUNCH("k_term_count", st, k_term_count<<<grid_for(g.n_src), 256, 0, st>>>(g.src_lin, (int)g.n_src, g.flags, N, cnt));
-    g.term_off = dev_alloc_n<int>(g.n_src + 1, st);
-    BAE_CUDA(cudaMemsetAsync(cnt + g.n_src, 0, sizeof(int), st));
-    g.n_terms = exclusive_scan(cnt, g.term_off, g.n_src + 1, sums, d_total, st);
     g.term_idx = dev_alloc_n<int>(g.n_terms, st);
     g.term_coef = dev_alloc_n<float>(g.n_terms, st);
-    BAE_LAUNCH("k_term_fill", st, k_term_fill<<<grid_for(g.n_src), 256, 0, st>>>(g.src_lin, (int)g.n_src, g.flags, N, gidx, g.term_off, layer,
+    BAE_LAUNCH("k_term_fill", st, k_term_fill<<<grid_for(g.n_src), 256, 0, st>>>(g.src_lin, (int)g.n_src, g.flags, N, g.node_of, g.term_off, layer,
                                                    g.term_idx, g.term_coef));
-    g.line_off = dev_alloc_n<int>((long long)N * N + 1, st);
-    BAE_LAUNCH("k_line_offsets", st, k_line_offsets<<<grid_for((long long)N * N + 1), 256, 0, st>>>(g.src_lin, (int)g.n_src, N, g.line_off));
     // x-planes holding every source (gamma- and D-nodes, or M+ for the
-    // volume term) and every gathered node (gamma- and the partners, one
-    // step from gamma-): the lists are in lexicographic order, so the first
-    // and last entries bound them
-    int ends[4] = {0, 0, 0, 0};
-    BAE_CUDA(cudaMemcpyAsync(ends + 0, g.gm, sizeof(int), cudaMemcpyDeviceToHost, st));
-    BAE_CUDA(cudaMemcpyAsync(ends + 1, g.gm + (g.n_gm - 1), sizeof(int), cudaMemcpyDeviceToHost, st));
-    BAE_CUDA(cudaMemcpyAsync(ends + 2, g.src_lin, sizeof(int), cudaMemcpyDeviceToHost, st));
-    BAE_CUDA(cudaMemcpyAsync(ends + 3, g.src_lin + (g.n_src - 1), sizeof(int), cudaMemcpyDeviceToHost, st));
-    BAE_CUDA(cudaStreamSynchronize(st));
-    const long long nn = (long long)N * N;
-    const long long first = std::min(ends[0], ends[2]) / nn, last = std::max(ends[1], ends[3]) / nn;
+    // volume term, whose planes lie between) and every gathered node
+    // (gamma- and the partners, one step from gamma-)
+    const long long first = N - rec[I_FIRST], last = rec[I_LAST] - 1;
     g.plane_lo = (int)std::max(0LL, first - 1);
     g.plane_hi = (int)std::min((long long)N, last + 2);
 }

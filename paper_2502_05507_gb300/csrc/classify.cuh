@@ -16,6 +16,7 @@ struct Geometry {
     long long n_gm = 0, n_gp = 0, n_mp = 0, n_src = 0, n_terms = 0;
     uint8_t* flags = nullptr;     // N^3: bit0 M+, bit1 gamma-, bit2 gamma+, bit3 D-node, bits4-6 |D_n|
     int* gm = nullptr;            // gamma- linear indices, lexicographic
+    int* node_of = nullptr;       // N^3: index in gm of a gamma- node (set at gamma- nodes only)
     int* partner = nullptr;       // closure partner per gamma- node
     double* t = nullptr;          // closure weight per gamma- node
     double* xstar = nullptr;      // boundary points, 3 per gamma- node

@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(CPlaneGeo<T, L>::PT) k_cplane_fwd(ConvArgs<T> 
                 }
             }
             const int base = p * G::XS;
-            fft_n2k<L, false>(v, xch, base, R1 + 1, 1, t, a.tw);
+            fft_n2k<L, false, true>(v, xch, base, R1 + 1, 1, t, a.tw);
             C* z = xch + base;
 #pragma unroll
             for (int q2 = 0; q2 < Q; ++q2)
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(CPlaneGeo<T, L>::PT) k_cplane_fwd(ConvArgs<T> 
                 const int owner = m < HALF ? (R1 * m) / NR : 0;
                 v[m] = (ok && m < HALF) ? part[owner][(long long)(n - owner * NR) * N1 + col] : cmake<C>((T)0.0, (T)0.0);
             }
-            fft_n2k<L, false>(v, xch, c, R1 * G::PW, G::PW, t, a.tw);
+            fft_n2k<L, false, true>(v, xch, c, R1 * G::PW, G::PW, t, a.tw);
             if (col0 == 0) split_column0<L>(v, xch, c, t);
             if (ok) {
 #pragma unroll

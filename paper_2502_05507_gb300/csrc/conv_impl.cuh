@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(Geo<T, L>::KT) k_kpass_fwd(ConvArgs<T> a) {
         }
     }
     const int base = p * G::XS;
-    fft_n2k<L, false>(v, xch, base, R1 + 1, 1, t, a.tw);
+    fft_n2k<L, false, true>(v, xch, base, R1 + 1, 1, t, a.tw);
     // natural order into the exchange area, then split the two spectra
     // X_a = (Z[k] + conj Z[L-k]) / 2, X_b = (Z[k] - conj Z[L-k]) / 2i
     C* z = xch + base;
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(Geo<T, L>::CT) k_colpass(ConvArgs<T> a) {
             const bool live = MODE != COL_CONV_I || (n >= a.plane_lo() && n < a.plane_hi());
             v[m] = (ok && m < R2 / 2 && live) ? in[n * stride] : zero;
         }
-        fft_n2k<L, false>(v, xch, c, R1 * W, W, t, a.tw);
+        fft_n2k<L, false, true>(v, xch, c, R1 * W, W, t, a.tw);
     }
 
     if (MODE == COL_FWD_J) {
@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(512) k_plane_fwd(ConvArgs<T> a) {
                 }
             }
             const int base = p * G::XS;
-            fft_n2k<L, false>(v, xch, base, R1 + 1, 1, t, a.tw);
+            fft_n2k<L, false, true>(v, xch, base, R1 + 1, 1, t, a.tw);
             C* z = xch + base;
 #pragma unroll
             for (int q2 = 0; q2 < Q; ++q2)
@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(512) k_plane_fwd(ConvArgs<T> a) {
                 const int n = t + R1 * m;
                 v[m] = (ok && m < R2 / 2) ? plane[(long long)n * N1 + col] : cmake<C>((T)0.0, (T)0.0);
             }
-            fft_n2k<L, false>(v, xch, c, R1 * G::PW, G::PW, t, a.tw);
+            fft_n2k<L, false, true>(v, xch, c, R1 * G::PW, G::PW, t, a.tw);
             if (col0 == 0) split_column0<L>(v, xch, c, t);
             if (ok) {
 #pragma unroll

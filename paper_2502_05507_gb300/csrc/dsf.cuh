@@ -66,6 +66,39 @@ struct __align__(16) dsc {
 
 template <> struct Cplx<dsf> { using type = dsc; };
 
+// a b + c d with one TwoSum: TwoProd (FMA) of both high products, the cross
+// terms with the low parts added to their errors, a.lo b.lo and c.lo d.lo
+// dropped as in the product above (19 float operations where two products
+// and a sum take 25)
+__device__ __forceinline__ dsf dot2(dsf a, dsf b, dsf c, dsf d) {
+    const float p = __fmul_rn(a.hi, b.hi), q = __fmul_rn(c.hi, d.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    float f = __fmaf_rn(c.hi, d.hi, -q);
+    f = __fmaf_rn(c.hi, d.lo, f);
+    f = __fmaf_rn(c.lo, d.hi, f);
+    const dsf s = two_sum(p, q);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(e, f)));
+}
+
+// sum without the closing Fast2Sum: hi + lo is the same sloppy sum, lo is
+// not brought below half an ulp of hi (it grows by about that much per sum
+// until the next product renormalises). Only the complex sums of the
+// transforms use it.
+__device__ __forceinline__ dsf add_nr(dsf a, dsf b) {
+    const dsf s = two_sum(a.hi, b.hi);
+    return dsf(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
+// complex operations of the transforms (found by argument-dependent lookup
+// ahead of the generic templates)
+__device__ __forceinline__ dsc cadd(dsc a, dsc b) { return dsc{add_nr(a.x, b.x), add_nr(a.y, b.y)}; }
+__device__ __forceinline__ dsc csub(dsc a, dsc b) { return dsc{add_nr(a.x, -b.x), add_nr(a.y, -b.y)}; }
+__device__ __forceinline__ dsc cmul(dsc a, dsc b) { return dsc{dot2(a.x, b.x, -a.y, b.y), dot2(a.x, b.y, a.y, b.x)}; }
+__device__ __forceinline__ dsc cmulc(dsc a, dsc b) { return dsc{dot2(a.x, b.x, a.y, b.y), dot2(a.y, b.x, -a.x, b.y)}; }
+__device__ __forceinline__ dsc crot(dsc x, dsf c, dsf s) { return dsc{dot2(x.x, c, -x.y, s), dot2(x.x, s, x.y, c)}; }
+
 template <>
 __device__ __forceinline__ dsc ldg_c<dsc>(const dsc* p) {
     const float4 v = __ldg(reinterpret_cast<const float4*>(p));

@@ -42,6 +42,12 @@ __host__ __device__ constexpr Root32 root32(int m) {
     return {sr, -cr};
 }
 
+// x (c + i s)
+template <typename C, typename T>
+__device__ __forceinline__ C crot(C x, T c, T s) {
+    return cmake<C>(x.x * c - x.y * s, x.x * s + x.y * c);
+}
+
 // x * exp(-/+ 2 pi i M / R) with compile-time M, R | 32
 template <int R, int M, bool INV, typename C>
 __device__ __forceinline__ C wmul(C x) {
@@ -60,7 +66,7 @@ __device__ __forceinline__ C wmul(C x) {
     constexpr Root32 w = root32(m);
     const T c = (T)w.c;
     const T s = INV ? (T)w.s : (T)-w.s;
-    return cmake<C>(x.x * c - x.y * s, x.x * s + x.y * c);
+    return crot(x, c, s);
 }
 
 template <bool INV, typename C>
@@ -117,6 +123,38 @@ __device__ __forceinline__ void rdft(C* v) {
     }
 }
 
+// rdft of v[0..R) whose upper half v[R/2..R) is zero (the zero-padded
+// inputs of the forward transforms): the butterflies with a zero operand
+// are dropped (same values as rdft up to the sign of zeros)
+template <int R, bool INV, typename C>
+__device__ __forceinline__ void rdft_zhi(C* v) {
+    if constexpr (R == 2) {
+        v[1] = v[0];
+    } else if constexpr (R == 4) {
+        const C x0 = v[0], x1 = v[1];
+        const C t3 = wmul<4, 1, INV>(x1);
+        v[0] = cadd(x0, x1);
+        v[2] = csub(x0, x1);
+        v[1] = cadd(x0, t3);
+        v[3] = csub(x0, t3);
+    } else {
+        C e[R / 2], o[R / 2];   // both halves have a zero upper half again
+#pragma unroll
+        for (int i = 0; i < R / 2; ++i) {
+            e[i] = v[2 * i];
+            o[i] = v[2 * i + 1];
+        }
+        rdft_zhi<R / 2, INV>(e);
+        rdft_zhi<R / 2, INV>(o);
+        TwTail<R, INV, C, 1>::run(o);
+#pragma unroll
+        for (int k = 0; k < R / 2; ++k) {
+            v[k] = cadd(e[k], o[k]);
+            v[k + R / 2] = csub(e[k], o[k]);
+        }
+    }
+}
+
 template <int L> struct Factors;
 template <> struct Factors<16> { static constexpr int R1 = 4, R2 = 4; };
 template <> struct Factors<32> { static constexpr int R1 = 4, R2 = 8; };
@@ -132,11 +170,13 @@ template <> struct Factors<512> { static constexpr int R1 = 16, R2 = 32; };
 
 // n-layout -> k-layout (forward, or inverse when INV: then from the
 // n-layout of X to the k-layout of the inverse transform, same steps with
-// conjugate twiddles). tw: exp(-2 pi i m / L), m < L.
-template <int L, bool INV, typename C>
+// conjugate twiddles). tw: exp(-2 pi i m / L), m < L. ZHI: the input rows
+// n >= L/2 are zero (v[m] = 0 for m >= R2 / 2).
+template <int L, bool INV, bool ZHI = false, typename C>
 __device__ __forceinline__ void fft_n2k(C* v, C* xch, int base, int sk, int sn, int t, const C* __restrict__ tw) {
     constexpr int R1 = Factors<L>::R1, R2 = Factors<L>::R2, Q = R2 / R1;
-    rdft<R2, INV>(v);                                   // v[k2] = Y[t][k2]
+    if constexpr (ZHI) rdft_zhi<R2, INV>(v);          // v[k2] = Y[t][k2]
+    else rdft<R2, INV>(v);
 #pragma unroll
     for (int k2 = 1; k2 < R2; ++k2) {
         const C w = ldg_c(tw + t * k2);

@@ -1,7 +1,6 @@
 // Restricted additive Schwarz right preconditioner of the BAE (see
-// precond.cuh): built on the device (a node map, then one thread per
-// gamma- node forms its neighbourhood block and solves for its own row of
-// that block's inverse).
+// precond.cuh): built on the device, one warp per gamma- node forms its
+// neighbourhood block and solves for its own row of that block's inverse.
 #include <algorithm>
 
 #include "lgf.cuh"
@@ -12,12 +11,6 @@ namespace bae {
 namespace {
 
 
-// node_of[lin] = gamma- index of grid node lin, -1 elsewhere
-__global__ void k_node_map(const int* __restrict__ gm, long long n, int* node_of) {
-    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
-        node_of[gm[r]] = (int)r;
-}
-
 // G_s at a lattice offset from the sorted table (offsets below NEAR_TN per axis)
 __device__ __forceinline__ float lgf_at(const float* tab, int dx, int dy, int dz) {
     int a = dx < 0 ? -dx : dx, b = dy < 0 ? -dy : dy, c = dz < 0 ? -dz : dz;
@@ -27,131 +20,174 @@ __device__ __forceinline__ float lgf_at(const float* tab, int dx, int dy, int dz
     return tab[a * (a + 1) * (a + 2) / 6 + b * (b + 1) / 2 + c];
 }
 
-// potential at node x of a unit density at gamma- node c: single layer
-// G(x - c); double layer |D_c| G(x - c) - sum_{k in D_c} G(x - k), or the
-// single-layer column when D_c is empty (eqs. [single_potential],
-// [double_potential])
-__device__ float kval(const float* tab, const uint8_t* flags, int N, int layer, long long x, long long c) {
-    const long long NN = (long long)N * N;
-    const int xi = (int)(x / NN), xj = (int)((x / N) % N), xk = (int)(x % N);
-    const int ci = (int)(c / NN), cj = (int)((c / N) % N), ck = (int)(c % N);
-    const float g0 = lgf_at(tab, xi - ci, xj - cj, xk - ck);
-    if (layer != BAE_LAYER_DOUBLE) return g0;
+// potential at node x = (xi, xj, xk) of a unit density at gamma- node c:
+// single layer G(x - c); double layer |D_c| G(x - c) - sum_{k in D_c}
+// G(x - k), or the single-layer column when D_c is empty (eqs.
+// [single_potential], [double_potential]); dmask bit d: neighbour d of c
+// is a D-node (outside M+ and gamma-)
+__device__ __forceinline__ float kval(const float* tab, int xi, int xj, int xk, int ci, int cj, int ck,
+                                      unsigned dmask) {
+    const int di = xi - ci, dj = xj - cj, dk = xk - ck;
+    const float g0 = lgf_at(tab, di, dj, dk);
+    if (dmask == 0) return g0;
     float acc = 0.f;
     int nd = 0;
-    const int d[6][3] = {{1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
-    for (int q = 0; q < 6; ++q) {
-        const int ki = ci + d[q][0], kj = cj + d[q][1], kk = ck + d[q][2];
-        if (flags[((long long)ki * N + kj) * N + kk] & 3) continue;   // in N+ = M+ and gamma-
-        acc -= lgf_at(tab, xi - ki, xj - kj, xk - kk);
-        ++nd;
-    }
-    return nd == 0 ? g0 : acc + (float)nd * g0;
+    // neighbours +i, -i, +j, -j, +k, -k of c: x - k = (x - c) - e_d
+    if (dmask & 1) { acc -= lgf_at(tab, di - 1, dj, dk); ++nd; }
+    if (dmask & 2) { acc -= lgf_at(tab, di + 1, dj, dk); ++nd; }
+    if (dmask & 4) { acc -= lgf_at(tab, di, dj - 1, dk); ++nd; }
+    if (dmask & 8) { acc -= lgf_at(tab, di, dj + 1, dk); ++nd; }
+    if (dmask & 16) { acc -= lgf_at(tab, di, dj, dk - 1); ++nd; }
+    if (dmask & 32) { acc -= lgf_at(tab, di, dj, dk + 1); ++nd; }
+    return acc + (float)nd * g0;
 }
 
-// One thread per gamma- node r: S = the gamma- nodes of the 3 x 3 x 3
-// neighbourhood of r (in node order), A_S = A[S, S] from the LGF table, and
-// row r of M^{-1} = the row of r in inv(A_S), from the LU solve (partial
-// pivoting) of A_S^T z = e_r; a numerically singular block keeps the identity
-// row. Written into the MAXR slots of r.
-__global__ void __launch_bounds__(64) k_ras_rows(const int* __restrict__ gm, const int* __restrict__ partner,
-                                                 const double* __restrict__ t, const uint8_t* __restrict__ flags,
-                                                 const double* __restrict__ tab64, const int* __restrict__ node_of,
-                                                 long long n, int N, int layer, int* col, double* val) {
+constexpr int RAS_WARPS = 4;    // nodes in flight per CTA, one warp each
+constexpr int MS = MAXR + 2;    // odd row stride of a block in shared memory
+
+struct RasNode {
+    int g[3][MAXR], x[3][MAXR];   // coordinates of member p and of its partner
+    float t[MAXR];
+    unsigned dmask[MAXR];
+    int S[MAXR];
+    float M[MAXR * MS];
+};
+
+// One warp per gamma- node r. S = the gamma- nodes of the 3 x 3 x 3
+// neighbourhood of r (lane l < 27 probes one offset; the ballot keeps node
+// order), A_S = A[S, S] from the LGF table (lanes over entries), and row r
+// of M^{-1} = the row of r in inv(A_S), from Gaussian elimination with
+// partial pivoting of A_S^T z = e_r: lane p owns row p of A_S^T (|S| <= 27
+// lanes), the pivot row of step c is the unused row with the largest
+// |entry| in column c, and the back substitution runs over the columns with
+// each row's right-hand side in its lane. A numerically singular block keeps
+// the identity row.
+__global__ void __launch_bounds__(32 * RAS_WARPS) k_ras_rows(const int* __restrict__ gm, const int* __restrict__ partner,
+                                                          const double* __restrict__ t, const uint8_t* __restrict__ flags,
+                                                          const double* __restrict__ tab64, const int* __restrict__ node_of,
+                                                          long long n, int N, int layer, int* __restrict__ len,
+                                                          int* __restrict__ col, float* __restrict__ val) {
     __shared__ float tab[NEAR_TAB];
+    __shared__ RasNode sh[RAS_WARPS];
     for (int e = threadIdx.x; e < NEAR_TAB; e += blockDim.x) tab[e] = (float)tab64[e];
     __syncthreads();
-    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
-        const long long lin = gm[r], NN = (long long)N * N;
-        int S[MAXR];
-        int k = 0, me = 0;
-        for (int di = -1; di <= 1; ++di)
-            for (int dj = -1; dj <= 1; ++dj)
-                for (int dk = -1; dk <= 1; ++dk) {
-                    const int s = node_of[lin + di * NN + dj * N + dk];   // gamma- is not on a box face
-                    if (s < 0) continue;
-                    if (s == (int)r) me = k;
-                    S[k++] = s;
-                }
-        // M = A_S^T, row-major: M[q][p] = A_S[p][q] (float32)
-        float M[MAXR][MAXR], z[MAXR];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    RasNode& R = sh[w];
+    const long long NN = (long long)N * N;
+    for (long long r = (long long)blockIdx.x * RAS_WARPS + w; r < n; r += (long long)gridDim.x * RAS_WARPS) {
+        const long long lin = gm[r];
+        int s = -1;
+        if (lane < 27) {   // gamma- is not on a box face: the neighbourhood is in the grid
+            const long long y = lin + (lane / 9 - 1) * NN + ((lane / 3) % 3 - 1) * (long long)N + (lane % 3 - 1);
+            if (flags[y] & 2) s = node_of[y];
+        }
+        const unsigned ball = __ballot_sync(FULL, s >= 0);
+        const int k = __popc(ball);
+        const int me = __popc(ball & ((1u << 13) - 1));   // lane 13 probes r itself
+        if (s >= 0) {
+            const int p = __popc(ball & ((1u << lane) - 1));
+            const long long g = gm[s], x = partner[s];
+            R.S[p] = s;
+            R.g[0][p] = (int)(g / NN); R.g[1][p] = (int)((g / N) % N); R.g[2][p] = (int)(g % N);
+            R.x[0][p] = (int)(x / NN); R.x[1][p] = (int)((x / N) % N); R.x[2][p] = (int)(x % N);
+            R.t[p] = (float)t[s];
+            unsigned dm = 0;
+            if (layer == BAE_LAYER_DOUBLE) {
+                const long long off[6] = {NN, -NN, N, -(long long)N, 1, -1};
+                for (int d = 0; d < 6; ++d)
+                    if (!(flags[g + off[d]] & 3)) dm |= 1u << d;   // not in N+ = M+ and gamma-
+            }
+            R.dmask[p] = dm;
+        }
+        __syncwarp();
+        // M = A_S^T: M[q][p] = A_S[p][q] = t_p K(g_p, g_q) + (1 - t_p) K(x_p, g_q)
         float scale = 0.f;
-        for (int p = 0; p < k; ++p) {
-            const int rp = S[p];
-            const float tp = (float)t[rp];
-            for (int q = 0; q < k; ++q) {
-                const long long cq = gm[S[q]];
-                const float v = tp * kval(tab, flags, N, layer, gm[rp], cq) + (1.f - tp) * kval(tab, flags, N, layer, partner[rp], cq);
-                M[q][p] = v;
-                scale = fmaxf(scale, fabsf(v));
-            }
-            z[p] = p == me ? 1.f : 0.f;
+        for (int e = lane; e < k * k; e += 32) {
+            const int p = e / k, q = e - p * k;
+            const int ci = R.g[0][q], cj = R.g[1][q], ck = R.g[2][q];
+            const unsigned dm = R.dmask[q];
+            const float tp = R.t[p];
+            const float v = tp * kval(tab, R.g[0][p], R.g[1][p], R.g[2][p], ci, cj, ck, dm) +
+                            (1.f - tp) * kval(tab, R.x[0][p], R.x[1][p], R.x[2][p], ci, cj, ck, dm);
+            R.M[q * MS + p] = v;
+            scale = fmaxf(scale, fabsf(v));
         }
+        for (int o = 16; o > 0; o >>= 1) scale = fmaxf(scale, __shfl_xor_sync(FULL, scale, o));
+        __syncwarp();
+        float zr = lane == me ? 1.f : 0.f;   // right-hand side of row `lane`
+        bool used = lane >= k;
+        int mystep = MAXR;                  // elimination step at which row `lane` was the pivot
         bool ok = true;
-        for (int c = 0; c < k; ++c) {   // forward elimination with partial pivoting
-            int piv = c;
-            for (int q = c + 1; q < k; ++q)
-                if (fabsf(M[q][c]) > fabsf(M[piv][c])) piv = q;
-            if (!(fabsf(M[piv][c]) > 1e-6f * scale)) {
-                ok = false;
-                break;
+        for (int c = 0; c < k; ++c) {
+            const float mc = lane < k ? R.M[lane * MS + c] : 0.f;
+            float best = used ? -1.f : fabsf(mc);
+            int bl = lane;
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ob = __shfl_xor_sync(FULL, best, o);
+                const int ol = __shfl_xor_sync(FULL, bl, o);
+                if (ob > best || (ob == best && ol < bl)) { best = ob; bl = ol; }
             }
-            if (piv != c) {
-                for (int q = c; q < k; ++q) {
-                    const float x = M[piv][q];
-                    M[piv][q] = M[c][q];
-                    M[c][q] = x;
+            if (!(best > 1e-6f * scale)) { ok = false; break; }   // warp-uniform
+            const float pv = __shfl_sync(FULL, mc, bl);
+            const float zp = __shfl_sync(FULL, zr, bl);
+            if (lane == bl) { used = true; mystep = c; }
+            if (!used) {
+                const float f = mc / pv;
+                if (f != 0.f) {
+                    for (int q = c + 1; q < k; ++q) R.M[lane * MS + q] -= f * R.M[bl * MS + q];
+                    zr -= f * zp;
                 }
-                const float x = z[piv];
-                z[piv] = z[c];
-                z[c] = x;
             }
-            const float dinv = 1.f / M[c][c];
-            for (int p = c + 1; p < k; ++p) {
-                const float f = M[p][c] * dinv;
-                if (f == 0.f) continue;
-                for (int q = c + 1; q < k; ++q) M[p][q] -= f * M[c][q];
-                z[p] -= f * z[c];
-            }
+            __syncwarp();
         }
+        // back substitution: the pivot row of step c has entries only in
+        // columns >= c; x_c from it, then the rows of earlier steps drop column c
+        float xr = 0.f;   // x_lane
         if (ok)
-            for (int c = k - 1; c >= 0; --c) {   // back substitution
-                float x = z[c];
-                for (int q = c + 1; q < k; ++q) x -= M[c][q] * z[q];
-                z[c] = x / M[c][c];
+            for (int c = k - 1; c >= 0; --c) {
+                const int piv = __ffs(__ballot_sync(FULL, mystep == c)) - 1;
+                const float xc = __shfl_sync(FULL, zr, piv) / R.M[piv * MS + c];
+                if (lane == c) xr = xc;
+                if (mystep < c) zr -= R.M[lane * MS + c] * xc;
             }
-        for (int q = 0; q < MAXR; ++q) {
-            const bool use = q < k;
-            col[r * MAXR + q] = use ? S[q] : (int)r;
-            val[r * MAXR + q] = use ? (ok ? (double)z[q] : (q == me ? 1.0 : 0.0)) : 0.0;
+        else
+            xr = lane == me ? 1.f : 0.f;
+        if (lane < k) {
+            col[lane * n + r] = R.S[lane];
+            val[lane * n + r] = xr;
         }
+        if (lane == 0) len[r] = k;
+        __syncwarp();
     }
 }
 
-__global__ void k_precond_apply(const int* __restrict__ col, const double* __restrict__ val, long long n,
-                                const double* in, long long in_stride, const int* row, long long row_stride, double* out,
-                                long long out_stride, const int* active) {
+// y = M^{-1} x for one batch row per blockIdx.y: slot-major rows (slot q of
+// row r at q n + r), float values, float64 arithmetic
+__global__ void __launch_bounds__(128) k_precond_apply(const int* __restrict__ len, const int* __restrict__ col,
+                                                       const float* __restrict__ val, long long n, const double* in,
+                                                       long long in_stride, const int* row, long long row_stride,
+                                                       double* out, long long out_stride, const int* active) {
     const int b = blockIdx.y;
     if (active && !active[b]) return;
     const double* x = in + b * in_stride + (row ? (long long)row[b] * row_stride : 0);
     double* y = out + b * out_stride;
     for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+        const int k = len[r];
         double acc = 0.0;
-        for (int q = 0; q < MAXR; ++q) {
-            const double v = val[r * MAXR + q];
-            if (v != 0.0) acc += v * x[col[r * MAXR + q]];
-        }
+#pragma unroll 4
+        for (int q = 0; q < k; ++q) acc += (double)val[q * n + r] * x[col[q * n + r]];
         y[r] = acc;
     }
 }
 
-int grid_for(long long n) { return (int)std::min<long long>((n + 255) / 256, 4864); }
-
 }  // namespace
 
 void Precond::release() {
+    if (len) dev_free(len, stream);
     if (col) dev_free(col, stream);
     if (val) dev_free(val, stream);
+    len = nullptr;
     col = nullptr;
     val = nullptr;
     built = false;
@@ -160,7 +196,7 @@ void Precond::release() {
 void build_precond(const Geometry& g, double s, const double* near, Precond& out) {
     cudaStream_t st = g.stream;
     const int N = g.N;
-    const long long n = g.n_gm, n3 = (long long)N * N * N;
+    const long long n = g.n_gm;
     // G_s at offsets [0, NEAR_TN)^3, the function the convolution's spectrum comes from
     double* own = nullptr;
     if (!near) {
@@ -168,18 +204,16 @@ void build_precond(const Geometry& g, double s, const double* near, Precond& out
         lgf_table(NEAR_TN, s, own, st);
         near = own;
     }
-    int* node_of = dev_alloc_n<int>(n3, st);
-    BAE_CUDA(cudaMemsetAsync(node_of, 0xff, (size_t)n3 * sizeof(int), st));
     out.release();
     out.stream = st;
     out.n = n;
+    out.len = dev_alloc_n<int>(n, st);
     out.col = dev_alloc_n<int>(n * MAXR, st);
-    out.val = dev_alloc_n<double>(n * MAXR, st);
-    BAE_LAUNCH("k_node_map", st, k_node_map<<<grid_for(n), 256, 0, st>>>(g.gm, n, node_of));
+    out.val = dev_alloc_n<float>(n * MAXR, st);
+    const int ctas = (int)std::min<long long>((n + RAS_WARPS - 1) / RAS_WARPS, 152LL * 16);
     BAE_LAUNCH("k_ras_rows", st,
-               k_ras_rows<<<grid_for(n), 64, 0, st>>>(g.gm, g.partner, g.t, g.flags, near, node_of, n, N, g.layer,
-                                                       out.col, out.val));
-    dev_free(node_of, st);
+               k_ras_rows<<<ctas, 32 * RAS_WARPS, 0, st>>>(g.gm, g.partner, g.t, g.flags, near, g.node_of, n, N, g.layer,
+                                                           out.len, out.col, out.val));
     if (own) dev_free(own, st);
     out.built = true;
 }
@@ -187,9 +221,10 @@ void build_precond(const Geometry& g, double s, const double* near, Precond& out
 void precond_apply(const Precond& p, const double* in, long long in_stride, const int* row, long long row_stride,
                    double* out, long long out_stride, int nb, const int* active, cudaStream_t st) {
     if (p.n == 0 || nb == 0) return;
+    const int ctas = (int)std::min<long long>((p.n + 127) / 128, 152LL * 8);
     BAE_LAUNCH("k_precond_apply", st,
-               k_precond_apply<<<dim3(std::min(grid_for(p.n), 1216), nb), 256, 0, st>>>(
-                   p.col, p.val, p.n, in, in_stride, row, row_stride, out, out_stride, active));
+               k_precond_apply<<<dim3(ctas, nb), 128, 0, st>>>(p.len, p.col, p.val, p.n, in, in_stride, row, row_stride,
+                                                               out, out_stride, active));
 }
 
 }  // namespace bae

@@ -28,16 +28,17 @@ struct Precond {
     bool built = false;
     cudaStream_t stream = nullptr;
     long long n = 0;
-    // row r of M^{-1}: col[r * MAXR + q], val[r * MAXR + q], q < MAXR (unused
-    // slots have value 0)
+    // row r of M^{-1}: len[r] slots, slot q at col[q * n + r], val[q * n + r]
+    // (slot-major: consecutive rows are adjacent in each slot)
+    int* len = nullptr;
     int* col = nullptr;
-    double* val = nullptr;
+    float* val = nullptr;
     void release();
 };
 
 // Builds the preconditioner of the problem's BAE (layer and LGF parameter
-// s = kappa^2 h^2 as in the geometry) on the geometry's stream: a small LGF
-// table, a node map, and one thread per gamma- node that forms its
+// s = kappa^2 h^2 as in the geometry) on the geometry's stream: one warp
+// per gamma- node (found through the geometry's node map) forms its
 // neighbourhood block and solves for its row in float32 (a preconditioner
 // only approximates the inverse; M^{-1} itself is applied exactly in
 // float64, so the preconditioned system is unchanged).
