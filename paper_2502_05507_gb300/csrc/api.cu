@@ -386,6 +386,23 @@ out_t<T>* apply_volume(bae_problem* P, int nb, const double* f, double scale, bo
     return a.v;
 }
 
+// v[b] = K q[b] + sum_{x in M+} G(m - x) scale f[b](x): one convolution of
+// the layer and volume sources (disjoint nodes)
+template <typename T>
+out_t<T>* apply_combined(bae_problem* P, int nb, const double* q, const double* f, double scale, bool pruned) {
+    ConvArgs<T> a = conv_args<T>(P, nb, pruned);
+    a.mode = SRC_DENSITY;
+    a.q = q;
+    a.q_stride = n_gm(P);
+    a.rec = P->geo.recipe();
+    a.f = f;
+    a.flags = P->geo.flags;
+    a.scale = scale;
+    a.v = vbuf<T>(P, nb);
+    conv_apply<T>(a, P->ctx->stream);
+    return a.v;
+}
+
 // Aq[b] = Phi K q[b], both [nb][n_gm] on the device
 template <typename T>
 void boundary_apply(bae_problem* P, int nb, const double* q, double* Aq) {
@@ -408,6 +425,12 @@ double* apply_potential64(bae_problem* P, int prec, int nb, const double* q, boo
 double* apply_volume64(bae_problem* P, int prec, int nb, const double* f, double scale, bool pruned = false) {
     return prec == BAE_DF64 ? apply_volume<dsf>(P, nb, f, scale, pruned)
                             : apply_volume<double>(P, nb, f, scale, pruned);
+}
+
+double* apply_combined64(bae_problem* P, int prec, int nb, const double* q, const double* f, double scale,
+                         bool pruned) {
+    return prec == BAE_DF64 ? apply_combined<dsf>(P, nb, q, f, scale, pruned)
+                            : apply_combined<double>(P, nb, q, f, scale, pruned);
 }
 
 // --------------------------------------------------------------- GMRES
@@ -726,17 +749,27 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
     std::vector<bae_stats> st_local(nb);
     for (auto& s : st_local) std::memset(&s, 0, sizeof(s));
 
-    // particular solution u_p = G_h[chi_{M+} f] (float64) and b = g - Phi u_p
-    double* up = P->ws().up.need((long long)nb * n3);
-    {
-        double* v = apply_volume64(P, hp, nb, d_f, h * h, true);
-        BAE_CUDA(cudaMemcpyAsync(up, v, (size_t)nb * n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        for (auto& s : st_local) s.applies_fp64 += 1;
-    }
+    // particular solution u_p = G_h[chi_{M+} f] and b = g - Phi u_p. Mixed
+    // precision needs u_p only for the first inner right-hand side, so there
+    // it is a float32 apply: each float64-accurate residual below convolves
+    // the layer and volume sources together, r = g - Phi (K q + u_p), and u
+    // is that sum on N+. Otherwise u_p is float64 and kept for u.
+    const bool mixed = o.precision == BAE_MIXED;
     double* bvec = P->ws().x.need((long long)nb * n * 3);   // [b | q | r] blocks
     double* q = bvec + (long long)nb * n;
     double* res = q + (long long)nb * n;
-    closure_gather<double>(up, n3, P->geo.gm, P->geo.partner, P->geo.t, n, nb, res, n, st);
+    double* up = nullptr;
+    if (mixed) {
+        const float* v = apply_volume<float>(P, nb, d_f, h * h, true);
+        closure_gather<float>(v, n3, P->geo.gm, P->geo.partner, P->geo.t, n, nb, res, n, st);
+        for (auto& s : st_local) s.applies_fp32 += 1;
+    } else {
+        up = P->ws().up.need((long long)nb * n3);
+        double* v = apply_volume64(P, hp, nb, d_f, h * h, true);
+        BAE_CUDA(cudaMemcpyAsync(up, v, (size_t)nb * n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        for (auto& s : st_local) s.applies_fp64 += 1;
+        closure_gather<double>(up, n3, P->geo.gm, P->geo.partner, P->geo.t, n, nb, res, n, st);
+    }
     {
         std::vector<int> all(nb);
         for (int b = 0; b < nb; ++b) all[b] = b;
@@ -763,15 +796,16 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
     std::vector<double> relres(nb, 0.0);
     double* v_last = nullptr;   // float64 K q of the final q, [nb][N^3]
 
-    // residual r = b - A64 q (also leaves K q in the float64 volume buffer)
+    // residual r = b - A64 q = g - Phi (K q + u_p), with K q (+ u_p when
+    // mixed) left in the float64 volume buffer
     auto true_residual = [&]() {
         int* d_all = P->ws().active.need(nb);
         BAE_CUDA(cudaMemcpyAsync(d_all, all.data(), nb * sizeof(int), cudaMemcpyHostToDevice, st));
         double* tmp = P->ws().tmp.need((long long)nb * n);
-        double* v = apply_potential64(P, hp, nb, q, true);
+        double* v = mixed ? apply_combined64(P, hp, nb, q, d_f, h * h, true) : apply_potential64(P, hp, nb, q, true);
         closure_gather<double>(v, n3, P->geo.gm, P->geo.partner, P->geo.t, n, nb, tmp, n, st);
         for (auto& s : st_local) s.applies_fp64 += 1;
-        kr_sub(bvec, tmp, d_all, nb, n, res, st);
+        kr_sub(mixed ? d_g : bvec, tmp, d_all, nb, n, res, st);
         kr_norm2(res, d_all, nb, n, n2 + nb, krylov_chunks(n), n2, st);
         BAE_CUDA(cudaMemcpyAsync(rn2.data(), n2, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
         BAE_CUDA(cudaStreamSynchronize(st));
@@ -845,7 +879,7 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
         if (!v_last) true_residual();
     }
 
-    // outputs: u = u_p + K q on N+, density q
+    // outputs: u = u_p + K q on N+ (v_last holds the sum when mixed), density q
     bool q_host = density && !is_device_ptr(density);
     bool u_host = u && !is_device_ptr(u);
     if (u) {

@@ -34,7 +34,8 @@ struct ConvArgs {
     // optional per-item flags: items with active[b] == 0 are skipped
     const int* active = nullptr;
     SrcRecipe rec;
-    // SRC_VOLUME: rho = scale * f on nodes with (flags & 1)
+    // SRC_VOLUME: rho = scale * f on nodes with (flags & 1); in SRC_DENSITY
+    // mode a non-null f adds these volume sources to the layer sources
     const double* f = nullptr;
     const uint8_t* flags = nullptr;
     double scale = 1.0;

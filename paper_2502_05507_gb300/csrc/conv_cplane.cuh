@@ -42,7 +42,10 @@ __global__ void __launch_bounds__(CPlaneGeo<T, L>::PT) k_cplane_fwd(ConvArgs<T> 
                 T* ra = reinterpret_cast<T*>(rows + (long long)(act ? jla : 0) * N1);
                 T* rb = reinterpret_cast<T*>(rows + (long long)(act ? jlb : 0) * N1);
                 if (act)
-                    for (int k = t; k < N; k += R1) { ra[k] = (T)0.0; rb[k] = (T)0.0; }
+                    for (int k = t; k < N; k += R1) {
+                        ra[k] = volume_or_zero(a, b, la * N + k);
+                        rb[k] = volume_or_zero(a, b, lb * N + k);
+                    }
                 __syncthreads();
                 if (act) {
                     const double* q = a.q + (long long)b * a.q_stride + (a.q_row ? (long long)a.q_row[b] * a.q_row_stride : 0);

@@ -65,6 +65,16 @@ template <typename T, int L> struct PlaneGeo {
 // to float32 anyway, and on GB300 every float64 warp instruction occupies
 // the FP64 pipe for ~64 cycles. The float64 and double-float applies sum in
 // float64.
+// Initial value of node x (linear index) of batch item b in a density
+// apply: zero, or the volume source scale f on M+ when f is set (the
+// combined apply K q + G_h[chi_{M+} f]; the layer sources sit on gamma- and
+// D-nodes, outside M+, so the two never share a node)
+template <typename T>
+__device__ __forceinline__ T volume_or_zero(const ConvArgs<T>& a, int b, long long x) {
+    if (a.f && (a.flags[x] & 1)) return (T)(a.scale * a.f[(long long)b * a.N * a.N * a.N + x]);
+    return (T)0.0;
+}
+
 template <typename T>
 __device__ __forceinline__ T source_value(const SrcRecipe& rec, int s, const double* q) {
     if constexpr (std::is_same<T, float>::value) {

@@ -68,7 +68,8 @@ __global__ void __launch_bounds__(Geo<T, L>::KT) k_kpass_fwd(ConvArgs<T> a) {
 
     C v[R2];
     if (a.mode == SRC_DENSITY) {
-        for (int k = t; k < 2 * N; k += R1) r[k] = (T)0;
+        for (int k = t; k < 2 * N; k += R1)
+            r[k] = active ? volume_or_zero(a, b, (k < N ? la : lb) * N + (k < N ? k : k - N)) : (T)0;
         __syncthreads();
         if (active) {
             const double* q = a.q + (long long)b * a.q_stride + (a.q_row ? (long long)a.q_row[b] * a.q_row_stride : 0);
@@ -339,7 +340,10 @@ __global__ void __launch_bounds__(512) k_plane_fwd(ConvArgs<T> a) {
                 T* ra = reinterpret_cast<T*>(plane + (long long)(act ? ja : 0) * N1);
                 T* rb = reinterpret_cast<T*>(plane + (long long)(act ? jb : 0) * N1);
                 if (act)
-                    for (int k = t; k < N; k += R1) { ra[k] = (T)0.0; rb[k] = (T)0.0; }
+                    for (int k = t; k < N; k += R1) {
+                        ra[k] = volume_or_zero(a, b, la * N + k);
+                        rb[k] = volume_or_zero(a, b, lb * N + k);
+                    }
                 __syncthreads();
                 if (act) {
                     const double* q = a.q + (long long)b * a.q_stride + (a.q_row ? (long long)a.q_row[b] * a.q_row_stride : 0);
