@@ -84,8 +84,8 @@ typedef struct bae_options {
     int    precond;      /* BAE_MIXED only: right-preconditions the inner
                             float32 GMRES with a restricted additive Schwarz
                             inverse of the BAE matrix (each gamma- node's row
-                            of the inverse of its 3 x 3 x 3 neighbourhood
-                            block; a local form of the right preconditioning
+                            of the inverse of its 5 x 5 x 5 neighbourhood
+                            block, at most 32 nearest nodes; a local form of the right preconditioning
                             in Section 4's remark; built once per problem on
                             the device from a small LGF table): 1 (default)
                             in every refinement step, 2 in the steps after

@@ -43,7 +43,31 @@ __device__ __forceinline__ float kval(const float* tab, int xi, int xj, int xk, 
 }
 
 constexpr int RAS_WARPS = 4;    // nodes in flight per CTA, one warp each
-constexpr int MS = MAXR + 2;    // odd row stride of a block in shared memory
+constexpr int NB_W = 2 * NB_R + 1, NB_N = NB_W * NB_W * NB_W;
+
+// the offsets of the neighbourhood by increasing distance (ties in
+// lexicographic order), so that a capped block keeps the nearest nodes
+struct NbOffsets {
+    signed char d[NB_N][3];
+};
+constexpr NbOffsets make_nb_offsets() {
+    NbOffsets o{};
+    int n = 0;
+    for (int r2 = 0; r2 <= 3 * NB_R * NB_R; ++r2)
+        for (int a = -NB_R; a <= NB_R; ++a)
+            for (int b = -NB_R; b <= NB_R; ++b)
+                for (int c = -NB_R; c <= NB_R; ++c)
+                    if (a * a + b * b + c * c == r2) {
+                        o.d[n][0] = (signed char)a;
+                        o.d[n][1] = (signed char)b;
+                        o.d[n][2] = (signed char)c;
+                        ++n;
+                    }
+    return o;
+}
+__constant__ NbOffsets c_nb = make_nb_offsets();
+static_assert(2 * NB_R + 2 < NEAR_TN, "the LGF table must reach the block's offsets");
+constexpr int MS = MAXR + 1;    // odd row stride of a block in shared memory
 
 struct RasNode {
     int g[3][MAXR], x[3][MAXR];   // coordinates of member p and of its partner
@@ -53,23 +77,26 @@ struct RasNode {
     float M[MAXR * MS];
 };
 
-// One warp per gamma- node r. S = the gamma- nodes of the 3 x 3 x 3
-// neighbourhood of r (lane l < 27 probes one offset; the ballot keeps node
-// order), A_S = A[S, S] from the LGF table (lanes over entries), and row r
-// of M^{-1} = the row of r in inv(A_S), from Gaussian elimination with
-// partial pivoting of A_S^T z = e_r: lane p owns row p of A_S^T (|S| <= 27
-// lanes), the pivot row of step c is the unused row with the largest
-// |entry| in column c, and the back substitution runs over the columns with
-// each row's right-hand side in its lane. A numerically singular block keeps
-// the identity row.
+// One warp per gamma- node r. S = the gamma- nodes of the neighbourhood of
+// r, nearest first (the lanes probe 32 offsets per round; a ballot keeps the
+// order; at most MAXR, r itself first), A_S = A[S, S] from the LGF table
+// (lanes over entries), and row r of M^{-1} = the row of r in inv(A_S), from
+// Gaussian elimination with partial pivoting of A_S^T z = e_r: lane p owns
+// row p of A_S^T, the pivot row of step c is the unused row with the
+// largest |entry| in column c, and the back substitution runs over the
+// columns with each row's right-hand side in its lane. A numerically
+// singular block keeps the identity row.
 __global__ void __launch_bounds__(32 * RAS_WARPS) k_ras_rows(const int* __restrict__ gm, const int* __restrict__ partner,
                                                           const double* __restrict__ t, const uint8_t* __restrict__ flags,
                                                           const double* __restrict__ tab64, const int* __restrict__ node_of,
                                                           long long n, int N, int layer, int* __restrict__ len,
                                                           int* __restrict__ col, float* __restrict__ val) {
     __shared__ float tab[NEAR_TAB];
+    __shared__ signed char nbo[NB_N][3];
     __shared__ RasNode sh[RAS_WARPS];
     for (int e = threadIdx.x; e < NEAR_TAB; e += blockDim.x) tab[e] = (float)tab64[e];
+    for (int e = threadIdx.x; e < NB_N; e += blockDim.x)
+        for (int c = 0; c < 3; ++c) nbo[e][c] = c_nb.d[e][c];
     __syncthreads();
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -77,29 +104,37 @@ __global__ void __launch_bounds__(32 * RAS_WARPS) k_ras_rows(const int* __restri
     const long long NN = (long long)N * N;
     for (long long r = (long long)blockIdx.x * RAS_WARPS + w; r < n; r += (long long)gridDim.x * RAS_WARPS) {
         const long long lin = gm[r];
-        int s = -1;
-        if (lane < 27) {   // gamma- is not on a box face: the neighbourhood is in the grid
-            const long long y = lin + (lane / 9 - 1) * NN + ((lane / 3) % 3 - 1) * (long long)N + (lane % 3 - 1);
-            if (flags[y] & 2) s = node_of[y];
-        }
-        const unsigned ball = __ballot_sync(FULL, s >= 0);
-        const int k = __popc(ball);
-        const int me = __popc(ball & ((1u << 13) - 1));   // lane 13 probes r itself
-        if (s >= 0) {
-            const int p = __popc(ball & ((1u << lane) - 1));
-            const long long g = gm[s], x = partner[s];
-            R.S[p] = s;
-            R.g[0][p] = (int)(g / NN); R.g[1][p] = (int)((g / N) % N); R.g[2][p] = (int)(g % N);
-            R.x[0][p] = (int)(x / NN); R.x[1][p] = (int)((x / N) % N); R.x[2][p] = (int)(x % N);
-            R.t[p] = (float)t[s];
-            unsigned dm = 0;
-            if (layer == BAE_LAYER_DOUBLE) {
-                const long long off[6] = {NN, -NN, N, -(long long)N, 1, -1};
-                for (int d = 0; d < 6; ++d)
-                    if (!(flags[g + off[d]] & 3)) dm |= 1u << d;   // not in N+ = M+ and gamma-
+        const int ri = (int)(lin / NN), rj = (int)((lin / N) % N), rk = (int)(lin % N);
+        int k = 0;
+        for (int base = 0; base < NB_N && k < MAXR; base += 32) {
+            const int e = base + lane;
+            int s = -1;
+            if (e < NB_N) {
+                const int ii = ri + nbo[e][0], jj = rj + nbo[e][1], kk = rk + nbo[e][2];
+                if ((unsigned)ii < (unsigned)N && (unsigned)jj < (unsigned)N && (unsigned)kk < (unsigned)N) {
+                    const long long y = (ii * NN) + (long long)jj * N + kk;
+                    if (flags[y] & 2) s = node_of[y];
+                }
             }
-            R.dmask[p] = dm;
+            const unsigned ball = __ballot_sync(FULL, s >= 0);
+            const int p = k + __popc(ball & ((1u << lane) - 1));
+            if (s >= 0 && p < MAXR) {
+                const long long g = gm[s], x = partner[s];
+                R.S[p] = s;
+                R.g[0][p] = (int)(g / NN); R.g[1][p] = (int)((g / N) % N); R.g[2][p] = (int)(g % N);
+                R.x[0][p] = (int)(x / NN); R.x[1][p] = (int)((x / N) % N); R.x[2][p] = (int)(x % N);
+                R.t[p] = (float)t[s];
+                unsigned dm = 0;
+                if (layer == BAE_LAYER_DOUBLE) {
+                    const long long off[6] = {NN, -NN, N, -(long long)N, 1, -1};
+                    for (int d = 0; d < 6; ++d)
+                        if (!(flags[g + off[d]] & 3)) dm |= 1u << d;   // not in N+ = M+ and gamma-
+                }
+                R.dmask[p] = dm;
+            }
+            k = min(MAXR, k + __popc(ball));
         }
+        const int me = 0;   // offset 0 comes first: r itself
         __syncwarp();
         // M = A_S^T: M[q][p] = A_S[p][q] = t_p K(g_p, g_q) + (1 - t_p) K(x_p, g_q)
         float scale = 0.f;

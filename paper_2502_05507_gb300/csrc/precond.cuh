@@ -5,9 +5,10 @@
 // but its near-field entries dominate. Section 4 remarks that right
 // preconditioning by the dense D_- improves the spectrum but costs too much,
 // and the numerical section asks for preconditioning; this is a local form:
-// for every gamma- node r, S_r = the gamma- nodes of the 3 x 3 x 3
-// neighbourhood of r (about 9, at most 27), and row r of M^{-1} is the row
-// of r in inv(A[S_r, S_r]). GMRES solves A M^{-1} y = b, q = M^{-1} y.
+// for every gamma- node r, S_r = the gamma- nodes of the 5 x 5 x 5
+// neighbourhood of r (about 25 on a smooth surface; the MAXR nearest when
+// there are more), and row r of M^{-1} is the row of r in inv(A[S_r, S_r]).
+// GMRES solves A M^{-1} y = b, q = M^{-1} y.
 //
 // A M^{-1} v is computed as A z with z = M^{-1} v formed by a small sparse
 // kernel in float64 (inside the captured GMRES step), so the convolution
@@ -20,8 +21,9 @@
 
 namespace bae {
 
-constexpr int MAXR = 27;   // gamma- nodes in a 3 x 3 x 3 neighbourhood, at most
-constexpr int NEAR_TN = 8;  // the blocks use G_s at offsets [0, NEAR_TN)^3 (up to 4 per axis)
+constexpr int MAXR = 32;   // members of a neighbourhood block, at most (one per lane of a warp)
+constexpr int NB_R = 2;    // the neighbourhood: offsets up to NB_R per axis
+constexpr int NEAR_TN = 8;  // the blocks use G_s at offsets [0, NEAR_TN)^3 (up to 2 NB_R + 2 per axis)
 constexpr int NEAR_TAB = NEAR_TN * (NEAR_TN + 1) * (NEAR_TN + 2) / 6;   // sorted-table length
 
 struct Precond {
