@@ -131,11 +131,12 @@ def kernel_model(n, pb, n_gm, npl=None):
 
 
 FP64_PEAK_TFLOPS = 1.25   # nominal FP64 rate of GB300 (a probe measured 1.20)
-# double-float kernels run on the float32 pipes: one float64-equivalent flop
-# of an FFT butterfly mix (4 mul + 6 add per radix-2 step) costs 14.8 float32
-# instructions (add 20, mul 7); the float32 instruction rate is half the
-# measured 70.2 TFLOP/s FMA rate
-DF64_OPS_PER_FLOP = 14.8
+# double-float kernels run on the float32 pipes: a radix-2 butterfly (10
+# float64-equivalent flops: one complex product, two complex sums) costs 70
+# float32 instructions (a complex product as two fused a b + c d forms of 19,
+# a sum 8), 7 per flop; the float32 instruction rate is half the measured
+# 70.2 TFLOP/s FMA rate
+DF64_OPS_PER_FLOP = 7.0
 FP32_INST_PEAK_T = 35.1
 
 

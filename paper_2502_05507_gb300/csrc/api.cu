@@ -253,6 +253,10 @@ struct bae_ctx {
     std::map<int, Twiddles> tw;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaEvent_t poll_ev[2] = {nullptr, nullptr};
+    // second stream: set-up work that overlaps the main stream's (the
+    // Schwarz rows), ordered by the fork and join events
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     int* pinned = nullptr;       // mapped host memory the kernels write the live flags into
     int* pinned_dev = nullptr;   // its device address
     int pinned_cap = 0;
@@ -561,14 +565,21 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
     a.gm = P->geo.gm;
     a.partner = P->geo.partner;
     a.t = P->geo.t;
-    // right preconditioning: the step applies A to z = M^{-1} V[j]
+    // right preconditioning: the step applies A to z = M^{-1} V[j]; the
+    // fused step forms the next z itself (after arn_init: z of V[0] here)
     double* zpre = pre ? ws.zpre.need((long long)nb * n) : nullptr;
+    const bool fuse_pre = pre && a.coop_grid > 0;
+    if (fuse_pre) {
+        a.pre_col = P->pre.col;
+        a.pre_val = P->pre.val;
+        a.zpre = zpre;
+    }
     auto one_step = [&]() {
         const double* q = a.V;
         long long qs = (long long)(m + 1) * n;
         const int* qrow = a.j;
         if (pre) {
-            precond_apply(P->pre, a.V, qs, a.j, n, zpre, n, nb, a.flag, st);
+            if (!fuse_pre) precond_apply(P->pre, a.V, qs, a.j, n, zpre, n, nb, a.flag, st);
             q = zpre;
             qs = n;
             qrow = nullptr;
@@ -621,6 +632,7 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
             }
             kr_norm2(r, d_all, nb, n, npart + nb, krylov_chunks(n), npart, st);
             arn_init(a, r, npart, member, st);
+            if (fuse_pre) precond_apply(P->pre, a.V, (long long)(m + 1) * n, nullptr, 0, zpre, n, nb, member, st);
             // the fused step applies the rotations of a column one step later:
             // one more launch finishes the last column of the cycle
             const int steps = std::min(m, iters_left) + (a.coop_grid > 0 ? 1 : 0);
@@ -722,6 +734,17 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
     const long long n3 = P->n3();
     const int n = (int)n_gm(P);
     const double h = P->geo.h;
+    // the right preconditioner of the inner solves (restricted additive
+    // Schwarz) is built on the side stream while this one checks the inputs
+    // and forms the first right-hand side; the inner solves wait for it
+    const bool any_pre = o.precision == BAE_MIXED && o.precond != 0;
+    if (any_pre && !P->pre.built) {
+        BAE_CUDA(cudaEventRecord(P->ctx->fork_ev, st));
+        BAE_CUDA(cudaStreamWaitEvent(P->ctx->side, P->ctx->fork_ev, 0));
+        build_precond(P->geo, P->s, P->spec->near, P->pre, P->ctx->side);
+        BAE_CUDA(cudaEventRecord(P->ctx->join_ev, P->ctx->side));
+        P->pre.pending = true;
+    }
 
     // stage host inputs
     const double* d_f = f;
@@ -826,10 +849,12 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
         // iterative refinement: inner float32-apply GMRES on A d = r, q += d,
         // r = b - A64 q in float64
         double* d = P->ws().vstage.need((long long)nb * n);
-        // right preconditioner of the inner solves (restricted additive
-        // Schwarz; the inner unknown is y with d = M^{-1} y)
-        const bool any_pre = o.precond != 0;
-        if (any_pre && !P->pre.built) build_precond(P->geo, P->s, P->spec->near, P->pre);
+        // right preconditioner of the inner solves (the inner unknown is y
+        // with d = M^{-1} y), built on the side stream above
+        if (P->pre.pending) {
+            BAE_CUDA(cudaStreamWaitEvent(st, P->ctx->join_ev, 0));
+            P->pre.pending = false;
+        }
         double* dq = any_pre ? P->ws().qpre.need((long long)nb * n) : d;
         BAE_CUDA(cudaMemcpyAsync(res, bvec, (size_t)nb * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
         rn2 = bn2;
@@ -1066,6 +1091,9 @@ int bae_ctx_create(int device, void* stream, bae_ctx** out) {
         BAE_CUDA(cudaEventCreate(&c->ev1));
         BAE_CUDA(cudaEventCreateWithFlags(&c->poll_ev[0], cudaEventDisableTiming));
         BAE_CUDA(cudaEventCreateWithFlags(&c->poll_ev[1], cudaEventDisableTiming));
+        BAE_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+        BAE_CUDA(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
+        BAE_CUDA(cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming));
         // keep freed blocks of the default pool for reuse (problem set-up
         // and work space come from it)
         cudaMemPool_t pool;
@@ -1095,6 +1123,12 @@ void bae_ctx_destroy(bae_ctx* ctx) {
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     for (cudaEvent_t e : ctx->poll_ev)
         if (e) cudaEventDestroy(e);
+    if (ctx->side) {
+        cudaStreamSynchronize(ctx->side);
+        cudaStreamDestroy(ctx->side);
+    }
+    if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+    if (ctx->join_ev) cudaEventDestroy(ctx->join_ev);
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -1161,6 +1195,7 @@ int bae_problem_create(bae_ctx* ctx, int N, double h, const double origin[3], co
 void bae_problem_destroy(bae_problem* P) {
     if (!P) return;
     cudaSetDevice(P->ctx->device);
+    if (P->pre.pending) cudaStreamSynchronize(P->ctx->side);   // a build the main stream never waited for
     cudaStreamSynchronize(P->ctx->stream);
     P->pre.release();
     P->geo.release();

@@ -693,6 +693,46 @@ __global__ void __launch_bounds__(256) k_arn_step_coop(Arnoldi a) {
                      s_red[1]);
         __syncthreads();
     }
+    if (!a.pre_col) return;
+    // phase 6: z = M^{-1} V[j+1] on the chunk's rows: warp w takes rows
+    // 8 w .. 8 w + 7 of each item, lane q slot q, the same products and
+    // shuffle tree as the separate preconditioner kernel. The slots of the
+    // CTA's first item are loaded before the barrier (they do not depend on
+    // V[j+1]); V[j+1] is read through L2 (other CTAs wrote it).
+    constexpr int RW = ACH / 8;   // rows per warp (8 warps)
+    static_assert(ACH % 8 == 0, "rows per warp");
+    const int lane = threadIdx.x & 31, wr = (threadIdx.x >> 5) * RW;
+    int pc[RW];
+    float pv[RW];
+    auto load_slots = [&](int item) {
+        const long long r0 = (long long)(item % a.nchunk) * ACH + wr;
+#pragma unroll
+        for (int u = 0; u < RW; ++u) {
+            const long long r = r0 + u;
+            pc[u] = r < a.n ? __ldg(a.pre_col + r * 32 + lane) : 0;
+            pv[u] = r < a.n ? __ldg(a.pre_val + r * 32 + lane) : 0.f;
+        }
+    };
+    if ((int)blockIdx.x < items) load_slots(blockIdx.x);
+    grid_barrier(a.bar2, GI, a.err);   // V[j+1] complete
+    for (int item = blockIdx.x; item < items; item += NI) {
+        const int b = item / a.nchunk, c = item % a.nchunk;
+        if (item != (int)blockIdx.x) load_slots(item);
+        if (!s_flag[b]) continue;
+        const double* x = a.V + ((long long)b * (m + 1) + s_j[b] + 1) * a.n;
+        double* z = a.zpre + (long long)b * a.n;
+        const long long r0 = (long long)c * ACH + wr;
+        double xv[RW];
+#pragma unroll
+        for (int u = 0; u < RW; ++u) xv[u] = r0 + u < a.n ? __ldcg(x + pc[u]) : 0.0;
+#pragma unroll
+        for (int u = 0; u < RW; ++u) {
+            double v = (double)pv[u] * xv[u];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0 && r0 + u < a.n) z[r0 + u] = v;
+        }
+    }
 }
 
 // y = R^{-1} g, one warp per RHS (column-oriented back substitution)

@@ -82,6 +82,12 @@ struct Arnoldi {
     int* live = nullptr;                   // [nb]
     int* live_host = nullptr;              // [nb] device address of mapped host memory, or null
     double* pcol = nullptr;                // [nb][2][m + 2]
+    // right preconditioner rows (32 slots per row, column r and value 0 in
+    // unused slots): when set, the fused step ends with z = M^{-1} V[j+1]
+    // (the next step's apply reads z) after one more grid barrier
+    const int* pre_col = nullptr;
+    const float* pre_val = nullptr;
+    double* zpre = nullptr;                // [nb][n]
     unsigned long long* bar2 = nullptr;
 };
 

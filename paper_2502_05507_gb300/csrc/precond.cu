@@ -11,13 +11,20 @@ namespace bae {
 namespace {
 
 
-// G_s at a lattice offset from the sorted table (offsets below NEAR_TN per axis)
-__device__ __forceinline__ float lgf_at(const float* tab, int dx, int dy, int dz) {
+// G_s on the offset cube [-TE, TE]^3 in shared memory, filled from the
+// sorted table (offsets below NEAR_TN per axis, sorted by absolute value)
+constexpr int TE = NEAR_TN - 1, TW = 2 * TE + 1, TCUBE = TW * TW * TW;
+
+__device__ __forceinline__ float lgf_sorted(const double* __restrict__ tab, int dx, int dy, int dz) {
     int a = dx < 0 ? -dx : dx, b = dy < 0 ? -dy : dy, c = dz < 0 ? -dz : dz;
     if (a < b) { const int x = a; a = b; b = x; }
     if (b < c) { const int x = b; b = c; c = x; }
     if (a < b) { const int x = a; a = b; b = x; }
-    return tab[a * (a + 1) * (a + 2) / 6 + b * (b + 1) / 2 + c];
+    return (float)tab[a * (a + 1) * (a + 2) / 6 + b * (b + 1) / 2 + c];
+}
+
+__device__ __forceinline__ float lgf_at(const float* cube, int dx, int dy, int dz) {
+    return cube[((dx + TE) * TW + (dy + TE)) * TW + (dz + TE)];
 }
 
 // potential at node x = (xi, xj, xk) of a unit density at gamma- node c:
@@ -42,7 +49,7 @@ __device__ __forceinline__ float kval(const float* tab, int xi, int xj, int xk, 
     return acc + (float)nd * g0;
 }
 
-constexpr int RAS_WARPS = 4;    // nodes in flight per CTA, one warp each
+constexpr int RAS_WARPS = 6;    // nodes in flight per CTA, one warp each (static shared memory < 48 KB)
 constexpr int NB_W = 2 * NB_R + 1, NB_N = NB_W * NB_W * NB_W;
 
 // the offsets of the neighbourhood by increasing distance (ties in
@@ -86,53 +93,78 @@ struct RasNode {
 // largest |entry| in column c, and the back substitution runs over the
 // columns with each row's right-hand side in its lane. A numerically
 // singular block keeps the identity row.
-__global__ void __launch_bounds__(32 * RAS_WARPS) k_ras_rows(const int* __restrict__ gm, const int* __restrict__ partner,
-                                                          const double* __restrict__ t, const uint8_t* __restrict__ flags,
+// Per gamma- node s: its grid index, its closure partner's, t (float bits)
+// and the D-node mask of its six neighbours (double layer; bit d: neighbour
+// d outside N+ = M+ and gamma-), 16 bytes read once per block member.
+__global__ void k_member_info(const int* __restrict__ gm, const int* __restrict__ partner, const double* __restrict__ t,
+                              const uint8_t* __restrict__ flags, long long n, int N, int layer, int4* __restrict__ info) {
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+        const int g = gm[s];
+        unsigned dm = 0;
+        if (layer == BAE_LAYER_DOUBLE) {
+            const int off[6] = {N * N, -N * N, N, -N, 1, -1};
+            for (int d = 0; d < 6; ++d)
+                if (!(flags[g + off[d]] & 3)) dm |= 1u << d;
+        }
+        info[s] = make_int4(g, partner[s], __float_as_int((float)t[s]), (int)dm);
+    }
+}
+
+__global__ void __launch_bounds__(32 * RAS_WARPS) k_ras_rows(const int* __restrict__ gm, const int4* __restrict__ minfo,
+                                                          const uint8_t* __restrict__ flags,
                                                           const double* __restrict__ tab64, const int* __restrict__ node_of,
-                                                          long long n, int N, int layer, int* __restrict__ len,
-                                                          int* __restrict__ col, float* __restrict__ val) {
-    __shared__ float tab[NEAR_TAB];
+                                                          long long n, int N, int* __restrict__ col,
+                                                          float* __restrict__ val) {
+    __shared__ float tab[TCUBE];
     __shared__ signed char nbo[NB_N][3];
     __shared__ RasNode sh[RAS_WARPS];
-    for (int e = threadIdx.x; e < NEAR_TAB; e += blockDim.x) tab[e] = (float)tab64[e];
+    for (int e = threadIdx.x; e < TCUBE; e += blockDim.x)
+        tab[e] = lgf_sorted(tab64, e / (TW * TW) - TE, (e / TW) % TW - TE, e % TW - TE);
     for (int e = threadIdx.x; e < NB_N; e += blockDim.x)
         for (int c = 0; c < 3; ++c) nbo[e][c] = c_nb.d[e][c];
     __syncthreads();
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     RasNode& R = sh[w];
-    const long long NN = (long long)N * N;
+    const int NN = N * N;   // N^3 < 2^31
+    constexpr int ROUNDS = (NB_N + 31) / 32;
     for (long long r = (long long)blockIdx.x * RAS_WARPS + w; r < n; r += (long long)gridDim.x * RAS_WARPS) {
-        const long long lin = gm[r];
-        const int ri = (int)(lin / NN), rj = (int)((lin / N) % N), rk = (int)(lin % N);
-        int k = 0;
-        for (int base = 0; base < NB_N && k < MAXR; base += 32) {
-            const int e = base + lane;
-            int s = -1;
+        const int lin = gm[r];
+        const int ri = lin / NN, rj = (lin / N) % N, rk = lin % N;
+        // every probe's flags first (independent loads), then the node indices
+        int y[ROUNDS], s[ROUNDS];
+#pragma unroll
+        for (int q = 0; q < ROUNDS; ++q) {
+            const int e = q * 32 + lane;
+            y[q] = -1;
             if (e < NB_N) {
                 const int ii = ri + nbo[e][0], jj = rj + nbo[e][1], kk = rk + nbo[e][2];
-                if ((unsigned)ii < (unsigned)N && (unsigned)jj < (unsigned)N && (unsigned)kk < (unsigned)N) {
-                    const long long y = (ii * NN) + (long long)jj * N + kk;
-                    if (flags[y] & 2) s = node_of[y];
-                }
+                if ((unsigned)ii < (unsigned)N && (unsigned)jj < (unsigned)N && (unsigned)kk < (unsigned)N)
+                    y[q] = (ii * N + jj) * N + kk;
             }
-            const unsigned ball = __ballot_sync(FULL, s >= 0);
+        }
+#pragma unroll
+        for (int q = 0; q < ROUNDS; ++q) s[q] = (y[q] >= 0 && (flags[y[q]] & 2)) ? 0 : -1;
+#pragma unroll
+        for (int q = 0; q < ROUNDS; ++q)
+            if (s[q] == 0) s[q] = node_of[y[q]];
+        // members in probe order (nearest first), at most MAXR
+        int k = 0, mine = -1;
+#pragma unroll
+        for (int q = 0; q < ROUNDS; ++q) {
+            const unsigned ball = __ballot_sync(FULL, s[q] >= 0);
             const int p = k + __popc(ball & ((1u << lane) - 1));
-            if (s >= 0 && p < MAXR) {
-                const long long g = gm[s], x = partner[s];
-                R.S[p] = s;
-                R.g[0][p] = (int)(g / NN); R.g[1][p] = (int)((g / N) % N); R.g[2][p] = (int)(g % N);
-                R.x[0][p] = (int)(x / NN); R.x[1][p] = (int)((x / N) % N); R.x[2][p] = (int)(x % N);
-                R.t[p] = (float)t[s];
-                unsigned dm = 0;
-                if (layer == BAE_LAYER_DOUBLE) {
-                    const long long off[6] = {NN, -NN, N, -(long long)N, 1, -1};
-                    for (int d = 0; d < 6; ++d)
-                        if (!(flags[g + off[d]] & 3)) dm |= 1u << d;   // not in N+ = M+ and gamma-
-                }
-                R.dmask[p] = dm;
-            }
+            if (s[q] >= 0 && p < MAXR) R.S[p] = s[q];
             k = min(MAXR, k + __popc(ball));
+        }
+        __syncwarp();
+        if (lane < k) mine = R.S[lane];
+        if (mine >= 0) {
+            const int4 f = minfo[mine];
+            R.g[0][lane] = f.x / NN; R.g[1][lane] = (f.x / N) % N; R.g[2][lane] = f.x % N;
+            R.x[0][lane] = f.y / NN; R.x[1][lane] = (f.y / N) % N; R.x[2][lane] = f.y % N;
+            R.t[lane] = __int_as_float(f.z);
+            R.dmask[lane] = (unsigned)f.w;
         }
         const int me = 0;   // offset 0 comes first: r itself
         __syncwarp();
@@ -156,20 +188,21 @@ __global__ void __launch_bounds__(32 * RAS_WARPS) k_ras_rows(const int* __restri
         bool ok = true;
         for (int c = 0; c < k; ++c) {
             const float mc = lane < k ? R.M[lane * MS + c] : 0.f;
-            float best = used ? -1.f : fabsf(mc);
-            int bl = lane;
-            for (int o = 16; o > 0; o >>= 1) {
-                const float ob = __shfl_xor_sync(FULL, best, o);
-                const int ol = __shfl_xor_sync(FULL, bl, o);
-                if (ob > best || (ob == best && ol < bl)) { best = ob; bl = ol; }
-            }
-            if (!(best > 1e-6f * scale)) { ok = false; break; }   // warp-uniform
+            // pivot: one integer max over the lanes of (|entry| bits with the
+            // low 5 mantissa bits replaced by 31 - lane), so equal keys go to
+            // the lower row; used rows take key 0
+            const unsigned key = used ? 0u : ((__float_as_uint(fabsf(mc)) & ~31u) | (unsigned)(31 - lane));
+            const unsigned top = __reduce_max_sync(FULL, key);
+            const int bl = 31 - (int)(top & 31u);
+            const float best = __uint_as_float(top & ~31u);
+            if (top == 0u || !(best > 1e-6f * scale)) { ok = false; break; }   // warp-uniform
             const float pv = __shfl_sync(FULL, mc, bl);
             const float zp = __shfl_sync(FULL, zr, bl);
             if (lane == bl) { used = true; mystep = c; }
             if (!used) {
-                const float f = mc / pv;
+                const float f = __fdividef(mc, pv);
                 if (f != 0.f) {
+#pragma unroll 4
                     for (int q = c + 1; q < k; ++q) R.M[lane * MS + q] -= f * R.M[bl * MS + q];
                     zr -= f * zp;
                 }
@@ -182,24 +215,23 @@ __global__ void __launch_bounds__(32 * RAS_WARPS) k_ras_rows(const int* __restri
         if (ok)
             for (int c = k - 1; c >= 0; --c) {
                 const int piv = __ffs(__ballot_sync(FULL, mystep == c)) - 1;
-                const float xc = __shfl_sync(FULL, zr, piv) / R.M[piv * MS + c];
+                const float xc = __fdividef(__shfl_sync(FULL, zr, piv), R.M[piv * MS + c]);
                 if (lane == c) xr = xc;
                 if (mystep < c) zr -= R.M[lane * MS + c] * xc;
             }
         else
             xr = lane == me ? 1.f : 0.f;
-        if (lane < k) {
-            col[lane * n + r] = R.S[lane];
-            val[lane * n + r] = xr;
-        }
-        if (lane == 0) len[r] = k;
+        // all MAXR slots: unused ones hold (r, 0)
+        col[r * MAXR + lane] = lane < k ? R.S[lane] : (int)r;
+        val[r * MAXR + lane] = lane < k ? xr : 0.f;
         __syncwarp();
     }
 }
 
-// y = M^{-1} x for one batch row per blockIdx.y: slot-major rows (slot q of
-// row r at q n + r), float values, float64 arithmetic
-__global__ void __launch_bounds__(128) k_precond_apply(const int* __restrict__ len, const int* __restrict__ col,
+// y = M^{-1} x for one batch row per blockIdx.y: one warp per row, lane q
+// takes slot q (row-major slots, float values, float64 products), a
+// shuffle tree sums them
+__global__ void __launch_bounds__(256) k_precond_apply(const int* __restrict__ col,
                                                        const float* __restrict__ val, long long n, const double* in,
                                                        long long in_stride, const int* row, long long row_stride,
                                                        double* out, long long out_stride, const int* active) {
@@ -207,29 +239,27 @@ __global__ void __launch_bounds__(128) k_precond_apply(const int* __restrict__ l
     if (active && !active[b]) return;
     const double* x = in + b * in_stride + (row ? (long long)row[b] * row_stride : 0);
     double* y = out + b * out_stride;
-    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
-        const int k = len[r];
-        double acc = 0.0;
-#pragma unroll 4
-        for (int q = 0; q < k; ++q) acc += (double)val[q * n + r] * x[col[q * n + r]];
-        y[r] = acc;
+    const int lane = threadIdx.x & 31;
+    const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long r = w0; r < n; r += nw) {
+        double v = (double)val[r * MAXR + lane] * x[col[r * MAXR + lane]];   // unused slots: 0 x[r]
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) y[r] = v;
     }
 }
 
 }  // namespace
 
 void Precond::release() {
-    if (len) dev_free(len, stream);
     if (col) dev_free(col, stream);
     if (val) dev_free(val, stream);
-    len = nullptr;
     col = nullptr;
     val = nullptr;
     built = false;
 }
 
-void build_precond(const Geometry& g, double s, const double* near, Precond& out) {
-    cudaStream_t st = g.stream;
+void build_precond(const Geometry& g, double s, const double* near, Precond& out, cudaStream_t st) {
     const int N = g.N;
     const long long n = g.n_gm;
     // G_s at offsets [0, NEAR_TN)^3, the function the convolution's spectrum comes from
@@ -240,15 +270,19 @@ void build_precond(const Geometry& g, double s, const double* near, Precond& out
         near = own;
     }
     out.release();
-    out.stream = st;
+    out.stream = g.stream;
     out.n = n;
-    out.len = dev_alloc_n<int>(n, st);
     out.col = dev_alloc_n<int>(n * MAXR, st);
     out.val = dev_alloc_n<float>(n * MAXR, st);
-    const int ctas = (int)std::min<long long>((n + RAS_WARPS - 1) / RAS_WARPS, 152LL * 16);
+    int4* minfo = dev_alloc_n<int4>(n, st);
+    BAE_LAUNCH("k_member_info", st,
+               k_member_info<<<(int)std::min<long long>((n + 255) / 256, 152LL * 8), 256, 0, st>>>(
+                   g.gm, g.partner, g.t, g.flags, n, N, g.layer, minfo));
+    const int ctas = (int)std::min<long long>((n + RAS_WARPS - 1) / RAS_WARPS, 152LL * 4);
     BAE_LAUNCH("k_ras_rows", st,
-               k_ras_rows<<<ctas, 32 * RAS_WARPS, 0, st>>>(g.gm, g.partner, g.t, g.flags, near, g.node_of, n, N, g.layer,
-                                                           out.len, out.col, out.val));
+               k_ras_rows<<<ctas, 32 * RAS_WARPS, 0, st>>>(g.gm, minfo, g.flags, near, g.node_of, n, N, out.col,
+                                                           out.val));
+    dev_free(minfo, st);
     if (own) dev_free(own, st);
     out.built = true;
 }
@@ -256,9 +290,9 @@ void build_precond(const Geometry& g, double s, const double* near, Precond& out
 void precond_apply(const Precond& p, const double* in, long long in_stride, const int* row, long long row_stride,
                    double* out, long long out_stride, int nb, const int* active, cudaStream_t st) {
     if (p.n == 0 || nb == 0) return;
-    const int ctas = (int)std::min<long long>((p.n + 127) / 128, 152LL * 8);
+    const int ctas = (int)std::min<long long>((p.n + 7) / 8, 152LL * 16);   // 8 rows per 256-thread CTA
     BAE_LAUNCH("k_precond_apply", st,
-               k_precond_apply<<<dim3(ctas, nb), 128, 0, st>>>(p.len, p.col, p.val, p.n, in, in_stride, row, row_stride,
+               k_precond_apply<<<dim3(ctas, nb), 256, 0, st>>>(p.col, p.val, p.n, in, in_stride, row, row_stride,
                                                                out, out_stride, active));
 }
 

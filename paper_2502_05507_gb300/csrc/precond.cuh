@@ -23,16 +23,17 @@ namespace bae {
 
 constexpr int MAXR = 32;   // members of a neighbourhood block, at most (one per lane of a warp)
 constexpr int NB_R = 2;    // the neighbourhood: offsets up to NB_R per axis
+static_assert(MAXR == 32, "a row's slots map onto the lanes of a warp (the fused Arnoldi step relies on it)");
 constexpr int NEAR_TN = 8;  // the blocks use G_s at offsets [0, NEAR_TN)^3 (up to 2 NB_R + 2 per axis)
 constexpr int NEAR_TAB = NEAR_TN * (NEAR_TN + 1) * (NEAR_TN + 2) / 6;   // sorted-table length
 
 struct Precond {
     bool built = false;
-    cudaStream_t stream = nullptr;
+    bool pending = false;          // built on another stream; the owner's stream has not waited yet
+    cudaStream_t stream = nullptr; // owner's stream (frees)
     long long n = 0;
-    // row r of M^{-1}: len[r] slots, slot q at col[q * n + r], val[q * n + r]
-    // (slot-major: consecutive rows are adjacent in each slot)
-    int* len = nullptr;
+    // row r of M^{-1}: slot q at col[r * MAXR + q], val[r * MAXR + q] (unused
+    // slots: column r, value 0)
     int* col = nullptr;
     float* val = nullptr;
     void release();
@@ -46,7 +47,9 @@ struct Precond {
 // float64, so the preconditioned system is unchanged).
 // near: G_s on the sorted offsets below NEAR_TN (lgf_table(NEAR_TN, s)),
 // device; computed here when null.
-void build_precond(const Geometry& g, double s, const double* near, Precond& out);
+// Runs on stream `on` (which must already be ordered after the geometry's
+// build); the arrays are freed on the geometry's stream.
+void build_precond(const Geometry& g, double s, const double* near, Precond& out, cudaStream_t on);
 
 // out[b] = M^{-1} in[b] with in[b] at in + b in_stride (+ row[b] row_stride
 // when row is not null, device), out[b] at out + b out_stride, for items
