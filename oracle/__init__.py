@@ -22,6 +22,9 @@ potentials and lattice Green's function in 3D"):
   fd.py          the discrete problem assembled as a sparse finite-difference
                  system (eq. [discrete] plus the closure rows), solved directly
   solve.py       Algorithm 1 end to end (double or single layer)
+  direct.py      the direct formulation: unknown u on gamma, difference
+                 potentials P w = G_h[chi_{M-} L_h w] (eqs. [dp], [bep],
+                 [direct_sys], [discrete_green])
 
 Equations are cited by their LaTeX labels in brackets, e.g. eq. [lgf].
 Parity status per function is listed in each module header.
