@@ -546,6 +546,49 @@ def run_star256(args):
             "table": rows}
 
 
+def run_direct128(args):
+    """The torus N=128 workload (kappa^2 = 10, tol 1e-10, mixed precision)
+    with the direct formulation (unknown u on gamma = gamma- u gamma+,
+    difference potentials), beside the double layer: solves/s, iterations,
+    and the agreement of the two solutions on N+ (the same discrete problem)."""
+    import torch
+    import workloads as W
+    from paper_2502_05507_gb300 import Context, Problem
+    ctx = Context(0)
+    torch.cuda.set_stream(ctx.stream)
+    P = W.torus_helmholtz(128, kappa2=10.0)
+    phi, f = _problem_inputs(P, torch, 0)
+    rows, us = [], {}
+    for layer in ("direct", "double"):
+        pr0 = Problem(ctx, phi, P.grid.h, P.grid.origin, P.kappa2, layer)
+        g = torch.from_numpy(P.g_at(pr0.boundary_points())).cuda()
+        n_unk = pr0.n_unknowns
+        pr0.close()
+
+        def step():
+            pr = Problem(ctx, phi, P.grid.h, P.grid.origin, P.kappa2, layer)
+            out = pr.solve(f, g, tol=TOL, precision="mixed", max_iter=2000)
+            pr.close()
+            return out
+        for _ in range(max(1, args.warmup)):
+            step()
+        times = []
+        for _ in range(max(1, args.steps)):
+            (q, u, st), dt = _timed(step, torch)
+            times.append(dt)
+        us[layer] = u.cpu().numpy()
+        rows.append({"layer": layer, "unknowns": n_unk, "iterations": st["iterations"],
+                     "refinements": st["refinements"], "solves_per_s": 1.0 / float(np.median(times)),
+                     "ms_p50": 1e3 * float(np.median(times)), "rel_residual": st["rel_residual"]})
+    m = P.phi < 0
+    diff = float(np.max(np.abs(us["direct"] - us["double"])) / np.max(np.abs(us["double"][m])))
+    ctx.close()
+    return {"metric": METRIC, "value": rows[0]["solves_per_s"], "unit": UNIT, "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f32 conv + df64 refinement",
+            "config": {"workload": "torus R=0.5 r=0.2, kappa^2=10, N=128, direct formulation (eq. direct_sys)"},
+            "table": rows, "rel_diff_direct_vs_double_on_grid": diff}
+
+
 def run_serving(args):
     """Serving trace: requests with N in {32,64,128,256}, kappa^2 in {0,10},
     random spheres/ellipsoids/tori, u = exp(a.x); Poisson arrivals at 0.8x
@@ -605,7 +648,7 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--workload", default="torus128",
-                    choices=["torus128", "sphere32", "batched64", "star256", "serving"])
+                    choices=["torus128", "sphere32", "batched64", "star256", "serving", "direct128"])
     ap.add_argument("--requests", type=int, default=2000, help="serving: number of requests")
     ap.add_argument("--nrhs", type=int, default=64, help="batched64: right-hand sides (at most 64)")
     ap.add_argument("--slots", type=int, default=6, help="serving: concurrent slots")
@@ -622,7 +665,7 @@ def main():
         return
     import torch
     extra = {"sphere32": run_sphere32, "batched64": run_batched64, "star256": run_star256,
-             "serving": run_serving}
+             "serving": run_serving, "direct128": run_direct128}
     if args.workload in extra:
         if rank == 0:
             print(json.dumps(extra[args.workload](args)))

@@ -48,6 +48,10 @@ extern "C" {
 /* layer type of the indirect formulation (Section 3.2) */
 #define BAE_LAYER_DOUBLE 0     /* D(m,n), eq. [double_potential] (default)     */
 #define BAE_LAYER_SINGLE 1     /* S(m,n) = G(m-n), eq. [single_potential]      */
+#define BAE_LAYER_DIRECT 2     /* direct formulation: the unknown is u on
+                                  gamma = gamma- then gamma+ (n_gm + n_gp values),
+                                  difference potentials G_h[chi_{M-} L_h u]
+                                  (eqs. [dp], [bep], [direct_sys])              */
 
 /* arithmetic of the potential apply */
 #define BAE_FP64  0            /* every step in float64                        */
@@ -194,9 +198,19 @@ int bae_problem_create(bae_ctx* ctx, int N, double h, const double origin[3],
 
 void bae_problem_destroy(bae_problem* prob);
 
-/* |gamma-| (unknowns of the boundary system), |gamma+|, |M+|. Any pointer
- * may be NULL. Host-side, no device work. */
+/* |gamma-| (the boundary points, and the unknowns of the layer
+ * formulations), |gamma+|, |M+|. Any pointer may be NULL. Host-side, no
+ * device work. */
 int bae_problem_sizes(const bae_problem* prob, int64_t* n_gm, int64_t* n_gp, int64_t* n_mp);
+
+/* Unknowns of the boundary system: n_gm for the single and double layer,
+ * n_gm + n_gp for BAE_LAYER_DIRECT (u on gamma-, then on gamma+). This is
+ * the length of every density q below. Host-side, no device work. */
+int bae_problem_unknowns(const bae_problem* prob, int64_t* n);
+
+/* gp_idx[n_gp]: linear indices of gamma+ (lexicographic; the order of the
+ * gamma+ unknowns of the direct formulation). Host or device pointer. */
+int bae_gamma_plus(const bae_problem* prob, int32_t* gp_idx);
 
 /* The x-planes [*lo, *hi) that hold every source (gamma-, the D-nodes, M+)
  * and every node a solve reads back (gamma-, the closure partners, M+):
@@ -223,13 +237,19 @@ int bae_classification(const bae_problem* prob, uint8_t* flags, int32_t* gm_idx,
 /* v = K q on the whole N^3 grid, K the problem's layer potential
  * (Section 3.2: single eq. [single_potential], double eq. [double_potential]),
  * i.e. the source stencil rho = B q, the free-space convolution with G_s by
- * a zero-padded (2N)^3 FFT, v(m) = sum_x G_s(m-x) rho(x).
- * q: n_gm doubles; v: N^3 doubles. precision BAE_FP64 or BAE_FP32. */
+ * a zero-padded (2N)^3 FFT, v(m) = sum_x G_s(m-x) rho(x). For
+ * BAE_LAYER_DIRECT, q is u on gamma and v the difference potential
+ * P q = G_s * [chi_{M-} ((6 + s) q - sum of the six neighbours of q)]
+ * (eq. [dp] with G_h = h^2 G_s, s = kappa2 h^2).
+ * q: bae_problem_unknowns() doubles; v: N^3 doubles. precision BAE_FP64 or
+ * BAE_FP32. */
 int bae_potential_apply(bae_problem* prob, int precision, const double* q, double* v);
 
 /* The boundary operator of eq. [double_bae] (or its single-layer analogue):
  * (A q)_m = t(m) (Kq)(m) + (1 - t(m)) (Kq)(p(m)) for every gamma- node m.
- * q, Aq: n_gm doubles. precision BAE_FP64 or BAE_FP32. */
+ * BAE_LAYER_DIRECT (eq. [direct_sys] with eq. [inhom]): the closure rows
+ * t(m) q(m) + (1 - t(m)) q(p(m)) on gamma-, then q(p) - (P q)(p) on gamma+.
+ * q, Aq: bae_problem_unknowns() doubles. precision BAE_FP64 or BAE_FP32. */
 int bae_boundary_apply(bae_problem* prob, int precision, const double* q, double* Aq);
 
 /* The same potential apply as bae_potential_apply, for callers that must not
@@ -240,7 +260,7 @@ int bae_boundary_apply(bae_problem* prob, int precision, const double* q, double
  * file-scope device array of 8 MiB that every GPU the library touches holds
  * until the process exits. The paper has no counterpart; this is a
  * deployment variant of the hot path.
- *  - q (n_gm doubles) and v (N^3 doubles) must be device memory of the
+ *  - q (bae_problem_unknowns() doubles) and v (N^3 doubles) must be device memory of the
  *    problem's device; host pointers are rejected (BAE_ERR_INVALID_ARG),
  *    since staging them would need allocations.
  *  - Size limit: float32 up to N = 64, float64 up to N = 32; larger problems
@@ -266,8 +286,12 @@ int bae_particular(bae_problem* prob, int precision, const double* f, double* up
 /* Solves the BAE of eq. [double_bae] (or single layer) by unrestarted-
  * per-cycle GMRES with zero initial guess and no preconditioner:
  *   b = g - Phi u_p,  A q = b,  u = u_p + K q.
+ * BAE_LAYER_DIRECT solves eq. [direct_sys] with eq. [inhom] for q = u on
+ * gamma: b = [g; u_p on gamma+], u = u_p + P q on M+ and q on gamma-
+ * (eq. [discrete_green]); opts->precond is ignored there.
  * f: N^3 doubles (paper sign, -Lap u + kappa2 u = f); g: n_gm doubles, the
- * Dirichlet data at bae_boundary_points(). Outputs: density q (n_gm doubles)
+ * Dirichlet data at bae_boundary_points(). Outputs: density q
+ * (bae_problem_unknowns() doubles)
  * and u (N^3 doubles: the discrete solution on N+ = M+ u gamma-, 0 elsewhere);
  * either may be NULL. opts may be NULL (defaults); stats may be NULL.
  * BAE_ERR_NOT_CONVERGED leaves valid outputs and stats. */
@@ -314,7 +338,7 @@ typedef struct bae_request {
 
 typedef struct bae_result {
     int status;                  /* BAE_OK or the solve's error code            */
-    int64_t n_gm;                /* length of the density                       */
+    int64_t n_gm;                /* length of the density (bae_problem_unknowns) */
     bae_stats stats;
     double t_submit, t_admit, t_done;  /* seconds on the server's steady clock   */
 } bae_result;
@@ -328,8 +352,8 @@ int bae_server_submit(bae_server* srv, const bae_request* req, int64_t* ticket);
 /* Waits up to timeout_ms (0: no wait, < 0: forever) for the request; returns
  * BAE_OK with *out filled when it is done, BAE_PENDING otherwise. */
 int bae_server_poll(bae_server* srv, int64_t ticket, int timeout_ms, bae_result* out);
-/* Copies the finished request's density (n_gm doubles) to out (host or
- * device, capacity doubles). */
+/* Copies the finished request's density (bae_problem_unknowns() doubles of
+ * its problem) to out (host or device, capacity doubles). */
 int bae_server_density(bae_server* srv, int64_t ticket, double* out, int64_t capacity);
 /* Forgets a finished request. */
 int bae_server_release(bae_server* srv, int64_t ticket);

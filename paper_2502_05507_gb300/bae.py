@@ -17,9 +17,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libbae.so")
 
 OK, ERR_INVALID_ARG, ERR_GEOMETRY, ERR_OOM, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_CUDA = range(7)
-LAYER_DOUBLE, LAYER_SINGLE = 0, 1
+LAYER_DOUBLE, LAYER_SINGLE, LAYER_DIRECT = 0, 1, 2
 FP64, MIXED, FP32, DF64 = 0, 1, 2, 3
-_LAYERS = {"double": LAYER_DOUBLE, "single": LAYER_SINGLE}
+_LAYERS = {"double": LAYER_DOUBLE, "single": LAYER_SINGLE, "direct": LAYER_DIRECT}
 _PREC = {"fp64": FP64, "mixed": MIXED, "fp32": FP32, "df64": DF64}
 
 
@@ -96,6 +96,8 @@ def lib():
             "bae_problem_create": (_I, [_P, _I, _D, _P, _P, _D, _I, _P]),
             "bae_problem_destroy": (None, [_P]),
             "bae_problem_sizes": (_I, [_P, _P, _P, _P]),
+            "bae_problem_unknowns": (_I, [_P, _P]),
+            "bae_gamma_plus": (_I, [_P, _P]),
             "bae_problem_plane_range": (_I, [_P, _P, _P]),
             "bae_boundary_points": (_I, [_P, _P]),
             "bae_classification": (_I, [_P, _P, _P, _P, _P]),
@@ -124,7 +126,7 @@ def lib():
 EXPORTED = ["bae_version", "bae_last_error", "bae_default_options", "bae_launch_count", "bae_set_conv_schedule", "bae_profile_start",
             "bae_profile_stop", "bae_ctx_create", "bae_ctx_destroy",
             "bae_lgf_table", "bae_lgf_spectrum", "bae_problem_create", "bae_problem_destroy",
-            "bae_problem_sizes", "bae_problem_plane_range", "bae_boundary_points", "bae_classification", "bae_potential_apply",
+            "bae_problem_sizes", "bae_problem_unknowns", "bae_gamma_plus", "bae_problem_plane_range", "bae_boundary_points", "bae_classification", "bae_potential_apply",
             "bae_potential_apply_noalloc",
             "bae_boundary_apply", "bae_particular", "bae_solve", "bae_solve_batched", "bae_server_create",
             "bae_server_submit", "bae_server_poll", "bae_server_density", "bae_server_release", "bae_server_clock",
@@ -266,6 +268,8 @@ class Problem:
         a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
         _check(lib().bae_problem_sizes(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
         self.n_gm, self.n_gp, self.n_mp = a.value, b.value, c.value
+        _check(lib().bae_problem_unknowns(self._h, ctypes.byref(a)))
+        self.n_unknowns = a.value   # n_gm, or n_gm + n_gp for the direct formulation
 
     def close(self):
         if self._h:
@@ -298,6 +302,12 @@ class Problem:
         _check(lib().bae_classification(self._h, _ptr(flags), _ptr(gm), _ptr(partner), _ptr(t)))
         return dict(flags=flags, gm=gm, partner=partner, t=t)
 
+    def gamma_plus(self):
+        """Linear indices of gamma+ (lexicographic)."""
+        gp = np.empty(self.n_gp, np.int32)
+        _check(lib().bae_gamma_plus(self._h, _ptr(gp)))
+        return gp
+
     def potential_apply(self, q, precision="fp64", out=None):
         q = _as_f64(q)
         out = _new((self.N,) * 3, np.float64, q) if out is None else out
@@ -312,7 +322,7 @@ class Problem:
 
     def boundary_apply(self, q, precision="fp64", out=None):
         q = _as_f64(q)
-        out = _new((self.n_gm,), np.float64, q) if out is None else out
+        out = _new((self.n_unknowns,), np.float64, q) if out is None else out
         _check(lib().bae_boundary_apply(self._h, _PREC[precision], _ptr(q), _ptr(out)))
         return out
 
@@ -350,7 +360,7 @@ class Problem:
         torch CUDA tensors or numpy arrays; outputs follow f's kind."""
         f = _as_f64(f)
         g = _as_f64(g)
-        density = _new((self.n_gm,), np.float64, f) if density is None else density
+        density = _new((self.n_unknowns,), np.float64, f) if density is None else density
         u = _new((self.N,) * 3, np.float64, f) if u is None else u
         st = Stats()
         o = self._opts(tol, precision, max_iter, restart, max_refine, inner_tol, use_graphs, residual_precision,
@@ -366,7 +376,7 @@ class Problem:
         f = _as_f64(f)
         g = _as_f64(g)
         nrhs = int(f.shape[0])
-        density = _new((nrhs, self.n_gm), np.float64, f) if density is None else density
+        density = _new((nrhs, self.n_unknowns), np.float64, f) if density is None else density
         u = _new((nrhs,) + (self.N,) * 3, np.float64, f) if u is None else u
         st = (Stats * nrhs)()
         o = self._opts(tol, precision, max_iter, restart, max_refine, inner_tol, use_graphs, residual_precision,

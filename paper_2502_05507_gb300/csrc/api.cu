@@ -148,14 +148,17 @@ struct Workspace {
     Grow<unsigned long long> arnBar;
     Grow<double> in_f, in_g, out_q, out_u;    // staging of host arguments
     Grow<double> qpre, zpre;                  // M^{-1} y of the preconditioned inner solves
+    Grow<double> ydir64, bprime;              // direct formulation: operator rows, [g; 0]
+    Grow<float> ydir32;
     void set_stream(cudaStream_t st) {
         Grow<double>* ds[] = {&v64, &up, &vstage, &V, &w, &partial, &h, &hsave, &x, &r, &bvec, &tmp,
-                              &qstage, &n2, &in_f, &in_g, &out_q, &out_u, &qpre, &zpre};
+                              &qstage, &n2, &in_f, &in_g, &out_q, &out_u, &qpre, &zpre, &ydir64, &bprime};
         for (auto* d : ds) d->st = st;
         Grow<double>* ds2[] = {&arnH, &arnCS, &arnG, &arnY, &arnScal, &arnP};
         for (auto* d : ds2) d->st = st;
         A.st = B.st = st;
         v32.st = st;
+        ydir32.st = st;
         active.st = arnI.st = st;
         arnCtr.st = st;
         arnBar.st = st;
@@ -295,6 +298,11 @@ struct bae_problem {
     Precond pre;   // right preconditioner, built on the first mixed solve that asks for it
     std::shared_ptr<Spectrum> spec;
     double kappa2 = 0.0, s = 0.0;
+    // direct formulation: the Arnoldi gather reads the operator rows as they
+    // are (row r of the vector at index r, weight 1)
+    int* iota = nullptr;
+    double* ones = nullptr;
+    bool direct() const { return geo.layer == BAE_LAYER_DIRECT; }
     Workspace& ws() { return ctx->ws; }
     long long n3() const { return (long long)geo.N * geo.N * geo.N; }
 };
@@ -323,6 +331,7 @@ bool problem_view(const bae_problem* P, ProblemView& out) {
 namespace {
 
 long long n_gm(const bae_problem* P) { return P->geo.n_gm; }
+long long n_unk(const bae_problem* P) { return P->geo.n_unk; }
 
 // pruned: only the x-planes that hold sources or gathered / reconstructed
 // nodes are transformed (applies whose output is read at gamma-, the
@@ -370,7 +379,7 @@ out_t<T>* apply_potential(bae_problem* P, int nb, const double* q, bool pruned =
     ConvArgs<T> a = conv_args<T>(P, nb, pruned);
     a.mode = SRC_DENSITY;
     a.q = q;
-    a.q_stride = n_gm(P);
+    a.q_stride = n_unk(P);
     a.rec = P->geo.recipe();
     a.v = vbuf<T>(P, nb);
     conv_apply<T>(a, P->ctx->stream);
@@ -397,7 +406,7 @@ out_t<T>* apply_combined(bae_problem* P, int nb, const double* q, const double* 
     ConvArgs<T> a = conv_args<T>(P, nb, pruned);
     a.mode = SRC_DENSITY;
     a.q = q;
-    a.q_stride = n_gm(P);
+    a.q_stride = n_unk(P);
     a.rec = P->geo.recipe();
     a.f = f;
     a.flags = P->geo.flags;
@@ -411,8 +420,12 @@ out_t<T>* apply_combined(bae_problem* P, int nb, const double* q, const double* 
 template <typename T>
 void boundary_apply(bae_problem* P, int nb, const double* q, double* Aq) {
     out_t<T>* v = apply_potential<T>(P, nb, q, true);
-    closure_gather<out_t<T>>(v, P->n3(), P->geo.gm, P->geo.partner, P->geo.t, (int)n_gm(P), nb, Aq, n_gm(P),
-                      P->ctx->stream);
+    if (P->direct())
+        direct_rows<out_t<T>, double>(v, P->n3(), q, n_unk(P), nullptr, 0, P->geo.gp, P->geo.partner_u, P->geo.t,
+                                      n_gm(P), n_unk(P), nb, nullptr, Aq, n_unk(P), P->ctx->stream);
+    else
+        closure_gather<out_t<T>>(v, P->n3(), P->geo.gm, P->geo.partner, P->geo.t, (int)n_gm(P), nb, Aq, n_gm(P),
+                                 P->ctx->stream);
 }
 
 void boundary_apply_prec(bae_problem* P, int prec, int nb, const double* q, double* Aq) {
@@ -469,8 +482,12 @@ template <typename T>
 void apply_rows(bae_problem* P, int nb, const double* q, long long q_stride, const int* q_row,
                 long long q_row_stride, const int* active, double* out) {
     out_t<T>* v = potential_rows<T>(P, nb, q, q_stride, q_row, q_row_stride, active);
-    closure_gather<out_t<T>>(v, P->n3(), P->geo.gm, P->geo.partner, P->geo.t, (int)n_gm(P), nb, out, n_gm(P),
-                      P->ctx->stream, active);
+    if (P->direct())
+        direct_rows<out_t<T>, double>(v, P->n3(), q, q_stride, q_row, q_row_stride, P->geo.gp, P->geo.partner_u,
+                                      P->geo.t, n_gm(P), n_unk(P), nb, active, out, n_unk(P), P->ctx->stream);
+    else
+        closure_gather<out_t<T>>(v, P->n3(), P->geo.gm, P->geo.partner, P->geo.t, (int)n_gm(P), nb, out, n_gm(P),
+                                 P->ctx->stream, active);
 }
 
 void apply_rows_prec(bae_problem* P, int prec, int nb, const double* q, long long q_stride, const int* q_row,
@@ -492,7 +509,7 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
            bool use_graph, bool pre = false) {
     cudaStream_t st = P->ctx->stream;
     Workspace& ws = P->ws();
-    const int n = (int)n_gm(P);
+    const int n = (int)n_unk(P);
     const int m = std::max(1, std::min(restart, max_iter));
     Arnoldi a;
     a.n = n;
@@ -561,10 +578,14 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
     // one step: v = K V[j] for the iterating RHS, then the Arnoldi passes
     // (whose first pass gathers w = Phi v)
     a.v_f32 = prec == BAE_FP32;
-    a.v_stride = P->n3();
-    a.gm = P->geo.gm;
-    a.partner = P->geo.partner;
-    a.t = P->geo.t;
+    const bool direct = P->direct();
+    a.v_stride = direct ? n : P->n3();
+    a.gm = direct ? P->iota : P->geo.gm;
+    a.partner = direct ? P->iota : P->geo.partner;
+    a.t = direct ? P->ones : P->geo.t;
+    // direct formulation: the step's operator rows, in the apply's precision
+    float* y32 = direct && prec == BAE_FP32 ? ws.ydir32.need((long long)nb * n) : nullptr;
+    double* y64 = direct && prec != BAE_FP32 ? ws.ydir64.need((long long)nb * n) : nullptr;
     // right preconditioning: the step applies A to z = M^{-1} V[j]; the
     // fused step forms the next z itself (after arn_init: z of V[0] here)
     double* zpre = pre ? ws.zpre.need((long long)nb * n) : nullptr;
@@ -587,6 +608,17 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
         if (prec == BAE_FP32) a.v = potential_rows<float>(P, nb, q, qs, qrow, n, a.flag);
         else if (prec == BAE_DF64) a.v = potential_rows<dsf>(P, nb, q, qs, qrow, n, a.flag);
         else a.v = potential_rows<double>(P, nb, q, qs, qrow, n, a.flag);
+        if (direct) {
+            if (y32) {
+                direct_rows<float, float>(static_cast<const float*>(a.v), P->n3(), q, qs, qrow, n, P->geo.gp,
+                                          P->geo.partner_u, P->geo.t, n_gm(P), n, nb, a.flag, y32, n, st);
+                a.v = y32;
+            } else {
+                direct_rows<double, double>(static_cast<const double*>(a.v), P->n3(), q, qs, qrow, n, P->geo.gp,
+                                            P->geo.partner_u, P->geo.t, n_gm(P), n, nb, a.flag, y64, n, st);
+                a.v = y64;
+            }
+        }
         arn_step(a, st);
     };
     // size every buffer and set every kernel attribute the step needs before
@@ -732,12 +764,14 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
     cudaStream_t st = P->ctx->stream;
     BAE_CUDA(cudaEventRecord(P->ctx->ev0, st));
     const long long n3 = P->n3();
-    const int n = (int)n_gm(P);
+    const int ng = (int)n_gm(P);    // gamma- nodes: boundary points and g
+    const int n = (int)n_unk(P);    // unknowns (ng, or ng + |gamma+| for the direct formulation)
+    const bool direct = P->direct();
     const double h = P->geo.h;
     // the right preconditioner of the inner solves (restricted additive
     // Schwarz) is built on the side stream while this one checks the inputs
     // and forms the first right-hand side; the inner solves wait for it
-    const bool any_pre = o.precision == BAE_MIXED && o.precond != 0;
+    const bool any_pre = o.precision == BAE_MIXED && o.precond != 0 && !direct;
     if (any_pre && !P->pre.built) {
         BAE_CUDA(cudaEventRecord(P->ctx->fork_ev, st));
         BAE_CUDA(cudaStreamWaitEvent(P->ctx->side, P->ctx->fork_ev, 0));
@@ -755,8 +789,8 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
         d_f = p;
     }
     if (!is_device_ptr(g)) {
-        double* p = P->ws().in_g.need((long long)nb * n);
-        BAE_CUDA(cudaMemcpyAsync(p, g, (size_t)nb * n * sizeof(double), cudaMemcpyHostToDevice, st));
+        double* p = P->ws().in_g.need((long long)nb * ng);
+        BAE_CUDA(cudaMemcpyAsync(p, g, (size_t)nb * ng * sizeof(double), cudaMemcpyHostToDevice, st));
         d_g = p;
     }
     {   // f on M+ and g must be finite
@@ -764,7 +798,7 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
         int bad = 0;
         BAE_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(int), st));
         kr_nonfinite(d_f, (long long)nb * n3, P->geo.flags, n3, d_bad, st);
-        kr_nonfinite(d_g, (long long)nb * n, nullptr, 1, d_bad, st);
+        kr_nonfinite(d_g, (long long)nb * ng, nullptr, 1, d_bad, st);
         BAE_CUDA(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
         BAE_CUDA(cudaStreamSynchronize(st));
         BAE_REQUIRE(!bad, BAE_ERR_INVALID_ARG, "f (on M+) or g contains non-finite values");
@@ -777,30 +811,51 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
     // it is a float32 apply: each float64-accurate residual below convolves
     // the layer and volume sources together, r = g - Phi (K q + u_p), and u
     // is that sum on N+. Otherwise u_p is float64 and kept for u.
+    //
+    // Direct formulation (eq. [direct_sys] with eq. [inhom]): the unknown
+    // is u on gamma; with b' = [g; 0] and rows(w, x) = [closure of x; x -
+    // w on gamma+], b = [g; u_p on gamma+] = b' - rows(u_p, 0), and every
+    // residual is b - A x = b' - rows(P x + u_p, x) (one combined apply); u
+    // is P x + u_p on M+ and x on gamma-.
     const bool mixed = o.precision == BAE_MIXED;
     double* bvec = P->ws().x.need((long long)nb * n * 3);   // [b | q | r] blocks
     double* q = bvec + (long long)nb * n;
     double* res = q + (long long)nb * n;
     double* up = nullptr;
+    BAE_CUDA(cudaMemsetAsync(q, 0, (size_t)nb * n * sizeof(double), st));
+    double* bp = nullptr;
+    if (direct) {
+        bp = P->ws().bprime.need((long long)nb * n);
+        BAE_CUDA(cudaMemsetAsync(bp, 0, (size_t)nb * n * sizeof(double), st));
+        BAE_CUDA(cudaMemcpy2DAsync(bp, (size_t)n * sizeof(double), d_g, (size_t)ng * sizeof(double),
+                                   (size_t)ng * sizeof(double), nb, cudaMemcpyDeviceToDevice, st));
+    }
     if (mixed) {
         const float* v = apply_volume<float>(P, nb, d_f, h * h, true);
-        closure_gather<float>(v, n3, P->geo.gm, P->geo.partner, P->geo.t, n, nb, res, n, st);
+        if (direct)
+            direct_rows<float, double>(v, n3, q, n, nullptr, 0, P->geo.gp, P->geo.partner_u, P->geo.t, ng, n, nb,
+                                       nullptr, res, n, st);
+        else
+            closure_gather<float>(v, n3, P->geo.gm, P->geo.partner, P->geo.t, n, nb, res, n, st);
         for (auto& s : st_local) s.applies_fp32 += 1;
     } else {
         up = P->ws().up.need((long long)nb * n3);
         double* v = apply_volume64(P, hp, nb, d_f, h * h, true);
         BAE_CUDA(cudaMemcpyAsync(up, v, (size_t)nb * n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
         for (auto& s : st_local) s.applies_fp64 += 1;
-        closure_gather<double>(up, n3, P->geo.gm, P->geo.partner, P->geo.t, n, nb, res, n, st);
+        if (direct)
+            direct_rows<double, double>(up, n3, q, n, nullptr, 0, P->geo.gp, P->geo.partner_u, P->geo.t, ng, n, nb,
+                                        nullptr, res, n, st);
+        else
+            closure_gather<double>(up, n3, P->geo.gm, P->geo.partner, P->geo.t, n, nb, res, n, st);
     }
     {
         std::vector<int> all(nb);
         for (int b = 0; b < nb; ++b) all[b] = b;
         int* d_act = P->ws().active.need(nb);
         BAE_CUDA(cudaMemcpyAsync(d_act, all.data(), nb * sizeof(int), cudaMemcpyHostToDevice, st));
-        kr_sub(d_g, res, d_act, nb, n, bvec, st);
+        kr_sub(direct ? bp : d_g, res, d_act, nb, n, bvec, st);
     }
-    BAE_CUDA(cudaMemsetAsync(q, 0, (size_t)nb * n * sizeof(double), st));
 
     // ||b||
     std::vector<double> bn2(nb), rn2(nb);
@@ -825,10 +880,15 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
         int* d_all = P->ws().active.need(nb);
         BAE_CUDA(cudaMemcpyAsync(d_all, all.data(), nb * sizeof(int), cudaMemcpyHostToDevice, st));
         double* tmp = P->ws().tmp.need((long long)nb * n);
-        double* v = mixed ? apply_combined64(P, hp, nb, q, d_f, h * h, true) : apply_potential64(P, hp, nb, q, true);
-        closure_gather<double>(v, n3, P->geo.gm, P->geo.partner, P->geo.t, n, nb, tmp, n, st);
+        const bool comb = mixed || direct;
+        double* v = comb ? apply_combined64(P, hp, nb, q, d_f, h * h, true) : apply_potential64(P, hp, nb, q, true);
+        if (direct)
+            direct_rows<double, double>(v, n3, q, n, nullptr, 0, P->geo.gp, P->geo.partner_u, P->geo.t, ng, n, nb,
+                                        nullptr, tmp, n, st);
+        else
+            closure_gather<double>(v, n3, P->geo.gm, P->geo.partner, P->geo.t, n, nb, tmp, n, st);
         for (auto& s : st_local) s.applies_fp64 += 1;
-        kr_sub(mixed ? d_g : bvec, tmp, d_all, nb, n, res, st);
+        kr_sub(direct ? bp : (mixed ? d_g : bvec), tmp, d_all, nb, n, res, st);
         kr_norm2(res, d_all, nb, n, n2 + nb, krylov_chunks(n), n2, st);
         BAE_CUDA(cudaMemcpyAsync(rn2.data(), n2, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
         BAE_CUDA(cudaStreamSynchronize(st));
@@ -867,7 +927,7 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
             if (act.empty() || iters_left <= 0) break;
             // every refinement step (precond 1) or the steps after the first
             // (precond 2)
-            const bool use_pre = o.precond == 1 || (o.precond == 2 && step > 0);
+            const bool use_pre = any_pre && (o.precond == 1 || (o.precond == 2 && step > 0));
             std::vector<RhsState> Si(nb);
             for (int b : act) {
                 // reduce the residual by inner_tol; when that lands within ten
@@ -909,7 +969,8 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
     bool u_host = u && !is_device_ptr(u);
     if (u) {
         double* du = u_host ? P->ws().out_u.need((long long)nb * n3) : u;
-        volume_combine<double>(v_last, up, P->geo.flags, n3, nb, du, st);
+        volume_combine<double>(v_last, direct ? nullptr : up, P->geo.flags, n3, nb, du, st);
+        if (direct) scatter_gm(q, n, P->geo.gm, ng, nb, du, n3, st);   // u on gamma- is the unknown there
         if (u_host) BAE_CUDA(cudaMemcpyAsync(u, du, (size_t)nb * n3 * sizeof(double), cudaMemcpyDeviceToHost, st));
     }
     if (density) {
@@ -1172,7 +1233,8 @@ int bae_problem_create(bae_ctx* ctx, int N, double h, const double origin[3], co
         BAE_REQUIRE(std::isfinite(kappa2) && kappa2 >= 0, BAE_ERR_INVALID_ARG, "kappa2 must be finite and >= 0");
         BAE_REQUIRE(std::isfinite(origin[0]) && std::isfinite(origin[1]) && std::isfinite(origin[2]),
                     BAE_ERR_INVALID_ARG, "origin must be finite");
-        BAE_REQUIRE(layer == BAE_LAYER_DOUBLE || layer == BAE_LAYER_SINGLE, BAE_ERR_INVALID_ARG, "unknown layer");
+        BAE_REQUIRE(layer == BAE_LAYER_DOUBLE || layer == BAE_LAYER_SINGLE || layer == BAE_LAYER_DIRECT,
+                    BAE_ERR_INVALID_ARG, "unknown layer");
         auto P = std::make_unique<bae_problem>();
         P->ctx = ctx;
         P->kappa2 = kappa2;
@@ -1180,13 +1242,24 @@ int bae_problem_create(bae_ctx* ctx, int N, double h, const double origin[3], co
         const long long n3 = (long long)N * N * N;
         const double* d_phi = device_in(ctx->ws.in_f, phi, n3, ctx->stream);
         try {
-            build_geometry(d_phi, N, h, origin, layer, P->geo, ctx->stream);
+            build_geometry(d_phi, N, h, origin, layer, P->s, P->geo, ctx->stream);
         } catch (...) {
             P->geo.release();
             throw;
         }
         P->spec = ctx->spectrum(N, P->s);
         ctx->twiddles(2 * N);   // built here so that later applies allocate nothing
+        if (P->direct()) {
+            const long long nu = P->geo.n_unk;
+            std::vector<int> io(nu);
+            std::vector<double> on(nu, 1.0);
+            for (long long r = 0; r < nu; ++r) io[r] = (int)r;
+            P->iota = dev_alloc_n<int>(nu, ctx->stream);
+            P->ones = dev_alloc_n<double>(nu, ctx->stream);
+            BAE_CUDA(cudaMemcpyAsync(P->iota, io.data(), nu * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+            BAE_CUDA(cudaMemcpyAsync(P->ones, on.data(), nu * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+            BAE_CUDA(cudaStreamSynchronize(ctx->stream));
+        }
         *out = P.release();
         return BAE_OK;
     });
@@ -1198,6 +1271,8 @@ void bae_problem_destroy(bae_problem* P) {
     if (P->pre.pending) cudaStreamSynchronize(P->ctx->side);   // a build the main stream never waited for
     cudaStreamSynchronize(P->ctx->stream);
     P->pre.release();
+    if (P->iota) dev_free(P->iota, P->ctx->stream);
+    if (P->ones) dev_free(P->ones, P->ctx->stream);
     P->geo.release();
     delete P;
 }
@@ -1246,6 +1321,25 @@ int bae_classification(const bae_problem* P, uint8_t* flags, int32_t* gm_idx, in
     });
 }
 
+int bae_problem_unknowns(const bae_problem* P, int64_t* n) {
+    return guarded([&]() -> int {
+        BAE_REQUIRE(P && n, BAE_ERR_INVALID_ARG, "null argument");
+        *n = P->geo.n_unk;
+        return BAE_OK;
+    });
+}
+
+int bae_gamma_plus(const bae_problem* P, int32_t* gp_idx) {
+    return guarded([&]() -> int {
+        BAE_REQUIRE(P && gp_idx, BAE_ERR_INVALID_ARG, "null argument");
+        check_device(P->ctx);
+        cudaStream_t st = P->ctx->stream;
+        copy_out(gp_idx, P->geo.gp, P->geo.n_gp, st);
+        BAE_CUDA(cudaStreamSynchronize(st));
+        return BAE_OK;
+    });
+}
+
 int bae_potential_apply(bae_problem* P, int precision, const double* q, double* v) {
     return guarded([&]() -> int {
         BAE_REQUIRE(P && q && v, BAE_ERR_INVALID_ARG, "null argument");
@@ -1253,7 +1347,7 @@ int bae_potential_apply(bae_problem* P, int precision, const double* q, double* 
                     "precision must be BAE_FP64, BAE_FP32 or BAE_DF64");
         check_device(P->ctx);
         cudaStream_t st = P->ctx->stream;
-        const double* dq = device_in(P->ws().in_g, q, P->geo.n_gm, st);
+        const double* dq = device_in(P->ws().in_g, q, P->geo.n_unk, st);
         const long long n3 = P->n3();
         const bool vh = !is_device_ptr(v);
         double* dv = vh ? P->ws().out_u.need(n3) : v;
@@ -1277,7 +1371,7 @@ int bae_boundary_apply(bae_problem* P, int precision, const double* q, double* A
                     "precision must be BAE_FP64, BAE_FP32 or BAE_DF64");
         check_device(P->ctx);
         cudaStream_t st = P->ctx->stream;
-        const long long n = P->geo.n_gm;
+        const long long n = P->geo.n_unk;
         const double* dq = device_in(P->ws().in_g, q, n, st);
         const bool oh = !is_device_ptr(Aq);
         double* dA = oh ? P->ws().out_q.need(n) : Aq;

@@ -54,14 +54,14 @@ __device__ int block_exclusive_scan(int v, int* s_warp) {
 constexpr int LINE_T = 128;
 
 // slots of the small device record the host reads once
-enum { I_ERR = 0, I_GP, I_MP, I_FIRST, I_LAST, I_NGM, I_NSRC, I_NTERM, I_COUNT };
+enum { I_ERR = 0, I_GP, I_MP, I_FIRST, I_LAST, I_NGM, I_NSRC, I_NTERM, I_NGPL, I_COUNT };
 
 __device__ __forceinline__ bool in_grid(int i, int j, int k, int N) {
     return (unsigned)i < (unsigned)N && (unsigned)j < (unsigned)N && (unsigned)k < (unsigned)N;
 }
 
-// bits per node from phi: bit0 in M+ (phi < 0), bit1 an M+ neighbour (nodes
-// outside the box count as exterior)
+// bits per node from phi: bit0 in M+ (phi < 0), bit1 an M+ neighbour, bit2
+// a neighbour outside M+ (nodes outside the box count as exterior)
 __global__ void __launch_bounds__(LINE_T) k_nbits(const double* __restrict__ phi, int N, uint8_t* __restrict__ nb,
                                                  int* __restrict__ info) {
     const int line = blockIdx.x, i = line / N, j = line - i * N;
@@ -69,12 +69,13 @@ __global__ void __launch_bounds__(LINE_T) k_nbits(const double* __restrict__ phi
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
         const double p = phi[base + k];
         if (!isfinite(p)) atomicOr(info + I_ERR, 1);
-        bool h = false;
+        bool h = false, e = false;
         for (int d = 0; d < 6; ++d) {
             const int ii = i + c_dir[d][0], jj = j + c_dir[d][1], kk = k + c_dir[d][2];
             if (in_grid(ii, jj, kk, N) && phi[((long long)ii * N + jj) * N + kk] < 0.0) h = true;
+            else e = true;
         }
-        nb[base + k] = (uint8_t)((p < 0.0 ? 1 : 0) | (h ? 2 : 0));
+        nb[base + k] = (uint8_t)((p < 0.0 ? 1 : 0) | (h ? 2 : 0) | (e ? 4 : 0));
     }
 }
 
@@ -83,11 +84,14 @@ __global__ void __launch_bounds__(LINE_T) k_nbits(const double* __restrict__ phi
 // exterior neighbour (bit2), D-node = outside N+ = M+ and gamma-, next to a
 // gamma- node (bit3), and for gamma- nodes |D_n| = the neighbours outside
 // N+ (bits 4-6). Per line: the gamma- nodes, the sources (flags & src_mask)
-// and their stencil terms (1 per gamma- node, one per gamma- neighbour of a
-// D-node); gamma+ and M+ counts and the range of source planes go to info.
+// and their stencil terms (a D-node: one per gamma- neighbour; a gamma- node:
+// 1, or with `direct` 1 + its neighbours in gamma = gamma- u gamma+), the
+// gamma+ nodes; M+ and gamma+ totals and the range of source planes go to
+// info.
 __global__ void __launch_bounds__(LINE_T) k_flags_lines(const uint8_t* __restrict__ nb, int N, int src_mask,
-                                                       uint8_t* __restrict__ flags, int* __restrict__ cnt_gm,
-                                                       int* __restrict__ cnt_src, int* __restrict__ cnt_term,
+                                                       bool direct, uint8_t* __restrict__ flags,
+                                                       int* __restrict__ cnt_gm, int* __restrict__ cnt_src,
+                                                       int* __restrict__ cnt_term, int* __restrict__ cnt_gp,
                                                        int* __restrict__ info) {
     __shared__ int s_red[5][LINE_T / 32];
     const int line = blockIdx.x, i = line / N, j = line - i * N;
@@ -96,13 +100,14 @@ __global__ void __launch_bounds__(LINE_T) k_flags_lines(const uint8_t* __restric
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
         const int me = nb[base + k];
         bool out_nb = false;
-        int n_out = 0, n_gm = 0;
+        int n_out = 0, n_gm = 0, n_gam = 0;
         for (int d = 0; d < 6; ++d) {
             const int ii = i + c_dir[d][0], jj = j + c_dir[d][1], kk = k + c_dir[d][2];
             const int q = in_grid(ii, jj, kk, N) ? nb[((long long)ii * N + jj) * N + kk] : 0;
             if (!(q & 1)) out_nb = true;
             if (!(q & 3)) ++n_out;               // not in N+
             if (!(q & 1) && (q & 2)) ++n_gm;     // a gamma- node
+            if ((q & 1) ? (q & 4) : (q & 2)) ++n_gam;   // gamma+ or gamma-
         }
         const bool in = me & 1, gm = !in && (me & 2);
         const bool gp = in && out_nb;
@@ -114,7 +119,7 @@ __global__ void __launch_bounds__(LINE_T) k_flags_lines(const uint8_t* __restric
         const bool src = (f & src_mask) != 0;
         c[0] += gm;
         c[1] += src;
-        c[2] += src ? (gm ? 1 : n_gm) : 0;
+        c[2] += src ? (gm ? (direct ? 1 + n_gam : 1) : n_gm) : 0;
         c[3] += gp;
         c[4] += in;
     }
@@ -132,6 +137,7 @@ __global__ void __launch_bounds__(LINE_T) k_flags_lines(const uint8_t* __restric
         cnt_gm[line] = t[0];
         cnt_src[line] = t[1];
         cnt_term[line] = t[2];
+        cnt_gp[line] = t[3];
         if (t[3]) atomicAdd(info + I_GP, t[3]);
         if (t[4]) atomicAdd(info + I_MP, t[4]);
         if (t[1]) {
@@ -141,12 +147,12 @@ __global__ void __launch_bounds__(LINE_T) k_flags_lines(const uint8_t* __restric
     }
 }
 
-// In-place exclusive scans of the three per-line counts (nl + 1 entries,
+// In-place exclusive scans of the four per-line counts (nl + 1 entries,
 // the last one becomes the total), one CTA each; totals to info.
-__global__ void __launch_bounds__(1024) k_scan_lines(int* c0, int* c1, int* c2, int nl, int* info) {
+__global__ void __launch_bounds__(1024) k_scan_lines(int* c0, int* c1, int* c2, int* c3, int nl, int* info) {
     __shared__ int s_warp[33];
     __shared__ int s_carry;
-    int* arr = blockIdx.x == 0 ? c0 : (blockIdx.x == 1 ? c1 : c2);
+    int* arr = blockIdx.x == 0 ? c0 : (blockIdx.x == 1 ? c1 : (blockIdx.x == 2 ? c2 : c3));
     if (threadIdx.x == 0) s_carry = 0;
     __syncthreads();
     for (int base = 0; base <= nl; base += blockDim.x * SCAN_E) {
@@ -173,37 +179,52 @@ __global__ void __launch_bounds__(1024) k_scan_lines(int* c0, int* c1, int* c2, 
 
 // The lists in lexicographic order: per line, the CTA scans its nodes
 // (gamma-, source and term counts packed in one int: at most 256, 256 and
-// 1536 per line) from the line's offsets. node_of[x] = index of gamma- node
-// x (set only at gamma- nodes); term_off[s] = first term of source s.
+// 1792 per line; gamma+ in a second scan) from the line's offsets.
+// node_of[x] = index of gamma- node x, n_gm + index of gamma+ node x (set
+// only there: the unknown numbers of the direct formulation); term_off[s] =
+// first term of source s.
 __global__ void __launch_bounds__(LINE_T) k_scatter_lines(const uint8_t* __restrict__ flags, int N, int src_mask,
-                                                         const int* __restrict__ off_gm, const int* __restrict__ off_src,
-                                                         const int* __restrict__ off_term, const int* __restrict__ info,
-                                                         int* __restrict__ gm, int* __restrict__ node_of,
-                                                         int* __restrict__ src_lin, int* __restrict__ term_off) {
+                                                         bool direct, const int* __restrict__ off_gm,
+                                                         const int* __restrict__ off_src,
+                                                         const int* __restrict__ off_term,
+                                                         const int* __restrict__ off_gp, const int* __restrict__ info,
+                                                         int* __restrict__ gm, int* __restrict__ gp,
+                                                         int* __restrict__ node_of, int* __restrict__ src_lin,
+                                                         int* __restrict__ term_off) {
     __shared__ int s_warp[33];
     const int line = blockIdx.x, i = line / N, j = line - i * N;
     if (line == (int)gridDim.x - 1 && threadIdx.x == 0) term_off[info[I_NSRC]] = info[I_NTERM];
-    int pg = off_gm[line], ps = off_src[line], pt = off_term[line];
-    if (ps == off_src[line + 1]) return;   // no source (so no gamma- node) on this line: the whole CTA
+    int pg = off_gm[line], ps = off_src[line], pt = off_term[line], pp = off_gp[line];
+    const int ngm = info[I_NGM];
+    if (ps == off_src[line + 1] && pp == off_gp[line + 1]) return;   // nothing on this line: the whole CTA
     const int base = line * N;
     for (int k0 = 0; k0 < N; k0 += blockDim.x) {
         const int k = k0 + (int)threadIdx.x;
-        int g = 0, s = 0, nt = 0;
+        int g = 0, s = 0, nt = 0, p = 0;
         if (k < N) {
             const int f = flags[base + k];
             g = (f >> 1) & 1;
+            p = (f >> 2) & 1;
             s = (f & src_mask) != 0;
-            if (s && g) {
-                nt = 1;
-            } else if (s) {
-                for (int d = 0; d < 6; ++d) {
-                    const int ii = i + c_dir[d][0], jj = j + c_dir[d][1], kk = k + c_dir[d][2];
-                    if (in_grid(ii, jj, kk, N) && (flags[(ii * N + jj) * N + kk] & 2)) ++nt;
-                }
+            if (s) {
+                const int want = g ? 6 : 2;   // gamma- and gamma+ neighbours, or gamma- neighbours
+                nt = g ? 1 : 0;
+                if (!g || direct)
+                    for (int d = 0; d < 6; ++d) {
+                        const int ii = i + c_dir[d][0], jj = j + c_dir[d][1], kk = k + c_dir[d][2];
+                        if (in_grid(ii, jj, kk, N) && (flags[(ii * N + jj) * N + kk] & want)) ++nt;
+                    }
             }
         }
         const int ex = block_exclusive_scan(g | (s << 10) | (nt << 20), s_warp);
         const int tot = s_warp[32];
+        const int exp_ = block_exclusive_scan(p, s_warp);
+        const int totp = s_warp[32];
+        if (p) {
+            gp[pp + exp_] = base + k;
+            node_of[base + k] = ngm + pp + exp_;
+        }
+        pp += totp;
         if (g) {
             gm[pg + (ex & 1023)] = base + k;
             node_of[base + k] = pg + (ex & 1023);
@@ -253,21 +274,48 @@ __global__ void k_closure(const double* __restrict__ phi, const uint8_t* __restr
     }
 }
 
+// unknown number of each gamma- node's closure partner (a gamma+ node)
+__global__ void k_partner_unknown(const int* __restrict__ partner, int n, const int* __restrict__ node_of,
+                                  int* __restrict__ pu) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) pu[r] = node_of[partner[r]];
+}
+
 // ------------------------------------------------------------ source recipe
 // rho(x) = coef(x) q(x) on gamma- (coef = |D_x| for the double layer, or 1
 // when D_x is empty or for the single layer); rho(k) = -sum q(n) over the
 // gamma- neighbours n of a D-node k (k is in D_n for each of them).
+//
+// Direct formulation (eq. [dp]): rho = chi_{M-} (6 + s - neighbour sum) u
+// on gamma: at a gamma- node n, (6 + s) u(n) minus u at its neighbours in
+// gamma (gamma- and gamma+); at a D-node, minus u at its gamma- neighbours
+// (a node outside N+ has no gamma+ neighbour). gidx holds the unknown
+// number of every gamma node.
 __global__ void k_term_fill(const int* __restrict__ src, int ns, const uint8_t* __restrict__ flags, int N,
-                            const int* __restrict__ gidx, const int* __restrict__ off, int layer,
-                            int* __restrict__ tidx, float* __restrict__ tcoef) {
+                            const int* __restrict__ gidx, const int* __restrict__ off, int layer, double s6,
+                            int* __restrict__ tidx, double* __restrict__ tcoef) {
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += gridDim.x * blockDim.x) {
         const int x = src[s];
         int e = off[s];
         const uint8_t f = flags[x];
+        if ((f & 2) && layer == BAE_LAYER_DIRECT) {
+            tidx[e] = gidx[x];
+            tcoef[e] = s6;
+            ++e;
+            const int i = x / (N * N), j = (x / N) % N, k = x % N;
+            for (int d = 0; d < 6; ++d) {
+                const int y = ((i + c_dir[d][0]) * N + j + c_dir[d][1]) * N + k + c_dir[d][2];   // in the grid
+                if (flags[y] & 6) {
+                    tidx[e] = gidx[y];
+                    tcoef[e] = -1.0;
+                    ++e;
+                }
+            }
+            continue;
+        }
         if (f & 2) {
             const int c = f >> 4;
             tidx[e] = gidx[x];
-            tcoef[e] = (layer == BAE_LAYER_DOUBLE && c > 0) ? (float)c : 1.0f;
+            tcoef[e] = (layer == BAE_LAYER_DOUBLE && c > 0) ? (double)c : 1.0;
             continue;
         }
         const int i = x / (N * N), j = (x / N) % N, k = x % N;
@@ -277,7 +325,7 @@ __global__ void k_term_fill(const int* __restrict__ src, int ns, const uint8_t* 
             const int y = (ii * N + jj) * N + kk;
             if (flags[y] & 2) {
                 tidx[e] = gidx[y];
-                tcoef[e] = -1.0f;
+                tcoef[e] = -1.0;
                 ++e;
             }
         }
@@ -297,13 +345,14 @@ int grid_for(long long n) { return (int)std::min<long long>((n + 255) / 256, 152
 }  // namespace
 
 void Geometry::release() {
-    void* ps[] = {flags, gm, node_of, partner, t, xstar, line_off, src_lin, term_off, term_idx, term_coef};
+    void* ps[] = {flags, gm, gp, node_of, partner, partner_u, t, xstar, line_off, src_lin, term_off, term_idx,
+                  term_coef};
     for (void* p : ps) if (p) dev_free(p, stream);
-    flags = nullptr; gm = node_of = partner = nullptr; t = xstar = nullptr;
+    flags = nullptr; gm = gp = node_of = partner = partner_u = nullptr; t = xstar = nullptr;
     line_off = src_lin = term_off = term_idx = nullptr; term_coef = nullptr;
 }
 
-void build_geometry(const double* phi, int N, double h, const double origin[3], int layer, Geometry& g,
+void build_geometry(const double* phi, int N, double h, const double origin[3], int layer, double s, Geometry& g,
                     cudaStream_t st) {
     const long long n3 = (long long)N * N * N;
     Scratch sc(st);
@@ -318,14 +367,18 @@ void build_geometry(const double* phi, int N, double h, const double origin[3], 
     BAE_CUDA(cudaMemsetAsync(info, 0, I_COUNT * sizeof(int), st));
     uint8_t* nbits = sc.get<uint8_t>(n3);
     BAE_LAUNCH("k_nbits", st, k_nbits<<<(unsigned)nl, LINE_T, 0, st>>>(phi, N, nbits, info));
-    const int src_mask = layer == BAE_LAYER_DOUBLE ? (2 | 8) : 2;   // gamma- and D-nodes, or gamma- only
+    const bool direct = layer == BAE_LAYER_DIRECT;
+    // gamma- and D-nodes (double layer, direct formulation), or gamma- only
+    const int src_mask = layer == BAE_LAYER_SINGLE ? 2 : (2 | 8);
     g.flags = dev_alloc_n<uint8_t>(n3, st);
     g.line_off = dev_alloc_n<int>(nl + 1, st);   // per-line source counts, then their scan
     int* off_gm = sc.get<int>(nl + 1);
     int* off_term = sc.get<int>(nl + 1);
+    int* off_gp = sc.get<int>(nl + 1);
     BAE_LAUNCH("k_flags_lines", st,
-               k_flags_lines<<<(unsigned)nl, LINE_T, 0, st>>>(nbits, N, src_mask, g.flags, off_gm, g.line_off, off_term, info));
-    BAE_LAUNCH("k_scan_lines", st, k_scan_lines<<<3, 1024, 0, st>>>(off_gm, g.line_off, off_term, (int)nl, info));
+               k_flags_lines<<<(unsigned)nl, LINE_T, 0, st>>>(nbits, N, src_mask, direct, g.flags, off_gm, g.line_off,
+                                                              off_term, off_gp, info));
+    BAE_LAUNCH("k_scan_lines", st, k_scan_lines<<<4, 1024, 0, st>>>(off_gm, g.line_off, off_term, off_gp, (int)nl, info));
     int rec[I_COUNT];
     BAE_CUDA(cudaMemcpyAsync(rec, info, sizeof(rec), cudaMemcpyDeviceToHost, st));
     BAE_CUDA(cudaStreamSynchronize(st));
@@ -338,24 +391,32 @@ void build_geometry(const double* phi, int N, double h, const double origin[3], 
     g.n_mp = rec[I_MP];
     if (g.n_gm == 0) throw Error(BAE_ERR_GEOMETRY, "gamma- is empty (no interior node)");
 
+    g.n_unk = direct ? g.n_gm + g.n_gp : g.n_gm;
     g.gm = dev_alloc_n<int>(g.n_gm, st);
+    g.gp = dev_alloc_n<int>(std::max(1LL, g.n_gp), st);
     g.node_of = dev_alloc_n<int>(n3, st);
     g.src_lin = dev_alloc_n<int>(g.n_src, st);
     g.term_off = dev_alloc_n<int>(g.n_src + 1, st);
     BAE_LAUNCH("k_scatter_lines", st,
-               k_scatter_lines<<<(unsigned)nl, LINE_T, 0, st>>>(g.flags, N, src_mask, off_gm, g.line_off, off_term, info,
-                                                                g.gm, g.node_of, g.src_lin, g.term_off));
+               k_scatter_lines<<<(unsigned)nl, LINE_T, 0, st>>>(g.flags, N, src_mask, direct, off_gm, g.line_off,
+                                                                off_term, off_gp, info, g.gm, g.gp, g.node_of,
+                                                                g.src_lin, g.term_off));
     // closure
     g.partner = dev_alloc_n<int>(g.n_gm, st);
     g.t = dev_alloc_n<double>(g.n_gm, st);
     g.xstar = dev_alloc_n<double>(3 * g.n_gm, st);
     BAE_LAUNCH("k_closure", st, k_closure<<<grid_for(g.n_gm), 256, 0, st>>>(phi, g.flags, g.gm, (int)g.n_gm, N, h, origin[0], origin[1], origin[2],
                                                 g.partner, g.t, g.xstar));
+    if (direct) {
+        g.partner_u = dev_alloc_n<int>(g.n_gm, st);
+        BAE_LAUNCH("k_partner_unknown", st,
+                   k_partner_unknown<<<grid_for(g.n_gm), 256, 0, st>>>(g.partner, (int)g.n_gm, g.node_of, g.partner_u));
+    }
     // source recipe
     g.term_idx = dev_alloc_n<int>(g.n_terms, st);
-    g.term_coef = dev_alloc_n<float>(g.n_terms, st);
+    g.term_coef = dev_alloc_n<double>(g.n_terms, st);
     BAE_LAUNCH("k_term_fill", st, k_term_fill<<<grid_for(g.n_src), 256, 0, st>>>(g.src_lin, (int)g.n_src, g.flags, N, g.node_of, g.term_off, layer,
-                                                   g.term_idx, g.term_coef));
+                                                   6.0 + s, g.term_idx, g.term_coef));
     // x-planes holding every source (gamma- and D-nodes, or M+ for the
     // volume term, whose planes lie between) and every gathered node
     // (gamma- and the partners, one step from gamma-)

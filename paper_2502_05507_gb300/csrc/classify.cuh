@@ -14,9 +14,12 @@ struct Geometry {
     int layer = BAE_LAYER_DOUBLE;
     cudaStream_t stream = nullptr;  // stream that owns the allocations
     long long n_gm = 0, n_gp = 0, n_mp = 0, n_src = 0, n_terms = 0;
+    long long n_unk = 0;          // unknowns: n_gm, or n_gm + n_gp (direct formulation: u on gamma- then gamma+)
     uint8_t* flags = nullptr;     // N^3: bit0 M+, bit1 gamma-, bit2 gamma+, bit3 D-node, bits4-6 |D_n|
     int* gm = nullptr;            // gamma- linear indices, lexicographic
-    int* node_of = nullptr;       // N^3: index in gm of a gamma- node (set at gamma- nodes only)
+    int* gp = nullptr;            // gamma+ linear indices, lexicographic
+    int* node_of = nullptr;       // N^3: unknown number of a gamma node (gamma-: its gm index, gamma+: n_gm + gp index; set there only)
+    int* partner_u = nullptr;     // direct formulation: unknown number of each gamma- node's partner
     int* partner = nullptr;       // closure partner per gamma- node
     double* t = nullptr;          // closure weight per gamma- node
     double* xstar = nullptr;      // boundary points, 3 per gamma- node
@@ -24,7 +27,7 @@ struct Geometry {
     int* src_lin = nullptr;
     int* term_off = nullptr;
     int* term_idx = nullptr;
-    float* term_coef = nullptr;
+    double* term_coef = nullptr;
     // x-planes [plane_lo, plane_hi) contain every source and every node the
     // gather and the reconstruction read
     int plane_lo = 0, plane_hi = 0;
@@ -44,7 +47,8 @@ struct Geometry {
 // Classifies phi (device, N^3 float64), builds the closure and the source
 // recipe. Throws Error(BAE_ERR_GEOMETRY) when gamma- is empty or when M+ or
 // gamma- reaches the box faces, Error(BAE_ERR_INVALID_ARG) on non-finite phi.
-void build_geometry(const double* phi, int N, double h, const double origin[3], int layer,
+// s = kappa^2 h^2 (the direct formulation's source stencil uses 6 + s).
+void build_geometry(const double* phi, int N, double h, const double origin[3], int layer, double s,
                     Geometry& g, cudaStream_t st);
 
 }  // namespace bae

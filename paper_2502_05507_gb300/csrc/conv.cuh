@@ -13,8 +13,8 @@ struct SrcRecipe {
     const int* line_off = nullptr;   // N*N + 1 offsets into src_lin
     const int* src_lin = nullptr;    // linear grid index of each source node
     const int* term_off = nullptr;   // ns + 1 offsets into term_idx/term_coef
-    const int* term_idx = nullptr;   // gamma- index of each term
-    const float* term_coef = nullptr;
+    const int* term_idx = nullptr;   // unknown number of each term
+    const double* term_coef = nullptr;
 };
 
 enum SourceMode { SRC_DENSITY = 0, SRC_VOLUME = 1 };
@@ -89,6 +89,19 @@ template <typename T>
 void closure_gather(const T* v, long long v_stride, const int* gm, const int* partner, const double* t,
                     int n, int nbatch, double* out, long long out_stride, cudaStream_t st,
                     const int* active = nullptr);
+
+// Rows of the direct formulation for items with active[b] != 0 (all
+// device arrays, capturable): y[b][r] = t[r] x(r) + (1 - t[r]) x(pu[r]) for
+// r < n_gm (the closure), y[b][n_gm + k] = x(n_gm + k) - w[b][gp[k]] (gamma+);
+// x[b] at x + b x_stride (+ x_row[b] x_row_stride when x_row is set).
+template <typename W, typename Y>
+void direct_rows(const W* w, long long w_stride, const double* x, long long x_stride, const int* x_row,
+                 long long x_row_stride, const int* gp, const int* pu, const double* t, long long n_gm, long long n_unk,
+                 int nb, const int* active, Y* y, long long y_stride, cudaStream_t st);
+
+// u[b][gm[r]] = q[b][r] for r < n
+void scatter_gm(const double* q, long long q_stride, const int* gm, long long n, int nb, double* u, long long n3,
+                cudaStream_t st);
 
 // u[b][x] = (nplus(x) ? add[b][x] + v[b][x] : 0) over the N^3 grid
 template <typename T>

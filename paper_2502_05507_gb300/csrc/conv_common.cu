@@ -108,6 +108,41 @@ __global__ void k_closure_gather(const T* v, long long v_stride, const int* gm, 
     }
 }
 
+// Rows of the direct formulation (eq. [direct_sys] with eq. [inhom]):
+// y[r] = t x(m_r) + (1 - t) x(p(m_r)) on the n_gm gamma- rows (the closure),
+// y[n_gm + k] = x(gp_k) - w(gp_k) on gamma+, for items with active[b] != 0;
+// x is read like the convolution's density, w [nb][w_stride].
+template <typename W, typename Y>
+__global__ void k_direct_rows(const W* __restrict__ w, long long w_stride, const double* x, long long x_stride,
+                              const int* x_row, long long x_row_stride, const int* __restrict__ gp,
+                              const int* __restrict__ pu, const double* __restrict__ t, long long n_gm,
+                              long long n_unk, const int* active, Y* y, long long y_stride) {
+    const int b = blockIdx.y;
+    if (active && !active[b]) return;
+    const double* xb = x + b * x_stride + (x_row ? (long long)x_row[b] * x_row_stride : 0);
+    const W* wb = w + b * w_stride;
+    Y* yb = y + b * y_stride;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n_unk; r += (long long)gridDim.x * blockDim.x) {
+        double v;
+        if (r < n_gm) {
+            const double tr = t[r];
+            v = tr * xb[r] + (1.0 - tr) * xb[pu[r]];
+        } else {
+            v = xb[r] - (double)wb[gp[r - n_gm]];
+        }
+        yb[r] = (Y)v;
+    }
+}
+
+// u[b][gm[r]] = q[b][r]: the gamma- values of the direct formulation's
+// unknown into the reconstructed grid function
+__global__ void k_scatter_gm(const double* q, long long q_stride, const int* __restrict__ gm, long long n,
+                             double* u, long long n3) {
+    const int b = blockIdx.y;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
+        u[b * n3 + gm[r]] = q[b * q_stride + r];
+}
+
 template <typename T>
 __global__ void k_volume_combine(const T* v, const double* add, const uint8_t* flags, long long n3, double* u) {
     const int b = blockIdx.y;
@@ -171,6 +206,21 @@ void closure_gather(const T* v, long long v_stride, const int* gm, const int* pa
     BAE_LAUNCH(kname<T>("closure_gather.f32", "closure_gather.f64", "closure_gather.f64"), st, k_closure_gather<T><<<grid, 256, 0, st>>>(v, v_stride, gm, partner, t, n, out, out_stride, active));
 }
 
+template <typename W, typename Y>
+void direct_rows(const W* w, long long w_stride, const double* x, long long x_stride, const int* x_row,
+                 long long x_row_stride, const int* gp, const int* pu, const double* t, long long n_gm, long long n_unk,
+                 int nb, const int* active, Y* y, long long y_stride, cudaStream_t st) {
+    dim3 grid(ceil_div(n_unk, 256) < 1184 ? ceil_div(n_unk, 256) : 1184, nb);
+    BAE_LAUNCH("k_direct_rows", st, k_direct_rows<W, Y><<<grid, 256, 0, st>>>(w, w_stride, x, x_stride, x_row, x_row_stride,
+                                                                              gp, pu, t, n_gm, n_unk, active, y, y_stride));
+}
+
+void scatter_gm(const double* q, long long q_stride, const int* gm, long long n, int nb, double* u, long long n3,
+                cudaStream_t st) {
+    dim3 grid(ceil_div(n, 256) < 1184 ? ceil_div(n, 256) : 1184, nb);
+    BAE_LAUNCH("k_scatter_gm", st, k_scatter_gm<<<grid, 256, 0, st>>>(q, q_stride, gm, n, u, n3));
+}
+
 template <typename T>
 void volume_combine(const T* v, const double* add, const uint8_t* flags, long long n3, int nbatch,
                     double* u, cudaStream_t st) {
@@ -198,6 +248,9 @@ template void conv_prepare<double>(int);
 template void conv_prepare<dsf>(int);
 template void closure_gather<float>(const float*, long long, const int*, const int*, const double*, int, int, double*, long long, cudaStream_t, const int*);
 template void closure_gather<double>(const double*, long long, const int*, const int*, const double*, int, int, double*, long long, cudaStream_t, const int*);
+template void direct_rows<float, float>(const float*, long long, const double*, long long, const int*, long long, const int*, const int*, const double*, long long, long long, int, const int*, float*, long long, cudaStream_t);
+template void direct_rows<float, double>(const float*, long long, const double*, long long, const int*, long long, const int*, const int*, const double*, long long, long long, int, const int*, double*, long long, cudaStream_t);
+template void direct_rows<double, double>(const double*, long long, const double*, long long, const int*, long long, const int*, const int*, const double*, long long, long long, int, const int*, double*, long long, cudaStream_t);
 template void volume_combine<float>(const float*, const double*, const uint8_t*, long long, int, double*, cudaStream_t);
 template void volume_combine<double>(const double*, const double*, const uint8_t*, long long, int, double*, cudaStream_t);
 template void widen<float>(const float*, long long, double*, cudaStream_t);

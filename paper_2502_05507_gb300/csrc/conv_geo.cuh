@@ -77,17 +77,11 @@ __device__ __forceinline__ T volume_or_zero(const ConvArgs<T>& a, int b, long lo
 
 template <typename T>
 __device__ __forceinline__ T source_value(const SrcRecipe& rec, int s, const double* q) {
-    if constexpr (std::is_same<T, float>::value) {
-        float val = 0.f;
-        for (int e = rec.term_off[s]; e < rec.term_off[s + 1]; ++e)
-            val = __fmaf_rn(rec.term_coef[e], (float)q[rec.term_idx[e]], val);
-        return val;
-    } else {
-        double val = 0.0;
-        for (int e = rec.term_off[s]; e < rec.term_off[s + 1]; ++e)
-            val += (double)rec.term_coef[e] * q[rec.term_idx[e]];
-        return (T)val;
-    }
+    // float64 sum, one rounding to T: the direct formulation's stencil
+    // (6 + s) u(n) - sum u(y) cancels to O(h^2) u for smooth u
+    double val = 0.0;
+    for (int e = rec.term_off[s]; e < rec.term_off[s + 1]; ++e) val += rec.term_coef[e] * q[rec.term_idx[e]];
+    return (T)val;
 }
 
 // ------------------------------------------ programmatic dependent launch

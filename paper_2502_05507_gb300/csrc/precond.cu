@@ -289,6 +289,7 @@ void build_precond(const Geometry& g, double s, const double* near, Precond& out
 
 void precond_apply(const Precond& p, const double* in, long long in_stride, const int* row, long long row_stride,
                    double* out, long long out_stride, int nb, const int* active, cudaStream_t st) {
+    BAE_REQUIRE(p.built, BAE_ERR_INVALID_ARG, "internal: preconditioner applied before it was built");
     if (p.n == 0 || nb == 0) return;
     const int ctas = (int)std::min<long long>((p.n + 7) / 8, 152LL * 16);   // 8 rows per 256-thread CTA
     BAE_LAUNCH("k_precond_apply", st,

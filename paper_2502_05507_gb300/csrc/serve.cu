@@ -74,10 +74,12 @@ struct bae_server {
         rc = bae_boundary_points(P, xyz.data());
         if (rc == BAE_OK) {
             if (q.boundary) q.boundary(xyz.data(), n_gm, g.data(), q.user);
-            r->density.assign((size_t)n_gm, 0.0);
+            int64_t n_unk = 0;
+            bae_problem_unknowns(P, &n_unk);
+            r->density.assign((size_t)n_unk, 0.0);
             rc = bae_solve(P, q.f, g.data(), &q.opts, r->density.data(), q.u_out, &r->res.stats);
         }
-        r->res.n_gm = n_gm;
+        r->res.n_gm = (int64_t)r->density.size();   // the density's length
         bae_problem_destroy(P);
         return rc;
     }
