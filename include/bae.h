@@ -288,7 +288,8 @@ int bae_particular(bae_problem* prob, int precision, const double* f, double* up
  *   b = g - Phi u_p,  A q = b,  u = u_p + K q.
  * BAE_LAYER_DIRECT solves eq. [direct_sys] with eq. [inhom] for q = u on
  * gamma: b = [g; u_p on gamma+], u = u_p + P q on M+ and q on gamma-
- * (eq. [discrete_green]); opts->precond is ignored there.
+ * (eq. [discrete_green]); its Schwarz blocks (opts->precond) take the
+ * gamma nodes of each neighbourhood (closure rows, and delta - P rows).
  * f: N^3 doubles (paper sign, -Lap u + kappa2 u = f); g: n_gm doubles, the
  * Dirichlet data at bae_boundary_points(). Outputs: density q
  * (bae_problem_unknowns() doubles)

@@ -771,7 +771,7 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
     // the right preconditioner of the inner solves (restricted additive
     // Schwarz) is built on the side stream while this one checks the inputs
     // and forms the first right-hand side; the inner solves wait for it
-    const bool any_pre = o.precision == BAE_MIXED && o.precond != 0 && !direct;
+    const bool any_pre = o.precision == BAE_MIXED && o.precond != 0;
     if (any_pre && !P->pre.built) {
         BAE_CUDA(cudaEventRecord(P->ctx->fork_ev, st));
         BAE_CUDA(cudaStreamWaitEvent(P->ctx->side, P->ctx->fork_ev, 0));

@@ -39,6 +39,7 @@ struct Geometry {
         r.term_off = term_off;
         r.term_idx = term_idx;
         r.term_coef = term_coef;
+        r.wide = layer == BAE_LAYER_DIRECT;
         return r;
     }
     void release();

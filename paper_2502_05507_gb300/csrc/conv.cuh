@@ -15,6 +15,9 @@ struct SrcRecipe {
     const int* term_off = nullptr;   // ns + 1 offsets into term_idx/term_coef
     const int* term_idx = nullptr;   // unknown number of each term
     const double* term_coef = nullptr;
+    // sum the terms in float64 before the float32 rounding (the direct
+    // formulation's (6 + s) u(n) - sum u(y) cancels to O(h^2 u))
+    bool wide = false;
 };
 
 enum SourceMode { SRC_DENSITY = 0, SRC_VOLUME = 1 };

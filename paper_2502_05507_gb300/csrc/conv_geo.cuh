@@ -77,8 +77,15 @@ __device__ __forceinline__ T volume_or_zero(const ConvArgs<T>& a, int b, long lo
 
 template <typename T>
 __device__ __forceinline__ T source_value(const SrcRecipe& rec, int s, const double* q) {
-    // float64 sum, one rounding to T: the direct formulation's stencil
-    // (6 + s) u(n) - sum u(y) cancels to O(h^2) u for smooth u
+    if constexpr (std::is_same<T, float>::value) {
+        if (!rec.wide) {   // small integer coefficients: a float32 sum
+            float val = 0.f;
+            for (int e = rec.term_off[s]; e < rec.term_off[s + 1]; ++e)
+                val = __fmaf_rn((float)rec.term_coef[e], (float)q[rec.term_idx[e]], val);
+            return val;
+        }
+    }
+    // float64 sum, one rounding to T
     double val = 0.0;
     for (int e = rec.term_off[s]; e < rec.term_off[s + 1]; ++e) val += rec.term_coef[e] * q[rec.term_idx[e]];
     return (T)val;

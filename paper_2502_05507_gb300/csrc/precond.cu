@@ -93,28 +93,40 @@ struct RasNode {
 // largest |entry| in column c, and the back substitution runs over the
 // columns with each row's right-hand side in its lane. A numerically
 // singular block keeps the identity row.
-// Per gamma- node s: its grid index, its closure partner's, t (float bits)
-// and the D-node mask of its six neighbours (double layer; bit d: neighbour
-// d outside N+ = M+ and gamma-), 16 bytes read once per block member.
-__global__ void k_member_info(const int* __restrict__ gm, const int* __restrict__ partner, const double* __restrict__ t,
-                              const uint8_t* __restrict__ flags, long long n, int N, int layer, int4* __restrict__ info) {
+// Per unknown s: its grid index, its closure partner (grid index; for the
+// direct formulation the partner's unknown number, -1 on gamma+), t (float
+// bits; 1 on gamma+) and a neighbour mask (bit d set for neighbour d
+// outside N+ = M+ and gamma- in the double layer, outside M+ in the direct
+// formulation; bit 6: a gamma+ unknown), 16 bytes read once per block member.
+__global__ void k_member_info(const int* __restrict__ lin_of, const int* __restrict__ partner,
+                              const int* __restrict__ partner_u, const double* __restrict__ t,
+                              const uint8_t* __restrict__ flags, long long n, long long n_gm, int N, int layer,
+                              int4* __restrict__ info) {
+    const int off[6] = {N * N, -N * N, N, -N, 1, -1};
     for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
-        const int g = gm[s];
+        const int g = lin_of[s];
         unsigned dm = 0;
-        if (layer == BAE_LAYER_DOUBLE) {
-            const int off[6] = {N * N, -N * N, N, -N, 1, -1};
+        if (layer == BAE_LAYER_DIRECT) {
+            for (int d = 0; d < 6; ++d)
+                if (!(flags[g + off[d]] & 1)) dm |= 1u << d;
+            if (s < n_gm)
+                info[s] = make_int4(g, partner_u[s], __float_as_int((float)t[s]), (int)dm);
+            else
+                info[s] = make_int4(g, -1, __float_as_int(1.f), (int)(dm | 64u));
+            continue;
+        }
+        if (layer == BAE_LAYER_DOUBLE)
             for (int d = 0; d < 6; ++d)
                 if (!(flags[g + off[d]] & 3)) dm |= 1u << d;
-        }
         info[s] = make_int4(g, partner[s], __float_as_int((float)t[s]), (int)dm);
     }
 }
 
-__global__ void __launch_bounds__(32 * RAS_WARPS) k_ras_rows(const int* __restrict__ gm, const int4* __restrict__ minfo,
+__global__ void __launch_bounds__(32 * RAS_WARPS) k_ras_rows(const int* __restrict__ lin_of, const int4* __restrict__ minfo,
                                                           const uint8_t* __restrict__ flags,
                                                           const double* __restrict__ tab64, const int* __restrict__ node_of,
-                                                          long long n, int N, int* __restrict__ col,
-                                                          float* __restrict__ val) {
+                                                          long long n, int N, bool direct, float s6,
+                                                          int* __restrict__ col, float* __restrict__ val) {
     __shared__ float tab[TCUBE];
     __shared__ signed char nbo[NB_N][3];
     __shared__ RasNode sh[RAS_WARPS];
@@ -129,8 +141,9 @@ __global__ void __launch_bounds__(32 * RAS_WARPS) k_ras_rows(const int* __restri
     const int NN = N * N;   // N^3 < 2^31
     constexpr int ROUNDS = (NB_N + 31) / 32;
     for (long long r = (long long)blockIdx.x * RAS_WARPS + w; r < n; r += (long long)gridDim.x * RAS_WARPS) {
-        const int lin = gm[r];
+        const int lin = lin_of[r];
         const int ri = lin / NN, rj = (lin / N) % N, rk = lin % N;
+        const int member = direct ? 6 : 2;   // gamma nodes, or gamma- nodes
         // every probe's flags first (independent loads), then the node indices
         int y[ROUNDS], s[ROUNDS];
 #pragma unroll
@@ -144,7 +157,7 @@ __global__ void __launch_bounds__(32 * RAS_WARPS) k_ras_rows(const int* __restri
             }
         }
 #pragma unroll
-        for (int q = 0; q < ROUNDS; ++q) s[q] = (y[q] >= 0 && (flags[y[q]] & 2)) ? 0 : -1;
+        for (int q = 0; q < ROUNDS; ++q) s[q] = (y[q] >= 0 && (flags[y[q]] & member)) ? 0 : -1;
 #pragma unroll
         for (int q = 0; q < ROUNDS; ++q)
             if (s[q] == 0) s[q] = node_of[y[q]];
@@ -162,21 +175,43 @@ __global__ void __launch_bounds__(32 * RAS_WARPS) k_ras_rows(const int* __restri
         if (mine >= 0) {
             const int4 f = minfo[mine];
             R.g[0][lane] = f.x / NN; R.g[1][lane] = (f.x / N) % N; R.g[2][lane] = f.x % N;
-            R.x[0][lane] = f.y / NN; R.x[1][lane] = (f.y / N) % N; R.x[2][lane] = f.y % N;
+            if (direct) {
+                R.x[0][lane] = f.y;   // the partner's unknown number (-1 on gamma+)
+            } else {
+                R.x[0][lane] = f.y / NN; R.x[1][lane] = (f.y / N) % N; R.x[2][lane] = f.y % N;
+            }
             R.t[lane] = __int_as_float(f.z);
             R.dmask[lane] = (unsigned)f.w;
         }
         const int me = 0;   // offset 0 comes first: r itself
         __syncwarp();
-        // M = A_S^T: M[q][p] = A_S[p][q] = t_p K(g_p, g_q) + (1 - t_p) K(x_p, g_q)
+        // M = A_S^T: M[q][p] = A_S[p][q] = t_p K(g_p, g_q) + (1 - t_p) K(x_p, g_q);
+        // direct formulation: a gamma- row is the closure (t_p at itself,
+        // 1 - t_p at its partner), a gamma+ row delta - P with
+        // P(p, q) = (6 + s) G(p - q) [q in M-] - sum_{y ~ q, y in M-} G(p - y)
         float scale = 0.f;
         for (int e = lane; e < k * k; e += 32) {
             const int p = e / k, q = e - p * k;
             const int ci = R.g[0][q], cj = R.g[1][q], ck = R.g[2][q];
             const unsigned dm = R.dmask[q];
             const float tp = R.t[p];
-            const float v = tp * kval(tab, R.g[0][p], R.g[1][p], R.g[2][p], ci, cj, ck, dm) +
-                            (1.f - tp) * kval(tab, R.x[0][p], R.x[1][p], R.x[2][p], ci, cj, ck, dm);
+            float v;
+            if (!direct) {
+                v = tp * kval(tab, R.g[0][p], R.g[1][p], R.g[2][p], ci, cj, ck, dm) +
+                    (1.f - tp) * kval(tab, R.x[0][p], R.x[1][p], R.x[2][p], ci, cj, ck, dm);
+            } else if (!(R.dmask[p] & 64u)) {
+                v = (p == q ? tp : 0.f) + (R.S[q] == R.x[0][p] ? 1.f - tp : 0.f);
+            } else {
+                const int di = R.g[0][p] - ci, dj = R.g[1][p] - cj, dk = R.g[2][p] - ck;
+                float pv = (dm & 64u) ? 0.f : s6 * lgf_at(tab, di, dj, dk);
+                if (dm & 1) pv -= lgf_at(tab, di - 1, dj, dk);
+                if (dm & 2) pv -= lgf_at(tab, di + 1, dj, dk);
+                if (dm & 4) pv -= lgf_at(tab, di, dj - 1, dk);
+                if (dm & 8) pv -= lgf_at(tab, di, dj + 1, dk);
+                if (dm & 16) pv -= lgf_at(tab, di, dj, dk - 1);
+                if (dm & 32) pv -= lgf_at(tab, di, dj, dk + 1);
+                v = (p == q ? 1.f : 0.f) - pv;
+            }
             R.M[q * MS + p] = v;
             scale = fmaxf(scale, fabsf(v));
         }
@@ -261,7 +296,8 @@ void Precond::release() {
 
 void build_precond(const Geometry& g, double s, const double* near, Precond& out, cudaStream_t st) {
     const int N = g.N;
-    const long long n = g.n_gm;
+    const bool direct = g.layer == BAE_LAYER_DIRECT;
+    const long long n = direct ? g.n_unk : g.n_gm;
     // G_s at offsets [0, NEAR_TN)^3, the function the convolution's spectrum comes from
     double* own = nullptr;
     if (!near) {
@@ -274,15 +310,25 @@ void build_precond(const Geometry& g, double s, const double* near, Precond& out
     out.n = n;
     out.col = dev_alloc_n<int>(n * MAXR, st);
     out.val = dev_alloc_n<float>(n * MAXR, st);
+    // grid index of every unknown: gamma-, then (direct) gamma+
+    int* lin_of = g.gm;
+    int* lin_own = nullptr;
+    if (direct) {
+        lin_own = dev_alloc_n<int>(n, st);
+        BAE_CUDA(cudaMemcpyAsync(lin_own, g.gm, g.n_gm * sizeof(int), cudaMemcpyDeviceToDevice, st));
+        BAE_CUDA(cudaMemcpyAsync(lin_own + g.n_gm, g.gp, g.n_gp * sizeof(int), cudaMemcpyDeviceToDevice, st));
+        lin_of = lin_own;
+    }
     int4* minfo = dev_alloc_n<int4>(n, st);
     BAE_LAUNCH("k_member_info", st,
                k_member_info<<<(int)std::min<long long>((n + 255) / 256, 152LL * 8), 256, 0, st>>>(
-                   g.gm, g.partner, g.t, g.flags, n, N, g.layer, minfo));
+                   lin_of, g.partner, g.partner_u, g.t, g.flags, n, g.n_gm, N, g.layer, minfo));
     const int ctas = (int)std::min<long long>((n + RAS_WARPS - 1) / RAS_WARPS, 152LL * 4);
     BAE_LAUNCH("k_ras_rows", st,
-               k_ras_rows<<<ctas, 32 * RAS_WARPS, 0, st>>>(g.gm, minfo, g.flags, near, g.node_of, n, N, out.col,
-                                                           out.val));
+               k_ras_rows<<<ctas, 32 * RAS_WARPS, 0, st>>>(lin_of, minfo, g.flags, near, g.node_of, n, N, direct,
+                                                           (float)(6.0 + s), out.col, out.val));
     dev_free(minfo, st);
+    if (lin_own) dev_free(lin_own, st);
     if (own) dev_free(own, st);
     out.built = true;
 }

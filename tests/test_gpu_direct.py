@@ -136,3 +136,23 @@ def test_direct_batched_equals_alone(ctx):
             assert stb[b]["iterations"] == st1["iterations"]
     finally:
         prob.close()
+
+
+def test_direct_precond_same_solution_fewer_iterations(ctx):
+    # Schwarz blocks of the direct system (closure rows t, 1 - t; gamma+ rows
+    # delta - P): the same solution in far fewer inner iterations
+    import torch
+    P = W.torus_helmholtz(64, kappa2=10.0)
+    prob = _problem(ctx, P)
+    try:
+        gv = torch.from_numpy(P.g_at(np.asarray(prob.boundary_points()))).cuda()
+        f = torch.from_numpy(P.f()).cuda()
+        _, u0, s0 = prob.solve(f, gv, tol=1e-10, precision="mixed", precond=0, max_iter=2000)
+        _, u1, s1 = prob.solve(f, gv, tol=1e-10, precision="mixed", precond=1, max_iter=2000)
+        assert s1["rel_residual"] <= 1e-10
+        u0, u1 = u0.cpu().numpy(), u1.cpu().numpy()
+        assert np.max(np.abs(u1 - u0)) <= 1e-8 * np.max(np.abs(u0))
+        assert s1["iterations"] < 0.5 * s0["iterations"], (s0, s1)
+        print("direct precond", s0["iterations"], "->", s1["iterations"])
+    finally:
+        prob.close()
