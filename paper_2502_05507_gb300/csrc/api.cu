@@ -497,6 +497,21 @@ void apply_rows_prec(bae_problem* P, int prec, int nb, const double* q, long lon
     else apply_rows<double>(P, nb, q, q_stride, q_row, q_row_stride, active, out);
 }
 
+// A captured GMRES step and the values it was captured with: the next
+// gmres call of the same solve (the inner solves of iterative refinement)
+// replays it when every captured pointer and parameter is the same.
+struct StepGraph {
+    cudaGraphExec_t exec = nullptr;
+    long long kernels = 0;
+    std::vector<uintptr_t> key;
+    StepGraph() = default;
+    StepGraph(const StepGraph&) = delete;
+    StepGraph& operator=(const StepGraph&) = delete;
+    ~StepGraph() {
+        if (exec) cudaGraphExecDestroy(exec);
+    }
+};
+
 // Restarted GMRES for the RHS b in `which` (rows of rhs/x [nb][n], device):
 // every Arnoldi step (apply of precision `prec`, CGS2, Givens) runs on the
 // device; with use_graph it is captured once as a CUDA graph and replayed.
@@ -506,7 +521,7 @@ void apply_rows_prec(bae_problem* P, int prec, int nb, const double* q, long lon
 // A M^{-1} y = rhs; the caller maps it back with M^{-1})
 void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, const double* rhs, double* x,
            bool x_zero, std::vector<RhsState>& S, int max_iter, int restart, std::vector<int>& applies,
-           bool use_graph, bool pre = false) {
+           bool use_graph, bool pre = false, StepGraph* cache = nullptr) {
     cudaStream_t st = P->ctx->stream;
     Workspace& ws = P->ws();
     const int n = (int)n_unk(P);
@@ -573,6 +588,7 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
     long long graph_kernels = 0;
     int iters_left = max_iter;
     std::vector<int> ncols(nb), flg(nb);
+    int coop_err = 0;   // the fused step's barrier error flag, read with each cycle's results
     std::vector<double> est(nb);
 
     // one step: v = K V[j] for the iterating RHS, then the Arnoldi passes
@@ -642,6 +658,36 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
         conv_prepare<double>(P->geo.N);
     }
 
+    // a graph captured by an earlier call with the same values is replayed
+    std::vector<uintptr_t> key;
+    if (use_graph && cache) {
+        auto add = [&](const void* p) { key.push_back(reinterpret_cast<uintptr_t>(p)); };
+        for (long long v : {(long long)prec, (long long)nb, (long long)m, (long long)n, (long long)pre,
+                            (long long)fuse_pre, (long long)direct, (long long)a.coop_grid,
+                            (long long)a.coop_resident, (long long)forced_sched()})
+            key.push_back((uintptr_t)v);
+        add(P); add(a.V); add(a.w); add(a.part); add(a.h1); add(a.hcol); add(a.H); add(a.cs); add(a.g); add(a.y);
+        add(scal); add(ibuf); add(a.ctr); add(a.bar); add(a.pcol); add(a.live_host); add(zpre); add(y32); add(y64);
+        add(ws.A.p); add(ws.B.p); add(ws.v32.p); add(ws.v64.p); add(P->pre.col); add(P->pre.val);
+        if (cache->exec && cache->key == key) {
+            exec = cache->exec;
+            graph_kernels = cache->kernels;
+        }
+    }
+    // a graph made here goes to the cache (replacing its previous one) or is destroyed
+    auto drop_exec = [&](bool keep) {
+        if (!exec) return;
+        if (cache && exec == cache->exec) return;
+        if (keep && cache && !key.empty()) {
+            if (cache->exec) cudaGraphExecDestroy(cache->exec);
+            cache->exec = exec;
+            cache->kernels = graph_kernels;
+            cache->key = key;
+        } else {
+            cudaGraphExecDestroy(exec);
+        }
+        exec = nullptr;
+    };
     try {
         while (iters_left > 0) {
             int any = 0;
@@ -704,13 +750,15 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
                     if (!live) break;
                 }
             }
+            // one host read per cycle: columns, estimates and the barrier
+            // error flag, after the solution update
+            arn_finish(a, x, st);
             BAE_CUDA(cudaMemcpyAsync(ncols.data(), a.ncols, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
+            BAE_CUDA(cudaMemcpyAsync(est.data(), a.est, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+            if (a.coop_grid > 0) BAE_CUDA(cudaMemcpyAsync(&coop_err, a.err, sizeof(int), cudaMemcpyDeviceToHost, st));
             BAE_CUDA(cudaStreamSynchronize(st));
             int maxc = 0;
             for (int b = 0; b < nb; ++b) maxc = std::max(maxc, ncols[b]);
-            arn_finish(a, x, maxc, st);
-            BAE_CUDA(cudaMemcpyAsync(est.data(), a.est, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
-            BAE_CUDA(cudaStreamSynchronize(st));
             for (int b = 0; b < nb; ++b) {
                 if (!mem[b]) continue;
                 S[b].iterations += ncols[b];
@@ -725,16 +773,11 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
             (void)launched;
         }
     } catch (...) {
-        if (exec) cudaGraphExecDestroy(exec);
+        drop_exec(false);
         throw;
     }
-    if (exec) cudaGraphExecDestroy(exec);
-    if (a.coop_grid > 0) {
-        int err = 0;
-        BAE_CUDA(cudaMemcpyAsync(&err, a.err, sizeof(int), cudaMemcpyDeviceToHost, st));
-        BAE_CUDA(cudaStreamSynchronize(st));
-        BAE_REQUIRE(err == 0, BAE_ERR_CUDA, "GMRES: a grid barrier of the fused Arnoldi step timed out");
-    }
+    drop_exec(true);
+    BAE_REQUIRE(coop_err == 0, BAE_ERR_CUDA, "GMRES: a grid barrier of the fused Arnoldi step timed out");
 }
 
 // ------------------------------------------------------------ full solve
@@ -793,16 +836,12 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
         BAE_CUDA(cudaMemcpyAsync(p, g, (size_t)nb * ng * sizeof(double), cudaMemcpyHostToDevice, st));
         d_g = p;
     }
-    {   // f on M+ and g must be finite
-        int* d_bad = P->ws().arnI.need(4);
-        int bad = 0;
-        BAE_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(int), st));
-        kr_nonfinite(d_f, (long long)nb * n3, P->geo.flags, n3, d_bad, st);
-        kr_nonfinite(d_g, (long long)nb * ng, nullptr, 1, d_bad, st);
-        BAE_CUDA(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
-        BAE_CUDA(cudaStreamSynchronize(st));
-        BAE_REQUIRE(!bad, BAE_ERR_INVALID_ARG, "f (on M+) or g contains non-finite values");
-    }
+    // f on M+ and g must be finite: the flag is read with ||b|| below (one
+    // host read; non-finite inputs only make the discarded b non-finite)
+    int* d_bad = P->ws().arnI.need(4);
+    BAE_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(int), st));
+    kr_nonfinite(d_f, (long long)nb * n3, P->geo.flags, n3, d_bad, st);
+    kr_nonfinite(d_g, (long long)nb * ng, nullptr, 1, d_bad, st);
     std::vector<bae_stats> st_local(nb);
     for (auto& s : st_local) std::memset(&s, 0, sizeof(s));
 
@@ -866,7 +905,10 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
     BAE_CUDA(cudaMemcpyAsync(d_act, all.data(), nb * sizeof(int), cudaMemcpyHostToDevice, st));
     kr_norm2(bvec, d_act, nb, n, n2 + nb, krylov_chunks(n), n2, st);
     BAE_CUDA(cudaMemcpyAsync(bn2.data(), n2, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+    int bad = 0;
+    BAE_CUDA(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
     BAE_CUDA(cudaStreamSynchronize(st));
+    BAE_REQUIRE(!bad, BAE_ERR_INVALID_ARG, "f (on M+) or g contains non-finite values");
 
     std::vector<RhsState> S(nb);
     std::vector<int> iters_used(nb, 0);
@@ -920,6 +962,7 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
         rn2 = bn2;
         for (int b = 0; b < nb; ++b) relres[b] = bn2[b] > 0 ? 1.0 : 0.0;
         int iters_left = o.max_iter;
+        StepGraph step_graph;   // the inner solves' captured step, shared by the refinement steps
         for (int step = 0; step < std::max(1, o.max_refine); ++step) {
             std::vector<int> act;
             for (int b = 0; b < nb; ++b)
@@ -946,7 +989,8 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
                 if (std::find(act.begin(), act.end(), b) == act.end()) Si[b].converged = true;
             BAE_CUDA(cudaMemsetAsync(d, 0, (size_t)nb * n * sizeof(double), st));
             std::vector<int> applies(nb, 0);
-            gmres(P, BAE_FP32, nb, act, res, d, true, Si, iters_left, o.restart, applies, o.use_graphs != 0, use_pre);
+            gmres(P, BAE_FP32, nb, act, res, d, true, Si, iters_left, o.restart, applies, o.use_graphs != 0, use_pre,
+                  &step_graph);
             if (use_pre) precond_apply(P->pre, d, n, nullptr, 0, dq, n, nb, nullptr, st);
             int used = 0;
             for (int b : act) {

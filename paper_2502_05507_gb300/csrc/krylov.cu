@@ -17,10 +17,12 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// x[b] += sum_{i < cols} V[b][i] y[b][i], V [nb][mp1][n], y [nb][ystride]
-__global__ void k_combine(const double* __restrict__ V, int n, int mp1, int cols, const double* __restrict__ y,
-                          int ystride, double* __restrict__ x) {
+// x[b] += sum_{i < ncols[b]} V[b][i] y[b][i], V [nb][mp1][n], y [nb][ystride]
+__global__ void k_combine(const double* __restrict__ V, int n, int mp1, const int* __restrict__ ncols,
+                          const double* __restrict__ y, int ystride, double* __restrict__ x) {
     const int b = blockIdx.y;
+    const int cols = ncols[b];
+    if (cols <= 0) return;
     const double* yb = y + (long long)b * ystride;
     for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
         double acc = 0.0;
@@ -847,11 +849,9 @@ void arn_step(const Arnoldi& a, cudaStream_t st) {
     BAE_LAUNCH("k_arn_update_next", st, k_arn_update_next<<<grid, 256, sh_h, st>>>(a));
 }
 
-void arn_finish(const Arnoldi& a, double* x, int maxcols, cudaStream_t st) {
+void arn_finish(const Arnoldi& a, double* x, cudaStream_t st) {
     BAE_LAUNCH("k_arn_backsub", st, k_arn_backsub<<<a.nb, 32, a.m * sizeof(double), st>>>(a));
-    if (maxcols <= 0) return;
-    // every RHS: those with ncols = 0 have y = 0
-    BAE_LAUNCH("k_combine", st, k_combine<<<dim3(blocks_for(a.n), a.nb), 256, 0, st>>>(a.V, a.n, a.m + 1, maxcols, a.y, a.m, x));
+    BAE_LAUNCH("k_combine", st, k_combine<<<dim3(blocks_for(a.n), a.nb), 256, 0, st>>>(a.V, a.n, a.m + 1, a.ncols, a.y, a.m, x));
 }
 
 }  // namespace bae

@@ -107,7 +107,8 @@ void arn_step(const Arnoldi& a, cudaStream_t st);
 // *resident: every (RHS, chunk) item gets its own resident CTA, which keeps
 // its chunk of the basis in shared memory.
 int arn_coop_grid(int n, int nb, int m, bool* resident);
-// End of a cycle: y = R^{-1} g for every RHS with ncols > 0, x += V y.
-void arn_finish(const Arnoldi& a, double* x, int maxcols, cudaStream_t st);
+// End of a cycle: y = R^{-1} g for every RHS with ncols > 0, x += V y
+// (each RHS over its own ncols columns, read on the device).
+void arn_finish(const Arnoldi& a, double* x, cudaStream_t st);
 
 }  // namespace bae
