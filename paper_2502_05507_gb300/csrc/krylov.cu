@@ -697,8 +697,8 @@ __global__ void __launch_bounds__(256) k_arn_step_coop(Arnoldi a) {
     }
     if (!a.pre_col) return;
     // phase 6: z = M^{-1} V[j+1] on the chunk's rows: warp w takes rows
-    // 8 w .. 8 w + 7 of each item, lane q slot q, the same products and
-    // shuffle tree as the separate preconditioner kernel. The slots of the
+    // 8 w .. 8 w + 7 of each item, lane q slot q, the same float32 products
+    // and shuffle tree as the separate preconditioner kernel. The slots of the
     // CTA's first item are loaded before the barrier (they do not depend on
     // V[j+1]); V[j+1] is read through L2 (other CTAs wrote it).
     constexpr int RW = ACH / 8;   // rows per warp (8 warps)
@@ -729,10 +729,10 @@ __global__ void __launch_bounds__(256) k_arn_step_coop(Arnoldi a) {
         for (int u = 0; u < RW; ++u) xv[u] = r0 + u < a.n ? __ldcg(x + pc[u]) : 0.0;
 #pragma unroll
         for (int u = 0; u < RW; ++u) {
-            double v = (double)pv[u] * xv[u];
+            float v = pv[u] * (float)xv[u];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0 && r0 + u < a.n) z[r0 + u] = v;
+            if (lane == 0 && r0 + u < a.n) z[r0 + u] = (double)v;
         }
     }
 }

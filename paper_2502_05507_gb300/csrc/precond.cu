@@ -264,8 +264,10 @@ __global__ void __launch_bounds__(32 * RAS_WARPS) k_ras_rows(const int* __restri
 }
 
 // y = M^{-1} x for one batch row per blockIdx.y: one warp per row, lane q
-// takes slot q (row-major slots, float values, float64 products), a
-// shuffle tree sums them
+// takes slot q (row-major slots), a float32 product and a float32 shuffle
+// tree (a float64 warp instruction holds a GB300 sub-partition's FP64 pipe
+// for ~64 cycles; the inner float32 solves that apply M^{-1} round z to
+// float32 anyway), the sum stored as float64
 __global__ void __launch_bounds__(256) k_precond_apply(const int* __restrict__ col,
                                                        const float* __restrict__ val, long long n, const double* in,
                                                        long long in_stride, const int* row, long long row_stride,
@@ -277,10 +279,10 @@ __global__ void __launch_bounds__(256) k_precond_apply(const int* __restrict__ c
     const int lane = threadIdx.x & 31;
     const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long r = w0; r < n; r += nw) {
-        double v = (double)val[r * MAXR + lane] * x[col[r * MAXR + lane]];   // unused slots: 0 x[r]
+        float v = val[r * MAXR + lane] * (float)x[col[r * MAXR + lane]];   // unused slots: 0 x[r]
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) y[r] = v;
+        if (lane == 0) y[r] = (double)v;
     }
 }
 
