@@ -232,6 +232,10 @@ int bae_boundary_points(const bae_problem* prob, double* xyz);
 int bae_classification(const bae_problem* prob, uint8_t* flags, int32_t* gm_idx,
                        int32_t* partner, double* t);
 
+/* mask[N^3] = 1 on M+ (phi < 0, the nodes where u is the solution of eq.
+ * [discrete]), 0 elsewhere; host or device pointer. */
+int bae_interior_mask(const bae_problem* prob, uint8_t* mask);
+
 /* ---------------------------------------- the potential apply (hot path) */
 
 /* v = K q on the whole N^3 grid, K the problem's layer potential

@@ -98,6 +98,7 @@ def lib():
             "bae_problem_sizes": (_I, [_P, _P, _P, _P]),
             "bae_problem_unknowns": (_I, [_P, _P]),
             "bae_gamma_plus": (_I, [_P, _P]),
+            "bae_interior_mask": (_I, [_P, _P]),
             "bae_problem_plane_range": (_I, [_P, _P, _P]),
             "bae_boundary_points": (_I, [_P, _P]),
             "bae_classification": (_I, [_P, _P, _P, _P, _P]),
@@ -126,7 +127,7 @@ def lib():
 EXPORTED = ["bae_version", "bae_last_error", "bae_default_options", "bae_launch_count", "bae_set_conv_schedule", "bae_profile_start",
             "bae_profile_stop", "bae_ctx_create", "bae_ctx_destroy",
             "bae_lgf_table", "bae_lgf_spectrum", "bae_problem_create", "bae_problem_destroy",
-            "bae_problem_sizes", "bae_problem_unknowns", "bae_gamma_plus", "bae_problem_plane_range", "bae_boundary_points", "bae_classification", "bae_potential_apply",
+            "bae_problem_sizes", "bae_problem_unknowns", "bae_gamma_plus", "bae_interior_mask", "bae_problem_plane_range", "bae_boundary_points", "bae_classification", "bae_potential_apply",
             "bae_potential_apply_noalloc",
             "bae_boundary_apply", "bae_particular", "bae_solve", "bae_solve_batched", "bae_server_create",
             "bae_server_submit", "bae_server_poll", "bae_server_density", "bae_server_release", "bae_server_clock",
@@ -301,6 +302,12 @@ class Problem:
         t = np.empty(self.n_gm, np.float64)
         _check(lib().bae_classification(self._h, _ptr(flags), _ptr(gm), _ptr(partner), _ptr(t)))
         return dict(flags=flags, gm=gm, partner=partner, t=t)
+
+    def interior_mask(self):
+        """M+ as a bool array (N, N, N)."""
+        m = np.empty((self.N,) * 3, np.uint8)
+        _check(lib().bae_interior_mask(self._h, _ptr(m)))
+        return m.astype(bool)
 
     def gamma_plus(self):
         """Linear indices of gamma+ (lexicographic)."""

@@ -1365,6 +1365,24 @@ int bae_classification(const bae_problem* P, uint8_t* flags, int32_t* gm_idx, in
     });
 }
 
+int bae_interior_mask(const bae_problem* P, uint8_t* mask) {
+    return guarded([&]() -> int {
+        BAE_REQUIRE(P && mask, BAE_ERR_INVALID_ARG, "null argument");
+        check_device(P->ctx);
+        cudaStream_t st = P->ctx->stream;
+        const long long n3 = P->n3();
+        if (is_device_ptr(mask)) {
+            mask_bit(P->geo.flags, n3, 1, mask, st);
+        } else {
+            uint8_t* d = reinterpret_cast<uint8_t*>(P->ctx->ws.out_u.need((n3 + 7) / 8));
+            mask_bit(P->geo.flags, n3, 1, d, st);
+            BAE_CUDA(cudaMemcpyAsync(mask, d, (size_t)n3, cudaMemcpyDeviceToHost, st));
+        }
+        BAE_CUDA(cudaStreamSynchronize(st));
+        return BAE_OK;
+    });
+}
+
 int bae_problem_unknowns(const bae_problem* P, int64_t* n) {
     return guarded([&]() -> int {
         BAE_REQUIRE(P && n, BAE_ERR_INVALID_ARG, "null argument");

@@ -102,6 +102,9 @@ void direct_rows(const W* w, long long w_stride, const double* x, long long x_st
                  long long x_row_stride, const int* gp, const int* pu, const double* t, long long n_gm, long long n_unk,
                  int nb, const int* active, Y* y, long long y_stride, cudaStream_t st);
 
+// out[x] = (flags[x] & bit) != 0 for x < n
+void mask_bit(const uint8_t* flags, long long n, uint8_t bit, uint8_t* out, cudaStream_t st);
+
 // u[b][gm[r]] = q[b][r] for r < n
 void scatter_gm(const double* q, long long q_stride, const int* gm, long long n, int nb, double* u, long long n3,
                 cudaStream_t st);

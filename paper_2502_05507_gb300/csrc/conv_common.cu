@@ -206,6 +206,16 @@ void closure_gather(const T* v, long long v_stride, const int* gm, const int* pa
     BAE_LAUNCH(kname<T>("closure_gather.f32", "closure_gather.f64", "closure_gather.f64"), st, k_closure_gather<T><<<grid, 256, 0, st>>>(v, v_stride, gm, partner, t, n, out, out_stride, active));
 }
 
+__global__ void k_mask_bit(const uint8_t* __restrict__ flags, long long n, uint8_t bit, uint8_t* __restrict__ out) {
+    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n; x += (long long)gridDim.x * blockDim.x)
+        out[x] = (flags[x] & bit) ? 1 : 0;
+}
+
+void mask_bit(const uint8_t* flags, long long n, uint8_t bit, uint8_t* out, cudaStream_t st) {
+    const int grid = (int)(ceil_div(n, 256) < 2432 ? ceil_div(n, 256) : 2432);
+    BAE_LAUNCH("k_mask_bit", st, k_mask_bit<<<grid, 256, 0, st>>>(flags, n, bit, out));
+}
+
 template <typename W, typename Y>
 void direct_rows(const W* w, long long w_stride, const double* x, long long x_stride, const int* x_row,
                  long long x_row_stride, const int* gp, const int* pu, const double* t, long long n_gm, long long n_unk,

@@ -39,6 +39,7 @@ def test_gamma_plus_and_unknowns(ctx, make):
     try:
         cls = grid.classify(P.phi, P.grid.h, P.grid.origin)
         assert np.array_equal(prob.gamma_plus(), cls.gp_idx)
+        assert np.array_equal(prob.interior_mask(), cls.inside)
         assert prob.n_unknowns == cls.gm_idx.size + cls.gp_idx.size
     finally:
         prob.close()
