@@ -544,8 +544,7 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
     double* scal = ws.arnScal.need((long long)nb * 5);
     a.est = scal;
     a.target = scal + nb;
-    a.inv = scal + 2 * nb;
-    double* nrm2 = scal + 3 * nb;
+    a.inv = scal + 2 * nb;   // scal + 3 nb: spare
     int* ibuf = ws.arnI.need((long long)nb * 6 + 1);
     a.flag = ibuf;
     a.ncols = ibuf + nb;

@@ -9,7 +9,6 @@ namespace bae {
 namespace {
 
 constexpr int CH = 512;        // elements per chunk
-constexpr int ICH = 16;        // basis vectors per CTA in the dot kernel
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
