@@ -216,7 +216,7 @@ def run_ours(args, rank, world, dev):
     prob0.close()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
 
-    def step(precision, use_graphs=True):
+    def step(precision, use_graphs=False):
         pr = Problem(ctx, phi, P.grid.h, P.grid.origin, P.kappa2, "double")
         q, u, st = pr.solve(f, g, tol=TOL, precision=precision, use_graphs=use_graphs)
         pr.close()
@@ -267,10 +267,10 @@ def run_ours(args, rank, world, dev):
         ctx.close()
         return out if rank == 0 else None
 
-    # per-kernel device times: the same steps again, launched kernel by
-    # kernel (use_graphs=False: the same kernels outside CUDA graphs) with
-    # every launch bracketed by CUDA events; kept out of the timed region,
-    # where the event records would add host time to every step
+    # per-kernel device times: the same steps again (launched kernel by
+    # kernel, as in the timed region) with every launch bracketed by CUDA
+    # events; kept out of the timed region, where the event records would
+    # add host time to every step
     profile_start(60 * max(l1 - l0, 1) // max(args.steps, 1) + 5000)
     for k in range(min(args.steps, 5)):
         _flush_l2(flush)

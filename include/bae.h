@@ -79,9 +79,11 @@ typedef struct bae_options {
     double inner_tol;    /* inner float32 GMRES reduction per step, default 1e-5;
                             the step that can reach tol aims at 0.3 tol ||b|| */
     int    use_graphs;   /* 1: each Arnoldi step (apply, CGS2, Givens) is captured
-                            once as a CUDA graph and replayed; 0: launched
-                            kernel by kernel (same kernels, for per-kernel
-                            timing). Default 1. */
+                            as a CUDA graph once per solve and replayed; 0:
+                            launched kernel by kernel with programmatic
+                            launch overlap (same kernels). Default 0: per
+                            solve, the capture costs more than the launches
+                            it saves (measured on the bench workloads). */
     int    residual_precision;  /* BAE_MIXED only: arithmetic of the particular
                             solution, the refinement residuals and the
                             reconstruction, BAE_DF64 (default) or BAE_FP64 */

@@ -339,7 +339,7 @@ class Problem:
         _check(lib().bae_particular(self._h, _PREC[precision], _ptr(f), _ptr(out)))
         return out
 
-    def _opts(self, tol, precision, max_iter, restart, max_refine, inner_tol, use_graphs=True,
+    def _opts(self, tol, precision, max_iter, restart, max_refine, inner_tol, use_graphs=False,
               residual_precision=None, precond=None):
         o = Options()
         lib().bae_default_options(ctypes.byref(o))
@@ -361,7 +361,7 @@ class Problem:
         return o
 
     def solve(self, f, g, tol=1e-10, precision="fp64", max_iter=None, restart=None, max_refine=None,
-              inner_tol=None, density=None, u=None, allow_not_converged=False, use_graphs=True,
+              inner_tol=None, density=None, u=None, allow_not_converged=False, use_graphs=False,
               residual_precision=None, precond=None):
         """Returns (density, u, stats dict). f (N^3) and g (n_gm) may be
         torch CUDA tensors or numpy arrays; outputs follow f's kind."""
@@ -377,7 +377,7 @@ class Problem:
         return density, u, st.as_dict()
 
     def solve_batched(self, f, g, tol=1e-10, precision="fp64", max_iter=None, restart=None, max_refine=None,
-                      inner_tol=None, density=None, u=None, allow_not_converged=False, use_graphs=True,
+                      inner_tol=None, density=None, u=None, allow_not_converged=False, use_graphs=False,
                       residual_precision=None, precond=None):
         """f [nrhs, N, N, N], g [nrhs, n_gm]; returns (density, u, [stats])."""
         f = _as_f64(f)

@@ -1171,7 +1171,7 @@ void bae_default_options(bae_options* o) {
     o->precision = BAE_FP64;
     o->max_refine = 8;
     o->inner_tol = 1e-5;
-    o->use_graphs = 1;
+    o->use_graphs = 0;
     o->residual_precision = BAE_DF64;
     o->precond = 1;
 }
