@@ -30,7 +30,9 @@ Readings (paper garbled or silent):
 
 Parity: pinned (tests/test_oracle_lgf.py): Watson closed form, lattice
 identity, symmetry, far-field expansion, and for s > 0 the periodic
-trapezoid sum of Section 2.2.
+trapezoid sum of Section 2.2; the closed-form periodic spectrum against the
+spectrum of the Bessel table where its applicability rule holds, and its
+failure where it does not.
 """
 from __future__ import annotations
 
@@ -176,6 +178,33 @@ def far_field(n) -> float:
           - 244 * (k * k * j ** 6 + l * l * j ** 6 + k ** 6 * j * j + l ** 6 * j * j + k * k * l ** 6 + k ** 6 * l * l)
           + 23 * (j ** 8 + k ** 8 + l ** 8))
     return 1.0 / (4 * math.pi * r) + t2 / (16 * math.pi * r ** 7) + t3 / (128 * math.pi * r ** 13)
+
+
+def periodic_decay(s: float) -> float:
+    """mu with cosh(mu) = 1 + s/2: G_s decays like exp(-mu |n|) along an
+    axis (the slowest direction) for s > 0."""
+    return math.acosh(1.0 + 0.5 * s) if s > 0 else 0.0
+
+
+def periodic_spectrum_applies(N: int, s: float) -> bool:
+    """The (2N)-periodic Green's function equals the even embedding of G_s
+    on the (2N)^3 box up to the images at distance >= N: its deviation,
+    summed over the box, is below (2N)^3 exp(-mu N); the closed form is used
+    when that is below 1e-14 (Section 2.2, the sigma > 0 trapezoid rule
+    with M = 2N)."""
+    return s > 0 and (2 * N) ** 3 * math.exp(-periodic_decay(s) * N) < 1e-14
+
+
+def periodic_spectrum(N: int, s: float) -> np.ndarray:
+    """The real spectrum of the (2N)-periodic Green's function, i.e. the
+    2N-point trapezoid rule of the Fourier integral eq. [lgf] read in
+    frequency space: 1 / (6 + s - 2 sum_i cos(pi k_i / N)) on the (2N, 2N,
+    N + 1) half spectrum (the layout of potentials.lgf_spectrum)."""
+    k = np.arange(2 * N)
+    c = np.cos(np.pi * k / N)
+    c3 = c[: N + 1]
+    sym = 6.0 + s - 2.0 * (c[:, None, None] + c[None, :, None] + c3[None, None, :])
+    return 1.0 / sym
 
 
 def periodic_trapezoid(M: int, s: float) -> np.ndarray:

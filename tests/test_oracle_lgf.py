@@ -104,3 +104,27 @@ def test_positive_and_decreasing(table16_s):
     v = table16_s.cube
     assert np.all(v > 0)
     assert np.all(np.diff(v[:, 0, 0]) < 0)
+
+
+@pytest.mark.parametrize("N,s", [(16, 25.0), (32, 9.0), (8, 200.0)])
+def test_periodic_spectrum_equals_table_spectrum(N, s):
+    # large s: the (2N)-periodic Green's function (closed-form spectrum, the
+    # 2N-point trapezoid rule of Section 2.2) is the embedded free-lattice
+    # G_s up to exp(-mu N) images, far below round-off
+    from oracle import potentials as pot
+    assert lgf.periodic_spectrum_applies(N, s)
+    ref = pot.lgf_spectrum(lgf.LGFTable(N, s))
+    got = lgf.periodic_spectrum(N, s)
+    assert got.shape == ref.shape
+    assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("N,s", [(16, 0.04), (32, 0.5)])
+def test_periodic_spectrum_rejected_for_slow_decay(N, s):
+    # small s: G_s has not decayed within the box, the images matter, and the
+    # rule keeps the table route
+    from oracle import potentials as pot
+    assert not lgf.periodic_spectrum_applies(N, s)
+    ref = pot.lgf_spectrum(lgf.LGFTable(N, s))
+    got = lgf.periodic_spectrum(N, s)
+    assert np.max(np.abs(got - ref)) > 1e-8 * np.max(np.abs(ref))
