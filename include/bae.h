@@ -180,7 +180,11 @@ int bae_lgf_table(bae_ctx* ctx, int N, double s, double* values);
 /* The real spectrum of G_s embedded evenly in the (2N)^3 periodic box
  * (offset N set to 0), on the octant 0 <= k_i <= N: ghat[(k1 (N+1) + k2)(N+1)
  * + k3] = sum_n Gemb(n) cos(pi k.n / N), unscaled. (N+1)^3 doubles. N must be
- * a power of two in [8, 256]. */
+ * a power of two in [8, 256]. When (2N)^3 exp(-mu N) < 1e-14 (cosh mu =
+ * 1 + s/2: G_s has decayed far below round-off within the box) it is the
+ * closed-form spectrum of the (2N)-periodic Green's function,
+ * 1 / (6 + s - 2 sum cos(pi k_i / N)) (the 2N-point trapezoid rule of
+ * Section 2.2), equal to the embedded one to round-off. */
 int bae_lgf_spectrum(bae_ctx* ctx, int N, double s, double* ghat);
 
 /* -------------------------------------------------- problem (Algorithm 1) */

@@ -284,6 +284,21 @@ __global__ void k_cos_pass(const double* __restrict__ in, double* __restrict__ o
     }
 }
 
+// The spectrum of the (2N)-periodic Green's function in closed form, i.e.
+// the 2N-point trapezoid rule of the Fourier integral eq. [lgf] read in
+// frequency space (Section 2.2, sigma > 0): scale / (6 + s - 2 sum_i
+// cos(pi k_i / N)) on the octant 0 <= k_i <= N.
+__global__ void k_periodic_spectrum(int N, double s, double scale, double* g64, float* g32) {
+    const long long N1 = N + 1, n3 = N1 * N1 * N1;
+    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n3; x += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(x / (N1 * N1)), j = (int)((x / N1) % N1), k = (int)(x % N1);
+        const double c = cospi((double)i / N) + cospi((double)j / N) + cospi((double)k / N);
+        const double v = scale / (6.0 + s - 2.0 * c);
+        g64[x] = v;
+        if (g32) g32[x] = (float)v;
+    }
+}
+
 __global__ void k_scale_out(const double* in, long long n, double scale, double* g64, float* g32) {
     for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n; x += (long long)gridDim.x * blockDim.x) {
         const double v = in[x] * scale;
@@ -334,12 +349,27 @@ void lgf_table(int N, double s, double* out, cudaStream_t st) {
     table_into(N, s, out, st);
 }
 
+bool periodic_spectrum_applies(int N, double s) {
+    if (!(s > 0.0)) return false;
+    const double mu = std::acosh(1.0 + 0.5 * s);   // G_s ~ exp(-mu |n|) along an axis
+    return std::pow(2.0 * N, 3) * std::exp(-mu * N) < 1e-14;
+}
+
 void lgf_spectrum(int N, double s, double scale, double* g64, float* g32, cudaStream_t st) {
     BAE_REQUIRE(is_pow2(N) && N >= 8 && N <= 256, BAE_ERR_INVALID_ARG,
                 "lgf_spectrum: N must be a power of two in [8, 256]");
     BAE_REQUIRE(std::isfinite(s) && s >= 0.0, BAE_ERR_INVALID_ARG, "lgf_spectrum: s must be finite and >= 0");
     const long long N1 = N + 1;
     const long long n3 = N1 * N1 * N1;
+    if (periodic_spectrum_applies(N, s)) {
+        // the images of the (2N)-periodic Green's function are below
+        // round-off: no table, no cosine transform
+        BAE_LAUNCH("k_periodic_spectrum", st,
+                   k_periodic_spectrum<<<(int)std::min<long long>((n3 + 255) / 256, 152LL * 16), 256, 0, st>>>(
+                       N, s, scale, g64, g32));
+        BAE_CUDA(cudaStreamSynchronize(st));
+        return;
+    }
     const long long ntri = (long long)N * (N + 1) * (N + 2) / 6;
     DevBuf<double> tab(ntri, st), c0(n3, st), c1(n3, st), Cm(N1 * N, st);
     table_into(N, s, tab.p, st);

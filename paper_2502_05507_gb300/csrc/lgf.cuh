@@ -12,6 +12,11 @@ void lgf_table(int N, double s, double* out, cudaStream_t st);
 // Octant spectrum of G_s evenly embedded in (2N)^3 (offset N set to 0):
 // ghat[(k1 (N+1) + k2)(N+1) + k3] = sum_n Gemb(n) cos(pi k.n / N), times
 // `scale`. Writes float64 into g64 and, if g32 is not null, float32 into g32.
+// Whether the spectrum of the (2N)-periodic Green's function (closed form)
+// equals the embedded G_s to round-off: (2N)^3 exp(-mu N) < 1e-14 with
+// cosh(mu) = 1 + s/2; lgf_spectrum then skips the table.
+bool periodic_spectrum_applies(int N, double s);
+
 void lgf_spectrum(int N, double s, double scale, double* g64, float* g32, cudaStream_t st);
 
 // Twiddle tables exp(-2 pi i m / L), m < L, on the device.

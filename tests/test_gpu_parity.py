@@ -54,8 +54,10 @@ def test_lgf_table_full_size_sampled(ctx):
             assert abs(got[i] - ref) <= 1e-13 * abs(ref) + 1e-17, (tri[i], got[i], ref)
 
 
-@pytest.mark.parametrize("N,s", [(8, 0.0), (16, 10.0 / 256.0), (32, 0.0)])
+@pytest.mark.parametrize("N,s", [(8, 0.0), (16, 10.0 / 256.0), (32, 0.0), (16, 25.0), (32, 9.0)])
 def test_lgf_spectrum_matches_oracle(ctx, N, s):
+    # (16, 25) and (32, 9): the closed-form periodic spectrum on the GPU
+    # against the spectrum of the oracle's Bessel table
     got = ctx.lgf_spectrum(N, s)
     ref = OP.lgf_spectrum(OL.LGFTable(N, s))[: N + 1, : N + 1, :]
     assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
@@ -274,3 +276,23 @@ def test_solve_errors_and_not_converged(ctx):
     assert st["iterations"] == 3 and st["rel_residual"] > 1e-10
     assert torch.isfinite(u).all()
     prob.close()
+
+
+def test_large_kappa_solve_matches_fd(ctx):
+    # kappa^2 = 2304 at N = 32 (s = 9): the spectrum comes from the closed form
+    import torch
+    from oracle import fd
+    from paper_2502_05507_gb300 import Problem
+    P = W.sphere_exp(32, kappa2=2304.0)
+    prob = Problem(ctx, torch.from_numpy(P.phi).cuda(), P.grid.h, P.grid.origin, P.kappa2, "double")
+    try:
+        cls = OG.classify(P.phi, P.grid.h, P.grid.origin)
+        gv = P.g_at(np.asarray(prob.boundary_points()))
+        for prec in ("fp64", "mixed"):
+            q, u, st = prob.solve(torch.from_numpy(P.f()).cuda(), torch.from_numpy(gv).cuda(), tol=1e-10,
+                                  precision=prec)
+            ufd = fd.solve_fd(cls, P.f(), gv, P.grid.h, P.kappa2 * P.grid.h ** 2)
+            m = cls.nplus
+            assert np.max(np.abs(u.cpu().numpy()[m] - ufd[m])) <= 1e-8 * np.max(np.abs(ufd[m])), (prec, st)
+    finally:
+        prob.close()
