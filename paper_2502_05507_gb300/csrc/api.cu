@@ -1292,6 +1292,14 @@ int bae_problem_create(bae_ctx* ctx, int N, double h, const double origin[3], co
         }
         P->spec = ctx->spectrum(N, P->s);
         ctx->twiddles(2 * N);   // built here so that later applies allocate nothing
+        // the Schwarz rows of the default (mixed, preconditioned) solve, built
+        // on the side stream from here on; a solve waits for them only when it
+        // uses them
+        BAE_CUDA(cudaEventRecord(ctx->fork_ev, ctx->stream));
+        BAE_CUDA(cudaStreamWaitEvent(ctx->side, ctx->fork_ev, 0));
+        build_precond(P->geo, P->s, P->spec->near, P->pre, ctx->side);
+        BAE_CUDA(cudaEventRecord(ctx->join_ev, ctx->side));
+        P->pre.pending = true;
         if (P->direct()) {
             const long long nu = P->geo.n_unk;
             std::vector<int> io(nu);
