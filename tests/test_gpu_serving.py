@@ -55,3 +55,30 @@ def test_server_mix_equals_alone(slots, budget):
     for t in tickets:
         srv.release(t)
     srv.close()
+
+
+def test_server_direct_formulation_equals_alone():
+    # a direct-formulation request: its density is u on gamma- then gamma+
+    # (n_gm + n_gp values) and the result matches the same solve alone
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2502_05507_gb300 import Context, Problem, Server
+    P = W.torus_helmholtz(32, kappa2=10.0)
+    srv = Server(0, slots=2, hbm_budget_bytes=64 << 30)
+    t = srv.submit(P.phi, P.grid.h, P.grid.origin, P.f(), P.g_at, kappa2=P.kappa2, layer="direct",
+                   precision="mixed")
+    r = srv.poll(t)
+    d = srv.density(t)
+    assert r["status"] == 0, r
+    ctx = Context(0)
+    prob = Problem(ctx, torch.from_numpy(P.phi).cuda(), P.grid.h, P.grid.origin, P.kappa2, "direct")
+    g = torch.from_numpy(P.g_at(prob.boundary_points())).cuda()
+    q1, u1, st1 = prob.solve(torch.from_numpy(P.f()).cuda(), g, tol=1e-10, precision="mixed")
+    assert d.size == prob.n_unknowns == prob.n_gm + prob.n_gp
+    assert np.array_equal(d, q1.cpu().numpy())
+    assert np.array_equal(r["u"], u1.cpu().numpy())
+    prob.close()
+    ctx.close()
+    srv.release(t)
+    srv.close()
