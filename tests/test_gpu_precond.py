@@ -80,3 +80,29 @@ def test_precond_batched_equals_alone(ctx):
             assert stb[b]["iterations"] == st1["iterations"]
     finally:
         prob.close()
+
+
+def test_problems_destroyed_while_their_rows_build(ctx):
+    # the Schwarz rows start on a side stream at problem creation: problems
+    # closed at once, or solved without them (float64), must leave the
+    # context usable and the next preconditioned solve unchanged
+    import torch
+    from paper_2502_05507_gb300 import Problem
+    P = W.torus_helmholtz(64, kappa2=10.0)
+    phi = torch.from_numpy(P.phi).cuda()
+    f = torch.from_numpy(P.f()).cuda()
+    for _ in range(8):
+        Problem(ctx, phi, P.grid.h, P.grid.origin, P.kappa2, "double").close()
+    prob = Problem(ctx, phi, P.grid.h, P.grid.origin, P.kappa2, "double")
+    g = torch.from_numpy(P.g_at(prob.boundary_points())).cuda()
+    _, u64, st64 = prob.solve(f, g, tol=1e-10, precision="fp64")
+    prob.close()
+    outs = []
+    for _ in range(2):
+        prob = Problem(ctx, phi, P.grid.h, P.grid.origin, P.kappa2, "double")
+        _, u, st = prob.solve(f, g, tol=1e-10, precision="mixed", precond=1)
+        outs.append((u.cpu().numpy(), st))
+        prob.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert outs[0][1]["iterations"] == outs[1][1]["iterations"]
+    assert np.max(np.abs(outs[0][0] - u64.cpu().numpy())) <= 1e-8 * np.max(np.abs(u64.cpu().numpy()))
