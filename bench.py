@@ -1,17 +1,25 @@
 """Benchmark of the BAE hot path on GB300.
 
-Workload (default): modified Helmholtz kappa^2 = 10 on the torus R = 0.5,
-r = 0.2 in [-1,1]^3, N = 128 (h = 1/64), u = sin(2x) cos(y) exp(z), double
-layer, GMRES tolerance 1e-10. One step = one full solve of Algorithm 1 for
-that problem: classification from phi (the LGF spectrum per (N, kappa^2 h^2)
-is cached by the context, as the numerical section reuses tables), the
-particular solution, the GMRES solve with float32 convolutions inside float64
-iterative refinement, and the volume reconstruction. Inputs are synthetic
-and resident in device memory; the L2 cache is flushed between steps.
+Headline workload (default, `--workload batched64`): 64 right-hand sides
+u_k = exp(a_k . x) (a_k seeded unit vectors) of the Poisson problem on the
+torus R = 0.5, r = 0.2 in [-1,1]^3, N = 128 (h = 1/64), double layer, GMRES
+tolerance 1e-10. One step = one batched solve of Algorithm 1 for the 64
+right-hand sides: classification from phi (the LGF spectrum per
+(N, kappa^2 h^2) is cached by the context, as the numerical section reuses
+tables), the particular solutions, the batched GMRES with float32
+convolutions inside iterative refinement whose residuals use the
+double-float (about 48-bit) apply, float64 Gram-Schmidt and Givens, and the
+volume reconstruction. Inputs are synthetic and resident in device memory
+(1.1 GB of f, larger than the L2); the L2 is also flushed between steps.
+
+Extra keys of the same line: the single right-hand side kappa^2 = 10 torus
+(N = 128) and the N = 256 star table (kappa^2 in {0, 1, 100}, single and
+double layer), each with its own timing and error against the exact
+solution.
 
 Prints one JSON line (rank 0). `--impl reference` times the CPU oracle on
 the host cores instead. Multi-GPU (torchrun): independent replicas, one
-problem per rank, no collective on the data path ("scaling": "weak").
+batched problem per rank, no collective on the data path ("scaling": "weak").
 """
 from __future__ import annotations
 
@@ -19,6 +27,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import subprocess
 import sys
 import threading
@@ -33,8 +42,14 @@ METRIC = "BAE solves/s + p50/p99 latency at 1e-8 err; LGF-conv GB/s vs HBM peak"
 UNIT = "solves/s"
 TOL = 1e-10
 N = 128
-KAPPA2 = 10.0
-WORKLOAD = "torus R=0.5 r=0.2, kappa^2=10, N=128 (h=1/64), double layer, GMRES tol 1e-10"
+NRHS = 64
+WORKLOAD = ("64 right-hand sides u_k = exp(a_k.x) (a_k = normalised default_rng(3) normals), Poisson, "
+            "torus R=0.5 r=0.2 in [-1,1]^3, N=128 (h=1/64), double layer, GMRES tol 1e-10, one batched solve "
+            "per step")
+DTYPE_MIXED = "f32 conv + double-float (~48-bit) residual applies + f64 Gram-Schmidt/Givens"
+# nominal float32 lane rate from the unit counts and the clock: 152 SMs x
+# 128 FP32 lanes x 2.07 GHz (an FMA is one lane operation)
+FP32_LANE_PEAK_T = 152 * 128 * 2.07e9 / 1e12
 
 
 def _peaks():
@@ -44,6 +59,26 @@ def _peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+# Arm CPU part numbers of /proc/cpuinfo that the GPU hosts may report
+_ARM_PARTS = {"0xd4f": "Arm Neoverse-V2 (NVIDIA Grace)", "0xd40": "Arm Neoverse-V1", "0xd0c": "Arm Neoverse-N1",
+              "0xd49": "Arm Neoverse-N2", "0xd8f": "Arm Neoverse-V3"}
+
+
+def _cpu_model():
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key, _, val = line.partition(":")
+                key = key.strip().lower()
+                if key == "model name":
+                    return val.strip()
+                if key == "cpu part":
+                    return _ARM_PARTS.get(val.strip(), "Arm CPU part " + val.strip())
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
 
 
 # ------------------------------------------------------------------ clocks
@@ -98,12 +133,13 @@ class ClockSampler:
 
 
 # ------------------------------------------------------ roofline arithmetic
-def kernel_model(n, pb, n_gm, npl=None):
-    """Algorithmic (bytes, flops) of one launch of each convolution pass for
-    one right-hand side at grid size n, element precision pb bytes (complex
-    = 2 pb), when the solve transforms npl of the n x-planes (the planes that
-    hold sources or read-back nodes; all n if None). FFT flops use the
-    5 L log2 L convention per complex transform of length L = 2n; the
+def kernel_model(n, pb, n_gm, npl=None, nb=1):
+    """Algorithmic (bytes, flops) per right-hand side of one launch of each
+    convolution pass at grid size n, element precision pb bytes (complex =
+    2 pb), when the solve transforms npl of the n x-planes (the planes that
+    hold sources or read-back nodes; all n if None) and nb right-hand sides
+    share the launch (the spectrum is read once per launch). FFT flops use
+    the 5 L log2 L convention per complex transform of length L = 2n; the
     spectral multiply counts 2 flops per element."""
     npl = n if npl is None else npl
     c = 2 * pb
@@ -119,7 +155,7 @@ def kernel_model(n, pb, n_gm, npl=None):
         "conv_kfwd": (A + src, (npl * n / 2) * F),
         "conv_jfwd": (A + B, npl * n * F),
         # i pass: reads and writes the rows of the transformed planes
-        "conv_i": (2 * B + n1 ** 3 * pb, 2 * (2 * n * n) * F + 2.0 * (2 * n * n) * L),
+        "conv_i": (2 * B + n1 ** 3 * pb / nb, 2 * (2 * n * n) * F + 2.0 * (2 * n * n) * L),
         "conv_jinv": (A + B, npl * n * F),
         "conv_kinv": (A + npl * n * n * pb, (npl * n / 2) * F),
         # k and j fused per plane (one CTA, or a cluster): A stays on chip
@@ -130,237 +166,376 @@ def kernel_model(n, pb, n_gm, npl=None):
     }
 
 
+def apply_bytes_min(n, pb, npl, nb=1):
+    """The minimum a float32 (pb = 4) apply must move per right-hand side
+    when the padded field cannot stay on chip: the 2 n^2 npl complex
+    elements of the transformed planes after the xy stage are written once
+    by it, read and written by the i stage and read by the xy^-1 stage
+    (64 n^2 npl bytes); the spectrum octant is read once per launch (shared
+    by the batch) and the float32 potential written on the transformed
+    planes."""
+    c = 2 * pb
+    return 8 * c * n * n * npl + (n + 1) ** 3 * pb / nb + pb * n * n * npl
+
+
 FP64_PEAK_TFLOPS = 1.25   # nominal FP64 rate of GB300 (a probe measured 1.20)
 # double-float kernels run on the float32 pipes: a radix-2 butterfly (10
 # float64-equivalent flops: one complex product, two complex sums) costs 70
 # float32 instructions (a complex product as two fused a b + c d forms of 19,
-# a sum 8), 7 per flop; the float32 instruction rate is half the measured
-# 70.2 TFLOP/s FMA rate
+# a sum 8), 7 per flop
 DF64_OPS_PER_FLOP = 7.0
-FP32_INST_PEAK_T = 35.1
 
 
-# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
-# the default workload's convolution kernels, from one ncu capture of the
-# current kernels (profiles/conv_i_traffic_torus_N128.md); a kernel changed
-# since its capture must be dropped from this table (its traffic is then
-# reported as null)
-NCU_TRAFFIC_TORUS128 = {
-    "conv_i.f32": 33.98e6,
-}
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum)
+# of convolution kernels at the headline workload, from one ncu capture of
+# the current kernels (profiles/); a kernel changed since its capture is
+# dropped from this table (its traffic is then reported as null). Keyed by
+# (kernel, N, right-hand sides per launch).
+NCU_TRAFFIC = {}
 
 
-def roofline_for(name, ms_total, launches, n_gm, hbm, hbm_kind, npl=None):
+def roofline_for(name, ms_total, launches, n, n_gm, hbm, hbm_kind, npl=None, nb=1):
     base, _, prec = name.partition(".")
-    model = kernel_model(N, 4 if prec == "f32" else 8, n_gm, npl)
+    model = kernel_model(n, 4 if prec == "f32" else 8, n_gm, npl, nb)
     if base not in model:
         return None
     nbytes, flops = model[base]
+    nbytes *= nb
+    flops *= nb
     t = (ms_total / launches) / 1000.0
+    common = {"kernel": name, "us_per_launch": t * 1e6, "rhs_per_launch": nb}
     if prec == "df64":
         a = flops * DF64_OPS_PER_FLOP / t / 1e12
-        return {"kernel": name, "bound": "alu", "achieved": a, "peak": FP32_INST_PEAK_T,
-                "unit": "T float32 instructions/s", "frac": a / FP32_INST_PEAK_T, "traffic": None,
-                "peak_kind": "measured float32 FMA probe / 2", "us_per_launch": t * 1e6,
+        return {**common, "bound": "alu", "achieved": a, "peak": FP32_LANE_PEAK_T,
+                "unit": "T float32 lane-ops/s", "frac": a / FP32_LANE_PEAK_T, "traffic": None,
+                "peak_kind": "nominal float32 lane rate (152 SMs x 128 lanes x 2.07 GHz)",
                 "algorithmic_flops_fp64_equiv": flops}
     if prec == "f64":
         a = flops / t / 1e12
-        return {"kernel": name, "bound": "alu", "achieved": a, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+        return {**common, "bound": "alu", "achieved": a, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": a / FP64_PEAK_TFLOPS, "traffic": None, "peak_kind": "nominal FP64 (recipe table)",
-                "us_per_launch": t * 1e6, "algorithmic_flops": flops}
+                "algorithmic_flops": flops}
     a = nbytes / t / 1e9
-    return {"kernel": name, "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
-            "traffic": NCU_TRAFFIC_TORUS128.get(name) if N == 128 else None,
-            "peak_kind": hbm_kind + " HBM copy bandwidth", "us_per_launch": t * 1e6,
-            "algorithmic_bytes": nbytes}
+    return {**common, "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
+            "traffic": NCU_TRAFFIC.get((name, n, nb)), "peak_kind": hbm_kind + " HBM copy bandwidth",
+            "algorithmic_bytes": nbytes, "fp32_flops_5LlogL": flops,
+            "fp32_frac_of_lane_peak_5LlogL": flops / t / 1e12 / (2 * FP32_LANE_PEAK_T)}
 
 
-def aggregate_replicas(local_ms, steps, world, device):
+def kernel_table(prof, top=16):
+    kt = sorted(prof.items(), key=lambda kv: -kv[1][0])
+    tot = sum(v[0] for v in prof.values())
+    return [{"name": k, "ms_total": round(v[0], 3), "launches": v[1],
+             "us_per_launch": round(1000.0 * v[0] / max(v[1], 1), 2),
+             "share": round(v[0] / tot, 4) if tot else None} for k, v in kt[:top]]
+
+
+def apply_summary(prof, n, npl, nb, hbm, suffix=".f32"):
+    """Whole float32 apply: the minimum bytes of apply_bytes_min over the
+    summed time per apply of the passes that ran (either schedule)."""
+    names = [k for k in prof if k.startswith("conv_") and k.endswith(suffix)]
+    ikey = "conv_i" + suffix
+    if ikey not in prof:
+        return None
+    napp = prof[ikey][1]
+    t_apply = sum(prof[k][0] for k in names) / napp / 1000.0
+    nbytes = apply_bytes_min(n, 4, npl, nb) * nb
+    return {"us_per_apply": t_apply * 1e6, "rhs_per_apply": nb, "passes": sorted(k.split(".")[0] for k in names),
+            "min_bytes": nbytes, "GBps": nbytes / t_apply / 1e9, "frac_hbm": nbytes / t_apply / 1e9 / hbm,
+            "bytes_model": "per rhs 64 N^2 npl (xy out 16, i in+out 32, xy^-1 in 16 B per complex element) "
+                           "+ 4 N^2 npl potential out + 4 (N+1)^3 / nb spectrum"}
+
+
+def aggregate_replicas(local_ms, steps, world, device, units_per_step=1):
     """Whole-job throughput of independent replicas: every rank solved
-    `steps` problems in local_ms; the job took the slowest rank's time (a
-    MAX all-reduce, the only collective: the solves exchange nothing)."""
+    `steps` x `units_per_step` problems in local_ms; the job took the slowest
+    rank's time (a MAX all-reduce, the only collective: the solves exchange
+    nothing)."""
     total_ms = float(local_ms)
     if world > 1:
         import torch
         t = torch.tensor([total_ms], device=device, dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(t.item())
-    return steps * world / (total_ms / 1000.0), total_ms
+    return steps * units_per_step * world / (total_ms / 1000.0), total_ms
 
 
 def _flush_l2(buf):
     buf.add_(1.0)
 
 
-def _problem_inputs(P, torch, dev):
-    phi = torch.from_numpy(P.phi).to(dev)
-    f = torch.from_numpy(P.f()).to(dev)
-    return phi, f
+def _timed_loop(step, steps, torch, flush, world=1):
+    """Events around each step on the current stream, the L2 flushed before
+    each; returns per-step ms and the last step's result."""
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    out = None
+    for k in range(steps):
+        _flush_l2(flush)
+        e0[k].record()
+        out = step()
+        e1[k].record()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    return np.array([a.elapsed_time(b) for a, b in zip(e0, e1)]), out
 
 
+def _rel_err(u, ref, mask):
+    return float(np.max(np.abs(u[mask] - ref[mask])) / np.max(np.abs(ref[mask])))
+
+
+# ----------------------------------------------------- headline: batched64
 def run_ours(args, rank, world, dev):
     import torch
     import workloads as W
     from paper_2502_05507_gb300 import Context, Problem, launch_count, profile_start, profile_stop
 
     torch.cuda.set_device(dev)
-    P = W.torus_helmholtz(N, kappa2=KAPPA2)
+    nrhs = args.nrhs
+    dirs = W.torus_batch_dirs(64, seed=3)[:nrhs]
+    probs = [W.torus_poisson_dir(N, a) for a in dirs]
+    P0 = probs[0]
     ctx = Context(dev)
-    phi, f = _problem_inputs(P, torch, dev)
-    prob0 = Problem(ctx, phi, P.grid.h, P.grid.origin, P.kappa2, "double")
-    xs = prob0.boundary_points()
-    g = torch.from_numpy(P.g_at(xs)).to(dev)
-    n_gm = prob0.n_gm
-    plo, phi_ = prob0.plane_range()
+    torch.cuda.set_stream(ctx.stream)   # events, flushes and library work share one stream
+    phi = torch.from_numpy(P0.phi).to(dev)
+    pr0 = Problem(ctx, phi, P0.grid.h, P0.grid.origin, 0.0, "double")
+    xs = np.asarray(pr0.boundary_points())
+    n_gm = pr0.n_gm
+    plo, phi_ = pr0.plane_range()
     npl = phi_ - plo
-    prob0.close()
+    pr0.close()
+    f_h = np.stack([P.f() for P in probs])
+    g_h = np.stack([P.g_at(xs) for P in probs])
+    f = torch.from_numpy(f_h).to(dev)
+    g = torch.from_numpy(g_h).to(dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
 
-    def step(precision, use_graphs=False):
-        pr = Problem(ctx, phi, P.grid.h, P.grid.origin, P.kappa2, "double")
-        q, u, st = pr.solve(f, g, tol=TOL, precision=precision, use_graphs=use_graphs)
+    def step(residual="df64"):
+        pr = Problem(ctx, phi, P0.grid.h, P0.grid.origin, 0.0, "double")
+        out = pr.solve_batched(f, g, tol=TOL, precision="mixed", residual_precision=residual)
         pr.close()
-        return q, u, st
+        return out
 
-    torch.cuda.set_stream(ctx.stream)   # events, flushes and library work share one stream
     for _ in range(max(args.warmup, 0)):
-        step(args.precision)
+        step()
     torch.cuda.synchronize()
 
     # ---------------------------------------------------------- timed region
     clocks = ClockSampler(dev)
     clocks.start()
-    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
     l0 = launch_count()
-    stats = []
-    for k in range(args.steps):
-        _flush_l2(flush)
-        e0[k].record()
-        q, u, st = step(args.precision)
-        e1[k].record()
-        stats.append(st)
-    torch.cuda.synchronize()
+    ms, (q, u, st) = _timed_loop(step, args.steps, torch, flush, world)
     l1 = launch_count()
-    if world > 1:
-        torch.distributed.barrier()
     clk = clocks.stop()
-    ms = np.array([a.elapsed_time(b) for a, b in zip(e0, e1)])
-    value, total_ms = aggregate_replicas(float(ms.sum()), args.steps, world, torch.device("cuda", dev))
+    value, total_ms = aggregate_replicas(float(ms.sum()), args.steps, world, torch.device("cuda", dev), nrhs)
 
+    it = [s["iterations"] for s in st]
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": float(ms.mean()), "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f32 conv + f64 refinement" if args.precision == "mixed"
-           else "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "precision": args.precision, "l2": "flushed between steps (256 MB write)",
+           "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_MIXED, "data": "synthetic",
+           "config": {"workload": WORKLOAD, "rhs_per_step": nrhs, "precision": "mixed (residual double-float)",
+                      "l2": "inputs (1.1 GB of f) larger than L2, and a 256 MB write between steps",
                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
            "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)),
-                          "min": float(ms.min()), "max": float(ms.max())},
-           "solve": {"iterations": int(stats[-1]["iterations"]), "refinements": int(stats[-1]["refinements"]),
-                     "applies_fp32": int(stats[-1]["applies_fp32"]), "applies_fp64": int(stats[-1]["applies_fp64"]),
-                     "rel_residual": stats[-1]["rel_residual"], "n_gm": n_gm},
+                          "min": float(ms.min()), "max": float(ms.max()),
+                          "note": "per batched step; every right-hand side of a step completes with it"},
+           "timed_region_s": float(ms.sum()) / 1000.0,
+           "solve": {"iterations_max": max(it), "iterations_min": min(it),
+                     "refinements_max": max(s["refinements"] for s in st),
+                     "applies_fp32_max": max(s["applies_fp32"] for s in st),
+                     "applies_fp64_accurate_max": max(s["applies_fp64"] for s in st),
+                     "rel_residual_max": max(s["rel_residual"] for s in st), "n_gm": n_gm,
+                     "planes_transformed": npl},
            "gpu_launches": int(l1 - l0), "clocks": clk}
     if rank != 0 or args.only_timed:
         ctx.close()
         return out if rank == 0 else None
+    interior = P0.phi < 0   # M+, where Algorithm 1 defines the solution
+    ud = u.cpu().numpy()
+    out["max_err_vs_exact"] = max(_rel_err(ud[k], probs[k].u_exact(), interior) for k in range(nrhs))
 
-    # per-kernel device times: the same steps again (launched kernel by
-    # kernel, as in the timed region) with every launch bracketed by CUDA
-    # events; kept out of the timed region, where the event records would
-    # add host time to every step
+    # the same steps with float64 residual applies (the north_star form)
+    ms64, (q64, u64, st64) = _timed_loop(lambda: step("fp64"), args.steps, torch, flush)
+    out["mixed_fp64_residual"] = {"value": nrhs * 1000.0 / float(ms64.mean()), "unit": UNIT,
+                                  "ms_per_step": float(ms64.mean()), "steps": args.steps,
+                                  "iterations_max": max(s["iterations"] for s in st64),
+                                  "dtype": "f32 conv + f64 residual applies + f64 Gram-Schmidt/Givens"}
+    u64d = u64.cpu().numpy()
+
+    # per-kernel device times: two more steps with every launch bracketed by
+    # events (kept out of the timed region, where the event records would
+    # add host time to every step)
+    hbm, hbm_kind = _peaks()
     profile_start(60 * max(l1 - l0, 1) // max(args.steps, 1) + 5000)
-    for k in range(min(args.steps, 5)):
+    for _ in range(2):
         _flush_l2(flush)
-        step(args.precision, use_graphs=False)
+        step()
     torch.cuda.synchronize()
     prof = profile_stop()
+    out["kernels"] = kernel_table(prof)
+    dom = next((k["name"] for k in out["kernels"] if k["name"].startswith("conv_")), None)
+    out["roofline"] = roofline_for(dom, prof[dom][0], prof[dom][1], N, n_gm, hbm, hbm_kind, npl, nrhs) \
+        if dom else None
+    out["conv_f32_apply"] = apply_summary(prof, N, npl, nrhs, hbm)
 
-    # ------------------------------------------------------ kernel roofline
-    hbm, hbm_kind = _peaks()
-    kt = sorted(prof.items(), key=lambda kv: -kv[1][0])
-    tot = sum(v[0] for v in prof.values())
-    out["kernels"] = [{"name": k, "ms_total": round(v[0], 3), "launches": v[1],
-                       "share": round(v[0] / tot, 4) if tot else None} for k, v in kt[:14]]
-    dom = next((k for k, _ in kt if k.startswith("conv_")), None)
-    out["roofline"] = roofline_for(dom, prof[dom][0], prof[dom][1], n_gm, hbm, hbm_kind, npl) if dom else None
-    # the float32 i-pass (forward FFT, ghat multiply, inverse FFT) inside the timed region
-    if "conv_i.f32" in prof:
-        out["conv_f32_roofline"] = roofline_for("conv_i.f32", *prof["conv_i.f32"], n_gm, hbm, hbm_kind, npl)
-    # whole float32 apply: algorithmic bytes of the passes that ran / their
-    # summed time per apply (either schedule the autotuner picked)
-    if "conv_i.f32" in prof:
-        napp = prof["conv_i.f32"][1]
-        m = kernel_model(N, 4, n_gm, npl)
-        names = [k for k in prof if k.startswith("conv_") and k.endswith(".f32")]
-        nbytes = sum(m[k.split(".")[0]][0] * prof[k][1] / napp for k in names)
-        t_apply = sum(prof[k][0] for k in names) / napp / 1000.0
-        out["conv_f32_apply"] = {"us": t_apply * 1e6, "passes": sorted(k.split(".")[0] for k in names),
-                                 "algorithmic_bytes": nbytes, "GBps": nbytes / t_apply / 1e9,
-                                 "frac_hbm": nbytes / t_apply / 1e9 / hbm,
-                                 "note": "N=128 buffers fit in the 129 MB L2, so this can exceed HBM peak"}
-
-    # ------------------------------------- other arithmetics, for comparison
-    interior = P.phi < 0   # M+, where Algorithm 1 defines the solution
-    ud = u.cpu().numpy()
+    # the plain float64 GPU form (and double-float throughout) on 8 of the
+    # right-hand sides: solves/s at the same tolerance
     others = {}
-    for label, prec, res in (("fp64", "fp64", None), ("df64", "df64", None), ("mixed_fp64_residual", "mixed", "fp64")):
-        def run():
-            pr = Problem(ctx, phi, P.grid.h, P.grid.origin, P.kappa2, "double")
-            out_ = pr.solve(f, g, tol=TOL, precision=prec, residual_precision=res)
-            pr.close()
-            return out_
-        run()
-        torch.cuda.synchronize()
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        t0.record()
-        qo, uo_, sto = run()
-        t1.record()
-        torch.cuda.synchronize()
-        uu = uo_.cpu().numpy()
-        others[label] = {"solves_per_s": 1000.0 / t0.elapsed_time(t1), "iterations": sto["iterations"],
-                         "applies_fp64_accurate": sto["applies_fp64"], "applies_fp32": sto["applies_fp32"],
-                         "u": uu}
-    uf = others["fp64"]["u"]
-    out["err_mixed_vs_fp64"] = float(np.max(np.abs(ud - uf)[interior]) / np.max(np.abs(uf[interior])))
-    out["other_arithmetic"] = {k: {kk: vv for kk, vv in v.items() if kk != "u"} for k, v in others.items()}
-    out["fp64_solve"] = out["other_arithmetic"]["fp64"]
-
-    # --------------------------------------------------------- e2e (host)
-    phi_h, f_h = P.phi, P.f()
-    g_h = P.g_at(xs.cpu().numpy() if hasattr(xs, "cpu") else xs)
-    e2e_ms = []
-    for k in range(min(args.steps, 8) + 1):
+    for label, prec in (("fp64", "fp64"), ("df64", "df64")):
+        k8 = min(8, nrhs)
+        pr = Problem(ctx, phi, P0.grid.h, P0.grid.origin, 0.0, "double")
+        pr.solve_batched(f[:k8].contiguous(), g[:k8].contiguous(), tol=TOL, precision=prec)
         torch.cuda.synchronize()
         t = time.perf_counter()
-        pr = Problem(ctx, phi_h, P.grid.h, P.grid.origin, P.kappa2, "double")
-        qh, uh, sth = pr.solve(f_h, g_h, tol=TOL, precision=args.precision)
+        qo, uo, sto = pr.solve_batched(f[:k8].contiguous(), g[:k8].contiguous(), tol=TOL, precision=prec)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        pr.close()
+        uo = uo.cpu().numpy()
+        others[label] = {"solves_per_s": k8 / dt, "rhs": k8, "iterations_max": max(s["iterations"] for s in sto),
+                         "u": uo}
+    uf = others["fp64"]["u"]
+    k8 = uf.shape[0]
+    out["err_mixed_vs_fp64_gpu"] = max(_rel_err(ud[k], uf[k], interior) for k in range(k8))
+    out["other_arithmetic"] = {k: {kk: vv for kk, vv in v.items() if kk != "u"} for k, v in others.items()}
+
+    # --------------------------------------------------------- e2e (host)
+    # through the public API with host buffers: phi, f and g copied in and
+    # u and the densities copied out by the library inside every step
+    pinned = [torch.from_numpy(f_h).pin_memory(), torch.from_numpy(g_h).pin_memory(),
+              torch.from_numpy(P0.phi).pin_memory(), torch.empty(f_h.shape, dtype=torch.float64).pin_memory(),
+              torch.empty((nrhs, n_gm), dtype=torch.float64).pin_memory()]
+    f_pin, g_pin, phi_pin, u_pin, q_pin = (t.numpy() for t in pinned)
+    e2e_ms = []
+    for k in range(min(args.steps, 5) + 1):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        pr = Problem(ctx, phi_pin, P0.grid.h, P0.grid.origin, 0.0, "double")
+        pr.solve_batched(f_pin, g_pin, tol=TOL, precision="mixed", density=q_pin, u=u_pin)
         pr.close()
         dt = time.perf_counter() - t
         if k > 0:
             e2e_ms.append(dt * 1000.0)
-    out["e2e"] = {"value": 1000.0 / float(np.mean(e2e_ms)), "unit": UNIT,
-                  "h2d_bytes_per_step": int(phi_h.nbytes + f_h.nbytes + g_h.nbytes),
-                  "d2h_bytes_per_step": int(qh.nbytes + uh.nbytes)}
+    out["e2e"] = {"value": nrhs * 1000.0 / float(np.mean(e2e_ms)), "unit": UNIT,
+                  "h2d_bytes_per_step": int(phi_pin.nbytes + f_pin.nbytes + g_pin.nbytes),
+                  "d2h_bytes_per_step": int(u_pin.nbytes + q_pin.nbytes), "steps": len(e2e_ms),
+                  "host_buffers": "pinned"}
+
+    # --------------------------------------------------- secondary configs
+    if not args.no_extra:
+        out["torus128_kappa10"] = run_torus128_extra(ctx, torch, flush, hbm, hbm_kind)
+        out["star256"] = run_star256_table(ctx, torch)
 
     # --------------------------------------------------------- cpu baseline
     if world == 1 and not args.no_cpu:
-        out["cpu_baseline"], uo = cpu_oracle_solve(P)
-        m = interior
-        out["err_vs_oracle"] = {"mixed": float(np.max(np.abs(ud[m] - uo[m])) / np.max(np.abs(uo[m]))),
-                                "fp64": float(np.max(np.abs(uf[m] - uo[m])) / np.max(np.abs(uo[m]))),
-                                "on": "M+ (interior nodes), max-norm relative"}
+        out["cpu_baseline"], uo = cpu_oracle_solve(probs[0])
+        out["err_vs_oracle"] = {"mixed": _rel_err(ud[0], uo, interior),
+                                "mixed_fp64_residual": _rel_err(u64d[0], uo, interior),
+                                "fp64_gpu": _rel_err(uf[0], uo, interior),
+                                "on": "M+ (interior nodes), max-norm relative, right-hand side 0"}
     ctx.close()
     return out
 
 
+def run_torus128_extra(ctx, torch, flush, hbm, hbm_kind, steps=50, warmup=3):
+    """Single right-hand side: kappa^2 = 10 torus, N = 128, u = sin 2x cos y
+    e^z (mixed precision): solves/s, p50/p99, per-kernel roofline."""
+    import workloads as W
+    from paper_2502_05507_gb300 import Problem, profile_start, profile_stop
+    P = W.torus_helmholtz(N, kappa2=10.0)
+    phi = torch.from_numpy(P.phi).cuda()
+    f = torch.from_numpy(P.f()).cuda()
+    pr0 = Problem(ctx, phi, P.grid.h, P.grid.origin, P.kappa2, "double")
+    g = torch.from_numpy(P.g_at(np.asarray(pr0.boundary_points()))).cuda()
+    n_gm = pr0.n_gm
+    plo, phi_ = pr0.plane_range()
+    pr0.close()
+
+    def step():
+        pr = Problem(ctx, phi, P.grid.h, P.grid.origin, P.kappa2, "double")
+        r = pr.solve(f, g, tol=TOL, precision="mixed")
+        pr.close()
+        return r
+    for _ in range(warmup):
+        step()
+    ms, (q, u, st) = _timed_loop(step, steps, torch, flush)
+    profile_start(20000)
+    for _ in range(3):
+        _flush_l2(flush)
+        step()
+    torch.cuda.synchronize()
+    prof = profile_stop()
+    m = P.phi < 0
+    dom = next((k["name"] for k in kernel_table(prof) if k["name"].startswith("conv_")), None)
+    return {"workload": "torus R=0.5 r=0.2, kappa^2=10, N=128, u=sin2x cos y e^z, double layer, tol 1e-10, "
+                        "one right-hand side", "solves_per_s": 1000.0 / float(ms.mean()), "steps": steps,
+            "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
+            "iterations": st["iterations"], "rel_residual": st["rel_residual"],
+            "max_err_vs_exact": _rel_err(u.cpu().numpy(), P.u_exact(), m),
+            "kernels": kernel_table(prof, 8),
+            "roofline": roofline_for(dom, prof[dom][0], prof[dom][1], N, n_gm, hbm, hbm_kind, phi_ - plo, 1)
+            if dom else None,
+            "conv_f32_apply": apply_summary(prof, N, phi_ - plo, 1, hbm),
+            "note": "N=128 single right-hand side: every buffer of the apply (~45 MB) stays in the 129 MB L2"}
+
+
+def run_star256_table(ctx, torch, reps=3):
+    """N=256 star, kappa^2 in {0, 1, 100}, double vs single layer: GMRES
+    iterations and solves/s (mixed precision), with the float32 apply's
+    bytes per second at this size."""
+    import workloads as W
+    from paper_2502_05507_gb300 import Problem, profile_start, profile_stop
+    hbm, _ = _peaks()
+    rows = []
+    for k2 in (0.0, 1.0, 100.0):
+        for layer in ("double", "single"):
+            P = W.star(256, kappa2=k2, layer=layer)
+            phi = torch.from_numpy(P.phi).cuda()
+            f = torch.from_numpy(P.f()).cuda()
+            pr0 = Problem(ctx, phi, P.grid.h, P.grid.origin, k2, layer)
+            g = torch.from_numpy(P.g_at(np.asarray(pr0.boundary_points()))).cuda()
+            n_gm = pr0.n_gm
+            plo, phi_ = pr0.plane_range()
+            pr0.close()
+
+            def step():
+                pr = Problem(ctx, phi, P.grid.h, P.grid.origin, k2, layer)
+                r = pr.solve(f, g, tol=TOL, precision="mixed", max_iter=2000, restart=400)
+                pr.close()
+                return r
+            step()
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(reps):
+                t = time.perf_counter()
+                q, u, st = step()
+                torch.cuda.synchronize()
+                ts.append(time.perf_counter() - t)
+            row = {"kappa2": k2, "layer": layer, "iterations": st["iterations"],
+                   "solves_per_s": 1.0 / float(np.median(ts)), "ms_p50": 1e3 * float(np.median(ts)),
+                   "rel_residual": st["rel_residual"], "n_gm": n_gm,
+                   "max_err_vs_exact": _rel_err(u.cpu().numpy(), P.u_exact(), P.phi < 0)}
+            if k2 == 0.0 and layer == "double":
+                profile_start(20000)
+                step()
+                torch.cuda.synchronize()
+                prof = profile_stop()
+                row["kernels"] = kernel_table(prof, 10)
+                row["conv_f32_apply"] = apply_summary(prof, 256, phi_ - plo, 1, hbm)
+            rows.append(row)
+    return {"workload": "star r=0.6+0.1 sin5t cos3p, N=256, kappa^2 in {0,1,100}, double vs single layer, "
+                        "u = exp(a.x), tol 1e-10, mixed precision", "table": rows,
+            "solves_per_s_mean": float(np.mean([r["solves_per_s"] for r in rows]))}
+
+
 def cpu_oracle_solve(P):
     """The oracle (FFT route, float64 scipy.fft on every host core) solving
-    the same problem once; the LGF table is built beforehand and not timed
-    (the GPU side caches it too)."""
+    one right-hand side of the workload once; the LGF table is built
+    beforehand and not timed (the GPU side caches it too)."""
     from oracle import lgf as OL
     from oracle import potentials as OP
     from oracle import solve as OS
@@ -374,52 +549,52 @@ def cpu_oracle_solve(P):
     r = OS.solve(P.phi, P.grid.h, P.grid.origin, P.f(), P.g_at, P.kappa2, layer="double", tol=TOL,
                  potential="fft", spectrum=spec, workers=cores)
     dt = time.perf_counter() - t
-    return ({"value": 1.0 / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-             "sample": f"one full oracle solve of the workload (FFT route, {r.iterations} GMRES iterations, "
-                       f"{dt:.1f} s); LGF table build ({t_table:.1f} s) excluded as cached"},
+    return ({"value": 1.0 / dt, "unit": UNIT, "cores": cores, "cpu": _cpu_model(), "kind": "oracle",
+             "sample": f"one full oracle solve of right-hand side 0 of the workload (FFT route, {r.iterations} "
+                       f"GMRES iterations, {dt:.1f} s); LGF table build ({t_table:.1f} s) excluded as cached"},
             r.u)
 
 
 def run_reference(args):
-    """The oracle as the reference arm: each step is a bounded sample, one
-    oracle boundary-operator apply (the unit of a GMRES iteration);
-    solves/s = 1 / (mean apply time x applies per oracle solve), the apply
-    count taken from one untimed full oracle solve of the same workload."""
+    """The oracle as the reference arm, on the headline workload: each step
+    (warm-up or timed) is one full oracle solve (FFT route, float64
+    scipy.fft on all host cores, unpreconditioned MGS GMRES) of one of the 64
+    right-hand sides, in order; solves/s = timed steps / their total time.
+    The LGF table is built once before the steps (cached on both sides)."""
     import workloads as W
-    from oracle import grid as OG
     from oracle import lgf as OL
     from oracle import potentials as OP
     from oracle import solve as OS
     cores = os.cpu_count() or 1
-    P = W.torus_helmholtz(N, kappa2=KAPPA2)
-    s = P.kappa2 * P.grid.h ** 2
-    spec = OP.lgf_spectrum(OL.LGFTable(N, s))
-    full = OS.solve(P.phi, P.grid.h, P.grid.origin, P.f(), P.g_at, P.kappa2, layer="double", tol=TOL,
-                    potential="fft", spectrum=spec, workers=cores)
-    applies = full.iterations + 2
-    cls = OG.classify(P.phi, P.grid.h, P.grid.origin)
-    q = np.random.default_rng(0).standard_normal(cls.gm_idx.size)
+    dirs = W.torus_batch_dirs(64, seed=3)
+    spec = OP.lgf_spectrum(OL.LGFTable(N, 0.0))
+    k = 0
 
-    def apply_once():
-        v = OP.fft_convolve(OP.source_density(cls, q, "double"), spectrum=spec, workers=cores).reshape(-1)
-        return OS.closure_apply(cls, v)
+    def one():
+        nonlocal k
+        P = W.torus_poisson_dir(N, dirs[k % len(dirs)])
+        k += 1
+        t = time.perf_counter()
+        r = OS.solve(P.phi, P.grid.h, P.grid.origin, P.f(), P.g_at, 0.0, layer="double", tol=TOL,
+                     potential="fft", spectrum=spec, workers=cores)
+        return time.perf_counter() - t, r.iterations
 
     for _ in range(args.warmup):
-        apply_once()
-    ts = []
+        one()
+    ts, its = [], []
     for _ in range(args.steps):
-        t = time.perf_counter()
-        apply_once()
-        ts.append(time.perf_counter() - t)
-    per_solve = float(np.mean(ts)) * applies
-    value = 1.0 / per_solve
+        dt, itn = one()
+        ts.append(dt)
+        its.append(itn)
+    total = float(np.sum(ts))
+    value = len(ts) / total if ts else 0.0
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1000.0 * per_solve, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "warmup": args.warmup, "ms_per_step": 1000.0 * total / max(len(ts), 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": WORKLOAD, "precision": "fp64 (oracle)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{args.steps} oracle boundary applies (scipy.fft float64), scaled by "
-                                       f"{applies} applies per oracle solve"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "cpu": _cpu_model(), "kind": "oracle",
+                             "sample": f"each step one full oracle solve of one of the 64 right-hand sides (FFT "
+                                       f"route, {int(np.median(its)) if its else 0} GMRES iterations median)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -439,9 +614,10 @@ def run_sphere32(args):
     P = W.sphere_exp(32)
     ctx = Context(0)
     torch.cuda.set_stream(ctx.stream)
-    phi, f = _problem_inputs(P, torch, 0)
+    phi = torch.from_numpy(P.phi).cuda()
+    f = torch.from_numpy(P.f()).cuda()
     pr0 = Problem(ctx, phi, P.grid.h, P.grid.origin, 0.0, "double")
-    g = torch.from_numpy(P.g_at(pr0.boundary_points())).cuda()
+    g = torch.from_numpy(P.g_at(np.asarray(pr0.boundary_points()))).cuda()
     pr0.close()
 
     def step():
@@ -466,84 +642,31 @@ def run_sphere32(args):
             "iterations": st["iterations"], "max_err_vs_exact": float(np.max(np.abs(u[m] - P.u_exact()[m])))}
 
 
-def run_batched64(args):
-    """64 right-hand sides u_k = exp(a_k . x) on the N=128 Poisson torus, one
-    batched mixed-precision solve per step."""
+def run_torus128(args):
+    """The single right-hand side kappa^2 = 10 torus (N = 128) alone, with
+    the given steps and warm-up."""
     import torch
-    import workloads as W
-    from paper_2502_05507_gb300 import Context, Problem
-    nrhs = args.nrhs
-    dirs = W.torus_batch_dirs(64, seed=3)[:nrhs]
-    probs = [W.torus_poisson_dir(128, a) for a in dirs]
+    from paper_2502_05507_gb300 import Context
     ctx = Context(0)
     torch.cuda.set_stream(ctx.stream)
-    P0 = probs[0]
-    phi = torch.from_numpy(P0.phi).cuda()
-    pr0 = Problem(ctx, phi, P0.grid.h, P0.grid.origin, 0.0, "double")
-    xs = pr0.boundary_points()
-    pr0.close()
-    f = torch.from_numpy(np.stack([P.f() for P in probs])).cuda()
-    g = torch.from_numpy(np.stack([P.g_at(xs) for P in probs])).cuda()
-
-    def step():
-        pr = Problem(ctx, phi, P0.grid.h, P0.grid.origin, 0.0, "double")
-        out = pr.solve_batched(f, g, tol=TOL, precision="mixed")
-        pr.close()
-        return out
-    for _ in range(max(1, args.warmup)):
-        step()
-    ms = []
-    for _ in range(args.steps):
-        (q, u, st), dt = _timed(step, torch)
-        ms.append(dt * 1e3)
-    ms = np.array(ms)
-    u = u.cpu().numpy()
-    m = P0.phi < 0
-    errs = [float(np.max(np.abs(u[k][m] - probs[k].u_exact()[m]))) for k in range(nrhs)]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    hbm, hbm_kind = _peaks()
+    t = run_torus128_extra(ctx, torch, flush, hbm, hbm_kind, steps=args.steps, warmup=args.warmup)
     ctx.close()
-    return {"metric": METRIC, "value": nrhs * 1e3 / ms.mean(), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms.mean(), "higher_is_better": True,
-            "dtype": "f32 conv + df64 refinement",
-            "config": {"workload": f"{nrhs} RHS exp(a_k.x), Poisson torus R=0.5 r=0.2, N=128, one batched solve per step"},
-            "iterations_max": max(s_["iterations"] for s_ in st), "rel_residual_max": max(s_["rel_residual"] for s_ in st),
-            "max_err_vs_exact": max(errs)}
+    return {"metric": METRIC, "value": t["solves_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "dtype": DTYPE_MIXED,
+            "config": {"workload": t["workload"]}, **{k: v for k, v in t.items() if k != "workload"}}
 
 
 def run_star256(args):
-    """N=256 star, kappa^2 in {0, 1, 100}, double vs single layer: GMRES
-    iterations and solves/s (mixed precision)."""
     import torch
-    import workloads as W
-    from paper_2502_05507_gb300 import Context, Problem
+    from paper_2502_05507_gb300 import Context
     ctx = Context(0)
     torch.cuda.set_stream(ctx.stream)
-    rows = []
-    for k2 in (0.0, 1.0, 100.0):
-        for layer in ("double", "single"):
-            P = W.star(256, kappa2=k2, layer=layer)
-            phi, f = _problem_inputs(P, torch, 0)
-            pr0 = Problem(ctx, phi, P.grid.h, P.grid.origin, k2, layer)
-            g = torch.from_numpy(P.g_at(pr0.boundary_points())).cuda()
-            n_gm = pr0.n_gm
-            pr0.close()
-
-            def step():
-                pr = Problem(ctx, phi, P.grid.h, P.grid.origin, k2, layer)
-                out = pr.solve(f, g, tol=TOL, precision="mixed", max_iter=2000, restart=400)
-                pr.close()
-                return out
-            step()
-            (q, u, st), dt = _timed(step, torch)
-            uu = u.cpu().numpy()
-            m = P.phi < 0
-            rows.append({"kappa2": k2, "layer": layer, "iterations": st["iterations"], "solves_per_s": 1.0 / dt,
-                         "rel_residual": st["rel_residual"], "n_gm": n_gm,
-                         "max_err_vs_exact": float(np.max(np.abs(uu[m] - P.u_exact()[m])))})
+    t = run_star256_table(ctx, torch)
     ctx.close()
-    return {"metric": METRIC, "value": float(np.mean([r["solves_per_s"] for r in rows])), "unit": UNIT,
-            "n_gpus": 1, "higher_is_better": True, "dtype": "f32 conv + df64 refinement",
-            "config": {"workload": "star r=0.6+0.1 sin5t cos3p, N=256, kappa^2 in {0,1,100}, double vs single layer"},
-            "table": rows}
+    return {"metric": METRIC, "value": t["solves_per_s_mean"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+            "dtype": DTYPE_MIXED, "config": {"workload": t["workload"]}, "table": t["table"]}
 
 
 def run_direct128(args):
@@ -557,11 +680,12 @@ def run_direct128(args):
     ctx = Context(0)
     torch.cuda.set_stream(ctx.stream)
     P = W.torus_helmholtz(128, kappa2=10.0)
-    phi, f = _problem_inputs(P, torch, 0)
+    phi = torch.from_numpy(P.phi).cuda()
+    f = torch.from_numpy(P.f()).cuda()
     rows, us = [], {}
     for layer in ("direct", "double"):
         pr0 = Problem(ctx, phi, P.grid.h, P.grid.origin, P.kappa2, layer)
-        g = torch.from_numpy(P.g_at(pr0.boundary_points())).cuda()
+        g = torch.from_numpy(P.g_at(np.asarray(pr0.boundary_points()))).cuda()
         n_unk = pr0.n_unknowns
         pr0.close()
 
@@ -584,7 +708,7 @@ def run_direct128(args):
     diff = float(np.max(np.abs(us["direct"] - us["double"])) / np.max(np.abs(us["double"][m])))
     ctx.close()
     return {"metric": METRIC, "value": rows[0]["solves_per_s"], "unit": UNIT, "n_gpus": 1,
-            "higher_is_better": True, "dtype": "f32 conv + df64 refinement",
+            "higher_is_better": True, "dtype": DTYPE_MIXED,
             "config": {"workload": "torus R=0.5 r=0.2, kappa^2=10, N=128, direct formulation (eq. direct_sys)"},
             "table": rows, "rel_diff_direct_vs_double_on_grid": diff}
 
@@ -593,7 +717,6 @@ def run_serving(args):
     """Serving trace: requests with N in {32,64,128,256}, kappa^2 in {0,10},
     random spheres/ellipsoids/tori, u = exp(a.x); Poisson arrivals at 0.8x
     the measured saturation throughput; p50/p99 latency and solves/s."""
-    import torch
     import workloads as W
     from paper_2502_05507_gb300 import Server
     nreq = args.requests
@@ -630,7 +753,7 @@ def run_serving(args):
     ok = sum(1 for r in res if r["status"] == 0)
     srv.close()
     return {"metric": METRIC, "value": ok / wall, "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
-            "dtype": "f32 conv + df64 refinement",
+            "dtype": DTYPE_MIXED,
             "config": {"workload": f"serving trace, {nreq} Poisson-arrival requests, N in {{32,64,128,256}}, "
                                    f"kappa^2 in {{0,10}}, spheres/ellipsoids/tori", "slots": args.slots,
                        "arrival_rate_per_s": lam, "saturation_solves_per_s": sat_rate},
@@ -645,16 +768,16 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--workload", default="torus128",
-                    choices=["torus128", "sphere32", "batched64", "star256", "serving", "direct128"])
+    ap.add_argument("--no-extra", action="store_true", help="skip the N=128 single-RHS and N=256 star keys")
+    ap.add_argument("--workload", default="batched64",
+                    choices=["batched64", "torus128", "sphere32", "star256", "serving", "direct128"])
     ap.add_argument("--requests", type=int, default=2000, help="serving: number of requests")
-    ap.add_argument("--nrhs", type=int, default=64, help="batched64: right-hand sides (at most 64)")
+    ap.add_argument("--nrhs", type=int, default=NRHS, help="batched64: right-hand sides (at most 64)")
     ap.add_argument("--slots", type=int, default=6, help="serving: concurrent slots")
     ap.add_argument("--hbm-gb", type=float, default=96.0, help="serving: device-memory budget")
     ap.add_argument("--only-timed", action="store_true",
-                    help="warm-up and timed steps only (no profile, fp64 comparison, e2e or CPU baseline)")
+                    help="warm-up and timed steps only (no profile, comparisons, e2e or CPU baseline)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -664,8 +787,7 @@ def main():
             print(json.dumps(run_reference(args)))
         return
     import torch
-    extra = {"sphere32": run_sphere32, "batched64": run_batched64, "star256": run_star256,
-             "serving": run_serving, "direct128": run_direct128}
+    extra = {"torus128": run_torus128, "sphere32": run_sphere32, "star256": run_star256, "serving": run_serving, "direct128": run_direct128}
     if args.workload in extra:
         if rank == 0:
             print(json.dumps(extra[args.workload](args)))
