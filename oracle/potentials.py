@@ -21,6 +21,17 @@ definitions above, `direct_potential` does the sum term by term and
 `fft_convolve` does the same linear convolution with a zero-padded (2N)^3
 FFT (the "3D FFTs" of Section 2.2 and Algorithm 1).
 
+Finite auxiliary box (eq. [aux] with eq. [ps], Algorithm 1's "u_p via FFT"
+on the finite grid): `box_particular` solves L_h u = chi_{M+} f on the box
+nodes M0 with u = 0 on the layer around them, by the sine basis that
+diagonalizes the 7-point operator there. Reading (the paper does not fix
+where the box boundary sits on the cell-centred grid): M0 = the nodes with
+all indices in [1, N - 1], u = 0 on the layers of index 0 and N (the first
+just inside the N^3 array, the second just outside it), so the basis
+sin(pi k i / N), k = 1..N-1, has period 2N, the same as the zero-padded
+free-lattice convolution. Pinned in tests/test_oracle_potentials.py by the
+difference equation on M0, the zero layers, and a sparse direct solve.
+
 Parity: pinned in tests/test_oracle_potentials.py by lattice harmonicity on
 M+ (Propositions of Section 3.2), the lattice equation for u_p, agreement of
 the direct and FFT routes, and the dense identities of Section 3.2.
@@ -136,3 +147,20 @@ def fft_convolve(rho: np.ndarray, table=None, spectrum: np.ndarray | None = None
     rf = sfft.rfftn(rho, s=(2 * N,) * 3, workers=workers)
     v = sfft.irfftn(rf * spectrum, s=(2 * N,) * 3, workers=workers)
     return v[:N, :N, :N]
+
+
+def box_particular(f: np.ndarray, h: float, s: float, inside: np.ndarray) -> np.ndarray:
+    """u = G_h[chi_{M+} f] on the finite auxiliary box (eqs. [aux], [ps]) in
+    lattice units: (6 + s) u(m) - sum of the six neighbours = h^2 f(m) [m in
+    M+] for m in M0 = [1, N-1]^3, u = 0 on the layers 0 and N. In the basis
+    sin(pi k i / N) (k = 1..N-1 per axis; a type-I sine transform of length
+    N - 1) the operator is diagonal with eigenvalue 6 + s - 2 sum_d cos(pi
+    k_d / N). Returns the N^3 array (zero on the layer 0)."""
+    N = f.shape[0]
+    q = (h * h) * np.where(inside, np.asarray(f, dtype=np.float64), 0.0)[1:, 1:, 1:]
+    Q = sfft.dstn(q, type=1)
+    c = 2.0 * np.cos(np.pi * np.arange(1, N) / N)
+    lam = (6.0 + s) - (c[:, None, None] + c[None, :, None] + c[None, None, :])
+    u = np.zeros((N, N, N))
+    u[1:, 1:, 1:] = sfft.idstn(Q / lam, type=1)
+    return u

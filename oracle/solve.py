@@ -14,9 +14,11 @@ Steps, in the order of Algorithm 1:
   7. u = u_p + K q on N+ (discrete generalized Green's formula,
      eq. [discrete_green], with the layer potential as the density term).
 
-Readings: the particular solution is the free-lattice convolution with G_s
-rather than the finite-box FFT solve of eq. [aux]; the discrete solution on
-N+ is unique, so u on N+ is the same (only q differs). Sign convention: f
+Readings: by default the particular solution is the free-lattice
+convolution with G_s rather than the finite-box FFT solve of eq. [aux];
+the discrete solution on N+ is unique, so u on N+ is the same (only q
+differs). `particular="box"` takes the finite-box solve of eq. [aux]
+(potentials.box_particular) as Algorithm 1 prints it. Sign convention: f
 is the paper's, -Lap u + kappa^2 u = f.
 
 `potential="direct"` evaluates every potential by direct summation over the
@@ -54,7 +56,7 @@ def closure_apply(cls, v_flat):
 
 
 def solve(phi, h, origin, f, g_fn, kappa2, layer="double", tol=1e-10, maxiter=500,
-          potential="direct", table=None, spectrum=None, workers=1) -> Result:
+          potential="direct", table=None, spectrum=None, workers=1, particular="lattice") -> Result:
     """g_fn(xstar (n,3)) -> Dirichlet data at the boundary points."""
     sec = {}
     t0 = time.perf_counter()
@@ -77,7 +79,11 @@ def solve(phi, h, origin, f, g_fn, kappa2, layer="double", tol=1e-10, maxiter=50
 
     t0 = time.perf_counter()
     fmask = np.where(cls.inside, np.asarray(f, dtype=np.float64), 0.0)
-    if potential == "fft":
+    if particular == "box":
+        up = pot.box_particular(np.asarray(f, dtype=np.float64), h, s, cls.inside).reshape(-1)
+    elif particular != "lattice":
+        raise ValueError(particular)
+    elif potential == "fft":
         up = pot.fft_convolve((h * h) * fmask, spectrum=spectrum, workers=workers).reshape(-1)
     else:
         up = np.zeros(N ** 3)

@@ -131,3 +131,62 @@ def test_single_layer_smallest_singular_value():
         Sm = pot.layer_matrix(T, cls, cls.gm_idx, "single")
         assert np.allclose(Sm, Sm.T, atol=0)
         assert np.linalg.svd(Sm, compute_uv=False).min() >= 1.0 / 12.0
+
+
+# ------------------------------------------ finite-box particular solution
+def _box_sparse(f, h, s, inside):
+    """eq. [aux] with q = chi_{M+} f assembled as a sparse system over the box
+    nodes M0 = [1, N-1]^3 (u = 0 on the layers 0 and N) and solved directly."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spl
+    N = f.shape[0]
+    n = N - 1
+    idx = np.arange(n ** 3).reshape(n, n, n)
+    rows, cols, vals = [], [], []
+    for i in range(n):
+        for j in range(n):
+            for k in range(n):
+                r = idx[i, j, k]
+                rows.append(r), cols.append(r), vals.append(6.0 + s)
+                for d in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)):
+                    a, b, c = i + d[0], j + d[1], k + d[2]
+                    if 0 <= a < n and 0 <= b < n and 0 <= c < n:
+                        rows.append(r), cols.append(idx[a, b, c]), vals.append(-1.0)
+    A = sp.csr_matrix((vals, (rows, cols)), shape=(n ** 3, n ** 3))
+    rhs = (h * h) * np.where(inside, f, 0.0)[1:, 1:, 1:].reshape(-1)
+    u = np.zeros((N, N, N))
+    u[1:, 1:, 1:] = spl.spsolve(A.tocsc(), rhs).reshape(n, n, n)
+    return u
+
+
+@pytest.mark.parametrize("kappa2", [0.0, 10.0])
+def test_box_particular_solves_aux_problem(kappa2):
+    # eq. [aux]: the difference equation on M0 and zero on the box layer, and
+    # the same values as a sparse direct solve of that system
+    P = W.sphere_exp(8, radius=0.55, kappa2=kappa2)
+    h, s = P.grid.h, kappa2 * P.grid.h ** 2
+    inside = P.phi < 0
+    f = P.f()
+    u = pot.box_particular(f, h, s, inside)
+    assert np.all(u[0, :, :] == 0) and np.all(u[:, 0, :] == 0) and np.all(u[:, :, 0] == 0)
+    ext = np.zeros((9, 9, 9))                  # append the zero layer N
+    ext[:8, :8, :8] = u
+    r = lattice_op(ext, s)[1:8, 1:8, 1:8]
+    rhs = (h * h) * np.where(inside, f, 0.0)[1:, 1:, 1:]
+    assert np.max(np.abs(r - rhs)) <= 1e-13 * np.max(np.abs(rhs))
+    ref = _box_sparse(f, h, s, inside)
+    assert np.max(np.abs(u - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_box_particular_route_equals_fd():
+    # Algorithm 1 with the finite-box particular solution: a different
+    # density, the same discrete solution on N+ as the sparse FD system
+    from oracle import solve as S
+    P = W.torus_helmholtz(16, kappa2=10.0)
+    r = S.solve(P.phi, P.grid.h, P.grid.origin, P.f(), P.g_at, P.kappa2, tol=1e-13, potential="fft",
+                particular="box")
+    u_fd, cls = S.solve_fd(P.phi, P.grid.h, P.grid.origin, P.f(), P.g_at, P.kappa2)
+    m = cls.nplus
+    assert np.max(np.abs(r.u[m] - u_fd[m])) <= 1e-11 * np.max(np.abs(u_fd[m]))
+    r0 = S.solve(P.phi, P.grid.h, P.grid.origin, P.f(), P.g_at, P.kappa2, tol=1e-13, potential="fft")
+    assert np.max(np.abs(r.q - r0.q)) > 1e-6 * np.max(np.abs(r0.q))   # the densities differ
