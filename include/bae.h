@@ -18,8 +18,11 @@
  *  - Array arguments are plain pointers that may point to device memory of
  *    the context's device or to host memory (pageable or pinned); the
  *    library detects which (cudaPointerGetAttributes) and stages host arrays
- *    through its own device buffers, copying on the context stream. The
+ *    through its own device buffers, copying on the context stream. Device
+ *    memory of another GPU is rejected with BAE_ERR_INVALID_ARG. The
  *    caller owns every array it passes; the library never frees them.
+ *  - Each call makes its context's device current while it runs and
+ *    restores the calling thread's current device before it returns.
  *  - All work is issued on the context's stream. Entry points return after
  *    the stream has finished the call's work (results are ready to read).
  *  - Handles own their device memory; a problem must be destroyed before its
@@ -140,6 +143,26 @@ long long bae_launch_count(void);
 #define BAE_SCHED_PASSES 0
 #define BAE_SCHED_PLANE 1
 int bae_set_conv_schedule(int schedule);
+
+/* Host-side fault injection for the library's own failure tests (the paper
+ * has no counterpart). Nothing here faults or hangs a GPU: the failures are
+ * made on the host or by bounded device waits. Process-wide.
+ *  - BAE_FAULT_NONE: clears every injection (arg ignored).
+ *  - BAE_FAULT_BARRIER: the next `arg` launches of the fused (cooperative)
+ *    Arnoldi step wait at each grid barrier for one CTA more than the grid
+ *    has, polling about a millisecond instead of half a second; the waits
+ *    run out, the kernel records the error and returns, and the solve
+ *    returns BAE_ERR_TIMEOUT. Steps replayed from a CUDA graph
+ *    (use_graphs) are not affected. The context stays usable.
+ *  - BAE_FAULT_ALLOC_CAP: every device allocation of the library (work
+ *    space, problem data, spectra) larger than `arg` bytes fails as out of
+ *    memory (BAE_ERR_OOM) until cleared; arg <= 0 clears it. A failed
+ *    bae_problem_create frees what it had made; the context stays usable.
+ * Returns BAE_ERR_INVALID_ARG for an unknown kind. */
+#define BAE_FAULT_NONE 0
+#define BAE_FAULT_BARRIER 1
+#define BAE_FAULT_ALLOC_CAP 2
+int bae_inject_fault(int kind, long long arg);
 
 /* Process-wide kernel timing. bae_profile_start pre-creates CUDA events for
  * up to max_launches launches; from then on every kernel launch of the
@@ -279,6 +302,9 @@ int bae_boundary_apply(bae_problem* prob, int precision, const double* q, double
  *    bae_problem_create, which does allocate, at set-up.
  *  - The first call on a device looks up the device address of the array
  *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - The call never times convolution schedules: it uses the schedule an
+ *    earlier apply of the same precision and N (one right-hand side) chose,
+ *    or bae_set_conv_schedule's, else the plane-fused default.
  *  - Every call uses the same array and leaves its contents behind; nothing
  *    in it needs clearing, since each call writes every element it reads.
  *    Calls whose GPU work overlaps in time (several host threads, several

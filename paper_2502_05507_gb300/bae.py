@@ -87,6 +87,7 @@ def lib():
             "bae_default_options": (None, [_P]),
             "bae_launch_count": (ctypes.c_longlong, []),
             "bae_set_conv_schedule": (_I, [_I]),
+            "bae_inject_fault": (_I, [_I, ctypes.c_longlong]),
             "bae_profile_start": (_I, [_I]),
             "bae_profile_stop": (_I, [ctypes.c_char_p, _I, _P, _P, _I, _P]),
             "bae_ctx_create": (_I, [_I, _P, _P]),
@@ -124,7 +125,8 @@ def lib():
     return _lib
 
 
-EXPORTED = ["bae_version", "bae_last_error", "bae_default_options", "bae_launch_count", "bae_set_conv_schedule", "bae_profile_start",
+EXPORTED = ["bae_version", "bae_last_error", "bae_default_options", "bae_launch_count", "bae_set_conv_schedule",
+            "bae_inject_fault", "bae_profile_start",
             "bae_profile_stop", "bae_ctx_create", "bae_ctx_destroy",
             "bae_lgf_table", "bae_lgf_spectrum", "bae_problem_create", "bae_problem_destroy",
             "bae_problem_sizes", "bae_problem_unknowns", "bae_gamma_plus", "bae_interior_mask", "bae_problem_plane_range", "bae_boundary_points", "bae_classification", "bae_potential_apply",
@@ -186,6 +188,14 @@ def _as_f64(a):
 def launch_count() -> int:
     """Kernels launched by the library in this process so far."""
     return int(lib().bae_launch_count())
+
+
+FAULT_NONE, FAULT_BARRIER, FAULT_ALLOC_CAP = 0, 1, 2
+
+
+def inject_fault(kind: int, arg: int = 0):
+    """bae_inject_fault: host-side fault injection for failure tests."""
+    _check(lib().bae_inject_fault(int(kind), int(arg)))
 
 
 SCHEDULES = {"auto": -1, "passes": 0, "plane": 1}

@@ -80,7 +80,21 @@ void prof_pop(cudaStream_t st) {
     g_prof.pending = nullptr;
 }
 
+// host-side fault injection (bae_inject_fault): the cap on the size of one
+// device allocation (0: none) and the number of fused Arnoldi launches whose
+// barrier waits are made to run out
+static std::atomic<long long> g_alloc_cap{0};
+static std::atomic<long long> g_fault_barrier{0};
+
+void alloc_check(size_t bytes) {
+    const long long cap = g_alloc_cap.load();
+    if (cap > 0 && (long long)bytes > cap)
+        throw Error(BAE_ERR_OOM, "device allocation of " + std::to_string(bytes) +
+                                     " bytes refused (injected allocation cap of " + std::to_string(cap) + " bytes)");
+}
+
 void* dev_alloc(size_t bytes, cudaStream_t st) {
+    alloc_check(bytes);
     void* p = nullptr;
     BAE_CUDA(cudaMallocAsync(&p, bytes ? bytes : 16, st));
     return p;
@@ -148,6 +162,7 @@ struct Workspace {
     Grow<unsigned long long> arnBar;
     Grow<double> in_f, in_g, out_q, out_u;    // staging of host arguments
     Grow<double> qpre, zpre;                  // M^{-1} y of the preconditioned inner solves
+    Grow<float> arnV32, arnZ32;               // float32 copies of the newest basis vector and its M^{-1}
     Grow<double> ydir64, bprime;              // direct formulation: operator rows, [g; 0]
     Grow<float> ydir32;
     void set_stream(cudaStream_t st) {
@@ -158,6 +173,7 @@ struct Workspace {
         for (auto* d : ds2) d->st = st;
         A.st = B.st = st;
         v32.st = st;
+        arnV32.st = arnZ32.st = st;
         ydir32.st = st;
         active.st = arnI.st = st;
         arnCtr.st = st;
@@ -171,6 +187,8 @@ struct Twiddles {
     dsc* twds = nullptr;
 };
 
+}  // namespace
+
 bool is_device_ptr(const void* p) {
     if (!p) return false;
     cudaPointerAttributes a;
@@ -179,10 +197,15 @@ bool is_device_ptr(const void* p) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    if (a.type != cudaMemoryTypeDevice) return false;
+    int cur = -1;
+    BAE_CUDA(cudaGetDevice(&cur));
+    BAE_REQUIRE(a.device == cur, BAE_ERR_INVALID_ARG,
+                "array is device memory of GPU " + std::to_string(a.device) + ", the call runs on GPU " +
+                    std::to_string(cur));
+    return true;
 }
-
-}  // namespace
 }  // namespace bae
 
 using namespace bae;
@@ -216,8 +239,11 @@ struct SpectrumCache {
             sp->N = N;
             sp->s = s;
             const long long n3 = (long long)(N + 1) * (N + 1) * (N + 1);
+            alloc_check(n3 * sizeof(double));
             BAE_CUDA(cudaMalloc(&sp->g64, n3 * sizeof(double)));
+            alloc_check(n3 * sizeof(float));
             BAE_CUDA(cudaMalloc(&sp->g32, n3 * sizeof(float)));
+            alloc_check(n3 * sizeof(dsf));
             BAE_CUDA(cudaMalloc(&sp->gds, n3 * sizeof(dsf)));
             sp->bytes = n3 * (sizeof(double) + sizeof(float) + sizeof(dsf));
             const double L = 2.0 * N;
@@ -265,14 +291,17 @@ struct bae_ctx {
     int pinned_cap = 0;
     Workspace ws;
 
-    int* pinned_flags(int nb) {   // host-pinned, device-mapped [nb] polling buffer
-        if (nb > pinned_cap) {
+    // host-pinned, device-mapped polling buffer: [nb] live flags, then the
+    // barrier error flag of the fused Arnoldi step
+    int* pinned_flags(int nb) {
+        if (nb + 1 > pinned_cap) {
             if (pinned) cudaFreeHost(pinned);
             pinned = nullptr;
             pinned_dev = nullptr;
-            BAE_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&pinned), (size_t)nb * sizeof(int), cudaHostAllocMapped));
+            BAE_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&pinned), (size_t)(nb + 1) * sizeof(int),
+                                   cudaHostAllocMapped));
             BAE_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&pinned_dev), pinned, 0));
-            pinned_cap = nb;
+            pinned_cap = nb + 1;
         }
         return pinned;
     }
@@ -316,6 +345,7 @@ bool problem_view(const bae_problem* P, ProblemView& out) {
     out.device = P->ctx->device;
     out.N = P->geo.N;
     out.n_gm = P->geo.n_gm;
+    out.n_unk = P->geo.n_unk;
     out.stream = P->ctx->stream;
     out.rec = P->geo.recipe();
     out.ghat64 = P->spec->g64;
@@ -463,13 +493,17 @@ struct RhsState {
 // capturable in a graph); returns v [nb][N^3]
 template <typename T>
 out_t<T>* potential_rows(bae_problem* P, int nb, const double* q, long long q_stride, const int* q_row,
-                         long long q_row_stride, const int* active) {
+                         long long q_row_stride, const int* active, const float* q32 = nullptr) {
     ConvArgs<T> a = conv_args<T>(P, nb, true);
     a.mode = SRC_DENSITY;
     a.q = q;
     a.q_stride = q_stride;
     a.q_row = q_row;
     a.q_row_stride = q_row_stride;
+    if (std::is_same<T, float>::value && q32) {
+        a.q32 = q32;
+        a.q32_stride = n_unk(P);
+    }
     a.active = active;
     a.rec = P->geo.recipe();
     a.v = vbuf<T>(P, nb);
@@ -544,8 +578,8 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
     double* scal = ws.arnScal.need((long long)nb * 5);
     a.est = scal;
     a.target = scal + nb;
-    a.inv = scal + 2 * nb;   // scal + 3 nb: spare
-    int* ibuf = ws.arnI.need((long long)nb * 6 + 1);
+    a.inv = scal + 2 * nb;
+    int* ibuf = ws.arnI.need((long long)nb * 7 + 2);
     a.flag = ibuf;
     a.ncols = ibuf + nb;
     int* member = ibuf + 2 * nb;
@@ -558,6 +592,10 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
     a.err = ibuf + 4 * nb;
     a.gflag = ibuf + 4 * nb + 1;
     a.live = ibuf + 5 * nb + 1;
+    a.v32 = ws.arnV32.need((long long)nb * n);
+    a.reo = ibuf + 6 * nb + 1;
+    a.any_reo = ibuf + 7 * nb + 1;
+    a.hn = scal + 3 * nb;
     a.n2 = scal + 4 * nb;
     a.pcol = ws.arnP.need((long long)nb * 2 * (m + 2));
     double* r = ws.r.need((long long)nb * n);
@@ -578,10 +616,13 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
     BAE_CUDA(cudaMemsetAsync(a.ctr, 0, (size_t)nb * 3 * sizeof(unsigned int), st));
     BAE_CUDA(cudaMemsetAsync(a.bar, 0, 2 * sizeof(unsigned long long), st));
     BAE_CUDA(cudaMemsetAsync(a.err, 0, sizeof(int), st));
+    BAE_CUDA(cudaMemsetAsync(a.any_reo, 0, sizeof(int), st));
     // the kernels that decide the flags also write live[b] into mapped host
     // memory: no copy between the replayed steps
     volatile int* hlive = P->ctx->pinned_flags(nb);
     a.live_host = P->ctx->pinned_dev;
+    a.err_host = P->ctx->pinned_dev + nb;
+    hlive[nb] = 0;
     cudaEvent_t ev[2] = {P->ctx->poll_ev[0], P->ctx->poll_ev[1]};
     cudaGraphExec_t exec = nullptr;
     long long graph_kernels = 0;
@@ -604,6 +645,7 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
     // right preconditioning: the step applies A to z = M^{-1} V[j]; the
     // fused step forms the next z itself (after arn_init: z of V[0] here)
     double* zpre = pre ? ws.zpre.need((long long)nb * n) : nullptr;
+    a.z32 = pre ? ws.arnZ32.need((long long)nb * n) : nullptr;
     const bool fuse_pre = pre && a.coop_grid > 0;
     if (fuse_pre) {
         a.pre_col = P->pre.col;
@@ -614,13 +656,17 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
         const double* q = a.V;
         long long qs = (long long)(m + 1) * n;
         const int* qrow = a.j;
+        // the float32 apply reads the float32 copy of its density: z32, or
+        // v32 (the newest basis vector, the row a.j selects)
+        const float* q32 = a.v32;
         if (pre) {
-            if (!fuse_pre) precond_apply(P->pre, a.V, qs, a.j, n, zpre, n, nb, a.flag, st);
+            if (!fuse_pre) precond_apply(P->pre, a.V, qs, a.j, n, zpre, n, nb, a.flag, st, a.v32, a.z32);
             q = zpre;
             qs = n;
             qrow = nullptr;
+            q32 = a.z32;
         }
-        if (prec == BAE_FP32) a.v = potential_rows<float>(P, nb, q, qs, qrow, n, a.flag);
+        if (prec == BAE_FP32) a.v = potential_rows<float>(P, nb, q, qs, qrow, n, a.flag, q32);
         else if (prec == BAE_DF64) a.v = potential_rows<dsf>(P, nb, q, qs, qrow, n, a.flag);
         else a.v = potential_rows<double>(P, nb, q, qs, qrow, n, a.flag);
         if (direct) {
@@ -634,7 +680,18 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
                 a.v = y64;
             }
         }
-        arn_step(a, st);
+        // fault injection (tests only): this launch's barrier waits run out
+        // after ~8k polls (about a millisecond) instead of half a second
+        const bool inject = a.coop_grid > 0 && !use_graph && g_fault_barrier.load() > 0;
+        if (inject) {
+            g_fault_barrier.fetch_sub(1);
+            Arnoldi af = a;
+            af.bar_extra = 1;
+            af.spin_limit = 1 << 13;
+            arn_step(af, st);
+        } else {
+            arn_step(a, st);
+        }
     };
     // size every buffer and set every kernel attribute the step needs before
     // any capture (nothing may allocate or configure inside it)
@@ -667,6 +724,7 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
             key.push_back((uintptr_t)v);
         add(P); add(a.V); add(a.w); add(a.part); add(a.h1); add(a.hcol); add(a.H); add(a.cs); add(a.g); add(a.y);
         add(scal); add(ibuf); add(a.ctr); add(a.bar); add(a.pcol); add(a.live_host); add(zpre); add(y32); add(y64);
+        add(a.v32); add(a.z32);
         add(ws.A.p); add(ws.B.p); add(ws.v32.p); add(ws.v64.p); add(P->pre.col); add(P->pre.val);
         if (cache->exec && cache->key == key) {
             exec = cache->exec;
@@ -709,7 +767,8 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
             }
             kr_norm2(r, d_all, nb, n, npart + nb, krylov_chunks(n), npart, st);
             arn_init(a, r, npart, member, st);
-            if (fuse_pre) precond_apply(P->pre, a.V, (long long)(m + 1) * n, nullptr, 0, zpre, n, nb, member, st);
+            if (fuse_pre)
+                precond_apply(P->pre, a.V, (long long)(m + 1) * n, nullptr, 0, zpre, n, nb, member, st, a.v32, a.z32);
             // the fused step applies the rotations of a column one step later:
             // one more launch finishes the last column of the cycle
             const int steps = std::min(m, iters_left) + (a.coop_grid > 0 ? 1 : 0);
@@ -746,7 +805,7 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
                     BAE_CUDA(cudaEventSynchronize(ev[(it - 1) & 1]));
                     int live = 0;
                     for (int b = 0; b < nb; ++b) live |= hlive[b];
-                    if (!live) break;
+                    if (!live || hlive[nb]) break;   // converged, or a barrier wait ran out
                 }
             }
             // one host read per cycle: columns, estimates and the barrier
@@ -756,6 +815,8 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
             BAE_CUDA(cudaMemcpyAsync(est.data(), a.est, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
             if (a.coop_grid > 0) BAE_CUDA(cudaMemcpyAsync(&coop_err, a.err, sizeof(int), cudaMemcpyDeviceToHost, st));
             BAE_CUDA(cudaStreamSynchronize(st));
+            BAE_REQUIRE(coop_err == 0, BAE_ERR_TIMEOUT,
+                        "GMRES: a bounded grid-barrier wait of the fused Arnoldi step ran out");
             int maxc = 0;
             for (int b = 0; b < nb; ++b) maxc = std::max(maxc, ncols[b]);
             for (int b = 0; b < nb; ++b) {
@@ -776,7 +837,6 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
         throw;
     }
     drop_exec(true);
-    BAE_REQUIRE(coop_err == 0, BAE_ERR_CUDA, "GMRES: a grid barrier of the fused Arnoldi step timed out");
 }
 
 // ------------------------------------------------------------ full solve
@@ -1047,6 +1107,7 @@ struct Staged {
 
 template <typename F>
 int guarded(F&& fn) {
+    DeviceGuard dg;   // the caller's current device is restored on return
     try {
         return fn();
     } catch (const Error& e) {
@@ -1094,6 +1155,23 @@ int bae_set_conv_schedule(int schedule) {
         BAE_REQUIRE(schedule >= BAE_SCHED_AUTO && schedule <= BAE_SCHED_PLANE, BAE_ERR_INVALID_ARG,
                     "schedule must be BAE_SCHED_AUTO, BAE_SCHED_PASSES or BAE_SCHED_PLANE");
         bae::set_forced_sched(schedule);
+        return BAE_OK;
+    });
+}
+
+int bae_inject_fault(int kind, long long arg) {
+    return guarded([&]() -> int {
+        if (kind == BAE_FAULT_NONE) {
+            g_alloc_cap.store(0);
+            g_fault_barrier.store(0);
+        } else if (kind == BAE_FAULT_BARRIER) {
+            BAE_REQUIRE(arg >= 0, BAE_ERR_INVALID_ARG, "arg must be >= 0");
+            g_fault_barrier.store(arg);
+        } else if (kind == BAE_FAULT_ALLOC_CAP) {
+            g_alloc_cap.store(arg > 0 ? arg : 0);
+        } else {
+            throw Error(BAE_ERR_INVALID_ARG, "unknown fault kind");
+        }
         return BAE_OK;
     });
 }
@@ -1213,6 +1291,7 @@ int bae_ctx_create(int device, void* stream, bae_ctx** out) {
 
 void bae_ctx_destroy(bae_ctx* ctx) {
     if (!ctx) return;
+    bae::DeviceGuard dg;
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     ctx->cache.reset();
@@ -1290,8 +1369,9 @@ int bae_problem_create(bae_ctx* ctx, int N, double h, const double origin[3], co
             P->geo.release();
             throw;
         }
-        P->spec = ctx->spectrum(N, P->s);
-        ctx->twiddles(2 * N);   // built here so that later applies allocate nothing
+        try {
+            P->spec = ctx->spectrum(N, P->s);
+            ctx->twiddles(2 * N);   // built here so that later applies allocate nothing
         // the Schwarz rows of the default (mixed, preconditioned) solve, built
         // on the side stream from here on; a solve waits for them only when it
         // uses them
@@ -1311,6 +1391,18 @@ int bae_problem_create(bae_ctx* ctx, int N, double h, const double origin[3], co
             BAE_CUDA(cudaMemcpyAsync(P->ones, on.data(), nu * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
             BAE_CUDA(cudaStreamSynchronize(ctx->stream));
         }
+        } catch (...) {
+            // a failure after the geometry (no memory for the spectrum, the
+            // Schwarz rows or the direct formulation's arrays) leaves the
+            // context usable: everything made so far is freed
+            cudaStreamSynchronize(ctx->side);
+            cudaStreamSynchronize(ctx->stream);
+            P->pre.release();
+            if (P->iota) dev_free(P->iota, ctx->stream);
+            if (P->ones) dev_free(P->ones, ctx->stream);
+            P->geo.release();
+            throw;
+        }
         *out = P.release();
         return BAE_OK;
     });
@@ -1318,6 +1410,7 @@ int bae_problem_create(bae_ctx* ctx, int N, double h, const double origin[3], co
 
 void bae_problem_destroy(bae_problem* P) {
     if (!P) return;
+    bae::DeviceGuard dg;
     cudaSetDevice(P->ctx->device);
     if (P->pre.pending) cudaStreamSynchronize(P->ctx->side);   // a build the main stream never waited for
     cudaStreamSynchronize(P->ctx->stream);

@@ -340,16 +340,22 @@ struct Scratch {
     template <typename T> T* get(long long n) { T* p = dev_alloc_n<T>(n, st); ptrs.push_back(p); return p; }
 };
 
+// out[i] = nearest float32 of in[i]
+__global__ void k_to_float(const double* __restrict__ in, long long n, float* __restrict__ out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = (float)in[i];
+}
+
 int grid_for(long long n) { return (int)std::min<long long>((n + 255) / 256, 152LL * 32); }
 
 }  // namespace
 
 void Geometry::release() {
     void* ps[] = {flags, gm, gp, node_of, partner, partner_u, t, xstar, line_off, src_lin, term_off, term_idx,
-                  term_coef};
+                  term_coef, term_coef32};
     for (void* p : ps) if (p) dev_free(p, stream);
     flags = nullptr; gm = gp = node_of = partner = partner_u = nullptr; t = xstar = nullptr;
-    line_off = src_lin = term_off = term_idx = nullptr; term_coef = nullptr;
+    line_off = src_lin = term_off = term_idx = nullptr; term_coef = nullptr; term_coef32 = nullptr;
 }
 
 void build_geometry(const double* phi, int N, double h, const double origin[3], int layer, double s, Geometry& g,
@@ -417,6 +423,8 @@ void build_geometry(const double* phi, int N, double h, const double origin[3], 
     g.term_coef = dev_alloc_n<double>(g.n_terms, st);
     BAE_LAUNCH("k_term_fill", st, k_term_fill<<<grid_for(g.n_src), 256, 0, st>>>(g.src_lin, (int)g.n_src, g.flags, N, g.node_of, g.term_off, layer,
                                                    6.0 + s, g.term_idx, g.term_coef));
+    g.term_coef32 = dev_alloc_n<float>(g.n_terms, st);
+    BAE_LAUNCH("k_to_float", st, k_to_float<<<grid_for(g.n_terms), 256, 0, st>>>(g.term_coef, g.n_terms, g.term_coef32));
     // x-planes holding every source (gamma- and D-nodes, or M+ for the
     // volume term, whose planes lie between) and every gathered node
     // (gamma- and the partners, one step from gamma-)

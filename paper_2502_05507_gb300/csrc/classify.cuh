@@ -28,6 +28,7 @@ struct Geometry {
     int* term_off = nullptr;
     int* term_idx = nullptr;
     double* term_coef = nullptr;
+    float* term_coef32 = nullptr;  // the coefficients rounded to float32 (small integers and 6 + s)
     // x-planes [plane_lo, plane_hi) contain every source and every node the
     // gather and the reconstruction read
     int plane_lo = 0, plane_hi = 0;
@@ -39,6 +40,7 @@ struct Geometry {
         r.term_off = term_off;
         r.term_idx = term_idx;
         r.term_coef = term_coef;
+        r.term_coef32 = term_coef32;
         r.wide = layer == BAE_LAYER_DIRECT;
         return r;
     }

@@ -35,6 +35,9 @@ void prof_pop(cudaStream_t st);
 // Stream-ordered device allocation from the device's default memory pool
 // (kept pooled: freed blocks are reused without returning to the driver).
 void* dev_alloc(size_t bytes, cudaStream_t st);
+// throws BAE_ERR_OOM when an injected allocation cap (bae_inject_fault)
+// refuses an allocation of this size
+void alloc_check(size_t bytes);
 void dev_free(void* p, cudaStream_t st);
 template <typename T>
 T* dev_alloc_n(long long n, cudaStream_t st) {
@@ -52,6 +55,31 @@ T* dev_alloc_n(long long n, cudaStream_t st) {
     } while (0)
 
 #define BAE_CHECK_LAUNCH() BAE_CUDA(cudaGetLastError())
+
+// Restores the calling thread's current CUDA device on scope exit: every
+// entry point switches to its context's device and leaves the caller's
+// choice as it found it.
+struct DeviceGuard {
+    int saved = -1;
+    DeviceGuard() {
+        if (cudaGetDevice(&saved) != cudaSuccess) {
+            cudaGetLastError();
+            saved = -1;
+        }
+    }
+    ~DeviceGuard() {
+        if (saved >= 0) cudaSetDevice(saved);
+    }
+    DeviceGuard(const DeviceGuard&) = delete;
+    DeviceGuard& operator=(const DeviceGuard&) = delete;
+};
+
+// Whether p is memory the kernels of the current device may read or write:
+// true for device memory of the current device and for managed memory,
+// false for host memory (pageable or pinned), which the callers stage.
+// Device memory of another GPU is rejected (BAE_ERR_INVALID_ARG): the
+// kernels of this device cannot be assumed to reach it.
+bool is_device_ptr(const void* p);
 
 #define BAE_LAUNCH(name, st, ...)            \
     do {                                     \

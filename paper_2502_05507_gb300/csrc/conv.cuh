@@ -15,6 +15,7 @@ struct SrcRecipe {
     const int* term_off = nullptr;   // ns + 1 offsets into term_idx/term_coef
     const int* term_idx = nullptr;   // unknown number of each term
     const double* term_coef = nullptr;
+    const float* term_coef32 = nullptr;   // the same coefficients rounded to float32
     // sum the terms in float64 before the float32 rounding (the direct
     // formulation's (6 + s) u(n) - sum u(y) cancels to O(h^2 u))
     bool wide = false;
@@ -34,6 +35,12 @@ struct ConvArgs {
     long long q_stride = 0;
     const int* q_row = nullptr;
     long long q_row_stride = 0;
+    // optional float32 copy of the density the float32 apply reads (the
+    // values of q rounded to float32; item b at q32 + b q32_stride, the row
+    // q_row selects): saves the float64 -> float32 conversions, which run on
+    // GB300's narrow float64 pipe
+    const float* q32 = nullptr;
+    long long q32_stride = 0;
     // optional per-item flags: items with active[b] == 0 are skipped
     const int* active = nullptr;
     SrcRecipe rec;
@@ -52,6 +59,9 @@ struct ConvArgs {
     // caller reads (p1 == 0: all N planes). Planes outside are skipped: their
     // sources are zero, and their part of v is left unwritten.
     int p0 = 0, p1 = 0;
+    // never time schedules in this apply: use the choice made by an earlier
+    // apply of the same (element type, N, batch size), else the default
+    bool no_tune = false;
     __host__ __device__ int plane_lo() const { return p1 > 0 ? p0 : 0; }
     __host__ __device__ int plane_hi() const { return p1 > 0 ? p1 : N; }
 };

@@ -49,6 +49,7 @@ __global__ void __launch_bounds__(CPlaneGeo<T, L>::PT) k_cplane_fwd(ConvArgs<T> 
                 __syncthreads();
                 if (act) {
                     const double* q = a.q + (long long)b * a.q_stride + (a.q_row ? (long long)a.q_row[b] * a.q_row_stride : 0);
+                    const float* q32 = a.q32 ? a.q32 + (long long)b * a.q32_stride : nullptr;
 #pragma unroll
                     for (int half = 0; half < 2; ++half) {
                         const long long l = half ? lb : la;
@@ -56,7 +57,7 @@ __global__ void __launch_bounds__(CPlaneGeo<T, L>::PT) k_cplane_fwd(ConvArgs<T> 
                         const int s0 = a.rec.line_off[l], s1 = a.rec.line_off[l + 1];
                         for (int s = s0 + t; s < s1; s += R1) {
                             const int k = a.rec.src_lin[s] - (int)(l * N);
-                            rr[k] = source_value<T>(a.rec, s, q);
+                            rr[k] = source_value<T>(a.rec, s, q, q32);
                         }
                     }
                 }
@@ -121,7 +122,7 @@ __global__ void __launch_bounds__(CPlaneGeo<T, L>::PT) k_cplane_fwd(ConvArgs<T> 
                 v[m] = (ok && m < HALF) ? part[owner][(long long)(n - owner * NR) * N1 + col] : cmake<C>((T)0.0, (T)0.0);
             }
             fft_n2k<L, false, true>(v, xch, c, R1 * G::PW, G::PW, t, a.tw);
-            if (col0 == 0) split_column0<L>(v, xch, c, t);
+            if (col0 == 0) split_column0<Plan2<L>, L>(v, xch, c, t);
             if (ok) {
 #pragma unroll
                 for (int q2 = 0; q2 < Q; ++q2)

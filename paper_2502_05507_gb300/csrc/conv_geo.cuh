@@ -9,19 +9,31 @@
 
 namespace bae {
 
+// Transform plan of the pass kernels per element type and length: the
+// three-level 8 x 8 x 8 plan for 16-byte elements at L = 512 (float64 and
+// double-float, whose two-level 16 x 32 split needs ~200-255 registers per
+// thread), the two-level plan elsewhere.
+template <typename T, int L> struct PlanOf { using type = Plan2<L>; };
+template <> struct PlanOf<double, 512> { using type = Plan3_512; };
+template <> struct PlanOf<dsf, 512> { using type = Plan3_512; };
+
 // Launch geometry per transform length and precision.
 template <typename T, int L> struct Geo {
     using C = cplx_t<T>;
-    static constexpr int R1 = Factors<L>::R1, R2 = Factors<L>::R2;
-    // column passes: W columns per CTA, R1 threads per column
+    using PL = typename PlanOf<T, L>::type;
+    static constexpr bool THREE = PL::TH * PL::S == L && PL::TH > PL::S;
+    static constexpr int TH = PL::TH, S = PL::S;   // threads per line, values per thread
+    // column passes: W columns per CTA, TH threads per column (three-level:
+    // 4 columns of 16-byte elements, 64 bytes per row segment, 256 threads)
     static constexpr int WB = 65536 / (L * (int)sizeof(C));
-    static constexpr int W = WB > 32 ? 32 : (WB < 8 ? 8 : WB);
-    static constexpr int CT = W * R1;
-    // line passes (k): P line pairs per CTA, R1 threads per pair
+    static constexpr int W = THREE ? 4 : (WB > 32 ? 32 : (WB < 8 ? 8 : WB));
+    static constexpr int CT = W * TH;
+    static constexpr int XL = PL::XLEN;            // exchange positions per column
+    // line passes (k): P line pairs per CTA, TH threads per pair
     static constexpr int PB = 65536 / (L * (int)sizeof(C));
-    static constexpr int P = (256 / R1) < PB ? (256 / R1) : (PB < 4 ? 4 : PB);
-    static constexpr int KT = P * R1;
-    static constexpr int XS = R2 * (R1 + 1) + 1;   // exchange stride per pair (odd)
+    static constexpr int P = THREE ? 4 : ((256 / TH) < PB ? (256 / TH) : (PB < 4 ? 4 : PB));
+    static constexpr int KT = P * TH;
+    static constexpr int XS = PL::XS;              // exchange stride per pair (odd)
 };
 
 template <typename T>
@@ -76,12 +88,14 @@ __device__ __forceinline__ T volume_or_zero(const ConvArgs<T>& a, int b, long lo
 }
 
 template <typename T>
-__device__ __forceinline__ T source_value(const SrcRecipe& rec, int s, const double* q) {
+__device__ __forceinline__ T source_value(const SrcRecipe& rec, int s, const double* q, const float* q32) {
     if constexpr (std::is_same<T, float>::value) {
         if (!rec.wide) {   // small integer coefficients: a float32 sum
             float val = 0.f;
-            for (int e = rec.term_off[s]; e < rec.term_off[s + 1]; ++e)
-                val = __fmaf_rn((float)rec.term_coef[e], (float)q[rec.term_idx[e]], val);
+            for (int e = rec.term_off[s]; e < rec.term_off[s + 1]; ++e) {
+                const int k = rec.term_idx[e];
+                val = __fmaf_rn(rec.term_coef32[e], q32 ? q32[k] : (float)q[k], val);
+            }
             return val;
         }
     }
@@ -164,28 +178,23 @@ __device__ __forceinline__ C slot_split(C zk, C zr, int k, int N) {
     return cmake<C>((zr.y + zk.y) * half, (zk.x - zr.x) * half);
 }
 
-// After the forward j transform of a column group (column c held by R1
-// threads t in k-layout, k = t + q R1 + R2 k1; the exchange buffer free),
-// replaces the outputs of column c == 0 by its slots. Every thread of the
-// CTA calls it (two barriers).
-template <int L, typename C>
+// After the forward j transform of a column group (column c held by the
+// plan's TH threads t in k-layout, slot s holding k = PL::kidx(t, s); the
+// exchange buffer free), replaces the outputs of column c == 0 by its
+// slots. Every thread of the CTA calls it (two barriers).
+template <typename PL, int L, typename C>
 __device__ __forceinline__ void split_column0(C* v, C* xch, int c, int t) {
-    constexpr int R1 = Factors<L>::R1, R2 = Factors<L>::R2, Q = R2 / R1;
     if (c == 0) {
 #pragma unroll
-        for (int q = 0; q < Q; ++q)
-#pragma unroll
-            for (int k1 = 0; k1 < R1; ++k1) xch[t + q * R1 + R2 * k1] = v[q * R1 + k1];
+        for (int s = 0; s < PL::S; ++s) xch[PL::kidx(t, s)] = v[s];
     }
     __syncthreads();
     if (c == 0) {
 #pragma unroll
-        for (int q = 0; q < Q; ++q)
-#pragma unroll
-            for (int k1 = 0; k1 < R1; ++k1) {
-                const int k = t + q * R1 + R2 * k1;
-                v[q * R1 + k1] = slot_split(v[q * R1 + k1], xch[(L - k) & (L - 1)], k, L / 2);
-            }
+        for (int s = 0; s < PL::S; ++s) {
+            const int k = PL::kidx(t, s);
+            v[s] = slot_split(v[s], xch[(L - k) & (L - 1)], k, L / 2);
+        }
     }
     __syncthreads();
 }

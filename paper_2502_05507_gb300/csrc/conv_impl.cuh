@@ -52,50 +52,52 @@ __global__ void __launch_bounds__(Geo<T, L>::KT) k_kpass_fwd(ConvArgs<T> a) {
     wait_prior_grid();   // results of the previous kernel on the stream
     using C = cplx_t<T>;
     using G = Geo<T, L>;
-    constexpr int N = L / 2, N1 = N + 1, R1 = G::R1, R2 = G::R2;
+    using PL = typename G::PL;
+    constexpr int N = L / 2, N1 = N + 1, TH = G::TH, S = G::S;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* xch = reinterpret_cast<C*>(smem_raw);                 // P * XS
     T* rho = reinterpret_cast<T*>(xch + G::P * G::XS);      // P * 2N
 
     const int b = blockIdx.z;
     if (a.active && !a.active[b]) return;   // whole CTA: no barrier is skipped
-    const int t = threadIdx.x % R1;
-    const int p = threadIdx.x / R1;
+    const int t = threadIdx.x % TH;
+    const int p = threadIdx.x / TH;
     const long long pair = (long long)a.plane_lo() * (N / 2) + (long long)blockIdx.x * G::P + p;
     const bool active = pair < (long long)a.plane_hi() * (N / 2);
     const long long la = 2 * pair, lb = la + 1;
     T* r = rho + p * 2 * N;
 
-    C v[R2];
+    C v[S];
     if (a.mode == SRC_DENSITY) {
-        for (int k = t; k < 2 * N; k += R1)
+        for (int k = t; k < 2 * N; k += TH)
             r[k] = active ? volume_or_zero(a, b, (k < N ? la : lb) * N + (k < N ? k : k - N)) : (T)0;
         __syncthreads();
         if (active) {
             const double* q = a.q + (long long)b * a.q_stride + (a.q_row ? (long long)a.q_row[b] * a.q_row_stride : 0);
+            const float* q32 = a.q32 ? a.q32 + (long long)b * a.q32_stride : nullptr;
 #pragma unroll
             for (int half = 0; half < 2; ++half) {
                 const long long l = half ? lb : la;
                 const int s0 = a.rec.line_off[l], s1 = a.rec.line_off[l + 1];
-                for (int s = s0 + t; s < s1; s += R1) {
+                for (int s = s0 + t; s < s1; s += TH) {
                     const int k = a.rec.src_lin[s] - (int)(l * N);
-                    r[half * N + k] = source_value<T>(a.rec, s, q);
+                    r[half * N + k] = source_value<T>(a.rec, s, q, q32);
                 }
             }
         }
         __syncthreads();
 #pragma unroll
-        for (int m = 0; m < R2; ++m) {
-            const int n = t + R1 * m;
-            v[m] = (m < R2 / 2) ? cmake<C>(r[n], r[N + n]) : cmake<C>((T)0, (T)0);
+        for (int m = 0; m < S; ++m) {
+            const int n = t + TH * m;
+            v[m] = (m < S / 2) ? cmake<C>(r[n], r[N + n]) : cmake<C>((T)0, (T)0);
         }
     } else {
         const double* f = a.f + (long long)b * N * N * N;
 #pragma unroll
-        for (int m = 0; m < R2; ++m) {
-            const int n = t + R1 * m;
+        for (int m = 0; m < S; ++m) {
+            const int n = t + TH * m;
             T va = (T)0.0, vb = (T)0.0;
-            if (active && m < R2 / 2) {
+            if (active && m < S / 2) {
                 const long long xa = la * N + n, xb = lb * N + n;
                 va = (a.flags[xa] & 1) ? (T)(a.scale * f[xa]) : (T)0;
                 vb = (a.flags[xb] & 1) ? (T)(a.scale * f[xb]) : (T)0;
@@ -104,18 +106,16 @@ __global__ void __launch_bounds__(Geo<T, L>::KT) k_kpass_fwd(ConvArgs<T> a) {
         }
     }
     const int base = p * G::XS;
-    fft_n2k<L, false, true>(v, xch, base, R1 + 1, 1, t, a.tw);
+    PL::template fwd<true>(v, xch, base, 1, t, a.tw);
     // natural order into the exchange area, then split the two spectra
     // X_a = (Z[k] + conj Z[L-k]) / 2, X_b = (Z[k] - conj Z[L-k]) / 2i
     C* z = xch + base;
 #pragma unroll
-    for (int q = 0; q < R2 / R1; ++q)
-#pragma unroll
-        for (int k1 = 0; k1 < R1; ++k1) z[t + q * R1 + R2 * k1] = v[q * R1 + k1];
+    for (int s = 0; s < S; ++s) z[PL::kidx(t, s)] = v[s];
     __syncthreads();
     if (active) {
         C* A = a.A + (long long)b * N * N * N1;
-        for (int k = t; k < N; k += R1) {
+        for (int k = t; k < N; k += TH) {
             C xa, xb;
             split_lines(z, k, L, xa, xb);
             A[la * N1 + k] = xa;
@@ -132,9 +132,10 @@ __global__ void __launch_bounds__(Geo<T, L>::CT) k_colpass(ConvArgs<T> a) {
     wait_prior_grid();   // results of the previous kernel on the stream
     using C = cplx_t<T>;
     using G = Geo<T, L>;
-    constexpr int N = L / 2, N1 = N + 1, R1 = G::R1, R2 = G::R2, W = G::W, Q = R2 / R1;
+    using PL = typename G::PL;
+    constexpr int N = L / 2, N1 = N + 1, TH = G::TH, S = G::S, W = G::W;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* xch = reinterpret_cast<C*>(smem_raw);   // L * W
+    C* xch = reinterpret_cast<C*>(smem_raw);   // XL * W
 
     const int b = blockIdx.z;
     if (a.active && !a.active[b]) return;
@@ -158,39 +159,35 @@ __global__ void __launch_bounds__(Geo<T, L>::CT) k_colpass(ConvArgs<T> a) {
         in = Bb + (long long)o * (2 * N) * N1 + col; out = Ab + (long long)o * N * N1 + col; stride = N1;
     }
 
-    C v[R2];
+    C v[S];
     const C zero = cmake<C>((T)0, (T)0);
     if (MODE == COL_INV_J) {
         // k-layout load of all L rows (column 0: merge slots k and L - k)
 #pragma unroll
-        for (int q = 0; q < Q; ++q)
-#pragma unroll
-            for (int k1 = 0; k1 < R1; ++k1) {
-                const int k = t + q * R1 + R2 * k1;
-                C x = ok ? in[k * stride] : zero;
-                if (col0 && c == 0) x = slot_merge(x, in[((L - k) & (L - 1)) * stride], k, N);
-                v[q * R1 + k1] = x;
-            }
-        fft_k2n<L, true>(v, xch, c, R1 * W, W, t, a.tw);
+        for (int s = 0; s < S; ++s) {
+            const int k = PL::kidx(t, s);
+            C x = ok ? in[k * stride] : zero;
+            if (col0 && c == 0) x = slot_merge(x, in[((L - k) & (L - 1)) * stride], k, N);
+            v[s] = x;
+        }
+        PL::inv(v, xch, c, W, t, a.tw);
     } else {
         // n-layout load of the N nonzero rows
 #pragma unroll
-        for (int m = 0; m < R2; ++m) {
-            const int n = t + R1 * m;
+        for (int m = 0; m < S; ++m) {
+            const int n = t + TH * m;
             // rows outside [p0, p1) are zero planes (not even written)
             const bool live = MODE != COL_CONV_I || (n >= a.plane_lo() && n < a.plane_hi());
-            v[m] = (ok && m < R2 / 2 && live) ? in[n * stride] : zero;
+            v[m] = (ok && m < S / 2 && live) ? in[n * stride] : zero;
         }
-        fft_n2k<L, false, true>(v, xch, c, R1 * W, W, t, a.tw);
+        PL::template fwd<true>(v, xch, c, W, t, a.tw);
     }
 
     if (MODE == COL_FWD_J) {
-        if (col0) split_column0<L>(v, xch, c, t);   // column 0: separate F0 and FN
+        if (col0) split_column0<PL, L>(v, xch, c, t);   // column 0: separate F0 and FN
         if (ok) {
 #pragma unroll
-            for (int q = 0; q < Q; ++q)
-#pragma unroll
-                for (int k1 = 0; k1 < R1; ++k1) out[(t + q * R1 + R2 * k1) * stride] = v[q * R1 + k1];
+            for (int s = 0; s < S; ++s) out[PL::kidx(t, s) * stride] = v[s];
         }
         return;
     }
@@ -204,56 +201,48 @@ __global__ void __launch_bounds__(Geo<T, L>::CT) k_colpass(ConvArgs<T> a) {
         if (col0 && (o == 0 || o == N)) {   // y = F0 + i FN, both Hermitian in p
             if (c == 0) {
 #pragma unroll
-                for (int q = 0; q < Q; ++q)
-#pragma unroll
-                    for (int k1 = 0; k1 < R1; ++k1) xch[t + q * R1 + R2 * k1] = v[q * R1 + k1];
+                for (int s = 0; s < S; ++s) xch[PL::kidx(t, s)] = v[s];
             }
             __syncthreads();
             if (c == 0) {
                 const T half = (T)0.5;
 #pragma unroll
-                for (int q = 0; q < Q; ++q)
-#pragma unroll
-                    for (int k1 = 0; k1 < R1; ++k1) {
-                        const int k = t + q * R1 + R2 * k1;
-                        const int ii = k <= N ? k : L - k;
-                        const T g0 = g[(long long)ii * N1 * N1], gn = g[(long long)ii * N1 * N1 + N];
-                        // (g0 + gN) y(p) / 2 + (g0 - gN) conj y(-p) / 2
-                        const C yr = cconj(xch[(L - k) & (L - 1)]);
-                        const C y = v[q * R1 + k1];
-                        const T sp = (g0 + gn) * half, sm = (g0 - gn) * half;
-                        v[q * R1 + k1] = cmake<C>(y.x * sp + yr.x * sm, y.y * sp + yr.y * sm);
-                    }
+                for (int s = 0; s < S; ++s) {
+                    const int k = PL::kidx(t, s);
+                    const int ii = k <= N ? k : L - k;
+                    const T g0 = g[(long long)ii * N1 * N1], gn = g[(long long)ii * N1 * N1 + N];
+                    // (g0 + gN) y(p) / 2 + (g0 - gN) conj y(-p) / 2
+                    const C yr = cconj(xch[(L - k) & (L - 1)]);
+                    const C y = v[s];
+                    const T sp = (g0 + gn) * half, sm = (g0 - gn) * half;
+                    v[s] = cmake<C>(y.x * sp + yr.x * sm, y.y * sp + yr.y * sm);
+                }
             }
             __syncthreads();
             if (c != 0) {
 #pragma unroll
-                for (int q = 0; q < Q; ++q)
-#pragma unroll
-                    for (int k1 = 0; k1 < R1; ++k1) {
-                        const int k = t + q * R1 + R2 * k1;
-                        const int ii = k <= N ? k : L - k;
-                        v[q * R1 + k1] = cscale(v[q * R1 + k1], g[(long long)ii * N1 * N1]);
-                    }
+                for (int s = 0; s < S; ++s) {
+                    const int k = PL::kidx(t, s);
+                    const int ii = k <= N ? k : L - k;
+                    v[s] = cscale(v[s], g[(long long)ii * N1 * N1]);
+                }
             }
         } else {
 #pragma unroll
-            for (int q = 0; q < Q; ++q)
-#pragma unroll
-                for (int k1 = 0; k1 < R1; ++k1) {
-                    const int k = t + q * R1 + R2 * k1;
-                    const int ii = k <= N ? k : L - k;
-                    v[q * R1 + k1] = cscale(v[q * R1 + k1], g[(long long)ii * N1 * N1]);
-                }
+            for (int s = 0; s < S; ++s) {
+                const int k = PL::kidx(t, s);
+                const int ii = k <= N ? k : L - k;
+                v[s] = cscale(v[s], g[(long long)ii * N1 * N1]);
+            }
         }
-        fft_k2n<L, true>(v, xch, c, R1 * W, W, t, a.tw);
+        PL::inv(v, xch, c, W, t, a.tw);
     }
     // n-layout store of the first N rows
     if (ok) {
 #pragma unroll
-        for (int m = 0; m < R2; ++m) {
-            const int n = t + R1 * m;
-            if (m < R2 / 2 && (MODE != COL_CONV_I || (n >= a.plane_lo() && n < a.plane_hi())))
+        for (int m = 0; m < S; ++m) {
+            const int n = t + TH * m;
+            if (m < S / 2 && (MODE != COL_CONV_I || (n >= a.plane_lo() && n < a.plane_hi())))
                 out[n * stride] = v[m];
         }
     }
@@ -265,40 +254,39 @@ __global__ void __launch_bounds__(Geo<T, L>::KT) k_kpass_inv(ConvArgs<T> a) {
     wait_prior_grid();   // results of the previous kernel on the stream
     using C = cplx_t<T>;
     using G = Geo<T, L>;
-    constexpr int N = L / 2, N1 = N + 1, R1 = G::R1, R2 = G::R2, Q = R2 / R1;
+    using PL = typename G::PL;
+    constexpr int N = L / 2, N1 = N + 1, TH = G::TH, S = G::S;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* xch = reinterpret_cast<C*>(smem_raw);
 
     const int b = blockIdx.z;
     if (a.active && !a.active[b]) return;
-    const int t = threadIdx.x % R1;
-    const int p = threadIdx.x / R1;
+    const int t = threadIdx.x % TH;
+    const int p = threadIdx.x / TH;
     const long long pair = (long long)a.plane_lo() * (N / 2) + (long long)blockIdx.x * G::P + p;
     const bool active = pair < (long long)a.plane_hi() * (N / 2);
     const long long la = 2 * pair, lb = la + 1;
     const C* A = a.A + (long long)b * N * N * N1;
 
-    C v[R2];
+    C v[S];
 #pragma unroll
-    for (int q = 0; q < Q; ++q)
-#pragma unroll
-        for (int k1 = 0; k1 < R1; ++k1) {
-            const int k = t + q * R1 + R2 * k1;
-            C z = cmake<C>((T)0, (T)0);
-            if (active) {
-                const C xa = line_spectrum(A + la * N1, k, N);
-                const C xb = line_spectrum(A + lb * N1, k, N);
-                z = cmake<C>(xa.x - xb.y, xa.y + xb.x);   // xa + i xb
-            }
-            v[q * R1 + k1] = z;
+    for (int s = 0; s < S; ++s) {
+        const int k = PL::kidx(t, s);
+        C z = cmake<C>((T)0, (T)0);
+        if (active) {
+            const C xa = line_spectrum(A + la * N1, k, N);
+            const C xb = line_spectrum(A + lb * N1, k, N);
+            z = cmake<C>(xa.x - xb.y, xa.y + xb.x);   // xa + i xb
         }
-    fft_k2n<L, true>(v, xch, p * G::XS, R1 + 1, 1, t, a.tw);
+        v[s] = z;
+    }
+    PL::inv(v, xch, p * G::XS, 1, t, a.tw);
     if (active) {
         typename OutOf<T>::type* out = a.v + (long long)b * N * N * N;
 #pragma unroll
-        for (int m = 0; m < R2; ++m) {
-            const int n = t + R1 * m;
-            if (m < R2 / 2) {
+        for (int m = 0; m < S; ++m) {
+            const int n = t + TH * m;
+            if (m < S / 2) {
                 out[la * N + n] = to_out(v[m].x);
                 out[lb * N + n] = to_out(v[m].y);
             }
@@ -347,6 +335,7 @@ __global__ void __launch_bounds__(512) k_plane_fwd(ConvArgs<T> a) {
                 __syncthreads();
                 if (act) {
                     const double* q = a.q + (long long)b * a.q_stride + (a.q_row ? (long long)a.q_row[b] * a.q_row_stride : 0);
+                    const float* q32 = a.q32 ? a.q32 + (long long)b * a.q32_stride : nullptr;
 #pragma unroll
                     for (int half = 0; half < 2; ++half) {
                         const long long l = half ? lb : la;
@@ -354,7 +343,7 @@ __global__ void __launch_bounds__(512) k_plane_fwd(ConvArgs<T> a) {
                         const int s0 = a.rec.line_off[l], s1 = a.rec.line_off[l + 1];
                         for (int s = s0 + t; s < s1; s += R1) {
                             const int k = a.rec.src_lin[s] - (int)(l * N);
-                            r[k] = source_value<T>(a.rec, s, q);
+                            r[k] = source_value<T>(a.rec, s, q, q32);
                         }
                     }
                 }
@@ -411,7 +400,7 @@ __global__ void __launch_bounds__(512) k_plane_fwd(ConvArgs<T> a) {
                 v[m] = (ok && m < R2 / 2) ? plane[(long long)n * N1 + col] : cmake<C>((T)0.0, (T)0.0);
             }
             fft_n2k<L, false, true>(v, xch, c, R1 * G::PW, G::PW, t, a.tw);
-            if (col0 == 0) split_column0<L>(v, xch, c, t);
+            if (col0 == 0) split_column0<Plan2<L>, L>(v, xch, c, t);
             if (ok) {
 #pragma unroll
                 for (int q2 = 0; q2 < Q; ++q2)
@@ -507,7 +496,7 @@ void configure_conv() {
     using G = Geo<T, L>;
     constexpr int N = L / 2;
     const size_t smem_k = (size_t)G::P * G::XS * sizeof(C) + (size_t)G::P * 2 * N * sizeof(T);
-    const size_t smem_c = (size_t)L * G::W * sizeof(C);
+    const size_t smem_c = (size_t)G::XL * G::W * sizeof(C);
     // once per instantiation (thread-safe static initialisation)
     static const bool configured = [&]() {
         BAE_CUDA(cudaFuncSetAttribute(k_kpass_fwd<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_k));
@@ -534,7 +523,7 @@ void launch_sched(const ConvArgs<T>& a, cudaStream_t st, int sched) {
     using PG = PlaneGeo<T, L>;
     constexpr int N = L / 2;
     const size_t smem_k = (size_t)G::P * G::XS * sizeof(C) + (size_t)G::P * 2 * N * sizeof(T);
-    const size_t smem_c = (size_t)L * G::W * sizeof(C);
+    const size_t smem_c = (size_t)G::XL * G::W * sizeof(C);
     const int nb = a.nbatch;
     const int np = a.plane_hi() - a.plane_lo();   // x-planes holding sources or read outputs
     const dim3 gk(ceil_div((long long)np * N / 2, G::P), 1, nb);
@@ -586,7 +575,8 @@ void run_conv(const ConvArgs<T>& a, cudaStream_t st) {
         int sched = tune_lookup(key);
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         BAE_CUDA(cudaStreamIsCapturing(st, &cs));
-        if (sched < 0 && cs != cudaStreamCaptureStatusNone) sched = a.nbatch <= 4 ? SCHED_PLANE : SCHED_PASSES;
+        if (sched < 0 && (cs != cudaStreamCaptureStatusNone || a.no_tune))
+            sched = a.nbatch <= 4 ? SCHED_PLANE : SCHED_PASSES;
         if (sched >= 0) {
             launch_sched<T, L>(a, st, sched);
             return;

@@ -218,4 +218,106 @@ __device__ __forceinline__ void fft_k2n(C* v, C* xch, int base, int sk, int sn, 
     rdft<R2, INV>(v);                                   // v[n2] = x[t + R1 n2]
 }
 
+
+// ------------------------------------------------------------ transform plans
+// A plan fixes how one line of length L is spread over the threads that
+// transform it: TH threads per line, S values per thread. In both plans the
+// n-layout is "thread t holds x[t + TH m] in slot m" (m < S), so a forward
+// transform's zero upper half is exactly the slots m >= S / 2; the k-layout
+// (after a forward transform, before an inverse one) is given by kidx(t, s).
+// The exchange area of a line holds XLEN positions; position p of the line
+// whose area starts at xch + base sits at xch[base + p * es], es = 1 for a
+// private area per line (line passes; XS positions apart) or es = the number
+// of lines interleaved element by element (column passes).
+
+// Two levels (fft_n2k / fft_k2n above): TH = R1, S = R2.
+template <int L>
+struct Plan2 {
+    static constexpr int R1 = Factors<L>::R1, R2 = Factors<L>::R2;
+    static constexpr int TH = R1, S = R2;
+    static constexpr int XS = R2 * (R1 + 1) + 1;   // private area stride (odd)
+    static constexpr int XLEN = L;
+    // slot s = q R1 + k1 holds X[t + q R1 + R2 k1]
+    __host__ __device__ static constexpr int kidx(int t, int s) { return t + (s / R1) * R1 + R2 * (s % R1); }
+    template <bool ZHI, typename C>
+    __device__ __forceinline__ static void fwd(C* v, C* xch, int base, int es, int t, const C* __restrict__ tw) {
+        fft_n2k<L, false, ZHI>(v, xch, base, es == 1 ? R1 + 1 : R1 * es, es, t, tw);
+    }
+    template <typename C>
+    __device__ __forceinline__ static void inv(C* v, C* xch, int base, int es, int t, const C* __restrict__ tw) {
+        fft_k2n<L, true>(v, xch, base, es == 1 ? R1 + 1 : R1 * es, es, t, tw);
+    }
+};
+
+// Three levels for L = 512 = 8 x 8 x 8: 64 threads per line, 8 values each
+// (the two-level 16 x 32 split holds 32 values per thread, which for
+// 16-byte elements means ~200-255 registers and few warps per SM). With
+// n = t + 64 m, t = t1 + 8 t2, and k = k3 + 8 k2 + 64 k1:
+//   X[k] = sum_t1 W8^{t1 k1} W64^{t1 k2} sum_t2 W8^{t2 k2}
+//          [ W512^{t k3} sum_m W8^{m k3} x[t + 64 m] ]
+// stage A: thread t, DFT over m (slots k3), twiddle W512^{t k3};
+// exchange; stage B: thread t1 + 8 k3, DFT over t2 (slots k2), twiddle
+// W64^{t1 k2}; exchange; stage C: thread k3 + 8 k2, DFT over t1: slot k1
+// holds X[t + 64 k1]. The inverse runs the stages backwards with conjugate
+// twiddles. Positions are padded by one per 64 so that 16-byte accesses of
+// the line passes do not collide in shared-memory banks.
+struct Plan3_512 {
+    static constexpr int TH = 64, S = 8;
+    static constexpr int XLEN = 512 + 8;
+    static constexpr int XS = XLEN + 1;
+    __host__ __device__ static constexpr int kidx(int t, int s) { return t + 64 * s; }
+    __device__ __forceinline__ static int pos(int p) { return p + (p >> 6); }
+
+    template <bool ZHI, typename C>
+    __device__ __forceinline__ static void fwd(C* v, C* xch, int base, int es, int t, const C* __restrict__ tw) {
+        if constexpr (ZHI) rdft_zhi<8, false>(v);       // v[k3]
+        else rdft<8, false>(v);
+#pragma unroll
+        for (int k3 = 1; k3 < 8; ++k3) v[k3] = cmul(v[k3], ldg_c(tw + t * k3));
+#pragma unroll
+        for (int k3 = 0; k3 < 8; ++k3) xch[base + pos(k3 * 64 + t) * es] = v[k3];
+        __syncthreads();
+        const int t1 = t & 7, k3 = t >> 3;
+#pragma unroll
+        for (int t2 = 0; t2 < 8; ++t2) v[t2] = xch[base + pos(k3 * 64 + t1 + 8 * t2) * es];
+        __syncthreads();
+        rdft<8, false>(v);                               // v[k2]
+#pragma unroll
+        for (int k2 = 1; k2 < 8; ++k2) v[k2] = cmul(v[k2], ldg_c(tw + 8 * t1 * k2));
+#pragma unroll
+        for (int k2 = 0; k2 < 8; ++k2) xch[base + pos((k3 * 8 + k2) * 8 + t1) * es] = v[k2];
+        __syncthreads();
+        const int c3 = t & 7, c2 = t >> 3;
+#pragma unroll
+        for (int u1 = 0; u1 < 8; ++u1) v[u1] = xch[base + pos((c3 * 8 + c2) * 8 + u1) * es];
+        __syncthreads();
+        rdft<8, false>(v);                               // v[k1] = X[t + 64 k1]
+    }
+
+    template <typename C>
+    __device__ __forceinline__ static void inv(C* v, C* xch, int base, int es, int t, const C* __restrict__ tw) {
+        const int c3 = t & 7, c2 = t >> 3;               // this thread's (k3, k2)
+        rdft<8, true>(v);                                // v[t1]
+#pragma unroll
+        for (int u1 = 0; u1 < 8; ++u1) xch[base + pos((c3 * 8 + c2) * 8 + u1) * es] = v[u1];
+        __syncthreads();
+        const int t1 = t & 7, k3 = t >> 3;
+#pragma unroll
+        for (int k2 = 0; k2 < 8; ++k2) v[k2] = xch[base + pos((k3 * 8 + k2) * 8 + t1) * es];
+        __syncthreads();
+#pragma unroll
+        for (int k2 = 1; k2 < 8; ++k2) v[k2] = cmulc(v[k2], ldg_c(tw + 8 * t1 * k2));
+        rdft<8, true>(v);                                // v[t2]
+#pragma unroll
+        for (int t2 = 0; t2 < 8; ++t2) xch[base + pos(k3 * 64 + t1 + 8 * t2) * es] = v[t2];
+        __syncthreads();
+#pragma unroll
+        for (int j3 = 0; j3 < 8; ++j3) v[j3] = xch[base + pos(j3 * 64 + t) * es];
+        __syncthreads();
+#pragma unroll
+        for (int j3 = 1; j3 < 8; ++j3) v[j3] = cmulc(v[j3], ldg_c(tw + t * j3));
+        rdft<8, true>(v);                                // v[m] = x[t + 64 m]
+    }
+};
+
 }  // namespace bae

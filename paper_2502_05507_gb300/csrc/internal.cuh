@@ -11,6 +11,7 @@ struct ProblemView {
     int device = 0;
     int N = 0;
     long long n_gm = 0;
+    long long n_unk = 0;              // unknowns: n_gm, or n_gm + |gamma+| (direct formulation)
     cudaStream_t stream = nullptr;
     SrcRecipe rec;
     const double* ghat64 = nullptr;   // octant spectrum, 1/(2N)^3 folded in

@@ -50,15 +50,6 @@ void* scratch_on_current_device() {
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
-bool on_device(const void* p) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
 template <typename T>
 void apply_into(const ProblemView& pv, const double* q, double* v, unsigned char* scratch) {
     using C = cplx_t<T>;
@@ -78,7 +69,8 @@ void apply_into(const ProblemView& pv, const double* q, double* v, unsigned char
     a.nbatch = 1;
     a.mode = SRC_DENSITY;
     a.q = q;
-    a.q_stride = pv.n_gm;
+    a.q_stride = pv.n_unk;
+    a.no_tune = true;   // never times schedules inside this call
     a.rec = pv.rec;
     a.A = reinterpret_cast<C*>(scratch);
     a.B = reinterpret_cast<C*>(scratch + bytes_A);
@@ -106,10 +98,12 @@ extern "C" int bae_potential_apply_noalloc(bae_problem* prob, int precision, con
         ProblemView pv;
         BAE_REQUIRE(prob && q && v, BAE_ERR_INVALID_ARG, "null argument");
         BAE_REQUIRE(problem_view(prob, pv), BAE_ERR_INVALID_ARG, "invalid problem handle");
+        DeviceGuard dg;   // the caller's current device is restored on return
         BAE_CUDA(cudaSetDevice(pv.device));
         BAE_REQUIRE(precision == BAE_FP64 || precision == BAE_FP32, BAE_ERR_INVALID_ARG,
                     "precision must be BAE_FP64 or BAE_FP32");
-        BAE_REQUIRE(on_device(q) && on_device(v), BAE_ERR_INVALID_ARG,
+        // device memory of another GPU is rejected inside is_device_ptr
+        BAE_REQUIRE(is_device_ptr(q) && is_device_ptr(v), BAE_ERR_INVALID_ARG,
                     "bae_potential_apply_noalloc: q and v must be device memory (host arrays would need staging)");
         BAE_REQUIRE(pv.tw64 && pv.tw32, BAE_ERR_INVALID_ARG, "problem has no twiddle table");
         unsigned char* scratch = static_cast<unsigned char*>(scratch_on_current_device());

@@ -268,21 +268,30 @@ __global__ void __launch_bounds__(32 * RAS_WARPS) k_ras_rows(const int* __restri
 // tree (a float64 warp instruction holds a GB300 sub-partition's FP64 pipe
 // for ~64 cycles; the inner float32 solves that apply M^{-1} round z to
 // float32 anyway), the sum stored as float64
+// in32 (optional): the same input already rounded to float32 ([nb][n], the
+// row the row indices select); out32 (optional): y in float32 as well
 __global__ void __launch_bounds__(256) k_precond_apply(const int* __restrict__ col,
                                                        const float* __restrict__ val, long long n, const double* in,
                                                        long long in_stride, const int* row, long long row_stride,
-                                                       double* out, long long out_stride, const int* active) {
+                                                       const float* in32, double* out, long long out_stride,
+                                                       float* out32, const int* active) {
     const int b = blockIdx.y;
     if (active && !active[b]) return;
     const double* x = in + b * in_stride + (row ? (long long)row[b] * row_stride : 0);
+    const float* x32 = in32 ? in32 + b * n : nullptr;
     double* y = out + b * out_stride;
+    float* y32 = out32 ? out32 + b * n : nullptr;
     const int lane = threadIdx.x & 31;
     const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long r = w0; r < n; r += nw) {
-        float v = val[r * MAXR + lane] * (float)x[col[r * MAXR + lane]];   // unused slots: 0 x[r]
+        const int k = col[r * MAXR + lane];   // unused slots: 0 x[r]
+        float v = val[r * MAXR + lane] * (x32 ? x32[k] : (float)x[k]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) y[r] = (double)v;
+        if (lane == 0) {
+            y[r] = (double)v;
+            if (y32) y32[r] = v;
+        }
     }
 }
 
@@ -336,13 +345,14 @@ void build_precond(const Geometry& g, double s, const double* near, Precond& out
 }
 
 void precond_apply(const Precond& p, const double* in, long long in_stride, const int* row, long long row_stride,
-                   double* out, long long out_stride, int nb, const int* active, cudaStream_t st) {
+                   double* out, long long out_stride, int nb, const int* active, cudaStream_t st, const float* in32,
+                   float* out32) {
     BAE_REQUIRE(p.built, BAE_ERR_INVALID_ARG, "internal: preconditioner applied before it was built");
     if (p.n == 0 || nb == 0) return;
     const int ctas = (int)std::min<long long>((p.n + 7) / 8, 152LL * 16);   // 8 rows per 256-thread CTA
     BAE_LAUNCH("k_precond_apply", st,
                k_precond_apply<<<dim3(ctas, nb), 256, 0, st>>>(p.col, p.val, p.n, in, in_stride, row, row_stride,
-                                                               out, out_stride, active));
+                                                               in32, out, out_stride, out32, active));
 }
 
 }  // namespace bae

@@ -54,8 +54,11 @@ void build_precond(const Geometry& g, double s, const double* near, Precond& out
 // out[b] = M^{-1} in[b] with in[b] at in + b in_stride (+ row[b] row_stride
 // when row is not null, device), out[b] at out + b out_stride, for items
 // with active[b] != 0 when active is not null (a mask; all device arrays,
-// capturable in a graph).
+// capturable in a graph). in32 (optional): the selected input rows already
+// rounded to float32, [nb][n] (read instead of converting in); out32
+// (optional): out rounded to float32 as well, [nb][n].
 void precond_apply(const Precond& p, const double* in, long long in_stride, const int* row, long long row_stride,
-                   double* out, long long out_stride, int nb, const int* active, cudaStream_t st);
+                   double* out, long long out_stride, int nb, const int* active, cudaStream_t st,
+                   const float* in32 = nullptr, float* out32 = nullptr);
 
 }  // namespace bae

@@ -29,22 +29,28 @@ def ctx():
     c.close()
 
 
-def _problem(ctx, P):
+def _problem(ctx, P, layer="double"):
     import torch
     from paper_2502_05507_gb300 import Problem
-    return Problem(ctx, torch.from_numpy(P.phi).cuda(), P.grid.h, P.grid.origin, P.kappa2, "double")
+    return Problem(ctx, torch.from_numpy(P.phi).cuda(), P.grid.h, P.grid.origin, P.kappa2, layer)
 
 
-@pytest.mark.parametrize("N,precision", [(32, "fp64"), (32, "fp32"), (64, "fp32")])
-def test_noalloc_matches_allocating_apply_twice(ctx, N, precision):
+# the last case runs a smaller float64 problem after the larger float32 one
+# has left its data in the shared array
+CASES = [(32, "fp64", "double"), (32, "fp32", "double"), (32, "fp64", "single"), (32, "fp32", "direct"),
+         (64, "fp32", "double"), (64, "fp32", "direct"), (32, "fp64", "double")]
+
+
+@pytest.mark.parametrize("N,precision,layer", CASES)
+def test_noalloc_matches_allocating_apply_twice(ctx, N, precision, layer):
     import torch
     from paper_2502_05507_gb300 import bae
     L = bae.lib()
     P = W.torus_helmholtz(N, kappa2=10.0)
-    prob = _problem(ctx, P)
+    prob = _problem(ctx, P, layer)
     prec = bae._PREC[precision]
     for call in range(2):   # two calls in a row share the same static scratch
-        q = torch.from_numpy(W.random_density(prob.n_gm, seed=100 + call)).cuda()
+        q = torch.from_numpy(W.random_density(prob.n_unknowns, seed=100 + call)).cuda()
         ref = torch.empty((N,) * 3, dtype=torch.float64, device="cuda")
         got = torch.full((N,) * 3, float("nan"), dtype=torch.float64, device="cuda")
         assert L.bae_potential_apply(prob._h, prec, q.data_ptr(), ref.data_ptr()) == bae.OK
@@ -61,7 +67,7 @@ def test_noalloc_rejects_oversize_and_host_arrays(ctx):
     L = bae.lib()
     P = W.torus_helmholtz(128, kappa2=10.0)
     prob = _problem(ctx, P)
-    q = torch.zeros(prob.n_gm, dtype=torch.float64, device="cuda")
+    q = torch.zeros(prob.n_unknowns, dtype=torch.float64, device="cuda")
     v = torch.zeros((128,) * 3, dtype=torch.float64, device="cuda")
     rc = L.bae_potential_apply_noalloc(prob._h, bae.FP32, q.data_ptr(), v.data_ptr())
     assert rc == bae.ERR_INVALID_ARG
@@ -69,8 +75,24 @@ def test_noalloc_rejects_oversize_and_host_arrays(ctx):
     prob.close()
     P = W.sphere_exp(16)
     prob = _problem(ctx, P)
-    qh = np.zeros(prob.n_gm)
+    qh = np.zeros(prob.n_unknowns)
     vh = np.zeros((16,) * 3)
     rc = L.bae_potential_apply_noalloc(prob._h, bae.FP64, qh.ctypes.data, vh.ctypes.data)
     assert rc == bae.ERR_INVALID_ARG
+    prob.close()
+
+
+def test_noalloc_restores_current_device(ctx):
+    """The call switches to the problem's device while it runs and gives
+    the caller back the device that was current before."""
+    import torch
+    from paper_2502_05507_gb300 import bae
+    L = bae.lib()
+    P = W.sphere_exp(16)
+    prob = _problem(ctx, P)
+    q = torch.zeros(prob.n_unknowns, dtype=torch.float64, device="cuda")
+    v = torch.zeros((16,) * 3, dtype=torch.float64, device="cuda")
+    before = torch.cuda.current_device()
+    assert L.bae_potential_apply_noalloc(prob._h, bae.FP64, q.data_ptr(), v.data_ptr()) == bae.OK
+    assert torch.cuda.current_device() == before
     prob.close()
