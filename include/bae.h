@@ -100,7 +100,20 @@ typedef struct bae_options {
                             in every refinement step, 2 in the steps after
                             the first, 0 never. The solution is the same to
                             tol.                                           */
+    int    particular;   /* particular solution u_p = G_h[chi_{M+} f] (eq. [ps]):
+                            BAE_PARTICULAR_LATTICE (default) convolves with the
+                            free-lattice G_h; BAE_PARTICULAR_BOX solves the
+                            auxiliary problem of eq. [aux] on the finite box
+                            (zero on the layers 0 and N of every axis), as
+                            Algorithm 1 prints it. u on N+ is the same discrete
+                            solution either way; the density differs. The box
+                            form costs one float64-accurate apply more per
+                            solve (u_p is kept, not folded into the
+                            residuals). Not for BAE_LAYER_DIRECT.           */
 } bae_options;
+
+#define BAE_PARTICULAR_LATTICE 0
+#define BAE_PARTICULAR_BOX     1
 
 typedef struct bae_stats {
     int    iterations;       /* GMRES iterations, all cycles and refinement steps */
@@ -316,6 +329,15 @@ int bae_potential_apply_noalloc(bae_problem* prob, int precision, const double* 
  * up(m) = sum_{x in M+} G_s(m-x) h^2 f(x) on the whole grid.
  * f, up: N^3 doubles (paper sign). precision BAE_FP64 or BAE_FP32. */
 int bae_particular(bae_problem* prob, int precision, const double* f, double* up);
+
+/* Particular solution on the finite auxiliary box (eq. [aux] with eq. [ps]):
+ * up solves (6 + s) up(m) - sum of the six neighbours = h^2 f(m) [m in M+]
+ * for every m with all indices in [1, N-1], with up = 0 on the layers of
+ * index 0 and N (s = kappa2 h^2). It is the convolution of the source,
+ * extended oddly about those layers, with the (2N)-periodic Green's
+ * function, on the same zero-padded transform as the potential apply.
+ * f, up: N^3 doubles (paper sign). precision BAE_FP64 or BAE_DF64. */
+int bae_box_particular(bae_problem* prob, int precision, const double* f, double* up);
 
 /* ---------------------------------------------------- solve (Algorithm 1) */
 

@@ -40,7 +40,8 @@ class GeometryError(BAEError):
 class Options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("restart", ctypes.c_int),
                 ("precision", ctypes.c_int), ("max_refine", ctypes.c_int), ("inner_tol", ctypes.c_double),
-                ("use_graphs", ctypes.c_int), ("residual_precision", ctypes.c_int), ("precond", ctypes.c_int)]
+                ("use_graphs", ctypes.c_int), ("residual_precision", ctypes.c_int), ("precond", ctypes.c_int),
+                ("particular", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -107,6 +108,7 @@ def lib():
             "bae_potential_apply_noalloc": (_I, [_P, _I, _P, _P]),
             "bae_boundary_apply": (_I, [_P, _I, _P, _P]),
             "bae_particular": (_I, [_P, _I, _P, _P]),
+            "bae_box_particular": (_I, [_P, _I, _P, _P]),
             "bae_solve": (_I, [_P, _P, _P, _P, _P, _P, _P]),
             "bae_solve_batched": (_I, [_P, _I, _P, _P, _P, _P, _P, _P]),
             "bae_server_create": (_I, [_I, _I, ctypes.c_int64, _P]),
@@ -131,7 +133,7 @@ EXPORTED = ["bae_version", "bae_last_error", "bae_default_options", "bae_launch_
             "bae_lgf_table", "bae_lgf_spectrum", "bae_problem_create", "bae_problem_destroy",
             "bae_problem_sizes", "bae_problem_unknowns", "bae_gamma_plus", "bae_interior_mask", "bae_problem_plane_range", "bae_boundary_points", "bae_classification", "bae_potential_apply",
             "bae_potential_apply_noalloc",
-            "bae_boundary_apply", "bae_particular", "bae_solve", "bae_solve_batched", "bae_server_create",
+            "bae_boundary_apply", "bae_particular", "bae_box_particular", "bae_solve", "bae_solve_batched", "bae_server_create",
             "bae_server_submit", "bae_server_poll", "bae_server_density", "bae_server_release", "bae_server_clock",
             "bae_server_destroy"]
 
@@ -343,6 +345,13 @@ class Problem:
         _check(lib().bae_boundary_apply(self._h, _PREC[precision], _ptr(q), _ptr(out)))
         return out
 
+    def box_particular(self, f, precision="fp64", out=None):
+        """bae_box_particular: u_p on the finite auxiliary box of eq. [aux]."""
+        f = _as_f64(f)
+        out = _new((self.N,) * 3, np.float64, f) if out is None else out
+        _check(lib().bae_box_particular(self._h, _PREC[precision], _ptr(f), _ptr(out)))
+        return out
+
     def particular(self, f, precision="fp64", out=None):
         f = _as_f64(f)
         out = _new((self.N,) * 3, np.float64, f) if out is None else out
@@ -350,9 +359,11 @@ class Problem:
         return out
 
     def _opts(self, tol, precision, max_iter, restart, max_refine, inner_tol, use_graphs=False,
-              residual_precision=None, precond=None):
+              residual_precision=None, precond=None, particular=None):
         o = Options()
         lib().bae_default_options(ctypes.byref(o))
+        if particular is not None:   # "lattice" (free-lattice G_h) or "box" (eq. [aux])
+            o.particular = {"lattice": 0, "box": 1}[particular]
         o.use_graphs = 1 if use_graphs else 0
         if precond is not None:   # False/0: never, True/1: every refinement step, 2: after the first
             o.precond = int(precond)
@@ -372,7 +383,7 @@ class Problem:
 
     def solve(self, f, g, tol=1e-10, precision="fp64", max_iter=None, restart=None, max_refine=None,
               inner_tol=None, density=None, u=None, allow_not_converged=False, use_graphs=False,
-              residual_precision=None, precond=None):
+              residual_precision=None, precond=None, particular=None):
         """Returns (density, u, stats dict). f (N^3) and g (n_gm) may be
         torch CUDA tensors or numpy arrays; outputs follow f's kind."""
         f = _as_f64(f)
@@ -381,7 +392,7 @@ class Problem:
         u = _new((self.N,) * 3, np.float64, f) if u is None else u
         st = Stats()
         o = self._opts(tol, precision, max_iter, restart, max_refine, inner_tol, use_graphs, residual_precision,
-                       precond)
+                       precond, particular)
         rc = lib().bae_solve(self._h, _ptr(f), _ptr(g), ctypes.byref(o), _ptr(density), _ptr(u), ctypes.byref(st))
         _check(rc, allow_not_converged)
         return density, u, st.as_dict()

@@ -7,6 +7,7 @@
 #include <condition_variable>
 #include <mutex>
 #include <set>
+#include <tuple>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -217,13 +218,15 @@ namespace bae {
 struct SpectrumCache {
     std::mutex mu;
     std::condition_variable cv;
-    std::map<std::pair<int, uint64_t>, std::shared_ptr<Spectrum>> map;
-    std::set<std::pair<int, uint64_t>> building;
+    // key: (N, kind, bit pattern of s); kind 0 = the free-lattice G_s, 1 =
+    // the finite-box Green's function of eq. [aux]
+    std::map<std::tuple<int, int, uint64_t>, std::shared_ptr<Spectrum>> map;
+    std::set<std::tuple<int, int, uint64_t>> building;
 
-    std::shared_ptr<Spectrum> get(int N, double s, cudaStream_t st) {
+    std::shared_ptr<Spectrum> get(int N, double s, cudaStream_t st, int kind = 0) {
         uint64_t bits;
         std::memcpy(&bits, &s, sizeof(bits));
-        const auto key = std::make_pair(N, bits);
+        const auto key = std::make_tuple(N, kind, bits);
         std::unique_lock<std::mutex> lock(mu);
         for (;;) {
             auto it = map.find(key);
@@ -247,10 +250,16 @@ struct SpectrumCache {
             BAE_CUDA(cudaMalloc(&sp->gds, n3 * sizeof(dsf)));
             sp->bytes = n3 * (sizeof(double) + sizeof(float) + sizeof(dsf));
             const double L = 2.0 * N;
-            lgf_spectrum(N, s, 1.0 / (L * L * L), sp->g64, sp->g32, st);
-            to_dsf(sp->g64, n3, sp->gds, st);
-            BAE_CUDA(cudaMalloc(&sp->near, NEAR_TAB * sizeof(double)));
-            lgf_table(NEAR_TN, s, sp->near, st);
+            if (kind == 1) {
+                box_spectrum(N, s, 1.0 / (L * L * L), sp->g64, sp->g32, st);
+                to_dsf(sp->g64, n3, sp->gds, st);
+            } else {
+                lgf_spectrum(N, s, 1.0 / (L * L * L), sp->g64, sp->g32, st);
+                to_dsf(sp->g64, n3, sp->gds, st);
+                alloc_check(NEAR_TAB * sizeof(double));
+                BAE_CUDA(cudaMalloc(&sp->near, NEAR_TAB * sizeof(double)));
+                lgf_table(NEAR_TN, s, sp->near, st);
+            }
             BAE_CUDA(cudaStreamSynchronize(st));
         } catch (...) {
             lock.lock();
@@ -318,7 +327,7 @@ struct bae_ctx {
         return tw[L] = t;
     }
 
-    std::shared_ptr<Spectrum> spectrum(int N, double s) { return cache->get(N, s, stream); }
+    std::shared_ptr<Spectrum> spectrum(int N, double s, int kind = 0) { return cache->get(N, s, stream, kind); }
 };
 
 struct bae_problem {
@@ -326,6 +335,7 @@ struct bae_problem {
     Geometry geo;
     Precond pre;   // right preconditioner, built on the first mixed solve that asks for it
     std::shared_ptr<Spectrum> spec;
+    std::shared_ptr<Spectrum> spec_box;   // finite-box spectrum, fetched by the first box apply
     double kappa2 = 0.0, s = 0.0;
     // direct formulation: the Arnoldi gather reads the operator rows as they
     // are (row r of the vector at index r, weight 1)
@@ -427,6 +437,29 @@ out_t<T>* apply_volume(bae_problem* P, int nb, const double* f, double scale, bo
     a.v = vbuf<T>(P, nb);
     conv_apply<T>(a, P->ctx->stream);
     return a.v;
+}
+
+// v[b] = G_box[chi_{M+} scale f[b]] (eq. [aux]): the finite-box particular
+// solution, float64 or double-float
+template <typename T>
+out_t<T>* apply_box(bae_problem* P, int nb, const double* f, double scale, bool pruned) {
+    static_assert(sizeof(T) == 8, "the finite-box apply is float64-accurate");
+    if (!P->spec_box) P->spec_box = P->ctx->spectrum(P->geo.N, P->s, 1);
+    ConvArgs<T> a = conv_args<T>(P, nb, pruned);
+    if constexpr (std::is_same<T, dsf>::value) a.ghat = P->spec_box->gds;
+    else a.ghat = reinterpret_cast<const T*>(P->spec_box->g64);
+    a.mode = SRC_VOLUME;
+    a.box = true;
+    a.f = f;
+    a.flags = P->geo.flags;
+    a.scale = scale;
+    a.v = vbuf<T>(P, nb);
+    conv_apply<T>(a, P->ctx->stream);
+    return a.v;
+}
+
+double* apply_box64(bae_problem* P, int prec, int nb, const double* f, double scale, bool pruned = false) {
+    return prec == BAE_DF64 ? apply_box<dsf>(P, nb, f, scale, pruned) : apply_box<double>(P, nb, f, scale, pruned);
 }
 
 // v[b] = K q[b] + sum_{x in M+} G(m - x) scale f[b](x): one convolution of
@@ -578,8 +611,8 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
     double* scal = ws.arnScal.need((long long)nb * 5);
     a.est = scal;
     a.target = scal + nb;
-    a.inv = scal + 2 * nb;
-    int* ibuf = ws.arnI.need((long long)nb * 7 + 2);
+    a.inv = scal + 2 * nb;   // scal + 3 nb: spare
+    int* ibuf = ws.arnI.need((long long)nb * 6 + 1);
     a.flag = ibuf;
     a.ncols = ibuf + nb;
     int* member = ibuf + 2 * nb;
@@ -593,9 +626,6 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
     a.gflag = ibuf + 4 * nb + 1;
     a.live = ibuf + 5 * nb + 1;
     a.v32 = ws.arnV32.need((long long)nb * n);
-    a.reo = ibuf + 6 * nb + 1;
-    a.any_reo = ibuf + 7 * nb + 1;
-    a.hn = scal + 3 * nb;
     a.n2 = scal + 4 * nb;
     a.pcol = ws.arnP.need((long long)nb * 2 * (m + 2));
     double* r = ws.r.need((long long)nb * n);
@@ -616,7 +646,7 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
     BAE_CUDA(cudaMemsetAsync(a.ctr, 0, (size_t)nb * 3 * sizeof(unsigned int), st));
     BAE_CUDA(cudaMemsetAsync(a.bar, 0, 2 * sizeof(unsigned long long), st));
     BAE_CUDA(cudaMemsetAsync(a.err, 0, sizeof(int), st));
-    BAE_CUDA(cudaMemsetAsync(a.any_reo, 0, sizeof(int), st));
+
     // the kernels that decide the flags also write live[b] into mapped host
     // memory: no copy between the replayed steps
     volatile int* hlive = P->ctx->pinned_flags(nb);
@@ -813,6 +843,7 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
             arn_finish(a, x, st);
             BAE_CUDA(cudaMemcpyAsync(ncols.data(), a.ncols, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
             BAE_CUDA(cudaMemcpyAsync(est.data(), a.est, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+
             if (a.coop_grid > 0) BAE_CUDA(cudaMemcpyAsync(&coop_err, a.err, sizeof(int), cudaMemcpyDeviceToHost, st));
             BAE_CUDA(cudaStreamSynchronize(st));
             BAE_REQUIRE(coop_err == 0, BAE_ERR_TIMEOUT,
@@ -860,6 +891,11 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
     BAE_REQUIRE(o.residual_precision == BAE_FP64 || o.residual_precision == BAE_DF64, BAE_ERR_INVALID_ARG,
                 "residual_precision must be BAE_FP64 or BAE_DF64");
     BAE_REQUIRE(o.precond >= 0 && o.precond <= 2, BAE_ERR_INVALID_ARG, "precond must be 0, 1 or 2");
+    BAE_REQUIRE(o.particular == BAE_PARTICULAR_LATTICE || o.particular == BAE_PARTICULAR_BOX, BAE_ERR_INVALID_ARG,
+                "particular must be BAE_PARTICULAR_LATTICE or BAE_PARTICULAR_BOX");
+    BAE_REQUIRE(o.particular == BAE_PARTICULAR_LATTICE || P->geo.layer != BAE_LAYER_DIRECT, BAE_ERR_INVALID_ARG,
+                "the finite-box particular solution is for the layer formulations (the direct formulation's "
+                "difference potentials use the free-lattice G)");
     // arithmetic of every float64-accurate apply (particular solution,
     // refinement residuals, reconstruction)
     const int hp = o.precision == BAE_MIXED ? o.residual_precision : o.precision;
@@ -916,6 +952,11 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
     // residual is b - A x = b' - rows(P x + u_p, x) (one combined apply); u
     // is P x + u_p on M+ and x on gamma-.
     const bool mixed = o.precision == BAE_MIXED;
+    // finite-box particular solution (eq. [aux]): kept in float64-accurate
+    // arithmetic for b and for u, never folded into the residual applies
+    // (the layer potential uses the free-lattice G, the box part does not)
+    const bool box = o.particular == BAE_PARTICULAR_BOX;
+    const bool comb = (mixed || direct) && !box;   // residuals convolve layer + volume sources together
     double* bvec = P->ws().x.need((long long)nb * n * 3);   // [b | q | r] blocks
     double* q = bvec + (long long)nb * n;
     double* res = q + (long long)nb * n;
@@ -928,7 +969,7 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
         BAE_CUDA(cudaMemcpy2DAsync(bp, (size_t)n * sizeof(double), d_g, (size_t)ng * sizeof(double),
                                    (size_t)ng * sizeof(double), nb, cudaMemcpyDeviceToDevice, st));
     }
-    if (mixed) {
+    if (mixed && !box) {
         const float* v = apply_volume<float>(P, nb, d_f, h * h, true);
         if (direct)
             direct_rows<float, double>(v, n3, q, n, nullptr, 0, P->geo.gp, P->geo.partner_u, P->geo.t, ng, n, nb,
@@ -938,7 +979,7 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
         for (auto& s : st_local) s.applies_fp32 += 1;
     } else {
         up = P->ws().up.need((long long)nb * n3);
-        double* v = apply_volume64(P, hp, nb, d_f, h * h, true);
+        double* v = box ? apply_box64(P, hp, nb, d_f, h * h, true) : apply_volume64(P, hp, nb, d_f, h * h, true);
         BAE_CUDA(cudaMemcpyAsync(up, v, (size_t)nb * n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
         for (auto& s : st_local) s.applies_fp64 += 1;
         if (direct)
@@ -981,7 +1022,6 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
         int* d_all = P->ws().active.need(nb);
         BAE_CUDA(cudaMemcpyAsync(d_all, all.data(), nb * sizeof(int), cudaMemcpyHostToDevice, st));
         double* tmp = P->ws().tmp.need((long long)nb * n);
-        const bool comb = mixed || direct;
         double* v = comb ? apply_combined64(P, hp, nb, q, d_f, h * h, true) : apply_potential64(P, hp, nb, q, true);
         if (direct)
             direct_rows<double, double>(v, n3, q, n, nullptr, 0, P->geo.gp, P->geo.partner_u, P->geo.t, ng, n, nb,
@@ -989,7 +1029,7 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
         else
             closure_gather<double>(v, n3, P->geo.gm, P->geo.partner, P->geo.t, n, nb, tmp, n, st);
         for (auto& s : st_local) s.applies_fp64 += 1;
-        kr_sub(direct ? bp : (mixed ? d_g : bvec), tmp, d_all, nb, n, res, st);
+        kr_sub(direct ? bp : (comb ? d_g : bvec), tmp, d_all, nb, n, res, st);
         kr_norm2(res, d_all, nb, n, n2 + nb, krylov_chunks(n), n2, st);
         BAE_CUDA(cudaMemcpyAsync(rn2.data(), n2, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
         BAE_CUDA(cudaStreamSynchronize(st));
@@ -1252,6 +1292,7 @@ void bae_default_options(bae_options* o) {
     o->use_graphs = 0;
     o->residual_precision = BAE_DF64;
     o->precond = 1;
+    o->particular = BAE_PARTICULAR_LATTICE;
 }
 
 int bae_ctx_create(int device, void* stream, bae_ctx** out) {
@@ -1563,6 +1604,25 @@ int bae_particular(bae_problem* P, int precision, const double* f, double* up) {
             float* r = apply_volume<float>(P, 1, df, h2);
             widen<float>(r, n3, du, st);
         }
+        if (oh) copy_out(up, du, n3, st);
+        BAE_CUDA(cudaStreamSynchronize(st));
+        return BAE_OK;
+    });
+}
+
+int bae_box_particular(bae_problem* P, int precision, const double* f, double* up) {
+    return guarded([&]() -> int {
+        BAE_REQUIRE(P && f && up, BAE_ERR_INVALID_ARG, "null argument");
+        BAE_REQUIRE(precision == BAE_FP64 || precision == BAE_DF64, BAE_ERR_INVALID_ARG,
+                    "precision must be BAE_FP64 or BAE_DF64");
+        check_device(P->ctx);
+        cudaStream_t st = P->ctx->stream;
+        const long long n3 = P->n3();
+        const double* df = device_in(P->ws().in_f, f, n3, st);
+        const bool oh = !is_device_ptr(up);
+        double* du = oh ? P->ws().out_u.need(n3) : up;
+        double* r = apply_box64(P, precision, 1, df, P->geo.h * P->geo.h);
+        BAE_CUDA(cudaMemcpyAsync(du, r, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
         if (oh) copy_out(up, du, n3, st);
         BAE_CUDA(cudaStreamSynchronize(st));
         return BAE_OK;

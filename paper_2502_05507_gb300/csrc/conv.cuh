@@ -59,6 +59,12 @@ struct ConvArgs {
     // caller reads (p1 == 0: all N planes). Planes outside are skipped: their
     // sources are zero, and their part of v is left unwritten.
     int p0 = 0, p1 = 0;
+    // finite auxiliary box (eq. [aux], SRC_VOLUME only, float64 and
+    // double-float): the source is extended oddly about the layers 0 and N
+    // of every axis (loads of the upper half return the negated mirror
+    // instead of zero padding) and ghat is the box spectrum; runs the five
+    // separate passes
+    bool box = false;
     // never time schedules in this apply: use the choice made by an earlier
     // apply of the same (element type, N, batch size), else the default
     bool no_tune = false;

@@ -47,7 +47,10 @@ namespace {
 
 // ------------------------------------------------------------- k pass (R2C)
 // Two real k-lines (i, 2p) and (i, 2p+1) per complex transform z = x_a + i x_b.
-template <typename T, int L>
+// BOX: the finite auxiliary box of eq. [aux] (volume sources only): the
+// upper half of each line holds the negated mirror of the lower half, x[2N -
+// n] = -x[n], x[N] = 0 (odd about the layers 0 and N), instead of zeros.
+template <typename T, int L, bool BOX = false>
 __global__ void __launch_bounds__(Geo<T, L>::KT) k_kpass_fwd(ConvArgs<T> a) {
     wait_prior_grid();   // results of the previous kernel on the stream
     using C = cplx_t<T>;
@@ -97,16 +100,22 @@ __global__ void __launch_bounds__(Geo<T, L>::KT) k_kpass_fwd(ConvArgs<T> a) {
         for (int m = 0; m < S; ++m) {
             const int n = t + TH * m;
             T va = (T)0.0, vb = (T)0.0;
-            if (active && m < S / 2) {
-                const long long xa = la * N + n, xb = lb * N + n;
+            // the sample read: n in the lower half; 2N - n mirrored (BOX)
+            const int nn = m < S / 2 ? n : ((BOX && n > N) ? 2 * N - n : -1);
+            if (active && nn >= 0) {
+                const long long xa = la * N + nn, xb = lb * N + nn;
                 va = (a.flags[xa] & 1) ? (T)(a.scale * f[xa]) : (T)0;
                 vb = (a.flags[xb] & 1) ? (T)(a.scale * f[xb]) : (T)0;
+                if (m >= S / 2) {
+                    va = -va;
+                    vb = -vb;
+                }
             }
             v[m] = cmake<C>(va, vb);
         }
     }
     const int base = p * G::XS;
-    PL::template fwd<true>(v, xch, base, 1, t, a.tw);
+    PL::template fwd<!BOX>(v, xch, base, 1, t, a.tw);
     // natural order into the exchange area, then split the two spectra
     // X_a = (Z[k] + conj Z[L-k]) / 2, X_b = (Z[k] - conj Z[L-k]) / 2i
     C* z = xch + base;
@@ -127,7 +136,7 @@ __global__ void __launch_bounds__(Geo<T, L>::KT) k_kpass_fwd(ConvArgs<T> a) {
 // ----------------------------------------------------- column passes (j, i)
 enum ColMode { COL_FWD_J = 0, COL_CONV_I = 1, COL_INV_J = 2 };
 
-template <typename T, int L, int MODE>
+template <typename T, int L, int MODE, bool BOX = false>
 __global__ void __launch_bounds__(Geo<T, L>::CT) k_colpass(ConvArgs<T> a) {
     wait_prior_grid();   // results of the previous kernel on the stream
     using C = cplx_t<T>;
@@ -172,15 +181,19 @@ __global__ void __launch_bounds__(Geo<T, L>::CT) k_colpass(ConvArgs<T> a) {
         }
         PL::inv(v, xch, c, W, t, a.tw);
     } else {
-        // n-layout load of the N nonzero rows
+        // n-layout load of the N nonzero rows (BOX: and their negated
+        // mirrors in the upper half)
 #pragma unroll
         for (int m = 0; m < S; ++m) {
             const int n = t + TH * m;
+            const int nn = m < S / 2 ? n : ((BOX && n > N) ? 2 * N - n : -1);
             // rows outside [p0, p1) are zero planes (not even written)
-            const bool live = MODE != COL_CONV_I || (n >= a.plane_lo() && n < a.plane_hi());
-            v[m] = (ok && m < S / 2 && live) ? in[n * stride] : zero;
+            const bool live = nn >= 0 && (MODE != COL_CONV_I || (nn >= a.plane_lo() && nn < a.plane_hi()));
+            C x = (ok && live) ? in[nn * stride] : zero;
+            if (BOX && m >= S / 2) x = cmake<C>(-x.x, -x.y);
+            v[m] = x;
         }
-        PL::template fwd<true>(v, xch, c, W, t, a.tw);
+        PL::template fwd<!BOX>(v, xch, c, W, t, a.tw);
     }
 
     if (MODE == COL_FWD_J) {
@@ -504,6 +517,13 @@ void configure_conv() {
         BAE_CUDA(cudaFuncSetAttribute(k_colpass<T, L, COL_FWD_J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
         BAE_CUDA(cudaFuncSetAttribute(k_colpass<T, L, COL_CONV_I>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
         BAE_CUDA(cudaFuncSetAttribute(k_colpass<T, L, COL_INV_J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
+        if constexpr (sizeof(C) == 16) {
+            BAE_CUDA(cudaFuncSetAttribute(k_kpass_fwd<T, L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_k));
+            BAE_CUDA(cudaFuncSetAttribute(k_colpass<T, L, COL_FWD_J, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem_c));
+            BAE_CUDA(cudaFuncSetAttribute(k_colpass<T, L, COL_CONV_I, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem_c));
+        }
         if constexpr (PlaneGeo<T, L>::FITS) {
             BAE_CUDA(cudaFuncSetAttribute(k_plane_fwd<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)PlaneGeo<T, L>::SMEM));
@@ -528,6 +548,25 @@ void launch_sched(const ConvArgs<T>& a, cudaStream_t st, int sched) {
     const int np = a.plane_hi() - a.plane_lo();   // x-planes holding sources or read outputs
     const dim3 gk(ceil_div((long long)np * N / 2, G::P), 1, nb);
     const int ncolblk = ceil_div(N, G::W);   // column 0 also holds kk = N
+    if (a.box) {
+        // finite box: the forward passes with mirrored upper halves, the
+        // ordinary inverse passes
+        if constexpr (sizeof(C) == 16) {
+            BAE_LAUNCH(kname<T>("conv_box_kfwd.f32", "conv_box_kfwd.f64", "conv_box_kfwd.df64"), st,
+                       launch_pdl(k_kpass_fwd<T, L, true>, gk, G::KT, smem_k, st, a));
+            BAE_LAUNCH(kname<T>("conv_box_jfwd.f32", "conv_box_jfwd.f64", "conv_box_jfwd.df64"), st,
+                       launch_pdl(k_colpass<T, L, COL_FWD_J, true>, dim3(ncolblk, np, nb), G::CT, smem_c, st, a));
+            BAE_LAUNCH(kname<T>("conv_box_i.f32", "conv_box_i.f64", "conv_box_i.df64"), st,
+                       launch_pdl(k_colpass<T, L, COL_CONV_I, true>, dim3(ncolblk, 2 * N, nb), G::CT, smem_c, st, a));
+            BAE_LAUNCH(kname<T>("conv_jinv.f32", "conv_jinv.f64", "conv_jinv.df64"), st,
+                       launch_pdl(k_colpass<T, L, COL_INV_J>, dim3(ncolblk, np, nb), G::CT, smem_c, st, a));
+            BAE_LAUNCH(kname<T>("conv_kinv.f32", "conv_kinv.f64", "conv_kinv.df64"), st,
+                       launch_pdl(k_kpass_inv<T, L>, gk, G::KT, smem_k, st, a));
+            return;
+        } else {
+            throw Error(BAE_ERR_INVALID_ARG, "finite-box apply needs float64 or double-float");
+        }
+    }
     if (sched == SCHED_PLANE) {
         if constexpr (PG::FITS)
             BAE_LAUNCH(kname<T>("conv_plane_fwd.f32", "conv_plane_fwd.f64", "conv_plane_fwd.df64"), st,
@@ -556,6 +595,10 @@ void launch_sched(const ConvArgs<T>& a, cudaStream_t st, int sched) {
 template <typename T, int L>
 void run_conv(const ConvArgs<T>& a, cudaStream_t st) {
     configure_conv<T, L>();
+    if (a.box) {
+        launch_sched<T, L>(a, st, SCHED_PASSES);
+        return;
+    }
     using PG = PlaneGeo<T, L>;
     if constexpr (!PG::FITS && !CPlaneGeo<T, L>::USE) {
         launch_sched<T, L>(a, st, SCHED_PASSES);

@@ -317,100 +317,16 @@ __device__ __forceinline__ void givens_apply(double* s_col, const double* s_cs, 
     g[j] = cj * g[j];
 }
 
-// Gram-Schmidt of each Arnoldi step: one projection h1 = V^T w with the
-// norm of the remainder from the Pythagorean identity, hn^2 = ||w||^2 -
-// ||h1||^2 (V orthonormal), and a second projection (reorthogonalization,
-// the second pass of CGS2) where the remainder lost much of the norm: the
-// criterion of Daniel, Gragg, Kaufman and Stewart (1976) with eta = 1/sqrt 2,
-// hn^2 < ||w||^2 / 2. A single projection multiplies the basis' loss of
-// orthogonality by ||h1|| / hn; where the criterion keeps one pass that
-// factor is at most 1, so the loss stays at the rounding level, as with two
-// passes in every step.
-// The decision uses the same sums in both step forms (fused and
-// three-kernel), so both stay bit-identical.
-constexpr double REO_THETA = 0.5;
-
-// One warp: ||h[0..j]||^2 in a fixed order (lanes over rows, then the
-// shuffle tree), the decision, and for right-hand sides that need no second
-// projection the norm hn and 1 / hn. Lane 0 writes reo[b] (and raises
-// *any_reo when set). n2: ||w||^2 of the step.
-__device__ __forceinline__ void decide_reorth(const Arnoldi& a, int b, int j, double n2) {
-    const int lane = threadIdx.x & 31;
-    const double* h = a.h1 + (long long)b * (a.m + 1);
-    double acc = 0.0;
-    for (int i = lane; i <= j; i += 32) {
-        const double x = __ldcg(h + i);
-        acc += x * x;
-    }
-    acc = warp_sum(acc);
-    if (lane == 0) {
-        const double hn2 = n2 - acc;
-        const int reo = hn2 < REO_THETA * n2 ? 1 : 0;
-        a.reo[b] = reo;
-        if (reo) {
-            if (a.any_reo) atomicOr(a.any_reo, 1);
-        } else {
-            const double hn = sqrt(fmax(hn2, 0.0));
-            a.hn[b] = hn;
-            a.inv[b] = hn > 0.0 ? 1.0 / hn : 0.0;
-        }
-    }
-}
-
-// The block's end of a step of the three-kernel form: with the Hessenberg
-// column in s_col[0..j] and its subdiagonal hn, applies the staged
-// rotations, forms the new one, updates the residual estimate and the flag,
-// sets inv = 1 / hn, advances j and stores the column. Every thread of the
-// block calls it.
-__device__ __forceinline__ void finish_column(const Arnoldi& a, int b, int j, double hn, double* s_col,
-                                              double* s_cs, double* s_sn) {
-    const int m = a.m;
-    double* cs = a.cs + (long long)b * m;
-    double* sn = a.sn + (long long)b * m;
-    for (int i = threadIdx.x; i < j; i += blockDim.x) {
-        s_cs[i] = cs[i];
-        s_sn[i] = sn[i];
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double* g = a.g + (long long)b * (m + 1);
-        s_col[j + 1] = hn;
-        givens_apply(s_col, s_cs, s_sn, j, cs, sn, g);
-        const double e = fabs(g[j + 1]);
-        a.est[b] = e;
-        a.ncols[b] = j + 1;
-        a.inv[b] = hn > 0.0 ? 1.0 / hn : 0.0;
-        a.flag[b] = (e > a.target[b] && hn > 0.0 && j + 1 < m) ? 1 : 0;
-        a.live[b] = a.flag[b];
-        if (a.live_host) {
-            a.live_host[b] = a.flag[b];
-            __threadfence_system();
-        }
-        a.j[b] = j + 1;   // every block of this RHS has read j already
-    }
-    __syncthreads();
-    double* col = a.H + ((long long)b * m + j) * (m + 1);
-    for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) col[i] = s_col[i];
-}
-
 // pass 1: w = A V[j] by the closure gather of the potential v (the same
-// expression as closure_gather), h1 = V^T w over rows i <= j and ||w||^2.
-// The last block reduces h1 and ||w||^2 and decides on the second
-// projection; without it, it finishes the step's column (hcol = h1).
+// expression as closure_gather), then h1 = V^T w over rows i <= j
 template <typename VT>
 __global__ void __launch_bounds__(256) k_arn_gather_dots(Arnoldi a) {
-    extern __shared__ double s_dyn[];
-    const int m = a.m;
-    double* s_col = s_dyn;               // m + 2
-    double* s_cs = s_col + (m + 2);      // m
-    double* s_sn = s_cs + m;             // m
     __shared__ double s_w[ACH];
     __shared__ double s_red8[8 * 32];
     __shared__ int s_last;
     const int b = blockIdx.y;
     if (!a.flag[b]) return;
-    const int j = a.j[b];
-    const int cols = j + 1;
+    const int cols = a.j[b] + 1;
     const int c = blockIdx.x;
     const long long r0 = (long long)c * ACH;
     double* w = a.w + (long long)b * a.n;
@@ -426,38 +342,20 @@ __global__ void __launch_bounds__(256) k_arn_gather_dots(Arnoldi a) {
         s_w[threadIdx.x] = val;
     }
     __syncthreads();
-    double* part = a.part + (long long)b * (m + 2) * a.nchunk;
-    const double* Vb = a.V + (long long)b * (m + 1) * a.n;
+    double* part = a.part + (long long)b * (a.m + 2) * a.nchunk;
+    const double* Vb = a.V + (long long)b * (a.m + 1) * a.n;
     chunk_dots(global_rows(Vb, a.n, r0), cols, s_w, part, a.nchunk, c, s_red8);
-    if (threadIdx.x >= 224) {   // the last warp: ||w||^2 over the chunk
-        const int l = threadIdx.x - 224;
-        double acc = s_w[l] * s_w[l] + s_w[l + 32] * s_w[l + 32];
-        acc = warp_sum(acc);
-        if (l == 0) part[(long long)(m + 1) * a.nchunk + c] = acc;
-    }
     if (last_block(a.ctr + 3 * b + 0, gridDim.x, &s_last)) {
-        double* h1 = a.h1 + (long long)b * (m + 1);
-        reduce_rows(part, a.nchunk, cols, h1, nullptr, nullptr);
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            double acc = 0.0;
-            for (int q = threadIdx.x; q < a.nchunk; q += 32) acc += __ldcg(part + (long long)(m + 1) * a.nchunk + q);
-            acc = warp_sum(acc);
-            decide_reorth(a, b, j, acc);
-        }
-        __syncthreads();
-        if (__ldcg(a.reo + b) == 0) {
-            for (int i = threadIdx.x; i <= j; i += blockDim.x) s_col[i] = __ldcg(h1 + i);
-            finish_column(a, b, j, __ldcg(a.hn + b), s_col, s_cs, s_sn);
-        }
+        reduce_rows(part, a.nchunk, cols, a.h1 + (long long)b * (a.m + 1), nullptr, nullptr);
         if (threadIdx.x == 0) a.ctr[3 * b + 0] = 0;
     }
 }
 
-// pass 2, only where the decision above asks for it: w -= V h1, then
-// h2 = V^T w and ||w||^2. The last block forms hcol = h1 + h2 and the
-// subdiagonal ||w - V h2|| by the Pythagorean identity ||w||^2 - ||h2||^2,
-// and finishes the column.
+// pass 2: w -= V h1, then h2 = V^T w and ||w||^2. The last block forms
+// hcol = h1 + h2 and the new subdiagonal entry ||w - V h2|| by the
+// Pythagorean identity ||w||^2 - ||h2||^2 (V orthonormal), applies the
+// Givens rotations (staged in shared memory), updates the residual
+// estimate and the flag, sets inv = 1 / ||w - V h2|| and advances j.
 __global__ void __launch_bounds__(256) k_arn_update_dots(Arnoldi a) {
     extern __shared__ double s_dyn[];
     const int m = a.m;
@@ -470,7 +368,7 @@ __global__ void __launch_bounds__(256) k_arn_update_dots(Arnoldi a) {
     __shared__ double s_n2;
     __shared__ int s_last;
     const int b = blockIdx.y;
-    if (!a.flag[b] || !a.reo[b]) return;
+    if (!a.flag[b]) return;
     const int j = a.j[b];
     const int cols = j + 1;
     const int c = blockIdx.x;
@@ -499,7 +397,13 @@ __global__ void __launch_bounds__(256) k_arn_update_dots(Arnoldi a) {
             if (threadIdx.x == 0) s_n2 = acc;
         }
         __syncthreads();
+        double* cs = a.cs + (long long)b * m;
+        double* sn = a.sn + (long long)b * m;
         for (int i = threadIdx.x; i <= j; i += blockDim.x) s_col[i] = __ldcg(hc + i);
+        for (int i = threadIdx.x; i < j; i += blockDim.x) {
+            s_cs[i] = cs[i];
+            s_sn[i] = sn[i];
+        }
         if (threadIdx.x < 32) {   // ||h2||^2 in a fixed order
             double acc = 0.0;
             for (int i = threadIdx.x; i <= j; i += 32) {
@@ -510,8 +414,27 @@ __global__ void __launch_bounds__(256) k_arn_update_dots(Arnoldi a) {
             if (threadIdx.x == 0) s_n2 = fmax(s_n2 - acc, 0.0);
         }
         __syncthreads();
-        finish_column(a, b, j, sqrt(s_n2), s_col, s_cs, s_sn);
-        if (threadIdx.x == 0) a.ctr[3 * b + 1] = 0;
+        if (threadIdx.x == 0) {
+            const double hn = sqrt(s_n2);
+            double* g = a.g + (long long)b * (m + 1);
+            s_col[j + 1] = hn;
+            givens_apply(s_col, s_cs, s_sn, j, cs, sn, g);
+            const double e = fabs(g[j + 1]);
+            a.est[b] = e;
+            a.ncols[b] = j + 1;
+            a.inv[b] = hn > 0.0 ? 1.0 / hn : 0.0;
+            a.flag[b] = (e > a.target[b] && hn > 0.0 && j + 1 < m) ? 1 : 0;
+            a.live[b] = a.flag[b];
+            if (a.live_host) {
+                a.live_host[b] = a.flag[b];
+                __threadfence_system();
+            }
+            a.j[b] = j + 1;   // every block of this RHS has read j already
+            a.ctr[3 * b + 1] = 0;
+        }
+        __syncthreads();
+        double* col = a.H + ((long long)b * m + j) * (m + 1);
+        for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) col[i] = s_col[i];
     }
 }
 
@@ -586,7 +509,6 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* ctr, unsigned l
 // norm partials) goes to n2[b] when n2 is set.
 __device__ __forceinline__ void coop_reduce(const Arnoldi& a, int nctas, const int* s_j, const int* s_flag,
                                             double* out, double* out2, const double* add, double* n2) {
-    // s_flag selects the right-hand sides reduced here
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int nw = nctas * (blockDim.x >> 5);
@@ -612,42 +534,6 @@ __device__ __forceinline__ void coop_reduce(const Arnoldi& a, int nctas, const i
     }
 }
 
-// The first reduction of a step: h1[b][i] for rows i <= j_b and ||w||^2
-// (row m + 1, into n2[b]) of the iterating right-hand sides, one warp per
-// row in the order of reduce_rows. The warp that completes the last of the
-// j_b + 2 rows of a right-hand side (a per-RHS counter) takes the decision
-// on the second projection for it (decide_reorth), so no grid barrier sits
-// between the sums and the decision.
-__device__ __forceinline__ void coop_reduce_first(const Arnoldi& a, int nctas, const int* s_j, const int* s_flag) {
-    const int lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int nw = nctas * (blockDim.x >> 5);
-    const int rows = a.m + 2;
-    for (int item = gw; item < a.nb * rows; item += nw) {
-        const int b = item / rows, i = item % rows;
-        if (!s_flag[b]) continue;
-        const bool norm = i == a.m + 1;
-        if (!norm && i > s_j[b]) continue;
-        const double* p = a.part + ((long long)b * (a.m + 2) + i) * a.nchunk;
-        double acc = 0.0;
-        for (int c = lane; c < a.nchunk; c += 32) acc += __ldcg(p + c);
-        acc = warp_sum(acc);
-        unsigned int t = 0;
-        if (lane == 0) {
-            if (norm) a.n2[b] = acc;
-            else a.h1[(long long)b * (a.m + 1) + i] = acc;
-            __threadfence();
-            t = atomicAdd(a.ctr + 3 * b + 2, 1u);
-        }
-        t = __shfl_sync(0xffffffffu, t, 0);
-        if (t == (unsigned int)(s_j[b] + 1)) {
-            __threadfence();
-            decide_reorth(a, b, s_j[b], __ldcg(a.n2 + b));
-            if (lane == 0) a.ctr[3 * b + 2] = 0;
-        }
-    }
-}
-
 // SV: every CTA holds exactly one (RHS, chunk) item and keeps its chunk of
 // the basis rows V[0..j] in shared memory (copied asynchronously while the
 // gather runs), so the three projections read it from there; the sums are
@@ -664,7 +550,7 @@ __global__ void __launch_bounds__(256) k_arn_step_coop(Arnoldi a) {
     __shared__ double s_acc[8 * ACH];
     __shared__ double s_w[ACH];
     __shared__ double s_red[2];
-    __shared__ int s_j[COOP_MAX_NB], s_flag[COOP_MAX_NB], s_reo[COOP_MAX_NB];
+    __shared__ int s_j[COOP_MAX_NB], s_flag[COOP_MAX_NB];
     const unsigned long long G = gridDim.x;
     const int NI = (int)gridDim.x - a.nb;   // chunk CTAs; the last nb CTAs do the rotations
     const int items = a.nb * a.nchunk;
@@ -758,9 +644,29 @@ __global__ void __launch_bounds__(256) k_arn_step_coop(Arnoldi a) {
         if (SV) asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         __syncthreads();
         const RowView V = SV ? shared_rows(s_V) : global_rows(a.V + (long long)b * (m + 1) * a.n, a.n, r0);
+        chunk_dots(V, s_j[b] + 1, s_w, a.part + (long long)b * (m + 2) * a.nchunk, a.nchunk, c, s_acc);
+        __syncthreads();
+    }
+    if (!grid_barrier(a.bar, G + a.bar_extra, a.err, a.err_host, a.spin_limit)) return;   // all G CTAs
+    const unsigned long long GI = (unsigned long long)NI;
+    // phase 2: h1
+    coop_reduce(a, NI, s_j, s_flag, a.h1, nullptr, nullptr, nullptr);
+    if (!grid_barrier(a.bar2, GI + a.bar_extra, a.err, a.err_host, a.spin_limit)) return;   // chunk CTAs only
+    // phase 3: w -= V h1, partial dots for h2 and ||w||^2
+    for (int item = blockIdx.x; item < items; item += NI) {
+        const int b = item / a.nchunk, c = item % a.nchunk;
+        if (!s_flag[b]) continue;
+        const int cols = s_j[b] + 1;
+        const long long r0 = (long long)c * ACH;
+        const double* h1 = a.h1 + (long long)b * (m + 1);
+        for (int i = threadIdx.x; i < cols; i += blockDim.x) s_h[i] = __ldcg(h1 + i);
+        __syncthreads();
+        const double* Vb = a.V + (long long)b * (m + 1) * a.n;
         double* part = a.part + (long long)b * (m + 2) * a.nchunk;
-        chunk_dots(V, s_j[b] + 1, s_w, part, a.nchunk, c, s_acc);
-        if (threadIdx.x >= 224) {   // the last warp: ||w||^2 over the chunk
+        const RowView V = SV ? shared_rows(s_V) : global_rows(Vb, a.n, r0);
+        chunk_update(V, a.n, r0, cols, s_h, a.w + (long long)b * a.n, s_acc, s_w);
+        chunk_dots(V, cols, s_w, part, a.nchunk, c, s_acc);
+        if (threadIdx.x >= 224) {
             const int l = threadIdx.x - 224;
             double acc = s_w[l] * s_w[l] + s_w[l + 32] * s_w[l + 32];
             acc = warp_sum(acc);
@@ -768,81 +674,37 @@ __global__ void __launch_bounds__(256) k_arn_step_coop(Arnoldi a) {
         }
         __syncthreads();
     }
-    // the previous step read the flag before its launch ended; this step's
-    // decisions raise it after the next barrier
-    if (blockIdx.x == 0 && threadIdx.x == 0) *a.any_reo = 0;
-    if (!grid_barrier(a.bar, G + a.bar_extra, a.err, a.err_host, a.spin_limit)) return;   // all G CTAs
-    const unsigned long long GI = (unsigned long long)NI;
-    // phase 2: h1, ||w||^2 and, per right-hand side, the decision on the
-    // second projection (with hn and 1 / hn where none is needed)
-    coop_reduce_first(a, NI, s_j, s_flag);
-    if (!grid_barrier(a.bar2, GI + a.bar_extra, a.err, a.err_host, a.spin_limit)) return;   // chunk CTAs only
-    for (int b = threadIdx.x; b < a.nb; b += blockDim.x) s_reo[b] = s_flag[b] ? __ldcg(a.reo + b) : 0;
-    __syncthreads();
-    if (__ldcg(a.any_reo) != 0) {   // the same value in every CTA after the barrier
-        // phase 3 (right-hand sides whose norm cancelled): w -= V h1, partial
-        // dots for h2 and ||w||^2
-        for (int item = blockIdx.x; item < items; item += NI) {
-            const int b = item / a.nchunk, c = item % a.nchunk;
-            if (!s_reo[b]) continue;
-            const int cols = s_j[b] + 1;
-            const long long r0 = (long long)c * ACH;
-            const double* h1 = a.h1 + (long long)b * (m + 1);
-            for (int i = threadIdx.x; i < cols; i += blockDim.x) s_h[i] = __ldcg(h1 + i);
-            __syncthreads();
-            const double* Vb = a.V + (long long)b * (m + 1) * a.n;
-            double* part = a.part + (long long)b * (m + 2) * a.nchunk;
-            const RowView V = SV ? shared_rows(s_V) : global_rows(Vb, a.n, r0);
-            chunk_update(V, a.n, r0, cols, s_h, a.w + (long long)b * a.n, s_acc, s_w);
-            chunk_dots(V, cols, s_w, part, a.nchunk, c, s_acc);
-            if (threadIdx.x >= 224) {
-                const int l = threadIdx.x - 224;
-                double acc = s_w[l] * s_w[l] + s_w[l + 32] * s_w[l + 32];
-                acc = warp_sum(acc);
-                if (l == 0) part[(long long)(m + 1) * a.nchunk + c] = acc;
-            }
-            __syncthreads();
-        }
-        if (!grid_barrier(a.bar2, GI + a.bar_extra, a.err, a.err_host, a.spin_limit)) return;
-        // phase 4: h2 (into h1), hcol = h1 + h2, ||w||^2
-        coop_reduce(a, NI, s_j, s_reo, a.hcol, a.h1, a.h1, a.n2);
-        if (!grid_barrier(a.bar2, GI + a.bar_extra, a.err, a.err_host, a.spin_limit)) return;
-    }
+    if (!grid_barrier(a.bar2, GI + a.bar_extra, a.err, a.err_host, a.spin_limit)) return;
+    // phase 4: h2 (into h1), hcol = h1 + h2, ||w||^2
+    coop_reduce(a, NI, s_j, s_flag, a.hcol, a.h1, a.h1, a.n2);
+    if (!grid_barrier(a.bar2, GI + a.bar_extra, a.err, a.err_host, a.spin_limit)) return;
 
-    // phase 5: V[j+1] = (w - V h) / hn with h = h1 (one projection) or h2
-    // (w already holds w - V h1); with the second projection hn =
-    // sqrt(||w||^2 - ||h2||^2) is formed here (every CTA, same order). The
-    // CTA of chunk 0 stores the column (h1, or h1 + h2, then hn) for the
-    // rotations of the next step.
+    // phase 5: hn = sqrt(||w||^2 - ||h2||^2) (every CTA, same order), then
+    // V[j+1] = (w - V h2) / hn; the CTA of chunk 0 stores the column
+    // (hcol, then hn) for the rotations of the next step
     for (int item = blockIdx.x; item < items; item += NI) {
         const int b = item / a.nchunk, c = item % a.nchunk;
         if (!s_flag[b]) continue;
         const int j = s_j[b], cols = j + 1;
-        const bool reo = s_reo[b] != 0;
-        const double* h = a.h1 + (long long)b * (m + 1);
-        for (int i = threadIdx.x; i < cols; i += blockDim.x) s_h[i] = __ldcg(h + i);
+        const double* h2 = a.h1 + (long long)b * (m + 1);
+        for (int i = threadIdx.x; i < cols; i += blockDim.x) s_h[i] = __ldcg(h2 + i);
         if (threadIdx.x < 32) {
-            if (reo) {
-                double acc = 0.0;
-                for (int i = threadIdx.x; i <= j; i += 32) {
-                    const double x = __ldcg(h + i);
-                    acc += x * x;
-                }
-                acc = warp_sum(acc);
-                if (threadIdx.x == 0) {
-                    const double hn = sqrt(fmax(__ldcg(a.n2 + b) - acc, 0.0));
-                    s_red[0] = hn;
-                    s_red[1] = hn > 0.0 ? 1.0 / hn : 0.0;
-                }
-            } else if (threadIdx.x == 0) {
-                s_red[0] = __ldcg(a.hn + b);
-                s_red[1] = __ldcg(a.inv + b);
+            double acc = 0.0;
+            for (int i = threadIdx.x; i <= j; i += 32) {
+                const double x = __ldcg(h2 + i);
+                acc += x * x;
+            }
+            acc = warp_sum(acc);
+            if (threadIdx.x == 0) {
+                const double hn = sqrt(fmax(__ldcg(a.n2 + b) - acc, 0.0));
+                s_red[0] = hn;
+                s_red[1] = hn > 0.0 ? 1.0 / hn : 0.0;
             }
         }
         __syncthreads();
         if (c == 0) {
             double* pc = a.pcol + ((long long)b * 2 + (j & 1)) * (m + 2);
-            const double* hc = reo ? a.hcol + (long long)b * (m + 1) : h;
+            const double* hc = a.hcol + (long long)b * (m + 1);
             for (int i = threadIdx.x; i <= j; i += blockDim.x) pc[i] = __ldcg(hc + i);
             if (threadIdx.x == 0) pc[j + 1] = s_red[0];
         }
@@ -976,7 +838,6 @@ void arn_step(const Arnoldi& a, cudaStream_t st) {
     BAE_REQUIRE(a.v && a.gm && a.partner && a.t, BAE_ERR_INVALID_ARG, "arn_step: gather inputs not set");
     const size_t sh_h = (size_t)(a.m + 1) * sizeof(double);
     const size_t sh_g = (size_t)(4 * a.m + 3) * sizeof(double);
-    const size_t sh_c = (size_t)(3 * a.m + 2) * sizeof(double);
     if (a.coop_grid > 0) {
         BAE_REQUIRE(a.bar && a.bar2 && a.err && a.n2 && a.gflag && a.live && a.pcol && a.nb <= COOP_MAX_NB &&
                         a.coop_grid > a.nb,
@@ -1007,9 +868,9 @@ void arn_step(const Arnoldi& a, cudaStream_t st) {
     }
     const dim3 grid(a.nchunk, a.nb);
     if (a.v_f32)
-        BAE_LAUNCH("k_arn_gather_dots.f32", st, k_arn_gather_dots<float><<<grid, 256, sh_c, st>>>(a));
+        BAE_LAUNCH("k_arn_gather_dots.f32", st, k_arn_gather_dots<float><<<grid, 256, 0, st>>>(a));
     else
-        BAE_LAUNCH("k_arn_gather_dots.f64", st, k_arn_gather_dots<double><<<grid, 256, sh_c, st>>>(a));
+        BAE_LAUNCH("k_arn_gather_dots.f64", st, k_arn_gather_dots<double><<<grid, 256, 0, st>>>(a));
     BAE_LAUNCH("k_arn_update_dots", st, k_arn_update_dots<<<grid, 256, sh_g, st>>>(a));
     BAE_LAUNCH("k_arn_update_next", st, k_arn_update_next<<<grid, 256, sh_h, st>>>(a));
 }

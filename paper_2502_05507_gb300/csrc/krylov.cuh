@@ -89,15 +89,6 @@ struct Arnoldi {
     const float* pre_val = nullptr;
     double* zpre = nullptr;                // [nb][n]
     unsigned long long* bar2 = nullptr;
-    // bounded barrier waits: polls before a wait gives up; err_host, when
-    // set, is mapped host memory the failing CTA also flags (the host stops
-    // the cycle after the step). bar_extra > 0 only under host fault
-    // injection: the barriers then wait for that many CTAs more than the
-    // grid has, so every wait runs out (see bae_inject_fault).
-    // Gram-Schmidt: reo[b] = 1 where the step's first projection left a
-    // remainder too small for the Pythagorean norm and a second projection
-    // runs; *any_reo = 1 when some right-hand side of the fused step needs
-    // it; hn[b] = the subdiagonal of a one-projection column
     // float32 copies, rounded where the float64 values are written: v32
     // [nb][n] of the newest basis vector V[j] and, with the preconditioner,
     // z32 [nb][n] of z = M^{-1} V[j]; the float32 applies and the
@@ -105,9 +96,11 @@ struct Arnoldi {
     // float64 pipe, which also converts, is narrow)
     float* v32 = nullptr;
     float* z32 = nullptr;
-    int* reo = nullptr;
-    int* any_reo = nullptr;
-    double* hn = nullptr;
+    // bounded barrier waits: polls before a wait gives up; err_host, when
+    // set, is mapped host memory the failing CTA also flags (the host stops
+    // the cycle after the step). bar_extra > 0 only under host fault
+    // injection: the barriers then wait for that many CTAs more than the
+    // grid has, so every wait runs out (see bae_inject_fault).
     long long spin_limit = 1LL << 22;
     int* err_host = nullptr;
     int bar_extra = 0;

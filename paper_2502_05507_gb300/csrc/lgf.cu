@@ -349,6 +349,33 @@ void lgf_table(int N, double s, double* out, cudaStream_t st) {
     table_into(N, s, out, st);
 }
 
+// The spectrum of the finite-box Green's function of eq. [aux]: with the
+// source extended oddly about the layers 0 and N in every axis, the box
+// solve is the convolution with the (2N)-periodic Green's function, whose
+// spectrum is scale / (6 + s - 2 sum cos(pi k_d / N)). Its only pole (s = 0,
+// k = 0) multiplies a zero of the odd data and is set to 0.
+__global__ void k_box_spectrum(int N, double s, double scale, double* g64, float* g32) {
+    const long long N1 = N + 1, n3 = N1 * N1 * N1;
+    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n3; x += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(x / (N1 * N1)), j = (int)((x / N1) % N1), k = (int)(x % N1);
+        const double c = cospi((double)i / N) + cospi((double)j / N) + cospi((double)k / N);
+        const double d = 6.0 + s - 2.0 * c;
+        const double v = d != 0.0 ? scale / d : 0.0;
+        g64[x] = v;
+        if (g32) g32[x] = (float)v;
+    }
+}
+
+void box_spectrum(int N, double s, double scale, double* g64, float* g32, cudaStream_t st) {
+    BAE_REQUIRE(is_pow2(N) && N >= 8 && N <= 256, BAE_ERR_INVALID_ARG,
+                "box_spectrum: N must be a power of two in [8, 256]");
+    BAE_REQUIRE(std::isfinite(s) && s >= 0.0, BAE_ERR_INVALID_ARG, "box_spectrum: s must be finite and >= 0");
+    const long long N1 = N + 1, n3 = N1 * N1 * N1;
+    BAE_LAUNCH("k_box_spectrum", st,
+               k_box_spectrum<<<(int)std::min<long long>((n3 + 255) / 256, 152LL * 16), 256, 0, st>>>(N, s, scale,
+                                                                                                        g64, g32));
+}
+
 bool periodic_spectrum_applies(int N, double s) {
     if (!(s > 0.0)) return false;
     const double mu = std::acosh(1.0 + 0.5 * s);   // G_s ~ exp(-mu |n|) along an axis

@@ -19,6 +19,12 @@ bool periodic_spectrum_applies(int N, double s);
 
 void lgf_spectrum(int N, double s, double scale, double* g64, float* g32, cudaStream_t st);
 
+// Octant spectrum (same layout) of the finite-box Green's function of eq.
+// [aux] (zero on the layers 0 and N of every axis), for sources extended
+// oddly about those layers: scale / (6 + s - 2 sum cos(pi k_d / N)), 0 at
+// the pole (s = 0, k = 0).
+void box_spectrum(int N, double s, double scale, double* g64, float* g32, cudaStream_t st);
+
 // Twiddle tables exp(-2 pi i m / L), m < L, on the device.
 void make_twiddles(int L, double2* tw64, float2* tw32, cudaStream_t st);
 

@@ -212,3 +212,23 @@ def trace_problem(req, layer="double"):
         fn = lambda x, y, z: phi_torus(x, y, z, *params)
     return _make(f"{kind}_N{N}", cell_centred(N), fn, k2, layer,
                  lambda x, y, z: sol_exp_dir(x, y, z, a, k2))
+
+
+def trace_tensors(req, device="cuda"):
+    """phi and f (paper sign) of a serving-trace request as float64 torch
+    tensors computed on `device`, with the formulas of trace_problem (for
+    benchmarks that must not spend host time evaluating N^3 samples)."""
+    import torch
+    N, k2, kind, params, a = req["N"], req["kappa2"], req["kind"], req["params"], req["a"]
+    g = cell_centred(N)
+    ax = g.origin + torch.arange(N, dtype=torch.float64, device=device) * g.h
+    x, y, z = ax.view(N, 1, 1), ax.view(1, N, 1), ax.view(1, 1, N)
+    if kind == "sphere":
+        phi = x * x + y * y + z * z - params[0] ** 2
+    elif kind == "ellipsoid":
+        phi = x * x / params[0] ** 2 + y * y / params[1] ** 2 + z * z / params[2] ** 2 - 1.0
+    else:
+        phi = (torch.sqrt(x * x + y * y) - params[0]) ** 2 + z * z - params[1] ** 2
+    u = torch.exp(float(a[0]) * x + float(a[1]) * y + float(a[2]) * z)
+    f = (-float(np.dot(a, a)) + k2) * u
+    return phi.expand(N, N, N).contiguous(), f.expand(N, N, N).contiguous()
