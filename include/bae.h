@@ -141,20 +141,30 @@ void bae_default_options(bae_options* opts);
 long long bae_launch_count(void);
 
 /* Schedule of the FFT convolution inside every potential apply of this
- * process (all contexts): BAE_SCHED_AUTO (-1, the default) times the two
- * schedules on the first apply of each (precision, N, batch size) outside
- * graph capture and keeps the faster; BAE_SCHED_PASSES (0) runs the k, j and
- * i transforms as five separate kernels; BAE_SCHED_PLANE (1) fuses the k and
- * j transforms per x-plane (one CTA per plane where the plane of k-spectra
- * fits in shared memory, a thread-block cluster sharing it through
- * distributed shared memory where it does not). Both compute the same
- * convolution (Section 3.2, the discrete potentials as lattice sums); they
- * differ in rounding order only. Overrides the BAE_CONV_PLANE environment
- * variable. Returns BAE_ERR_INVALID_ARG for any other value. Not part of the
- * method: a performance control. */
+ * process (all contexts): BAE_SCHED_AUTO (-1, the default) times every
+ * schedule the (precision, N) can run on the first apply of each
+ * (precision, N, batch size) outside graph capture and keeps the fastest;
+ * BAE_SCHED_PASSES (0) runs the k, j and i transforms as five separate
+ * kernels; BAE_SCHED_PLANE (1) fuses the k and j transforms per x-plane (one
+ * CTA per plane where the plane of k-spectra fits in shared memory, a
+ * thread-block cluster sharing it through distributed shared memory where it
+ * does not); BAE_SCHED_PASSES_ALT (2) runs the five passes with a second
+ * launch geometry (float32: column blocks of half the width at N = 128, the
+ * three-level 8 x 8 x 8 transform at N = 256; elsewhere the same as
+ * BAE_SCHED_PASSES); BAE_SCHED_PERSIST (3) runs the five passes as
+ * persistent kernels, each launched with at most the CTAs that are resident
+ * at once, striding over the tiles of every right-hand side of the batch.
+ * All compute the same convolution (Section 3.2, the
+ * discrete potentials as lattice sums); they differ in rounding order only.
+ * A schedule the size cannot run falls back to BAE_SCHED_PASSES. Overrides
+ * the BAE_CONV_PLANE environment variable (0, 1, 2 or 3: the same values).
+ * Returns BAE_ERR_INVALID_ARG for any other value. Not part of the method:
+ * a performance control. */
 #define BAE_SCHED_AUTO (-1)
 #define BAE_SCHED_PASSES 0
 #define BAE_SCHED_PLANE 1
+#define BAE_SCHED_PASSES_ALT 2
+#define BAE_SCHED_PERSIST 3
 int bae_set_conv_schedule(int schedule);
 
 /* Host-side fault injection for the library's own failure tests (the paper
@@ -371,7 +381,11 @@ int bae_solve_batched(bae_problem* prob, int nrhs, const double* f, const double
  * `slots` concurrent slots (each a context with its own CUDA stream and work
  * space) when a slot is free and the request's device-memory estimate fits
  * in hbm_budget_bytes next to the requests in flight; work of different
- * slots overlaps on the device. Requests of any N, kappa2, geometry and
+ * slots overlaps on the device. With two or more slots, the first half run
+ * on streams of the device's highest priority and take small requests
+ * (N <= 64) first, the others on the lowest priority and take large ones
+ * first; a slot with none of its class queued takes the first request that
+ * fits. Requests of any N, kappa2, geometry and
  * layer mix freely; LGF spectra are cached on the device per
  * (N, kappa2 h^2) and shared by all slots; Krylov state stays on the
  * device. A request's result does not depend on what else is in flight. */

@@ -200,13 +200,15 @@ def inject_fault(kind: int, arg: int = 0):
     _check(lib().bae_inject_fault(int(kind), int(arg)))
 
 
-SCHEDULES = {"auto": -1, "passes": 0, "plane": 1}
+SCHEDULES = {"auto": -1, "passes": 0, "plane": 1, "passes_alt": 2, "persist": 3}
 
 
 def set_conv_schedule(schedule: str = "auto"):
     """Forces the FFT convolution schedule of every potential apply in this
-    process: "passes" (five kernels), "plane" (k and j fused per x-plane) or
-    "auto" (timed once per precision, N and batch size)."""
+    process: "passes" (five kernels), "passes_alt" (the same with the second
+    launch geometry), "persist" (the five as persistent kernels), "plane" (k
+    and j fused per x-plane) or "auto" (every runnable schedule timed once
+    per precision, N and batch size)."""
     if schedule not in SCHEDULES:
         raise ValueError(f"schedule must be one of {sorted(SCHEDULES)}")
     _check(lib().bae_set_conv_schedule(SCHEDULES[schedule]))

@@ -1192,8 +1192,9 @@ long long bae_launch_count(void) { return bae::g_launches.load(); }
 
 int bae_set_conv_schedule(int schedule) {
     return guarded([&]() -> int {
-        BAE_REQUIRE(schedule >= BAE_SCHED_AUTO && schedule <= BAE_SCHED_PLANE, BAE_ERR_INVALID_ARG,
-                    "schedule must be BAE_SCHED_AUTO, BAE_SCHED_PASSES or BAE_SCHED_PLANE");
+        BAE_REQUIRE(schedule >= BAE_SCHED_AUTO && schedule <= BAE_SCHED_PERSIST, BAE_ERR_INVALID_ARG,
+                    "schedule must be BAE_SCHED_AUTO, BAE_SCHED_PASSES, BAE_SCHED_PLANE, BAE_SCHED_PASSES_ALT or "
+                    "BAE_SCHED_PERSIST");
         bae::set_forced_sched(schedule);
         return BAE_OK;
     });

@@ -57,9 +57,11 @@ int forced_sched() {
     const int api = g_forced.load();
     if (api != -2) return api;
     static const int env = []() {
+        // BAE_CONV_PLANE = 0 (passes), 1 (plane), 2 (passes, variant
+        // geometry), 3 (persistent passes)
         const char* e = getenv("BAE_CONV_PLANE");
-        if (!e) return -1;
-        return e[0] == '0' ? (int)SCHED_PASSES : (int)SCHED_PLANE;
+        if (!e || e[0] < '0' || e[0] > '3') return -1;
+        return (int)(e[0] - '0');
     }();
     return env;
 }

@@ -13,20 +13,29 @@ namespace bae {
 // three-level 8 x 8 x 8 plan for 16-byte elements at L = 512 (float64 and
 // double-float, whose two-level 16 x 32 split needs ~200-255 registers per
 // thread), the two-level plan elsewhere.
-template <typename T, int L> struct PlanOf { using type = Plan2<L>; };
-template <> struct PlanOf<double, 512> { using type = Plan3_512; };
-template <> struct PlanOf<dsf, 512> { using type = Plan3_512; };
+// V selects a geometry variant of the pass kernels for the autotuner:
+// variant 1 exists for float32 at L = 256 (column blocks of half the width,
+// 16 columns) and L = 512 (the three-level plan); elsewhere it equals 0.
+template <typename T, int L, int V = 0> struct PlanOf { using type = Plan2<L>; };
+template <int V> struct PlanOf<double, 512, V> { using type = Plan3_512; };
+template <int V> struct PlanOf<dsf, 512, V> { using type = Plan3_512; };
+template <> struct PlanOf<float, 512, 1> { using type = Plan3_512; };
 
-// Launch geometry per transform length and precision.
-template <typename T, int L> struct Geo {
+template <typename T, int L> struct HasAlt {
+    static constexpr bool value = std::is_same<T, float>::value && (L == 256 || L == 512);
+};
+
+// Launch geometry per transform length, precision and variant.
+template <typename T, int L, int V = 0> struct Geo {
     using C = cplx_t<T>;
-    using PL = typename PlanOf<T, L>::type;
+    using PL = typename PlanOf<T, L, V>::type;
     static constexpr bool THREE = PL::TH * PL::S == L && PL::TH > PL::S;
     static constexpr int TH = PL::TH, S = PL::S;   // threads per line, values per thread
     // column passes: W columns per CTA, TH threads per column (three-level:
-    // 4 columns of 16-byte elements, 64 bytes per row segment, 256 threads)
+    // 128-byte row segments, 8 columns of float32 or 4 of 16-byte elements)
     static constexpr int WB = 65536 / (L * (int)sizeof(C));
-    static constexpr int W = THREE ? 4 : (WB > 32 ? 32 : (WB < 8 ? 8 : WB));
+    static constexpr int W0 = THREE ? 128 / (int)sizeof(C) / 2 : (WB > 32 ? 32 : (WB < 8 ? 8 : WB));
+    static constexpr int W = (V == 1 && !THREE && HasAlt<T, L>::value) ? W0 / 2 : W0;
     static constexpr int CT = W * TH;
     static constexpr int XL = PL::XLEN;            // exchange positions per column
     // line passes (k): P line pairs per CTA, TH threads per pair
@@ -34,6 +43,10 @@ template <typename T, int L> struct Geo {
     static constexpr int P = THREE ? 4 : ((256 / TH) < PB ? (256 / TH) : (PB < 4 ? 4 : PB));
     static constexpr int KT = P * TH;
     static constexpr int XS = PL::XS;              // exchange stride per pair (odd)
+    // resident CTAs per SM the compiler must allow (register cap): three per
+    // SM for the three-level plan (at most 85 registers per thread, as its
+    // kernels need), no constraint otherwise
+    static constexpr int MINB = THREE ? 3 : 1;
 };
 
 template <typename T>

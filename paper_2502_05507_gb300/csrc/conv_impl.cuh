@@ -31,6 +31,8 @@
 // holds a nonzero input / a kept output exactly when m < R2 / 2; the kernels
 // test m, a compile-time index, so the compiler drops the arithmetic on the
 // zero padding and on the discarded half.
+#include <map>
+#include <mutex>
 #include <string>
 #include <type_traits>
 
@@ -50,22 +52,21 @@ namespace {
 // BOX: the finite auxiliary box of eq. [aux] (volume sources only): the
 // upper half of each line holds the negated mirror of the lower half, x[2N -
 // n] = -x[n], x[N] = 0 (odd about the layers 0 and N), instead of zeros.
-template <typename T, int L, bool BOX = false>
-__global__ void __launch_bounds__(Geo<T, L>::KT) k_kpass_fwd(ConvArgs<T> a) {
-    wait_prior_grid();   // results of the previous kernel on the stream
+template <typename T, int L, bool BOX, int V>
+__device__ __forceinline__ void kpass_fwd_tile(const ConvArgs<T>& a, int bx, int bz) {
     using C = cplx_t<T>;
-    using G = Geo<T, L>;
+    using G = Geo<T, L, V>;
     using PL = typename G::PL;
     constexpr int N = L / 2, N1 = N + 1, TH = G::TH, S = G::S;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* xch = reinterpret_cast<C*>(smem_raw);                 // P * XS
     T* rho = reinterpret_cast<T*>(xch + G::P * G::XS);      // P * 2N
 
-    const int b = blockIdx.z;
+    const int b = bz;
     if (a.active && !a.active[b]) return;   // whole CTA: no barrier is skipped
     const int t = threadIdx.x % TH;
     const int p = threadIdx.x / TH;
-    const long long pair = (long long)a.plane_lo() * (N / 2) + (long long)blockIdx.x * G::P + p;
+    const long long pair = (long long)a.plane_lo() * (N / 2) + (long long)bx * G::P + p;
     const bool active = pair < (long long)a.plane_hi() * (N / 2);
     const long long la = 2 * pair, lb = la + 1;
     T* r = rho + p * 2 * N;
@@ -133,27 +134,48 @@ __global__ void __launch_bounds__(Geo<T, L>::KT) k_kpass_fwd(ConvArgs<T> a) {
     }
 }
 
+// PERSIST: a grid of at most the resident CTAs strides over the tiles (pair
+// block, right-hand side); otherwise one tile per CTA of the grid (pair
+// blocks, 1, right-hand sides). Separate instantiations: inside a tile loop
+// the compiler keeps loop invariants (twiddles, offsets) in registers,
+// which halves the occupancy of the one-tile form.
+template <typename T, int L, bool BOX = false, int V = 0, bool PERSIST = false>
+__global__ void __launch_bounds__(Geo<T, L, V>::KT, Geo<T, L, V>::MINB) k_kpass_fwd(ConvArgs<T> a) {
+    wait_prior_grid();   // results of the previous kernel on the stream
+    if constexpr (PERSIST) {
+        constexpr int N = L / 2;
+        const long long gkx =
+            ((long long)(a.plane_hi() - a.plane_lo()) * (N / 2) + Geo<T, L, V>::P - 1) / Geo<T, L, V>::P;
+        const long long ntiles = gkx * a.nbatch;
+        for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            kpass_fwd_tile<T, L, BOX, V>(a, (int)(tile % gkx), (int)(tile / gkx));
+            __syncthreads();   // the next tile reuses the shared memory
+        }
+    } else {
+        kpass_fwd_tile<T, L, BOX, V>(a, (int)blockIdx.x, (int)blockIdx.z);
+    }
+}
+
 // ----------------------------------------------------- column passes (j, i)
 enum ColMode { COL_FWD_J = 0, COL_CONV_I = 1, COL_INV_J = 2 };
 
-template <typename T, int L, int MODE, bool BOX = false>
-__global__ void __launch_bounds__(Geo<T, L>::CT) k_colpass(ConvArgs<T> a) {
-    wait_prior_grid();   // results of the previous kernel on the stream
+template <typename T, int L, int MODE, bool BOX, int V>
+__device__ __forceinline__ void colpass_tile(const ConvArgs<T>& a, int bx, int by, int bz) {
     using C = cplx_t<T>;
-    using G = Geo<T, L>;
+    using G = Geo<T, L, V>;
     using PL = typename G::PL;
     constexpr int N = L / 2, N1 = N + 1, TH = G::TH, S = G::S, W = G::W;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* xch = reinterpret_cast<C*>(smem_raw);   // XL * W
 
-    const int b = blockIdx.z;
+    const int b = bz;
     if (a.active && !a.active[b]) return;
-    const int o = MODE == COL_CONV_I ? (int)blockIdx.y : a.plane_lo() + (int)blockIdx.y;   // jj, or i
+    const int o = MODE == COL_CONV_I ? by : a.plane_lo() + by;   // jj, or i
     const int c = threadIdx.x % W;
     const int t = threadIdx.x / W;
-    const int col = blockIdx.x * W + c;     // kk (column 0 holds kk = 0 and N)
+    const int col = bx * W + c;             // kk (column 0 holds kk = 0 and N)
     const bool ok = col < N;
-    const bool col0 = blockIdx.x == 0;      // this CTA holds column 0 (c == 0)
+    const bool col0 = bx == 0;              // this CTA holds column 0 (c == 0)
 
     C* Ab = a.A + (long long)b * N * N * N1;
     C* Bb = a.B + (long long)b * N * (2 * N) * N1;
@@ -261,22 +283,43 @@ __global__ void __launch_bounds__(Geo<T, L>::CT) k_colpass(ConvArgs<T> a) {
     }
 }
 
-// ----------------------------------------------------------- k pass (C2R)
-template <typename T, int L>
-__global__ void __launch_bounds__(Geo<T, L>::KT) k_kpass_inv(ConvArgs<T> a) {
+// tiles (column block, line, right-hand side), column blocks fastest:
+// strided over a grid of resident CTAs (PERSIST) or one per CTA of the grid
+// (column blocks, lines, right-hand sides)
+template <typename T, int L, int MODE, bool BOX = false, int V = 0, bool PERSIST = false>
+__global__ void __launch_bounds__(Geo<T, L, V>::CT, Geo<T, L, V>::MINB) k_colpass(ConvArgs<T> a) {
     wait_prior_grid();   // results of the previous kernel on the stream
+    if constexpr (PERSIST) {
+        constexpr int N = L / 2;
+        constexpr int ncb = (N + Geo<T, L, V>::W - 1) / Geo<T, L, V>::W;
+        const int ny = MODE == COL_CONV_I ? 2 * N : a.plane_hi() - a.plane_lo();
+        const long long per_b = (long long)ncb * ny;
+        const long long ntiles = per_b * a.nbatch;
+        for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            const long long rem = tile % per_b;
+            colpass_tile<T, L, MODE, BOX, V>(a, (int)(rem % ncb), (int)(rem / ncb), (int)(tile / per_b));
+            __syncthreads();   // the next tile reuses the shared memory
+        }
+    } else {
+        colpass_tile<T, L, MODE, BOX, V>(a, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z);
+    }
+}
+
+// ----------------------------------------------------------- k pass (C2R)
+template <typename T, int L, int V>
+__device__ __forceinline__ void kpass_inv_tile(const ConvArgs<T>& a, int bx, int bz) {
     using C = cplx_t<T>;
-    using G = Geo<T, L>;
+    using G = Geo<T, L, V>;
     using PL = typename G::PL;
     constexpr int N = L / 2, N1 = N + 1, TH = G::TH, S = G::S;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* xch = reinterpret_cast<C*>(smem_raw);
 
-    const int b = blockIdx.z;
+    const int b = bz;
     if (a.active && !a.active[b]) return;
     const int t = threadIdx.x % TH;
     const int p = threadIdx.x / TH;
-    const long long pair = (long long)a.plane_lo() * (N / 2) + (long long)blockIdx.x * G::P + p;
+    const long long pair = (long long)a.plane_lo() * (N / 2) + (long long)bx * G::P + p;
     const bool active = pair < (long long)a.plane_hi() * (N / 2);
     const long long la = 2 * pair, lb = la + 1;
     const C* A = a.A + (long long)b * N * N * N1;
@@ -304,6 +347,23 @@ __global__ void __launch_bounds__(Geo<T, L>::KT) k_kpass_inv(ConvArgs<T> a) {
                 out[lb * N + n] = to_out(v[m].y);
             }
         }
+    }
+}
+
+template <typename T, int L, int V = 0, bool PERSIST = false>
+__global__ void __launch_bounds__(Geo<T, L, V>::KT, Geo<T, L, V>::MINB) k_kpass_inv(ConvArgs<T> a) {
+    wait_prior_grid();   // results of the previous kernel on the stream
+    if constexpr (PERSIST) {
+        constexpr int N = L / 2;
+        const long long gkx =
+            ((long long)(a.plane_hi() - a.plane_lo()) * (N / 2) + Geo<T, L, V>::P - 1) / Geo<T, L, V>::P;
+        const long long ntiles = gkx * a.nbatch;
+        for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            kpass_inv_tile<T, L, V>(a, (int)(tile % gkx), (int)(tile / gkx));
+            __syncthreads();   // the next tile reuses the shared memory
+        }
+    } else {
+        kpass_inv_tile<T, L, V>(a, (int)blockIdx.x, (int)blockIdx.z);
     }
 }
 
@@ -517,6 +577,27 @@ void configure_conv() {
         BAE_CUDA(cudaFuncSetAttribute(k_colpass<T, L, COL_FWD_J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
         BAE_CUDA(cudaFuncSetAttribute(k_colpass<T, L, COL_CONV_I>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
         BAE_CUDA(cudaFuncSetAttribute(k_colpass<T, L, COL_INV_J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
+        // the persistent instantiations of the variant-0 passes
+        BAE_CUDA(cudaFuncSetAttribute(k_kpass_fwd<T, L, false, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem_k));
+        BAE_CUDA(cudaFuncSetAttribute(k_kpass_inv<T, L, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem_k));
+        BAE_CUDA(cudaFuncSetAttribute(k_colpass<T, L, COL_FWD_J, false, 0, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
+        BAE_CUDA(cudaFuncSetAttribute(k_colpass<T, L, COL_CONV_I, false, 0, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
+        BAE_CUDA(cudaFuncSetAttribute(k_colpass<T, L, COL_INV_J, false, 0, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
+        if constexpr (HasAlt<T, L>::value) {
+            using GA = Geo<T, L, 1>;
+            const size_t ak = (size_t)GA::P * GA::XS * sizeof(C) + (size_t)GA::P * 2 * N * sizeof(T);
+            const size_t ac = (size_t)GA::XL * GA::W * sizeof(C);
+            BAE_CUDA(cudaFuncSetAttribute(k_kpass_fwd<T, L, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ak));
+            BAE_CUDA(cudaFuncSetAttribute(k_kpass_inv<T, L, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ak));
+            BAE_CUDA(cudaFuncSetAttribute(k_colpass<T, L, COL_FWD_J, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ac));
+            BAE_CUDA(cudaFuncSetAttribute(k_colpass<T, L, COL_CONV_I, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ac));
+            BAE_CUDA(cudaFuncSetAttribute(k_colpass<T, L, COL_INV_J, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ac));
+        }
         if constexpr (sizeof(C) == 16) {
             BAE_CUDA(cudaFuncSetAttribute(k_kpass_fwd<T, L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_k));
             BAE_CUDA(cudaFuncSetAttribute(k_colpass<T, L, COL_FWD_J, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -536,58 +617,128 @@ void configure_conv() {
     (void)configured;
 }
 
+// CTAs of `kernel` resident on one SM at `threads` threads and `smem`
+// bytes (cached per kernel; every launch site uses one configuration)
+template <typename K>
+int resident_per_sm(K kernel, int threads, size_t smem) {
+    static std::mutex mu;
+    static std::map<const void*, int> cache;
+    const void* key = reinterpret_cast<const void*>(kernel);
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int n = 0;
+    BAE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem));
+    cache[key] = n > 0 ? n : 1;
+    return cache[key];
+}
+
+inline int sm_count() {
+    static const int n = []() {
+        int dev = 0, c = 0;
+        BAE_CUDA(cudaGetDevice(&dev));
+        BAE_CUDA(cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev));
+        return c;
+    }();
+    return n;
+}
+
+// Grid of a persistent pass kernel: at most the CTAs resident at once
+template <typename K>
+dim3 persist_grid(long long ntiles, K kernel, int threads, size_t smem) {
+    const long long cap = (long long)resident_per_sm(kernel, threads, smem) * sm_count();
+    return dim3((unsigned)(ntiles < 1 ? 1 : (ntiles < cap ? ntiles : cap)));
+}
+
+// The five pass kernels with the launch geometry of variant V: one tile per
+// CTA, or (PERSIST) the persistent instantiations on grids of resident CTAs.
+template <typename T, int L, int V, bool BOX = false, bool PERSIST = false>
+void launch_passes(const ConvArgs<T>& a, cudaStream_t st) {
+    using C = cplx_t<T>;
+    using G = Geo<T, L, V>;
+    constexpr int N = L / 2;
+    const size_t smem_k = (size_t)G::P * G::XS * sizeof(C) + (size_t)G::P * 2 * N * sizeof(T);
+    const size_t smem_c = (size_t)G::XL * G::W * sizeof(C);
+    const int nb = a.nbatch;
+    const int np = a.plane_hi() - a.plane_lo();   // x-planes holding sources or read outputs
+    const int gkx = ceil_div((long long)np * N / 2, G::P);
+    const int ncb = ceil_div(N, G::W);           // column 0 also holds kk = N
+    auto kf = k_kpass_fwd<T, L, BOX, V, PERSIST>;
+    auto jf = k_colpass<T, L, COL_FWD_J, BOX, V, PERSIST>;
+    auto ci = k_colpass<T, L, COL_CONV_I, BOX, V, PERSIST>;
+    auto ji = k_colpass<T, L, COL_INV_J, false, V, PERSIST>;
+    auto ki = k_kpass_inv<T, L, V, PERSIST>;
+    dim3 gk(gkx, 1, nb), gj(ncb, np, nb), gi(ncb, 2 * N, nb);
+    if (PERSIST) {
+        gk = persist_grid((long long)gkx * nb, kf, G::KT, smem_k);
+        gj = persist_grid((long long)ncb * np * nb, jf, G::CT, smem_c);
+        gi = persist_grid((long long)ncb * 2 * N * nb, ci, G::CT, smem_c);
+    }
+    const dim3 gji = PERSIST ? persist_grid((long long)ncb * np * nb, ji, G::CT, smem_c) : gj;
+    const dim3 gki = PERSIST ? persist_grid((long long)gkx * nb, ki, G::KT, smem_k) : gk;
+    BAE_LAUNCH(BOX ? kname<T>("conv_box_kfwd.f32", "conv_box_kfwd.f64", "conv_box_kfwd.df64")
+                   : kname<T>("conv_kfwd.f32", "conv_kfwd.f64", "conv_kfwd.df64"), st,
+               launch_pdl(kf, gk, G::KT, smem_k, st, a));
+    BAE_LAUNCH(BOX ? kname<T>("conv_box_jfwd.f32", "conv_box_jfwd.f64", "conv_box_jfwd.df64")
+                   : kname<T>("conv_jfwd.f32", "conv_jfwd.f64", "conv_jfwd.df64"), st,
+               launch_pdl(jf, gj, G::CT, smem_c, st, a));
+    BAE_LAUNCH(BOX ? kname<T>("conv_box_i.f32", "conv_box_i.f64", "conv_box_i.df64")
+                   : kname<T>("conv_i.f32", "conv_i.f64", "conv_i.df64"), st,
+               launch_pdl(ci, gi, G::CT, smem_c, st, a));
+    BAE_LAUNCH(kname<T>("conv_jinv.f32", "conv_jinv.f64", "conv_jinv.df64"), st,
+               launch_pdl(ji, gji, G::CT, smem_c, st, a));
+    BAE_LAUNCH(kname<T>("conv_kinv.f32", "conv_kinv.f64", "conv_kinv.df64"), st,
+               launch_pdl(ki, gki, G::KT, smem_k, st, a));
+}
+
 template <typename T, int L>
 void launch_sched(const ConvArgs<T>& a, cudaStream_t st, int sched) {
     using C = cplx_t<T>;
     using G = Geo<T, L>;
     using PG = PlaneGeo<T, L>;
     constexpr int N = L / 2;
-    const size_t smem_k = (size_t)G::P * G::XS * sizeof(C) + (size_t)G::P * 2 * N * sizeof(T);
     const size_t smem_c = (size_t)G::XL * G::W * sizeof(C);
     const int nb = a.nbatch;
-    const int np = a.plane_hi() - a.plane_lo();   // x-planes holding sources or read outputs
-    const dim3 gk(ceil_div((long long)np * N / 2, G::P), 1, nb);
-    const int ncolblk = ceil_div(N, G::W);   // column 0 also holds kk = N
+    const int np = a.plane_hi() - a.plane_lo();
     if (a.box) {
         // finite box: the forward passes with mirrored upper halves, the
         // ordinary inverse passes
         if constexpr (sizeof(C) == 16) {
-            BAE_LAUNCH(kname<T>("conv_box_kfwd.f32", "conv_box_kfwd.f64", "conv_box_kfwd.df64"), st,
-                       launch_pdl(k_kpass_fwd<T, L, true>, gk, G::KT, smem_k, st, a));
-            BAE_LAUNCH(kname<T>("conv_box_jfwd.f32", "conv_box_jfwd.f64", "conv_box_jfwd.df64"), st,
-                       launch_pdl(k_colpass<T, L, COL_FWD_J, true>, dim3(ncolblk, np, nb), G::CT, smem_c, st, a));
-            BAE_LAUNCH(kname<T>("conv_box_i.f32", "conv_box_i.f64", "conv_box_i.df64"), st,
-                       launch_pdl(k_colpass<T, L, COL_CONV_I, true>, dim3(ncolblk, 2 * N, nb), G::CT, smem_c, st, a));
-            BAE_LAUNCH(kname<T>("conv_jinv.f32", "conv_jinv.f64", "conv_jinv.df64"), st,
-                       launch_pdl(k_colpass<T, L, COL_INV_J>, dim3(ncolblk, np, nb), G::CT, smem_c, st, a));
-            BAE_LAUNCH(kname<T>("conv_kinv.f32", "conv_kinv.f64", "conv_kinv.df64"), st,
-                       launch_pdl(k_kpass_inv<T, L>, gk, G::KT, smem_k, st, a));
+            launch_passes<T, L, 0, true>(a, st);
             return;
         } else {
             throw Error(BAE_ERR_INVALID_ARG, "finite-box apply needs float64 or double-float");
         }
     }
-    if (sched == SCHED_PLANE) {
-        if constexpr (PG::FITS)
-            BAE_LAUNCH(kname<T>("conv_plane_fwd.f32", "conv_plane_fwd.f64", "conv_plane_fwd.df64"), st,
-                       launch_pdl(k_plane_fwd<T, L>, dim3(np, nb), PG::PT, PG::SMEM, st, a));
-        else if constexpr (CPlaneGeo<T, L>::USE)
-            cplane_launch<T, L>(a, st, false);
-    } else {
-        BAE_LAUNCH(kname<T>("conv_kfwd.f32", "conv_kfwd.f64", "conv_kfwd.df64"), st, launch_pdl(k_kpass_fwd<T, L>, gk, G::KT, smem_k, st, a));
-        BAE_LAUNCH(kname<T>("conv_jfwd.f32", "conv_jfwd.f64", "conv_jfwd.df64"), st, launch_pdl(k_colpass<T, L, COL_FWD_J>, dim3(ncolblk, np, nb), G::CT, smem_c, st, a));
+    if (sched == SCHED_PASSES_ALT) {
+        // the five passes with the variant-1 geometry (HasAlt), else variant 0
+        if constexpr (HasAlt<T, L>::value) {
+            launch_passes<T, L, 1>(a, st);
+            return;
+        }
+        sched = SCHED_PASSES;
     }
-    BAE_LAUNCH(kname<T>("conv_i.f32", "conv_i.f64", "conv_i.df64"), st, launch_pdl(k_colpass<T, L, COL_CONV_I>, dim3(ncolblk, 2 * N, nb), G::CT, smem_c, st, a));
-    if (sched == SCHED_PLANE) {
-        if constexpr (PG::FITS)
-            BAE_LAUNCH(kname<T>("conv_plane_inv.f32", "conv_plane_inv.f64", "conv_plane_inv.df64"), st,
-                       launch_pdl(k_plane_inv<T, L>, dim3(np, nb), PG::PT, PG::SMEM, st, a));
-        else if constexpr (CPlaneGeo<T, L>::USE)
-            cplane_launch<T, L>(a, st, true);
-    } else {
-        BAE_LAUNCH(kname<T>("conv_jinv.f32", "conv_jinv.f64", "conv_jinv.df64"), st, launch_pdl(k_colpass<T, L, COL_INV_J>, dim3(ncolblk, np, nb), G::CT, smem_c, st, a));
-        BAE_LAUNCH(kname<T>("conv_kinv.f32", "conv_kinv.f64", "conv_kinv.df64"), st, launch_pdl(k_kpass_inv<T, L>, gk, G::KT, smem_k, st, a));
+    if (sched == SCHED_PERSIST) {
+        launch_passes<T, L, 0, false, true>(a, st);
+        return;
     }
+    if (sched == SCHED_PASSES) {
+        launch_passes<T, L, 0>(a, st);
+        return;
+    }
+    // plane-fused k and j passes around the i pass
+    if constexpr (PG::FITS)
+        BAE_LAUNCH(kname<T>("conv_plane_fwd.f32", "conv_plane_fwd.f64", "conv_plane_fwd.df64"), st,
+                   launch_pdl(k_plane_fwd<T, L>, dim3(np, nb), PG::PT, PG::SMEM, st, a));
+    else if constexpr (CPlaneGeo<T, L>::USE)
+        cplane_launch<T, L>(a, st, false);
+    BAE_LAUNCH(kname<T>("conv_i.f32", "conv_i.f64", "conv_i.df64"), st,
+               launch_pdl(k_colpass<T, L, COL_CONV_I>, dim3(ceil_div(N, G::W), 2 * N, nb), G::CT, smem_c, st, a));
+    if constexpr (PG::FITS)
+        BAE_LAUNCH(kname<T>("conv_plane_inv.f32", "conv_plane_inv.f64", "conv_plane_inv.df64"), st,
+                   launch_pdl(k_plane_inv<T, L>, dim3(np, nb), PG::PT, PG::SMEM, st, a));
+    else if constexpr (CPlaneGeo<T, L>::USE)
+        cplane_launch<T, L>(a, st, true);
 }
 
 }  // namespace
@@ -600,52 +751,56 @@ void run_conv(const ConvArgs<T>& a, cudaStream_t st) {
         return;
     }
     using PG = PlaneGeo<T, L>;
-    if constexpr (!PG::FITS && !CPlaneGeo<T, L>::USE) {
-        launch_sched<T, L>(a, st, SCHED_PASSES);
+    // the schedules this (element type, L) can run: the five passes, their
+    // variant geometry, the plane-fused passes (one CTA, or a cluster)
+    bool plane = PG::FITS;
+    if constexpr (!PG::FITS && CPlaneGeo<T, L>::USE) plane = cplane_ready<T, L>();
+    const bool alt = HasAlt<T, L>::value;
+    auto runnable = [&](int sc) {
+        return sc == SCHED_PASSES || sc == SCHED_PERSIST || (sc == SCHED_PASSES_ALT && alt) ||
+               (sc == SCHED_PLANE && plane);
+    };
+    if (forced_sched() >= 0) {
+        launch_sched<T, L>(a, st, runnable(forced_sched()) ? forced_sched() : SCHED_PASSES);
         return;
-    } else {
-        if constexpr (!PG::FITS) {
-            if (!cplane_ready<T, L>()) {
-                launch_sched<T, L>(a, st, SCHED_PASSES);
-                return;
-            }
-        }
-        if (forced_sched() >= 0) {
-            launch_sched<T, L>(a, st, forced_sched());
-            return;
-        }
-        const std::string key = std::string(tname<T>()) + "/N" + std::to_string(L / 2) + "/nb" + std::to_string(a.nbatch);
-        int sched = tune_lookup(key);
-        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-        BAE_CUDA(cudaStreamIsCapturing(st, &cs));
-        if (sched < 0 && (cs != cudaStreamCaptureStatusNone || a.no_tune))
-            sched = a.nbatch <= 4 ? SCHED_PLANE : SCHED_PASSES;
-        if (sched >= 0) {
-            launch_sched<T, L>(a, st, sched);
-            return;
-        }
-        // time both schedules on the real data: five rounds in alternating
-        // order, three back-to-back applies per timing, keep each schedule's
-        // best round (the two are often within 10%, where a single launch
-        // mostly measures launch jitter); every apply leaves a valid result
-        cudaEvent_t e[3];
-        for (auto& x : e) BAE_CUDA(cudaEventCreate(&x));
-        float best[2] = {1e30f, 1e30f};
-        for (int rep = 0; rep < 5; ++rep)
-            for (int k = 0; k < 2; ++k) {
-                const int sc = (rep & 1) ? 1 - k : k;
-                BAE_CUDA(cudaEventRecord(e[0], st));
-                for (int r = 0; r < 3; ++r) launch_sched<T, L>(a, st, sc);
-                BAE_CUDA(cudaEventRecord(e[1], st));
-                BAE_CUDA(cudaEventSynchronize(e[1]));
-                float ms = 0.f;
-                BAE_CUDA(cudaEventElapsedTime(&ms, e[0], e[1]));
-                best[sc] = ms < best[sc] ? ms : best[sc];
-            }
-        for (auto& x : e) cudaEventDestroy(x);
-        sched = best[SCHED_PLANE] < best[SCHED_PASSES] ? SCHED_PLANE : SCHED_PASSES;
-        tune_store(key, sched);
     }
+    const std::string key = std::string(tname<T>()) + "/N" + std::to_string(L / 2) + "/nb" + std::to_string(a.nbatch);
+    int sched = tune_lookup(key);
+    if (sched >= 0 && !runnable(sched)) sched = -1;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    BAE_CUDA(cudaStreamIsCapturing(st, &cs));
+    if (sched < 0 && (cs != cudaStreamCaptureStatusNone || a.no_tune))
+        sched = (a.nbatch <= 4 && plane) ? SCHED_PLANE : SCHED_PASSES;
+    if (sched >= 0) {
+        launch_sched<T, L>(a, st, sched);
+        return;
+    }
+    // time every runnable schedule on the real data: five rounds in rotating
+    // order, three back-to-back applies per timing, keep each schedule's
+    // best round (schedules are often within 10%, where a single launch
+    // mostly measures launch jitter); every apply leaves a valid result
+    int cand[4], nc = 0;
+    for (int sc : {SCHED_PASSES, SCHED_PASSES_ALT, SCHED_PLANE, SCHED_PERSIST})
+        if (runnable(sc)) cand[nc++] = sc;
+    cudaEvent_t e[2];
+    for (auto& x : e) BAE_CUDA(cudaEventCreate(&x));
+    float best[4] = {1e30f, 1e30f, 1e30f, 1e30f};
+    for (int rep = 0; rep < 5; ++rep)
+        for (int k = 0; k < nc; ++k) {
+            const int ci = (k + rep) % nc;
+            BAE_CUDA(cudaEventRecord(e[0], st));
+            for (int r = 0; r < 3; ++r) launch_sched<T, L>(a, st, cand[ci]);
+            BAE_CUDA(cudaEventRecord(e[1], st));
+            BAE_CUDA(cudaEventSynchronize(e[1]));
+            float ms = 0.f;
+            BAE_CUDA(cudaEventElapsedTime(&ms, e[0], e[1]));
+            best[ci] = ms < best[ci] ? ms : best[ci];
+        }
+    for (auto& x : e) cudaEventDestroy(x);
+    int bi = 0;
+    for (int k = 1; k < nc; ++k)
+        if (best[k] < best[bi]) bi = k;
+    tune_store(key, cand[bi]);
 }
 
 

@@ -3,11 +3,20 @@
 //
 // Each slot is a context with its own CUDA stream and work space, driven by
 // one host worker thread, so the device work of different requests
-// overlaps. A queued request is admitted (in queue order, skipping requests
-// that do not fit) as soon as a slot is free and its device-memory estimate
-// fits next to the requests in flight. All slots share one LGF spectrum
-// cache. A request's arithmetic is exactly that of bae_solve on a fresh
-// context: the kernels and reductions do not depend on the other slots.
+// overlaps. A queued request is admitted as soon as a slot is free and its
+// device-memory estimate fits next to the requests in flight. All slots
+// share one LGF spectrum cache. A request's arithmetic is exactly that of
+// bae_solve on a fresh context: the kernels and reductions do not depend on
+// the other slots.
+//
+// Priority classes: with two or more slots, the first half of the slots run
+// on streams of the device's highest priority and prefer small requests
+// (N <= 64), the others on the lowest priority and prefer large ones; a slot
+// with no request of its class queued takes the first one that fits, so no
+// slot idles while work waits. Small solves are latency-bound (a few
+// hundred short launches), large ones fill the GPU for tens of
+// milliseconds; with the same priority the small ones wait behind the large
+// ones' kernels (an N = 32 solve of ~1 ms alone took ~9 ms in the mix).
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -49,6 +58,8 @@ struct bae_server {
     int64_t budget = 0;
     int64_t in_use = 0;
     std::vector<bae_ctx*> slots;
+    std::vector<cudaStream_t> streams;   // one per slot, owned by the server
+    std::vector<int> small_class;        // per slot: 1 = high priority, prefers N <= 64
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<Req*> queue;
@@ -92,14 +103,22 @@ struct bae_server {
                 std::unique_lock<std::mutex> lock(mu);
                 for (;;) {
                     if (stop) return;
-                    for (auto it = queue.begin(); it != queue.end(); ++it) {
-                        // admit if it fits; a request larger than the whole budget
-                        // runs alone rather than never
-                        if (in_use + (*it)->footprint <= budget || in_use == 0) {
-                            r = *it;
-                            queue.erase(it);
-                            break;
+                    // the first request of this slot's class that fits, else
+                    // the first that fits; a request larger than the whole
+                    // budget runs alone rather than never
+                    auto pick = queue.end();
+                    for (int pass = 0; pass < 2 && pick == queue.end(); ++pass)
+                        for (auto it = queue.begin(); it != queue.end(); ++it) {
+                            const bool fits = in_use + (*it)->footprint <= budget || in_use == 0;
+                            const bool mine = ((*it)->rq.N <= 64) == (small_class[slot] != 0);
+                            if (fits && (pass == 1 || mine)) {
+                                pick = it;
+                                break;
+                            }
                         }
+                    if (pick != queue.end()) {
+                        r = *pick;
+                        queue.erase(pick);
                     }
                     if (r) break;
                     cv_work.wait(lock);
@@ -131,11 +150,33 @@ int bae_server_create(int device, int slots, int64_t hbm_budget_bytes, bae_serve
     auto s = std::make_unique<bae_server>();
     s->device = device;
     s->budget = hbm_budget_bytes;
+    int least = 0, greatest = 0;
+    {
+        bae::DeviceGuard dg;
+        if (cudaSetDevice(device) != cudaSuccess || cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+            cudaGetLastError();
+            bae::set_last_error("bae_server_create: no such CUDA device");
+            return BAE_ERR_INVALID_ARG;
+        }
+        for (int i = 0; i < slots; ++i) {
+            const int small = (slots >= 2 && i < slots / 2) ? 1 : 0;
+            cudaStream_t st = nullptr;
+            if (cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, small ? greatest : least) != cudaSuccess) {
+                cudaGetLastError();
+                for (cudaStream_t x : s->streams) cudaStreamDestroy(x);
+                bae::set_last_error("bae_server_create: stream creation failed");
+                return BAE_ERR_CUDA;
+            }
+            s->streams.push_back(st);
+            s->small_class.push_back(small);
+        }
+    }
     for (int i = 0; i < slots; ++i) {
         bae_ctx* c = nullptr;
-        const int rc = bae_ctx_create(device, nullptr, &c);
+        const int rc = bae_ctx_create(device, s->streams[i], &c);
         if (rc != BAE_OK) {
             for (bae_ctx* x : s->slots) bae_ctx_destroy(x);
+            for (cudaStream_t x : s->streams) cudaStreamDestroy(x);
             return rc;
         }
         if (!s->slots.empty()) bae::ctx_share_cache(c, s->slots.front());
@@ -230,6 +271,11 @@ void bae_server_destroy(bae_server* srv) {
     srv->cv_work.notify_all();
     for (auto& t : srv->workers) t.join();
     for (bae_ctx* c : srv->slots) bae_ctx_destroy(c);
+    {
+        bae::DeviceGuard dg;
+        cudaSetDevice(srv->device);
+        for (cudaStream_t x : srv->streams) cudaStreamDestroy(x);
+    }
     delete srv;
 }
 

@@ -49,8 +49,9 @@ def test_apply_full_size(setup):
 
 @pytest.mark.parametrize("precision,tol", [("fp32", 2e-6), ("fp64", 1e-12), ("df64", 1e-12)])
 def test_apply_full_size_each_schedule(setup, precision, tol):
-    # the five-pass schedule and the plane-fused one (one CTA per plane for
-    # float32, a two-CTA cluster sharing the plane for the 16-byte types)
+    # the five-pass schedule, its second launch geometry (float32: half-width
+    # column blocks) and the plane-fused one (one CTA per plane for float32,
+    # a two-CTA cluster sharing the plane for the 16-byte types)
     import torch
     from paper_2502_05507_gb300 import set_conv_schedule
     P, cls, spec, prob = setup["P"], setup["cls"], setup["spec"], setup["prob"]
@@ -58,7 +59,7 @@ def test_apply_full_size_each_schedule(setup, precision, tol):
     ref = OP.fft_convolve(OP.source_density(cls, q, "double"), spectrum=spec, workers=-1)
     scale = np.max(np.abs(ref))
     try:
-        for name in ("passes", "plane"):
+        for name in ("passes", "passes_alt", "persist", "plane"):
             set_conv_schedule(name)
             v = prob.potential_apply(torch.from_numpy(q).cuda(), precision).cpu().numpy()
             assert np.max(np.abs(v - ref)) <= tol * scale, name

@@ -1,9 +1,13 @@
-"""The two schedules of the FFT convolution inside the potential apply
+"""The schedules of the FFT convolution inside the potential apply
 (Section 3.2: the discrete potentials as lattice sums with the LGF): five
-separate transform passes, or the k and j transforms fused per x-plane (one
-CTA per plane where the plane fits in shared memory, a thread-block cluster
-sharing it through distributed shared memory where it does not: float32 at
-N = 256, float64 and double-float at N >= 128).
+separate transform passes, the same with the second launch geometry
+(float32: half-width column blocks at N = 128, the three-level transform at
+N = 256), the five passes as persistent kernels over all right-hand sides,
+or the k and j transforms fused per x-plane (one CTA per plane
+where the plane fits in shared memory, a thread-block cluster sharing it
+through distributed shared memory where it does not: float32 at N = 256,
+float64 and double-float at N >= 128). Every schedule the autotuner can
+pick is here.
 
 Each schedule is forced in turn and compared with the oracle: its FFT
 convolution at N = 64, and at N = 256 plain sums over the nonzero sources at
@@ -57,7 +61,7 @@ def test_schedules_n64_vs_oracle_fft(schedule, precision):
     ctx, prob = _gpu(P)
     try:
         out = {}
-        for name in ("passes", "plane"):
+        for name in ("passes", "passes_alt", "persist", "plane"):
             schedule(name)
             out[name] = _apply(prob, q, precision)
             assert np.max(np.abs(out[name] - ref)) <= TOL[precision] * scale, name
@@ -102,14 +106,15 @@ def test_schedules_n256_vs_sampled_direct_sums(schedule, kappa2):
     try:
         full = {}
         for precision in ("fp32", "fp64", "df64"):
-            for name in ("passes", "plane"):
+            for name in ("passes", "passes_alt", "persist", "plane"):
                 schedule(name)
                 v = _apply(prob, q, precision)
                 err = np.max(np.abs(v[targets] - ref))
                 assert err <= TOL[precision] * scale, (precision, name, err / scale)
                 full[precision, name] = v
-            d = np.max(np.abs(full[precision, "passes"] - full[precision, "plane"]))
-            assert d <= TOL[precision] * scale, (precision, d / scale)
+            for other in ("passes_alt", "persist", "plane"):
+                d = np.max(np.abs(full[precision, "passes"] - full[precision, other]))
+                assert d <= TOL[precision] * scale, (precision, other, d / scale)
     finally:
         prob.close()
         ctx.close()
@@ -129,7 +134,7 @@ def test_batched_solve_n256_cluster_schedule(schedule):
         f = np.stack([P.f(), np.zeros_like(P.f())])
         g = np.stack([g1, g2])
         res = {}
-        for name in ("passes", "plane"):
+        for name in ("passes", "passes_alt", "persist", "plane"):
             schedule(name)
             q, u, st = prob.solve_batched(torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda(), tol=1e-10,
                                           precision="mixed")
