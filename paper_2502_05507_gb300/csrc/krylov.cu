@@ -262,8 +262,46 @@ __device__ __forceinline__ void chunk_update(const RowView& V, long long n, long
 // warp order: ~2 float64 warp instructions per row instead of a shuffle
 // tree per row (each float64 warp instruction occupies GB300's FP64 pipe
 // for ~64 cycles). s_red: 8 x 32 doubles of shared memory.
+// The same sums when at most 32 / G rows are used (the first Arnoldi steps
+// of a cycle): lane = (row r = lane % R, element group g = lane / R), each
+// lane sums its row over the 8 / G elements g, g + G, ... of the warp's 8,
+// and the G groups meet through the shuffle tree, so a float64 warp
+// instruction has (nearly) all lanes busy instead of one per row.
+template <int G>
+__device__ __forceinline__ void chunk_dots_grouped(const RowView& V, int cols, const double* s_w, double* part,
+                                                   int nch, int c, double* s_red) {
+    constexpr int R = 32 / G, E = 8 / G;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r = lane % R, g = lane / R;
+    double acc = 0.0;
+    if (r < cols) {
+        double p0 = 0.0, p1 = 0.0;
+#pragma unroll
+        for (int u = 0; u < E; ++u) {
+            const int e = 8 * warp + g + G * u;
+            if (u & 1) p1 = __fma_rn(V.at(r, e), s_w[e], p1);
+            else p0 = __fma_rn(V.at(r, e), s_w[e], p0);
+        }
+        acc = E > 1 ? p0 + p1 : p0;
+    }
+#pragma unroll
+    for (int o = R; o < 32; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (g == 0) s_red[warp * 32 + r] = acc;
+    __syncthreads();
+    if (warp == 0 && lane < cols) {
+        double t = s_red[lane];
+#pragma unroll
+        for (int q = 1; q < 8; ++q) t += s_red[q * 32 + lane];
+        part[(long long)lane * nch + c] = t;
+    }
+    __syncthreads();
+}
+
 __device__ __forceinline__ void chunk_dots(const RowView& V, int cols, const double* s_w, double* part, int nch,
                                            int c, double* s_red) {
+    if (cols <= 4) return chunk_dots_grouped<8>(V, cols, s_w, part, nch, c, s_red);
+    if (cols <= 8) return chunk_dots_grouped<4>(V, cols, s_w, part, nch, c, s_red);
+    if (cols <= 16) return chunk_dots_grouped<2>(V, cols, s_w, part, nch, c, s_red);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double wv[8];
 #pragma unroll
