@@ -10,13 +10,17 @@
 namespace bae {
 
 // Transform plan of the pass kernels per element type and length: the
-// three-level 8 x 8 x 8 plan for 16-byte elements at L = 512 (float64 and
-// double-float, whose two-level 16 x 32 split needs ~200-255 registers per
-// thread), the two-level plan elsewhere.
+// three-level plans for 16-byte elements at L = 256 (8 x 8 x 4) and L = 512
+// (8 x 8 x 8) (float64 and double-float, whose two-level 16 x 16 and
+// 16 x 32 splits need ~170-255 registers per thread), the two-level plan
+// elsewhere.
 // V selects a geometry variant of the pass kernels for the autotuner:
 // variant 1 exists for float32 at L = 256 (column blocks of half the width,
-// 16 columns) and L = 512 (the three-level plan); elsewhere it equals 0.
+// 16 columns, three CTAs per SM) and L = 512 (the three-level plan);
+// elsewhere it equals 0.
 template <typename T, int L, int V = 0> struct PlanOf { using type = Plan2<L>; };
+template <int V> struct PlanOf<double, 256, V> { using type = Plan3_256; };
+template <int V> struct PlanOf<dsf, 256, V> { using type = Plan3_256; };
 template <int V> struct PlanOf<double, 512, V> { using type = Plan3_512; };
 template <int V> struct PlanOf<dsf, 512, V> { using type = Plan3_512; };
 template <> struct PlanOf<float, 512, 1> { using type = Plan3_512; };
@@ -32,21 +36,25 @@ template <typename T, int L, int V = 0> struct Geo {
     static constexpr bool THREE = PL::TH * PL::S == L && PL::TH > PL::S;
     static constexpr int TH = PL::TH, S = PL::S;   // threads per line, values per thread
     // column passes: W columns per CTA, TH threads per column (three-level:
-    // 128-byte row segments, 8 columns of float32 or 4 of 16-byte elements)
+    // 64-byte row segments at 64 threads per line, 128-byte ones at 32, so
+    // that a CTA has 256 threads for the 16-byte types)
     static constexpr int WB = 65536 / (L * (int)sizeof(C));
-    static constexpr int W0 = THREE ? 128 / (int)sizeof(C) / 2 : (WB > 32 ? 32 : (WB < 8 ? 8 : WB));
+    static constexpr int W0 = THREE ? (128 / (int)sizeof(C) / 2) * (64 / TH) : (WB > 32 ? 32 : (WB < 8 ? 8 : WB));
     static constexpr int W = (V == 1 && !THREE && HasAlt<T, L>::value) ? W0 / 2 : W0;
     static constexpr int CT = W * TH;
     static constexpr int XL = PL::XLEN;            // exchange positions per column
     // line passes (k): P line pairs per CTA, TH threads per pair
     static constexpr int PB = 65536 / (L * (int)sizeof(C));
-    static constexpr int P = THREE ? 4 : ((256 / TH) < PB ? (256 / TH) : (PB < 4 ? 4 : PB));
+    static constexpr int P = THREE ? 256 / TH : ((256 / TH) < PB ? (256 / TH) : (PB < 4 ? 4 : PB));
     static constexpr int KT = P * TH;
     static constexpr int XS = PL::XS;              // exchange stride per pair (odd)
     // resident CTAs per SM the compiler must allow (register cap): three per
     // SM for the three-level plan (at most 85 registers per thread, as its
-    // kernels need), no constraint otherwise
-    static constexpr int MINB = THREE ? 3 : 1;
+    // kernels need) and for variant 1 of float32 at L = 256 (its i pass
+    // otherwise takes 123 registers, two CTAs per SM), no constraint
+    // otherwise
+    static constexpr bool CAP3 = THREE || (V == 1 && std::is_same<T, float>::value && L == 256);
+    static constexpr int MINB = CAP3 ? 3 : 1;
 };
 
 template <typename T>

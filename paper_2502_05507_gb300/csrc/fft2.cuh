@@ -320,4 +320,94 @@ struct Plan3_512 {
     }
 };
 
+// Three levels for L = 256 = 8 x 8 x 4: 32 threads per line (one warp), 8
+// values each (the two-level 16 x 16 split holds 16 values per thread:
+// 170-210 registers for 16-byte elements, one 256-thread CTA per SM). With
+// n = t + 32 m, t = t1 + 4 t2 (t1 < 4, t2 < 8), k = k3 + 8 k2 + 64 k1:
+//   X[k] = sum_t1 W4^{t1 k1} W32^{t1 k2} sum_t2 W8^{t2 k2}
+//          [ W256^{t k3} sum_m W8^{m k3} x[t + 32 m] ]
+// stage A: thread t, DFT over m (slots k3), twiddle W256^{t k3}; exchange;
+// stage B: thread t1 + 4 k3, DFT over t2 (slots k2), twiddle W32^{t1 k2};
+// exchange; stage C: thread u takes the two pairs (k3, k2) = (u % 8,
+// u / 8 + 4 h), h < 2, each a 4-point DFT over t1. Slot s = h + 2 k1 then
+// holds X[u + 32 s]. The inverse runs the stages backwards with conjugate
+// twiddles. Positions are swizzled, p -> p ^ rev3((p >> 5) & 7) (rev3
+// reverses three bits), so that the 16-byte accesses of a line (one warp)
+// hit eight distinct bank groups in every stage: rows of 32 positions
+// apart land on distinct groups, and the two 4-aligned blocks read in stage
+// B land in different halves.
+struct Plan3_256 {
+    static constexpr int TH = 32, S = 8;
+    static constexpr int XLEN = 256;
+    static constexpr int XS = XLEN + 1;
+    __host__ __device__ static constexpr int kidx(int t, int s) { return t + 32 * s; }
+    __device__ __forceinline__ static int pos(int p) {
+        const int r = (p >> 5) & 7;
+        return p ^ (((r & 1) << 2) | (r & 2) | ((r >> 2) & 1));
+    }
+
+    template <bool ZHI, typename C>
+    __device__ __forceinline__ static void fwd(C* v, C* xch, int base, int es, int t, const C* __restrict__ tw) {
+        if constexpr (ZHI) rdft_zhi<8, false>(v);       // v[k3]
+        else rdft<8, false>(v);
+#pragma unroll
+        for (int k3 = 1; k3 < 8; ++k3) v[k3] = cmul(v[k3], ldg_c(tw + t * k3));
+#pragma unroll
+        for (int k3 = 0; k3 < 8; ++k3) xch[base + pos(k3 * 32 + t) * es] = v[k3];
+        __syncthreads();
+        const int t1 = t & 3, k3 = t >> 2;
+#pragma unroll
+        for (int t2 = 0; t2 < 8; ++t2) v[t2] = xch[base + pos(k3 * 32 + t1 + 4 * t2) * es];
+        __syncthreads();
+        rdft<8, false>(v);                               // v[k2]
+#pragma unroll
+        for (int k2 = 1; k2 < 8; ++k2) v[k2] = cmul(v[k2], ldg_c(tw + 8 * t1 * k2));
+#pragma unroll
+        for (int k2 = 0; k2 < 8; ++k2) xch[base + pos((k3 * 8 + k2) * 4 + t1) * es] = v[k2];
+        __syncthreads();
+        const int c3 = t & 7, c2 = t >> 3;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            C w[4];
+#pragma unroll
+            for (int u1 = 0; u1 < 4; ++u1) w[u1] = xch[base + pos((c3 * 8 + c2 + 4 * h) * 4 + u1) * es];
+            rdft<4, false>(w);                           // w[k1]
+#pragma unroll
+            for (int k1 = 0; k1 < 4; ++k1) v[h + 2 * k1] = w[k1];   // X[t + 32 (h + 2 k1)]
+        }
+        __syncthreads();
+    }
+
+    template <typename C>
+    __device__ __forceinline__ static void inv(C* v, C* xch, int base, int es, int t, const C* __restrict__ tw) {
+        const int c3 = t & 7, c2 = t >> 3;               // this thread's pairs (k3, k2 + 4 h)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            C w[4];
+#pragma unroll
+            for (int k1 = 0; k1 < 4; ++k1) w[k1] = v[h + 2 * k1];
+            rdft<4, true>(w);                            // w[t1]
+#pragma unroll
+            for (int u1 = 0; u1 < 4; ++u1) xch[base + pos((c3 * 8 + c2 + 4 * h) * 4 + u1) * es] = w[u1];
+        }
+        __syncthreads();
+        const int t1 = t & 3, k3 = t >> 2;
+#pragma unroll
+        for (int k2 = 0; k2 < 8; ++k2) v[k2] = xch[base + pos((k3 * 8 + k2) * 4 + t1) * es];
+        __syncthreads();
+#pragma unroll
+        for (int k2 = 1; k2 < 8; ++k2) v[k2] = cmulc(v[k2], ldg_c(tw + 8 * t1 * k2));
+        rdft<8, true>(v);                                // v[t2]
+#pragma unroll
+        for (int t2 = 0; t2 < 8; ++t2) xch[base + pos(k3 * 32 + t1 + 4 * t2) * es] = v[t2];
+        __syncthreads();
+#pragma unroll
+        for (int j3 = 0; j3 < 8; ++j3) v[j3] = xch[base + pos(j3 * 32 + t) * es];
+        __syncthreads();
+#pragma unroll
+        for (int j3 = 1; j3 < 8; ++j3) v[j3] = cmulc(v[j3], ldg_c(tw + t * j3));
+        rdft<8, true>(v);                                // v[m] = x[t + 32 m]
+    }
+};
+
 }  // namespace bae
