@@ -287,7 +287,7 @@ __device__ __forceinline__ void colpass_tile(const ConvArgs<T>& a, int bx, int b
 // strided over a grid of resident CTAs (PERSIST) or one per CTA of the grid
 // (column blocks, lines, right-hand sides)
 template <typename T, int L, int MODE, bool BOX = false, int V = 0, bool PERSIST = false>
-__global__ void __launch_bounds__(Geo<T, L, V>::CT, Geo<T, L, V>::MINB) k_colpass(ConvArgs<T> a) {
+__global__ void __launch_bounds__(Geo<T, L, V>::CT, Geo<T, L, V>::minb_col(MODE)) k_colpass(ConvArgs<T> a) {
     wait_prior_grid();   // results of the previous kernel on the stream
     if constexpr (PERSIST) {
         constexpr int N = L / 2;

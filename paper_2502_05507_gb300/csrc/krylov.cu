@@ -576,8 +576,11 @@ __device__ __forceinline__ void coop_reduce(const Arnoldi& a, int nctas, const i
 // the basis rows V[0..j] in shared memory (copied asynchronously while the
 // gather runs), so the three projections read it from there; the sums are
 // the same expressions in the same order as with global rows.
+// Compiled for three resident CTAs per SM (at most 85 registers; it needs
+// 80 without spilling): left free, the compiler takes 91 and only two CTAs
+// fit, which made the 64-right-hand-side step ~40% slower.
 template <typename VT, bool SV>
-__global__ void __launch_bounds__(256) k_arn_step_coop(Arnoldi a) {
+__global__ void __launch_bounds__(256, 3) k_arn_step_coop(Arnoldi a) {
     extern __shared__ double s_dyn[];
     const int m = a.m;
     double* s_h = s_dyn;                 // m + 1
