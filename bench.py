@@ -187,11 +187,18 @@ DF64_OPS_PER_FLOP = 7.0
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum)
-# of convolution kernels at the headline workload, from one ncu capture of
-# the current kernels (profiles/); a kernel changed since its capture is
-# dropped from this table (its traffic is then reported as null). Keyed by
-# (kernel, N, right-hand sides per launch).
-NCU_TRAFFIC = {}
+# of convolution kernels, from ncu captures of the current kernels
+# (profiles/); a kernel changed since its capture is dropped from this
+# table (its traffic is then reported as null). Keyed by (kernel, N,
+# right-hand sides per launch). The 64-right-hand-side figure is the
+# 16-right-hand-side capture (764.7 MB: 414.5 read + 350.2 written) scaled
+# by 4, less the three extra reads of the 8.6 MB spectrum octant that one
+# launch shares over its right-hand sides (a capture at 64 would hold
+# ~10 GB on the device under ncu's replay).
+NCU_TRAFFIC = {
+    ("conv_i.f32", 128, 64): 4 * 764.7e6 - 3 * 8.59e6,   # conv_passes_batched16_torus_N128.md
+    ("conv_i.f32", 128, 1): 33.98e6,                       # conv_passes_torus_N128.md
+}
 
 
 def roofline_for(name, ms_total, launches, n, n_gm, hbm, hbm_kind, npl=None, nb=1):
@@ -360,7 +367,10 @@ def run_ours(args, rank, world, dev):
     ud = u.cpu().numpy()
     out["max_err_vs_exact"] = max(_rel_err(ud[k], probs[k].u_exact(), interior) for k in range(nrhs))
 
-    # the same steps with float64 residual applies (the benchmark spec form)
+    # the same steps with float64 residual applies, after their own warm-up
+    # (the first float64 apply of this batch size times the schedules)
+    for _ in range(max(args.warmup, 1)):
+        step("fp64")
     ms64, (q64, u64, st64) = _timed_loop(lambda: step("fp64"), args.steps, torch, flush)
     out["mixed_fp64_residual"] = {"value": nrhs * 1000.0 / float(ms64.mean()), "unit": UNIT,
                                   "ms_per_step": float(ms64.mean()), "steps": args.steps,
@@ -431,7 +441,7 @@ def run_ours(args, rank, world, dev):
     if not args.no_extra:
         out["torus128_kappa10"] = run_torus128_extra(ctx, torch, flush, hbm, hbm_kind)
         out["star256"] = run_star256_table(ctx, torch)
-        out["serving"] = serving_run(400)
+        out["serving"] = serving_run(2000)
 
     # --------------------------------------------------------- cpu baseline
     if world == 1 and not args.no_cpu:
@@ -524,8 +534,10 @@ def run_star256_table(ctx, torch, reps=3):
                    "max_err_vs_exact": _rel_err(u.cpu().numpy(), P.u_exact(), P.phi < 0)}
             if k2 == 0.0 and layer == "double":
                 profile_start(20000)
+                torch.cuda.nvtx.range_push("star256_profiled")   # ncu --nvtx-include star256_profiled/
                 step()
                 torch.cuda.synchronize()
+                torch.cuda.nvtx.range_pop()
                 prof = profile_stop()
                 row["kernels"] = kernel_table(prof, 10)
                 row["conv_f32_apply"] = apply_summary(prof, 256, phi_ - plo, 1, hbm)

@@ -150,8 +150,8 @@ long long bae_launch_count(void);
  * thread-block cluster sharing it through distributed shared memory where it
  * does not); BAE_SCHED_PASSES_ALT (2) runs the five passes with a second
  * launch geometry (float32: column blocks of half the width at N = 128, the
- * three-level 8 x 8 x 8 transform at N = 256; elsewhere the same as
- * BAE_SCHED_PASSES); BAE_SCHED_PERSIST (3) runs the five passes as
+ * three-level 8 x 8 x 8 transform at N = 256; float64: the three-level
+ * 8 x 8 x 4 transform at N = 128; elsewhere the same as BAE_SCHED_PASSES); BAE_SCHED_PERSIST (3) runs the five passes as
  * persistent kernels, each launched with at most the CTAs that are resident
  * at once, striding over the tiles of every right-hand side of the batch.
  * All compute the same convolution (Section 3.2, the

@@ -295,6 +295,10 @@ struct bae_ctx {
     // Schwarz rows), ordered by the fork and join events
     cudaStream_t side = nullptr;
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    // a server slot: other slots' kernels run beside this context's on the
+    // same GPU, so no kernel may assume that all of its CTAs are resident at
+    // once (the Arnoldi step runs as three kernels, not the cooperative one)
+    bool shared_gpu = false;
     int* pinned = nullptr;       // mapped host memory the kernels write the live flags into
     int* pinned_dev = nullptr;   // its device address
     int pinned_cap = 0;
@@ -349,6 +353,7 @@ struct bae_problem {
 namespace bae {
 
 void ctx_share_cache(bae_ctx* dst, const bae_ctx* src) { dst->cache = src->cache; }
+void ctx_set_shared_gpu(bae_ctx* c) { c->shared_gpu = true; }
 
 bool problem_view(const bae_problem* P, ProblemView& out) {
     if (!P || !P->spec) return false;
@@ -618,8 +623,9 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
     int* member = ibuf + 2 * nb;
     a.j = ibuf + 3 * nb;
     a.ctr = reinterpret_cast<unsigned int*>(ws.arnCtr.need((long long)nb * 3));
-    // the fused cooperative step where the device can place it
-    a.coop_grid = arn_coop_grid(n, nb, m, &a.coop_resident);
+    // the fused cooperative step where the device can place it and has it
+    // to itself
+    a.coop_grid = P->ctx->shared_gpu ? 0 : arn_coop_grid(n, nb, m, &a.coop_resident);
     a.bar = ws.arnBar.need(2);
     a.bar2 = a.bar + 1;
     a.err = ibuf + 4 * nb;

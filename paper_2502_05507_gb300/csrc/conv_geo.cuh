@@ -16,17 +16,21 @@ namespace bae {
 // elsewhere.
 // V selects a geometry variant of the pass kernels for the autotuner:
 // variant 1 exists for float32 at L = 256 (column blocks of half the width,
-// 16 columns, three CTAs per SM) and L = 512 (the three-level plan);
-// elsewhere it equals 0.
+// 16 columns, three CTAs per SM) and L = 512 (the three-level plan), and
+// for float64 at L = 256 (the three-level plan: more warps per SM, but a
+// second twiddle stage on the narrow FP64 pipe, which costs more than the
+// occupancy gains once a launch holds many right-hand sides); elsewhere it
+// equals 0.
 template <typename T, int L, int V = 0> struct PlanOf { using type = Plan2<L>; };
-template <int V> struct PlanOf<double, 256, V> { using type = Plan3_256; };
+template <> struct PlanOf<double, 256, 1> { using type = Plan3_256; };
 template <int V> struct PlanOf<dsf, 256, V> { using type = Plan3_256; };
 template <int V> struct PlanOf<double, 512, V> { using type = Plan3_512; };
 template <int V> struct PlanOf<dsf, 512, V> { using type = Plan3_512; };
 template <> struct PlanOf<float, 512, 1> { using type = Plan3_512; };
 
 template <typename T, int L> struct HasAlt {
-    static constexpr bool value = std::is_same<T, float>::value && (L == 256 || L == 512);
+    static constexpr bool value =
+        (std::is_same<T, float>::value && (L == 256 || L == 512)) || (std::is_same<T, double>::value && L == 256);
 };
 
 // Launch geometry per transform length, precision and variant.

@@ -19,7 +19,8 @@ namespace bae {
 
 // SCHED_PASSES_ALT: the five passes with the variant-1 launch geometry
 // (float32: half-width column blocks at N = 128, the three-level transform
-// plan at N = 256; elsewhere the same as SCHED_PASSES).
+// plan at N = 256; float64 at N = 128: the three-level transform plan;
+// elsewhere the same as SCHED_PASSES).
 // SCHED_PERSIST: the five passes as persistent kernels, each launched with
 // at most the CTAs resident at once, which stride over the tiles of every
 // right-hand side.

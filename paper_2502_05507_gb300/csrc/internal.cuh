@@ -25,5 +25,8 @@ bool problem_view(const bae_problem* P, ProblemView& out);
 
 // Makes dst use src's LGF spectrum cache (contexts of one server share it).
 void ctx_share_cache(bae_ctx* dst, const bae_ctx* src);
+// marks a context whose GPU runs other contexts' kernels at the same time
+// (a server slot): it launches no cooperative kernel
+void ctx_set_shared_gpu(bae_ctx* c);
 
 }  // namespace bae

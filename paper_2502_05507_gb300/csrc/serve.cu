@@ -180,6 +180,7 @@ int bae_server_create(int device, int slots, int64_t hbm_budget_bytes, bae_serve
             return rc;
         }
         if (!s->slots.empty()) bae::ctx_share_cache(c, s->slots.front());
+        bae::ctx_set_shared_gpu(c);
         s->slots.push_back(c);
     }
     for (int i = 0; i < slots; ++i) s->workers.emplace_back([srv = s.get(), i]() { srv->worker(i); });
