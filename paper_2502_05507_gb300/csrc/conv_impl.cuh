@@ -76,16 +76,23 @@ __device__ __forceinline__ void kpass_fwd_tile(const ConvArgs<T>& a, int bx, int
         for (int k = t; k < 2 * N; k += TH)
             r[k] = active ? volume_or_zero(a, b, (k < N ? la : lb) * N + (k < N ? k : k - N)) : (T)0;
         __syncthreads();
-        if (active) {
-            const double* q = a.q + (long long)b * a.q_stride + (a.q_row ? (long long)a.q_row[b] * a.q_row_stride : 0);
-            const float* q32 = a.q32 ? a.q32 + (long long)b * a.q32_stride : nullptr;
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                const long long l = half ? lb : la;
-                const int s0 = a.rec.line_off[l], s1 = a.rec.line_off[l + 1];
-                for (int s = s0 + t; s < s1; s += TH) {
-                    const int k = a.rec.src_lin[s] - (int)(l * N);
-                    r[half * N + k] = source_value<T>(a.rec, s, q, q32);
+        {
+            // the sources of the CTA's lines are one contiguous range of the
+            // recipe (its line pairs are consecutive): every thread of the CTA
+            // takes sources of the range, so each chain of dependent loads
+            // (offsets, node, terms, density) runs once, not once per line
+            const long long l0 = 2 * ((long long)a.plane_lo() * (N / 2) + (long long)bx * G::P);
+            const long long l1 = 2 * min((long long)a.plane_lo() * (N / 2) + (long long)(bx + 1) * G::P,
+                                         (long long)a.plane_hi() * (N / 2));
+            if (l0 < l1) {
+                const double* q =
+                    a.q + (long long)b * a.q_stride + (a.q_row ? (long long)a.q_row[b] * a.q_row_stride : 0);
+                const float* q32 = a.q32 ? a.q32 + (long long)b * a.q32_stride : nullptr;
+                const int s0 = a.rec.line_off[l0], s1 = a.rec.line_off[l1];
+                for (int s = s0 + (int)threadIdx.x; s < s1; s += (int)blockDim.x) {
+                    const int lin = a.rec.src_lin[s];
+                    const int rel = (int)(lin / N - l0);   // line within the CTA: pair rel / 2, half rel % 2
+                    rho[(rel >> 1) * 2 * N + (rel & 1) * N + (lin % N)] = source_value<T>(a.rec, s, q, q32);
                 }
             }
         }
