@@ -14,6 +14,8 @@
 // local memory; one shared-memory round trip per transform.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace bae {
@@ -86,17 +88,58 @@ __device__ __forceinline__ void rdft4(C& x0, C& x1, C& x2, C& x3) {
     x3 = csub(t1, t3);
 }
 
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// The radix-2 butterfly lo = e + W o, hi = e - W o with W = W_R^{+-K} a
+// compile-time root. For float32 and float64 a general rotation is folded
+// into the butterfly with fused multiply-adds (the factorisation of Linzer
+// and Feig, "Implementation of efficient FFT algorithms on fused
+// multiply-add architectures", IEEE Trans. Signal Process. 41, 1993):
+// W o = f (o + i r o) with f the larger of |cos|, |sin| (so |r| <= 1), then
+// e +- f u: six fused operations instead of a four-operation rotation and
+// four additions. Rotations by multiples of pi/2 and the double-float type
+// keep the plain form.
+template <int R, int K, bool INV, typename C>
+__device__ __forceinline__ void bfly(const C& e, const C& o, C& lo, C& hi) {
+    using T = decltype(o.x);
+    constexpr int m = ((K * (32 / R)) % 32 + 32) % 32;
+    if constexpr (!(std::is_same<T, float>::value || std::is_same<T, double>::value) || m % 8 == 0) {
+        const C w = wmul<R, K, INV>(o);
+        lo = cadd(e, w);
+        hi = csub(e, w);
+    } else {
+        constexpr Root32 w = root32(m);
+        constexpr double c = w.c, sn = INV ? w.s : -w.s;   // W = c + i sn
+        T ux, uy, f;
+        if constexpr (c * c >= sn * sn) {   // W = c (1 + i sn/c)
+            constexpr double r = sn / c;
+            ux = fma_t((T)-r, o.y, o.x);
+            uy = fma_t((T)r, o.x, o.y);
+            f = (T)c;
+        } else {                            // W = sn (c/sn + i)
+            constexpr double r = c / sn;
+            ux = fma_t((T)r, o.x, -o.y);
+            uy = fma_t((T)r, o.y, o.x);
+            f = (T)sn;
+        }
+        lo = cmake<C>(fma_t(f, ux, e.x), fma_t(f, uy, e.y));
+        hi = cmake<C>(fma_t(-f, ux, e.x), fma_t(-f, uy, e.y));
+    }
+}
+
+// the butterflies k = K .. R/2 - 1 of a radix-2 step: v[k], v[k + R/2]
+template <int R, bool INV, typename C, int K>
+struct Bflies {
+    __device__ __forceinline__ static void run(const C* e, const C* o, C* v) {
+        bfly<R, K, INV>(e[K], o[K], v[K], v[K + R / 2]);
+        if constexpr (K + 1 < R / 2) Bflies<R, INV, C, K + 1>::run(e, o, v);
+    }
+};
+
 // In-register DFT of v[0..R) in natural order, R in {2, 4, 8, 16, 32}.
 template <int R, bool INV, typename C>
 __device__ __forceinline__ void rdft(C* v);
-
-template <int R, bool INV, typename C, int K>
-struct TwTail {  // v[K] *= W_R^{K} ... applied to the odd half (radix-2 split)
-    __device__ __forceinline__ static void run(C* odd) {
-        odd[K] = wmul<R, K, INV>(odd[K]);
-        if constexpr (K + 1 < R / 2) TwTail<R, INV, C, K + 1>::run(odd);
-    }
-};
 
 template <int R, bool INV, typename C>
 __device__ __forceinline__ void rdft(C* v) {
@@ -114,12 +157,7 @@ __device__ __forceinline__ void rdft(C* v) {
         }
         rdft<R / 2, INV>(e);
         rdft<R / 2, INV>(o);
-        TwTail<R, INV, C, 1>::run(o);
-#pragma unroll
-        for (int k = 0; k < R / 2; ++k) {
-            v[k] = cadd(e[k], o[k]);
-            v[k + R / 2] = csub(e[k], o[k]);
-        }
+        Bflies<R, INV, C, 0>::run(e, o, v);
     }
 }
 
@@ -146,12 +184,7 @@ __device__ __forceinline__ void rdft_zhi(C* v) {
         }
         rdft_zhi<R / 2, INV>(e);
         rdft_zhi<R / 2, INV>(o);
-        TwTail<R, INV, C, 1>::run(o);
-#pragma unroll
-        for (int k = 0; k < R / 2; ++k) {
-            v[k] = cadd(e[k], o[k]);
-            v[k + R / 2] = csub(e[k], o[k]);
-        }
+        Bflies<R, INV, C, 0>::run(e, o, v);
     }
 }
 
