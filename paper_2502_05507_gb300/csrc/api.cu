@@ -157,7 +157,7 @@ struct Workspace {
     Grow<double> v64, up, vstage;             // [nb][N^3]
     Grow<float> v32;
     Grow<double> V, w, partial, h, hsave, x, r, bvec, tmp, qstage, n2;   // Krylov
-    Grow<double> arnH, arnCS, arnG, arnY, arnScal, arnP;
+    Grow<double> arnH, arnHu, arnCS, arnG, arnY, arnScal;
     Grow<int> active, arnI;
     Grow<unsigned int> arnCtr;
     Grow<unsigned long long> arnBar;
@@ -170,7 +170,7 @@ struct Workspace {
         Grow<double>* ds[] = {&v64, &up, &vstage, &V, &w, &partial, &h, &hsave, &x, &r, &bvec, &tmp,
                               &qstage, &n2, &in_f, &in_g, &out_q, &out_u, &qpre, &zpre, &ydir64, &bprime};
         for (auto* d : ds) d->st = st;
-        Grow<double>* ds2[] = {&arnH, &arnCS, &arnG, &arnY, &arnScal, &arnP};
+        Grow<double>* ds2[] = {&arnH, &arnHu, &arnCS, &arnG, &arnY, &arnScal};
         for (auto* d : ds2) d->st = st;
         A.st = B.st = st;
         v32.st = st;
@@ -605,10 +605,11 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
     a.nchunk = arnoldi_chunks(n);
     a.V = ws.V.need((long long)nb * (m + 1) * n);
     a.w = ws.w.need((long long)nb * n);
-    a.part = ws.partial.need((long long)nb * (m + 2) * a.nchunk);
-    a.h1 = ws.h.need((long long)nb * (m + 1));
-    a.hcol = ws.hsave.need((long long)nb * (m + 1));
+    a.part = ws.partial.need((long long)nb * 2 * (m + 1) * a.nchunk);
+    a.cf = ws.h.need((long long)nb * 2 * (m + 1));
+    a.hs = ws.hsave.need((long long)nb * (m + 1));
     a.H = ws.arnH.need((long long)nb * m * (m + 1));
+    a.Hu = ws.arnHu.need((long long)nb * m * (m + 1));
     a.cs = ws.arnCS.need((long long)nb * m * 2);
     a.sn = a.cs + (long long)nb * m;
     a.g = ws.arnG.need((long long)nb * (m + 1));
@@ -616,8 +617,9 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
     double* scal = ws.arnScal.need((long long)nb * 5);
     a.est = scal;
     a.target = scal + nb;
-    a.inv = scal + 2 * nb;   // scal + 3 nb: spare
-    int* ibuf = ws.arnI.need((long long)nb * 6 + 1);
+    a.inv = scal + 2 * nb;
+    a.tco = scal + 3 * nb;
+    int* ibuf = ws.arnI.need((long long)nb * 8 + 1);
     a.flag = ibuf;
     a.ncols = ibuf + nb;
     int* member = ibuf + 2 * nb;
@@ -625,15 +627,16 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
     a.ctr = reinterpret_cast<unsigned int*>(ws.arnCtr.need((long long)nb * 3));
     // the fused cooperative step where the device can place it and has it
     // to itself
-    a.coop_grid = P->ctx->shared_gpu ? 0 : arn_coop_grid(n, nb, m, &a.coop_resident);
+    arn_configure(m);
+    a.coop_grid = P->ctx->shared_gpu ? 0 : arn_coop_grid(n, nb, m, &a.coop_resident, &a.coop_redundant);
     a.bar = ws.arnBar.need(2);
     a.bar2 = a.bar + 1;
     a.err = ibuf + 4 * nb;
     a.gflag = ibuf + 4 * nb + 1;
     a.live = ibuf + 5 * nb + 1;
+    a.jstep = ibuf + 6 * nb + 1;
+    a.ran = ibuf + 7 * nb + 1;
     a.v32 = ws.arnV32.need((long long)nb * n);
-    a.n2 = scal + 4 * nb;
-    a.pcol = ws.arnP.need((long long)nb * 2 * (m + 2));
     double* r = ws.r.need((long long)nb * n);
     double* tmp = ws.tmp.need((long long)nb * n);
     double* npart = ws.n2.need((long long)nb * krylov_chunks(n) + nb);
@@ -758,8 +761,9 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
                             (long long)fuse_pre, (long long)direct, (long long)a.coop_grid,
                             (long long)a.coop_resident, (long long)forced_sched()})
             key.push_back((uintptr_t)v);
-        add(P); add(a.V); add(a.w); add(a.part); add(a.h1); add(a.hcol); add(a.H); add(a.cs); add(a.g); add(a.y);
-        add(scal); add(ibuf); add(a.ctr); add(a.bar); add(a.pcol); add(a.live_host); add(zpre); add(y32); add(y64);
+        key.push_back((uintptr_t)a.coop_redundant);
+        add(P); add(a.V); add(a.w); add(a.part); add(a.cf); add(a.hs); add(a.H); add(a.Hu); add(a.cs); add(a.g);
+        add(a.y); add(scal); add(ibuf); add(a.ctr); add(a.bar); add(a.live_host); add(zpre); add(y32); add(y64);
         add(a.v32); add(a.z32);
         add(ws.A.p); add(ws.B.p); add(ws.v32.p); add(ws.v64.p); add(P->pre.col); add(P->pre.val);
         if (cache->exec && cache->key == key) {
@@ -805,9 +809,9 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
             arn_init(a, r, npart, member, st);
             if (fuse_pre)
                 precond_apply(P->pre, a.V, (long long)(m + 1) * n, nullptr, 0, zpre, n, nb, member, st, a.v32, a.z32);
-            // the fused step applies the rotations of a column one step later:
-            // one more launch finishes the last column of the cycle
-            const int steps = std::min(m, iters_left) + (a.coop_grid > 0 ? 1 : 0);
+            // a column becomes final (and is rotated) one step later: one
+            // more launch finishes the last column of the cycle
+            const int steps = std::min(m, iters_left) + 1;
             int launched = 0;
             for (int it = 0; it < steps; ++it) {
                 if (use_graph) {

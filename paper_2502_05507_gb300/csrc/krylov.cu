@@ -205,53 +205,61 @@ __device__ __forceinline__ RowView shared_rows(const double* sV) {
     return {sV, SV_STRIDE, lane, lane + 32, 0, -1};
 }
 
-// w[r0 .. r0+ACH) -= V[0..cols) h over the chunk; 8 warps split the rows
-// (warp q takes rows q, q+8, ...; four rows per loop trip so that eight
-// loads are in flight), partial sums combined in warp order. Indices past
-// the end of the vector are clamped (their results are never stored).
-// Leaves the new chunk in s_w (zero past the end) and stores it into w, or,
-// when dst is set, stores scale times it into dst instead.
-__device__ __forceinline__ void chunk_update(const RowView& V, long long n, long long r0, int cols, const double* s_h,
-                                             double* w, double* s_acc, double* s_w, double* dst = nullptr,
-                                             double scale = 1.0, float* dst32 = nullptr) {
+// The update of step j on the chunk [r0, r0 + ACH): with
+// S_c = sum_{i<j} V[i] c[i] and S_b = sum_{i<j} V[i] b[i] (8 warps split the
+// rows, warp q taking rows q, q + 8, ..., four rows per loop trip so that
+// eight loads are in flight; partial sums added in warp order),
+//   q_j = (u_j - S_c) inv,   u_{j+1} = (w - S_b - q_j t) inv,
+// u_j read from row j of the view. q_j goes to row j of Vg and u_{j+1} to
+// row j + 1 (and its float32 copy to v32). Indices past the end of the
+// vector are clamped and their results not stored. s_acc: 2 x 8 x ACH.
+__device__ __forceinline__ void chunk_next(const RowView& V, long long n, long long r0, int j, const double* s_c,
+                                           const double* s_b, double t, double inv, const double* w, double* Vg,
+                                           float* v32, double* s_acc) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double a0 = 0.0, a1 = 0.0;
+    double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
     int i = warp;
-    for (; i + 24 < cols; i += 32) {
+    for (; i + 24 < j; i += 32) {
         const double* v0 = V.base + (long long)i * V.rs;
         const double* v1 = v0 + 8 * V.rs;
         const double* v2 = v0 + 16 * V.rs;
         const double* v3 = v0 + 24 * V.rs;
         const double x0 = v0[V.oa], y0 = v0[V.ob], x1 = v1[V.oa], y1 = v1[V.ob];
         const double x2 = v2[V.oa], y2 = v2[V.ob], x3 = v3[V.oa], y3 = v3[V.ob];
-        a0 += x0 * s_h[i] + x1 * s_h[i + 8] + x2 * s_h[i + 16] + x3 * s_h[i + 24];
-        a1 += y0 * s_h[i] + y1 * s_h[i + 8] + y2 * s_h[i + 16] + y3 * s_h[i + 24];
+        a0 += x0 * s_c[i] + x1 * s_c[i + 8] + x2 * s_c[i + 16] + x3 * s_c[i + 24];
+        a1 += y0 * s_c[i] + y1 * s_c[i + 8] + y2 * s_c[i + 16] + y3 * s_c[i + 24];
+        b0 += x0 * s_b[i] + x1 * s_b[i + 8] + x2 * s_b[i + 16] + x3 * s_b[i + 24];
+        b1 += y0 * s_b[i] + y1 * s_b[i + 8] + y2 * s_b[i + 16] + y3 * s_b[i + 24];
     }
-    for (; i < cols; i += 8) {
+    for (; i < j; i += 8) {
         const double* v = V.base + (long long)i * V.rs;
-        a0 += v[V.oa] * s_h[i];
-        a1 += v[V.ob] * s_h[i];
+        const double x = v[V.oa], y = v[V.ob];
+        a0 += x * s_c[i];
+        a1 += y * s_c[i];
+        b0 += x * s_b[i];
+        b1 += y * s_b[i];
     }
     s_acc[warp * ACH + lane] = a0;
     s_acc[warp * ACH + lane + 32] = a1;
+    s_acc[(8 + warp) * ACH + lane] = b0;
+    s_acc[(8 + warp) * ACH + lane + 32] = b1;
     __syncthreads();
     if (threadIdx.x < ACH) {
-        const long long r = r0 + threadIdx.x;
-        double sub = 0.0;
+        const int e = threadIdx.x;
+        const long long r = r0 + e;
+        double sc = 0.0, sb = 0.0;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) sub += s_acc[q * ACH + threadIdx.x];
-        double val = 0.0;
-        if (r < n) {
-            val = w[r] - sub;
-            if (dst) {
-                const double y = val * scale;
-                dst[r] = y;
-                if (dst32) dst32[r] = (float)y;
-            } else {
-                w[r] = val;
-            }
+        for (int q = 0; q < 8; ++q) {
+            sc += s_acc[q * ACH + e];
+            sb += s_acc[(8 + q) * ACH + e];
         }
-        s_w[threadIdx.x] = val;
+        if (r < n) {
+            const double qv = (V.at(j, e) - sc) * inv;
+            const double un = (w[r] - sb - qv * t) * inv;
+            Vg[(long long)j * n + r] = qv;
+            Vg[(long long)(j + 1) * n + r] = un;
+            if (v32) v32[r] = (float)un;
+        }
     }
     __syncthreads();
 }
@@ -355,156 +363,221 @@ __device__ __forceinline__ void givens_apply(double* s_col, const double* s_cs, 
     g[j] = cj * g[j];
 }
 
-// pass 1: w = A V[j] by the closure gather of the potential v (the same
-// expression as closure_gather), then h1 = V^T w over rows i <= j
-template <typename VT>
-__global__ void __launch_bounds__(256) k_arn_gather_dots(Arnoldi a) {
-    __shared__ double s_w[ACH];
-    __shared__ double s_red8[8 * 32];
-    __shared__ int s_last;
-    const int b = blockIdx.y;
-    if (!a.flag[b]) return;
-    const int cols = a.j[b] + 1;
-    const int c = blockIdx.x;
-    const long long r0 = (long long)c * ACH;
-    double* w = a.w + (long long)b * a.n;
-    if (threadIdx.x < ACH) {
-        const long long r = r0 + threadIdx.x;
-        double val = 0.0;
-        if (r < a.n) {
-            const VT* vb = static_cast<const VT*>(a.v) + b * a.v_stride;
-            const double tr = a.t[r];
-            val = tr * (double)vb[a.gm[r]] + (1.0 - tr) * (double)vb[a.partner[r]];
-            w[r] = val;
-        }
-        s_w[threadIdx.x] = val;
+// ------------------------------------------------ the step's coefficients
+// Rows [0, j] of the two sets of partial sums reduced into cf (Q^T u with
+// u.u last, then from cf + m + 1 Q^T w with u.w last, when ran), one warp
+// per row in the order of reduce_rows; then r and t by two warps with
+// lane-strided sums and the fixed shuffle tree. Every CTA that needs them
+// (the rotation CTA, a chunk CTA in the redundant mode, the last block of
+// the three-kernel path) runs this same code, so all get the same bits.
+__device__ __forceinline__ void step_coeffs(const Arnoldi& a, int b, int j, bool ran, double* cf, double* s_rt) {
+    const int m = a.m, nch = a.nchunk;
+    const double* part = a.part + (long long)b * 2 * (m + 1) * nch;
+    reduce_rows(part, nch, j + 1, cf, nullptr, nullptr);
+    if (ran) reduce_rows(part + (long long)(m + 1) * nch, nch, j + 1, cf + m + 1, nullptr, nullptr);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp == 0) {   // r^2 = u.u - |c|^2 (Pythagoras: u_j is projected once, c = O(eps) |u_j|)
+        double acc = 0.0;
+        for (int i = lane; i < j; i += 32) acc += cf[i] * cf[i];
+        acc = warp_sum(acc);
+        if (lane == 0) s_rt[0] = sqrt(fmax(cf[j] - acc, 0.0));
+    } else if (warp == 1 && ran) {   // t r = u.w - c.b
+        double acc = 0.0;
+        for (int i = lane; i < j; i += 32) acc += cf[i] * cf[m + 1 + i];
+        acc = warp_sum(acc);
+        if (lane == 0) s_rt[1] = cf[m + 1 + j] - acc;
     }
     __syncthreads();
-    double* part = a.part + (long long)b * (a.m + 2) * a.nchunk;
-    const double* Vb = a.V + (long long)b * (a.m + 1) * a.n;
-    chunk_dots(global_rows(Vb, a.n, r0), cols, s_w, part, a.nchunk, c, s_red8);
-    if (last_block(a.ctr + 3 * b + 0, gridDim.x, &s_last)) {
-        reduce_rows(part, a.nchunk, cols, a.h1 + (long long)b * (a.m + 1), nullptr, nullptr);
-        if (threadIdx.x == 0) a.ctr[3 * b + 0] = 0;
+    if (threadIdx.x == 0) {
+        const double r = s_rt[0];
+        s_rt[2] = r > 0.0 ? 1.0 / r : 0.0;                   // inv
+        s_rt[3] = (ran && r > 0.0) ? s_rt[1] / r : 0.0;      // t
     }
+    __syncthreads();
 }
 
-// pass 2: w -= V h1, then h2 = V^T w and ||w||^2. The last block forms
-// hcol = h1 + h2 and the new subdiagonal entry ||w - V h2|| by the
-// Pythagorean identity ||w||^2 - ||h2||^2 (V orthonormal), applies the
-// Givens rotations (staged in shared memory), updates the residual
-// estimate and the flag, sets inv = 1 / ||w - V h2|| and advances j.
-__global__ void __launch_bounds__(256) k_arn_update_dots(Arnoldi a) {
-    extern __shared__ double s_dyn[];
+// The Hessenberg part of step j for right-hand side b (one CTA; cf and
+// s_rt from step_coeffs): column j - 1 (pending) becomes final, hs + c with
+// subdiagonal r, and is rotated (residual estimate, decision to go on);
+// column j (when ran) is stored pending as h = ([b; t] - H c) / r. Then the
+// flags and j advance. s_col: m + 2 doubles, s_cs / s_sn: m each.
+__device__ __forceinline__ void step_hessenberg(const Arnoldi& a, int b, int j, bool ran, bool pend, const double* cf,
+                                                const double* s_rt, double* s_col, double* s_cs, double* s_sn) {
     const int m = a.m;
-    double* s_h = s_dyn;                 // m + 1: h1
-    double* s_col = s_dyn + (m + 1);     // m + 2: the new Hessenberg column
-    double* s_cs = s_col + (m + 2);      // m
-    double* s_sn = s_cs + m;             // m
-    __shared__ double s_acc[8 * ACH];
-    __shared__ double s_w[ACH];
-    __shared__ double s_n2;
-    __shared__ int s_last;
-    const int b = blockIdx.y;
-    if (!a.flag[b]) return;
-    const int j = a.j[b];
-    const int cols = j + 1;
-    const int c = blockIdx.x;
-    const long long r0 = (long long)c * ACH;
-    double* h1 = a.h1 + (long long)b * (m + 1);
-    for (int i = threadIdx.x; i < cols; i += blockDim.x) s_h[i] = h1[i];
-    __syncthreads();
-    const double* Vb = a.V + (long long)b * (m + 1) * a.n;
-    chunk_update(global_rows(Vb, a.n, r0), a.n, r0, cols, s_h, a.w + (long long)b * a.n, s_acc, s_w);
-    double* part = a.part + (long long)b * (m + 2) * a.nchunk;
-    chunk_dots(global_rows(Vb, a.n, r0), cols, s_w, part, a.nchunk, c, s_acc);
-    if (threadIdx.x >= 224) {   // the last warp: ||w||^2 over the chunk
-        const int l = threadIdx.x - 224;
-        double acc = s_w[l] * s_w[l] + s_w[l + 32] * s_w[l + 32];
-        acc = warp_sum(acc);
-        if (l == 0) part[(long long)(m + 1) * a.nchunk + c] = acc;
-    }
-    if (last_block(a.ctr + 3 * b + 1, gridDim.x, &s_last)) {
-        double* hc = a.hcol + (long long)b * (m + 1);
-        // hcol = h1 + h2 (h1 still in s_h), then h1 <- h2
-        reduce_rows(part, a.nchunk, cols, hc, h1, s_h);
-        if (threadIdx.x < 32) {
-            double acc = 0.0;
-            for (int q = threadIdx.x; q < a.nchunk; q += 32) acc += __ldcg(part + (long long)(m + 1) * a.nchunk + q);
-            acc = warp_sum(acc);
-            if (threadIdx.x == 0) s_n2 = acc;
+    const double r = s_rt[0];
+    double* hs = a.hs + (long long)b * (m + 1);
+    double* Hu = a.Hu + (long long)b * m * (m + 1);
+    if (pend) {   // column j - 1: rows 0 .. j
+        for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+            const double x = i < j ? hs[i] + cf[i] : r;
+            s_col[i] = x;
+            Hu[(long long)(j - 1) * (m + 1) + i] = x;
         }
-        __syncthreads();
-        double* cs = a.cs + (long long)b * m;
-        double* sn = a.sn + (long long)b * m;
-        for (int i = threadIdx.x; i <= j; i += blockDim.x) s_col[i] = __ldcg(hc + i);
-        for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    }
+    __syncthreads();   // Hu complete and hs read before hs is overwritten
+    if (ran) {         // column j: rows 0 .. j, (H c)_i over the final columns k < j
+        const double inv = s_rt[2], t = s_rt[3];
+        for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+            double hc = 0.0;
+            for (int k = (i > 0 ? i - 1 : 0); k < j; ++k) hc += Hu[(long long)k * (m + 1) + i] * cf[k];
+            hs[i] = ((i < j ? cf[m + 1 + i] : t) - hc) * inv;
+        }
+    }
+    double* cs = a.cs + (long long)b * m;
+    double* sn = a.sn + (long long)b * m;
+    if (pend) {
+        for (int i = threadIdx.x; i < j - 1; i += blockDim.x) {
             s_cs[i] = cs[i];
             s_sn[i] = sn[i];
         }
-        if (threadIdx.x < 32) {   // ||h2||^2 in a fixed order
-            double acc = 0.0;
-            for (int i = threadIdx.x; i <= j; i += 32) {
-                const double x = __ldcg(h1 + i);
-                acc += x * x;
-            }
-            acc = warp_sum(acc);
-            if (threadIdx.x == 0) s_n2 = fmax(s_n2 - acc, 0.0);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const double hn = sqrt(s_n2);
-            double* g = a.g + (long long)b * (m + 1);
-            s_col[j + 1] = hn;
-            givens_apply(s_col, s_cs, s_sn, j, cs, sn, g);
-            const double e = fabs(g[j + 1]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bool converged = false;
+        if (pend) {
+            const int c = j - 1;
+            givens_apply(s_col, s_cs, s_sn, c, cs, sn, a.g + (long long)b * (m + 1));
+            const double e = fabs(a.g[(long long)b * (m + 1) + c + 1]);
             a.est[b] = e;
-            a.ncols[b] = j + 1;
-            a.inv[b] = hn > 0.0 ? 1.0 / hn : 0.0;
-            a.flag[b] = (e > a.target[b] && hn > 0.0 && j + 1 < m) ? 1 : 0;
-            a.live[b] = a.flag[b];
-            if (a.live_host) {
-                a.live_host[b] = a.flag[b];
-                __threadfence_system();
-            }
-            a.j[b] = j + 1;   // every block of this RHS has read j already
-            a.ctr[3 * b + 1] = 0;
+            a.ncols[b] = c + 1;
+            converged = !(e > a.target[b] && r > 0.0);
         }
-        __syncthreads();
-        double* col = a.H + ((long long)b * m + j) * (m + 1);
-        for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) col[i] = s_col[i];
+        const int gf = (ran && !converged) ? 1 : 0;
+        const int fl = (gf && j + 1 < m) ? 1 : 0;
+        a.gflag[b] = gf;
+        a.flag[b] = fl;
+        a.live[b] = gf | fl;
+        if (a.live_host) {
+            a.live_host[b] = gf | fl;
+            __threadfence_system();
+        }
+        a.j[b] = ran ? j + 1 : j;
+    }
+    __syncthreads();
+    if (pend) {
+        double* col = a.H + ((long long)b * m + (j - 1)) * (m + 1);
+        for (int i = threadIdx.x; i <= j; i += blockDim.x) col[i] = s_col[i];
     }
 }
 
-// pass 3: V[j] = (w - V h2) / ||w - V h2|| with j already advanced (w itself
-// is not written back: the next step's gather replaces it)
-__global__ void __launch_bounds__(256) k_arn_update_next(Arnoldi a) {
+// the coefficients the chunk update reads: c = cf[0..j), b = cf[m+1 ..
+// m+1+j), inv, t
+__device__ __forceinline__ void publish_coeffs(const Arnoldi& a, int b, int j, const double* cf, const double* s_rt) {
+    const int m = a.m;
+    double* out = a.cf + (long long)b * 2 * (m + 1);
+    for (int i = threadIdx.x; i < j; i += blockDim.x) {
+        out[i] = cf[i];
+        out[m + 1 + i] = cf[m + 1 + i];
+    }
+    if (threadIdx.x == 0) {
+        a.inv[b] = s_rt[2];
+        a.tco[b] = s_rt[3];
+    }
+}
+
+// w = the closure gather of the potential (eq. [double_bae]) on the chunk
+// (into global w and s_w, zero past the end), and s_u = the chunk of u_j
+template <typename VT>
+__device__ __forceinline__ void gather_chunk(const Arnoldi& a, int b, long long r0, bool ran, const double* uj,
+                                             double* s_w, double* s_u) {
+    if (threadIdx.x < ACH) {
+        const long long r = r0 + threadIdx.x;
+        double val = 0.0, uv = 0.0;
+        if (r < a.n) {
+            uv = uj[r];
+            if (ran) {
+                const VT* vb = static_cast<const VT*>(a.v) + b * a.v_stride;
+                const double tr = a.t[r];
+                val = tr * (double)vb[a.gm[r]] + (1.0 - tr) * (double)vb[a.partner[r]];
+                a.w[(long long)b * a.n + r] = val;
+            }
+        }
+        s_w[threadIdx.x] = val;
+        s_u[threadIdx.x] = uv;
+    }
+}
+
+// --------------------------------------------------- three-kernel step
+// kernel 1: gather w (when the RHS computes a column), partial sums of
+// Q^T u and u.u (and of Q^T w and u.w); the last CTA of each right-hand side
+// reduces them and does the Hessenberg part; the update kernel reads the
+// published coefficients and the step's j and flag.
+template <typename VT>
+__global__ void __launch_bounds__(256) k_arn_dots(Arnoldi a) {
     extern __shared__ double s_dyn[];
-    double* s_h = s_dyn;
-    __shared__ double s_acc[8 * ACH];
-    __shared__ double s_w[ACH];
+    const int m = a.m;
+    double* s_cf = s_dyn;                     // 2 (m + 1)
+    double* s_col = s_cf + 2 * (m + 1);       // m + 2
+    double* s_cs = s_col + (m + 2);           // m
+    double* s_sn = s_cs + m;                  // m
+    __shared__ double s_w[ACH], s_u[ACH];
+    __shared__ double s_red8[8 * 32];
+    __shared__ double s_rt[4];
+    __shared__ int s_last;
     const int b = blockIdx.y;
-    if (!a.flag[b]) return;
+    const bool ran = a.flag[b] != 0, pend = a.gflag[b] != 0;
+    if (!ran && !pend) {   // no update for this right-hand side in this step
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.ran[b] = 0;
+        return;
+    }
     const int j = a.j[b];
-    const int cols = j;   // rows 0 .. j-1: the basis before this step's vector
     const int c = blockIdx.x;
     const long long r0 = (long long)c * ACH;
-    const double* h2 = a.h1 + (long long)b * (a.m + 1);
-    for (int i = threadIdx.x; i < cols; i += blockDim.x) s_h[i] = h2[i];
+    const double* Vb = a.V + (long long)b * (m + 1) * a.n;
+    gather_chunk<VT>(a, b, r0, ran, Vb + (long long)j * a.n, s_w, s_u);
     __syncthreads();
-    double* Vb = a.V + (long long)b * (a.m + 1) * a.n;
-    chunk_update(global_rows(Vb, a.n, r0), a.n, r0, cols, s_h, a.w + (long long)b * a.n, s_acc, s_w,
-                 Vb + (long long)j * a.n, a.inv[b], a.v32 ? a.v32 + (long long)b * a.n : nullptr);
+    double* part = a.part + (long long)b * 2 * (m + 1) * a.nchunk;
+    const RowView V = global_rows(Vb, a.n, r0);
+    chunk_dots(V, j + 1, s_u, part, a.nchunk, c, s_red8);
+    if (ran) chunk_dots(V, j + 1, s_w, part + (long long)(m + 1) * a.nchunk, a.nchunk, c, s_red8);
+    if (last_block(a.ctr + 3 * b + 0, gridDim.x, &s_last)) {
+        step_coeffs(a, b, j, ran, s_cf, s_rt);
+        if (ran) publish_coeffs(a, b, j, s_cf, s_rt);
+        if (threadIdx.x == 0) {
+            a.jstep[b] = j;
+            a.ran[b] = ran ? 1 : 0;
+            a.ctr[3 * b + 0] = 0;
+        }
+        step_hessenberg(a, b, j, ran, pend, s_cf, s_rt, s_col, s_cs, s_sn);
+    }
+}
+
+// kernel 2: q_j into row j, u_{j+1} into row j + 1
+__global__ void __launch_bounds__(256) k_arn_next(Arnoldi a) {
+    extern __shared__ double s_dyn[];
+    double* s_c = s_dyn;              // m + 1
+    double* s_b = s_dyn + (a.m + 1);  // m + 1
+    __shared__ double s_acc[2 * 8 * ACH];
+    const int b = blockIdx.y;
+    if (!a.ran[b]) return;
+    const int j = a.jstep[b];
+    const int m = a.m;
+    const double* cf = a.cf + (long long)b * 2 * (m + 1);
+    for (int i = threadIdx.x; i < j; i += blockDim.x) {
+        s_c[i] = cf[i];
+        s_b[i] = cf[m + 1 + i];
+    }
+    __syncthreads();
+    const long long r0 = (long long)blockIdx.x * ACH;
+    double* Vb = a.V + (long long)b * (m + 1) * a.n;
+    chunk_next(global_rows(Vb, a.n, r0), a.n, r0, j, s_c, s_b, a.tco[b], a.inv[b], a.w + (long long)b * a.n, Vb,
+               a.v32 ? a.v32 + (long long)b * a.n : nullptr, s_acc);
 }
 
 // ------------------------------------------------ fused cooperative step
-// The three passes above and their last-CTA reductions as one cooperative
-// launch: the CTAs (all resident at once) meet at four grid barriers, and
-// the reductions are spread over all warps instead of one CTA. The sums use
-// the same partition and order as the three-kernel step, so both give
-// bit-identical results.
+// The two kernels above as one cooperative launch: the chunk CTAs (all
+// resident at once) form the partial sums, meet the rotation CTAs (one per
+// right-hand side) at a grid barrier, and, once the coefficients are
+// known, write q_j and u_{j+1}; the rotation CTAs reduce the coefficients,
+// publish them (a second grid barrier the chunk CTAs wait at) and then
+// finish and rotate the Hessenberg column while the chunk CTAs update. In
+// the redundant mode (one item per chunk CTA) every chunk CTA reduces its
+// right-hand side's coefficients itself and the second barrier goes. With
+// the preconditioner, z = M^{-1} u_{j+1} follows one more barrier. The
+// sums use the same partition and order as the two-kernel step, so both
+// give bit-identical results.
 constexpr int COOP_MAX_NB = 64;
-constexpr long long BAR_SPIN_LIMIT = 1LL << 22;   // about half a second of waiting
 
 // All CTAs of the grid wait here until every CTA has arrived. The counter
 // only grows (by G per barrier), so the k-th barrier of a CTA completes when
@@ -541,41 +614,19 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* ctr, unsigned l
     return s_ok != 0;
 }
 
-// out[b][i] = sum over chunks of part[b][i][*] for rows i <= j_b of the
-// iterating right-hand sides, one warp per row, in the order of reduce_rows;
-// with add, also out2 = out and out = add + out. Row m + 1 (the squared
-// norm partials) goes to n2[b] when n2 is set.
-__device__ __forceinline__ void coop_reduce(const Arnoldi& a, int nctas, const int* s_j, const int* s_flag,
-                                            double* out, double* out2, const double* add, double* n2) {
-    const int lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int nw = nctas * (blockDim.x >> 5);
-    const int rows = a.m + 2;
-    for (int item = gw; item < a.nb * rows; item += nw) {
-        const int b = item / rows, i = item % rows;
-        if (!s_flag[b]) continue;
-        const bool norm = i == a.m + 1;
-        if (norm ? !n2 : i > s_j[b]) continue;
-        const double* p = a.part + ((long long)b * (a.m + 2) + i) * a.nchunk;
-        double acc = 0.0;
-        for (int c = lane; c < a.nchunk; c += 32) acc += __ldcg(p + c);
-        acc = warp_sum(acc);
-        if (lane == 0) {
-            if (norm) {
-                n2[b] = acc;
-            } else {
-                const long long o = (long long)b * (a.m + 1) + i;
-                if (add) out[o] = __ldcg(add + o) + acc; else out[o] = acc;
-                if (out2) out2[o] = acc;
-            }
-        }
+// arrival without waiting (the CTA's writes made visible first)
+__device__ __forceinline__ void grid_arrive(unsigned long long* ctr) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(ctr, 1ull);
     }
 }
 
 // SV: every CTA holds exactly one (RHS, chunk) item and keeps its chunk of
-// the basis rows V[0..j] in shared memory (copied asynchronously while the
-// gather runs), so the three projections read it from there; the sums are
-// the same expressions in the same order as with global rows.
+// the rows V[0..j] in shared memory (copied asynchronously while the
+// gather runs), so both passes read it from there; the sums are the same
+// expressions in the same order as with global rows.
 // Compiled for three resident CTAs per SM (at most 85 registers; it needs
 // 80 without spilling): left free, the compiler takes 91 and only two CTAs
 // fit, which made the 64-right-hand-side step ~40% slower.
@@ -583,75 +634,43 @@ template <typename VT, bool SV>
 __global__ void __launch_bounds__(256, 3) k_arn_step_coop(Arnoldi a) {
     extern __shared__ double s_dyn[];
     const int m = a.m;
-    double* s_h = s_dyn;                 // m + 1
-    double* s_col = s_dyn + (m + 1);     // m + 2
-    double* s_cs = s_col + (m + 2);      // m
-    double* s_sn = s_cs + m;             // m
-    double* s_V = s_sn + m;              // SV: (m + 1) x SV_STRIDE
-    __shared__ double s_acc[8 * ACH];
-    __shared__ double s_w[ACH];
-    __shared__ double s_red[2];
-    __shared__ int s_j[COOP_MAX_NB], s_flag[COOP_MAX_NB];
+    double* s_cf = s_dyn;                     // 2 (m + 1)
+    double* s_col = s_cf + 2 * (m + 1);       // m + 2
+    double* s_cs = s_col + (m + 2);           // m
+    double* s_sn = s_cs + m;                  // m
+    double* s_V = s_sn + m;                   // SV: (m + 1) x SV_STRIDE
+    __shared__ double s_acc[2 * 8 * ACH];
+    __shared__ double s_w[ACH], s_u[ACH];
+    __shared__ double s_rt[4];
+    __shared__ int s_j[COOP_MAX_NB], s_flag[COOP_MAX_NB], s_pend[COOP_MAX_NB];
     const unsigned long long G = gridDim.x;
-    const int NI = (int)gridDim.x - a.nb;   // chunk CTAs; the last nb CTAs do the rotations
+    const int NI = (int)gridDim.x - a.nb;   // chunk CTAs; the last nb CTAs reduce and rotate
     const int items = a.nb * a.nchunk;
     // step index and flags as they were at the start of the step (the
-    // rotation CTAs advance them at the end)
+    // rotation CTAs advance them)
     for (int b = threadIdx.x; b < a.nb; b += blockDim.x) {
         s_j[b] = a.j[b];
         s_flag[b] = a.flag[b];
+        s_pend[b] = a.gflag[b];
     }
     __syncthreads();
 
     if ((int)blockIdx.x >= NI) {
-        // ---- rotations of the column stored by the previous step
+        // ---- the coefficients and the Hessenberg column of one right-hand side
         const int b = (int)blockIdx.x - NI;
         const int j = s_j[b];
-        const bool pending = a.gflag[b] != 0;   // column j - 1 waits in pcol[b][(j - 1) % 2]
-        const int c = j - 1;
-        double* cs = a.cs + (long long)b * m;
-        double* sn = a.sn + (long long)b * m;
-        if (pending) {
-            const double* pc = a.pcol + ((long long)b * 2 + (c & 1)) * (m + 2);
-            for (int i = threadIdx.x; i <= c + 1; i += blockDim.x) s_col[i] = pc[i];
-            for (int i = threadIdx.x; i < c; i += blockDim.x) {
-                s_cs[i] = cs[i];
-                s_sn[i] = sn[i];
-            }
+        const bool ran = s_flag[b] != 0, pend = s_pend[b] != 0;
+        if (!grid_barrier(a.bar, G + a.bar_extra, a.err, a.err_host, a.spin_limit)) return;   // partial sums complete
+        if (ran || pend) {
+            step_coeffs(a, b, j, ran, s_cf, s_rt);
+            if (ran && !a.coop_redundant) publish_coeffs(a, b, j, s_cf, s_rt);
         }
-        // every chunk CTA has read j and the flags once all CTAs are here
-        if (!grid_barrier(a.bar, G + a.bar_extra, a.err, a.err_host, a.spin_limit)) return;
-        if (threadIdx.x == 0) {
-            bool converged = false;
-            if (pending) {
-                const double hn = s_col[c + 1];
-                givens_apply(s_col, s_cs, s_sn, c, cs, sn, a.g + (long long)b * (m + 1));
-                const double e = fabs(a.g[(long long)b * (m + 1) + c + 1]);
-                a.est[b] = e;
-                a.ncols[b] = c + 1;
-                converged = !(e > a.target[b] && hn > 0.0);
-            }
-            const bool ran = s_flag[b] != 0;   // the chunk CTAs computed column j in this step
-            const int gf = (ran && !converged) ? 1 : 0;
-            const int fl = (ran && !converged && j + 1 < m) ? 1 : 0;
-            a.gflag[b] = gf;
-            a.flag[b] = fl;
-            a.live[b] = gf | fl;
-            if (a.live_host) {
-                a.live_host[b] = gf | fl;
-                __threadfence_system();
-            }
-            a.j[b] = ran ? j + 1 : j;
-        }
-        __syncthreads();
-        if (pending) {
-            double* col = a.H + ((long long)b * m + c) * (m + 1);
-            for (int i = threadIdx.x; i <= c + 1; i += blockDim.x) col[i] = s_col[i];
-        }
-        return;   // takes part in the first barrier only
+        if (!a.coop_redundant) grid_arrive(a.bar);   // the chunk CTAs may update
+        if (ran || pend) step_hessenberg(a, b, j, ran, pend, s_cf, s_rt, s_col, s_cs, s_sn);
+        return;
     }
 
-    if (SV && blockIdx.x < items && s_flag[blockIdx.x / a.nchunk]) {
+    if (SV && blockIdx.x < items && (s_flag[blockIdx.x / a.nchunk] || s_pend[blockIdx.x / a.nchunk])) {
         // the chunk of V[0..j] into shared memory, clamped at the vector end
         const int b = blockIdx.x / a.nchunk;
         const long long r0 = (long long)(blockIdx.x % a.nchunk) * ACH;
@@ -665,103 +684,60 @@ __global__ void __launch_bounds__(256, 3) k_arn_step_coop(Arnoldi a) {
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     }
-    // phase 1: w = gather of v, partial dots against V[0..j]
+    // phase 1: w = gather of v, partial sums against V[0..j] of u_j and w
     for (int item = blockIdx.x; item < items; item += NI) {
         const int b = item / a.nchunk, c = item % a.nchunk;
-        if (!s_flag[b]) continue;
+        const bool ran = s_flag[b] != 0;
+        if (!ran && !s_pend[b]) continue;
+        const int j = s_j[b];
         const long long r0 = (long long)c * ACH;
-        double* w = a.w + (long long)b * a.n;
-        if (threadIdx.x < ACH) {
-            const long long r = r0 + threadIdx.x;
-            double val = 0.0;
-            if (r < a.n) {
-                const VT* vb = static_cast<const VT*>(a.v) + b * a.v_stride;
-                const double tr = a.t[r];
-                val = tr * (double)vb[a.gm[r]] + (1.0 - tr) * (double)vb[a.partner[r]];
-                w[r] = val;
-            }
-            s_w[threadIdx.x] = val;
-        }
+        const double* Vb = a.V + (long long)b * (m + 1) * a.n;
+        gather_chunk<VT>(a, b, r0, ran, Vb + (long long)j * a.n, s_w, s_u);
         if (SV) asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         __syncthreads();
-        const RowView V = SV ? shared_rows(s_V) : global_rows(a.V + (long long)b * (m + 1) * a.n, a.n, r0);
-        chunk_dots(V, s_j[b] + 1, s_w, a.part + (long long)b * (m + 2) * a.nchunk, a.nchunk, c, s_acc);
+        const RowView V = SV ? shared_rows(s_V) : global_rows(Vb, a.n, r0);
+        double* part = a.part + (long long)b * 2 * (m + 1) * a.nchunk;
+        chunk_dots(V, j + 1, s_u, part, a.nchunk, c, s_acc);
+        if (ran) chunk_dots(V, j + 1, s_w, part + (long long)(m + 1) * a.nchunk, a.nchunk, c, s_acc);
         __syncthreads();
     }
     if (!grid_barrier(a.bar, G + a.bar_extra, a.err, a.err_host, a.spin_limit)) return;   // all G CTAs
-    const unsigned long long GI = (unsigned long long)NI;
-    // phase 2: h1
-    coop_reduce(a, NI, s_j, s_flag, a.h1, nullptr, nullptr, nullptr);
-    if (!grid_barrier(a.bar2, GI + a.bar_extra, a.err, a.err_host, a.spin_limit)) return;   // chunk CTAs only
-    // phase 3: w -= V h1, partial dots for h2 and ||w||^2
+    if (!a.coop_redundant && !grid_barrier(a.bar, G + a.bar_extra, a.err, a.err_host, a.spin_limit))
+        return;   // the rotation CTAs have published the coefficients
+    // phase 2: q_j into row j, u_{j+1} into row j + 1
     for (int item = blockIdx.x; item < items; item += NI) {
         const int b = item / a.nchunk, c = item % a.nchunk;
         if (!s_flag[b]) continue;
-        const int cols = s_j[b] + 1;
-        const long long r0 = (long long)c * ACH;
-        const double* h1 = a.h1 + (long long)b * (m + 1);
-        for (int i = threadIdx.x; i < cols; i += blockDim.x) s_h[i] = __ldcg(h1 + i);
-        __syncthreads();
-        const double* Vb = a.V + (long long)b * (m + 1) * a.n;
-        double* part = a.part + (long long)b * (m + 2) * a.nchunk;
-        const RowView V = SV ? shared_rows(s_V) : global_rows(Vb, a.n, r0);
-        chunk_update(V, a.n, r0, cols, s_h, a.w + (long long)b * a.n, s_acc, s_w);
-        chunk_dots(V, cols, s_w, part, a.nchunk, c, s_acc);
-        if (threadIdx.x >= 224) {
-            const int l = threadIdx.x - 224;
-            double acc = s_w[l] * s_w[l] + s_w[l + 32] * s_w[l + 32];
-            acc = warp_sum(acc);
-            if (l == 0) part[(long long)(m + 1) * a.nchunk + c] = acc;
-        }
-        __syncthreads();
-    }
-    if (!grid_barrier(a.bar2, GI + a.bar_extra, a.err, a.err_host, a.spin_limit)) return;
-    // phase 4: h2 (into h1), hcol = h1 + h2, ||w||^2
-    coop_reduce(a, NI, s_j, s_flag, a.hcol, a.h1, a.h1, a.n2);
-    if (!grid_barrier(a.bar2, GI + a.bar_extra, a.err, a.err_host, a.spin_limit)) return;
-
-    // phase 5: hn = sqrt(||w||^2 - ||h2||^2) (every CTA, same order), then
-    // V[j+1] = (w - V h2) / hn; the CTA of chunk 0 stores the column
-    // (hcol, then hn) for the rotations of the next step
-    for (int item = blockIdx.x; item < items; item += NI) {
-        const int b = item / a.nchunk, c = item % a.nchunk;
-        if (!s_flag[b]) continue;
-        const int j = s_j[b], cols = j + 1;
-        const double* h2 = a.h1 + (long long)b * (m + 1);
-        for (int i = threadIdx.x; i < cols; i += blockDim.x) s_h[i] = __ldcg(h2 + i);
-        if (threadIdx.x < 32) {
-            double acc = 0.0;
-            for (int i = threadIdx.x; i <= j; i += 32) {
-                const double x = __ldcg(h2 + i);
-                acc += x * x;
+        const int j = s_j[b];
+        double* s_c = s_cf;
+        double* s_b = s_cf + m + 1;
+        double t, inv;
+        if (a.coop_redundant) {   // the same reduction as the rotation CTA
+            step_coeffs(a, b, j, true, s_cf, s_rt);
+            t = s_rt[3];
+            inv = s_rt[2];
+        } else {
+            const double* cf = a.cf + (long long)b * 2 * (m + 1);
+            for (int i = threadIdx.x; i < j; i += blockDim.x) {
+                s_c[i] = __ldcg(cf + i);
+                s_b[i] = __ldcg(cf + m + 1 + i);
             }
-            acc = warp_sum(acc);
-            if (threadIdx.x == 0) {
-                const double hn = sqrt(fmax(__ldcg(a.n2 + b) - acc, 0.0));
-                s_red[0] = hn;
-                s_red[1] = hn > 0.0 ? 1.0 / hn : 0.0;
-            }
-        }
-        __syncthreads();
-        if (c == 0) {
-            double* pc = a.pcol + ((long long)b * 2 + (j & 1)) * (m + 2);
-            const double* hc = a.hcol + (long long)b * (m + 1);
-            for (int i = threadIdx.x; i <= j; i += blockDim.x) pc[i] = __ldcg(hc + i);
-            if (threadIdx.x == 0) pc[j + 1] = s_red[0];
+            t = __ldcg(a.tco + b);
+            inv = __ldcg(a.inv + b);
+            __syncthreads();
         }
         double* Vb = a.V + (long long)b * (m + 1) * a.n;
         const long long r0 = (long long)c * ACH;
         const RowView V = SV ? shared_rows(s_V) : global_rows(Vb, a.n, r0);
-        chunk_update(V, a.n, r0, cols, s_h, a.w + (long long)b * a.n, s_acc, s_w, Vb + (long long)(j + 1) * a.n,
-                     s_red[1], a.v32 ? a.v32 + (long long)b * a.n : nullptr);
-        __syncthreads();
+        chunk_next(V, a.n, r0, j, s_c, s_b, t, inv, a.w + (long long)b * a.n, Vb,
+                   a.v32 ? a.v32 + (long long)b * a.n : nullptr, s_acc);
     }
     if (!a.pre_col) return;
-    // phase 6: z = M^{-1} V[j+1] on the chunk's rows: warp w takes rows
+    // phase 3: z = M^{-1} u_{j+1} on the chunk's rows: warp w takes rows
     // 8 w .. 8 w + 7 of each item, lane q slot q, the same float32 products
     // and shuffle tree as the separate preconditioner kernel. The slots of the
     // CTA's first item are loaded before the barrier (they do not depend on
-    // V[j+1]); V[j+1] is read through L2 (other CTAs wrote it).
+    // u_{j+1}); u_{j+1} is read through L2 (other CTAs wrote it).
     constexpr int RW = ACH / 8;   // rows per warp (8 warps)
     static_assert(ACH % 8 == 0, "rows per warp");
     const int lane = threadIdx.x & 31, wr = (threadIdx.x >> 5) * RW;
@@ -777,12 +753,13 @@ __global__ void __launch_bounds__(256, 3) k_arn_step_coop(Arnoldi a) {
         }
     };
     if ((int)blockIdx.x < items) load_slots(blockIdx.x);
-    if (!grid_barrier(a.bar2, GI + a.bar_extra, a.err, a.err_host, a.spin_limit)) return;   // V[j+1] complete
+    if (!grid_barrier(a.bar2, (unsigned long long)NI + a.bar_extra, a.err, a.err_host, a.spin_limit))
+        return;   // u_{j+1} complete
     for (int item = blockIdx.x; item < items; item += NI) {
         const int b = item / a.nchunk, c = item % a.nchunk;
         if (item != (int)blockIdx.x) load_slots(item);
         if (!s_flag[b]) continue;
-        // V[j+1] in float32 (v32, written in phase 5 with the same rounding
+        // u_{j+1} in float32 (v32, written in phase 2 with the same rounding
         // the conversion here would make)
         const float* x = a.v32 + (long long)b * a.n;
         double* z = a.zpre + (long long)b * a.n;
@@ -837,22 +814,35 @@ void arn_init(const Arnoldi& a, const double* r, const double* nrm2, const int* 
 
 int arnoldi_chunks(int n) { return ceil_div(n, ACH); }
 
-int arn_coop_grid(int n, int nb, int m, bool* resident) {
+// dynamic shared memory of the step kernels: cf, the column, cs and sn
+static size_t step_smem(int m) { return (size_t)(5 * m + 4) * sizeof(double); }
+
+void arn_configure(int m) {
+    const int sh = (int)step_smem(m);
+    BAE_CUDA(cudaFuncSetAttribute(k_arn_dots<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sh));
+    BAE_CUDA(cudaFuncSetAttribute(k_arn_dots<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, sh));
+    BAE_CUDA(cudaFuncSetAttribute(k_arn_step_coop<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sh));
+    BAE_CUDA(cudaFuncSetAttribute(k_arn_step_coop<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sh));
+}
+
+int arn_coop_grid(int n, int nb, int m, bool* resident, bool* redundant) {
     static const bool off = []() {
         const char* e = getenv("BAE_ARNOLDI_COOP");
         return e && e[0] == '0';
     }();
+    *resident = false;
+    *redundant = false;
     if (off || nb > COOP_MAX_NB || n <= 0) return 0;
     int dev = 0, coop = 0, sms = 0;
     BAE_CUDA(cudaGetDevice(&dev));
     BAE_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
     BAE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     if (!coop) return 0;
-    const size_t sh = (size_t)(4 * m + 3) * sizeof(double);
+    arn_configure(m);
+    const size_t sh = step_smem(m);
     const long long items = (long long)nb * ceil_div(n, ACH);
     // resident basis chunks: one item per CTA, all CTAs on the device at once
     const size_t sh_sv = sh + (size_t)(m + 1) * SV_STRIDE * sizeof(double);
-    *resident = false;
     if (sh_sv <= 200 * 1024) {
         BAE_CUDA(cudaFuncSetAttribute(k_arn_step_coop<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)sh_sv));
@@ -863,6 +853,7 @@ int arn_coop_grid(int n, int nb, int m, bool* resident) {
         BAE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s64, k_arn_step_coop<double, true>, 256, sh_sv));
         if (items + nb <= (long long)std::min(s32, s64) * sms) {   // one CTA per chunk plus one rotation CTA per right-hand side
             *resident = true;
+            *redundant = true;
             return (int)(items + nb);
         }
     }
@@ -872,21 +863,24 @@ int arn_coop_grid(int n, int nb, int m, bool* resident) {
     const long long cap = (long long)std::min(k32, k64) * sms;
     // persistent chunk CTAs plus one rotation CTA per right-hand side
     if (cap <= nb) return 0;
-    return (int)std::min(cap, items + nb);
+    const long long grid = std::min(cap, items + nb);
+    *redundant = items <= grid - nb;   // one item per chunk CTA
+    return (int)grid;
 }
 
 void arn_step(const Arnoldi& a, cudaStream_t st) {
     BAE_REQUIRE(a.v && a.gm && a.partner && a.t, BAE_ERR_INVALID_ARG, "arn_step: gather inputs not set");
-    const size_t sh_h = (size_t)(a.m + 1) * sizeof(double);
-    const size_t sh_g = (size_t)(4 * a.m + 3) * sizeof(double);
+    BAE_REQUIRE(a.cf && a.hs && a.Hu && a.tco && a.gflag && a.live, BAE_ERR_INVALID_ARG,
+                "arn_step: step state not set");
+    const size_t sh = step_smem(a.m);
     if (a.coop_grid > 0) {
-        BAE_REQUIRE(a.bar && a.bar2 && a.err && a.n2 && a.gflag && a.live && a.pcol && a.nb <= COOP_MAX_NB &&
-                        a.coop_grid > a.nb,
+        BAE_REQUIRE(a.bar && a.bar2 && a.err && a.nb <= COOP_MAX_NB && a.coop_grid > a.nb &&
+                        (!a.coop_redundant || (long long)a.nb * a.nchunk <= a.coop_grid - a.nb),
                     BAE_ERR_INVALID_ARG, "arn_step: cooperative step state not set");
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(a.coop_grid);
         cfg.blockDim = dim3(256);
-        cfg.dynamicSmemBytes = sh_g + (a.coop_resident ? (size_t)(a.m + 1) * SV_STRIDE * sizeof(double) : 0);
+        cfg.dynamicSmemBytes = sh + (a.coop_resident ? (size_t)(a.m + 1) * SV_STRIDE * sizeof(double) : 0);
         cfg.stream = st;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeCooperative;
@@ -907,13 +901,13 @@ void arn_step(const Arnoldi& a, cudaStream_t st) {
         }
         return;
     }
+    BAE_REQUIRE(a.jstep && a.ran, BAE_ERR_INVALID_ARG, "arn_step: step state not set");
     const dim3 grid(a.nchunk, a.nb);
     if (a.v_f32)
-        BAE_LAUNCH("k_arn_gather_dots.f32", st, k_arn_gather_dots<float><<<grid, 256, 0, st>>>(a));
+        BAE_LAUNCH("k_arn_dots.f32", st, k_arn_dots<float><<<grid, 256, sh, st>>>(a));
     else
-        BAE_LAUNCH("k_arn_gather_dots.f64", st, k_arn_gather_dots<double><<<grid, 256, 0, st>>>(a));
-    BAE_LAUNCH("k_arn_update_dots", st, k_arn_update_dots<<<grid, 256, sh_g, st>>>(a));
-    BAE_LAUNCH("k_arn_update_next", st, k_arn_update_next<<<grid, 256, sh_h, st>>>(a));
+        BAE_LAUNCH("k_arn_dots.f64", st, k_arn_dots<double><<<grid, 256, sh, st>>>(a));
+    BAE_LAUNCH("k_arn_next", st, k_arn_next<<<grid, 256, (size_t)2 * (a.m + 1) * sizeof(double), st>>>(a));
 }
 
 void arn_finish(const Arnoldi& a, double* x, cudaStream_t st) {
