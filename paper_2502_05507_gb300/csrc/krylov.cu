@@ -632,6 +632,10 @@ __device__ __forceinline__ void grid_arrive(unsigned long long* ctr) {
 // fit, which made the 64-right-hand-side step ~40% slower.
 template <typename VT, bool SV>
 __global__ void __launch_bounds__(256, 3) k_arn_step_coop(Arnoldi a) {
+    // launched with programmatic stream serialisation: the launch is set up
+    // while the apply's last kernel runs; nothing is read before that kernel
+    // has completed
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
     extern __shared__ double s_dyn[];
     const int m = a.m;
     double* s_cf = s_dyn;                     // 2 (m + 1)
@@ -882,11 +886,13 @@ void arn_step(const Arnoldi& a, cudaStream_t st) {
         cfg.blockDim = dim3(256);
         cfg.dynamicSmemBytes = sh + (a.coop_resident ? (size_t)(a.m + 1) * SV_STRIDE * sizeof(double) : 0);
         cfg.stream = st;
-        cudaLaunchAttribute attr[1];
+        cudaLaunchAttribute attr[2];
         attr[0].id = cudaLaunchAttributeCooperative;
         attr[0].val.cooperative = 1;
+        attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[1].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = attr;
-        cfg.numAttrs = 1;
+        cfg.numAttrs = 2;
         if (a.coop_resident) {
             BAE_REQUIRE(a.coop_grid == a.nb * a.nchunk + a.nb, BAE_ERR_INVALID_ARG,
                         "arn_step: resident step needs one CTA per chunk and per right-hand side");
