@@ -81,7 +81,7 @@ typedef struct bae_options {
     int    max_refine;   /* outer refinement steps for BAE_MIXED, default 8     */
     double inner_tol;    /* inner float32 GMRES reduction per step, default 1e-5;
                             the step that can reach tol aims at 0.3 tol ||b|| */
-    int    use_graphs;   /* 1: each Arnoldi step (apply, CGS2, Givens) is captured
+    int    use_graphs;   /* 1: each Arnoldi step (apply, Gram-Schmidt, Givens) is captured
                             as a CUDA graph once per solve and replayed; 0:
                             launched kernel by kernel with programmatic
                             launch overlap (same kernels). Default 0: per

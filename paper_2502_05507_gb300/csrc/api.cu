@@ -297,7 +297,7 @@ struct bae_ctx {
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     // a server slot: other slots' kernels run beside this context's on the
     // same GPU, so no kernel may assume that all of its CTAs are resident at
-    // once (the Arnoldi step runs as three kernels, not the cooperative one)
+    // once (the Arnoldi step runs as two kernels, not the cooperative one)
     bool shared_gpu = false;
     int* pinned = nullptr;       // mapped host memory the kernels write the live flags into
     int* pinned_dev = nullptr;   // its device address
@@ -585,7 +585,7 @@ struct StepGraph {
 };
 
 // Restarted GMRES for the RHS b in `which` (rows of rhs/x [nb][n], device):
-// every Arnoldi step (apply of precision `prec`, CGS2, Givens) runs on the
+// every Arnoldi step (apply of precision `prec`, Gram-Schmidt, Givens) runs on the
 // device; with use_graph it is captured once as a CUDA graph and replayed.
 // The host only polls the convergence flags (double-buffered, one step
 // behind) and closes each cycle. x_zero: x is known to be 0.

@@ -344,7 +344,7 @@ __device__ __forceinline__ void chunk_dots(const RowView& V, int cols, const dou
 // Applies the rotations (s_cs[i], s_sn[i]), i < j, to the Hessenberg column
 // s_col[0..j+1] (s_col[j+1] = the new subdiagonal), forms the rotation that
 // zeroes s_col[j+1] (stored in cs[j], sn[j]) and rotates g[j], g[j+1]. One
-// thread; the three-kernel and the fused step share it.
+// thread; the two-kernel and the fused step share it.
 __device__ __forceinline__ void givens_apply(double* s_col, const double* s_cs, const double* s_sn, int j, double* cs,
                                              double* sn, double* g) {
     for (int i = 0; i < j; ++i) {
@@ -369,7 +369,7 @@ __device__ __forceinline__ void givens_apply(double* s_col, const double* s_cs, 
 // per row in the order of reduce_rows; then r and t by two warps with
 // lane-strided sums and the fixed shuffle tree. Every CTA that needs them
 // (the rotation CTA, a chunk CTA in the redundant mode, the last block of
-// the three-kernel path) runs this same code, so all get the same bits.
+// the two-kernel path) runs this same code, so all get the same bits.
 __device__ __forceinline__ void step_coeffs(const Arnoldi& a, int b, int j, bool ran, double* cf, double* s_rt) {
     const int m = a.m, nch = a.nchunk;
     const double* part = a.part + (long long)b * 2 * (m + 1) * nch;
@@ -498,7 +498,7 @@ __device__ __forceinline__ void gather_chunk(const Arnoldi& a, int b, long long 
     }
 }
 
-// --------------------------------------------------- three-kernel step
+// ----------------------------------------------------- two-kernel step
 // kernel 1: gather w (when the RHS computes a column), partial sums of
 // Q^T u and u.u (and of Q^T w and u.w); the last CTA of each right-hand side
 // reduces them and does the Hessenberg part; the update kernel reads the

@@ -1,5 +1,6 @@
 // Deterministic batched vector kernels for GMRES (classical Gram-Schmidt
-// with one reorthogonalisation). Every reduction uses a fixed partition of
+// with one reorthogonalisation, delayed by one step). Every reduction uses
+// a fixed partition of
 // the vector and a fixed summation order (partial sums per chunk, then the
 // last CTA to finish adds the partials in chunk order), so results do not
 // depend on timing or on which other right-hand sides share the launch.
@@ -68,7 +69,7 @@ struct Arnoldi {
     int* live = nullptr;        // [nb] flag | gflag: the host runs another step
     int* live_host = nullptr;   // [nb] device address of mapped host memory, or null
     int* ncols = nullptr;       // [nb] basis vectors used this cycle
-    int* jstep = nullptr;       // [nb] j and flag of the last step (three-kernel path:
+    int* jstep = nullptr;       // [nb] j and flag of the last step (two-kernel path:
     int* ran = nullptr;         //      the update kernel reads them)
     unsigned int* ctr = nullptr;  // [nb][3] last-block counters (self-resetting)
     int* j = nullptr;           // [nb] current step of each RHS

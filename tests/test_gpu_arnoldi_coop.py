@@ -1,8 +1,9 @@
 """The fused Arnoldi step (one cooperative kernel with grid barriers) and the
-three-kernel step use the same partition and order for every sum, so a solve
+two-kernel step use the same partition and order for every sum, so a solve
 gives bit-identical densities, solutions and iteration counts with either
-(GMRES of Section 4.1 around the BAE of eq. [double_bae]). The three-kernel
-step runs in a child process with BAE_ARNOLDI_COOP=0."""
+(GMRES of Section 4.1 around the BAE of eq. [double_bae], Gram-Schmidt with
+delayed reorthogonalisation). The two-kernel step runs in a child process
+with BAE_ARNOLDI_COOP=0."""
 import json
 import os
 import subprocess
