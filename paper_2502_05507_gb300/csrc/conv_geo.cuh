@@ -52,6 +52,10 @@ template <typename T, int L, int V = 0> struct Geo {
     static constexpr int P = THREE ? 256 / TH : ((256 / TH) < PB ? (256 / TH) : (PB < 4 ? 4 : PB));
     static constexpr int KT = P * TH;
     static constexpr int XS = PL::XS;              // exchange stride per pair (odd)
+    // stride of a pair's source lines (2N values) in the forward k pass:
+    // for 4-byte values the lines of one warp (32 / TH of them) would start
+    // on the same bank; TH values of padding shift each to its own banks
+    static constexpr int RS = L + ((int)sizeof(T) == 4 && TH < 32 ? TH : 0);
     // resident CTAs per SM the compiler must allow (register cap): three per
     // SM for the three-level plan (at most 85 registers per thread, as its
     // kernels need) and for variant 1 of float32 at L = 256 (its i pass

@@ -60,7 +60,7 @@ __device__ __forceinline__ void kpass_fwd_tile(const ConvArgs<T>& a, int bx, int
     constexpr int N = L / 2, N1 = N + 1, TH = G::TH, S = G::S;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* xch = reinterpret_cast<C*>(smem_raw);                 // P * XS
-    T* rho = reinterpret_cast<T*>(xch + G::P * G::XS);      // P * 2N
+    T* rho = reinterpret_cast<T*>(xch + G::P * G::XS);      // P * RS
 
     const int b = bz;
     if (a.active && !a.active[b]) return;   // whole CTA: no barrier is skipped
@@ -69,7 +69,7 @@ __device__ __forceinline__ void kpass_fwd_tile(const ConvArgs<T>& a, int bx, int
     const long long pair = (long long)a.plane_lo() * (N / 2) + (long long)bx * G::P + p;
     const bool active = pair < (long long)a.plane_hi() * (N / 2);
     const long long la = 2 * pair, lb = la + 1;
-    T* r = rho + p * 2 * N;
+    T* r = rho + p * G::RS;
 
     C v[S];
     if (a.mode == SRC_DENSITY) {
@@ -92,7 +92,7 @@ __device__ __forceinline__ void kpass_fwd_tile(const ConvArgs<T>& a, int bx, int
                 for (int s = s0 + (int)threadIdx.x; s < s1; s += (int)blockDim.x) {
                     const int lin = a.rec.src_lin[s];
                     const int rel = (int)(lin / N - l0);   // line within the CTA: pair rel / 2, half rel % 2
-                    rho[(rel >> 1) * 2 * N + (rel & 1) * N + (lin % N)] = source_value<T>(a.rec, s, q, q32);
+                    rho[(rel >> 1) * G::RS + (rel & 1) * N + (lin % N)] = source_value<T>(a.rec, s, q, q32);
                 }
             }
         }
@@ -575,7 +575,7 @@ void configure_conv() {
     using C = cplx_t<T>;
     using G = Geo<T, L>;
     constexpr int N = L / 2;
-    const size_t smem_k = (size_t)G::P * G::XS * sizeof(C) + (size_t)G::P * 2 * N * sizeof(T);
+    const size_t smem_k = (size_t)G::P * G::XS * sizeof(C) + (size_t)G::P * G::RS * sizeof(T);
     const size_t smem_c = (size_t)G::XL * G::W * sizeof(C);
     // once per instantiation (thread-safe static initialisation)
     static const bool configured = [&]() {
@@ -597,7 +597,7 @@ void configure_conv() {
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
         if constexpr (HasAlt<T, L>::value) {
             using GA = Geo<T, L, 1>;
-            const size_t ak = (size_t)GA::P * GA::XS * sizeof(C) + (size_t)GA::P * 2 * N * sizeof(T);
+            const size_t ak = (size_t)GA::P * GA::XS * sizeof(C) + (size_t)GA::P * GA::RS * sizeof(T);
             const size_t ac = (size_t)GA::XL * GA::W * sizeof(C);
             BAE_CUDA(cudaFuncSetAttribute(k_kpass_fwd<T, L, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ak));
             BAE_CUDA(cudaFuncSetAttribute(k_kpass_inv<T, L, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ak));
@@ -664,7 +664,7 @@ void launch_passes(const ConvArgs<T>& a, cudaStream_t st) {
     using C = cplx_t<T>;
     using G = Geo<T, L, V>;
     constexpr int N = L / 2;
-    const size_t smem_k = (size_t)G::P * G::XS * sizeof(C) + (size_t)G::P * 2 * N * sizeof(T);
+    const size_t smem_k = (size_t)G::P * G::XS * sizeof(C) + (size_t)G::P * G::RS * sizeof(T);
     const size_t smem_c = (size_t)G::XL * G::W * sizeof(C);
     const int nb = a.nbatch;
     const int np = a.plane_hi() - a.plane_lo();   // x-planes holding sources or read outputs
