@@ -63,11 +63,18 @@ template <typename T, int L, int V = 0> struct Geo {
     // otherwise
     static constexpr bool CAP3 = THREE || (V == 1 && std::is_same<T, float>::value && L == 256);
     static constexpr int MINB = CAP3 ? 3 : 1;
-    // the column passes: the same, except the three-level i pass at L = 256
-    // (spectral product and two transforms), which fits 128 registers
-    // without spilling at two CTAs per SM and runs ~3% faster so than with
-    // the spills of the three-CTA cap
-    static constexpr int minb_col(int mode) { return (THREE && L == 256 && mode == 1) ? 2 : MINB; }
+    // per pass, where it differs: the three-level i pass at L = 256
+    // (spectral product and two transforms) fits 128 registers without
+    // spilling at two CTAs per SM and runs ~3% faster so than with the
+    // spills of the three-CTA cap; the float32 variant-1 forward passes at
+    // L = 256 (forward k, forward j, i) fit 64 registers without spilling
+    // at four CTAs per SM and run 4-11% faster so at 64 right-hand sides,
+    // while the two inverse passes run 7% and 37% slower so and keep three
+    static constexpr bool F4 = V == 1 && std::is_same<T, float>::value && L == 256;
+    static constexpr int minb_col(int mode) {
+        return (THREE && L == 256 && mode == 1) ? 2 : (F4 && mode != 2) ? 4 : MINB;
+    }
+    static constexpr int MINB_KF = F4 ? 4 : MINB;   // forward k pass
 };
 
 template <typename T>

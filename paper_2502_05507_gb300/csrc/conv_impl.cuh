@@ -147,7 +147,7 @@ __device__ __forceinline__ void kpass_fwd_tile(const ConvArgs<T>& a, int bx, int
 // the compiler keeps loop invariants (twiddles, offsets) in registers,
 // which halves the occupancy of the one-tile form.
 template <typename T, int L, bool BOX = false, int V = 0, bool PERSIST = false>
-__global__ void __launch_bounds__(Geo<T, L, V>::KT, Geo<T, L, V>::MINB) k_kpass_fwd(ConvArgs<T> a) {
+__global__ void __launch_bounds__(Geo<T, L, V>::KT, Geo<T, L, V>::MINB_KF) k_kpass_fwd(ConvArgs<T> a) {
     wait_prior_grid();   // results of the previous kernel on the stream
     if constexpr (PERSIST) {
         constexpr int N = L / 2;
