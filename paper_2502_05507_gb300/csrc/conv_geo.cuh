@@ -70,11 +70,15 @@ template <typename T, int L, int V = 0> struct Geo {
     // L = 256 (forward k, forward j, i) fit 64 registers without spilling
     // at four CTAs per SM and run 4-11% faster so at 64 right-hand sides,
     // while the two inverse passes run 7% and 37% slower so and keep three;
-    // the three-level forward k and both j passes at L = 256 (16-byte
-    // types) fit 64 registers too and run 4-12% faster at four CTAs per SM
-    static constexpr bool F4 = (V == 1 && std::is_same<T, float>::value && L == 256) || (THREE && L == 256);
+    // the three-level forward k and both j passes of the 16-byte types fit
+    // 64 registers too and run 4-12% faster at four CTAs per SM (L = 256
+    // and 512; at L = 512 the i pass would spill and keeps three)
+    static constexpr bool F4 = (V == 1 && std::is_same<T, float>::value && L == 256) ||
+                               (THREE && (L == 256 || (L == 512 && sizeof(C) == 16)));
     static constexpr int minb_col(int mode) {
-        return (THREE && L == 256 && mode == 1) ? 2 : (F4 && (mode != 2 || THREE)) ? 4 : MINB;
+        if (THREE && L == 256 && mode == 1) return 2;
+        if (THREE && L == 512 && mode == 1) return MINB;
+        return (F4 && (mode != 2 || THREE)) ? 4 : MINB;
     }
     static constexpr int MINB_KF = F4 ? 4 : MINB;   // forward k pass
 };
