@@ -627,11 +627,13 @@ __device__ __forceinline__ void grid_arrive(unsigned long long* ctr) {
 // the rows V[0..j] in shared memory (copied asynchronously while the
 // gather runs), so both passes read it from there; the sums are the same
 // expressions in the same order as with global rows.
-// Compiled for three resident CTAs per SM (at most 85 registers; it needs
-// 80 without spilling): left free, the compiler takes 91 and only two CTAs
-// fit, which made the 64-right-hand-side step ~40% slower.
+// Compiled for four resident CTAs per SM (64 registers, a few spilled
+// values): more CTAs take more of the (RHS, chunk) items at once, and the
+// 64-right-hand-side step is 12% faster than at three CTAs per SM (80
+// registers, no spill); left free, the compiler takes ~90 registers and
+// only two CTAs fit.
 template <typename VT, bool SV>
-__global__ void __launch_bounds__(256, 3) k_arn_step_coop(Arnoldi a) {
+__global__ void __launch_bounds__(256, 4) k_arn_step_coop(Arnoldi a) {
     // launched with programmatic stream serialisation: the launch is set up
     // while the apply's last kernel runs; nothing is read before that kernel
     // has completed
