@@ -191,12 +191,12 @@ DF64_OPS_PER_FLOP = 7.0
 # (profiles/); a kernel changed since its capture is dropped from this
 # table (its traffic is then reported as null). Keyed by (kernel, N,
 # right-hand sides per launch). The 64-right-hand-side figure is the
-# 16-right-hand-side capture (764.6 MB: 414.5 read + 350.1 written) scaled
+# 16-right-hand-side capture (764.9 MB: 414.6 read + 350.4 written) scaled
 # by 4, less the three extra reads of the 8.6 MB spectrum octant that one
 # launch shares over its right-hand sides (a capture at 64 would hold
 # ~10 GB on the device under ncu's replay).
 NCU_TRAFFIC = {
-    ("conv_i.f32", 128, 64): 4 * 764.6e6 - 3 * 8.59e6,   # conv_passes_batched16_torus_N128.md
+    ("conv_i.f32", 128, 64): 4 * 764.9e6 - 3 * 8.59e6,   # conv_passes_batched16_torus_N128.md
     ("conv_i.f32", 128, 1): 33.98e6,                       # conv_passes_torus_N128.md
 }
 
