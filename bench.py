@@ -136,8 +136,9 @@ class ClockSampler:
 def kernel_model(n, pb, n_gm, npl=None, nb=1):
     """Algorithmic (bytes, flops) per right-hand side of one launch of each
     convolution pass at grid size n, element precision pb bytes (complex =
-    2 pb), when the solve transforms npl of the n x-planes (the planes that
-    hold sources or read-back nodes; all n if None) and nb right-hand sides
+    2 pb), when the solve transforms npl of the n planes along the axis the
+    convolution prunes (the planes that hold sources or read-back nodes, on
+    the axis with the fewest of them; all n if None) and nb right-hand sides
     share the launch (the spectrum is read once per launch). FFT flops use
     the 5 L log2 L convention per complex transform of length L = 2n; the
     spectral multiply counts 2 flops per element."""
@@ -187,18 +188,11 @@ DF64_OPS_PER_FLOP = 7.0
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum)
-# of convolution kernels, from ncu captures of the current kernels
-# (profiles/); a kernel changed since its capture is dropped from this
-# table (its traffic is then reported as null). Keyed by (kernel, N,
-# right-hand sides per launch). The 64-right-hand-side figure is the
-# 16-right-hand-side capture (764.9 MB: 414.6 read + 350.4 written) scaled
-# by 4, less the three extra reads of the 8.6 MB spectrum octant that one
-# launch shares over its right-hand sides (a capture at 64 would hold
-# ~10 GB on the device under ncu's replay).
-NCU_TRAFFIC = {
-    ("conv_i.f32", 128, 64): 4 * 764.9e6 - 3 * 8.59e6,   # conv_passes_batched16_torus_N128.md
-    ("conv_i.f32", 128, 1): 33.98e6,                       # conv_passes_torus_N128.md
-}
+# of convolution kernels, from ncu captures of the current kernels and
+# workloads (profiles/); a kernel or plane range changed since its capture
+# is dropped from this table (its traffic is then reported as null). Keyed
+# by (kernel, N, right-hand sides per launch).
+NCU_TRAFFIC = {}
 
 
 def roofline_for(name, ms_total, launches, n, n_gm, hbm, hbm_kind, npl=None, nb=1):
@@ -222,11 +216,23 @@ def roofline_for(name, ms_total, launches, n, n_gm, hbm, hbm_kind, npl=None, nb=
         return {**common, "bound": "alu", "achieved": a, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": a / FP64_PEAK_TFLOPS, "traffic": None, "peak_kind": "nominal FP64 (recipe table)",
                 "algorithmic_flops": flops}
+    # float32: bound by whichever of HBM and the float32 pipes it is closer
+    # to (the i pass, two length-2N transforms per element moved, is
+    # ALU-bound once the convolution transforms few planes)
     a = nbytes / t / 1e9
-    return {**common, "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
-            "traffic": NCU_TRAFFIC.get((name, n, nb)), "peak_kind": hbm_kind + " HBM copy bandwidth",
-            "algorithmic_bytes": nbytes, "fp32_flops_5LlogL": flops,
-            "fp32_frac_of_lane_peak_5LlogL": flops / t / 1e12 / (2 * FP32_LANE_PEAK_T)}
+    f_hbm = a / hbm
+    a_alu = flops / t / 1e12
+    f_alu = a_alu / (2 * FP32_LANE_PEAK_T)
+    both = {"algorithmic_bytes": nbytes, "GBps": a, "frac_hbm": f_hbm, "hbm_peak": hbm,
+            "hbm_peak_kind": hbm_kind + " HBM copy bandwidth", "traffic_bytes": NCU_TRAFFIC.get((name, n, nb)),
+            "fp32_flops_5LlogL": flops, "fp32_TFLOPs_5LlogL": a_alu, "frac_fp32": f_alu}
+    if f_alu > f_hbm:
+        return {**common, "bound": "alu", "achieved": a_alu, "peak": 2 * FP32_LANE_PEAK_T,
+                "unit": "TFLOP/s (5 L log2 L per transform)", "frac": f_alu,
+                "traffic": NCU_TRAFFIC.get((name, n, nb)),
+                "peak_kind": "nominal float32 FMA rate (152 SMs x 128 lanes x 2.07 GHz x 2 flops)", **both}
+    return {**common, "bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s", "frac": f_hbm,
+            "traffic": NCU_TRAFFIC.get((name, n, nb)), "peak_kind": hbm_kind + " HBM copy bandwidth", **both}
 
 
 def kernel_table(prof, top=16):
@@ -314,7 +320,7 @@ def run_ours(args, rank, world, dev):
     pr0 = Problem(ctx, phi, P0.grid.h, P0.grid.origin, 0.0, "double")
     xs = np.asarray(pr0.boundary_points())
     n_gm = pr0.n_gm
-    plo, phi_ = pr0.plane_range()
+    conv_axis, plo, phi_ = pr0.conv_planes()
     npl = phi_ - plo
     pr0.close()
     f_h = np.stack([P.f() for P in probs])
@@ -358,7 +364,7 @@ def run_ours(args, rank, world, dev):
                      "applies_fp32_max": max(s["applies_fp32"] for s in st),
                      "applies_fp64_accurate_max": max(s["applies_fp64"] for s in st),
                      "rel_residual_max": max(s["rel_residual"] for s in st), "n_gm": n_gm,
-                     "planes_transformed": npl},
+                     "planes_transformed": npl, "plane_axis": "xyz"[conv_axis]},
            "gpu_launches": int(l1 - l0), "clocks": clk}
     if rank != 0 or args.only_timed:
         ctx.close()
@@ -465,7 +471,7 @@ def run_torus128_extra(ctx, torch, flush, hbm, hbm_kind, steps=50, warmup=3):
     pr0 = Problem(ctx, phi, P.grid.h, P.grid.origin, P.kappa2, "double")
     g = torch.from_numpy(P.g_at(np.asarray(pr0.boundary_points()))).cuda()
     n_gm = pr0.n_gm
-    plo, phi_ = pr0.plane_range()
+    conv_axis, plo, phi_ = pr0.conv_planes()
     pr0.close()
 
     def step():
@@ -512,7 +518,7 @@ def run_star256_table(ctx, torch, reps=3):
             pr0 = Problem(ctx, phi, P.grid.h, P.grid.origin, k2, layer)
             g = torch.from_numpy(P.g_at(np.asarray(pr0.boundary_points()))).cuda()
             n_gm = pr0.n_gm
-            plo, phi_ = pr0.plane_range()
+            conv_axis, plo, phi_ = pr0.conv_planes()
             pr0.close()
 
             def step():

@@ -265,11 +265,24 @@ int bae_problem_unknowns(const bae_problem* prob, int64_t* n);
 int bae_gamma_plus(const bae_problem* prob, int32_t* gp_idx);
 
 /* The x-planes [*lo, *hi) that hold every source (gamma-, the D-nodes, M+)
- * and every node a solve reads back (gamma-, the closure partners, M+):
- * inside a solve and in bae_boundary_apply the convolution transforms only
- * these planes (the others are zero on input and unread on output). Not a
+ * and every node a solve reads back (gamma-, the closure partners, M+): the
+ * other planes are zero on input and unread on output. When
+ * bae_problem_conv_planes reports axis 0, inside a solve and in
+ * bae_boundary_apply the convolution transforms only these planes. Not a
  * quantity of the paper; a cost model aid. Host-side, no device work. */
 int bae_problem_plane_range(const bae_problem* prob, int* lo, int* hi);
+
+/* The planes that the applies inside a solve and bae_boundary_apply
+ * transform: *axis is the grid axis (0 x, 1 y, 2 z) with the fewest planes
+ * holding sources or read-back nodes (chosen only when it has at least a
+ * tenth fewer than x; always 0 for BAE_LAYER_DIRECT or with the environment
+ * variable BAE_CONV_AXIS=x at problem creation), [*lo, *hi) the range along
+ * it. The convolution skips zero planes only along the first axis of the
+ * grid it runs on, so those applies run on the grid with axes x and *axis
+ * swapped; the lattice Green's function is symmetric under permutations of
+ * the axes, so they compute the same potential (within rounding). Not a
+ * quantity of the paper; a cost model aid. Host-side, no device work. */
+int bae_problem_conv_planes(const bae_problem* prob, int* axis, int* lo, int* hi);
 
 /* Boundary points x*(m) of the closure rows, gamma- in lexicographic order:
  * xyz[3r + c]. The caller evaluates g there. */

@@ -102,6 +102,7 @@ def lib():
             "bae_gamma_plus": (_I, [_P, _P]),
             "bae_interior_mask": (_I, [_P, _P]),
             "bae_problem_plane_range": (_I, [_P, _P, _P]),
+            "bae_problem_conv_planes": (_I, [_P, _P, _P, _P]),
             "bae_boundary_points": (_I, [_P, _P]),
             "bae_classification": (_I, [_P, _P, _P, _P, _P]),
             "bae_potential_apply": (_I, [_P, _I, _P, _P]),
@@ -131,7 +132,8 @@ EXPORTED = ["bae_version", "bae_last_error", "bae_default_options", "bae_launch_
             "bae_inject_fault", "bae_profile_start",
             "bae_profile_stop", "bae_ctx_create", "bae_ctx_destroy",
             "bae_lgf_table", "bae_lgf_spectrum", "bae_problem_create", "bae_problem_destroy",
-            "bae_problem_sizes", "bae_problem_unknowns", "bae_gamma_plus", "bae_interior_mask", "bae_problem_plane_range", "bae_boundary_points", "bae_classification", "bae_potential_apply",
+            "bae_problem_sizes", "bae_problem_unknowns", "bae_gamma_plus", "bae_interior_mask", "bae_problem_plane_range",
+            "bae_problem_conv_planes", "bae_boundary_points", "bae_classification", "bae_potential_apply",
             "bae_potential_apply_noalloc",
             "bae_boundary_apply", "bae_particular", "bae_box_particular", "bae_solve", "bae_solve_batched", "bae_server_create",
             "bae_server_submit", "bae_server_poll", "bae_server_density", "bae_server_release", "bae_server_clock",
@@ -298,10 +300,17 @@ class Problem:
             pass
 
     def plane_range(self):
-        """(lo, hi): the x-planes the solve's convolutions transform."""
+        """(lo, hi): the x-planes that hold every source and read-back node."""
         lo, hi = ctypes.c_int(), ctypes.c_int()
         _check(lib().bae_problem_plane_range(self._h, ctypes.byref(lo), ctypes.byref(hi)))
         return lo.value, hi.value
+
+    def conv_planes(self):
+        """(axis, lo, hi): the axis (0 x, 1 y, 2 z) and plane range that the
+        convolutions inside a solve transform."""
+        ax, lo, hi = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().bae_problem_conv_planes(self._h, ctypes.byref(ax), ctypes.byref(lo), ctypes.byref(hi)))
+        return ax.value, lo.value, hi.value
 
     def boundary_points(self, like=None):
         out = _new((self.n_gm, 3), np.float64, like)

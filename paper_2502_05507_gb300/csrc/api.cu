@@ -378,9 +378,21 @@ namespace {
 long long n_gm(const bae_problem* P) { return P->geo.n_gm; }
 long long n_unk(const bae_problem* P) { return P->geo.n_unk; }
 
-// pruned: only the x-planes that hold sources or gathered / reconstructed
-// nodes are transformed (applies whose output is read at gamma-, the
-// partners and M+ only); otherwise the potential covers the whole grid
+// Pruned applies (whose output is read at gamma-, the partners and M+
+// only) transform only the planes that hold sources or read nodes, along
+// the first axis of the grid they run on: the geometry's swapped view
+// (Geometry::cv_swap), whose first axis is the one with the fewest such
+// planes. Their recipe and flags are the view's, f is read through the
+// swap, and their output is in the swapped layout: it is read back at
+// gm_of / partner_of and through volume_combine's swap. Unpruned applies
+// cover the whole grid in the plain layout.
+bool use_view(const bae_problem* P, bool pruned) { return pruned && P->geo.cv_swap != 0; }
+const int* gm_of(const bae_problem* P, bool pruned) { return use_view(P, pruned) ? P->geo.cv_gm : P->geo.gm; }
+const int* partner_of(const bae_problem* P, bool pruned) {
+    return use_view(P, pruned) ? P->geo.cv_partner : P->geo.partner;
+}
+int swap_of(const bae_problem* P, bool pruned) { return use_view(P, pruned) ? P->geo.cv_swap : 0; }
+
 template <typename T>
 ConvArgs<T> conv_args(bae_problem* P, int nb, bool pruned = false) {
     const int N = P->geo.N;
@@ -388,10 +400,14 @@ ConvArgs<T> conv_args(bae_problem* P, int nb, bool pruned = false) {
     ConvArgs<T> a;
     a.N = N;
     a.nbatch = nb;
+    const bool view = use_view(P, pruned);
     if (pruned) {
-        a.p0 = P->geo.plane_lo;
-        a.p1 = P->geo.plane_hi;
+        a.p0 = view ? P->geo.cv_lo : P->geo.plane_lo;
+        a.p1 = view ? P->geo.cv_hi : P->geo.plane_hi;
     }
+    a.rec = view ? P->geo.cv_recipe() : P->geo.recipe();
+    a.flags = view ? P->geo.cv_flags : P->geo.flags;
+    a.f_swap = swap_of(P, pruned);
     a.A = reinterpret_cast<cplx_t<T>*>(P->ws().A.need((long long)nb * N * N * N1));
     a.B = reinterpret_cast<cplx_t<T>*>(P->ws().B.need((long long)nb * N * 2 * N * N1));
     const Twiddles& tw = P->ctx->twiddles(2 * N);
@@ -425,7 +441,6 @@ out_t<T>* apply_potential(bae_problem* P, int nb, const double* q, bool pruned =
     a.mode = SRC_DENSITY;
     a.q = q;
     a.q_stride = n_unk(P);
-    a.rec = P->geo.recipe();
     a.v = vbuf<T>(P, nb);
     conv_apply<T>(a, P->ctx->stream);
     return a.v;
@@ -437,7 +452,6 @@ out_t<T>* apply_volume(bae_problem* P, int nb, const double* f, double scale, bo
     ConvArgs<T> a = conv_args<T>(P, nb, pruned);
     a.mode = SRC_VOLUME;
     a.f = f;
-    a.flags = P->geo.flags;
     a.scale = scale;
     a.v = vbuf<T>(P, nb);
     conv_apply<T>(a, P->ctx->stream);
@@ -456,7 +470,6 @@ out_t<T>* apply_box(bae_problem* P, int nb, const double* f, double scale, bool 
     a.mode = SRC_VOLUME;
     a.box = true;
     a.f = f;
-    a.flags = P->geo.flags;
     a.scale = scale;
     a.v = vbuf<T>(P, nb);
     conv_apply<T>(a, P->ctx->stream);
@@ -475,9 +488,7 @@ out_t<T>* apply_combined(bae_problem* P, int nb, const double* q, const double* 
     a.mode = SRC_DENSITY;
     a.q = q;
     a.q_stride = n_unk(P);
-    a.rec = P->geo.recipe();
     a.f = f;
-    a.flags = P->geo.flags;
     a.scale = scale;
     a.v = vbuf<T>(P, nb);
     conv_apply<T>(a, P->ctx->stream);
@@ -492,7 +503,7 @@ void boundary_apply(bae_problem* P, int nb, const double* q, double* Aq) {
         direct_rows<out_t<T>, double>(v, P->n3(), q, n_unk(P), nullptr, 0, P->geo.gp, P->geo.partner_u, P->geo.t,
                                       n_gm(P), n_unk(P), nb, nullptr, Aq, n_unk(P), P->ctx->stream);
     else
-        closure_gather<out_t<T>>(v, P->n3(), P->geo.gm, P->geo.partner, P->geo.t, (int)n_gm(P), nb, Aq, n_gm(P),
+        closure_gather<out_t<T>>(v, P->n3(), gm_of(P, true), partner_of(P, true), P->geo.t, (int)n_gm(P), nb, Aq, n_gm(P),
                                  P->ctx->stream);
 }
 
@@ -543,7 +554,6 @@ out_t<T>* potential_rows(bae_problem* P, int nb, const double* q, long long q_st
         a.q32_stride = n_unk(P);
     }
     a.active = active;
-    a.rec = P->geo.recipe();
     a.v = vbuf<T>(P, nb);
     conv_apply<T>(a, P->ctx->stream);
     return a.v;
@@ -558,7 +568,7 @@ void apply_rows(bae_problem* P, int nb, const double* q, long long q_stride, con
         direct_rows<out_t<T>, double>(v, P->n3(), q, q_stride, q_row, q_row_stride, P->geo.gp, P->geo.partner_u,
                                       P->geo.t, n_gm(P), n_unk(P), nb, active, out, n_unk(P), P->ctx->stream);
     else
-        closure_gather<out_t<T>>(v, P->n3(), P->geo.gm, P->geo.partner, P->geo.t, (int)n_gm(P), nb, out, n_gm(P),
+        closure_gather<out_t<T>>(v, P->n3(), gm_of(P, true), partner_of(P, true), P->geo.t, (int)n_gm(P), nb, out, n_gm(P),
                                  P->ctx->stream, active);
 }
 
@@ -675,8 +685,8 @@ void gmres(bae_problem* P, int prec, int nb, const std::vector<int>& which, cons
     a.v_f32 = prec == BAE_FP32;
     const bool direct = P->direct();
     a.v_stride = direct ? n : P->n3();
-    a.gm = direct ? P->iota : P->geo.gm;
-    a.partner = direct ? P->iota : P->geo.partner;
+    a.gm = direct ? P->iota : gm_of(P, true);   // the step's applies are pruned
+    a.partner = direct ? P->iota : partner_of(P, true);
     a.t = direct ? P->ones : P->geo.t;
     // direct formulation: the step's operator rows, in the apply's precision
     float* y32 = direct && prec == BAE_FP32 ? ws.ydir32.need((long long)nb * n) : nullptr;
@@ -985,7 +995,7 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
             direct_rows<float, double>(v, n3, q, n, nullptr, 0, P->geo.gp, P->geo.partner_u, P->geo.t, ng, n, nb,
                                        nullptr, res, n, st);
         else
-            closure_gather<float>(v, n3, P->geo.gm, P->geo.partner, P->geo.t, n, nb, res, n, st);
+            closure_gather<float>(v, n3, gm_of(P, true), partner_of(P, true), P->geo.t, n, nb, res, n, st);
         for (auto& s : st_local) s.applies_fp32 += 1;
     } else {
         up = P->ws().up.need((long long)nb * n3);
@@ -996,7 +1006,7 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
             direct_rows<double, double>(up, n3, q, n, nullptr, 0, P->geo.gp, P->geo.partner_u, P->geo.t, ng, n, nb,
                                         nullptr, res, n, st);
         else
-            closure_gather<double>(up, n3, P->geo.gm, P->geo.partner, P->geo.t, n, nb, res, n, st);
+            closure_gather<double>(up, n3, gm_of(P, true), partner_of(P, true), P->geo.t, n, nb, res, n, st);
     }
     {
         std::vector<int> all(nb);
@@ -1037,7 +1047,7 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
             direct_rows<double, double>(v, n3, q, n, nullptr, 0, P->geo.gp, P->geo.partner_u, P->geo.t, ng, n, nb,
                                         nullptr, tmp, n, st);
         else
-            closure_gather<double>(v, n3, P->geo.gm, P->geo.partner, P->geo.t, n, nb, tmp, n, st);
+            closure_gather<double>(v, n3, gm_of(P, true), partner_of(P, true), P->geo.t, n, nb, tmp, n, st);
         for (auto& s : st_local) s.applies_fp64 += 1;
         kr_sub(direct ? bp : (comb ? d_g : bvec), tmp, d_all, nb, n, res, st);
         kr_norm2(res, d_all, nb, n, n2 + nb, krylov_chunks(n), n2, st);
@@ -1122,7 +1132,8 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
     bool u_host = u && !is_device_ptr(u);
     if (u) {
         double* du = u_host ? P->ws().out_u.need((long long)nb * n3) : u;
-        volume_combine<double>(v_last, direct ? nullptr : up, P->geo.flags, n3, nb, du, st);
+        volume_combine<double>(v_last, direct ? nullptr : up, P->geo.flags, n3, nb, du, st, swap_of(P, true),
+                               P->geo.N);
         if (direct) scatter_gm(q, n, P->geo.gm, ng, nb, du, n3, st);   // u on gamma- is the unknown there
         if (u_host) BAE_CUDA(cudaMemcpyAsync(u, du, (size_t)nb * n3 * sizeof(double), cudaMemcpyDeviceToHost, st));
     }
@@ -1488,6 +1499,17 @@ int bae_problem_plane_range(const bae_problem* P, int* lo, int* hi) {
         BAE_REQUIRE(P && lo && hi, BAE_ERR_INVALID_ARG, "null argument");
         *lo = P->geo.plane_lo;
         *hi = P->geo.plane_hi;
+        return BAE_OK;
+    });
+}
+
+int bae_problem_conv_planes(const bae_problem* P, int* axis, int* lo, int* hi) {
+    return guarded([&]() -> int {
+        BAE_REQUIRE(P && axis && lo && hi, BAE_ERR_INVALID_ARG, "null argument");
+        const int sw = P->geo.cv_swap;
+        *axis = sw;
+        *lo = sw ? P->geo.cv_lo : P->geo.plane_lo;
+        *hi = sw ? P->geo.cv_hi : P->geo.plane_hi;
         return BAE_OK;
     });
 }

@@ -7,6 +7,7 @@
 // Every list is produced in lexicographic (i,j,k) order by a deterministic
 // exclusive scan, so the results are bit-identical from run to run.
 #include <algorithm>
+#include <cstdlib>
 #include <vector>
 
 #include "classify.cuh"
@@ -54,7 +55,8 @@ __device__ int block_exclusive_scan(int v, int* s_warp) {
 constexpr int LINE_T = 128;
 
 // slots of the small device record the host reads once
-enum { I_ERR = 0, I_GP, I_MP, I_FIRST, I_LAST, I_NGM, I_NSRC, I_NTERM, I_NGPL, I_COUNT };
+enum { I_ERR = 0, I_GP, I_MP, I_FIRST, I_LAST, I_NGM, I_NSRC, I_NTERM, I_NGPL, I_FIRSTY, I_LASTY, I_FIRSTZ, I_LASTZ,
+       I_COUNT };
 
 __device__ __forceinline__ bool in_grid(int i, int j, int k, int N) {
     return (unsigned)i < (unsigned)N && (unsigned)j < (unsigned)N && (unsigned)k < (unsigned)N;
@@ -97,6 +99,7 @@ __global__ void __launch_bounds__(LINE_T) k_flags_lines(const uint8_t* __restric
     const int line = blockIdx.x, i = line / N, j = line - i * N;
     const long long base = (long long)line * N;
     int c[5] = {0, 0, 0, 0, 0};   // gamma-, sources, terms, gamma+, M+
+    int klo = N, khi = -1;        // k range of this thread's sources
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
         const int me = nb[base + k];
         bool out_nb = false;
@@ -117,6 +120,10 @@ __global__ void __launch_bounds__(LINE_T) k_flags_lines(const uint8_t* __restric
         const int f = (in ? 1 : 0) | (gm ? 2 : 0) | (gp ? 4 : 0) | (dnode ? 8 : 0) | ((gm ? n_out : 0) << 4);
         flags[base + k] = (uint8_t)f;
         const bool src = (f & src_mask) != 0;
+        if (src) {
+            klo = min(klo, k);
+            khi = max(khi, k);
+        }
         c[0] += gm;
         c[1] += src;
         c[2] += src ? (gm ? (direct ? 1 + n_gam : 1) : n_gm) : 0;
@@ -128,6 +135,12 @@ __global__ void __launch_bounds__(LINE_T) k_flags_lines(const uint8_t* __restric
     for (int e = 0; e < 5; ++e) {
         const int v = __reduce_add_sync(0xffffffffu, c[e]);
         if (lane == 0) s_red[e][w] = v;
+    }
+    klo = __reduce_min_sync(0xffffffffu, klo);
+    khi = __reduce_max_sync(0xffffffffu, khi);
+    if (lane == 0 && khi >= 0) {
+        atomicMax(info + I_FIRSTZ, N - klo);
+        atomicMax(info + I_LASTZ, khi + 1);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -143,6 +156,8 @@ __global__ void __launch_bounds__(LINE_T) k_flags_lines(const uint8_t* __restric
         if (t[1]) {
             atomicMax(info + I_FIRST, N - i);
             atomicMax(info + I_LAST, i + 1);
+            atomicMax(info + I_FIRSTY, N - j);
+            atomicMax(info + I_LASTY, j + 1);
         }
     }
 }
@@ -348,14 +363,195 @@ __global__ void k_to_float(const double* __restrict__ in, long long n, float* __
 
 int grid_for(long long n) { return (int)std::min<long long>((n + 255) / 256, 152LL * 32); }
 
+// ------------------------------------------------- swapped convolution view
+// out[swap_axes(x)] = in[x] over the N^3 grid. sw = 1 maps k-lines onto
+// k-lines (a copy, grid-stride); sw = 2 transposes the (i, k) plane of
+// every j through a 32 x 32 shared-memory tile (grid: k tiles, i tiles, j;
+// 256 threads), so that reads and writes are both coalesced.
+template <typename T>
+__global__ void k_swap_grid(const T* __restrict__ in, T* __restrict__ out, int N, int sw) {
+    if (sw == 1) {
+        const long long n3 = (long long)N * N * N;
+        for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n3; x += (long long)gridDim.x * blockDim.x)
+            out[swap_axes(x, 1, N)] = in[x];
+        return;
+    }
+    __shared__ T tile[32][33];
+    const int j = blockIdx.z, i0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int r = ty; r < 32; r += 8) {
+        const int i = i0 + r, k = k0 + tx;
+        if (i < N && k < N) tile[r][tx] = in[((long long)i * N + j) * N + k];
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int k = k0 + r, i = i0 + tx;
+        if (i < N && k < N) out[((long long)k * N + j) * N + i] = tile[tx][r];
+    }
+}
+
+// smap[src_lin[s]] = s (smap preset to -1)
+__global__ void k_src_map(const int* __restrict__ src_lin, int ns, int* __restrict__ smap) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += gridDim.x * blockDim.x) smap[src_lin[s]] = s;
+}
+
+// Per line of the swapped grid: the number of its sources (swapped flags &
+// src_mask: the nodes the plain recipe lists) and of their terms.
+__global__ void __launch_bounds__(LINE_T) k_view_count(const uint8_t* __restrict__ vflags, int N, int sw,
+                                                      int src_mask, const int* __restrict__ smap,
+                                                      const int* __restrict__ term_off, int* __restrict__ cnt_src,
+                                                      int* __restrict__ cnt_term) {
+    __shared__ int s_red[2][LINE_T / 32];
+    const long long base = (long long)blockIdx.x * N;
+    int c0 = 0, c1 = 0;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        const int s = (vflags[base + k] & src_mask) ? smap[swap_axes(base + k, sw, N)] : -1;
+        if (s >= 0) {   // every source node of the swapped flags is in the plain recipe
+            c0 += 1;
+            c1 += term_off[s + 1] - term_off[s];
+        }
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    c0 = __reduce_add_sync(0xffffffffu, c0);
+    c1 = __reduce_add_sync(0xffffffffu, c1);
+    if (lane == 0) {
+        s_red[0][w] = c0;
+        s_red[1][w] = c1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t0 = 0, t1 = 0;
+        for (int x = 0; x < (int)(blockDim.x >> 5); ++x) {
+            t0 += s_red[0][x];
+            t1 += s_red[1][x];
+        }
+        cnt_src[blockIdx.x] = t0;
+        cnt_term[blockIdx.x] = t1;
+    }
+}
+
+// The swapped recipe in lexicographic order of the swapped grid: per line,
+// the CTA scans its sources (count in bits 0-10, terms from bit 11) from
+// the line's offsets; vorig[pos] = the source's number in the plain recipe.
+__global__ void __launch_bounds__(LINE_T) k_view_scatter(const uint8_t* __restrict__ vflags, int N, int sw,
+                                                        int src_mask, const int* __restrict__ smap,
+                                                        const int* __restrict__ term_off,
+                                                        const int* __restrict__ off_src,
+                                                        const int* __restrict__ off_term, int n_src, int n_terms,
+                                                        int* __restrict__ vsrc_lin, int* __restrict__ vterm_off,
+                                                        int* __restrict__ vorig) {
+    __shared__ int s_warp[33];
+    const int line = blockIdx.x;
+    if (line == (int)gridDim.x - 1 && threadIdx.x == 0) vterm_off[n_src] = n_terms;
+    int ps = off_src[line], pt = off_term[line];
+    if (ps == off_src[line + 1]) return;   // no source on this line: the whole CTA
+    const long long base = (long long)line * N;
+    for (int k0 = 0; k0 < N; k0 += blockDim.x) {
+        const int k = k0 + (int)threadIdx.x;
+        int sf = 0, nt = 0, s = -1;
+        if (k < N && (vflags[base + k] & src_mask)) s = smap[swap_axes(base + k, sw, N)];
+        if (s >= 0) {   // the same nodes as k_view_count counts
+            sf = 1;
+            nt = term_off[s + 1] - term_off[s];
+        }
+        const int ex = block_exclusive_scan(sf | (nt << 11), s_warp);
+        const int tot = s_warp[32];
+        if (sf) {
+            const int pos = ps + (ex & 2047);
+            vsrc_lin[pos] = (int)(base + k);
+            vterm_off[pos] = pt + (ex >> 11);
+            vorig[pos] = s;
+        }
+        ps += tot & 2047;
+        pt += tot >> 11;
+    }
+}
+
+// the terms of swapped source pos: those of plain source vorig[pos]
+__global__ void k_view_terms(const int* __restrict__ vorig, const int* __restrict__ vterm_off, int ns,
+                             const int* __restrict__ term_off, const int* __restrict__ term_idx,
+                             const double* __restrict__ term_coef, const float* __restrict__ term_coef32,
+                             int* __restrict__ vidx, double* __restrict__ vcoef, float* __restrict__ vcoef32) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < ns; p += gridDim.x * blockDim.x) {
+        const int s = vorig[p];
+        if (s < 0 || s >= ns) continue;   // preset -1: a position no scatter wrote
+        const int o = term_off[s], n = term_off[s + 1] - o, d = vterm_off[p];
+        for (int e = 0; e < n; ++e) {
+            vidx[d + e] = term_idx[o + e];
+            vcoef[d + e] = term_coef[o + e];
+            vcoef32[d + e] = term_coef32[o + e];
+        }
+    }
+}
+
+// out[r] = swap_axes(in[r])
+__global__ void k_swap_index(const int* __restrict__ in, long long n, int N, int sw, int* __restrict__ out) {
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
+        out[r] = (int)swap_axes(in[r], sw, N);
+}
+
+// Builds the swapped view (Geometry::cv_*) of a built geometry.
+void build_view(Geometry& g, int sw, int src_mask, Scratch& sc, cudaStream_t st) {
+    const int N = g.N;
+    const long long n3 = (long long)N * N * N, nl = (long long)N * N;
+    g.cv_swap = sw;
+    g.cv_lo = g.ext_lo[sw];
+    g.cv_hi = g.ext_hi[sw];
+    g.cv_flags = dev_alloc_n<uint8_t>(n3, st);
+    if (sw == 1)
+        BAE_LAUNCH("k_swap_grid", st, k_swap_grid<uint8_t><<<grid_for(n3), 256, 0, st>>>(g.flags, g.cv_flags, N, sw));
+    else
+        BAE_LAUNCH("k_swap_grid", st,
+                   k_swap_grid<uint8_t><<<dim3(ceil_div(N, 32), ceil_div(N, 32), N), 256, 0, st>>>(g.flags, g.cv_flags,
+                                                                                                   N, sw));
+    int* smap = sc.get<int>(n3);
+    BAE_CUDA(cudaMemsetAsync(smap, 0xff, n3 * sizeof(int), st));
+    BAE_LAUNCH("k_src_map", st, k_src_map<<<grid_for(g.n_src), 256, 0, st>>>(g.src_lin, (int)g.n_src, smap));
+    int* off_src = sc.get<int>(nl + 1);
+    int* off_term = sc.get<int>(nl + 1);
+    int* info = sc.get<int>(I_COUNT);
+    BAE_LAUNCH("k_view_count", st,
+               k_view_count<<<(unsigned)nl, LINE_T, 0, st>>>(g.cv_flags, N, sw, src_mask, smap, g.term_off, off_src,
+                                                             off_term));
+    // blocks 0 and 1 scan the two counts (the other two arrays are not read)
+    BAE_LAUNCH("k_scan_lines", st, k_scan_lines<<<2, 1024, 0, st>>>(off_src, off_term, off_src, off_term, (int)nl, info));
+    g.cv_line_off = off_src;
+    sc.ptrs.erase(std::find(sc.ptrs.begin(), sc.ptrs.end(), static_cast<void*>(off_src)));   // kept
+    g.cv_src_lin = dev_alloc_n<int>(g.n_src, st);
+    g.cv_term_off = dev_alloc_n<int>(g.n_src + 1, st);
+    int* vorig = sc.get<int>(std::max(1LL, g.n_src));
+    BAE_CUDA(cudaMemsetAsync(vorig, 0xff, std::max(1LL, g.n_src) * sizeof(int), st));
+    BAE_LAUNCH("k_view_scatter", st,
+               k_view_scatter<<<(unsigned)nl, LINE_T, 0, st>>>(g.cv_flags, N, sw, src_mask, smap, g.term_off, off_src,
+                                                               off_term, (int)g.n_src, (int)g.n_terms, g.cv_src_lin,
+                                                               g.cv_term_off, vorig));
+    g.cv_term_idx = dev_alloc_n<int>(g.n_terms, st);
+    g.cv_term_coef = dev_alloc_n<double>(g.n_terms, st);
+    g.cv_term_coef32 = dev_alloc_n<float>(g.n_terms, st);
+    BAE_LAUNCH("k_view_terms", st,
+               k_view_terms<<<grid_for(g.n_src), 256, 0, st>>>(vorig, g.cv_term_off, (int)g.n_src, g.term_off,
+                                                               g.term_idx, g.term_coef, g.term_coef32, g.cv_term_idx,
+                                                               g.cv_term_coef, g.cv_term_coef32));
+    g.cv_gm = dev_alloc_n<int>(g.n_gm, st);
+    g.cv_partner = dev_alloc_n<int>(g.n_gm, st);
+    BAE_LAUNCH("k_swap_index", st, k_swap_index<<<grid_for(g.n_gm), 256, 0, st>>>(g.gm, g.n_gm, N, sw, g.cv_gm));
+    BAE_LAUNCH("k_swap_index", st,
+               k_swap_index<<<grid_for(g.n_gm), 256, 0, st>>>(g.partner, g.n_gm, N, sw, g.cv_partner));
+}
+
 }  // namespace
 
 void Geometry::release() {
-    void* ps[] = {flags, gm, gp, node_of, partner, partner_u, t, xstar, line_off, src_lin, term_off, term_idx,
-                  term_coef, term_coef32};
+    void* ps[] = {flags,    gm,          gp,         node_of,     partner,      partner_u,   t,
+                  xstar,    line_off,    src_lin,    term_off,    term_idx,     term_coef,   term_coef32,
+                  cv_flags, cv_gm,       cv_partner, cv_line_off, cv_src_lin,   cv_term_off, cv_term_idx,
+                  cv_term_coef, cv_term_coef32};
     for (void* p : ps) if (p) dev_free(p, stream);
     flags = nullptr; gm = gp = node_of = partner = partner_u = nullptr; t = xstar = nullptr;
     line_off = src_lin = term_off = term_idx = nullptr; term_coef = nullptr; term_coef32 = nullptr;
+    cv_flags = nullptr; cv_gm = cv_partner = cv_line_off = cv_src_lin = cv_term_off = cv_term_idx = nullptr;
+    cv_term_coef = nullptr; cv_term_coef32 = nullptr;
+    cv_swap = 0;
 }
 
 void build_geometry(const double* phi, int N, double h, const double origin[3], int layer, double s, Geometry& g,
@@ -425,12 +621,26 @@ void build_geometry(const double* phi, int N, double h, const double origin[3], 
                                                    6.0 + s, g.term_idx, g.term_coef));
     g.term_coef32 = dev_alloc_n<float>(g.n_terms, st);
     BAE_LAUNCH("k_to_float", st, k_to_float<<<grid_for(g.n_terms), 256, 0, st>>>(g.term_coef, g.n_terms, g.term_coef32));
-    // x-planes holding every source (gamma- and D-nodes, or M+ for the
+    // planes holding every source (gamma- and D-nodes, or M+ for the
     // volume term, whose planes lie between) and every gathered node
-    // (gamma- and the partners, one step from gamma-)
-    const long long first = N - rec[I_FIRST], last = rec[I_LAST] - 1;
-    g.plane_lo = (int)std::max(0LL, first - 1);
-    g.plane_hi = (int)std::min((long long)N, last + 2);
+    // (gamma- and the partners, one step from gamma-), along each axis
+    const int slot[3][2] = {{I_FIRST, I_LAST}, {I_FIRSTY, I_LASTY}, {I_FIRSTZ, I_LASTZ}};
+    for (int ax = 0; ax < 3; ++ax) {
+        const long long first = N - rec[slot[ax][0]], last = rec[slot[ax][1]] - 1;
+        g.ext_lo[ax] = (int)std::max(0LL, first - 1);
+        g.ext_hi[ax] = (int)std::min((long long)N, last + 2);
+    }
+    g.plane_lo = g.ext_lo[0];
+    g.plane_hi = g.ext_hi[0];
+    // the axis of fewest planes (by more than a tenth) for the pruned
+    // applies, which transform only the planes of their first axis
+    const char* env = std::getenv("BAE_CONV_AXIS");
+    const bool keep_x = env && (env[0] == 'x' || env[0] == 'X');
+    int sw = 0;
+    if (!direct && !keep_x)
+        for (int ax = 1; ax < 3; ++ax)
+            if (10 * (g.ext_hi[ax] - g.ext_lo[ax]) < 9 * (g.ext_hi[sw] - g.ext_lo[sw])) sw = ax;
+    if (sw) build_view(g, sw, src_mask, sc, st);
 }
 
 }  // namespace bae

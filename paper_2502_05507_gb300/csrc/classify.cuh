@@ -32,6 +32,27 @@ struct Geometry {
     // x-planes [plane_lo, plane_hi) contain every source and every node the
     // gather and the reconstruction read
     int plane_lo = 0, plane_hi = 0;
+    // the same range along each axis (0: x, 1: y, 2: z)
+    int ext_lo[3] = {0, 0, 0}, ext_hi[3] = {0, 0, 0};
+
+    // Swapped view of the pruned applies: the convolution skips the zero
+    // planes of its first axis only, so it runs on the grid with axis 0
+    // swapped with the axis of fewest planes (cv_swap, see swap_axes; 0: no
+    // swap, where x is already the narrowest, for the direct formulation and
+    // when BAE_CONV_AXIS=x). cv_lo/cv_hi is the plane range along that axis;
+    // the recipe, the flags and the gathered indices below are the
+    // geometry's in the swapped layout (null when cv_swap == 0).
+    int cv_swap = 0;
+    int cv_lo = 0, cv_hi = 0;
+    uint8_t* cv_flags = nullptr;
+    int* cv_gm = nullptr;
+    int* cv_partner = nullptr;
+    int* cv_line_off = nullptr;
+    int* cv_src_lin = nullptr;
+    int* cv_term_off = nullptr;
+    int* cv_term_idx = nullptr;
+    double* cv_term_coef = nullptr;
+    float* cv_term_coef32 = nullptr;
 
     SrcRecipe recipe() const {
         SrcRecipe r;
@@ -41,6 +62,19 @@ struct Geometry {
         r.term_idx = term_idx;
         r.term_coef = term_coef;
         r.term_coef32 = term_coef32;
+        r.wide = layer == BAE_LAYER_DIRECT;
+        return r;
+    }
+    // the recipe of the swapped view (the plain one when cv_swap == 0)
+    SrcRecipe cv_recipe() const {
+        if (!cv_swap) return recipe();
+        SrcRecipe r;
+        r.line_off = cv_line_off;
+        r.src_lin = cv_src_lin;
+        r.term_off = cv_term_off;
+        r.term_idx = cv_term_idx;
+        r.term_coef = cv_term_coef;
+        r.term_coef32 = cv_term_coef32;
         r.wide = layer == BAE_LAYER_DIRECT;
         return r;
     }

@@ -135,4 +135,17 @@ inline int ilog2(long long v) {
     return r;
 }
 
+// Linear index of node x = (i*N + j)*N + k of an N^3 grid after swapping
+// grid axis 0 with axis sw (sw = 0: unchanged, 1: i <-> j, 2: i <-> k).
+// The swap is its own inverse. The lattice Green's function of the
+// 7-point operator is symmetric under permutations of the axes, so a
+// convolution may run on the swapped grid and its output be read back at
+// swapped indices.
+__host__ __device__ __forceinline__ long long swap_axes(long long x, int sw, int N) {
+    if (sw == 0) return x;
+    const long long nn = (long long)N * N;
+    const long long i = x / nn, j = (x / N) % N, k = x % N;
+    return sw == 1 ? (j * N + i) * N + k : (k * N + j) * N + i;
+}
+
 }  // namespace bae

@@ -49,6 +49,10 @@ struct ConvArgs {
     const double* f = nullptr;
     const uint8_t* flags = nullptr;
     double scale = 1.0;
+    // the grid of this apply has axes 0 and f_swap swapped (swap_axes):
+    // rec, flags and the output v are in the swapped layout, f in the
+    // caller's, so f is read at swap_axes(x) (0: no swap)
+    int f_swap = 0;
     // work buffers (per batch item): A = N*N*(N+1), B = N*2N*(N+1) complex
     cplx_t<T>* A = nullptr;
     cplx_t<T>* B = nullptr;
@@ -125,10 +129,12 @@ void mask_bit(const uint8_t* flags, long long n, uint8_t bit, uint8_t* out, cuda
 void scatter_gm(const double* q, long long q_stride, const int* gm, long long n, int nb, double* u, long long n3,
                 cudaStream_t st);
 
-// u[b][x] = (nplus(x) ? add[b][x] + v[b][x] : 0) over the N^3 grid
+// u[b][x] = (nplus(x) ? add[b][x] + v[b][x'] : 0) over the N^3 grid, with
+// x' = swap_axes(x, v_swap, N): v and add in the swapped layout, u and
+// flags in the grid's
 template <typename T>
 void volume_combine(const T* v, const double* add, const uint8_t* flags, long long n3, int nbatch,
-                    double* u, cudaStream_t st);
+                    double* u, cudaStream_t st, int v_swap = 0, int N = 0);
 
 // out[i] = nearest double-float of in[i]
 void to_dsf(const double* in, long long n, dsf* out, cudaStream_t st);

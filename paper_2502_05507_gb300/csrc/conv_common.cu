@@ -146,11 +146,17 @@ __global__ void k_scatter_gm(const double* q, long long q_stride, const int* __r
 }
 
 template <typename T>
-__global__ void k_volume_combine(const T* v, const double* add, const uint8_t* flags, long long n3, double* u) {
+__global__ void k_volume_combine(const T* v, const double* add, const uint8_t* flags, long long n3, double* u,
+                                 int v_swap, int N) {
     const int b = blockIdx.y;
     for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n3; x += (long long)gridDim.x * blockDim.x) {
         const bool np = (flags[x] & 3) != 0;   // M+ or gamma-
-        u[b * n3 + x] = np ? (add ? add[b * n3 + x] : 0.0) + (double)v[b * n3 + x] : 0.0;
+        double r = 0.0;
+        if (np) {
+            const long long xv = swap_axes(x, v_swap, N);
+            r = (add ? add[b * n3 + xv] : 0.0) + (double)v[b * n3 + xv];
+        }
+        u[b * n3 + x] = r;
     }
 }
 
@@ -235,9 +241,10 @@ void scatter_gm(const double* q, long long q_stride, const int* gm, long long n,
 
 template <typename T>
 void volume_combine(const T* v, const double* add, const uint8_t* flags, long long n3, int nbatch,
-                    double* u, cudaStream_t st) {
+                    double* u, cudaStream_t st, int v_swap, int N) {
+    BAE_REQUIRE(v_swap == 0 || (long long)N * N * N == n3, BAE_ERR_INVALID_ARG, "volume_combine: N must match n3");
     dim3 grid(ceil_div(n3, 256) < 2432 ? ceil_div(n3, 256) : 2432, nbatch);
-    BAE_LAUNCH("k_volume_combine", st, k_volume_combine<T><<<grid, 256, 0, st>>>(v, add, flags, n3, u));
+    BAE_LAUNCH("k_volume_combine", st, k_volume_combine<T><<<grid, 256, 0, st>>>(v, add, flags, n3, u, v_swap, N));
 }
 
 template <typename T>
@@ -263,8 +270,10 @@ template void closure_gather<double>(const double*, long long, const int*, const
 template void direct_rows<float, float>(const float*, long long, const double*, long long, const int*, long long, const int*, const int*, const double*, long long, long long, int, const int*, float*, long long, cudaStream_t);
 template void direct_rows<float, double>(const float*, long long, const double*, long long, const int*, long long, const int*, const int*, const double*, long long, long long, int, const int*, double*, long long, cudaStream_t);
 template void direct_rows<double, double>(const double*, long long, const double*, long long, const int*, long long, const int*, const int*, const double*, long long, long long, int, const int*, double*, long long, cudaStream_t);
-template void volume_combine<float>(const float*, const double*, const uint8_t*, long long, int, double*, cudaStream_t);
-template void volume_combine<double>(const double*, const double*, const uint8_t*, long long, int, double*, cudaStream_t);
+template void volume_combine<float>(const float*, const double*, const uint8_t*, long long, int, double*, cudaStream_t,
+                                     int, int);
+template void volume_combine<double>(const double*, const double*, const uint8_t*, long long, int, double*,
+                                      cudaStream_t, int, int);
 template void widen<float>(const float*, long long, double*, cudaStream_t);
 template void widen<double>(const double*, long long, double*, cudaStream_t);
 

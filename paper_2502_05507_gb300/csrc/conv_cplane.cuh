@@ -75,8 +75,8 @@ __global__ void __launch_bounds__(CPlaneGeo<T, L>::PT) k_cplane_fwd(ConvArgs<T> 
                     T va = (T)0.0, vb = (T)0.0;
                     if (act && m < R2 / 2) {
                         const long long xa = la * N + n, xb = lb * N + n;
-                        va = (a.flags[xa] & 1) ? (T)(a.scale * f[xa]) : (T)0.0;
-                        vb = (a.flags[xb] & 1) ? (T)(a.scale * f[xb]) : (T)0.0;
+                        va = (a.flags[xa] & 1) ? (T)(a.scale * f[swap_axes(xa, a.f_swap, N)]) : (T)0.0;
+                        vb = (a.flags[xb] & 1) ? (T)(a.scale * f[swap_axes(xb, a.f_swap, N)]) : (T)0.0;
                     }
                     v[m] = cmake<C>(va, vb);
                 }

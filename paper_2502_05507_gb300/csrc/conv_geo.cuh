@@ -130,7 +130,8 @@ template <typename T, int L> struct PlaneGeo {
 // D-nodes, outside M+, so the two never share a node)
 template <typename T>
 __device__ __forceinline__ T volume_or_zero(const ConvArgs<T>& a, int b, long long x) {
-    if (a.f && (a.flags[x] & 1)) return (T)(a.scale * a.f[(long long)b * a.N * a.N * a.N + x]);
+    if (a.f && (a.flags[x] & 1))
+        return (T)(a.scale * a.f[(long long)b * a.N * a.N * a.N + swap_axes(x, a.f_swap, a.N)]);
     return (T)0.0;
 }
 

@@ -112,8 +112,8 @@ __device__ __forceinline__ void kpass_fwd_tile(const ConvArgs<T>& a, int bx, int
             const int nn = m < S / 2 ? n : ((BOX && n > N) ? 2 * N - n : -1);
             if (active && nn >= 0) {
                 const long long xa = la * N + nn, xb = lb * N + nn;
-                va = (a.flags[xa] & 1) ? (T)(a.scale * f[xa]) : (T)0;
-                vb = (a.flags[xb] & 1) ? (T)(a.scale * f[xb]) : (T)0;
+                va = (a.flags[xa] & 1) ? (T)(a.scale * f[swap_axes(xa, a.f_swap, N)]) : (T)0;
+                vb = (a.flags[xb] & 1) ? (T)(a.scale * f[swap_axes(xb, a.f_swap, N)]) : (T)0;
                 if (m >= S / 2) {
                     va = -va;
                     vb = -vb;
@@ -441,8 +441,8 @@ __global__ void __launch_bounds__(512) k_plane_fwd(ConvArgs<T> a) {
                     T va = (T)0.0, vb = (T)0.0;
                     if (act && m < R2 / 2) {
                         const long long xa = la * N + n, xb = lb * N + n;
-                        va = (a.flags[xa] & 1) ? (T)(a.scale * f[xa]) : (T)0.0;
-                        vb = (a.flags[xb] & 1) ? (T)(a.scale * f[xb]) : (T)0.0;
+                        va = (a.flags[xa] & 1) ? (T)(a.scale * f[swap_axes(xa, a.f_swap, N)]) : (T)0.0;
+                        vb = (a.flags[xb] & 1) ? (T)(a.scale * f[swap_axes(xb, a.f_swap, N)]) : (T)0.0;
                     }
                     v[m] = cmake<C>(va, vb);
                 }
