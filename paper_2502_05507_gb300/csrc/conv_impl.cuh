@@ -166,7 +166,14 @@ __global__ void __launch_bounds__(Geo<T, L, V>::KT, Geo<T, L, V>::MINB_KF) k_kpa
 // ----------------------------------------------------- column passes (j, i)
 enum ColMode { COL_FWD_J = 0, COL_CONV_I = 1, COL_INV_J = 2 };
 
-template <typename T, int L, int MODE, bool BOX, int V>
+// MP > 0 (the i pass of a narrow plane range, !BOX): the nonzero rows
+// [p0, p1) lie in rows [lo0, lo0 + TH MP) with lo0 = p0 rounded down to a
+// multiple of TH, so the pencil is transformed shifted down by lo0: slot m
+// of thread t holds row lo0 + t + TH m, only slots m < MP are loaded (the
+// first DFT drops the zero slots) and only they are stored back (the last
+// DFT computes only those). A circular convolution commutes with the
+// shift, so the rows written are the same as without it.
+template <typename T, int L, int MODE, bool BOX, int V, int MP = 0>
 __device__ __forceinline__ void colpass_tile(const ConvArgs<T>& a, int bx, int by, int bz) {
     using C = cplx_t<T>;
     using G = Geo<T, L, V>;
@@ -175,9 +182,11 @@ __device__ __forceinline__ void colpass_tile(const ConvArgs<T>& a, int bx, int b
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* xch = reinterpret_cast<C*>(smem_raw);   // XL * W
 
+    static_assert(MP == 0 || (MODE == COL_CONV_I && !BOX && MP <= S / 2), "narrow i pass only");
     const int b = bz;
     if (a.active && !a.active[b]) return;
     const int o = MODE == COL_CONV_I ? by : a.plane_lo() + by;   // jj, or i
+    const int lo0 = MP > 0 ? (a.plane_lo() / TH) * TH : 0;       // row shift of a narrow i pass
     const int c = threadIdx.x % W;
     const int t = threadIdx.x / W;
     const int col = bx * W + c;             // kk (column 0 holds kk = 0 and N)
@@ -209,6 +218,15 @@ __device__ __forceinline__ void colpass_tile(const ConvArgs<T>& a, int bx, int b
             v[s] = x;
         }
         PL::inv(v, xch, c, W, t, a.tw);
+    } else if constexpr (MP > 0) {
+        // n-layout load of the rows lo0 + t + TH m, m < MP
+#pragma unroll
+        for (int m = 0; m < S; ++m) {
+            const int nn = lo0 + t + TH * m;
+            const bool live = m < MP && nn >= a.plane_lo() && nn < a.plane_hi();
+            v[m] = (ok && live) ? in[nn * stride] : zero;
+        }
+        PL::template fwd_nz<MP>(v, xch, c, W, t, a.tw);
     } else {
         // n-layout load of the N nonzero rows (BOX: and their negated
         // mirrors in the upper half)
@@ -279,12 +297,13 @@ __device__ __forceinline__ void colpass_tile(const ConvArgs<T>& a, int bx, int b
         }
         PL::inv(v, xch, c, W, t, a.tw);
     }
-    // n-layout store of the first N rows
+    // n-layout store of the first N rows (narrow i pass: of the rows
+    // lo0 + t + TH m, m < MP)
     if (ok) {
 #pragma unroll
         for (int m = 0; m < S; ++m) {
-            const int n = t + TH * m;
-            if (m < S / 2 && (MODE != COL_CONV_I || (n >= a.plane_lo() && n < a.plane_hi())))
+            const int n = lo0 + t + TH * m;
+            if (m < (MP > 0 ? MP : S / 2) && (MODE != COL_CONV_I || (n >= a.plane_lo() && n < a.plane_hi())))
                 out[n * stride] = v[m];
         }
     }
@@ -293,7 +312,7 @@ __device__ __forceinline__ void colpass_tile(const ConvArgs<T>& a, int bx, int b
 // tiles (column block, line, right-hand side), column blocks fastest:
 // strided over a grid of resident CTAs (PERSIST) or one per CTA of the grid
 // (column blocks, lines, right-hand sides)
-template <typename T, int L, int MODE, bool BOX = false, int V = 0, bool PERSIST = false>
+template <typename T, int L, int MODE, bool BOX = false, int V = 0, bool PERSIST = false, int MP = 0>
 __global__ void __launch_bounds__(Geo<T, L, V>::CT, Geo<T, L, V>::minb_col(MODE)) k_colpass(ConvArgs<T> a) {
     wait_prior_grid();   // results of the previous kernel on the stream
     if constexpr (PERSIST) {
@@ -304,11 +323,11 @@ __global__ void __launch_bounds__(Geo<T, L, V>::CT, Geo<T, L, V>::minb_col(MODE)
         const long long ntiles = per_b * a.nbatch;
         for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
             const long long rem = tile % per_b;
-            colpass_tile<T, L, MODE, BOX, V>(a, (int)(rem % ncb), (int)(rem / ncb), (int)(tile / per_b));
+            colpass_tile<T, L, MODE, BOX, V, MP>(a, (int)(rem % ncb), (int)(rem / ncb), (int)(tile / per_b));
             __syncthreads();   // the next tile reuses the shared memory
         }
     } else {
-        colpass_tile<T, L, MODE, BOX, V>(a, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z);
+        colpass_tile<T, L, MODE, BOX, V, MP>(a, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z);
     }
 }
 
@@ -657,6 +676,93 @@ dim3 persist_grid(long long ntiles, K kernel, int threads, size_t smem) {
     return dim3((unsigned)(ntiles < 1 ? 1 : (ntiles < cap ? ntiles : cap)));
 }
 
+// ------------------------------------------------------ narrow i pass
+// The i pass where the planes [p0, p1) span few blocks of TH rows: the
+// instantiation with MP slots (colpass_tile) for the smallest MP in {1, 2,
+// 4} below S / 2 that covers them. float32 and double-float at L >= 128;
+// the kernels are compiled in conv_inarrow_*.cu. Returns false (nothing
+// launched) where no narrow instantiation covers the span.
+template <typename T, int L> struct NarrowI {
+    static constexpr bool value = (std::is_same<T, float>::value || std::is_same<T, dsf>::value) && L >= 128;
+};
+
+template <typename T, int L, int V, bool PERSIST, int MP>
+void launch_narrow_mp(const ConvArgs<T>& a, dim3 grid, size_t smem, cudaStream_t st) {
+    auto k = k_colpass<T, L, COL_CONV_I, false, V, PERSIST, MP>;
+    static const bool configured = [&]() {
+        BAE_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        return true;
+    }();
+    (void)configured;
+    if constexpr (PERSIST) {   // a grid of this kernel's resident CTAs over every tile
+        using G = Geo<T, L, V>;
+        constexpr int N = L / 2;
+        grid = persist_grid((long long)ceil_div(N, G::W) * 2 * N * a.nbatch, k, G::CT, smem);
+    }
+    BAE_LAUNCH(kname<T>("conv_i.f32", "conv_i.f64", "conv_i.df64"), st,
+               launch_pdl(k, grid, Geo<T, L, V>::CT, smem, st, a));
+}
+
+}  // namespace
+
+// external linkage: explicitly instantiated once, in conv_inarrow_*.cu.
+// Every schedule's i pass takes the same transform (narrow or not) for the
+// same plane range, so the schedules stay bit-identical to one another.
+template <typename T, int L, int V, bool PERSIST>
+bool launch_conv_i_narrow(const ConvArgs<T>& a, dim3 grid, size_t smem, cudaStream_t st) {
+    constexpr int TH = Geo<T, L, V>::TH, S = Geo<T, L, V>::S;
+    const int lo0 = (a.plane_lo() / TH) * TH;
+    const int span = ceil_div(a.plane_hi() - lo0, TH);   // slots holding rows of [p0, p1)
+    if (span <= 1 && 1 < S / 2) {
+        launch_narrow_mp<T, L, V, PERSIST, 1>(a, grid, smem, st);
+        return true;
+    }
+    if constexpr (2 < S / 2) {
+        if (span <= 2) {
+            launch_narrow_mp<T, L, V, PERSIST, 2>(a, grid, smem, st);
+            return true;
+        }
+    }
+    if constexpr (4 < S / 2) {
+        if (span <= 4) {
+            launch_narrow_mp<T, L, V, PERSIST, 4>(a, grid, smem, st);
+            return true;
+        }
+    }
+    return false;
+}
+
+// the narrow kernels are compiled once, in conv_inarrow_*.cu
+#define BAE_NARROW_I(T, L, V, P) \
+    extern template bool launch_conv_i_narrow<T, L, V, P>(const ConvArgs<T>&, dim3, size_t, cudaStream_t);
+BAE_NARROW_I(float, 128, 0, false)
+BAE_NARROW_I(float, 256, 0, false)
+BAE_NARROW_I(float, 256, 1, false)
+BAE_NARROW_I(float, 512, 0, false)
+BAE_NARROW_I(float, 512, 1, false)
+BAE_NARROW_I(float, 128, 0, true)
+BAE_NARROW_I(float, 256, 0, true)
+BAE_NARROW_I(float, 512, 0, true)
+BAE_NARROW_I(dsf, 128, 0, false)
+BAE_NARROW_I(dsf, 256, 0, false)
+BAE_NARROW_I(dsf, 512, 0, false)
+BAE_NARROW_I(dsf, 128, 0, true)
+BAE_NARROW_I(dsf, 256, 0, true)
+BAE_NARROW_I(dsf, 512, 0, true)
+#undef BAE_NARROW_I
+
+namespace {
+
+// the i pass (not the finite box): narrow where it can be
+template <typename T, int L, int V, bool PERSIST = false>
+void launch_conv_i(const ConvArgs<T>& a, dim3 grid, size_t smem, cudaStream_t st) {
+    if constexpr (NarrowI<T, L>::value && (V == 0 || (HasAlt<T, L>::value && !PERSIST))) {
+        if (!a.box && launch_conv_i_narrow<T, L, V, PERSIST>(a, grid, smem, st)) return;
+    }
+    BAE_LAUNCH(kname<T>("conv_i.f32", "conv_i.f64", "conv_i.df64"), st,
+               launch_pdl(k_colpass<T, L, COL_CONV_I, false, V, PERSIST>, grid, Geo<T, L, V>::CT, smem, st, a));
+}
+
 // The five pass kernels with the launch geometry of variant V: one tile per
 // CTA, or (PERSIST) the persistent instantiations on grids of resident CTAs.
 template <typename T, int L, int V, bool BOX = false, bool PERSIST = false>
@@ -689,9 +795,12 @@ void launch_passes(const ConvArgs<T>& a, cudaStream_t st) {
     BAE_LAUNCH(BOX ? kname<T>("conv_box_jfwd.f32", "conv_box_jfwd.f64", "conv_box_jfwd.df64")
                    : kname<T>("conv_jfwd.f32", "conv_jfwd.f64", "conv_jfwd.df64"), st,
                launch_pdl(jf, gj, G::CT, smem_c, st, a));
-    BAE_LAUNCH(BOX ? kname<T>("conv_box_i.f32", "conv_box_i.f64", "conv_box_i.df64")
-                   : kname<T>("conv_i.f32", "conv_i.f64", "conv_i.df64"), st,
-               launch_pdl(ci, gi, G::CT, smem_c, st, a));
+    if constexpr (!BOX)
+        launch_conv_i<T, L, V, PERSIST>(a, gi, smem_c, st);
+    else
+        BAE_LAUNCH(BOX ? kname<T>("conv_box_i.f32", "conv_box_i.f64", "conv_box_i.df64")
+                       : kname<T>("conv_i.f32", "conv_i.f64", "conv_i.df64"), st,
+                   launch_pdl(ci, gi, G::CT, smem_c, st, a));
     BAE_LAUNCH(kname<T>("conv_jinv.f32", "conv_jinv.f64", "conv_jinv.df64"), st,
                launch_pdl(ji, gji, G::CT, smem_c, st, a));
     BAE_LAUNCH(kname<T>("conv_kinv.f32", "conv_kinv.f64", "conv_kinv.df64"), st,
@@ -739,8 +848,7 @@ void launch_sched(const ConvArgs<T>& a, cudaStream_t st, int sched) {
                    launch_pdl(k_plane_fwd<T, L>, dim3(np, nb), PG::PT, PG::SMEM, st, a));
     else if constexpr (CPlaneGeo<T, L>::USE)
         cplane_launch<T, L>(a, st, false);
-    BAE_LAUNCH(kname<T>("conv_i.f32", "conv_i.f64", "conv_i.df64"), st,
-               launch_pdl(k_colpass<T, L, COL_CONV_I>, dim3(ceil_div(N, G::W), 2 * N, nb), G::CT, smem_c, st, a));
+    launch_conv_i<T, L, 0>(a, dim3(ceil_div(N, G::W), 2 * N, nb), smem_c, st);
     if constexpr (PG::FITS)
         BAE_LAUNCH(kname<T>("conv_plane_inv.f32", "conv_plane_inv.f64", "conv_plane_inv.df64"), st,
                    launch_pdl(k_plane_inv<T, L>, dim3(np, nb), PG::PT, PG::SMEM, st, a));

@@ -188,6 +188,32 @@ __device__ __forceinline__ void rdft_zhi(C* v) {
     }
 }
 
+// rdft of v[0..R) whose inputs v[M..R) are zero, 1 <= M (the shifted
+// narrow inputs of the i pass): the butterflies with a zero operand are
+// dropped (same values as rdft up to the sign of zeros)
+template <int R, bool INV, int M, typename C>
+__device__ __forceinline__ void rdft_zpre(C* v) {
+    if constexpr (M >= R) {
+        rdft<R, INV>(v);
+    } else if constexpr (M == 1) {
+#pragma unroll
+        for (int k = 1; k < R; ++k) v[k] = v[0];
+    } else if constexpr (R == 4) {   // M == 2 (M == 3: the full DFT)
+        if constexpr (M == 2) rdft_zhi<4, INV>(v);
+        else rdft<4, INV>(v);
+    } else {
+        C e[R / 2], o[R / 2];
+#pragma unroll
+        for (int i = 0; i < R / 2; ++i) {
+            e[i] = v[2 * i];
+            o[i] = v[2 * i + 1];
+        }
+        rdft_zpre<R / 2, INV, (M + 1) / 2>(e);
+        rdft_zpre<R / 2, INV, M / 2>(o);
+        Bflies<R, INV, C, 0>::run(e, o, v);
+    }
+}
+
 template <int L> struct Factors;
 template <> struct Factors<16> { static constexpr int R1 = 4, R2 = 4; };
 template <> struct Factors<32> { static constexpr int R1 = 4, R2 = 8; };
@@ -204,11 +230,13 @@ template <> struct Factors<512> { static constexpr int R1 = 16, R2 = 32; };
 // n-layout -> k-layout (forward, or inverse when INV: then from the
 // n-layout of X to the k-layout of the inverse transform, same steps with
 // conjugate twiddles). tw: exp(-2 pi i m / L), m < L. ZHI: the input rows
-// n >= L/2 are zero (v[m] = 0 for m >= R2 / 2).
-template <int L, bool INV, bool ZHI = false, typename C>
+// n >= L/2 are zero (v[m] = 0 for m >= R2 / 2); NZ > 0: only v[m < NZ] are
+// nonzero (rows n < R1 NZ).
+template <int L, bool INV, bool ZHI = false, int NZ = 0, typename C>
 __device__ __forceinline__ void fft_n2k(C* v, C* xch, int base, int sk, int sn, int t, const C* __restrict__ tw) {
     constexpr int R1 = Factors<L>::R1, R2 = Factors<L>::R2, Q = R2 / R1;
-    if constexpr (ZHI) rdft_zhi<R2, INV>(v);          // v[k2] = Y[t][k2]
+    if constexpr (NZ > 0) rdft_zpre<R2, INV, NZ>(v);  // only v[m < NZ] nonzero
+    else if constexpr (ZHI) rdft_zhi<R2, INV>(v);     // v[k2] = Y[t][k2]
     else rdft<R2, INV>(v);
 #pragma unroll
     for (int k2 = 1; k2 < R2; ++k2) {
@@ -276,6 +304,11 @@ struct Plan2 {
     __device__ __forceinline__ static void fwd(C* v, C* xch, int base, int es, int t, const C* __restrict__ tw) {
         fft_n2k<L, false, ZHI>(v, xch, base, es == 1 ? R1 + 1 : R1 * es, es, t, tw);
     }
+    // forward transform whose slots m >= NZ are zero
+    template <int NZ, typename C>
+    __device__ __forceinline__ static void fwd_nz(C* v, C* xch, int base, int es, int t, const C* __restrict__ tw) {
+        fft_n2k<L, false, false, NZ>(v, xch, base, es == 1 ? R1 + 1 : R1 * es, es, t, tw);
+    }
     template <typename C>
     __device__ __forceinline__ static void inv(C* v, C* xch, int base, int es, int t, const C* __restrict__ tw) {
         fft_k2n<L, true>(v, xch, base, es == 1 ? R1 + 1 : R1 * es, es, t, tw);
@@ -303,8 +336,13 @@ struct Plan3_512 {
 
     template <bool ZHI, typename C>
     __device__ __forceinline__ static void fwd(C* v, C* xch, int base, int es, int t, const C* __restrict__ tw) {
-        if constexpr (ZHI) rdft_zhi<8, false>(v);       // v[k3]
-        else rdft<8, false>(v);
+        fwd_nz<ZHI ? 4 : 8>(v, xch, base, es, t, tw);
+    }
+    // forward transform whose slots m >= NZ are zero
+    template <int NZ, typename C>
+    __device__ __forceinline__ static void fwd_nz(C* v, C* xch, int base, int es, int t, const C* __restrict__ tw) {
+        if constexpr (NZ == 4) rdft_zhi<8, false>(v);   // v[k3]
+        else rdft_zpre<8, false, NZ>(v);
 #pragma unroll
         for (int k3 = 1; k3 < 8; ++k3) v[k3] = cmul(v[k3], ldg_c(tw + t * k3));
 #pragma unroll
@@ -381,8 +419,13 @@ struct Plan3_256 {
 
     template <bool ZHI, typename C>
     __device__ __forceinline__ static void fwd(C* v, C* xch, int base, int es, int t, const C* __restrict__ tw) {
-        if constexpr (ZHI) rdft_zhi<8, false>(v);       // v[k3]
-        else rdft<8, false>(v);
+        fwd_nz<ZHI ? 4 : 8>(v, xch, base, es, t, tw);
+    }
+    // forward transform whose slots m >= NZ are zero
+    template <int NZ, typename C>
+    __device__ __forceinline__ static void fwd_nz(C* v, C* xch, int base, int es, int t, const C* __restrict__ tw) {
+        if constexpr (NZ == 4) rdft_zhi<8, false>(v);   // v[k3]
+        else rdft_zpre<8, false, NZ>(v);
 #pragma unroll
         for (int k3 = 1; k3 < 8; ++k3) v[k3] = cmul(v[k3], ldg_c(tw + t * k3));
 #pragma unroll

@@ -11,7 +11,9 @@ results must equal the oracle's as before:
 - bae_boundary_apply on a z-flat torus (x <-> z) and a y-flat ellipsoid
   (x <-> y), both layers, float64/double-float 1e-12 and float32 2e-6
   against the oracle's FFT convolution, after a full-grid apply of another
-  density has filled every plane;
+  density has filled every plane; at N = 64 the float32 and double-float
+  i passes run their narrow (shifted, few-slot) transform, on a thin disk
+  the one-slot one;
 - mixed-precision solves of both geometries equal the oracle's u on M+ to
   1e-8, and the torus solve equals the unswapped one (BAE_CONV_AXIS=x) to
   1e-9."""
@@ -101,8 +103,11 @@ def test_conv_axis_environment_keeps_x(ctx, monkeypatch):
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-6), ("df64", 1e-12)])
 @pytest.mark.parametrize("layer", ["double", "single"])
-@pytest.mark.parametrize("make", [lambda: W.torus_helmholtz(32, kappa2=10.0), lambda: flat_ellipsoid(32)])
+@pytest.mark.parametrize("make", [lambda: W.torus_helmholtz(32, kappa2=10.0), lambda: flat_ellipsoid(32),
+                                  lambda: W.torus_helmholtz(64, kappa2=10.0), lambda: flat_ellipsoid(64)])
 def test_swapped_boundary_apply_matches_oracle(ctx, make, layer, precision, tol):
+    # at N = 64 the float32 and double-float i passes also take the narrow
+    # (shifted) transform: the planes span at most four blocks of its rows
     import torch
     P = make()
     prob = _problem(ctx, P, layer)
@@ -119,7 +124,36 @@ def test_swapped_boundary_apply_matches_oracle(ctx, make, layer, precision, tol)
     prob.close()
 
 
-@pytest.mark.parametrize("make", [lambda: W.torus_helmholtz(32, kappa2=10.0), lambda: flat_ellipsoid(32, 1.0)])
+def thin_disk(N=64, kappa2=0.0):
+    """Ellipsoid (0.7, 0.6, 0.04) centred at z = 0.37: at N = 64 its source
+    planes [40, 48) fill one block of eight rows, so the float32 and
+    double-float i passes (eight threads per line) run their one-slot
+    transform."""
+    return W._make(f"disk_N{N}", W.cell_centred(N),
+                   lambda x, y, z: (x / 0.7) ** 2 + (y / 0.6) ** 2 + ((z - 0.37) / 0.04) ** 2 - 1.0,
+                   kappa2, "double", lambda x, y, z: W.sol_exp_sum(x, y, z, kappa2))
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-6), ("df64", 1e-12)])
+@pytest.mark.parametrize("layer", ["double", "single"])
+def test_one_slot_i_pass_matches_oracle(ctx, layer, precision, tol):
+    import torch
+    P = thin_disk(64, 1.0)
+    prob = _problem(ctx, P, layer)
+    ax, lo, hi = prob.conv_planes()
+    assert ax == 2 and lo >= 40 and hi <= 48, (ax, lo, hi)
+    cls = OG.classify(P.phi, P.grid.h, P.grid.origin)
+    T = OL.LGFTable(P.grid.N, P.kappa2 * P.grid.h ** 2)
+    q = W.random_density(cls.gm_idx.size, seed=43)
+    Aq = prob.boundary_apply(torch.from_numpy(q).cuda(), precision).cpu().numpy()
+    ref = OP.fft_convolve(OP.source_density(cls, q, layer), table=T)
+    ref_A = OS.closure_apply(cls, ref.reshape(-1))
+    assert np.max(np.abs(Aq - ref_A)) <= tol * np.max(np.abs(ref))
+    prob.close()
+
+
+@pytest.mark.parametrize("make", [lambda: W.torus_helmholtz(32, kappa2=10.0), lambda: flat_ellipsoid(32, 1.0),
+                                  lambda: thin_disk(64, 1.0)])
 def test_swapped_solve_matches_oracle(ctx, make):
     import torch
     P = make()
@@ -156,3 +190,40 @@ def test_swapped_solve_equals_unswapped(ctx, monkeypatch):
         a, b = out[("auto", prec)], out[("x", prec)]
         assert np.max(np.abs(a - b)) <= 1e-9 * np.max(np.abs(b)), prec
     os.environ.pop("BAE_CONV_AXIS", None)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "df64"])
+@pytest.mark.parametrize("N", [64, 128])
+def test_narrow_i_pass_same_in_every_schedule(ctx, N, precision):
+    # every schedule the autotuner can pick runs the same i-pass transform
+    # for a given plane range, so a batch item and the same right-hand side
+    # alone stay bit-identical whichever schedule each size picked
+    import torch
+    from paper_2502_05507_gb300 import set_conv_schedule
+    P = W.torus_helmholtz(N, kappa2=10.0)
+    prob = _problem(ctx, P)
+    cls = OG.classify(P.phi, P.grid.h, P.grid.origin)
+    q = torch.from_numpy(W.random_density(cls.gm_idx.size, seed=44)).cuda()
+    out = {}
+    try:
+        for name in ("passes", "passes_alt", "persist", "plane"):
+            set_conv_schedule(name)
+            out[name] = prob.boundary_apply(q, precision).cpu().numpy()
+    finally:
+        set_conv_schedule("auto")
+    # the double-float cluster plane kernels (N >= 128) transform their k
+    # and j lines with the two-level plan, the passes with the three-level
+    # one: the same convolution in another rounding order
+    same_plan = precision == "fp32" or N < 128
+    for name, a in out.items():
+        if name == "plane" and not same_plan:
+            assert np.max(np.abs(a - out["passes"])) <= 1e-12 * np.max(np.abs(out["passes"])), name
+        else:
+            assert np.array_equal(a, out["passes"]), name
+    if N == 64:
+        T = OL.LGFTable(N, P.kappa2 * P.grid.h ** 2)
+        ref = OP.fft_convolve(OP.source_density(cls, q.cpu().numpy(), "double"), table=T)
+        ref_A = OS.closure_apply(cls, ref.reshape(-1))
+        tol = 2e-6 if precision == "fp32" else 1e-12
+        assert np.max(np.abs(out["passes"] - ref_A)) <= tol * np.max(np.abs(ref))
+    prob.close()
