@@ -192,7 +192,11 @@ DF64_OPS_PER_FLOP = 7.0
 # workloads (profiles/); a kernel or plane range changed since its capture
 # is dropped from this table (its traffic is then reported as null). Keyed
 # by (kernel, N, right-hand sides per launch).
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # conv_i_narrow_batched32_torus_N128.md: 494.0 MB per 32-right-hand-side
+    # launch, scaled by 2 less one extra read of the 8.6 MB spectrum octant
+    ("conv_i.f32", 128, 64): 2 * 494.0e6 - 8.59e6,
+}
 
 
 def roofline_for(name, ms_total, launches, n, n_gm, hbm, hbm_kind, npl=None, nb=1):
