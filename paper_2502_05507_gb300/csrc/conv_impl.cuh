@@ -288,11 +288,18 @@ __device__ __forceinline__ void colpass_tile(const ConvArgs<T>& a, int bx, int b
                 }
             }
         } else {
+            // slot s holds frequency k = t + k0(s), k0(s) = kidx(0, s) a
+            // compile-time multiple of TH, so the octant row min(k, L - k)
+            // is t + k0 when k0 < N and (L - k0) - t otherwise (k0 + t <= N
+            // in the first case, k0 >= N in the second): one per-thread
+            // offset and compile-time terms instead of a select per slot
+            constexpr int NN = N1 * N1;
+            const int tn = t * NN;
 #pragma unroll
             for (int s = 0; s < S; ++s) {
-                const int k = PL::kidx(t, s);
-                const int ii = k <= N ? k : L - k;
-                v[s] = cscale(v[s], g[(long long)ii * N1 * N1]);
+                const int k0 = PL::kidx(0, s);
+                const T gv = k0 < N ? g[tn + k0 * NN] : g[(L - k0) * NN - tn];
+                v[s] = cscale(v[s], gv);
             }
         }
         PL::inv(v, xch, c, W, t, a.tw);
