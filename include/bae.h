@@ -122,6 +122,10 @@ typedef struct bae_stats {
     int    applies_fp32;     /* float32 potential applies in this call            */
     double rel_residual;     /* final ||b - A q|| / ||b||, A applied in float64   */
     double ms_total;         /* wall time of the call on the context stream       */
+    int64_t h2d_bytes;       /* bytes of this right-hand side's inputs (f, g) the
+                                call copied from host memory (0: device inputs) */
+    int64_t d2h_bytes;       /* bytes of its outputs (u, density) it copied to
+                                host memory (0: device outputs)                 */
 } bae_stats;
 
 /* ------------------------------------------------------------- utilities */
@@ -376,6 +380,11 @@ int bae_box_particular(bae_problem* prob, int precision, const double* f, double
  * (bae_problem_unknowns() doubles)
  * and u (N^3 doubles: the discrete solution on N+ = M+ u gamma-, 0 elsewhere);
  * either may be NULL. opts may be NULL (defaults); stats may be NULL.
+ * Only the values of f on M+ are read (eq. [ps] takes chi_{M+} f); from
+ * host memory the call copies the box of planes that holds M+ (the planes
+ * with a source, one plane of margin, along each axis) and reports the
+ * bytes in stats->h2d_bytes. Inputs and outputs may be host or device
+ * memory independently.
  * BAE_ERR_NOT_CONVERGED leaves valid outputs and stats. */
 int bae_solve(bae_problem* prob, const double* f, const double* g, const bae_options* opts,
               double* density, double* u, bae_stats* stats);

@@ -46,7 +46,8 @@ class Options(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("refinements", ctypes.c_int), ("applies_fp64", ctypes.c_int),
-                ("applies_fp32", ctypes.c_int), ("rel_residual", ctypes.c_double), ("ms_total", ctypes.c_double)]
+                ("applies_fp32", ctypes.c_int), ("rel_residual", ctypes.c_double), ("ms_total", ctypes.c_double),
+                ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

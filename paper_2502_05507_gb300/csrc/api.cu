@@ -938,18 +938,40 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
         P->pre.pending = true;
     }
 
-    // stage host inputs
+    // stage host inputs. The solve reads f only on M+ (the volume source
+    // chi_{M+} f and the finiteness check), which lies inside the box of
+    // planes [ext_lo, ext_hi) along each axis (gamma- encloses M+): one 3D
+    // copy of that box per right-hand side; the rest of the device copy is
+    // never read.
     const double* d_f = f;
     const double* d_g = g;
+    long long h2d_rhs = 0;   // bytes copied per right-hand side
     if (!is_device_ptr(f)) {
         double* p = P->ws().in_f.need((long long)nb * n3);
-        BAE_CUDA(cudaMemcpyAsync(p, f, (size_t)nb * n3 * sizeof(double), cudaMemcpyHostToDevice, st));
+        const Geometry& G = P->geo;
+        const int NN = G.N;
+        const cudaExtent ext = make_cudaExtent((size_t)(G.ext_hi[2] - G.ext_lo[2]) * sizeof(double),
+                                               (size_t)(G.ext_hi[1] - G.ext_lo[1]), (size_t)(G.ext_hi[0] - G.ext_lo[0]));
+        for (int b = 0; b < nb; ++b) {
+            cudaMemcpy3DParms cp = {};
+            cp.srcPtr = make_cudaPitchedPtr(const_cast<double*>(f) + (long long)b * n3, (size_t)NN * sizeof(double),
+                                            (size_t)NN * sizeof(double), (size_t)NN);
+            cp.dstPtr = make_cudaPitchedPtr(p + (long long)b * n3, (size_t)NN * sizeof(double),
+                                            (size_t)NN * sizeof(double), (size_t)NN);
+            cp.srcPos = make_cudaPos((size_t)G.ext_lo[2] * sizeof(double), (size_t)G.ext_lo[1], (size_t)G.ext_lo[0]);
+            cp.dstPos = cp.srcPos;
+            cp.extent = ext;
+            cp.kind = cudaMemcpyHostToDevice;
+            BAE_CUDA(cudaMemcpy3DAsync(&cp, st));
+        }
+        h2d_rhs += (long long)ext.width * ext.height * ext.depth;
         d_f = p;
     }
     if (!is_device_ptr(g)) {
         double* p = P->ws().in_g.need((long long)nb * ng);
         BAE_CUDA(cudaMemcpyAsync(p, g, (size_t)nb * ng * sizeof(double), cudaMemcpyHostToDevice, st));
         d_g = p;
+        h2d_rhs += (long long)ng * sizeof(double);
     }
     // f on M+ and g must be finite: the flag is read with ||b|| below (one
     // host read; non-finite inputs only make the discarded b non-finite)
@@ -958,7 +980,10 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
     kr_nonfinite(d_f, (long long)nb * n3, P->geo.flags, n3, d_bad, st);
     kr_nonfinite(d_g, (long long)nb * ng, nullptr, 1, d_bad, st);
     std::vector<bae_stats> st_local(nb);
-    for (auto& s : st_local) std::memset(&s, 0, sizeof(s));
+    for (auto& s : st_local) {
+        std::memset(&s, 0, sizeof(s));
+        s.h2d_bytes = h2d_rhs;
+    }
 
     // particular solution u_p = G_h[chi_{M+} f] and b = g - Phi u_p. Mixed
     // precision needs u_p only for the first inner right-hand side, so there
@@ -1149,6 +1174,8 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
     for (int b = 0; b < nb; ++b) {
         st_local[b].rel_residual = relres[b];
         st_local[b].ms_total = ms;
+        st_local[b].d2h_bytes = (u_host ? n3 * (long long)sizeof(double) : 0) +
+                                (q_host ? (long long)n * (long long)sizeof(double) : 0);
         if (!(relres[b] <= o.tol) && bn2[b] > 0) rc = BAE_ERR_NOT_CONVERGED;
     }
     if (stats)

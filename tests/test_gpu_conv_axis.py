@@ -227,3 +227,45 @@ def test_narrow_i_pass_same_in_every_schedule(ctx, N, precision):
         tol = 2e-6 if precision == "fp32" else 1e-12
         assert np.max(np.abs(out["passes"] - ref_A)) <= tol * np.max(np.abs(ref))
     prob.close()
+
+
+def _source_box(cls):
+    """Per axis the planes holding a source (gamma-, D-nodes), one plane of
+    margin each side: the box that holds M+."""
+    N = cls.N
+    src = cls.gm | cls.dnode
+    box = []
+    for ax in range(3):
+        other = tuple(a for a in range(3) if a != ax)
+        idx = np.flatnonzero(np.any(src, axis=other))
+        box.append((max(0, idx.min() - 1), min(N, idx.max() + 2)))
+    return box
+
+
+@pytest.mark.parametrize("make,nrhs", [(lambda: W.torus_helmholtz(64, kappa2=10.0), 1), (lambda: flat_ellipsoid(32), 2)])
+def test_host_f_copies_the_box_of_m_plus(ctx, make, nrhs):
+    # a solve reads f only on M+: from host memory the library copies the
+    # box of planes that holds M+ (and reports the bytes), with the same
+    # result as from device memory
+    import torch
+    P = make()
+    prob = _problem(ctx, P)
+    cls = OG.classify(P.phi, P.grid.h, P.grid.origin)
+    box = _source_box(cls)
+    inside = np.zeros_like(cls.inside)
+    inside[box[0][0]:box[0][1], box[1][0]:box[1][1], box[2][0]:box[2][1]] = True
+    assert not np.any(cls.inside & ~inside)
+    xs = prob.boundary_points()
+    f = np.stack([P.f() * (1.0 + 0.1 * k) for k in range(nrhs)])
+    g = np.stack([P.g_at(xs) * (1.0 + 0.1 * k) for k in range(nrhs)])
+    qd, ud, sd = prob.solve_batched(torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda(), tol=1e-10,
+                                    precision="mixed")
+    qh, uh, sh = prob.solve_batched(f, g, tol=1e-10, precision="mixed")
+    assert np.array_equal(qh, qd.cpu().numpy()) and np.array_equal(uh, ud.cpu().numpy())
+    vol = int(np.prod([hi - lo for lo, hi in box]))
+    N = P.grid.N
+    for k in range(nrhs):
+        assert sd[k]["h2d_bytes"] == 0 and sd[k]["d2h_bytes"] == 0
+        assert sh[k]["h2d_bytes"] == 8 * (vol + xs.shape[0]), (sh[k], vol)
+        assert sh[k]["d2h_bytes"] == 8 * (N ** 3 + qh.shape[1])
+    prob.close()
