@@ -404,6 +404,11 @@ ConvArgs<T> conv_args(bae_problem* P, int nb, bool pruned = false) {
     if (pruned) {
         a.p0 = view ? P->geo.cv_lo : P->geo.plane_lo;
         a.p1 = view ? P->geo.cv_hi : P->geo.plane_hi;
+        // the line range along the grid's second axis (y, or x when x and
+        // y are swapped), rounded out to whole line pairs
+        const int ax2 = (view && P->geo.cv_swap == 1) ? 0 : 1;
+        a.q0 = P->geo.ext_lo[ax2] & ~1;
+        a.q1 = std::min(N, (P->geo.ext_hi[ax2] + 1) & ~1);
     }
     a.rec = view ? P->geo.cv_recipe() : P->geo.recipe();
     a.flags = view ? P->geo.cv_flags : P->geo.flags;

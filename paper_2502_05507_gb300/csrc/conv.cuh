@@ -74,6 +74,22 @@ struct ConvArgs {
     bool no_tune = false;
     __host__ __device__ int plane_lo() const { return p1 > 0 ? p0 : 0; }
     __host__ __device__ int plane_hi() const { return p1 > 0 ? p1 : N; }
+    // lines [q0, q1) along the second axis (even bounds) hold every source
+    // and every node read back (q1 == 0: all N). The k passes transform
+    // only the line pairs of the planes [p0, p1) inside it; the forward j
+    // pass reads the other rows as zeros and the inverse one does not write
+    // them. The plane-fused kernels transform every line.
+    int q0 = 0, q1 = 0;
+    __host__ __device__ int line_lo() const { return q1 > 0 ? q0 : 0; }
+    __host__ __device__ int line_hi() const { return q1 > 0 ? q1 : N; }
+    __host__ __device__ int pairs_per_plane() const { return (line_hi() - line_lo()) / 2; }
+    // line pairs of the k passes, and the first line of pair gp (pairs
+    // numbered plane by plane)
+    __host__ __device__ long long npairs() const { return (long long)(plane_hi() - plane_lo()) * pairs_per_plane(); }
+    __host__ __device__ long long pair_line(long long gp) const {
+        const int npq = pairs_per_plane();
+        return (long long)(plane_lo() + gp / npq) * N + line_lo() + 2 * (gp % npq);
+    }
 };
 
 template <typename T>

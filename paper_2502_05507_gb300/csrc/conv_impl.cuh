@@ -66,9 +66,10 @@ __device__ __forceinline__ void kpass_fwd_tile(const ConvArgs<T>& a, int bx, int
     if (a.active && !a.active[b]) return;   // whole CTA: no barrier is skipped
     const int t = threadIdx.x % TH;
     const int p = threadIdx.x / TH;
-    const long long pair = (long long)a.plane_lo() * (N / 2) + (long long)bx * G::P + p;
-    const bool active = pair < (long long)a.plane_hi() * (N / 2);
-    const long long la = 2 * pair, lb = la + 1;
+    const long long gp0 = (long long)bx * G::P;   // the CTA's first line pair
+    const long long np = a.npairs();
+    const bool active = gp0 + p < np;
+    const long long la = a.pair_line(gp0 + p), lb = la + 1;
     T* r = rho + p * G::RS;
 
     C v[S];
@@ -78,21 +79,26 @@ __device__ __forceinline__ void kpass_fwd_tile(const ConvArgs<T>& a, int bx, int
         __syncthreads();
         {
             // the sources of the CTA's lines are one contiguous range of the
-            // recipe (its line pairs are consecutive): every thread of the CTA
-            // takes sources of the range, so each chain of dependent loads
-            // (offsets, node, terms, density) runs once, not once per line
-            const long long l0 = 2 * ((long long)a.plane_lo() * (N / 2) + (long long)bx * G::P);
-            const long long l1 = 2 * min((long long)a.plane_lo() * (N / 2) + (long long)(bx + 1) * G::P,
-                                         (long long)a.plane_hi() * (N / 2));
-            if (l0 < l1) {
+            // recipe (from its first line to its last; across a plane
+            // boundary the lines between are outside [q0, q1) and hold no
+            // source): every thread of the CTA takes sources of the range,
+            // so each chain of dependent loads (offsets, node, terms,
+            // density) runs once, not once per line
+            const long long gp1 = min(gp0 + (long long)G::P, np);
+            if (gp0 < gp1) {
+                const long long l0 = a.pair_line(gp0), l1 = a.pair_line(gp1 - 1) + 2;
                 const double* q =
                     a.q + (long long)b * a.q_stride + (a.q_row ? (long long)a.q_row[b] * a.q_row_stride : 0);
                 const float* q32 = a.q32 ? a.q32 + (long long)b * a.q32_stride : nullptr;
                 const int s0 = a.rec.line_off[l0], s1 = a.rec.line_off[l1];
+                const int npq = a.pairs_per_plane(), jlo = a.line_lo(), jhi = a.line_hi();
                 for (int s = s0 + (int)threadIdx.x; s < s1; s += (int)blockDim.x) {
                     const int lin = a.rec.src_lin[s];
-                    const int rel = (int)(lin / N - l0);   // line within the CTA: pair rel / 2, half rel % 2
-                    rho[(rel >> 1) * G::RS + (rel & 1) * N + (lin % N)] = source_value<T>(a.rec, s, q, q32);
+                    const int line = lin / N, ip = line / N, jl = line % N;
+                    // pair within the CTA, half of the pair
+                    const long long loc = (long long)(ip - a.plane_lo()) * npq + (jl - jlo) / 2 - gp0;
+                    if (jl >= jlo && jl < jhi && loc >= 0 && loc < G::P)
+                        rho[loc * G::RS + (jl & 1) * N + (lin % N)] = source_value<T>(a.rec, s, q, q32);
                 }
             }
         }
@@ -151,8 +157,7 @@ __global__ void __launch_bounds__(Geo<T, L, V>::KT, Geo<T, L, V>::MINB_KF) k_kpa
     wait_prior_grid();   // results of the previous kernel on the stream
     if constexpr (PERSIST) {
         constexpr int N = L / 2;
-        const long long gkx =
-            ((long long)(a.plane_hi() - a.plane_lo()) * (N / 2) + Geo<T, L, V>::P - 1) / Geo<T, L, V>::P;
+        const long long gkx = (a.npairs() + Geo<T, L, V>::P - 1) / Geo<T, L, V>::P;
         const long long ntiles = gkx * a.nbatch;
         for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
             kpass_fwd_tile<T, L, BOX, V>(a, (int)(tile % gkx), (int)(tile / gkx));
@@ -234,8 +239,10 @@ __device__ __forceinline__ void colpass_tile(const ConvArgs<T>& a, int bx, int b
         for (int m = 0; m < S; ++m) {
             const int n = t + TH * m;
             const int nn = m < S / 2 ? n : ((BOX && n > N) ? 2 * N - n : -1);
-            // rows outside [p0, p1) are zero planes (not even written)
-            const bool live = nn >= 0 && (MODE != COL_CONV_I || (nn >= a.plane_lo() && nn < a.plane_hi()));
+            // rows outside [p0, p1) (i pass) or [q0, q1) (j pass) are zero
+            // (not even written)
+            const bool live = nn >= 0 && (MODE != COL_CONV_I || (nn >= a.plane_lo() && nn < a.plane_hi())) &&
+                              (MODE != COL_FWD_J || (nn >= a.line_lo() && nn < a.line_hi()));
             C x = (ok && live) ? in[nn * stride] : zero;
             if (BOX && m >= S / 2) x = cmake<C>(-x.x, -x.y);
             v[m] = x;
@@ -310,7 +317,8 @@ __device__ __forceinline__ void colpass_tile(const ConvArgs<T>& a, int bx, int b
 #pragma unroll
         for (int m = 0; m < S; ++m) {
             const int n = lo0 + t + TH * m;
-            if (m < (MP > 0 ? MP : S / 2) && (MODE != COL_CONV_I || (n >= a.plane_lo() && n < a.plane_hi())))
+            if (m < (MP > 0 ? MP : S / 2) && (MODE != COL_CONV_I || (n >= a.plane_lo() && n < a.plane_hi())) &&
+                (MODE != COL_INV_J || (n >= a.line_lo() && n < a.line_hi())))
                 out[n * stride] = v[m];
         }
     }
@@ -352,9 +360,9 @@ __device__ __forceinline__ void kpass_inv_tile(const ConvArgs<T>& a, int bx, int
     if (a.active && !a.active[b]) return;
     const int t = threadIdx.x % TH;
     const int p = threadIdx.x / TH;
-    const long long pair = (long long)a.plane_lo() * (N / 2) + (long long)bx * G::P + p;
-    const bool active = pair < (long long)a.plane_hi() * (N / 2);
-    const long long la = 2 * pair, lb = la + 1;
+    const long long gp = (long long)bx * G::P + p;
+    const bool active = gp < a.npairs();
+    const long long la = a.pair_line(gp), lb = la + 1;
     const C* A = a.A + (long long)b * N * N * N1;
 
     C v[S];
@@ -388,8 +396,7 @@ __global__ void __launch_bounds__(Geo<T, L, V>::KT, Geo<T, L, V>::MINB) k_kpass_
     wait_prior_grid();   // results of the previous kernel on the stream
     if constexpr (PERSIST) {
         constexpr int N = L / 2;
-        const long long gkx =
-            ((long long)(a.plane_hi() - a.plane_lo()) * (N / 2) + Geo<T, L, V>::P - 1) / Geo<T, L, V>::P;
+        const long long gkx = (a.npairs() + Geo<T, L, V>::P - 1) / Geo<T, L, V>::P;
         const long long ntiles = gkx * a.nbatch;
         for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
             kpass_inv_tile<T, L, V>(a, (int)(tile % gkx), (int)(tile / gkx));
@@ -781,7 +788,7 @@ void launch_passes(const ConvArgs<T>& a, cudaStream_t st) {
     const size_t smem_c = (size_t)G::XL * G::W * sizeof(C);
     const int nb = a.nbatch;
     const int np = a.plane_hi() - a.plane_lo();   // x-planes holding sources or read outputs
-    const int gkx = ceil_div((long long)np * N / 2, G::P);
+    const int gkx = ceil_div(a.npairs(), G::P);   // k-line pairs in [p0, p1) x [q0, q1)
     const int ncb = ceil_div(N, G::W);           // column 0 also holds kk = N
     auto kf = k_kpass_fwd<T, L, BOX, V, PERSIST>;
     auto jf = k_colpass<T, L, COL_FWD_J, BOX, V, PERSIST>;
