@@ -429,7 +429,8 @@ def run_ours(args, rank, world, dev):
     # through the public API with host buffers: phi, f and g copied in and
     # u and the densities copied out by the library inside every step (the
     # library copies the box of f that holds M+, the only part a solve
-    # reads; the bytes below are what it reports having copied)
+    # reads, and the same box of u, writing the zeros around it on the host;
+    # the bytes below are what it reports having copied)
     pinned = [torch.from_numpy(f_h).pin_memory(), torch.from_numpy(g_h).pin_memory(),
               torch.from_numpy(P0.phi).pin_memory(), torch.empty(f_h.shape, dtype=torch.float64).pin_memory(),
               torch.empty((nrhs, n_gm), dtype=torch.float64).pin_memory()]
@@ -450,7 +451,8 @@ def run_ours(args, rank, world, dev):
                   "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": len(e2e_ms),
                   "host_buffers": "pinned",
                   "host_input_bytes": int(phi_pin.nbytes + f_pin.nbytes + g_pin.nbytes),
-                  "note": "f is copied only in the box of planes that holds M+ (the library reports the bytes)"}
+                  "note": "the library copies f and u only in the box of planes that holds N+ and writes u's "
+                          "zeros around it on host threads (it reports the bytes it copied)"}
 
     # --------------------------------------------------- secondary configs
     if not args.no_extra:

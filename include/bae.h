@@ -383,8 +383,10 @@ int bae_box_particular(bae_problem* prob, int precision, const double* f, double
  * Only the values of f on M+ are read (eq. [ps] takes chi_{M+} f); from
  * host memory the call copies the box of planes that holds M+ (the planes
  * with a source, one plane of margin, along each axis) and reports the
- * bytes in stats->h2d_bytes. Inputs and outputs may be host or device
- * memory independently.
+ * bytes in stats->h2d_bytes. Likewise u, which is 0 outside N+: into host
+ * memory the call copies that box and writes the zeros around it with
+ * host threads while the device solves (stats->d2h_bytes). Inputs and
+ * outputs may be host or device memory independently.
  * BAE_ERR_NOT_CONVERGED leaves valid outputs and stats. */
 int bae_solve(bae_problem* prob, const double* f, const double* g, const bae_options* opts,
               double* density, double* u, bae_stats* stats);

@@ -12,6 +12,7 @@
 #include <map>
 #include <memory>
 #include <string>
+#include <thread>
 #include <type_traits>
 #include <vector>
 
@@ -901,6 +902,50 @@ struct HostArg {
     double* out = nullptr;
 };
 
+// Zeros of a host output u (nb right-hand sides of N^3 values) outside the
+// box [lo, hi) of every right-hand side, written by host threads while the
+// device solves. The solution is 0 outside N+, which the box holds, so only
+// the box is copied from the device. The destructor waits for the threads.
+class HostZeroFill {
+public:
+    HostZeroFill(double* u, int nb, int N, const int lo[3], const int hi[3]) {
+        const unsigned hc = std::thread::hardware_concurrency();
+        const int nt = (int)std::max(1u, std::min(8u, hc / 2));
+        for (int w = 0; w < nt; ++w)
+            th_.emplace_back([=]() {
+                const long long n3 = (long long)N * N * N, nn = (long long)N * N;
+                for (long long it = w; it < (long long)nb * N; it += nt) {   // item: (b, i)
+                    const long long b = it / N;
+                    const int i = (int)(it % N);
+                    double* plane = u + b * n3 + (long long)i * nn;
+                    if (i < lo[0] || i >= hi[0]) {
+                        std::memset(plane, 0, (size_t)nn * sizeof(double));
+                        continue;
+                    }
+                    for (int j = 0; j < N; ++j) {
+                        double* line = plane + (long long)j * N;
+                        if (j < lo[1] || j >= hi[1]) {
+                            std::memset(line, 0, (size_t)N * sizeof(double));
+                        } else {
+                            std::memset(line, 0, (size_t)lo[2] * sizeof(double));
+                            std::memset(line + hi[2], 0, (size_t)(N - hi[2]) * sizeof(double));
+                        }
+                    }
+                }
+            });
+    }
+    ~HostZeroFill() { join(); }
+    void join() {
+        for (auto& t : th_)
+            if (t.joinable()) t.join();
+    }
+    HostZeroFill(const HostZeroFill&) = delete;
+    HostZeroFill& operator=(const HostZeroFill&) = delete;
+
+private:
+    std::vector<std::thread> th_;
+};
+
 int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const bae_options* opts_in,
                double* density, double* u, bae_stats* stats) {
     bae_options o;
@@ -989,6 +1034,11 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
         std::memset(&s, 0, sizeof(s));
         s.h2d_bytes = h2d_rhs;
     }
+    // a host u: its zeros outside the box of N+ are written on the host
+    // while the device works; only the box is copied back at the end
+    const bool u_host = u && !is_device_ptr(u);
+    std::unique_ptr<HostZeroFill> zero_fill;
+    if (u_host) zero_fill.reset(new HostZeroFill(u, nb, P->geo.N, P->geo.ext_lo, P->geo.ext_hi));
 
     // particular solution u_p = G_h[chi_{M+} f] and b = g - Phi u_p. Mixed
     // precision needs u_p only for the first inner right-hand side, so there
@@ -1159,13 +1209,31 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
 
     // outputs: u = u_p + K q on N+ (v_last holds the sum when mixed), density q
     bool q_host = density && !is_device_ptr(density);
-    bool u_host = u && !is_device_ptr(u);
+    long long d2h_u = 0;   // bytes of u copied per right-hand side
     if (u) {
         double* du = u_host ? P->ws().out_u.need((long long)nb * n3) : u;
         volume_combine<double>(v_last, direct ? nullptr : up, P->geo.flags, n3, nb, du, st, swap_of(P, true),
                                P->geo.N);
         if (direct) scatter_gm(q, n, P->geo.gm, ng, nb, du, n3, st);   // u on gamma- is the unknown there
-        if (u_host) BAE_CUDA(cudaMemcpyAsync(u, du, (size_t)nb * n3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        if (u_host) {   // the box that holds N+, one 3D copy per right-hand side
+            const Geometry& G = P->geo;
+            const size_t NN = (size_t)G.N;
+            const cudaExtent ext = make_cudaExtent((size_t)(G.ext_hi[2] - G.ext_lo[2]) * sizeof(double),
+                                                   (size_t)(G.ext_hi[1] - G.ext_lo[1]),
+                                                   (size_t)(G.ext_hi[0] - G.ext_lo[0]));
+            for (int b = 0; b < nb; ++b) {
+                cudaMemcpy3DParms cp = {};
+                cp.srcPtr = make_cudaPitchedPtr(du + (long long)b * n3, NN * sizeof(double), NN * sizeof(double), NN);
+                cp.dstPtr = make_cudaPitchedPtr(u + (long long)b * n3, NN * sizeof(double), NN * sizeof(double), NN);
+                cp.srcPos = make_cudaPos((size_t)G.ext_lo[2] * sizeof(double), (size_t)G.ext_lo[1],
+                                         (size_t)G.ext_lo[0]);
+                cp.dstPos = cp.srcPos;
+                cp.extent = ext;
+                cp.kind = cudaMemcpyDeviceToHost;
+                BAE_CUDA(cudaMemcpy3DAsync(&cp, st));
+            }
+            d2h_u = (long long)ext.width * ext.height * ext.depth;
+        }
     }
     if (density) {
         if (q_host) BAE_CUDA(cudaMemcpyAsync(density, q, (size_t)nb * n * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1173,14 +1241,14 @@ int solve_impl(bae_problem* P, int nb, const double* f, const double* g, const b
     }
     BAE_CUDA(cudaEventRecord(P->ctx->ev1, st));
     BAE_CUDA(cudaStreamSynchronize(st));
+    if (zero_fill) zero_fill->join();   // the zeros outside the box are in place
     float ms = 0.f;
     BAE_CUDA(cudaEventElapsedTime(&ms, P->ctx->ev0, P->ctx->ev1));
     int rc = BAE_OK;
     for (int b = 0; b < nb; ++b) {
         st_local[b].rel_residual = relres[b];
         st_local[b].ms_total = ms;
-        st_local[b].d2h_bytes = (u_host ? n3 * (long long)sizeof(double) : 0) +
-                                (q_host ? (long long)n * (long long)sizeof(double) : 0);
+        st_local[b].d2h_bytes = d2h_u + (q_host ? (long long)n * (long long)sizeof(double) : 0);
         if (!(relres[b] <= o.tol) && bn2[b] > 0) rc = BAE_ERR_NOT_CONVERGED;
     }
     if (stats)

@@ -245,8 +245,10 @@ def _source_box(cls):
 @pytest.mark.parametrize("make,nrhs", [(lambda: W.torus_helmholtz(64, kappa2=10.0), 1), (lambda: flat_ellipsoid(32), 2)])
 def test_host_f_copies_the_box_of_m_plus(ctx, make, nrhs):
     # a solve reads f only on M+: from host memory the library copies the
-    # box of planes that holds M+ (and reports the bytes), with the same
-    # result as from device memory
+    # box of planes that holds M+ (and reports the bytes); u is 0 outside
+    # N+, so into host memory it copies the same box and writes the zeros
+    # around it on the host (the host u starts uninitialised). Same results
+    # as with device memory.
     import torch
     P = make()
     prob = _problem(ctx, P)
@@ -267,5 +269,5 @@ def test_host_f_copies_the_box_of_m_plus(ctx, make, nrhs):
     for k in range(nrhs):
         assert sd[k]["h2d_bytes"] == 0 and sd[k]["d2h_bytes"] == 0
         assert sh[k]["h2d_bytes"] == 8 * (vol + xs.shape[0]), (sh[k], vol)
-        assert sh[k]["d2h_bytes"] == 8 * (N ** 3 + qh.shape[1])
+        assert sh[k]["d2h_bytes"] == 8 * (vol + qh.shape[1])
     prob.close()
