@@ -909,8 +909,10 @@ struct HostArg {
 class HostZeroFill {
 public:
     HostZeroFill(double* u, int nb, int N, const int lo[3], const int hi[3]) {
+        // up to 8 threads (half the host's), one per ~4 MB of the array
         const unsigned hc = std::thread::hardware_concurrency();
-        const int nt = (int)std::max(1u, std::min(8u, hc / 2));
+        const long long work = (long long)nb * N * N * N / (512LL * 1024);
+        const int nt = (int)std::max(1LL, std::min<long long>({8LL, (long long)(hc / 2), work}));
         for (int w = 0; w < nt; ++w)
             th_.emplace_back([=]() {
                 const long long n3 = (long long)N * N * N, nn = (long long)N * N;

@@ -507,7 +507,8 @@ void build_view(Geometry& g, int sw, int src_mask, Scratch& sc, cudaStream_t st)
     int* smap = sc.get<int>(n3);
     BAE_CUDA(cudaMemsetAsync(smap, 0xff, n3 * sizeof(int), st));
     BAE_LAUNCH("k_src_map", st, k_src_map<<<grid_for(g.n_src), 256, 0, st>>>(g.src_lin, (int)g.n_src, smap));
-    int* off_src = sc.get<int>(nl + 1);
+    g.cv_line_off = dev_alloc_n<int>(nl + 1, st);   // per-line source counts, then their scan
+    int* off_src = g.cv_line_off;
     int* off_term = sc.get<int>(nl + 1);
     int* info = sc.get<int>(I_COUNT);
     BAE_LAUNCH("k_view_count", st,
@@ -515,8 +516,6 @@ void build_view(Geometry& g, int sw, int src_mask, Scratch& sc, cudaStream_t st)
                                                              off_term));
     // blocks 0 and 1 scan the two counts (the other two arrays are not read)
     BAE_LAUNCH("k_scan_lines", st, k_scan_lines<<<2, 1024, 0, st>>>(off_src, off_term, off_src, off_term, (int)nl, info));
-    g.cv_line_off = off_src;
-    sc.ptrs.erase(std::find(sc.ptrs.begin(), sc.ptrs.end(), static_cast<void*>(off_src)));   // kept
     g.cv_src_lin = dev_alloc_n<int>(g.n_src, st);
     g.cv_term_off = dev_alloc_n<int>(g.n_src + 1, st);
     int* vorig = sc.get<int>(std::max(1LL, g.n_src));
