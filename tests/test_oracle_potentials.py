@@ -190,3 +190,27 @@ def test_box_particular_route_equals_fd():
     assert np.max(np.abs(r.u[m] - u_fd[m])) <= 1e-11 * np.max(np.abs(u_fd[m]))
     r0 = S.solve(P.phi, P.grid.h, P.grid.origin, P.f(), P.g_at, P.kappa2, tol=1e-13, potential="fft")
     assert np.max(np.abs(r.q - r0.q)) > 1e-6 * np.max(np.abs(r0.q))   # the densities differ
+
+
+@pytest.mark.parametrize("s", [0.0, 0.5])
+@pytest.mark.parametrize("perm", [(1, 0, 2), (2, 1, 0)])
+def test_lattice_convolution_commutes_with_axis_swaps(s, perm):
+    # The GPU convolution may run on the grid with two axes swapped and be
+    # read back through the swap: that rests on G_s being symmetric under
+    # permutations of the axes, so that G * (rho o P) = (G * rho) o P. The
+    # plain lattice sum on the original grid, with G by quadrature of eq.
+    # [lgf_bessel] at each signed, unsorted offset (no symmetry assumed), is
+    # compared with the FFT route on the swapped grid read back at the
+    # swapped node.
+    N = 12
+    rng = np.random.default_rng(7)
+    rho = np.zeros((N, N, N))
+    idx = rng.integers(2, N - 2, size=(24, 3))
+    rho[idx[:, 0], idx[:, 1], idx[:, 2]] = rng.standard_normal(24)
+    T = lgf.LGFTable(N, s)
+    v_swapped = pot.fft_convolve(np.ascontiguousarray(np.transpose(rho, perm)), table=T)
+    src = np.argwhere(rho != 0)
+    for m in rng.integers(0, N, size=(5, 3)):
+        direct = sum(rho[tuple(x)] * lgf.lgf_entry(tuple(int(v) for v in m - x), s) for x in src)
+        mp = tuple(int(m[a]) for a in perm)   # node m seen on the swapped grid
+        assert v_swapped[mp] == pytest.approx(direct, rel=1e-11, abs=1e-13)
