@@ -227,8 +227,12 @@ def roofline_for(name, ms_total, launches, n, n_gm, hbm, hbm_kind, npl=None, nb=
     f_hbm = a / hbm
     a_alu = flops / t / 1e12
     f_alu = a_alu / (2 * FP32_LANE_PEAK_T)
+    traffic = NCU_TRAFFIC.get((name, n, nb))
     both = {"algorithmic_bytes": nbytes, "GBps": a, "frac_hbm": f_hbm, "hbm_peak": hbm,
-            "hbm_peak_kind": hbm_kind + " HBM copy bandwidth", "traffic_bytes": NCU_TRAFFIC.get((name, n, nb)),
+            "hbm_peak_kind": hbm_kind + " HBM copy bandwidth", "traffic_bytes": traffic,
+            # ncu DRAM bytes over the same launch time
+            "traffic_GBps": traffic / t / 1e9 if traffic else None,
+            "traffic_frac_hbm": traffic / t / 1e9 / hbm if traffic else None,
             "fp32_flops_5LlogL": flops, "fp32_TFLOPs_5LlogL": a_alu, "frac_fp32": f_alu}
     if f_alu > f_hbm:
         return {**common, "bound": "alu", "achieved": a_alu, "peak": 2 * FP32_LANE_PEAK_T,

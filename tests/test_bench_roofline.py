@@ -30,6 +30,8 @@ def test_roofline_reports_the_binding_resource():
     assert r["frac"] == pytest.approx(a_alu / (2 * bench.FP32_LANE_PEAK_T))
     assert r["frac_hbm"] == pytest.approx(a_hbm / hbm)
     assert r["frac"] > r["frac_hbm"]
+    tr = bench.NCU_TRAFFIC[("conv_i.f32", 128, 64)]
+    assert r["traffic"] == tr and r["traffic_GBps"] == pytest.approx(tr / (t_ms / 1000) / 1e9)
     # the same bytes with far fewer flops per byte: HBM is the bound
     r2 = bench.roofline_for("conv_jfwd.f32", 0.18 * 40, 40, n, 1000, hbm, "measured", npl, nb)
     assert r2["bound"] == "hbm" and r2["frac"] == pytest.approx(r2["frac_hbm"])
